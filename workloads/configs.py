@@ -1,0 +1,101 @@
+"""The synthetic workloads: unit-cell mesh, lattice, wavenumbers and incident
+directions of the five benchmark configurations.
+
+Sizes, spacings and frequencies are the ones of the paper's kinds of workload
+(sphere arrays of the scattering study, a cylinder sonic-crystal barrier, a
+3-D lattice of cubes, a mixed request stream).  Speed of sound c = 343 m/s as
+in the numerical examples of the paper.
+"""
+from dataclasses import dataclass, field
+from typing import Callable, List, Tuple
+
+import numpy as np
+
+from .meshes import icosphere, capped_cylinder, cube
+
+SPEED_OF_SOUND = 343.0
+
+
+@dataclass
+class Workload:
+    name: str
+    make_mesh: Callable[[], Tuple[np.ndarray, np.ndarray]]
+    counts: Tuple[int, int, int]           # cells along the lattice vectors
+    lattice: np.ndarray                    # 3x3, row i = lattice vector i (metres)
+    wavenumbers: List[float]               # k = 2 pi f / c
+    directions: np.ndarray                 # R x 3 unit incidence directions
+    rhs_seed: int                          # PCG32 seed of the random test vectors
+    pbem_form: bool = False                # every offset dense (cells too tall for the FMM)
+    n_t: int = 0                           # truncation number (0 = not an FMM workload)
+    notes: str = ""
+
+    @property
+    def dim(self) -> int:
+        return sum(1 for m in self.counts if m > 1) or 1
+
+    def mesh(self):
+        return self.make_mesh()
+
+
+def fibonacci_directions(n: int) -> np.ndarray:
+    """n unit vectors spread uniformly over the sphere (spherical Fibonacci
+    lattice: z_i = 1 - (2 i + 1)/n, golden-angle longitude)."""
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    ga = np.pi * (3.0 - np.sqrt(5.0))
+    rho = np.sqrt(1.0 - z * z)
+    return np.stack([rho * np.cos(ga * i), rho * np.sin(ga * i), z], axis=1)
+
+
+def _freqs_to_k(freqs):
+    return [2.0 * np.pi * f / SPEED_OF_SOUND for f in freqs]
+
+
+_SEED = 220112050
+
+WORKLOADS = {
+    "sphere_row_4": Workload(
+        name="sphere_row_4",
+        make_mesh=lambda: icosphere(2, 0.2),
+        counts=(4, 1, 1),
+        lattice=np.diag([1.0, 1.0, 1.0]),
+        wavenumbers=[2.0],
+        directions=np.array([[1.0, 0.0, 0.0]]),
+        rhs_seed=_SEED + 0,
+        n_t=6,
+        notes="1-D row of 4 rigid spheres r=0.2 m, lattice 1.0 m, 320 triangles per cell, N=1,280, k=2",
+    ),
+    "sonic_crystal_3x20": Workload(
+        name="sonic_crystal_3x20",
+        make_mesh=lambda: capped_cylinder(0.15, 3.0, 20, 29),
+        counts=(3, 20, 1),
+        lattice=np.diag([0.4, 0.4, 3.0]),
+        wavenumbers=_freqs_to_k([100.0 * i for i in range(1, 11)]),
+        directions=np.array([[np.cos(np.pi / 6), np.sin(np.pi / 6), 0.0]]),
+        rhs_seed=_SEED + 1,
+        pbem_form=True,
+        notes="3x20 rigid capped cylinders r=0.15 m h=3.0 m, square lattice 0.4 m, 1,200 triangles per cell, N=72,000",
+    ),
+    "sphere_array_32x32": Workload(
+        name="sphere_array_32x32",
+        make_mesh=lambda: icosphere(2, 0.2),
+        counts=(32, 32, 1),
+        lattice=np.diag([0.6, 0.6, 1.0]),
+        wavenumbers=[4.0],
+        directions=np.array([[1.0, 0.0, 0.0]]),
+        rhs_seed=_SEED + 2,
+        n_t=8,
+        notes="32x32 rigid spheres r=0.2 m, lattice 0.6 m, 320 triangles per cell, N=327,680, k=4",
+    ),
+    "cube_lattice_16x16x4": Workload(
+        name="cube_lattice_16x16x4",
+        make_mesh=lambda: cube(0.3, 6),
+        counts=(16, 16, 4),
+        lattice=np.diag([0.5, 0.5, 0.5]),
+        wavenumbers=_freqs_to_k([200.0 * i for i in range(1, 9)]),
+        directions=fibonacci_directions(64),
+        rhs_seed=_SEED + 3,
+        n_t=12,
+        notes="16x16x4 rigid cubes edge 0.3 m in 0.5 m cells, 432 triangles per cell, N=442,368",
+    ),
+}
