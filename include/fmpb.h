@@ -1,0 +1,260 @@
+/*
+ * fmpb.h -- C ABI of the GB300 finite-periodic fast multipole BEM library.
+ *
+ * Method: Jelich, Zhao, Chen, Marburg, "Fast multipole boundary element
+ * method for the acoustic analysis of finite periodic structures"
+ * (arXiv 2201.12050).  A unit-cell boundary mesh is repeated on a lattice of
+ * M_x x M_y x M_z cells (Sec. 2.2).  The Burton-Miller collocation operator
+ * of a rigid boundary (Sec. 2.1, Eq. (bm) with dp/dn = 0) is applied either
+ *   - in the FMPBEM form S + U K V (Sec. 3.2, Eq. (2dPeriodicFMM)): the
+ *     near-field blocks S_delta (|delta|_inf <= 1), the P2M/L2P tables V_0,
+ *     U_0 shared by all cells and the multilevel block Toeplitz M2L matrix K,
+ *     or
+ *   - in the PBEM form T (Sec. 2.2, Eq. (toeplitzBEM)): one dense n x n block
+ *     per cell offset,
+ * and every block Toeplitz product is evaluated as a zero-padded block
+ * circulant convolution by FFT over the cell grid (Sec. 2.4, Eqs.
+ * (diagonalized), (modifiedFourierTransform1/2); Sec. 3.5, Eq.
+ * (FMPBEMsystem)).
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved doubles (fmpb_c64), the layout of
+ *     torch.complex128 and std::complex<double>.
+ *   - A cell is c = (iz*M_y + iy)*M_x + ix; dof i of cell c has global
+ *     index c*n + i (n = triangles of the unit cell).  Vectors with R
+ *     right-hand sides are RHS-major: element (r, c*n + i) at r*N + c*n + i.
+ *   - Pointer arguments documented "device" must point to memory of the
+ *     current CUDA device; "host" pointers are read before the call returns.
+ *     The caller owns every buffer it passes; the library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls returning device results do not synchronise
+ *     unless documented.  Calls on one operator share its scratch memory
+ *     and must be ordered on one stream.
+ *   - Every call returns a status.  No call aborts, traps or prints.  On
+ *     error the outputs are undefined (except FMPB_ENOCONV, see
+ *     fmpb_solve) and fmpb_last_error() describes the failure.
+ */
+#ifndef FMPB_H
+#define FMPB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMPB_VERSION_MAJOR 0
+#define FMPB_VERSION_MINOR 1
+
+typedef struct { double re, im; } fmpb_c64;
+
+typedef enum {
+  FMPB_OK = 0,
+  FMPB_EINVAL = -1,    /* invalid argument (null pointer, size, option) */
+  FMPB_ENOMEM = -2,    /* device or host allocation failed */
+  FMPB_EMESH = -3,     /* bad mesh: index out of range, degenerate triangle */
+  FMPB_EADMISS = -4,   /* FMM form forced on a cell the expansion cannot separate */
+  FMPB_ENOCONV = -5,   /* GMRES reached maxit before the tolerance */
+  FMPB_ETIMEOUT = -6,  /* a bounded wait expired */
+  FMPB_ENAN = -7,      /* NaN or Inf in an input vector */
+  FMPB_ECUDA = -8      /* a CUDA runtime call failed */
+} fmpb_status;
+
+typedef enum { FMPB_FORM_AUTO = -1, FMPB_FORM_FMM = 0, FMPB_FORM_PBEM = 1 } fmpb_form;
+typedef enum { FMPB_FP64 = 0, FMPB_FP32 = 1, FMPB_BF16 = 2 } fmpb_precision;
+
+/* Finite lattice (Sec. 2.2, Fig. PeriodicArray2d): counts[a] cells along
+ * lattice vector vectors[a] (metres).  counts[a] = 1 for an unused axis. */
+typedef struct {
+  int32_t counts[3];
+  double vectors[3][3];
+} fmpb_lattice;
+
+/* Human-readable description of the last error on the calling thread; valid
+ * until the next library call on that thread.  Never NULL. */
+const char *fmpb_last_error(void);
+/* Library version as (major << 16) | minor. */
+int fmpb_version(void);
+
+/* ------------------------------------------------------------------------
+ * Operator: everything the matrix-vector product needs for one
+ * (unit-cell mesh, lattice, wavenumber), resident on the current device.
+ * ---------------------------------------------------------------------- */
+typedef struct fmpb_operator fmpb_operator;
+
+typedef struct {
+  int form;        /* fmpb_form; AUTO picks FMM when every far cell pair is
+                      separated by more than the two cells' enclosing radii
+                      (the convergence condition of Eq. (greenFMM)), else PBEM */
+  int n_t;         /* truncation number of the FMM form (Eq. (greenFMM)), 1..20;
+                      0 = default 8 */
+  int precision;   /* fmpb_precision of the product; FMPB_FP64 only in this version */
+} fmpb_operator_opts;
+
+typedef struct {
+  int64_t n;             /* triangles (dofs) per cell */
+  int64_t n_cells;       /* M_x M_y M_z */
+  int64_t N;             /* n * n_cells */
+  int32_t dim;           /* lattice axes with more than one cell */
+  int32_t form;          /* fmpb_form actually built */
+  int32_t n_t;           /* truncation number (FMM form), 0 for PBEM */
+  int64_t B;             /* circulant block size: (n_t+1)^2 (FMM) or n (PBEM) */
+  int32_t P[3];          /* padded circulant length per axis, >= 2 M_a - 1 */
+  int64_t F;             /* P[0] P[1] P[2] */
+  int32_t n_near;        /* near offsets stored (3^dim) in the FMM form, else 0 */
+  size_t bytes_device;   /* device memory held by the operator (tables only) */
+} fmpb_operator_info;
+
+/*
+ * Builds the operator on the current device.
+ *   verts  host, nv x 3 doubles: unit-cell vertex coordinates (metres).  The
+ *          mesh origin is the cell's expansion centre.
+ *   tris   host, ntri x 3 int32: vertex indices of each flat triangle, wound
+ *          so that (v1-v0) x (v2-v0) points from the body into the fluid.
+ *   k      wavenumber omega/c > 0 (Eq. (helmholtz)).
+ *   opts   may be NULL (AUTO form, n_t = 8, FP64).
+ * Builds, all on the device: element geometry and quadrature rules; the
+ * offset blocks (all (2M-1)^d offsets in the PBEM form, the 3^d near offsets
+ * in the FMM form) by the collocation quadrature of Eq. (bm); in the FMM
+ * form the P2M/L2P tables (Eqs. (p2m), (l2p)) and the M2L blocks of every
+ * far offset (Eqs. (m2l), (wigner)); finally the FFT of the circulant first
+ * block column over the padded cell grid (Eq. (blockDiagonal)).  The input
+ * arrays are copied; the stream is synchronised before return.
+ * Errors: EINVAL (sizes, k <= 0, options), EMESH (index out of range or
+ * zero-area triangle), EADMISS (FMM forced but not admissible), ENOMEM,
+ * ECUDA.  *out is set only on success and is freed by
+ * fmpb_operator_destroy.
+ */
+fmpb_status fmpb_operator_create(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                                 const fmpb_lattice *lattice, double k,
+                                 const fmpb_operator_opts *opts, void *stream,
+                                 fmpb_operator **out);
+fmpb_status fmpb_operator_get_info(const fmpb_operator *op, fmpb_operator_info *info);
+/* Frees the operator's device memory (synchronises the device first).  NULL is a no-op. */
+void fmpb_operator_destroy(fmpb_operator *op);
+
+/*
+ * Right-hand side of Eq. (bm) for R incident plane waves
+ * p_inc = amp_r exp(i k d_r . x) (Eq. (planewave)):
+ * b_r(x_i) = p_inc(x_i) + (i/k) dp_inc/dn(x_i) at every collocation point.
+ *   dirs  host, R x 3 unit vectors; amps host, R values (NULL = all 1).
+ *   b     device, R x N.
+ */
+fmpb_status fmpb_rhs_plane_wave(const fmpb_operator *op, int R, const double *dirs,
+                                const fmpb_c64 *amps, fmpb_c64 *b, void *stream);
+
+/*
+ * y = A x for R vectors at once, A the collocation operator of the chosen
+ * form (Eq. (FMPBEMsystem) or the PBEM product of Sec. 2.4).
+ *   x, y  device, R x N each, must not overlap.
+ */
+fmpb_status fmpb_matvec(const fmpb_operator *op, int R, const fmpb_c64 *x, fmpb_c64 *y,
+                        void *stream);
+
+typedef struct {
+  double tol;        /* relative residual ||b - A p|| / ||b||; <= 0 selects 1e-8 */
+  int restart;       /* GMRES restart length m, 1..200; 0 selects 30 */
+  int maxit;         /* total iteration cap per RHS; 0 selects 1000 */
+  int timeout_ms;    /* wall-clock cap for the whole call; 0 = none */
+} fmpb_solve_opts;
+
+typedef struct {
+  int iters;            /* Arnoldi iterations used */
+  int converged;        /* 1 if the estimated residual met tol */
+  double relres_est;    /* residual estimate from the Givens recursion */
+  double relres_true;   /* ||b - A p|| / ||b|| recomputed with one product */
+} fmpb_solve_info;
+
+/*
+ * Solves A p_r = b_r for R right-hand sides by restarted GMRES (Sec. 4)
+ * with x0 = 0, no preconditioner, FP64 Arnoldi (two-pass classical
+ * Gram-Schmidt) and Givens rotations, all vectors and the Hessenberg data on
+ * the device; the host only sequences launches and reads one residual per
+ * RHS per iteration.
+ *   b, p   device, R x N; p is overwritten.
+ *   opts   may be NULL (defaults); info host, R entries, may be NULL.
+ * Returns FMPB_ENOCONV if some RHS missed the tolerance within maxit (p
+ * then holds the last iterate and info is filled), FMPB_ETIMEOUT if
+ * timeout_ms expired (same guarantees), FMPB_ENAN if b holds NaN/Inf.
+ * Synchronises the stream.
+ */
+fmpb_status fmpb_solve(const fmpb_operator *op, int R, const fmpb_c64 *b, fmpb_c64 *p,
+                       const fmpb_solve_opts *opts, fmpb_solve_info *info, void *stream);
+
+/*
+ * Total pressure at field points in the fluid (Eq. (cbie) with c(x) = 1):
+ * p(x) = p_inc(x) + sum_j int_{E_j} dG/dn_y(x, y) dA_y p_j over every
+ * element of every cell (direct sum).
+ *   p     device, R x N surface pressure.   dirs, amps as in fmpb_rhs_plane_wave.
+ *   pts   device, npts x 3 points (must not lie on an element).
+ *   out   device, R x npts.
+ */
+fmpb_status fmpb_field(const fmpb_operator *op, int R, const fmpb_c64 *p, const double *dirs,
+                       const fmpb_c64 *amps, int64_t npts, const double *pts, fmpb_c64 *out,
+                       void *stream);
+
+/* ------------------------------------------------------------------------
+ * Building blocks (the same kernels the operator uses), for callers that
+ * assemble their own products and for table-level checks.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Collocation blocks T_delta of Eq. (blockToeplizMatrix) (Sec. 2.2): entry
+ * (i, j) couples collocation point i of the cell at the origin with
+ * triangle j of the cell displaced by -delta . lattice vectors:
+ *   T_delta[i][j] = 1/2 [delta = 0, i = j] - int_{E_j} (dG/dn_y + (i/k) d2G/dn_x dn_y).
+ *   offsets host, n_off x 3 int32 (delta_x, delta_y, delta_z).
+ *   out     device, n_off x ntri x ntri, row-major per block.
+ */
+fmpb_status fmpb_build_blocks(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                              const fmpb_lattice *lattice, double k, int n_off,
+                              const int32_t *offsets, fmpb_c64 *out, void *stream);
+
+/*
+ * P2M table V_0 (B x n, Eq. (p2m)) and L2P table U_0 (n x B, Eq. (l2p) and
+ * its normal derivative, scaled by -(ik/4pi)(2n'+1)), B = (n_t+1)^2,
+ * coefficient (n', m) at q = n'(n'+1) + m.  Either output may be NULL.
+ */
+fmpb_status fmpb_multipole_tables(const double *verts, int64_t nv, const int32_t *tris,
+                                  int64_t ntri, double k, int n_t, fmpb_c64 *V0, fmpb_c64 *U0,
+                                  void *stream);
+
+/*
+ * M2L blocks K(d) (B x B each, Eqs. (m2l), (wigner)) for n_d translation
+ * vectors d = x_c - y_c.   dvecs host, n_d x 3;  out device, n_d x B x B.
+ */
+fmpb_status fmpb_m2l_blocks(double k, int n_t, int n_d, const double *dvecs, fmpb_c64 *out,
+                            void *stream);
+
+/*
+ * Padded circulant lengths P_a (smallest 2,3,5,7-smooth integer >= 2 M_a - 1,
+ * 1 for M_a = 1) and F = P_0 P_1 P_2 for a cell grid.
+ */
+fmpb_status fmpb_circulant_shape(const int32_t counts[3], int32_t P[3], int64_t *F);
+
+/*
+ * Spectrum of a multilevel block Toeplitz matrix (Eq. (blockDiagonal)):
+ * Lambda_f = sum_delta T_delta exp(-2 pi i f . (delta mod P) / P).
+ *   blocks  device, (2M_x-1)(2M_y-1)(2M_z-1) x B x B, offsets ordered with
+ *           delta_x fastest, each from 1-M_a to M_a-1.
+ *   spec    device, F x B x B (frequency-major).
+ */
+fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fmpb_c64 *blocks,
+                                    fmpb_c64 *spec, void *stream);
+
+/*
+ * y (+)= T x for the block Toeplitz T whose spectrum is `spec`, through the
+ * pruned FFT, the per-frequency B x B products and the pruned inverse FFT
+ * (Sec. 2.4).   x, y device, R x (n_cells B), cell-major as above.
+ *   accumulate  0: y = T x;  1: y += T x.
+ * Allocates its scratch (about 2 F R B complex values) per call.
+ */
+fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
+                                 const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMPB_H */

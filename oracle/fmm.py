@@ -29,6 +29,8 @@ q = n(n+1)+m.  Readings of garbled or silent points:
     the integer offset has max-norm <= 1 (the 3^d unique near blocks that the
     paper counts for square cells, Sec. 3.3).
 """
+from functools import lru_cache
+
 import numpy as np
 
 from . import special as sp
@@ -61,16 +63,17 @@ def l2p_table(cell: CellMesh, k: float, nt: int):
     return (fac[:, None] * (np.conj(I) + b * np.conj(dIdn))).T
 
 
-def m2l_block(dvec, k: float, nt: int):
-    """K(d) (B x B) from Eqs. (m2l), (wigner) with O_l evaluated at d."""
-    O = sp.wave_table(2 * nt, np.asarray(dvec, dtype=np.float64), k, "O")
+@lru_cache(maxsize=None)
+def _m2l_terms(nt: int):
+    """Every nonzero term of Eq. (m2l): for entry (q, q') and l in N the
+    coefficient (2n'+1)(-1)^{m+m'} W_{n',n,m',m,l} and the index of
+    O_l^{m+m'}.  Returned as flat arrays (entry, O index, coefficient)."""
     coeffs = sp.coeff_list(nt)
     B = len(coeffs)
-    K = np.zeros((B, B), dtype=complex)
+    ent, oidx, coef = [], [], []
     for qi, (n, m) in enumerate(coeffs):
         for qj, (n2, m2) in enumerate(coeffs):
             mu = m + m2
-            acc = 0.0 + 0.0j
             for l in range(max(abs(mu), abs(n - n2)), n + n2 + 1):
                 if (n + n2 - l) % 2:
                     continue
@@ -78,9 +81,20 @@ def m2l_block(dvec, k: float, nt: int):
                 if w3 == 0.0:
                     continue
                 W = (2 * l + 1) * (1j) ** ((n - n2 + l) % 4) * w3
-                acc += W * O[sp.coeff_index(l, mu)]
-            K[qi, qj] = (2 * n2 + 1) * (-1) ** ((m + m2) % 2) * acc
-    return K
+                ent.append(qi * B + qj)
+                oidx.append(sp.coeff_index(l, mu))
+                coef.append((2 * n2 + 1) * (-1) ** ((m + m2) % 2) * W)
+    return np.array(ent), np.array(oidx), np.array(coef)
+
+
+def m2l_block(dvec, k: float, nt: int):
+    """K(d) (B x B) from Eqs. (m2l), (wigner) with O_l evaluated at d."""
+    O = sp.wave_table(2 * nt, np.asarray(dvec, dtype=np.float64), k, "O")
+    ent, oidx, coef = _m2l_terms(nt)
+    B = (nt + 1) ** 2
+    K = np.zeros(B * B, dtype=complex)
+    np.add.at(K, ent, coef * O[oidx])
+    return K.reshape(B, B)
 
 
 def m2l_block_by_projection(dvec, k: float, nt: int, rho0: float, nq: int = 48):

@@ -1,0 +1,15 @@
+"""GB300 (sm_103a) implementation of the finite-periodic fast multipole BEM
+matrix-vector product and its GMRES solve (Jelich, Zhao, Chen, Marburg,
+arXiv 2201.12050).
+
+Every step runs in the CUDA library ``libfmpb.so`` (C ABI in
+``include/fmpb.h``); this package only marshals arguments.  PyTorch supplies
+device memory and streams.
+"""
+from ._lib import FmpbError, FmpbLibraryMissing, lib
+from .api import (Operator, build_blocks, multipole_tables, m2l_blocks, circulant_shape,
+                  circulant_spectrum, circulant_apply, FORM_AUTO, FORM_FMM, FORM_PBEM)
+
+__all__ = ["Operator", "build_blocks", "multipole_tables", "m2l_blocks", "circulant_shape",
+           "circulant_spectrum", "circulant_apply", "FmpbError", "FmpbLibraryMissing", "lib",
+           "FORM_AUTO", "FORM_FMM", "FORM_PBEM"]

@@ -1,0 +1,104 @@
+"""ctypes loader of ``libfmpb.so`` (argument marshalling only).
+
+The library is built in-tree by ``paper_2201_12050_gb300.build``.  There is
+no fallback: if the shared library is missing or cannot be loaded, every
+entry point raises ``FmpbLibraryMissing``.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmpb.so")
+
+STATUS = {0: "FMPB_OK", -1: "FMPB_EINVAL", -2: "FMPB_ENOMEM", -3: "FMPB_EMESH", -4: "FMPB_EADMISS",
+          -5: "FMPB_ENOCONV", -6: "FMPB_ETIMEOUT", -7: "FMPB_ENAN", -8: "FMPB_ECUDA"}
+
+
+class FmpbLibraryMissing(ImportError):
+    pass
+
+
+class FmpbError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("counts", ctypes.c_int32 * 3), ("vectors", (ctypes.c_double * 3) * 3)]
+
+
+class OperatorOpts(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("n_t", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class OperatorInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("N", ctypes.c_int64), ("dim", ctypes.c_int32),
+                ("form", ctypes.c_int32), ("n_t", ctypes.c_int32), ("B", ctypes.c_int64),
+                ("P", ctypes.c_int32 * 3), ("F", ctypes.c_int64), ("n_near", ctypes.c_int32),
+                ("bytes_device", ctypes.c_size_t)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("timeout_ms", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("relres_est", ctypes.c_double),
+                ("relres_true", ctypes.c_double)]
+
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+D = ctypes.c_double
+INT = ctypes.c_int
+
+# name -> (restype, argtypes); the entry points declared in include/fmpb.h
+SIGNATURES = {
+    "fmpb_last_error": (ctypes.c_char_p, []),
+    "fmpb_version": (INT, []),
+    "fmpb_operator_create": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, ctypes.POINTER(OperatorOpts), P,
+                                   ctypes.POINTER(P)]),
+    "fmpb_operator_get_info": (INT, [P, ctypes.POINTER(OperatorInfo)]),
+    "fmpb_operator_destroy": (None, [P]),
+    "fmpb_rhs_plane_wave": (INT, [P, INT, P, P, P, P]),
+    "fmpb_matvec": (INT, [P, INT, P, P, P]),
+    "fmpb_solve": (INT, [P, INT, P, P, ctypes.POINTER(SolveOpts), P, P]),
+    "fmpb_field": (INT, [P, INT, P, P, P, I64, P, P, P]),
+    "fmpb_build_blocks": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, INT, P, P, P]),
+    "fmpb_multipole_tables": (INT, [P, I64, P, I64, D, INT, P, P, P]),
+    "fmpb_m2l_blocks": (INT, [D, INT, INT, P, P, P]),
+    "fmpb_circulant_shape": (INT, [P, P, P]),
+    "fmpb_circulant_spectrum": (INT, [P, I64, P, P, P]),
+    "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (loaded once); raises FmpbLibraryMissing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FmpbLibraryMissing(f"{LIB_PATH} is not built; run paper_2201_12050_gb300.build.build()")
+    try:
+        L = ctypes.CDLL(LIB_PATH)
+    except OSError as e:
+        raise FmpbLibraryMissing(f"cannot load {LIB_PATH}: {e}") from e
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != 0:
+        raise FmpbError(status, lib().fmpb_last_error().decode())
+    return status

@@ -1,0 +1,190 @@
+"""Thin Python binding of the C ABI (include/fmpb.h), same names, argument
+marshalling only.  Device vectors are torch.complex128 CUDA tensors (the
+interleaved layout of fmpb_c64); host arrays are numpy.  Work is enqueued on
+torch's current CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, SolveOpts, SolveInfo, FmpbError)
+
+FORM_AUTO, FORM_FMM, FORM_PBEM = -1, 0, 1
+FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem"}
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    if isinstance(a, torch.Tensor):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _lattice(counts, vectors) -> Lattice:
+    L = Lattice()
+    c = list(counts) + [1] * (3 - len(counts))
+    for a in range(3):
+        L.counts[a] = int(c[a])
+    V = np.asarray(vectors, dtype=np.float64).reshape(3, 3)
+    for a in range(3):
+        for d in range(3):
+            L.vectors[a][d] = float(V[a, d])
+    return L
+
+
+def _cvec(x, N, name):
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128):
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if x.numel() % N:
+        raise ValueError(f"{name} has {x.numel()} entries, not a multiple of N = {N}")
+    return x.numel() // N
+
+
+class Operator:
+    """fmpb_operator: the tables of one (unit-cell mesh, lattice, k)."""
+
+    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0):
+        self._lib = lib()
+        v = _host(verts, np.float64)
+        t = _host(tris, np.int32)
+        self._lat = _lattice(counts, vectors)
+        opts = OperatorOpts(int(form), int(n_t), 0)
+        h = ctypes.c_void_p()
+        check(self._lib.fmpb_operator_create(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(self._lat),
+                                             float(k), ctypes.byref(opts), _stream(), ctypes.byref(h)))
+        self._h = h
+        self.k = float(k)
+        info = OperatorInfo()
+        check(self._lib.fmpb_operator_get_info(self._h, ctypes.byref(info)))
+        self.info = {f: (list(getattr(info, f)) if f == "P" else getattr(info, f)) for f, _ in info._fields_}
+        self.info["form_name"] = FORM_NAMES[self.info["form"]]
+        self.N = self.info["N"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmpb_operator_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def rhs_plane_wave(self, dirs, amps=None, out=None):
+        d = _host(dirs, np.float64).reshape(-1, 3)
+        R = len(d)
+        a = None if amps is None else _host(np.asarray(amps, dtype=np.complex128).reshape(R), np.complex128)
+        b = out if out is not None else torch.empty((R, self.N), dtype=torch.complex128, device="cuda")
+        check(self._lib.fmpb_rhs_plane_wave(self._h, R, _ptr(d), None if a is None else _ptr(a), _ptr(b), _stream()))
+        return b
+
+    def matvec(self, x, out=None):
+        R = _cvec(x, self.N, "x")
+        y = out if out is not None else torch.empty_like(x)
+        check(self._lib.fmpb_matvec(self._h, R, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def solve(self, b, tol=1e-8, restart=30, maxit=1000, timeout_ms=0, out=None, raise_on_noconv=True):
+        R = _cvec(b, self.N, "b")
+        p = out if out is not None else torch.empty_like(b)
+        opts = SolveOpts(float(tol), int(restart), int(maxit), int(timeout_ms))
+        infos = (SolveInfo * R)()
+        st = self._lib.fmpb_solve(self._h, R, _ptr(b), _ptr(p), ctypes.byref(opts), ctypes.cast(infos, ctypes.c_void_p),
+                                  _stream())
+        info = [{"iters": i.iters, "converged": bool(i.converged), "relres_est": i.relres_est,
+                 "relres_true": i.relres_true} for i in infos]
+        if st != 0 and (raise_on_noconv or st not in (-5, -6)):
+            check(st)
+        return p, info
+
+    def field(self, p, dirs, pts, amps=None):
+        R = _cvec(p, self.N, "p")
+        d = _host(dirs, np.float64).reshape(R, 3)
+        a = None if amps is None else _host(np.asarray(amps, dtype=np.complex128).reshape(R), np.complex128)
+        if not (isinstance(pts, torch.Tensor) and pts.is_cuda and pts.dtype == torch.float64):
+            pts = torch.as_tensor(np.asarray(pts, dtype=np.float64), device="cuda")
+        pts = pts.contiguous()
+        npts = pts.numel() // 3
+        out = torch.empty((R, npts), dtype=torch.complex128, device="cuda")
+        check(self._lib.fmpb_field(self._h, R, _ptr(p), _ptr(d), None if a is None else _ptr(a), npts, _ptr(pts),
+                                   _ptr(out), _stream()))
+        return out
+
+
+def build_blocks(verts, tris, counts, vectors, k, offsets):
+    """fmpb_build_blocks: T_delta for each offset, (n_off, n, n) on the device."""
+    v = _host(verts, np.float64)
+    t = _host(tris, np.int32)
+    off = _host(offsets, np.int32).reshape(-1, 3)
+    lat = _lattice(counts, vectors)
+    out = torch.empty((len(off), len(t), len(t)), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_build_blocks(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k), len(off), _ptr(off),
+                                  _ptr(out), _stream()))
+    return out
+
+
+def multipole_tables(verts, tris, k, n_t):
+    """fmpb_multipole_tables: (V_0 (B, n), U_0 (n, B)) on the device."""
+    v = _host(verts, np.float64)
+    t = _host(tris, np.int32)
+    B = (n_t + 1) ** 2
+    V0 = torch.empty((B, len(t)), dtype=torch.complex128, device="cuda")
+    U0 = torch.empty((len(t), B), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_multipole_tables(_ptr(v), len(v), _ptr(t), len(t), float(k), int(n_t), _ptr(V0), _ptr(U0),
+                                      _stream()))
+    return V0, U0
+
+
+def m2l_blocks(k, n_t, dvecs):
+    """fmpb_m2l_blocks: K(d) for each translation, (n_d, B, B)."""
+    d = _host(dvecs, np.float64).reshape(-1, 3)
+    B = (n_t + 1) ** 2
+    out = torch.empty((len(d), B, B), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_m2l_blocks(float(k), int(n_t), len(d), _ptr(d), _ptr(out), _stream()))
+    return out
+
+
+def circulant_shape(counts):
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    P = np.zeros(3, dtype=np.int32)
+    F = ctypes.c_int64()
+    check(lib().fmpb_circulant_shape(_ptr(c), _ptr(P), ctypes.byref(F)))
+    return P.tolist(), F.value
+
+
+def circulant_spectrum(counts, blocks):
+    """fmpb_circulant_spectrum: blocks (n_off, B, B) complex128 CUDA -> (F, B, B)."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    B = blocks.shape[-1]
+    _, F = circulant_shape(counts)
+    spec = torch.empty((F, B, B), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_circulant_spectrum(_ptr(c), B, _ptr(blocks.contiguous()), _ptr(spec), _stream()))
+    return spec
+
+
+def circulant_apply(counts, spec, x, out=None, accumulate=False):
+    """fmpb_circulant_apply: y (+)= T x for x of shape (R, n_cells * B)."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    B = spec.shape[-1]
+    ncell = int(np.prod(c))
+    R = _cvec(x, ncell * B, "x")
+    y = out if out is not None else torch.empty_like(x)
+    check(lib().fmpb_circulant_apply(_ptr(c), B, _ptr(spec), R, _ptr(x), _ptr(y), 1 if accumulate else 0, _stream()))
+    return y

@@ -1,0 +1,403 @@
+// C ABI of the library (include/fmpb.h): argument checking, the operator
+// object and the composition of the kernels into the FMPBEM and PBEM
+// products (Sec. 3.5, Eq. (FMPBEMsystem); Sec. 2.4).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "multipole.cuh"
+#include "nearfield.cuh"
+#include "gmres.cuh"
+
+namespace fmpb {
+
+static thread_local std::string g_error = "no error";
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+}
+
+fmpb_status cuda_status(cudaError_t e, const char* what) {
+  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FMPB_ENOMEM : FMPB_ECUDA;
+}
+
+fmpb_status circulant_spectrum_from_blocks(const CircShape& s, int64_t B, const cd* blocks, cd* spec, cudaStream_t st);
+
+static fmpb_status make_grid(const fmpb_lattice* lat, CellGrid& g) {
+  if (!lat) {
+    set_error("lattice is NULL");
+    return FMPB_EINVAL;
+  }
+  int64_t nc = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (lat->counts[a] < 1 || lat->counts[a] > 4096) {
+      set_error("lattice count %d out of range 1..4096", lat->counts[a]);
+      return FMPB_EINVAL;
+    }
+    g.M[a] = lat->counts[a];
+    nc *= lat->counts[a];
+    for (int d = 0; d < 3; ++d) {
+      g.L[a][d] = lat->vectors[a][d];
+      if (!std::isfinite(g.L[a][d])) {
+        set_error("lattice vector is not finite");
+        return FMPB_EINVAL;
+      }
+    }
+  }
+  if (nc > (1 << 24)) {
+    set_error("too many cells (%lld)", (long long)nc);
+    return FMPB_EINVAL;
+  }
+  g.ncells = (int)nc;
+  return FMPB_OK;
+}
+
+template <typename T>
+static fmpb_status dev_alloc(T** p, size_t count, size_t& bytes) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cannot allocate %zu bytes on the device", sizeof(T) * count);
+    return FMPB_ENOMEM;
+  }
+  bytes += sizeof(T) * count;
+  return FMPB_OK;
+}
+
+}  // namespace fmpb
+
+using namespace fmpb;
+
+struct fmpb_operator {
+  int device = 0;
+  DeviceMesh mesh;
+  CellGrid grid;
+  CircShape shape;
+  double k = 0.0;
+  int form = FMPB_FORM_PBEM;
+  int nt = 0;
+  int64_t B = 0;
+  int dim = 0;
+  cd* spec = nullptr;      // F x B x B
+  cd* S = nullptr;         // n_near x n x n (FMM form)
+  int* near_offs = nullptr;
+  int n_near = 0;
+  cd* V0 = nullptr;        // B x n
+  cd* U0 = nullptr;        // n x B
+  size_t bytes = 0;
+  // scratch, grown on demand (calls on one operator are stream-ordered)
+  cd* scratch = nullptr;
+  size_t scratch_elems = 0;
+
+  ~fmpb_operator() {
+    cudaDeviceSynchronize();
+    free_mesh(mesh);
+    cudaFree(spec);
+    cudaFree(S);
+    cudaFree(near_offs);
+    cudaFree(V0);
+    cudaFree(U0);
+    cudaFree(scratch);
+  }
+
+  fmpb_status ensure_scratch(size_t elems) {
+    if (elems <= scratch_elems) return FMPB_OK;
+    cudaFree(scratch);
+    scratch = nullptr;
+    scratch_elems = 0;
+    size_t dummy = 0;
+    FMPB_TRY(dev_alloc(&scratch, elems, dummy));
+    scratch_elems = elems;
+    return FMPB_OK;
+  }
+
+  fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st) {
+    const int64_t Nc = shape.ncells;
+    if (form == FMPB_FORM_PBEM) {
+      FMPB_TRY(ensure_scratch(circulant_scratch_elems(shape, B, R)));
+      return circulant_apply(shape, B, spec, R, x, y, false, scratch, st);
+    }
+    const size_t circ = circulant_scratch_elems(shape, B, R);
+    const size_t mom = (size_t)R * Nc * B;
+    FMPB_TRY(ensure_scratch(circ + 2 * mom));
+    cd* Mom = scratch + circ;
+    cd* Loc = Mom + mom;
+    FMPB_TRY(near_apply(S, near_offs, n_near, mesh.n, shape.M, R, x, y, false, st));
+    FMPB_TRY(p2m_apply(V0, mesh.n, (int)B, (int64_t)R * Nc, x, Mom, st));
+    FMPB_TRY(circulant_apply(shape, B, spec, R, Mom, Loc, false, scratch, st));
+    FMPB_TRY(l2p_apply(U0, mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
+    return FMPB_OK;
+  }
+};
+
+#define CHECK_ARG(cond, ...)      \
+  do {                            \
+    if (!(cond)) {                \
+      set_error(__VA_ARGS__);     \
+      return FMPB_EINVAL;         \
+    }                             \
+  } while (0)
+
+extern "C" {
+
+const char* fmpb_last_error(void) { return g_error.c_str(); }
+
+int fmpb_version(void) { return (FMPB_VERSION_MAJOR << 16) | FMPB_VERSION_MINOR; }
+
+fmpb_status fmpb_circulant_shape(const int32_t counts[3], int32_t P[3], int64_t* F) {
+  CHECK_ARG(counts && P && F, "circulant_shape: NULL argument");
+  int M[3];
+  for (int a = 0; a < 3; ++a) {
+    CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "circulant_shape: count out of range");
+    M[a] = counts[a];
+  }
+  CircShape s = make_shape(M);
+  for (int a = 0; a < 3; ++a) P[a] = s.P[a];
+  *F = s.F;
+  return FMPB_OK;
+}
+
+fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                 const fmpb_lattice* lattice, double k, const fmpb_operator_opts* opts, void* stream,
+                                 fmpb_operator** out) {
+  CHECK_ARG(out, "operator_create: out is NULL");
+  CHECK_ARG(k > 0.0 && std::isfinite(k), "operator_create: wavenumber must be positive");
+  fmpb_operator_opts o = opts ? *opts : fmpb_operator_opts{FMPB_FORM_AUTO, 0, FMPB_FP64};
+  CHECK_ARG(o.form >= -1 && o.form <= 1, "operator_create: bad form %d", o.form);
+  CHECK_ARG(o.precision == FMPB_FP64, "operator_create: only FMPB_FP64 products in this version");
+  const int nt = o.n_t > 0 ? o.n_t : 8;
+  CHECK_ARG(nt >= 1 && nt <= MAX_NT, "operator_create: n_t must be 1..%d", MAX_NT);
+  cudaStream_t st = (cudaStream_t)stream;
+  fmpb_operator* op = new (std::nothrow) fmpb_operator();
+  if (!op) {
+    set_error("operator_create: host allocation failed");
+    return FMPB_ENOMEM;
+  }
+  auto fail = [&](fmpb_status s) {
+    delete op;
+    return s;
+  };
+  cudaGetDevice(&op->device);
+  op->k = k;
+  fmpb_status s = make_grid(lattice, op->grid);
+  if (s != FMPB_OK) return fail(s);
+  s = upload_mesh(verts, nv, tris, ntri, op->mesh, st);
+  if (s != FMPB_OK) return fail(s);
+  op->shape = make_shape(op->grid.M);
+  const CircShape& sh = op->shape;
+  op->dim = (sh.M[0] > 1) + (sh.M[1] > 1) + (sh.M[2] > 1);
+  const int n = op->mesh.n;
+  // admissibility of the cell-as-box FMM: every far translation must exceed
+  // three cell radii (two-centre convergence ratio 2 rho / |d| <= 2/3)
+  double dmin = 1e300;
+  std::vector<int32_t> all_off, far_off, near_off;
+  for (int dz = 1 - sh.M[2]; dz < sh.M[2]; ++dz)
+    for (int dy = 1 - sh.M[1]; dy < sh.M[1]; ++dy)
+      for (int dx = 1 - sh.M[0]; dx < sh.M[0]; ++dx) {
+        int32_t dl[3] = {dx, dy, dz};
+        all_off.insert(all_off.end(), dl, dl + 3);
+        bool near = abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1;
+        (near ? near_off : far_off).insert((near ? near_off : far_off).end(), dl, dl + 3);
+        if (!near) {
+          double d2 = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            double v = dx * op->grid.L[0][c] + dy * op->grid.L[1][c] + dz * op->grid.L[2][c];
+            d2 += v * v;
+          }
+          dmin = fmin(dmin, sqrt(d2));
+        }
+      }
+  const double rho = op->mesh.radius;
+  int form = o.form;
+  if (form == FMPB_FORM_AUTO) form = (dmin >= 3.0 * rho) ? FMPB_FORM_FMM : FMPB_FORM_PBEM;
+  if (form == FMPB_FORM_FMM && !(dmin > 2.0 * rho)) {
+    set_error("operator_create: FMM form not admissible (nearest far cell at %.4g, cell radius %.4g)", dmin, rho);
+    return fail(FMPB_EADMISS);
+  }
+  op->form = form;
+  if (form == FMPB_FORM_PBEM) {
+    op->B = n;
+    const size_t elems = (size_t)sh.F * n * n;
+    s = dev_alloc(&op->spec, elems, op->bytes);
+    if (s != FMPB_OK) return fail(s);
+    if (cudaMemsetAsync(op->spec, 0, sizeof(cd) * elems, st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "memset"));
+    const int n_off = (int)(all_off.size() / 3);
+    std::vector<int64_t> dest(n_off);
+    for (int i = 0; i < n_off; ++i) dest[i] = offset_slot(sh, all_off[3 * i], all_off[3 * i + 1], all_off[3 * i + 2]);
+    s = build_blocks(op->mesh, op->grid, k, n_off, all_off.data(), dest.data(), op->spec, st);
+    if (s != FMPB_OK) return fail(s);
+    s = grid_fft_inplace(sh, (int64_t)n * n, op->spec, st);
+    if (s != FMPB_OK) return fail(s);
+  } else {
+    op->nt = nt;
+    op->B = (int64_t)(nt + 1) * (nt + 1);
+    const int64_t B = op->B;
+    op->n_near = (int)(near_off.size() / 3);
+    s = dev_alloc(&op->S, (size_t)op->n_near * n * n, op->bytes);
+    if (s == FMPB_OK) s = dev_alloc(&op->near_offs, near_off.size(), op->bytes);
+    if (s == FMPB_OK) s = dev_alloc(&op->V0, (size_t)B * n, op->bytes);
+    if (s == FMPB_OK) s = dev_alloc(&op->U0, (size_t)B * n, op->bytes);
+    if (s == FMPB_OK) s = dev_alloc(&op->spec, (size_t)sh.F * B * B, op->bytes);
+    if (s != FMPB_OK) return fail(s);
+    if (cudaMemcpyAsync(op->near_offs, near_off.data(), sizeof(int) * near_off.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(op->spec, 0, sizeof(cd) * (size_t)sh.F * B * B, st) != cudaSuccess)
+      return fail(cuda_status(cudaGetLastError(), "operator_create copies"));
+    std::vector<int64_t> dnear(op->n_near);
+    for (int i = 0; i < op->n_near; ++i) dnear[i] = i;
+    s = build_blocks(op->mesh, op->grid, k, op->n_near, near_off.data(), dnear.data(), op->S, st);
+    if (s == FMPB_OK) s = multipole_tables(op->mesh, k, nt, op->V0, op->U0, st);
+    if (s != FMPB_OK) return fail(s);
+    const int n_far = (int)(far_off.size() / 3);
+    std::vector<double> dvec(3 * (size_t)n_far);
+    std::vector<int64_t> dfar(n_far);
+    for (int i = 0; i < n_far; ++i) {
+      const int32_t* dl = &far_off[3 * i];
+      for (int c = 0; c < 3; ++c)
+        dvec[3 * i + c] = dl[0] * op->grid.L[0][c] + dl[1] * op->grid.L[1][c] + dl[2] * op->grid.L[2][c];
+      dfar[i] = offset_slot(sh, dl[0], dl[1], dl[2]);
+    }
+    s = m2l_blocks(nt, k, n_far, dvec.data(), dfar.data(), op->spec, st);
+    if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec, st);
+    if (s != FMPB_OK) return fail(s);
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "operator_create"));
+  *out = op;
+  return FMPB_OK;
+}
+
+fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* info) {
+  CHECK_ARG(op && info, "operator_get_info: NULL argument");
+  info->n = op->mesh.n;
+  info->n_cells = op->shape.ncells;
+  info->N = (int64_t)op->mesh.n * op->shape.ncells;
+  info->dim = op->dim;
+  info->form = op->form;
+  info->n_t = op->nt;
+  info->B = op->B;
+  for (int a = 0; a < 3; ++a) info->P[a] = op->shape.P[a];
+  info->F = op->shape.F;
+  info->n_near = op->n_near;
+  info->bytes_device = op->bytes;
+  return FMPB_OK;
+}
+
+void fmpb_operator_destroy(fmpb_operator* op) { delete op; }
+
+fmpb_status fmpb_rhs_plane_wave(const fmpb_operator* op, int R, const double* dirs, const fmpb_c64* amps,
+                                fmpb_c64* b, void* stream) {
+  CHECK_ARG(op && dirs && b, "rhs_plane_wave: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 65535, "rhs_plane_wave: R out of range");
+  return rhs_plane_wave(op->mesh, op->grid, op->k, R, dirs, amps, (cd*)b, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_matvec(const fmpb_operator* op, int R, const fmpb_c64* x, fmpb_c64* y, void* stream) {
+  CHECK_ARG(op && x && y, "matvec: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 4096, "matvec: R out of range");
+  CHECK_ARG((const void*)x != (const void*)y, "matvec: x and y must not alias");
+  return const_cast<fmpb_operator*>(op)->matvec(R, (const cd*)x, (cd*)y, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_solve(const fmpb_operator* op, int R, const fmpb_c64* b, fmpb_c64* p, const fmpb_solve_opts* opts,
+                       fmpb_solve_info* info, void* stream) {
+  CHECK_ARG(op && b && p, "solve: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 4096, "solve: R out of range");
+  CHECK_ARG((const void*)b != (const void*)p, "solve: b and p must not alias");
+  fmpb_solve_opts o = opts ? *opts : fmpb_solve_opts{0.0, 0, 0, 0};
+  fmpb_operator* mop = const_cast<fmpb_operator*>(op);
+  MatvecFn A = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st); };
+  const int64_t N = (int64_t)op->mesh.n * op->shape.ncells;
+  return gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_field(const fmpb_operator* op, int R, const fmpb_c64* p, const double* dirs, const fmpb_c64* amps,
+                       int64_t npts, const double* pts, fmpb_c64* out, void* stream) {
+  CHECK_ARG(op && p && dirs && pts && out, "field: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 65535 && npts >= 1, "field: R or npts out of range");
+  return field_points(op->mesh, op->grid, op->k, R, (const cd*)p, dirs, amps, npts, pts, (cd*)out,
+                      (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_build_blocks(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                              const fmpb_lattice* lattice, double k, int n_off, const int32_t* offsets, fmpb_c64* out,
+                              void* stream) {
+  CHECK_ARG(offsets && out && n_off >= 1, "build_blocks: bad offsets or output");
+  CHECK_ARG(k > 0.0 && std::isfinite(k), "build_blocks: wavenumber must be positive");
+  CellGrid g;
+  FMPB_TRY(make_grid(lattice, g));
+  DeviceMesh m;
+  cudaStream_t st = (cudaStream_t)stream;
+  FMPB_TRY(upload_mesh(verts, nv, tris, ntri, m, st));
+  std::vector<int64_t> dest(n_off);
+  for (int i = 0; i < n_off; ++i) dest[i] = i;
+  fmpb_status s = build_blocks(m, g, k, n_off, offsets, dest.data(), (cd*)out, st);
+  free_mesh(m);
+  return s;
+}
+
+fmpb_status fmpb_multipole_tables(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, double k,
+                                  int n_t, fmpb_c64* V0, fmpb_c64* U0, void* stream) {
+  CHECK_ARG(k > 0.0 && std::isfinite(k), "multipole_tables: wavenumber must be positive");
+  CHECK_ARG(n_t >= 1 && n_t <= MAX_NT, "multipole_tables: n_t must be 1..%d", MAX_NT);
+  DeviceMesh m;
+  cudaStream_t st = (cudaStream_t)stream;
+  FMPB_TRY(upload_mesh(verts, nv, tris, ntri, m, st));
+  fmpb_status s = multipole_tables(m, k, n_t, (cd*)V0, (cd*)U0, st);
+  if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "multipole_tables");
+  free_mesh(m);
+  return s;
+}
+
+fmpb_status fmpb_m2l_blocks(double k, int n_t, int n_d, const double* dvecs, fmpb_c64* out, void* stream) {
+  CHECK_ARG(k > 0.0 && std::isfinite(k), "m2l_blocks: wavenumber must be positive");
+  CHECK_ARG(n_t >= 1 && n_t <= MAX_NT, "m2l_blocks: n_t must be 1..%d", MAX_NT);
+  CHECK_ARG(n_d >= 1 && dvecs && out, "m2l_blocks: bad translations or output");
+  for (int i = 0; i < n_d; ++i) {
+    double r2 = dvecs[3 * i] * dvecs[3 * i] + dvecs[3 * i + 1] * dvecs[3 * i + 1] + dvecs[3 * i + 2] * dvecs[3 * i + 2];
+    CHECK_ARG(r2 > 0.0 && std::isfinite(r2), "m2l_blocks: translation %d is zero or not finite", i);
+  }
+  std::vector<int64_t> dest(n_d);
+  for (int i = 0; i < n_d; ++i) dest[i] = i;
+  return m2l_blocks(n_t, k, n_d, dvecs, dest.data(), (cd*)out, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fmpb_c64* blocks, fmpb_c64* spec,
+                                    void* stream) {
+  CHECK_ARG(counts && blocks && spec && B >= 1, "circulant_spectrum: bad arguments");
+  int M[3];
+  for (int a = 0; a < 3; ++a) {
+    CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "circulant_spectrum: count out of range");
+    M[a] = counts[a];
+  }
+  return circulant_spectrum_from_blocks(make_shape(M), B, (const cd*)blocks, (cd*)spec, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R, const fmpb_c64* x,
+                                 fmpb_c64* y, int accumulate, void* stream) {
+  CHECK_ARG(counts && spec && x && y && B >= 1, "circulant_apply: bad arguments");
+  CHECK_ARG(R >= 1 && R <= 4096, "circulant_apply: R out of range");
+  int M[3];
+  for (int a = 0; a < 3; ++a) {
+    CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "circulant_apply: count out of range");
+    M[a] = counts[a];
+  }
+  CircShape sh = make_shape(M);
+  cudaStream_t st = (cudaStream_t)stream;
+  cd* scratch = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&scratch, sizeof(cd) * circulant_scratch_elems(sh, B, R), st));
+  fmpb_status s = circulant_apply(sh, B, (const cd*)spec, R, (const cd*)x, (cd*)y, accumulate != 0, scratch, st);
+  cudaFreeAsync(scratch, st);
+  return s;
+}
+
+}  // extern "C"

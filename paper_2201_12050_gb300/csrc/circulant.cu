@@ -1,0 +1,260 @@
+// Block Toeplitz products through block circulant embedding and FFT over the
+// cell grid (Sec. 2.4, Eqs. (BlockCirculantMatrix), (diagonalized),
+// (blockDiagonal), (modifiedFourierTransform1/2); Sec. 3.5, Eq.
+// (FMPBEMsystem)).
+//
+// A multilevel block Toeplitz matrix with blocks T_delta (B x B) is embedded
+// in a circulant whose first block column holds T_delta at slot
+// (delta mod P) per axis, P >= 2M-1.  Its spectrum is
+//   Lambda_f = sum_delta T_delta exp(-2 pi i f.(delta mod P)/P),
+// and y = T x is computed as
+//   X_f = sum_{c < M} x_c exp(-2 pi i f.c/P)          (pruned forward DFT:
+//                                                      only M inputs per axis),
+//   Y_f = Lambda_f X_f                               (one B x B product per f),
+//   y_c = (1/F) sum_f Y_f exp(+2 pi i f.c/P), c < M   (pruned inverse: only
+//                                                      M outputs per axis).
+// Grid layout: slot-major, slot f = (fz Py + fy) Px + fx, then R x B (RHS
+// outer, coefficient inner); spectrum [f][b][b'] row-major.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace fmpb {
+
+int padded_length(int M) {
+  if (M <= 1) return 1;
+  int p = 2 * M - 1;
+  for (;; ++p) {
+    int q = p;
+    for (int f : {2, 3, 5, 7})
+      while (q % f == 0) q /= f;
+    if (q == 1) return p;
+  }
+}
+
+CircShape make_shape(const int M[3]) {
+  CircShape s;
+  s.F = 1;
+  s.ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    s.M[a] = M[a];
+    s.P[a] = padded_length(M[a]);
+    s.F *= s.P[a];
+    s.ncells *= M[a];
+  }
+  return s;
+}
+
+int64_t offset_slot(const CircShape& s, int dx, int dy, int dz) {
+  auto md = [](int d, int P) { return ((d % P) + P) % P; };
+  return ((int64_t)md(dz, s.P[2]) * s.P[1] + md(dy, s.P[1])) * s.P[0] + md(dx, s.P[0]);
+}
+
+// Direct DFT along one axis for the lines (o1, o2, i):
+//   out[o1 b1 + o2 b2 + f bf + i] (+)= scale sum_{j < Pin} in[o1 a1 + o2 a2 + j aj + i] w^{f j},
+// w = exp(sign 2 pi i / P), f < Pout.  A CTA loads one (o1, o2) line group
+// for TI consecutive inner indices into shared memory before writing, so the
+// call may run in place when in and out use the same strides.
+__global__ void k_dft_axis(const cd* in, cd* out, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
+                           int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign,
+                           double scale, int accumulate, int TI) {
+  extern __shared__ cd sm[];
+  cd* tw = sm;          // P twiddles
+  cd* tile = sm + P;    // Pin x TI
+  const int o1 = blockIdx.z;
+  const int o2 = blockIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * TI;
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * j / P, &s, &c);
+    tw[j] = mkc(c, sign * s);
+  }
+  const cd* src = in + o1 * a1 + o2 * a2 + i0;
+  for (int e = threadIdx.x; e < Pin * TI; e += blockDim.x) {
+    const int j = e / TI, ii = e - j * TI;
+    tile[e] = (i0 + ii < I) ? src[j * aj + ii] : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  cd* dst = out + o1 * b1 + o2 * b2 + i0;
+  for (int e = threadIdx.x; e < Pout * TI; e += blockDim.x) {
+    const int f = e / TI, ii = e - f * TI;
+    if (i0 + ii >= I) continue;
+    cd acc = mkc(0.0, 0.0);
+    int idx = 0;
+    for (int j = 0; j < Pin; ++j) {
+      acc = cfma(tile[j * TI + ii], tw[idx], acc);
+      idx += f;
+      if (idx >= P) idx -= P;
+    }
+    acc = cmulr(acc, scale);
+    cd* d = dst + f * bf + ii;
+    *d = accumulate ? cadd(*d, acc) : acc;
+  }
+}
+
+static fmpb_status dft_axis(const cd* in, cd* out, int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
+                            int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign, double scale,
+                            bool accumulate, cudaStream_t st) {
+  if (O1 > 65535 || O2 > 65535) {
+    set_error("dft_axis: line grid %d x %d exceeds the launch limits", O1, O2);
+    return FMPB_EINVAL;
+  }
+  const size_t budget = 96 * 1024;
+  int64_t TI = 32;
+  while (TI > 1 && (size_t)(Pin * TI + P) * sizeof(cd) > budget) TI /= 2;
+  if ((size_t)(Pin * TI + P) * sizeof(cd) > 200 * 1024) {
+    set_error("dft_axis: axis length %d too large", P);
+    return FMPB_EINVAL;
+  }
+  if (TI > I) TI = I;
+  size_t smem = (size_t)(Pin * TI + P) * sizeof(cd);
+  if (smem > 48 * 1024) FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
+  k_dft_axis<<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
+                                      accumulate ? 1 : 0, (int)TI);
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st) {
+  const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
+  if (Px > 1)
+    FMPB_TRY(dft_axis(grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner, inner, 0, (int64_t)Px * inner, inner,
+                      Px, Px, Px, -1, 1.0, false, st));
+  if (Py > 1)
+    FMPB_TRY(dft_axis(grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner,
+                      (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py, Py, Py, -1, 1.0, false, st));
+  if (Pz > 1)
+    FMPB_TRY(dft_axis(grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
+                      (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st));
+  return FMPB_OK;
+}
+
+// Y_f[r][b] = sum_b' Lambda_f[b][b'] X_f[r][b'], one warp per row b, RC RHS at
+// a time with X_f staged in shared memory.
+template <int RC>
+__global__ void k_block_product(const cd* __restrict__ spec, const cd* __restrict__ X, cd* __restrict__ Y,
+                                int64_t B, int R, int r0, int rows_per_cta) {
+  extern __shared__ cd xs[];   // RC x B
+  const int64_t f = blockIdx.y;
+  const int64_t RB = (int64_t)R * B;
+  const cd* Xf = X + f * RB + (int64_t)r0 * B;
+  const int rc = min(RC, R - r0);
+  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) xs[e] = Xf[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const cd* Lf = spec + f * B * B;
+  for (int64_t b = (int64_t)blockIdx.x * rows_per_cta + warp; b < min(B, (int64_t)(blockIdx.x + 1) * rows_per_cta);
+       b += nwarps) {
+    cd acc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) acc[r] = mkc(0.0, 0.0);
+    const cd* row = Lf + b * B;
+    for (int64_t bp = lane; bp < B; bp += 32) {
+      const cd a = row[bp];
+#pragma unroll
+      for (int r = 0; r < RC; ++r)
+        if (r < rc) acc[r] = cfma(a, xs[r * B + bp], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+      double re = acc[r].x, im = acc[r].y;
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0 && r < rc) Y[f * RB + (int64_t)(r0 + r) * B + b] = mkc(re, im);
+    }
+  }
+}
+
+static fmpb_status block_product(const cd* spec, const cd* X, cd* Y, int64_t F, int64_t B, int R, cudaStream_t st) {
+  if (F > 65535) {
+    set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
+    return FMPB_EINVAL;
+  }
+  constexpr int RC = 4;
+  const int threads = 256;
+  const int rows = 32;
+  const size_t smem = (size_t)RC * B * sizeof(cd);
+  if (smem > 200 * 1024) {
+    set_error("block_product: block size %lld too large", (long long)B);
+    return FMPB_EINVAL;
+  }
+  if (smem > 48 * 1024)
+    FMPB_CUDA(cudaFuncSetAttribute(k_block_product<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
+  for (int r0 = 0; r0 < R; r0 += RC) {
+    k_block_product<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows);
+    FMPB_CUDA(cudaGetLastError());
+  }
+  return FMPB_OK;
+}
+
+size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 * (size_t)s.F * R * B; }
+
+fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
+                            bool accumulate, cd* scratch, cudaStream_t st) {
+  const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
+  const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
+  const int64_t RB = (int64_t)R * B;
+  const int64_t Nc = s.ncells;
+  cd* A = scratch;
+  cd* G = scratch + (size_t)s.F * RB;
+  // forward x: x[r][cz][cy][cx][b] -> A[cz][cy][fx][r][b]
+  FMPB_TRY(dft_axis(x, A, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B, (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0,
+                    false, st));
+  // forward y: A[cz][cy][fx][rb] -> G[cz][fy][fx][rb]
+  FMPB_TRY(dft_axis(A, G, Mz, Px, RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, (int64_t)Py * Px * RB, RB,
+                    (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st));
+  // forward z: G[cz][fy fx][rb] -> A[fz][fy fx][rb]
+  FMPB_TRY(dft_axis(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz,
+                    -1, 1.0, false, st));
+  // per-frequency block products: A[f][r][b] -> G[f][r][b]
+  FMPB_TRY(block_product(spec, A, G, s.F, B, R, st));
+  // inverse z: G[fz][fy fx][rb] -> A[cz][fy fx][rb], cz < Mz
+  FMPB_TRY(dft_axis(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz, Mz, Pz,
+                    +1, 1.0, false, st));
+  // inverse y: A[cz][fy][fx][rb] -> G[cz][cy][fx][rb], cy < My
+  FMPB_TRY(dft_axis(A, G, Mz, Px, RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, (int64_t)My * Px * RB, RB,
+                    (int64_t)Px * RB, Py, My, Py, +1, 1.0, false, st));
+  // inverse x with crop and 1/F: G[cz][cy][fx][r][b] -> y[r][cz][cy][cx][b]
+  FMPB_TRY(dft_axis(G, y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B, (int64_t)Mx * B, B, Px, Mx, Px, +1,
+                    1.0 / (double)s.F, accumulate, st));
+  return FMPB_OK;
+}
+
+// Scatter blocks given in offset order (delta_x fastest, 1-M..M-1) into the
+// zeroed padded grid.
+__global__ void k_scatter_offsets(const cd* __restrict__ blocks, cd* __restrict__ grid, int64_t BB,
+                                  const int64_t* __restrict__ slot, int n_off) {
+  const size_t total = (size_t)BB * n_off;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(idx / BB);
+    const int64_t e = (int64_t)(idx - (size_t)o * BB);
+    grid[(size_t)slot[o] * BB + e] = blocks[idx];
+  }
+}
+
+fmpb_status circulant_spectrum_from_blocks(const CircShape& s, int64_t B, const cd* blocks, cd* spec,
+                                           cudaStream_t st) {
+  std::vector<int64_t> slots;
+  for (int dz = 1 - s.M[2]; dz < s.M[2]; ++dz)
+    for (int dy = 1 - s.M[1]; dy < s.M[1]; ++dy)
+      for (int dx = 1 - s.M[0]; dx < s.M[0]; ++dx) slots.push_back(offset_slot(s, dx, dy, dz));
+  const int n_off = (int)slots.size();
+  int64_t* dslot = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&dslot, sizeof(int64_t) * n_off, st));
+  FMPB_CUDA(cudaMemcpyAsync(dslot, slots.data(), sizeof(int64_t) * n_off, cudaMemcpyHostToDevice, st));
+  FMPB_CUDA(cudaMemsetAsync(spec, 0, sizeof(cd) * (size_t)s.F * B * B, st));
+  const size_t total = (size_t)B * B * n_off;
+  k_scatter_offsets<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(blocks, spec, B * B, dslot,
+                                                                                       n_off);
+  FMPB_CUDA(cudaGetLastError());
+  FMPB_TRY(grid_fft_inplace(s, B * B, spec, st));
+  FMPB_CUDA(cudaFreeAsync(dslot, st));
+  return FMPB_OK;
+}
+
+}  // namespace fmpb

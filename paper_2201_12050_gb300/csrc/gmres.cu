@@ -1,0 +1,398 @@
+// Restarted GMRES for R independent right-hand sides sharing each product
+// (Sec. 4: the systems of Eqs. (toeplitzBEM) and (FMPBEMsystem) are solved by
+// GMRES with a relative residual tolerance).  Every vector, the Hessenberg
+// columns and the Givens rotations live on the device in FP64; the Arnoldi
+// step is two-pass classical Gram-Schmidt.  The host sequences launches and
+// reads one residual estimate per RHS per iteration (the only device to host
+// traffic), and enforces the wall-clock limit between launches: no kernel
+// waits on anything.
+#include <chrono>
+#include <functional>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "gmres.cuh"
+
+namespace fmpb {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 64;   // partial sums per (vector, rhs)
+
+// partial[(v*R + r)*RED_BLOCKS + blk] = sum over chunk of conj(V_v[r]) w[r]
+__global__ void k_dots(const cd* __restrict__ V, int64_t vstride, int nvec, const cd* __restrict__ w, int R,
+                       int64_t N, cd* __restrict__ partial, const int* __restrict__ active) {
+  const int blk = blockIdx.x, v = blockIdx.y, r = blockIdx.z;
+  __shared__ double sre[RED_THREADS], sim[RED_THREADS];
+  double re = 0.0, im = 0.0;
+  if (active[r]) {
+    const cd* a = V + (int64_t)v * vstride + (int64_t)r * N;
+    const cd* b = w + (int64_t)r * N;
+    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+      cd x = a[i], y = b[i];
+      re = fma(x.x, y.x, fma(x.y, y.y, re));
+      im = fma(x.x, y.y, fma(-x.y, y.x, im));
+    }
+  }
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sre[threadIdx.x] += sre[threadIdx.x + s];
+      sim[threadIdx.x] += sim[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[((int64_t)v * R + r) * gridDim.x + blk] = mkc(sre[0], sim[0]);
+}
+
+// out[v*R + r] (+)= sum_blk partial  (fixed order: deterministic)
+__global__ void k_reduce_partials(const cd* __restrict__ partial, int nblk, int count, cd* __restrict__ out,
+                                  int accumulate) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  cd s = mkc(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(int64_t)t * nblk + b]);
+  out[t] = accumulate ? cadd(out[t], s) : s;
+}
+
+// w[r] -= sum_v V_v[r] h[v*R + r]
+__global__ void k_subtract_projection(const cd* __restrict__ V, int64_t vstride, int nvec,
+                                      const cd* __restrict__ h, cd* __restrict__ w, int R, int64_t N,
+                                      const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    cd acc = w[(int64_t)r * N + i];
+    for (int v = 0; v < nvec; ++v) {
+      cd hv = h[v * R + r];
+      cd a = V[(int64_t)v * vstride + (int64_t)r * N + i];
+      acc.x -= a.x * hv.x - a.y * hv.y;
+      acc.y -= a.x * hv.y + a.y * hv.x;
+    }
+    w[(int64_t)r * N + i] = acc;
+  }
+}
+
+// y[r] = x[r] * s[r]  (s real, per rhs; skipped for inactive rhs)
+__global__ void k_scale(const cd* __restrict__ x, cd* __restrict__ y, const double* __restrict__ s, int R,
+                        int64_t N, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  const double f = s[r];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    y[(int64_t)r * N + i] = cmulr(x[(int64_t)r * N + i], f);
+}
+
+// y = b - y  (residual from a product)
+__global__ void k_residual(const cd* __restrict__ b, cd* __restrict__ y, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = csub(b[i], y[i]);
+}
+
+// Per-RHS control state of one restart cycle.
+struct GmresState {
+  cd* H;           // R x (m+1) x m, column-major per rhs: H[r][j][i] at (r*m + j)*(m+1) + i
+  double* cs;      // R x m
+  cd* sn;          // R x m
+  cd* g;           // R x (m+1)
+  double* beta;    // R: ||r0||
+  double* inv;     // R: 1 / norm (scratch for k_scale)
+  double* bnorm;   // R
+  double* resid;   // R: current residual estimate / ||b||
+  int* active;     // R
+  int* jcount;     // R: Arnoldi columns completed this cycle
+};
+
+// Norms: sqrt(real(dot)) from the reduced dots.
+__global__ void k_sqrt_real(const cd* __restrict__ d, double* __restrict__ out, double* __restrict__ inv, int R) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double v = sqrt(fmax(d[r].x, 0.0));
+  out[r] = v;
+  if (inv) inv[r] = v > 0.0 ? 1.0 / v : 0.0;
+}
+
+// Start of a cycle: g = (beta, 0...), resid = beta / bnorm, active = resid > tol.
+__global__ void k_cycle_start(GmresState s, int R, int m, double tol) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  for (int i = 0; i <= m; ++i) s.g[r * (m + 1) + i] = mkc(0.0, 0.0);
+  s.g[r * (m + 1)] = mkc(s.beta[r], 0.0);
+  double rel = s.bnorm[r] > 0.0 ? s.beta[r] / s.bnorm[r] : 0.0;
+  s.resid[r] = rel;
+  s.active[r] = (rel > tol && s.beta[r] > 0.0) ? 1 : 0;
+  s.jcount[r] = 0;
+}
+
+// Column j of H from the projections h (nvec = j+1) and the norm of w;
+// applies the previous rotations, forms the new one, updates g and the
+// residual estimate.  One thread per rhs.
+__global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* __restrict__ wnorm, int R, int m,
+                         int j, double tol) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R || !s.active[r]) return;
+  cd* col = s.H + ((int64_t)r * m + j) * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h[i * R + r];
+  col[j + 1] = mkc(wnorm[r], 0.0);
+  for (int i = 0; i < j; ++i) {
+    // [c  s; -conj(s) c] applied to (col[i], col[i+1])
+    const double c = s.cs[r * m + i];
+    const cd sn = s.sn[r * m + i];
+    cd a = col[i], b = col[i + 1];
+    col[i] = cadd(cmulr(a, c), cmul(sn, b));
+    col[i + 1] = csub(cmulr(b, c), cmul(cconj(sn), a));
+  }
+  cd a = col[j], b = col[j + 1];
+  double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+  double c;
+  cd sn;
+  if (nb == 0.0) {
+    c = 1.0;
+    sn = mkc(0.0, 0.0);
+  } else if (na == 0.0) {
+    c = 0.0;
+    sn = mkc(1.0, 0.0);
+    a = mkc(0.0, 0.0);
+  } else {
+    double t = hypot(na, nb);
+    c = na / t;
+    // sn = (a/|a|) conj(b) / t
+    cd ua = mkc(a.x / na, a.y / na);
+    sn = cmulr(cmul(ua, cconj(b)), 1.0 / t);
+  }
+  s.cs[r * m + j] = c;
+  s.sn[r * m + j] = sn;
+  col[j] = cadd(cmulr(a, c), cmul(sn, b));
+  col[j + 1] = mkc(0.0, 0.0);
+  cd* g = s.g + r * (m + 1);
+  cd gj = g[j];
+  g[j] = cmulr(gj, c);
+  g[j + 1] = cmul(mkc(-sn.x, sn.y), gj);   // -conj(sn) g_j
+  s.jcount[r] = j + 1;
+  double rel = hypot(g[j + 1].x, g[j + 1].y) / s.bnorm[r];
+  s.resid[r] = rel;
+  if (rel <= tol || wnorm[r] == 0.0) s.active[r] = 0;
+}
+
+// Back substitution H y = g for the jcount[r] completed columns; y into g.
+__global__ void k_backsolve(GmresState s, int R, int m) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int J = s.jcount[r];
+  cd* g = s.g + r * (m + 1);
+  for (int i = J - 1; i >= 0; --i) {
+    cd acc = g[i];
+    for (int k = i + 1; k < J; ++k) acc = csub(acc, cmul(s.H[((int64_t)r * m + k) * (m + 1) + i], g[k]));
+    cd d = s.H[((int64_t)r * m + i) * (m + 1) + i];
+    double den = d.x * d.x + d.y * d.y;
+    g[i] = den > 0.0 ? mkc((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den) : mkc(0.0, 0.0);
+  }
+  for (int i = J; i <= m; ++i) g[i] = mkc(0.0, 0.0);
+}
+
+// x[r] += sum_{i < jcount[r]} V_i[r] y_i[r]
+__global__ void k_update_x(const cd* __restrict__ V, int64_t vstride, GmresState s, cd* __restrict__ x, int R,
+                           int m, int64_t N) {
+  const int r = blockIdx.y;
+  const int J = s.jcount[r];
+  if (J == 0) return;
+  const cd* y = s.g + r * (m + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    cd acc = x[(int64_t)r * N + i];
+    for (int v = 0; v < J; ++v) acc = cfma(V[(int64_t)v * vstride + (int64_t)r * N + i], y[v], acc);
+    x[(int64_t)r * N + i] = acc;
+  }
+}
+
+// NaN / Inf scan of the right-hand side.
+__global__ void k_finite_check(const cd* __restrict__ b, int64_t total, int* __restrict__ bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    cd v = b[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) *bad = 1;
+  }
+}
+
+namespace {
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
+                        fmpb_solve_info* info, cudaStream_t st) {
+  const double tol = o.tol > 0 ? o.tol : 1e-8;
+  const int m = o.restart > 0 ? o.restart : 30;
+  const int maxit = o.maxit > 0 ? o.maxit : 1000;
+  if (m > 200 || R < 1 || N < 1) {
+    set_error("gmres: restart must be 1..200 and R, N positive");
+    return FMPB_EINVAL;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t vstride = (int64_t)R * N;
+  // device memory: basis (m+1) R N, work vector R N, small state
+  DevBuf Vb, Wb, Sb, Pb;
+  const size_t small = sizeof(cd) * ((size_t)R * (m + 1) * m + (size_t)R * m + (size_t)R * (m + 1) +
+                                     (size_t)R * (m + 1) + 2 * (size_t)R) +
+                       sizeof(double) * (6 * (size_t)R + (size_t)R * m) + sizeof(int) * (3 * (size_t)R + 1) + 256;
+  if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
+      cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
+      cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 1) * R * RED_BLOCKS) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("gmres: cannot allocate the Krylov basis (%zu bytes)", sizeof(cd) * (size_t)(m + 2) * vstride);
+    return FMPB_ENOMEM;
+  }
+  cd* V = (cd*)Vb.p;
+  cd* W = (cd*)Wb.p;
+  cd* partial = (cd*)Pb.p;
+  char* sp = (char*)Sb.p;
+  auto take = [&](size_t bytes) {
+    char* p = sp;
+    sp += (bytes + 15) / 16 * 16;
+    return (void*)p;
+  };
+  GmresState s;
+  s.H = (cd*)take(sizeof(cd) * (size_t)R * (m + 1) * m);
+  s.sn = (cd*)take(sizeof(cd) * (size_t)R * m);
+  s.g = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+  cd* h = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+  cd* h2 = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+  cd* nrm2 = (cd*)take(sizeof(cd) * 2 * (size_t)R);
+  s.cs = (double*)take(sizeof(double) * (size_t)R * m);
+  s.beta = (double*)take(sizeof(double) * R);
+  s.inv = (double*)take(sizeof(double) * R);
+  s.bnorm = (double*)take(sizeof(double) * R);
+  s.resid = (double*)take(sizeof(double) * R);
+  double* wnorm = (double*)take(sizeof(double) * R);
+  double* dummy_inv = (double*)take(sizeof(double) * R);
+  s.active = (int*)take(sizeof(int) * R);
+  s.jcount = (int*)take(sizeof(int) * R);
+  int* all_active = (int*)take(sizeof(int) * R);
+  int* bad = (int*)take(sizeof(int));
+  (void)dummy_inv;
+
+  const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
+  const unsigned rb = grid_for(R, 64);
+
+  // all-active mask for norms of b and of true residuals
+  std::vector<int> ones(R, 1);
+  FMPB_CUDA(cudaMemcpyAsync(all_active, ones.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+  FMPB_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  k_finite_check<<<vec_blocks, 256, 0, st>>>(b, vstride, bad);
+  int hbad = 0;
+  FMPB_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FMPB_CUDA(cudaStreamSynchronize(st));
+  if (hbad) {
+    set_error("gmres: the right-hand side holds NaN or Inf");
+    return FMPB_ENAN;
+  }
+
+  auto norms = [&](const cd* X, double* out, double* invout) -> fmpb_status {
+    k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(X, 0, 1, X, R, N, partial, all_active);
+    k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0);
+    k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, out, invout, R);
+    FMPB_CUDA(cudaGetLastError());
+    return FMPB_OK;
+  };
+
+  FMPB_TRY(norms(b, s.bnorm, nullptr));
+  FMPB_CUDA(cudaMemsetAsync(x, 0, sizeof(cd) * vstride, st));
+
+  std::vector<double> hres(R), hbn(R);
+  std::vector<int> hact(R), iters(R, 0);
+  int total_it = 0;
+  bool timed_out = false;
+  bool first = true;
+  while (true) {
+    // r0 = b - A x  (x = 0 on the first cycle)
+    if (first) {
+      FMPB_CUDA(cudaMemcpyAsync(W, b, sizeof(cd) * vstride, cudaMemcpyDeviceToDevice, st));
+    } else {
+      FMPB_TRY(A(R, x, W, st));
+      k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride);
+    }
+    first = false;
+    FMPB_TRY(norms(W, s.beta, s.inv));
+    k_cycle_start<<<rb, 64, 0, st>>>(s, R, m, tol);
+    k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active);
+    FMPB_CUDA(cudaGetLastError());
+    FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    FMPB_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int r = 0; r < R; ++r) any |= hact[r] != 0;
+    if (!any) break;
+    for (int j = 0; j < m && total_it < maxit; ++j) {
+      cd* vj = V + (int64_t)j * vstride;
+      cd* vn = V + (int64_t)(j + 1) * vstride;
+      FMPB_TRY(A(R, vj, vn, st));
+      // two passes of classical Gram-Schmidt against v_0..v_j
+      k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active);
+      k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h, 0);
+      k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active);
+      k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active);
+      k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h2, 0);
+      k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, s.active);
+      k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1);
+      // ||w||, normalise
+      k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active);
+      k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0);
+      k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R);
+      k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, vn, s.inv, R, N, s.active);
+      k_givens<<<rb, 64, 0, st>>>(s, h, wnorm, R, m, j, tol);
+      FMPB_CUDA(cudaGetLastError());
+      ++total_it;
+      for (int r = 0; r < R; ++r)
+        if (hact[r]) iters[r]++;
+      FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+      FMPB_CUDA(cudaStreamSynchronize(st));
+      any = false;
+      for (int r = 0; r < R; ++r) any |= hact[r] != 0;
+      if (!any) break;
+      if (o.timeout_ms > 0 &&
+          std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+              o.timeout_ms) {
+        timed_out = true;
+        break;
+      }
+    }
+    k_backsolve<<<rb, 64, 0, st>>>(s, R, m);
+    k_update_x<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N);
+    FMPB_CUDA(cudaGetLastError());
+    if (!any || timed_out || total_it >= maxit) break;
+  }
+  // true residual with one more product
+  FMPB_TRY(A(R, x, W, st));
+  k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride);
+  FMPB_TRY(norms(W, s.beta, nullptr));
+  FMPB_CUDA(cudaMemcpyAsync(hres.data(), s.beta, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  FMPB_CUDA(cudaMemcpyAsync(hbn.data(), s.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  std::vector<double> hest(R);
+  FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  FMPB_CUDA(cudaStreamSynchronize(st));
+  bool all_conv = true;
+  for (int r = 0; r < R; ++r) {
+    double rel = hbn[r] > 0 ? hres[r] / hbn[r] : 0.0;
+    bool conv = hest[r] <= tol;
+    all_conv &= conv;
+    if (info) {
+      info[r].iters = iters[r];
+      info[r].converged = conv ? 1 : 0;
+      info[r].relres_est = hest[r];
+      info[r].relres_true = rel;
+    }
+  }
+  if (timed_out) {
+    set_error("gmres: wall-clock limit of %d ms reached", o.timeout_ms);
+    return FMPB_ETIMEOUT;
+  }
+  if (!all_conv) {
+    set_error("gmres: tolerance %.3g not reached within %d iterations", tol, maxit);
+    return FMPB_ENOCONV;
+  }
+  return FMPB_OK;
+}
+
+}  // namespace fmpb

@@ -1,0 +1,15 @@
+// Device GMRES driver (gmres.cu).
+#pragma once
+#include <functional>
+
+#include "common.cuh"
+
+namespace fmpb {
+
+// y = A x for R stacked vectors of length N on stream st.
+typedef std::function<fmpb_status(int R, const cd* x, cd* y, cudaStream_t st)> MatvecFn;
+
+fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
+                        fmpb_solve_info* info, cudaStream_t st);
+
+}  // namespace fmpb

@@ -1,0 +1,68 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <vector>
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fmpb {
+
+// Finite cell grid (Sec. 2.2): counts M[a] along lattice vectors L[a].
+struct CellGrid {
+  int M[3];
+  double L[3][3];
+  int ncells;
+  __host__ __device__ void cell_index(int c, int idx[3]) const {
+    idx[0] = c % M[0];
+    idx[1] = (c / M[0]) % M[1];
+    idx[2] = c / (M[0] * M[1]);
+  }
+  __host__ __device__ void cell_position(int c, double pos[3]) const {
+    int id[3];
+    cell_index(c, id);
+    for (int d = 0; d < 3; ++d) pos[d] = id[0] * L[0][d] + id[1] * L[1][d] + id[2] * L[2][d];
+  }
+};
+
+// Circulant embedding shape: padded lengths P[a] >= 2 M[a] - 1 (Sec. 2.4).
+struct CircShape {
+  int M[3];
+  int P[3];
+  int64_t F;
+  int64_t ncells;
+};
+int padded_length(int M);
+CircShape make_shape(const int M[3]);
+// Flat slot of offset delta in the padded grid: ((dz mod Pz) Py + (dy mod Py)) Px + (dx mod Px).
+int64_t offset_slot(const CircShape& s, int dx, int dy, int dz);
+
+struct DeviceMesh {
+  int n = 0;
+  Elem* el = nullptr;
+  QuadRules* qr_dev = nullptr;
+  QuadRules qr;
+  double radius = 0.0;   // max |vertex| about the origin (expansion centre)
+};
+
+fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, DeviceMesh& m,
+                        cudaStream_t st);
+void free_mesh(DeviceMesh& m);
+// Builds n_off collocation blocks; block o is written at out + dest[o] * n * n.
+fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n_off, const int32_t* offsets,
+                         const int64_t* dest_host, cd* out, cudaStream_t st);
+fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int R, const double* dirs_host,
+                           const fmpb_c64* amps_host, cd* b, cudaStream_t st);
+fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R, const cd* surf,
+                         const double* dirs_host, const fmpb_c64* amps_host, int64_t npts, const double* pts,
+                         cd* out, cudaStream_t st);
+
+// Circulant engine (circulant.cu)
+// In-place FFT over the padded grid of F slots, each holding `inner` values.
+fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st);
+// y (+)= T x through pruned FFT, block product, pruned inverse FFT.
+// scratch: 2 * F * R * B complex values.
+fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
+                            bool accumulate, cd* scratch, cudaStream_t st);
+size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R);
+
+}  // namespace fmpb

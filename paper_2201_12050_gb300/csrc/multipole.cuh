@@ -1,0 +1,25 @@
+// Multipole operators (multipole.cu).
+#pragma once
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace fmpb {
+
+constexpr int MAX_NT = 20;   // largest truncation number (B = 441)
+
+// q = n(n+1) + m  ->  (n, m)
+__host__ __device__ __forceinline__ void q_to_nm(int q, int& n, int& m) {
+  n = (int)sqrt((double)q);
+  while (n * n > q) --n;
+  while ((n + 1) * (n + 1) <= q) ++n;
+  m = q - n * (n + 1);
+}
+
+fmpb_status multipole_tables(const DeviceMesh& m, double k, int nt, cd* V0, cd* U0, cudaStream_t st);
+// K(d_o) for n_d translations; block o written at out + dest[o] B B (dest < 0 skipped).
+fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, const int64_t* dest_host, cd* out,
+                       cudaStream_t st);
+fmpb_status p2m_apply(const cd* V0, int n, int B, int64_t columns, const cd* p, cd* Mom, cudaStream_t st);
+fmpb_status l2p_apply(const cd* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st);
+
+}  // namespace fmpb

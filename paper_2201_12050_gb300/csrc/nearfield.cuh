@@ -1,0 +1,12 @@
+// Near-field product (nearfield.cu).
+#pragma once
+#include "common.cuh"
+
+namespace fmpb {
+
+// y (+)= sum_delta S_delta p_{c - delta}; offs_dev: n_near x 3 int offsets on
+// the device, S: n_near x n x n.
+fmpb_status near_apply(const cd* S, const int* offs_dev, int n_near, int n, const int M[3], int R, const cd* p, cd* y,
+                       bool accumulate, cudaStream_t st);
+
+}  // namespace fmpb

@@ -1,0 +1,520 @@
+// Collocation quadrature of the Burton-Miller operator for a rigid boundary
+// (Sec. 2.1, Eq. (bm) with dp/dn = 0) on flat triangles with constant
+// pressure: the offset blocks T_delta of the multilevel block Toeplitz form
+// (Sec. 2.2, Eq. (blockToeplizMatrix)), which are also the near-field blocks
+// S_delta of the FMPBEM (Sec. 3.2), the singular self term, the plane-wave
+// right-hand side and the field-point evaluation (Eq. (cbie), c = 1).
+//
+// Mesh normals n_m point into the fluid, the opposite of the paper's n, so
+//   T_delta[i][j] = 1/2 [self] - (D_ij + (i/k) H_ij),
+//   D_ij = int_{E_j} dG/dn_y,  H_ij = int_{E_j} d2G/dn_x dn_y  (mesh normals),
+// G = e^{ikr}/(4 pi r) (Eq. (green3dFull)).
+//
+// Quadrature rule (the operator's definition; d = |x_i - centroid_j|,
+// h = longest edge of E_j):
+//   d >= 4h        collapsed Gauss-Legendre 3x3 with apex v0,
+//   1.5h <= d < 4h collapsed 8x8,
+//   d < 1.5h       collapsed 8x8 on each of the four midpoint children,
+//   self           closed-form Hadamard finite part of r^-3 plus the polar
+//                  8x8 remainder on the children (x, v_a, v_b).
+// Collapsed rule of order q on (a, b, c): y(s,t) = a + s[(b-a) + t(c-b)],
+// dA = 2 area s ds dt, Gauss-Legendre nodes in s and t.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace fmpb {
+
+// ------------------------------------------------------------ geometry ----
+__global__ void k_prepare_elements(const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                                   int n, Elem* __restrict__ el) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  Elem E;
+  for (int a = 0; a < 3; ++a) {
+    int vid = tris[3 * e + a];
+    for (int d = 0; d < 3; ++d) E.v[a][d] = verts[3 * vid + d];
+  }
+  double e1[3], e2[3], cr[3];
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = E.v[1][d] - E.v[0][d];
+    e2[d] = E.v[2][d] - E.v[0][d];
+  }
+  cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+  E.area = 0.5 * len;
+  for (int d = 0; d < 3; ++d) {
+    E.nrm[d] = cr[d] / len;
+    E.c[d] = (E.v[0][d] + E.v[1][d] + E.v[2][d]) / 3.0;
+  }
+  double h = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    int b = (a + 1) % 3;
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double t = E.v[b][d] - E.v[a][d];
+      s += t * t;
+    }
+    h = fmax(h, sqrt(s));
+  }
+  E.hmax = h;
+  el[e] = E;
+}
+
+// Gauss-Legendre nodes/weights on [0,1] by Newton's method on P_q (three-term
+// recurrence), one thread per node.
+__device__ void gl_node(int q, int i, double* t, double* w) {
+  double x = cos(PI * (i + 0.75) / (q + 0.5));
+  double p0 = 1.0, p1 = x, dp = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    p0 = 1.0;
+    p1 = x;
+    for (int n = 2; n <= q; ++n) {
+      double p2 = ((2 * n - 1) * x * p1 - (n - 1) * p0) / n;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = q * (x * p1 - p0) / (x * x - 1.0);
+    double dx = p1 / dp;
+    x -= dx;
+    if (fabs(dx) < 1e-16) break;
+  }
+  p0 = 1.0;
+  p1 = x;
+  for (int n = 2; n <= q; ++n) {
+    double p2 = ((2 * n - 1) * x * p1 - (n - 1) * p0) / n;
+    p0 = p1;
+    p1 = p2;
+  }
+  dp = q * (x * p1 - p0) / (x * x - 1.0);
+  *t = 0.5 * (1.0 - x);                    // ascending order on [0, 1]
+  *w = 1.0 / ((1.0 - x * x) * dp * dp);    // 2/((1-x^2) P_q'^2), halved for [0, 1]
+}
+
+__global__ void k_gauss_legendre(QuadRules* qr) {
+  int i = threadIdx.x;
+  if (i < Q_FAR) gl_node(Q_FAR, i, &qr->t3[i], &qr->w3[i]);
+  if (i < Q_NEAR) gl_node(Q_NEAR, i, &qr->t8[i], &qr->w8[i]);
+}
+
+// ------------------------------------------------------------- kernels ----
+// Accumulates w*dG/dn_y into D and w*d2G/dn_x dn_y into H at one point.
+__device__ __forceinline__ void kernel_point(const double x[3], const double nx[3], const double y[3],
+                                             const double ny[3], double w, double k, cd& D, cd& H) {
+  const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  const double r = sqrt(r2);
+  const double ir = 1.0 / r;
+  const double kr = k * r;
+  double s, c;
+  sincos(kr, &s, &c);
+  const double dny = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
+  const double dnx = d0 * nx[0] + d1 * nx[1] + d2 * nx[2];
+  const double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
+  const double inv4pi = 0.25 / PI;
+  const double ir3 = ir * ir * ir;
+  // e^{ikr}(1 - ikr)
+  const double a_re = c + s * kr, a_im = s - c * kr;
+  const double f = w * dny * ir3 * inv4pi;
+  D.x = fma(a_re, f, D.x);
+  D.y = fma(a_im, f, D.y);
+  // e^{ikr}(3 - k^2 r^2 - 3ikr)
+  const double t = 3.0 - kr * kr;
+  const double b_re = c * t + 3.0 * s * kr, b_im = s * t - 3.0 * c * kr;
+  const double g1 = w * nn * ir3 * inv4pi;
+  const double g2 = w * dnx * dny * ir3 * ir * ir * inv4pi;
+  H.x += a_re * g1 - b_re * g2;
+  H.y += a_im * g1 - b_im * g2;
+}
+
+template <int Q>
+__device__ __forceinline__ void integrate_collapsed(const double a[3], const double b[3], const double cc[3],
+                                                    double two_area, const double* t, const double* w,
+                                                    const double x[3], const double nx[3], const double ny[3],
+                                                    double k, cd& D, cd& H) {
+  double ba[3], cb[3];
+  for (int d = 0; d < 3; ++d) {
+    ba[d] = b[d] - a[d];
+    cb[d] = cc[d] - b[d];
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double s = t[i];
+    const double ws = two_area * s * w[i];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      double y[3];
+      for (int d = 0; d < 3; ++d) y[d] = a[d] + s * (ba[d] + t[j] * cb[d]);
+      kernel_point(x, nx, y, ny, ws * w[j], k, D, H);
+    }
+  }
+}
+
+// D, H of element E (translated by shift) seen from (x, nx), by class.
+__device__ void element_dh(const Elem& E, const double shift[3], const double x[3], const double nx[3],
+                           double k, const QuadRules& qr, cd& D, cd& H) {
+  double v[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) v[a][d] = E.v[a][d] + shift[d];
+  double dc[3];
+  for (int d = 0; d < 3; ++d) dc[d] = x[d] - (E.c[d] + shift[d]);
+  const double dist = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
+  const double two_area = 2.0 * E.area;
+  D = mkc(0.0, 0.0);
+  H = mkc(0.0, 0.0);
+  if (dist >= FAR_RATIO * E.hmax) {
+    integrate_collapsed<Q_FAR>(v[0], v[1], v[2], two_area, qr.t3, qr.w3, x, nx, E.nrm, k, D, H);
+  } else if (dist >= NEAR_RATIO * E.hmax) {
+    integrate_collapsed<Q_NEAR>(v[0], v[1], v[2], two_area, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+  } else {
+    double m01[3], m12[3], m20[3];
+    for (int d = 0; d < 3; ++d) {
+      m01[d] = 0.5 * (v[0][d] + v[1][d]);
+      m12[d] = 0.5 * (v[1][d] + v[2][d]);
+      m20[d] = 0.5 * (v[2][d] + v[0][d]);
+    }
+    const double ta = 0.25 * two_area;
+    integrate_collapsed<Q_NEAR>(v[0], m01, m20, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+    integrate_collapsed<Q_NEAR>(m01, v[1], m12, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+    integrate_collapsed<Q_NEAR>(m20, m12, v[2], ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+    integrate_collapsed<Q_NEAR>(m01, m12, m20, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+  }
+}
+
+// T = -(D + (i/k) H)
+__device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
+  return mkc(-D.x + H.y / k, -D.y - H.x / k);
+}
+
+// One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
+// out + dest[o] * n * n.  The diagonal of the zero offset is left to
+// k_self_terms.
+__global__ void k_build_blocks(const Elem* __restrict__ el, int n, const double* __restrict__ shifts,
+                               const int64_t* __restrict__ dest, int n_off, int zero_off, cd* __restrict__ out,
+                               double k, QuadRules qr) {
+  const size_t nn = (size_t)n * n;
+  const size_t total = nn * (size_t)n_off;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(idx / nn);
+    const size_t rem = idx - (size_t)o * nn;
+    const int i = (int)(rem / n);
+    const int j = (int)(rem - (size_t)i * n);
+    if (o == zero_off && i == j) continue;
+    const Elem& Ti = el[i];
+    double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
+    double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
+    double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
+    cd D, H;
+    element_dh(el[j], sh, x, nx, k, qr, D, H);
+    out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
+  }
+}
+
+// sin x - x cos x without cancellation: series for |x| < 0.5.
+__device__ double sin_minus_xcos(double x) {
+  if (fabs(x) < 0.5) {
+    double x2 = x * x, term = x * x2, acc = 0.0;
+    // (-1)^{j+1} 2j x^{2j+1} / (2j+1)!
+    double fact = 6.0;   // 3!
+    for (int j = 1; j <= 9; ++j) {
+      double c = ((j & 1) ? 1.0 : -1.0) * 2.0 * j / fact;
+      acc += c * term;
+      term *= x2;
+      fact *= (double)(2 * j + 2) * (double)(2 * j + 3);
+    }
+    return acc;
+  }
+  double s, c;
+  sincos(x, &s, &c);
+  return s - x * c;
+}
+
+// Self term of element i (x_i at its centroid, on the flat panel):
+// D_ii = 0, H_ii = (1/4pi)[fp int r^-3 + int (e^{ikr}(1-ikr) - 1) r^-3].
+__global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict__ block0, double k,
+                             QuadRules qr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Elem& E = el[i];
+  const double* x = E.c;
+  double fp = 0.0;
+  for (int e = 0; e < 3; ++e) {
+    const double* a = E.v[e];
+    const double* b = E.v[(e + 1) % 3];
+    double eh[3], am[3], bm[3];
+    double L = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      eh[d] = b[d] - a[d];
+      L += eh[d] * eh[d];
+      am[d] = a[d] - x[d];
+      bm[d] = b[d] - x[d];
+    }
+    L = sqrt(L);
+    for (int d = 0; d < 3; ++d) eh[d] /= L;
+    double ta = am[0] * eh[0] + am[1] * eh[1] + am[2] * eh[2];
+    double tb = bm[0] * eh[0] + bm[1] * eh[1] + bm[2] * eh[2];
+    double hv[3] = {am[0] - ta * eh[0], am[1] - ta * eh[1], am[2] - ta * eh[2]};
+    double he = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+    double ra = sqrt(am[0] * am[0] + am[1] * am[1] + am[2] * am[2]);
+    double rb = sqrt(bm[0] * bm[0] + bm[1] * bm[1] + bm[2] * bm[2]);
+    fp -= (tb / rb - ta / ra) / he;
+  }
+  double rem_re = 0.0, rem_im = 0.0;
+  for (int e = 0; e < 3; ++e) {
+    const double* a = E.v[e];
+    const double* b = E.v[(e + 1) % 3];
+    double ax[3], ba[3], cr[3];
+    for (int d = 0; d < 3; ++d) {
+      ax[d] = a[d] - x[d];
+      ba[d] = b[d] - a[d];
+    }
+    double bx[3] = {b[0] - x[0], b[1] - x[1], b[2] - x[2]};
+    cr[0] = ax[1] * bx[2] - ax[2] * bx[1];
+    cr[1] = ax[2] * bx[0] - ax[0] * bx[2];
+    cr[2] = ax[0] * bx[1] - ax[1] * bx[0];
+    const double two_area = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    for (int p = 0; p < Q_SELF; ++p) {
+      const double s = qr.t8[p];
+      const double ws = two_area * s * qr.w8[p];
+      for (int q = 0; q < Q_SELF; ++q) {
+        double y[3];
+        for (int d = 0; d < 3; ++d) y[d] = x[d] + s * (ax[d] + qr.t8[q] * ba[d]);
+        double dx = y[0] - x[0], dy = y[1] - x[1], dz = y[2] - x[2];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double kr = k * r;
+        double sh = sin(0.5 * kr);
+        double re = -2.0 * sh * sh + kr * sin(kr);   // cos kr + kr sin kr - 1
+        double im = sin_minus_xcos(kr);              // sin kr - kr cos kr
+        double wr = ws * qr.w8[q] / (r * r * r);
+        rem_re += wr * re;
+        rem_im += wr * im;
+      }
+    }
+  }
+  const double inv4pi = 0.25 / PI;
+  cd H = mkc((fp + rem_re) * inv4pi, rem_im * inv4pi);
+  // 1/2 - (i/k) H
+  block0[(size_t)i * n + i] = mkc(0.5 + H.y / k, -H.x / k);
+}
+
+// ------------------------------------------------------- right-hand side --
+__global__ void k_rhs_plane_wave(const Elem* __restrict__ el, int n, CellGrid g, double k, int R,
+                                 const double* __restrict__ dirs, const cd* __restrict__ amps,
+                                 cd* __restrict__ b) {
+  const size_t N = (size_t)n * g.ncells;
+  const size_t total = N * R;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / N);
+    const size_t gi = idx - (size_t)r * N;
+    const int c = (int)(gi / n);
+    const int i = (int)(gi - (size_t)c * n);
+    double pos[3];
+    g.cell_position(c, pos);
+    const Elem& E = el[i];
+    const double* dv = dirs + 3 * r;
+    double ph = 0.0, dn = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      ph += dv[d] * (E.c[d] + pos[d]);
+      dn += dv[d] * E.nrm[d];
+    }
+    double s, co;
+    sincos(k * ph, &s, &co);
+    cd pinc = cmul(amps[r], mkc(co, s));
+    // p_inc + (i/k) * i k (d.n) p_inc = p_inc (1 - d.n)
+    b[idx] = cmulr(pinc, 1.0 - dn);
+  }
+}
+
+// ---------------------------------------------------------- field points --
+// out[r][p] = p_inc,r(x_p) + sum_{c, j} D(x_p, E_j + pos_c) surf[r][c*n + j]
+__global__ void k_field(const Elem* __restrict__ el, int n, CellGrid g, double k, int R,
+                        const double* __restrict__ dirs, const cd* __restrict__ amps,
+                        const cd* __restrict__ surf, int64_t npts, const double* __restrict__ pts,
+                        cd* __restrict__ out, QuadRules qr) {
+  const size_t total = (size_t)npts * R;
+  const size_t N = (size_t)n * g.ncells;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / npts);
+    const int64_t p = (int64_t)(idx - (size_t)r * npts);
+    double x[3] = {pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]};
+    double nx[3] = {0.0, 0.0, 1.0};
+    const double* dv = dirs + 3 * r;
+    double ph = dv[0] * x[0] + dv[1] * x[1] + dv[2] * x[2];
+    double s, co;
+    sincos(k * ph, &s, &co);
+    cd acc = cmul(amps[r], mkc(co, s));
+    for (int c = 0; c < g.ncells; ++c) {
+      double pos[3];
+      g.cell_position(c, pos);
+      for (int j = 0; j < n; ++j) {
+        cd D, H;
+        element_dh(el[j], pos, x, nx, k, qr, D, H);
+        acc = cfma(D, surf[(size_t)r * N + (size_t)c * n + j], acc);
+      }
+    }
+    out[idx] = acc;
+  }
+}
+
+// ------------------------------------------------------------ host side --
+fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, DeviceMesh& m,
+                        cudaStream_t st) {
+  if (!verts || !tris || nv < 3 || ntri < 1 || ntri > (1 << 20)) {
+    set_error("mesh: need verts (nv >= 3), tris (1 <= ntri <= 2^20)");
+    return FMPB_EINVAL;
+  }
+  // host validation: indices in range, finite coordinates, non-degenerate triangles
+  for (int64_t e = 0; e < 3 * nv; ++e)
+    if (!std::isfinite(verts[e])) {
+      set_error("mesh: vertex coordinate %lld is not finite", (long long)e);
+      return FMPB_EMESH;
+    }
+  for (int64_t t = 0; t < ntri; ++t) {
+    const int32_t* tv = tris + 3 * t;
+    for (int a = 0; a < 3; ++a)
+      if (tv[a] < 0 || tv[a] >= nv) {
+        set_error("mesh: triangle %lld references vertex %d (nv = %lld)", (long long)t, tv[a], (long long)nv);
+        return FMPB_EMESH;
+      }
+    const double* a = verts + 3 * tv[0];
+    const double* b = verts + 3 * tv[1];
+    const double* c = verts + 3 * tv[2];
+    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double l1 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    double l2 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    double ca = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
+    if (!(ca > 1e-24 * l1 * l2)) {
+      set_error("mesh: triangle %lld has (near) zero area", (long long)t);
+      return FMPB_EMESH;
+    }
+  }
+  m.n = (int)ntri;
+  double* dverts = nullptr;
+  int32_t* dtris = nullptr;
+  FMPB_CUDA(cudaMalloc(&dverts, sizeof(double) * 3 * nv));
+  cudaError_t e = cudaMalloc(&dtris, sizeof(int32_t) * 3 * ntri);
+  if (e == cudaSuccess) e = cudaMalloc(&m.el, sizeof(Elem) * ntri);
+  if (e == cudaSuccess) e = cudaMalloc(&m.qr_dev, sizeof(QuadRules));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dverts, verts, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dtris, tris, sizeof(int32_t) * 3 * ntri, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_prepare_elements<<<grid_for(ntri, 128), 128, 0, st>>>(dverts, dtris, (int)ntri, m.el);
+    k_gauss_legendre<<<1, 32, 0, st>>>(m.qr_dev);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&m.qr, m.qr_dev, sizeof(QuadRules), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dverts);
+  cudaFree(dtris);
+  if (e != cudaSuccess) return cuda_status(e, "upload_mesh");
+  // cell radius about the origin (expansion centre), from the host copy
+  double rho = 0.0;
+  for (int64_t t = 0; t < ntri; ++t)
+    for (int a = 0; a < 3; ++a) {
+      const double* v = verts + 3 * tris[3 * t + a];
+      rho = fmax(rho, sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    }
+  m.radius = rho;
+  return FMPB_OK;
+}
+
+void free_mesh(DeviceMesh& m) {
+  if (m.el) cudaFree(m.el);
+  if (m.qr_dev) cudaFree(m.qr_dev);
+  m.el = nullptr;
+  m.qr_dev = nullptr;
+}
+
+fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n_off, const int32_t* offsets,
+                         const int64_t* dest_host, cd* out, cudaStream_t st) {
+  // shifts: -delta . lattice
+  std::vector<double> shifts(3 * (size_t)n_off);
+  int zero_off = -1;
+  for (int o = 0; o < n_off; ++o) {
+    const int32_t* dl = offsets + 3 * o;
+    if (dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
+    for (int d = 0; d < 3; ++d)
+      shifts[3 * o + d] = -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
+  }
+  double* dshift = nullptr;
+  int64_t* ddest = nullptr;
+  FMPB_CUDA(cudaMalloc(&dshift, sizeof(double) * 3 * n_off));
+  cudaError_t e = cudaMalloc(&ddest, sizeof(int64_t) * n_off);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dshift, shifts.data(), sizeof(double) * 3 * n_off, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ddest, dest_host, sizeof(int64_t) * n_off, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    const size_t total = (size_t)m.n * m.n * n_off;
+    unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
+    k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.n, dshift, ddest, n_off, zero_off, out, k, m.qr);
+    if (zero_off >= 0)
+      k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
+                                                     k, m.qr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dshift);
+  cudaFree(ddest);
+  if (e != cudaSuccess) return cuda_status(e, "build_blocks");
+  return FMPB_OK;
+}
+
+fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int R, const double* dirs_host,
+                           const fmpb_c64* amps_host, cd* b, cudaStream_t st) {
+  std::vector<double> dirs(3 * (size_t)R);
+  std::vector<cd> amps(R);
+  for (int r = 0; r < R; ++r) {
+    double nrm = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      dirs[3 * r + d] = dirs_host[3 * r + d];
+      nrm += dirs[3 * r + d] * dirs[3 * r + d];
+    }
+    if (!(fabs(nrm - 1.0) < 1e-6)) {
+      set_error("rhs: direction %d is not a unit vector", r);
+      return FMPB_EINVAL;
+    }
+    amps[r] = amps_host ? mkc(amps_host[r].re, amps_host[r].im) : mkc(1.0, 0.0);
+  }
+  double* ddirs = nullptr;
+  cd* damps = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&ddirs, sizeof(double) * 3 * R, st));
+  FMPB_CUDA(cudaMallocAsync(&damps, sizeof(cd) * R, st));
+  FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
+  FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
+  const size_t total = (size_t)m.n * g.ncells * R;
+  k_rhs_plane_wave<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(m.el, m.n, g, k, R, ddirs,
+                                                                                      damps, b);
+  FMPB_CUDA(cudaGetLastError());
+  FMPB_CUDA(cudaFreeAsync(ddirs, st));
+  FMPB_CUDA(cudaFreeAsync(damps, st));
+  return FMPB_OK;
+}
+
+fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R, const cd* surf,
+                         const double* dirs_host, const fmpb_c64* amps_host, int64_t npts, const double* pts,
+                         cd* out, cudaStream_t st) {
+  std::vector<double> dirs(dirs_host, dirs_host + 3 * (size_t)R);
+  std::vector<cd> amps(R);
+  for (int r = 0; r < R; ++r) amps[r] = amps_host ? mkc(amps_host[r].re, amps_host[r].im) : mkc(1.0, 0.0);
+  double* ddirs = nullptr;
+  cd* damps = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&ddirs, sizeof(double) * 3 * R, st));
+  FMPB_CUDA(cudaMallocAsync(&damps, sizeof(cd) * R, st));
+  FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
+  FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
+  const size_t total = (size_t)npts * R;
+  k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, m.n, g, k, R, ddirs, damps,
+                                                                             surf, npts, pts, out, m.qr);
+  FMPB_CUDA(cudaGetLastError());
+  FMPB_CUDA(cudaFreeAsync(ddirs, st));
+  FMPB_CUDA(cudaFreeAsync(damps, st));
+  return FMPB_OK;
+}
+
+}  // namespace fmpb

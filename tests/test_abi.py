@@ -1,0 +1,55 @@
+"""The C ABI library loads and exports every entry point declared in
+include/fmpb.h; host-only calls and argument checking work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fmpb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmpb_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2201_12050_gb300 import build
+    build.build()
+    from paper_2201_12050_gb300 import lib
+    return lib()
+
+
+def test_every_declared_symbol_is_exported_and_bound(L):
+    from paper_2201_12050_gb300._lib import SIGNATURES
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(SIGNATURES) == names
+
+
+def test_host_only_calls(L):
+    from paper_2201_12050_gb300 import circulant_shape, FmpbError
+    assert L.fmpb_version() == (0 << 16) | 1
+    # smallest 2,3,5,7-smooth P >= 2M - 1 (Sec. 2.4 embedding; any P >= 2M-1 is exact)
+    assert circulant_shape([3, 20, 1]) == ([5, 40, 1], 200)
+    assert circulant_shape([32, 32]) == ([63, 63, 1], 3969)
+    assert circulant_shape([16, 16, 4]) == ([32, 32, 7], 7168)
+    assert circulant_shape([6]) == ([12, 1, 1], 12)      # 11 is not smooth
+    with pytest.raises(FmpbError) as e:
+        circulant_shape([0, 1, 1])
+    assert e.value.name == "FMPB_EINVAL"
+
+
+def test_argument_errors_are_statuses_not_crashes(L):
+    h = ctypes.c_void_p()
+    st = L.fmpb_operator_create(None, 0, None, 0, None, 1.0, None, None, None)
+    assert st == -1 and b"NULL" in L.fmpb_last_error()
+    st = L.fmpb_operator_create(None, 0, None, 0, None, -1.0, None, None, ctypes.byref(h))
+    assert st == -1 and b"wavenumber" in L.fmpb_last_error()
+    assert L.fmpb_matvec(None, 1, None, None, None) == -1
+    L.fmpb_operator_destroy(None)
