@@ -19,7 +19,8 @@ rule below is part of the operator's definition and the GPU library
 generates the same rule from the same description:
   * collapsed Gauss-Legendre rule of order q on a triangle (a, b, c) with apex
     a: y(s,t) = a + s[(b-a) + t(c-b)], dA = 2 area s ds dt, q x q nodes;
-  * d = |x_i - centroid_j|, h_j = longest edge of E_j:
+  * d = |x_i - centroid_j|, h_j = longest edge of E_j, thresholds scaled by
+    (1 + 1e-9) so that exact ties go to the more accurate class:
       far        d >= 4 h_j          : q = 3 on E_j (apex v0)
       near       1.5 h_j <= d < 4 h_j: q = 8 on E_j
       very near  d < 1.5 h_j, j != i : q = 8 on each of the four midpoint
@@ -33,6 +34,9 @@ import numpy as np
 
 FAR_RATIO = 4.0
 NEAR_RATIO = 1.5
+# ties (d/h within 1e-9 of a threshold, which regular meshes produce exactly)
+# go to the more accurate class, so that rounding cannot flip a decision
+TIE = 1e-9
 Q_FAR = 3
 Q_NEAR = 8
 Q_SELF = 8
@@ -165,8 +169,8 @@ def self_hyp(tri_v, k):
 def classify(x, cen, hmax):
     d = np.linalg.norm(x - cen, axis=-1)
     cls = np.full(d.shape, 2, dtype=np.int8)          # very near
-    cls[d >= NEAR_RATIO * hmax] = 1                  # near
-    cls[d >= FAR_RATIO * hmax] = 0                   # far
+    cls[d >= NEAR_RATIO * (1.0 + TIE) * hmax] = 1    # near
+    cls[d >= FAR_RATIO * (1.0 + TIE) * hmax] = 0     # far
     return cls
 
 

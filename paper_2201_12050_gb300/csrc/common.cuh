@@ -48,8 +48,11 @@ struct QuadRules {
   double t8[Q_NEAR], w8[Q_NEAR];
 };
 
-constexpr double FAR_RATIO = 4.0;
-constexpr double NEAR_RATIO = 1.5;
+// Class thresholds on d/h, scaled by (1 + 1e-9) so that exact ties (which
+// regular meshes produce) go to the more accurate class on every machine.
+constexpr double TIE = 1e-9;
+constexpr double FAR_RATIO = 4.0 * (1.0 + TIE);
+constexpr double NEAR_RATIO = 1.5 * (1.0 + TIE);
 constexpr double PI = 3.14159265358979323846;
 
 // ----------------------------------------------------------- status ------

@@ -235,44 +235,50 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   const int64_t vstride = (int64_t)R * N;
   // device memory: basis (m+1) R N, work vector R N, small state
   DevBuf Vb, Wb, Sb, Pb;
-  const size_t small = sizeof(cd) * ((size_t)R * (m + 1) * m + (size_t)R * m + (size_t)R * (m + 1) +
-                                     (size_t)R * (m + 1) + 2 * (size_t)R) +
-                       sizeof(double) * (6 * (size_t)R + (size_t)R * m) + sizeof(int) * (3 * (size_t)R + 1) + 256;
-  if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
-      cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
-      cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 1) * R * RED_BLOCKS) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("gmres: cannot allocate the Krylov basis (%zu bytes)", sizeof(cd) * (size_t)(m + 2) * vstride);
-    return FMPB_ENOMEM;
+  // control state: carve one allocation; the first pass (base = null) sizes it
+  GmresState s;
+  cd *h = nullptr, *h2 = nullptr, *nrm2 = nullptr;
+  double *wnorm = nullptr;
+  int *all_active = nullptr, *bad = nullptr;
+  size_t small = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    char* base = (char*)Sb.p;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+      void* p = base ? (void*)(base + off) : nullptr;
+      off += (bytes + 255) / 256 * 256;
+      return p;
+    };
+    s.H = (cd*)take(sizeof(cd) * (size_t)R * (m + 1) * m);
+    s.sn = (cd*)take(sizeof(cd) * (size_t)R * m);
+    s.g = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+    h = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+    h2 = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+    nrm2 = (cd*)take(sizeof(cd) * (size_t)R);
+    s.cs = (double*)take(sizeof(double) * (size_t)R * m);
+    s.beta = (double*)take(sizeof(double) * R);
+    s.inv = (double*)take(sizeof(double) * R);
+    s.bnorm = (double*)take(sizeof(double) * R);
+    s.resid = (double*)take(sizeof(double) * R);
+    wnorm = (double*)take(sizeof(double) * R);
+    s.active = (int*)take(sizeof(int) * R);
+    s.jcount = (int*)take(sizeof(int) * R);
+    all_active = (int*)take(sizeof(int) * R);
+    bad = (int*)take(sizeof(int));
+    if (pass == 0) {
+      small = off;
+      if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
+          cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
+          cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 1) * R * RED_BLOCKS) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("gmres: cannot allocate the Krylov basis (%zu bytes)", sizeof(cd) * (size_t)(m + 2) * vstride);
+        return FMPB_ENOMEM;
+      }
+    }
   }
   cd* V = (cd*)Vb.p;
   cd* W = (cd*)Wb.p;
   cd* partial = (cd*)Pb.p;
-  char* sp = (char*)Sb.p;
-  auto take = [&](size_t bytes) {
-    char* p = sp;
-    sp += (bytes + 15) / 16 * 16;
-    return (void*)p;
-  };
-  GmresState s;
-  s.H = (cd*)take(sizeof(cd) * (size_t)R * (m + 1) * m);
-  s.sn = (cd*)take(sizeof(cd) * (size_t)R * m);
-  s.g = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
-  cd* h = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
-  cd* h2 = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
-  cd* nrm2 = (cd*)take(sizeof(cd) * 2 * (size_t)R);
-  s.cs = (double*)take(sizeof(double) * (size_t)R * m);
-  s.beta = (double*)take(sizeof(double) * R);
-  s.inv = (double*)take(sizeof(double) * R);
-  s.bnorm = (double*)take(sizeof(double) * R);
-  s.resid = (double*)take(sizeof(double) * R);
-  double* wnorm = (double*)take(sizeof(double) * R);
-  double* dummy_inv = (double*)take(sizeof(double) * R);
-  s.active = (int*)take(sizeof(int) * R);
-  s.jcount = (int*)take(sizeof(int) * R);
-  int* all_active = (int*)take(sizeof(int) * R);
-  int* bad = (int*)take(sizeof(int));
-  (void)dummy_inv;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
   const unsigned rb = grid_for(R, 64);

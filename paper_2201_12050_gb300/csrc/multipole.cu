@@ -149,7 +149,7 @@ __device__ void sph_bessel_j(int nmax, double x, double* j) {
     return;
   }
   int N0 = nmax + 24 + (int)(1.5 * x);
-  double fp1 = 0.0, f = 1e-280, norm = 0.0;
+  double fp1 = 0.0, f = 1.0, norm = 0.0;
   for (int n = N0; n >= 0; --n) {
     // f = f_n (unnormalised); store n <= nmax
     if (n <= nmax) j[n] = f;

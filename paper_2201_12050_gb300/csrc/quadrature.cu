@@ -11,7 +11,8 @@
 // G = e^{ikr}/(4 pi r) (Eq. (green3dFull)).
 //
 // Quadrature rule (the operator's definition; d = |x_i - centroid_j|,
-// h = longest edge of E_j):
+// h = longest edge of E_j; thresholds scaled by 1 + 1e-9, ties to the more
+// accurate class):
 //   d >= 4h        collapsed Gauss-Legendre 3x3 with apex v0,
 //   1.5h <= d < 4h collapsed 8x8,
 //   d < 1.5h       collapsed 8x8 on each of the four midpoint children,
