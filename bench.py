@@ -1,0 +1,402 @@
+"""Benchmark of the FMPBEM/PBEM hot path on the sonic-crystal barrier workload.
+
+Workload: 3 x 20 rigid capped cylinders (r = 0.15 m, h = 3.0 m, square lattice
+0.4 m), 1,200 flat triangles per cell, N = 72,000 dofs, plane wave at 30 deg
+azimuth, frequencies 100..1000 Hz in 10 steps.  The cells are too tall for
+the cell-as-box multipole expansion, so the library builds the PBEM form:
+195 dense offset blocks, FFT over the padded 5 x 40 cell grid, circulant
+products inside GMRES.
+
+One step = one frequency of the sweep: operator build (collocation quadrature
+of every offset block, FFT of the first block column), plane-wave right-hand
+side, GMRES to relative residual 1e-8 (restart 30).  value = solves/s over K
+steps timed with CUDA events; e2e = the same through the public API with host
+buffers and the surface pressure copied back.  Under torchrun each rank runs
+its own frequencies (replicas, weak scaling) and the slowest rank's time
+counts.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import WORKLOADS, random_complex_vectors, SPEED_OF_SOUND  # noqa: E402
+
+WORKLOAD = "sonic_crystal_3x20"
+TOL = 1e-8
+RESTART = 30
+METRIC = "GMRES solves/s (operator build + solve, tol 1e-8) at N=72,000"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config_block(w, extra=None):
+    cfg = {
+        "workload": "sonic_crystal_3x20: 3x20 rigid capped cylinders r=0.15 h=3.0, lattice 0.4 m, "
+                    "1200 tri/cell, N=72000, PBEM form (195 offset blocks, P=5x40), 10 freqs 100-1000 Hz",
+        "N": 72000,
+        "frequencies_hz": [round(k * SPEED_OF_SOUND / (2 * math.pi), 3) for k in w.wavenumbers],
+        "gmres": {"tol": TOL, "restart": RESTART},
+        "l2": "inputs larger than L2: the 4.6 GB spectrum is streamed by every product",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------ clock probe --
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(index)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- our arm --
+
+def run_ours(args):
+    import torch
+    import paper_2201_12050_gb300 as gb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = WORKLOADS[WORKLOAD]
+    v, t = w.mesh()
+    ks = w.wavenumbers
+    d = w.directions
+    nf = len(ks)
+
+    def step(i):
+        k = ks[(i * world + rank) % nf]
+        op = gb.Operator(v, t, w.counts, w.lattice, k)
+        b = op.rhs_plane_wave(d)
+        p, info = op.solve(b, tol=TOL, restart=RESTART)
+        return op, p, info
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        op, p, info = step(i)
+        op.close()
+    barrier()
+    clocks = ClockSampler(local)
+    gb.profile_reset()
+    gb.profile_enable(True)
+    launches0 = gb.kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    iters = []
+    for i in range(args.steps):
+        op, p, info = step(args.warmup + i)
+        iters.append(info[0]["iters"])
+        relres = info[0]["relres_true"]
+        op.close()
+    e1.record(stream)
+    barrier()
+    gb.profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    launches = gb.kernel_launches() - launches0
+    prof = gb.profile_summary()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = args.steps * world / (ms / 1e3)
+
+    # product throughput on one operator (100 Hz), and the block-product roofline
+    op = gb.Operator(v, t, w.counts, w.lattice, ks[0])
+    info_op = op.info
+    x = torch.as_tensor(random_complex_vectors(w.rhs_seed, 1, op.N), device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.matvec(x, out=y)
+    torch.cuda.synchronize()
+    gb.profile_reset()
+    gb.profile_enable(True)
+    nmv = 20
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(nmv):
+        op.matvec(x, out=y)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    gb.profile_enable(False)
+    mv_ms = m0.elapsed_time(m1) / nmv
+    mv_prof = gb.profile_summary()
+    B, F = info_op["B"], info_op["F"]
+    spec_bytes = F * B * B * 16
+    bp_launches, bp_ms = mv_prof.get("block_product", (nmv, float("nan")))
+    bp_bytes = spec_bytes + 2 * F * B * 16           # spectrum once + X in + Y out, per launch
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    bp_gbs = bp_bytes / (bp_ms / bp_launches / 1e3) / 1e9
+
+    # e2e through the public API: host mesh in, host pressure out, wall clock
+    e2e_steps = max(2, min(args.steps, 4))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for i in range(e2e_steps):
+        k = ks[(i * world + rank) % nf]
+        op2 = gb.Operator(v, t, w.counts, w.lattice, k)
+        b = op2.rhs_plane_wave(d)
+        p, info = op2.solve(b, tol=TOL, restart=RESTART)
+        ph = p.cpu()
+        h2d += v.nbytes + t.nbytes + d.nbytes
+        d2h += ph.numel() * 16
+        op2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_steps * world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d // e2e_steps,
+           "d2h_bytes_per_step": d2h // e2e_steps}
+
+    # dominant kernel of the timed steps
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    total_prof = sum(v_[1] for v_ in prof.values())
+    roof = dominant_roofline(dom, prof, w, v, t, args.steps, hbm_peak, peaks, bp_gbs)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(w, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
+        "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+        "matvec": {"value": 1e3 / mv_ms, "unit": "matvecs/s", "ms": mv_ms,
+                   "block_product": {"bytes_per_launch": bp_bytes, "ms_per_launch": bp_ms / bp_launches,
+                                     "achieved_gbs": bp_gbs, "peak_gbs": hbm_peak,
+                                     "frac": bp_gbs / hbm_peak, "peak_source": "measured hbm_gbs" if peaks.get("hbm_gbs") else "fallback"},
+                   "kernels_ms_per_matvec": {k_: v_[1] / nmv for k_, v_ in mv_prof.items()}},
+        "gmres_iters": iters, "relres_true_last": relres,
+        "kernels_share": {k_: round(v_[1] / total_prof, 4) for k_, v_ in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "operator": {"form": info_op["form_name"], "B": B, "P": info_op["P"], "F": F,
+                     "bytes_device": info_op["bytes_device"]},
+    }
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, v, t, iters)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+QUAD_POINTS = {0: 9, 1: 64, 2: 256}
+FLOPS_PER_POINT = 80      # FP64 operations of one kernel evaluation
+
+
+def quadrature_points(w, v, t):
+    """Quadrature points evaluated by one PBEM build: pairs per class x rule size."""
+    from workloads.meshes import capped_cylinder  # noqa: F401  (mesh already given)
+    verts = np.asarray(v, dtype=float)
+    tri = verts[np.asarray(t)]
+    cen = tri.mean(axis=1)
+    h = np.max(np.linalg.norm(tri - np.roll(tri, 1, axis=1), axis=2), axis=1)
+    M = w.counts
+    L = np.asarray(w.lattice, dtype=float)
+    total = 0
+    for dz in range(1 - M[2], M[2]):
+        for dy in range(1 - M[1], M[1]):
+            for dx in range(1 - M[0], M[0]):
+                sh = -np.array([dx, dy, dz], dtype=float) @ L
+                dist = np.linalg.norm(cen[:, None, :] - (cen[None, :, :] + sh), axis=2)
+                r = dist / h[None, :]
+                far = r >= 4.0 * (1 + 1e-9)
+                near = (~far) & (r >= 1.5 * (1 + 1e-9))
+                vnear = ~(far | near)
+                if dx == 0 and dy == 0 and dz == 0:
+                    vnear[np.arange(len(t)), np.arange(len(t))] = False
+                total += 9 * far.sum() + 64 * near.sum() + 256 * vnear.sum()
+    return int(total)
+
+
+def dominant_roofline(dom, prof, w, v, t, steps, hbm_peak, peaks, bp_gbs):
+    name, (launches, total_ms) = dom
+    per_launch_s = total_ms / launches / 1e3
+    if name == "build_blocks":
+        pts = quadrature_points(w, v, t)
+        flops = pts * FLOPS_PER_POINT
+        achieved = flops / per_launch_s / 1e12
+        peak = 1.25      # FP64 FLOP/s of GB300 (nominal table; FMA-chain probe measured 1.2)
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "launches": launches,
+                "ms_per_launch": per_launch_s * 1e3, "work_per_launch": {"quadrature_points": pts,
+                                                                         "fp64_flops": flops},
+                "peak_source": "nominal FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)"}
+    if name == "block_product":
+        return {"kernel": name, "bound": "hbm", "achieved": bp_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bp_gbs / hbm_peak, "traffic": None, "launches": launches,
+                "ms_per_launch": per_launch_s * 1e3, "peak_source": "measured hbm_gbs"}
+    return {"kernel": name, "bound": "unmodelled", "launches": launches, "ms_per_launch": per_launch_s * 1e3,
+            "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
+
+
+# --------------------------------------------------- CPU oracle baseline --
+
+def _oracle_sample(w, v, t, k, n_rows, iters):
+    """Times the oracle on a bounded sample of one solve: n_rows target rows of
+    every offset block (quadrature) and one explicit block-Toeplitz product at
+    full size (all 3,600 cell pairs, one shared 1200x1200 block for timing).
+    Returns (seconds for the sample, extrapolated seconds per full solve)."""
+    from oracle import bem
+    cell = bem.CellMesh(v, t)
+    n = cell.n
+    rows = np.linspace(0, n - 1, n_rows).astype(int)
+
+    class Rows:
+        centroid = cell.centroid[rows]
+        normal = cell.normal[rows]
+
+    Rows.n = len(rows)
+    L = np.asarray(w.lattice, dtype=float)
+    t0 = time.perf_counter()
+    for delta in bem.all_offsets(w.counts):
+        shift = -np.asarray(delta, dtype=float) @ L
+        selfp = None
+        if not any(delta):
+            selfp = np.zeros((len(rows), n), dtype=bool)
+            selfp[np.arange(len(rows)), rows] = True
+        bem.dh_block(Rows, cell.v + shift, k, self_pairs=selfp)
+    t_rows = time.perf_counter() - t0
+    blk = np.asarray(random_complex_vectors(w.rhs_seed + 7, n, n))
+    blocks = {d_: blk for d_ in bem.all_offsets(w.counts)}
+    x = random_complex_vectors(w.rhs_seed, 1, n * int(np.prod(w.counts)))
+    t0 = time.perf_counter()
+    bem.toeplitz_matvec(blocks, w.counts, x)
+    t_mv = time.perf_counter() - t0
+    n_mv = (max(iters) if iters else 40) + 2
+    full = t_rows * n / n_rows + t_mv * n_mv
+    return t_rows + t_mv, full
+
+
+def _cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(w, v, t, iters, n_rows=24):
+    sample_s, full_s = _oracle_sample(w, v, t, w.wavenumbers[0], n_rows, iters)
+    return {"value": 1.0 / full_s, "unit": "solves/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{n_rows} of 1200 target rows of all 195 offset blocks (quadrature) + 1 explicit "
+                      f"block-Toeplitz product at full size, extrapolated to 1200 rows + "
+                      f"{(max(iters) if iters else 40) + 2} products; sample took {sample_s:.1f} s",
+            "seconds_per_solve_extrapolated": full_s}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    w = WORKLOADS[WORKLOAD]
+    v, t = w.mesh()
+    iters = [40]
+    for _ in range(args.warmup):
+        _oracle_sample(w, v, t, w.wavenumbers[0], 1, iters)
+    tot = 0.0
+    for i in range(args.steps):
+        _, full = _oracle_sample(w, v, t, w.wavenumbers[i % len(w.wavenumbers)], 1, iters)
+        tot += full
+    value = args.steps / tot
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": config_block(w, {"parallelism": "cpu oracle"}),
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": _cores(), "kind": "oracle",
+                            "sample": "per step: 1 of 1200 target rows of all 195 offset blocks + 1 full-size "
+                                      "explicit block-Toeplitz product, extrapolated to a 42-product solve"},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

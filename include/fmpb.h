@@ -84,9 +84,11 @@ int fmpb_version(void);
 typedef struct fmpb_operator fmpb_operator;
 
 typedef struct {
-  int form;        /* fmpb_form; AUTO picks FMM when every far cell pair is
-                      separated by more than the two cells' enclosing radii
-                      (the convergence condition of Eq. (greenFMM)), else PBEM */
+  int form;        /* fmpb_form; AUTO picks FMM when the nearest far cell
+                      (|delta|_inf >= 2) lies at least 3 cell radii away, so that
+                      the two-centre expansion of Eq. (greenFMM) converges with
+                      ratio 2 rho / |d| <= 2/3; else PBEM.  FMM forced with
+                      |d| <= 2 rho is refused (EADMISS). */
   int n_t;         /* truncation number of the FMM form (Eq. (greenFMM)), 1..20;
                       0 = default 8 */
   int precision;   /* fmpb_precision of the product; FMPB_FP64 only in this version */
@@ -252,6 +254,23 @@ fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fm
  */
 fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
                                  const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Telemetry (no counterpart in the paper; it reports wall-clock times of
+ * assembly and products only, Sec. 4).
+ * ---------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in the process. */
+uint64_t fmpb_kernel_launches(void);
+/* Enables (1) or disables (0) per-kernel timing: a CUDA event pair recorded
+ * on the launching stream around every kernel launch from then on. */
+void fmpb_profile_enable(int on);
+/* Drops the recorded timings (events are recycled). */
+fmpb_status fmpb_profile_reset(void);
+/* Waits for the recorded events and writes a JSON object
+ * {"kernel": [launches, total_ms], ...} into buf (len bytes, NUL-terminated).
+ * EINVAL if buf is too small. */
+fmpb_status fmpb_profile_summary(char *buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -188,3 +188,24 @@ def circulant_apply(counts, spec, x, out=None, accumulate=False):
     y = out if out is not None else torch.empty_like(x)
     check(lib().fmpb_circulant_apply(_ptr(c), B, _ptr(spec), R, _ptr(x), _ptr(y), 1 if accumulate else 0, _stream()))
     return y
+
+
+def kernel_launches() -> int:
+    """fmpb_kernel_launches: kernels launched by the library in this process."""
+    return int(lib().fmpb_kernel_launches())
+
+
+def profile_enable(on: bool = True):
+    lib().fmpb_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    check(lib().fmpb_profile_reset())
+
+
+def profile_summary() -> dict:
+    """Per-kernel {name: (launches, total_ms)} of the recorded launches."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib().fmpb_profile_summary(buf, len(buf)))
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}

@@ -17,6 +17,7 @@
 // outer, coefficient inner); spectrum [f][b][b'] row-major.
 #include "common.cuh"
 #include "internal.cuh"
+#include "profile.cuh"
 
 namespace fmpb {
 
@@ -109,8 +110,8 @@ static fmpb_status dft_axis(const cd* in, cd* out, int O1, int O2, int64_t I, in
   size_t smem = (size_t)(Pin * TI + P) * sizeof(cd);
   if (smem > 48 * 1024) FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
-  k_dft_axis<<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
-                                      accumulate ? 1 : 0, (int)TI);
+  FMPB_LAUNCH("dft_axis", st, k_dft_axis<<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
+                                      accumulate ? 1 : 0, (int)TI));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -185,7 +186,7 @@ static fmpb_status block_product(const cd* spec, const cd* X, cd* Y, int64_t F, 
     FMPB_CUDA(cudaFuncSetAttribute(k_block_product<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
   for (int r0 = 0; r0 < R; r0 += RC) {
-    k_block_product<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows);
+    FMPB_LAUNCH("block_product", st, k_block_product<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
     FMPB_CUDA(cudaGetLastError());
   }
   return FMPB_OK;
@@ -249,8 +250,8 @@ fmpb_status circulant_spectrum_from_blocks(const CircShape& s, int64_t B, const 
   FMPB_CUDA(cudaMemcpyAsync(dslot, slots.data(), sizeof(int64_t) * n_off, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemsetAsync(spec, 0, sizeof(cd) * (size_t)s.F * B * B, st));
   const size_t total = (size_t)B * B * n_off;
-  k_scatter_offsets<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(blocks, spec, B * B, dslot,
-                                                                                       n_off);
+  FMPB_LAUNCH("scatter_offsets", st, k_scatter_offsets<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(blocks, spec, B * B, dslot,
+                                                                                       n_off));
   FMPB_CUDA(cudaGetLastError());
   FMPB_TRY(grid_fft_inplace(s, B * B, spec, st));
   FMPB_CUDA(cudaFreeAsync(dslot, st));

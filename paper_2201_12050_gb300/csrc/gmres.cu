@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "profile.cuh"
 #include "gmres.cuh"
 
 namespace fmpb {
@@ -287,7 +288,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   std::vector<int> ones(R, 1);
   FMPB_CUDA(cudaMemcpyAsync(all_active, ones.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  k_finite_check<<<vec_blocks, 256, 0, st>>>(b, vstride, bad);
+  FMPB_LAUNCH("finite_check", st, k_finite_check<<<vec_blocks, 256, 0, st>>>(b, vstride, bad));
   int hbad = 0;
   FMPB_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   FMPB_CUDA(cudaStreamSynchronize(st));
@@ -297,9 +298,9 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   }
 
   auto norms = [&](const cd* X, double* out, double* invout) -> fmpb_status {
-    k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(X, 0, 1, X, R, N, partial, all_active);
-    k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0);
-    k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, out, invout, R);
+    FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(X, 0, 1, X, R, N, partial, all_active));
+    FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0));
+    FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, out, invout, R));
     FMPB_CUDA(cudaGetLastError());
     return FMPB_OK;
   };
@@ -318,12 +319,12 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       FMPB_CUDA(cudaMemcpyAsync(W, b, sizeof(cd) * vstride, cudaMemcpyDeviceToDevice, st));
     } else {
       FMPB_TRY(A(R, x, W, st));
-      k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride);
+      FMPB_LAUNCH("residual", st, k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride));
     }
     first = false;
     FMPB_TRY(norms(W, s.beta, s.inv));
-    k_cycle_start<<<rb, 64, 0, st>>>(s, R, m, tol);
-    k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active);
+    FMPB_LAUNCH("cycle_start", st, k_cycle_start<<<rb, 64, 0, st>>>(s, R, m, tol));
+    FMPB_LAUNCH("scale", st, k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active));
     FMPB_CUDA(cudaGetLastError());
     FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
     FMPB_CUDA(cudaStreamSynchronize(st));
@@ -335,19 +336,19 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       cd* vn = V + (int64_t)(j + 1) * vstride;
       FMPB_TRY(A(R, vj, vn, st));
       // two passes of classical Gram-Schmidt against v_0..v_j
-      k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active);
-      k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h, 0);
-      k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active);
-      k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active);
-      k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h2, 0);
-      k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, s.active);
-      k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1);
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h, 0));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h2, 0));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
       // ||w||, normalise
-      k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active);
-      k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0);
-      k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R);
-      k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, vn, s.inv, R, N, s.active);
-      k_givens<<<rb, 64, 0, st>>>(s, h, wnorm, R, m, j, tol);
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0));
+      FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R));
+      FMPB_LAUNCH("scale", st, k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, vn, s.inv, R, N, s.active));
+      FMPB_LAUNCH("givens", st, k_givens<<<rb, 64, 0, st>>>(s, h, wnorm, R, m, j, tol));
       FMPB_CUDA(cudaGetLastError());
       ++total_it;
       for (int r = 0; r < R; ++r)
@@ -364,14 +365,14 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         break;
       }
     }
-    k_backsolve<<<rb, 64, 0, st>>>(s, R, m);
-    k_update_x<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N);
+    FMPB_LAUNCH("backsolve", st, k_backsolve<<<rb, 64, 0, st>>>(s, R, m));
+    FMPB_LAUNCH("update_x", st, k_update_x<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
     FMPB_CUDA(cudaGetLastError());
     if (!any || timed_out || total_it >= maxit) break;
   }
   // true residual with one more product
   FMPB_TRY(A(R, x, W, st));
-  k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride);
+  FMPB_LAUNCH("residual", st, k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride));
   FMPB_TRY(norms(W, s.beta, nullptr));
   FMPB_CUDA(cudaMemcpyAsync(hres.data(), s.beta, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   FMPB_CUDA(cudaMemcpyAsync(hbn.data(), s.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));

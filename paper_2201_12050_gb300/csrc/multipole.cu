@@ -18,6 +18,7 @@
 //   K(d)[q][q'] = (2n'+1)(-1)^{m+m'} sum_l W O_l^{m+m'}(d),  d = x_c - y_c.
 #include "common.cuh"
 #include "internal.cuh"
+#include "profile.cuh"
 #include "multipole.cuh"
 
 namespace fmpb {
@@ -463,8 +464,8 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, int nt, cd* V0, cd* 
   }
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
-  if (V0) k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, m.qr, V0);
-  if (U0) k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, U0);
+  if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, m.qr, V0));
+  if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, U0));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -474,7 +475,7 @@ fmpb_status wigner_table(int nt, double** W3out, cudaStream_t st) {
   const size_t count = (size_t)B * B * (nt + 1);
   double* W3 = nullptr;
   FMPB_CUDA(cudaMallocAsync(&W3, sizeof(double) * count, st));
-  k_wigner_table<<<std::min<size_t>(grid_for(count, 128), 152 * 8), 128, 0, st>>>(nt, W3);
+  FMPB_LAUNCH("wigner_table", st, k_wigner_table<<<std::min<size_t>(grid_for(count, 128), 152 * 8), 128, 0, st>>>(nt, W3));
   FMPB_CUDA(cudaGetLastError());
   *W3out = W3;
   return FMPB_OK;
@@ -496,7 +497,7 @@ fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, cons
   FMPB_CUDA(cudaMemcpyAsync(dd_, dvecs_host, sizeof(double) * 3 * n_d, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemcpyAsync(dst, dest_host, sizeof(int64_t) * n_d, cudaMemcpyHostToDevice, st));
   const size_t smem = 3 * sizeof(double) * (2 * nt + 1) * (2 * nt + 1);
-  k_m2l_blocks<<<n_d, 256, smem, st>>>(nt, k, dd_, dst, W3, out);
+  FMPB_LAUNCH("m2l_blocks", st, k_m2l_blocks<<<n_d, 256, smem, st>>>(nt, k, dd_, dst, W3, out));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(dd_, st));
   FMPB_CUDA(cudaFreeAsync(dst, st));
@@ -505,13 +506,13 @@ fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, cons
 }
 
 fmpb_status p2m_apply(const cd* V0, int n, int B, int64_t columns, const cd* p, cd* Mom, cudaStream_t st) {
-  k_p2m_apply<<<(unsigned)columns, 256, sizeof(cd) * n, st>>>(V0, n, B, p, Mom);
+  FMPB_LAUNCH("p2m_apply", st, k_p2m_apply<<<(unsigned)columns, 256, sizeof(cd) * n, st>>>(V0, n, B, p, Mom));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
 
 fmpb_status l2p_apply(const cd* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st) {
-  k_l2p_apply<<<(unsigned)columns, 256, sizeof(cd) * B, st>>>(U0, n, B, Loc, y);
+  FMPB_LAUNCH("l2p_apply", st, k_l2p_apply<<<(unsigned)columns, 256, sizeof(cd) * B, st>>>(U0, n, B, Loc, y));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }

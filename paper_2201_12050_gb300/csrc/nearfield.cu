@@ -6,6 +6,7 @@
 // n x Nc matrix of cell vectors gathered with offset delta.
 #include "common.cuh"
 #include "internal.cuh"
+#include "profile.cuh"
 #include "nearfield.cuh"
 
 namespace fmpb {
@@ -84,7 +85,7 @@ fmpb_status near_apply(const cd* S, const int* offs_dev, int n_near, int n, cons
     return FMPB_EINVAL;
   }
   dim3 grid((unsigned)((Nc + NT_C - 1) / NT_C), (unsigned)((n + NT_I - 1) / NT_I), (unsigned)R);
-  k_near_apply<<<grid, 256, 0, st>>>(S, offs_dev, n_near, n, M[0], M[1], M[2], p, y, accumulate ? 1 : 0);
+  FMPB_LAUNCH("near_apply", st, k_near_apply<<<grid, 256, 0, st>>>(S, offs_dev, n_near, n, M[0], M[1], M[2], p, y, accumulate ? 1 : 0));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }

@@ -22,6 +22,7 @@
 // dA = 2 area s ds dt, Gauss-Legendre nodes in s and t.
 #include "common.cuh"
 #include "internal.cuh"
+#include "profile.cuh"
 
 namespace fmpb {
 
@@ -405,8 +406,8 @@ fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, in
   if (e == cudaSuccess) e = cudaMemcpyAsync(dverts, verts, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dtris, tris, sizeof(int32_t) * 3 * ntri, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    k_prepare_elements<<<grid_for(ntri, 128), 128, 0, st>>>(dverts, dtris, (int)ntri, m.el);
-    k_gauss_legendre<<<1, 32, 0, st>>>(m.qr_dev);
+    FMPB_LAUNCH("prepare_elements", st, k_prepare_elements<<<grid_for(ntri, 128), 128, 0, st>>>(dverts, dtris, (int)ntri, m.el));
+    FMPB_LAUNCH("gauss_legendre", st, k_gauss_legendre<<<1, 32, 0, st>>>(m.qr_dev));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&m.qr, m.qr_dev, sizeof(QuadRules), cudaMemcpyDeviceToHost, st);
@@ -453,10 +454,10 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
   if (e == cudaSuccess) {
     const size_t total = (size_t)m.n * m.n * n_off;
     unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
-    k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.n, dshift, ddest, n_off, zero_off, out, k, m.qr);
+    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.n, dshift, ddest, n_off, zero_off, out, k, m.qr));
     if (zero_off >= 0)
-      k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
-                                                     k, m.qr);
+      FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
+                                                     k, m.qr));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -489,8 +490,8 @@ fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int
   FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
   const size_t total = (size_t)m.n * g.ncells * R;
-  k_rhs_plane_wave<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(m.el, m.n, g, k, R, ddirs,
-                                                                                      damps, b);
+  FMPB_LAUNCH("rhs_plane_wave", st, k_rhs_plane_wave<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(m.el, m.n, g, k, R, ddirs,
+                                                                                      damps, b));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(ddirs, st));
   FMPB_CUDA(cudaFreeAsync(damps, st));
@@ -510,8 +511,8 @@ fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R
   FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
   const size_t total = (size_t)npts * R;
-  k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, m.n, g, k, R, ddirs, damps,
-                                                                             surf, npts, pts, out, m.qr);
+  FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, m.n, g, k, R, ddirs, damps,
+                                                                             surf, npts, pts, out, m.qr));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(ddirs, st));
   FMPB_CUDA(cudaFreeAsync(damps, st));

@@ -234,7 +234,7 @@ def test_solver_failure_statuses_are_reported_without_faults():
         op.solve(bad)
     assert e.value.name == "FMPB_ENAN"
     with pytest.raises(gb.FmpbError) as e:
-        gb.Operator(v, t, (6, 1, 1), np.eye(3) * 0.3, 2.0, form=gb.FORM_FMM)
+        gb.Operator(v, t, (6, 1, 1), np.eye(3) * 0.19, 2.0, form=gb.FORM_FMM)
     assert e.value.name == "FMPB_EADMISS"
     bad_t = t.copy()
     bad_t[3, 1] = 10_000
