@@ -36,7 +36,8 @@ from workloads import WORKLOADS, random_complex_vectors, SPEED_OF_SOUND  # noqa:
 
 WORKLOAD = "sonic_crystal_3x20"
 TOL = 1e-8
-RESTART = 30
+RESTART = 200          # the 3x20 crystal near its Bragg frequency needs long Krylov bases
+MAXIT = 3000
 METRIC = "GMRES solves/s (operator build + solve, tol 1e-8) at N=72,000"
 
 
@@ -62,7 +63,7 @@ def config_block(w, extra=None):
                     "1200 tri/cell, N=72000, PBEM form (195 offset blocks, P=5x40), 10 freqs 100-1000 Hz",
         "N": 72000,
         "frequencies_hz": [round(k * SPEED_OF_SOUND / (2 * math.pi), 3) for k in w.wavenumbers],
-        "gmres": {"tol": TOL, "restart": RESTART},
+        "gmres": {"tol": TOL, "restart": RESTART, "maxit": MAXIT, "x0": 0},
         "l2": "inputs larger than L2: the 4.6 GB spectrum is streamed by every product",
     }
     if extra:
@@ -145,7 +146,7 @@ def run_ours(args):
         k = ks[(i * world + rank) % nf]
         op = gb.Operator(v, t, w.counts, w.lattice, k)
         b = op.rhs_plane_wave(d)
-        p, info = op.solve(b, tol=TOL, restart=RESTART)
+        p, info = op.solve(b, tol=TOL, restart=RESTART, maxit=MAXIT, raise_on_noconv=False)
         return op, p, info
 
     def barrier():
@@ -166,11 +167,12 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
-    iters = []
+    iters, relres, conv = [], [], []
     for i in range(args.steps):
         op, p, info = step(args.warmup + i)
         iters.append(info[0]["iters"])
-        relres = info[0]["relres_true"]
+        relres.append(info[0]["relres_true"])
+        conv.append(info[0]["converged"])
         op.close()
     e1.record(stream)
     barrier()
@@ -223,7 +225,7 @@ def run_ours(args):
         k = ks[(i * world + rank) % nf]
         op2 = gb.Operator(v, t, w.counts, w.lattice, k)
         b = op2.rhs_plane_wave(d)
-        p, info = op2.solve(b, tol=TOL, restart=RESTART)
+        p, info = op2.solve(b, tol=TOL, restart=RESTART, maxit=MAXIT, raise_on_noconv=False)
         ph = p.cpu()
         h2d += v.nbytes + t.nbytes + d.nbytes
         d2h += ph.numel() * 16
@@ -249,7 +251,7 @@ def run_ours(args):
                                      "achieved_gbs": bp_gbs, "peak_gbs": hbm_peak,
                                      "frac": bp_gbs / hbm_peak, "peak_source": "measured hbm_gbs" if peaks.get("hbm_gbs") else "fallback"},
                    "kernels_ms_per_matvec": {k_: v_[1] / nmv for k_, v_ in mv_prof.items()}},
-        "gmres_iters": iters, "relres_true_last": relres,
+        "gmres": {"iters": iters, "relres_true_max": max(relres), "all_converged": all(conv)},
         "kernels_share": {k_: round(v_[1] / total_prof, 4) for k_, v_ in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "operator": {"form": info_op["form_name"], "B": B, "P": info_op["P"], "F": F,
                      "bytes_device": info_op["bytes_device"]},

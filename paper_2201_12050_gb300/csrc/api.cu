@@ -87,7 +87,7 @@ struct fmpb_operator {
   int nt = 0;
   int64_t B = 0;
   int dim = 0;
-  cd* spec = nullptr;      // F x B x B
+  cd* spec = nullptr;      // F x B x B, float-float pairs (re_hi, re_lo, im_hi, im_lo) per entry
   cd* S = nullptr;         // n_near x n x n (FMM form)
   int* near_offs = nullptr;
   int n_near = 0;
@@ -124,7 +124,7 @@ struct fmpb_operator {
     const int64_t Nc = shape.ncells;
     if (form == FMPB_FORM_PBEM) {
       FMPB_TRY(ensure_scratch(circulant_scratch_elems(shape, B, R)));
-      return circulant_apply(shape, B, spec, R, x, y, false, scratch, st);
+      return circulant_apply(shape, B, spec, R, x, y, false, scratch, st, true);
     }
     const size_t circ = circulant_scratch_elems(shape, B, R);
     const size_t mom = (size_t)R * Nc * B;
@@ -133,7 +133,7 @@ struct fmpb_operator {
     cd* Loc = Mom + mom;
     FMPB_TRY(near_apply(S, near_offs, n_near, mesh.n, shape.M, R, x, y, false, st));
     FMPB_TRY(p2m_apply(V0, mesh.n, (int)B, (int64_t)R * Nc, x, Mom, st));
-    FMPB_TRY(circulant_apply(shape, B, spec, R, Mom, Loc, false, scratch, st));
+    FMPB_TRY(circulant_apply(shape, B, spec, R, Mom, Loc, false, scratch, st, true));
     FMPB_TRY(l2p_apply(U0, mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
     return FMPB_OK;
   }
@@ -236,6 +236,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     s = build_blocks(op->mesh, op->grid, k, n_off, all_off.data(), dest.data(), op->spec, st);
     if (s != FMPB_OK) return fail(s);
     s = grid_fft_inplace(sh, (int64_t)n * n, op->spec, st);
+    if (s == FMPB_OK) s = spectrum_to_ff(op->spec, (size_t)sh.F * n * n, st);
     if (s != FMPB_OK) return fail(s);
   } else {
     op->nt = nt;
@@ -268,6 +269,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     }
     s = m2l_blocks(nt, k, n_far, dvec.data(), dfar.data(), op->spec, st);
     if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec, st);
+    if (s == FMPB_OK) s = spectrum_to_ff(op->spec, (size_t)sh.F * B * B, st);
     if (s != FMPB_OK) return fail(s);
   }
   cudaError_t e = cudaStreamSynchronize(st);

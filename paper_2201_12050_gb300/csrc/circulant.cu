@@ -169,6 +169,155 @@ __global__ void k_block_product(const cd* __restrict__ spec, const cd* __restric
   }
 }
 
+// ------------------------------------------------ float-float products ----
+// GB300 runs FP64 at 1/58 of its FP32 rate, so the operator keeps its
+// spectrum as float-float pairs (re_hi, re_lo, im_hi, im_lo): the same 16
+// bytes per entry as complex double, hi + lo carrying 48 significand bits.
+// Products use exact FP32 products (fma residual) and two-sum accumulation,
+// giving FP64-level accuracy (about 2^-47 per product) on the FP32 pipe.
+__device__ __forceinline__ float4 split_ff(cd v) {
+  const float rh = __double2float_rn(v.x);
+  const float ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (sh, sl) += a * x for a, x float-float complex; re and im separately.
+__device__ __forceinline__ void ff_cmac(const float4 a, const float4 x, float& rh, float& rl, float& ih, float& il) {
+  // hi x hi products with their exact rounding errors
+  const float p1 = a.x * x.x, e1 = fmaf(a.x, x.x, -p1);   // ar xr
+  const float p2 = a.z * x.z, e2 = fmaf(a.z, x.z, -p2);   // ai xi
+  const float p3 = a.x * x.z, e3 = fmaf(a.x, x.z, -p3);   // ar xi
+  const float p4 = a.z * x.x, e4 = fmaf(a.z, x.x, -p4);   // ai xr
+  // cross terms hi x lo + lo x hi
+  const float cr = fmaf(a.x, x.y, fmaf(a.y, x.x, -fmaf(a.z, x.w, a.w * x.z)));
+  const float ci = fmaf(a.x, x.w, fmaf(a.y, x.z, fmaf(a.z, x.y, a.w * x.x)));
+  float d, ed, s, es;
+  two_sum_f(p1, -p2, d, ed);
+  two_sum_f(rh, d, s, es);
+  rh = s;
+  rl += (es + ed) + ((e1 - e2) + cr);
+  two_sum_f(p3, p4, d, ed);
+  two_sum_f(ih, d, s, es);
+  ih = s;
+  il += (es + ed) + ((e3 + e4) + ci);
+}
+
+// warp sum of a float-float value
+__device__ __forceinline__ void ff_warp_sum(float& h, float& l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum_f(h, oh, s, e);
+    h = s;
+    l = l + ol + e;
+  }
+}
+
+// Y_f[r][b] = sum_b' Lambda_f[b][b'] X_f[r][b'] with Lambda in float-float,
+// X, Y complex double.  One warp per row, 4 independent 16-byte loads in
+// flight per lane, X_f split into float-float in shared memory.
+template <int RC>
+__global__ void __launch_bounds__(256) k_block_product_ff(const float4* __restrict__ spec, const cd* __restrict__ X,
+                                                          cd* __restrict__ Y, int64_t B, int R, int r0,
+                                                          int rows_per_cta) {
+  extern __shared__ float4 xs4[];   // RC x B
+  const int64_t f = blockIdx.y;
+  const int64_t RB = (int64_t)R * B;
+  const cd* Xf = X + f * RB + (int64_t)r0 * B;
+  const int rc = min(RC, R - r0);
+  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) xs4[e] = split_ff(Xf[e]);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const float4* Lf = spec + f * B * B;
+  const int64_t bend = min(B, (int64_t)(blockIdx.x + 1) * rows_per_cta);
+  for (int64_t b = (int64_t)blockIdx.x * rows_per_cta + warp; b < bend; b += nwarps) {
+    float rh[RC], rl[RC], ih[RC], il[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) rh[r] = rl[r] = ih[r] = il[r] = 0.f;
+    const float4* row = Lf + b * B;
+    int64_t bp = lane;
+    for (; bp + 96 < B; bp += 128) {
+      float4 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = __ldcs(row + bp + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+          if (r < rc) ff_cmac(a[u], xs4[r * B + bp + 32 * u], rh[r], rl[r], ih[r], il[r]);
+    }
+    for (; bp < B; bp += 32) {
+      const float4 a = __ldcs(row + bp);
+#pragma unroll
+      for (int r = 0; r < RC; ++r)
+        if (r < rc) ff_cmac(a, xs4[r * B + bp], rh[r], rl[r], ih[r], il[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+      ff_warp_sum(rh[r], rl[r]);
+      ff_warp_sum(ih[r], il[r]);
+      if (lane == 0 && r < rc)
+        Y[f * RB + (int64_t)(r0 + r) * B + b] = mkc((double)rh[r] + (double)rl[r], (double)ih[r] + (double)il[r]);
+    }
+  }
+}
+
+// In-place conversion of a complex-double array to float-float pairs.
+__global__ void k_to_ff(cd* __restrict__ a, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cd v = a[i];
+    reinterpret_cast<float4*>(a)[i] = split_ff(v);
+  }
+}
+
+fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st) {
+  FMPB_LAUNCH("to_ff", st, k_to_ff<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(spec, n));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+static fmpb_status block_product_ff(const float4* spec, const cd* X, cd* Y, int64_t F, int64_t B, int R,
+                                    cudaStream_t st) {
+  if (F > 65535) {
+    set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
+    return FMPB_EINVAL;
+  }
+  const int threads = 256;
+  const int rows = 32;
+  const int RC = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+  const size_t smem = (size_t)RC * B * sizeof(float4);
+  if (smem > 200 * 1024) {
+    set_error("block_product: block size %lld too large", (long long)B);
+    return FMPB_EINVAL;
+  }
+  dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
+  for (int r0 = 0; r0 < R; r0 += RC) {
+    if (RC == 4) {
+      if (smem > 48 * 1024)
+        FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMPB_LAUNCH("block_product", st, k_block_product_ff<4><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
+    } else if (RC == 2) {
+      if (smem > 48 * 1024)
+        FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMPB_LAUNCH("block_product", st, k_block_product_ff<2><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
+    } else {
+      if (smem > 48 * 1024)
+        FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMPB_LAUNCH("block_product", st, k_block_product_ff<1><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
+    }
+    FMPB_CUDA(cudaGetLastError());
+  }
+  return FMPB_OK;
+}
+
 static fmpb_status block_product(const cd* spec, const cd* X, cd* Y, int64_t F, int64_t B, int R, cudaStream_t st) {
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
@@ -186,7 +335,7 @@ static fmpb_status block_product(const cd* spec, const cd* X, cd* Y, int64_t F, 
     FMPB_CUDA(cudaFuncSetAttribute(k_block_product<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
   for (int r0 = 0; r0 < R; r0 += RC) {
-    FMPB_LAUNCH("block_product", st, k_block_product<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
+    FMPB_LAUNCH("block_product_f64", st, k_block_product<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
     FMPB_CUDA(cudaGetLastError());
   }
   return FMPB_OK;
@@ -195,7 +344,7 @@ static fmpb_status block_product(const cd* spec, const cd* X, cd* Y, int64_t F, 
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 * (size_t)s.F * R * B; }
 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
-                            bool accumulate, cd* scratch, cudaStream_t st) {
+                            bool accumulate, cd* scratch, cudaStream_t st, bool spec_ff) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
@@ -212,7 +361,10 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   FMPB_TRY(dft_axis(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz,
                     -1, 1.0, false, st));
   // per-frequency block products: A[f][r][b] -> G[f][r][b]
-  FMPB_TRY(block_product(spec, A, G, s.F, B, R, st));
+  if (spec_ff)
+    FMPB_TRY(block_product_ff(reinterpret_cast<const float4*>(spec), A, G, s.F, B, R, st));
+  else
+    FMPB_TRY(block_product(spec, A, G, s.F, B, R, st));
   // inverse z: G[fz][fy fx][rb] -> A[cz][fy fx][rb], cz < Mz
   FMPB_TRY(dft_axis(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz, Mz, Pz,
                     +1, 1.0, false, st));

@@ -61,8 +61,11 @@ fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R
 fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st);
 // y (+)= T x through pruned FFT, block product, pruned inverse FFT.
 // scratch: 2 * F * R * B complex values.
+// spec_ff: spectrum stored as float-float pairs (see spectrum_to_ff), else complex double.
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
-                            bool accumulate, cd* scratch, cudaStream_t st);
+                            bool accumulate, cd* scratch, cudaStream_t st, bool spec_ff = false);
+// In-place conversion of n complex doubles to float-float pairs (re_hi, re_lo, im_hi, im_lo).
+fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st);
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R);
 
 }  // namespace fmpb
