@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile-case", default=None, choices=["product", "build"],
+                    help="small case for kernel captures: 3x8 cylinders (1.8 GB spectrum), 500 Hz")
     return ap.parse_args()
 
 
@@ -396,9 +398,31 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_profile_case(args):
+    """3 x 8 cylinders at 500 Hz (PBEM form, P = 5 x 16, spectrum 1.84 GB, larger
+    than L2): one operator build, then 4 products.  Prints one JSON line."""
+    import torch
+    import paper_2201_12050_gb300 as gb
+    w = WORKLOADS[WORKLOAD]
+    v, t = w.mesh()
+    k = 2 * math.pi * 500.0 / SPEED_OF_SOUND
+    t0 = time.perf_counter()
+    op = gb.Operator(v, t, (3, 8, 1), w.lattice, k)
+    build_s = time.perf_counter() - t0
+    x = torch.as_tensor(random_complex_vectors(w.rhs_seed, 1, op.N), device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(4):
+        op.matvec(x, out=y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "N": op.N, "F": op.info["F"], "B": op.info["B"],
+                      "build_s": build_s, "y_norm": float(torch.linalg.vector_norm(y))}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile_case:
+        run_profile_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
