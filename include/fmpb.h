@@ -255,6 +255,30 @@ fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fm
 fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
                                  const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
 
+/*
+ * Same product as fmpb_circulant_apply, for callers that cannot allocate
+ * device memory during the call (for example a program whose device memory
+ * belongs to another runtime's pool, or a latency-bound loop that cannot
+ * accept the synchronisation an allocation may cause).  This entry point has
+ * no counterpart in the paper; it only changes where the temporaries live.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *     The scratch (2 F R B complex values) comes from one static device
+ *     array of 32 MiB, which every device that loads the library holds until
+ *     the process exits.  Products needing more than 32 MiB of scratch return
+ *     FMPB_EINVAL with the required size in fmpb_last_error().
+ *   - The first call on a device looks up that array's device address (with
+ *     the device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the same array.  The array keeps the
+ *     last call's contents, but nothing in it needs clearing: each call
+ *     writes every element it reads.  Calls that may overlap on the GPU
+ *     (different streams, or different host threads) race on the array and
+ *     must be serialised by the caller.
+ * Arguments, layouts and results are those of fmpb_circulant_apply.
+ */
+fmpb_status fmpb_circulant_apply_static(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
+                                        const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
+
 /* ------------------------------------------------------------------------
  * Telemetry (no counterpart in the paper; it reports wall-clock times of
  * assembly and products only, Sec. 4).

@@ -74,6 +74,7 @@ SIGNATURES = {
     "fmpb_circulant_shape": (INT, [P, P, P]),
     "fmpb_circulant_spectrum": (INT, [P, I64, P, P, P]),
     "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),
+    "fmpb_circulant_apply_static": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_kernel_launches": (ctypes.c_uint64, []),
     "fmpb_profile_enable": (None, [INT]),
     "fmpb_profile_reset": (INT, []),
