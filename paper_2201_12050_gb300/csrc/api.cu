@@ -235,8 +235,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     for (int i = 0; i < n_off; ++i) dest[i] = offset_slot(sh, all_off[3 * i], all_off[3 * i + 1], all_off[3 * i + 2]);
     s = build_blocks(op->mesh, op->grid, k, n_off, all_off.data(), dest.data(), op->spec, st);
     if (s != FMPB_OK) return fail(s);
-    s = grid_fft_inplace(sh, (int64_t)n * n, op->spec, st);
-    if (s == FMPB_OK) s = spectrum_to_ff(op->spec, (size_t)sh.F * n * n, st);
+    s = grid_fft_inplace(sh, (int64_t)n * n, op->spec, st);   // leaves float-float pairs
     if (s != FMPB_OK) return fail(s);
   } else {
     op->nt = nt;
@@ -268,8 +267,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
       dfar[i] = offset_slot(sh, dl[0], dl[1], dl[2]);
     }
     s = m2l_blocks(nt, k, n_far, dvec.data(), dfar.data(), op->spec, st);
-    if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec, st);
-    if (s == FMPB_OK) s = spectrum_to_ff(op->spec, (size_t)sh.F * B * B, st);
+    if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec, st);   // leaves float-float pairs
     if (s != FMPB_OK) return fail(s);
   }
   cudaError_t e = cudaStreamSynchronize(st);

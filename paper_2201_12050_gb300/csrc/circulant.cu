@@ -15,6 +15,14 @@
 //                                                      M outputs per axis).
 // Grid layout: slot-major, slot f = (fz Py + fy) Px + fx, then R x B (RHS
 // outer, coefficient inner); spectrum [f][b][b'] row-major.
+//
+// Arithmetic: GB300 executes FP64 at 1/58 of its FP32 rate, so every pass
+// (DFTs and block products) runs in float-float arithmetic on the FP32 pipe:
+// values are (hi, lo) FP32 pairs carrying 48 significand bits, products are
+// exact via the fma residual and sums use two-sum.  Intermediate grids and the
+// operator's spectrum are stored as float-float (16 bytes per complex value,
+// the size of complex double); inputs and outputs of the product are complex
+// double.
 #include "common.cuh"
 #include "internal.cuh"
 #include "profile.cuh"
@@ -48,125 +56,6 @@ CircShape make_shape(const int M[3]) {
 int64_t offset_slot(const CircShape& s, int dx, int dy, int dz) {
   auto md = [](int d, int P) { return ((d % P) + P) % P; };
   return ((int64_t)md(dz, s.P[2]) * s.P[1] + md(dy, s.P[1])) * s.P[0] + md(dx, s.P[0]);
-}
-
-// Direct DFT along one axis for the lines (o1, o2, i):
-//   out[o1 b1 + o2 b2 + f bf + i] (+)= scale sum_{j < Pin} in[o1 a1 + o2 a2 + j aj + i] w^{f j},
-// w = exp(sign 2 pi i / P), f < Pout.  A CTA loads one (o1, o2) line group
-// for TI consecutive inner indices into shared memory before writing, so the
-// call may run in place when in and out use the same strides.
-__global__ void k_dft_axis(const cd* in, cd* out, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
-                           int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign,
-                           double scale, int accumulate, int TI) {
-  extern __shared__ cd sm[];
-  cd* tw = sm;          // P twiddles
-  cd* tile = sm + P;    // Pin x TI
-  const int o1 = blockIdx.z;
-  const int o2 = blockIdx.y;
-  const int64_t i0 = (int64_t)blockIdx.x * TI;
-  for (int j = threadIdx.x; j < P; j += blockDim.x) {
-    double s, c;
-    sincospi(2.0 * j / P, &s, &c);
-    tw[j] = mkc(c, sign * s);
-  }
-  const cd* src = in + o1 * a1 + o2 * a2 + i0;
-  for (int e = threadIdx.x; e < Pin * TI; e += blockDim.x) {
-    const int j = e / TI, ii = e - j * TI;
-    tile[e] = (i0 + ii < I) ? src[j * aj + ii] : mkc(0.0, 0.0);
-  }
-  __syncthreads();
-  cd* dst = out + o1 * b1 + o2 * b2 + i0;
-  for (int e = threadIdx.x; e < Pout * TI; e += blockDim.x) {
-    const int f = e / TI, ii = e - f * TI;
-    if (i0 + ii >= I) continue;
-    cd acc = mkc(0.0, 0.0);
-    int idx = 0;
-    for (int j = 0; j < Pin; ++j) {
-      acc = cfma(tile[j * TI + ii], tw[idx], acc);
-      idx += f;
-      if (idx >= P) idx -= P;
-    }
-    acc = cmulr(acc, scale);
-    cd* d = dst + f * bf + ii;
-    *d = accumulate ? cadd(*d, acc) : acc;
-  }
-}
-
-static fmpb_status dft_axis(const cd* in, cd* out, int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
-                            int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign, double scale,
-                            bool accumulate, cudaStream_t st) {
-  if (O1 > 65535 || O2 > 65535) {
-    set_error("dft_axis: line grid %d x %d exceeds the launch limits", O1, O2);
-    return FMPB_EINVAL;
-  }
-  const size_t budget = 96 * 1024;
-  int64_t TI = 32;
-  while (TI > 1 && (size_t)(Pin * TI + P) * sizeof(cd) > budget) TI /= 2;
-  if ((size_t)(Pin * TI + P) * sizeof(cd) > 200 * 1024) {
-    set_error("dft_axis: axis length %d too large", P);
-    return FMPB_EINVAL;
-  }
-  if (TI > I) TI = I;
-  size_t smem = (size_t)(Pin * TI + P) * sizeof(cd);
-  if (smem > 48 * 1024) FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
-  FMPB_LAUNCH("dft_axis", st, k_dft_axis<<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
-                                      accumulate ? 1 : 0, (int)TI));
-  FMPB_CUDA(cudaGetLastError());
-  return FMPB_OK;
-}
-
-fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st) {
-  const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
-  if (Px > 1)
-    FMPB_TRY(dft_axis(grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner, inner, 0, (int64_t)Px * inner, inner,
-                      Px, Px, Px, -1, 1.0, false, st));
-  if (Py > 1)
-    FMPB_TRY(dft_axis(grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner,
-                      (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py, Py, Py, -1, 1.0, false, st));
-  if (Pz > 1)
-    FMPB_TRY(dft_axis(grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
-                      (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st));
-  return FMPB_OK;
-}
-
-// Y_f[r][b] = sum_b' Lambda_f[b][b'] X_f[r][b'], one warp per row b, RC RHS at
-// a time with X_f staged in shared memory.
-template <int RC>
-__global__ void k_block_product(const cd* __restrict__ spec, const cd* __restrict__ X, cd* __restrict__ Y,
-                                int64_t B, int R, int r0, int rows_per_cta) {
-  extern __shared__ cd xs[];   // RC x B
-  const int64_t f = blockIdx.y;
-  const int64_t RB = (int64_t)R * B;
-  const cd* Xf = X + f * RB + (int64_t)r0 * B;
-  const int rc = min(RC, R - r0);
-  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) xs[e] = Xf[e];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
-  const cd* Lf = spec + f * B * B;
-  for (int64_t b = (int64_t)blockIdx.x * rows_per_cta + warp; b < min(B, (int64_t)(blockIdx.x + 1) * rows_per_cta);
-       b += nwarps) {
-    cd acc[RC];
-#pragma unroll
-    for (int r = 0; r < RC; ++r) acc[r] = mkc(0.0, 0.0);
-    const cd* row = Lf + b * B;
-    for (int64_t bp = lane; bp < B; bp += 32) {
-      const cd a = row[bp];
-#pragma unroll
-      for (int r = 0; r < RC; ++r)
-        if (r < rc) acc[r] = cfma(a, xs[r * B + bp], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < RC; ++r) {
-      double re = acc[r].x, im = acc[r].y;
-      for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-      }
-      if (lane == 0 && r < rc) Y[f * RB + (int64_t)(r0 + r) * B + b] = mkc(re, im);
-    }
-  }
 }
 
 // ------------------------------------------------ float-float products ----
@@ -220,34 +109,172 @@ __device__ __forceinline__ void ff_warp_sum(float& h, float& l) {
   }
 }
 
-// Y_f[r][b] = sum_b' Lambda_f[b][b'] X_f[r][b'] with Lambda in float-float,
-// X, Y complex double.  One warp per row, 4 independent 16-byte loads in
-// flight per lane, X_f split into float-float in shared memory.
-template <int RC>
-__global__ void __launch_bounds__(256) k_block_product_ff(const float4* __restrict__ spec, const cd* __restrict__ X,
-                                                          cd* __restrict__ Y, int64_t B, int R, int r0,
+// Renormalise a float-float pair so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ float4 ff_norm(float rh, float rl, float ih, float il) {
+  const float a = rh + rl, b = ih + il;
+  return make_float4(a, rl - (a - rh), b, il - (b - ih));
+}
+
+__device__ __forceinline__ cd ff_to_cd(const float4 v) {
+  return mkc((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+// Direct DFT along one axis for the lines (o1, o2, i), float-float arithmetic:
+//   out[o1 b1 + o2 b2 + f bf + i] (+)= scale sum_{j < Pin} in[o1 a1 + o2 a2 + j aj + i] w^{f j},
+// w = exp(sign 2 pi i / P), f < Pout.  IN_FF / OUT_FF select float-float
+// (float4) or complex-double storage; both are 16 bytes per value, so one
+// buffer can change format in place.  A CTA loads one (o1, o2) line group
+// for TI consecutive inner indices into shared memory before writing, so the
+// call may run in place when in and out use the same strides.
+template <bool IN_FF, bool OUT_FF>
+__global__ void k_dft_axis_ff(const void* in_, void* out_, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
+                              int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign, double scale,
+                              int accumulate, int TI) {
+  extern __shared__ float4 smf[];
+  float4* tw = smf;          // P twiddles (float-float)
+  float4* tile = smf + P;    // Pin x TI
+  const int o1 = blockIdx.z;
+  const int o2 = blockIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * TI;
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * j / P, &sn, &cs);
+    tw[j] = split_ff(mkc(cs, sign * sn));
+  }
+  const int64_t base_in = o1 * a1 + o2 * a2 + i0;
+  for (int e = threadIdx.x; e < Pin * TI; e += blockDim.x) {
+    const int j = e / TI, ii = e - j * TI;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i0 + ii < I) {
+      if (IN_FF)
+        v = reinterpret_cast<const float4*>(in_)[base_in + j * aj + ii];
+      else
+        v = split_ff(reinterpret_cast<const cd*>(in_)[base_in + j * aj + ii]);
+    }
+    tile[e] = v;
+  }
+  __syncthreads();
+  const int64_t base_out = o1 * b1 + o2 * b2 + i0;
+  for (int e = threadIdx.x; e < Pout * TI; e += blockDim.x) {
+    const int f = e / TI, ii = e - f * TI;
+    if (i0 + ii >= I) continue;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    int idx = 0;
+    for (int j = 0; j < Pin; ++j) {
+      ff_cmac(tw[idx], tile[j * TI + ii], rh, rl, ih, il);
+      idx += f;
+      if (idx >= P) idx -= P;
+    }
+    const int64_t o = base_out + f * bf + ii;
+    if (OUT_FF) {
+      reinterpret_cast<float4*>(out_)[o] = ff_norm(rh, rl, ih, il);
+    } else {
+      cd v = mkc(((double)rh + (double)rl) * scale, ((double)ih + (double)il) * scale);
+      cd* d = reinterpret_cast<cd*>(out_) + o;
+      *d = accumulate ? cadd(*d, v) : v;
+    }
+  }
+}
+
+template <bool IN_FF, bool OUT_FF>
+static fmpb_status dft_axis(const void* in, void* out, int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
+                            int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign, double scale,
+                            bool accumulate, cudaStream_t st) {
+  if (O1 > 65535 || O2 > 65535) {
+    set_error("dft_axis: line grid %d x %d exceeds the launch limits", O1, O2);
+    return FMPB_EINVAL;
+  }
+  if (OUT_FF && (scale != 1.0 || accumulate)) {
+    set_error("dft_axis: scaling and accumulation need complex-double output");
+    return FMPB_EINVAL;
+  }
+  const size_t budget = 96 * 1024;
+  int64_t TI = 32;
+  while (TI > 1 && (size_t)(Pin * TI + P) * sizeof(float4) > budget) TI /= 2;
+  if ((size_t)(Pin * TI + P) * sizeof(float4) > 200 * 1024) {
+    set_error("dft_axis: axis length %d too large", P);
+    return FMPB_EINVAL;
+  }
+  if (TI > I) TI = I;
+  size_t smem = (size_t)(Pin * TI + P) * sizeof(float4);
+  if (smem > 48 * 1024)
+    FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis_ff<IN_FF, OUT_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
+  FMPB_LAUNCH("dft_axis", st, k_dft_axis_ff<IN_FF, OUT_FF><<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P,
+                                                                           sign, scale, accumulate ? 1 : 0, (int)TI));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+// In-place forward DFT of a complex-double grid of F slots x `inner`
+// values; the result is left in float-float format (the first pass converts).
+fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st) {
+  const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
+  bool ff = false;
+  if (Px > 1) {
+    FMPB_TRY((dft_axis<false, true>(grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner, inner, 0,
+                                    (int64_t)Px * inner, inner, Px, Px, Px, -1, 1.0, false, st)));
+    ff = true;
+  }
+  if (Py > 1) {
+    if (ff)
+      FMPB_TRY((dft_axis<true, true>(grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner,
+                                     (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py, Py, Py, -1, 1.0, false,
+                                     st)));
+    else
+      FMPB_TRY((dft_axis<false, true>(grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner,
+                                      (int64_t)Px * inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py,
+                                      Py, Py, -1, 1.0, false, st)));
+    ff = true;
+  }
+  if (Pz > 1) {
+    if (ff)
+      FMPB_TRY((dft_axis<true, true>(grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
+                                     (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st)));
+    else
+      FMPB_TRY((dft_axis<false, true>(grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
+                                      (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st)));
+    ff = true;
+  }
+  if (!ff) FMPB_TRY(spectrum_to_ff(grid, (size_t)s.F * inner, st));
+  return FMPB_OK;
+}
+
+// Y_f[r][b] = sum_b' Lambda_f[b][b'] X_f[r][b'] in float-float arithmetic.
+// X_f, Y_f are float-float (float4); the spectrum is float-float (SPEC_FF, the
+// operator's format) or complex double (split on the fly; the building-block
+// API keeps its spectrum in FP64).  One warp per row, 4 independent 16-byte
+// loads in flight per lane, X_f staged in shared memory for RC right-hand
+// sides at a time.
+template <int RC, bool SPEC_FF>
+__global__ void __launch_bounds__(256) k_block_product_ff(const void* __restrict__ spec_, const float4* __restrict__ X,
+                                                          float4* __restrict__ Y, int64_t B, int R, int r0,
                                                           int rows_per_cta) {
   extern __shared__ float4 xs4[];   // RC x B
   const int64_t f = blockIdx.y;
   const int64_t RB = (int64_t)R * B;
-  const cd* Xf = X + f * RB + (int64_t)r0 * B;
+  const float4* Xf = X + f * RB + (int64_t)r0 * B;
   const int rc = min(RC, R - r0);
-  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) xs4[e] = split_ff(Xf[e]);
+  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) xs4[e] = Xf[e];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  const float4* Lf = spec + f * B * B;
   const int64_t bend = min(B, (int64_t)(blockIdx.x + 1) * rows_per_cta);
   for (int64_t b = (int64_t)blockIdx.x * rows_per_cta + warp; b < bend; b += nwarps) {
     float rh[RC], rl[RC], ih[RC], il[RC];
 #pragma unroll
     for (int r = 0; r < RC; ++r) rh[r] = rl[r] = ih[r] = il[r] = 0.f;
-    const float4* row = Lf + b * B;
+    const int64_t row0 = (f * B + b) * B;
+    auto load = [&](int64_t k) -> float4 {
+      if (SPEC_FF) return __ldcs(reinterpret_cast<const float4*>(spec_) + row0 + k);
+      return split_ff(reinterpret_cast<const cd*>(spec_)[row0 + k]);
+    };
     int64_t bp = lane;
     for (; bp + 96 < B; bp += 128) {
       float4 a[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = __ldcs(row + bp + 32 * u);
+      for (int u = 0; u < 4; ++u) a[u] = load(bp + 32 * u);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -255,7 +282,7 @@ __global__ void __launch_bounds__(256) k_block_product_ff(const float4* __restri
           if (r < rc) ff_cmac(a[u], xs4[r * B + bp + 32 * u], rh[r], rl[r], ih[r], il[r]);
     }
     for (; bp < B; bp += 32) {
-      const float4 a = __ldcs(row + bp);
+      const float4 a = load(bp);
 #pragma unroll
       for (int r = 0; r < RC; ++r)
         if (r < rc) ff_cmac(a, xs4[r * B + bp], rh[r], rl[r], ih[r], il[r]);
@@ -264,8 +291,7 @@ __global__ void __launch_bounds__(256) k_block_product_ff(const float4* __restri
     for (int r = 0; r < RC; ++r) {
       ff_warp_sum(rh[r], rl[r]);
       ff_warp_sum(ih[r], il[r]);
-      if (lane == 0 && r < rc)
-        Y[f * RB + (int64_t)(r0 + r) * B + b] = mkc((double)rh[r] + (double)rl[r], (double)ih[r] + (double)il[r]);
+      if (lane == 0 && r < rc) Y[f * RB + (int64_t)(r0 + r) * B + b] = ff_norm(rh[r], rl[r], ih[r], il[r]);
     }
   }
 }
@@ -278,67 +304,61 @@ __global__ void k_to_ff(cd* __restrict__ a, size_t n) {
   }
 }
 
+// In-place conversion of float-float pairs back to complex double.
+__global__ void k_from_ff(cd* __restrict__ a, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(a)[i];
+    a[i] = ff_to_cd(v);
+  }
+}
+
 fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st) {
   FMPB_LAUNCH("to_ff", st, k_to_ff<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(spec, n));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
 
-static fmpb_status block_product_ff(const float4* spec, const cd* X, cd* Y, int64_t F, int64_t B, int R,
-                                    cudaStream_t st) {
-  if (F > 65535) {
-    set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
-    return FMPB_EINVAL;
-  }
-  const int threads = 256;
-  const int rows = 32;
-  const int RC = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+static fmpb_status spectrum_from_ff(cd* spec, size_t n, cudaStream_t st) {
+  FMPB_LAUNCH("from_ff", st, k_from_ff<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(spec, n));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+template <int RC, bool SPEC_FF>
+static fmpb_status launch_block_product(const void* spec, const float4* X, float4* Y, int64_t F, int64_t B, int R,
+                                        cudaStream_t st) {
+  const int threads = 256, rows = 32;
   const size_t smem = (size_t)RC * B * sizeof(float4);
-  if (smem > 200 * 1024) {
-    set_error("block_product: block size %lld too large", (long long)B);
-    return FMPB_EINVAL;
-  }
+  if (smem > 48 * 1024)
+    FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<RC, SPEC_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
   dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
   for (int r0 = 0; r0 < R; r0 += RC) {
-    if (RC == 4) {
-      if (smem > 48 * 1024)
-        FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      FMPB_LAUNCH("block_product", st, k_block_product_ff<4><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
-    } else if (RC == 2) {
-      if (smem > 48 * 1024)
-        FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      FMPB_LAUNCH("block_product", st, k_block_product_ff<2><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
-    } else {
-      if (smem > 48 * 1024)
-        FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      FMPB_LAUNCH("block_product", st, k_block_product_ff<1><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
-    }
+    FMPB_LAUNCH("block_product", st, k_block_product_ff<RC, SPEC_FF><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
     FMPB_CUDA(cudaGetLastError());
   }
   return FMPB_OK;
 }
 
-static fmpb_status block_product(const cd* spec, const cd* X, cd* Y, int64_t F, int64_t B, int R, cudaStream_t st) {
+static fmpb_status block_product(const void* spec, bool spec_ff, const float4* X, float4* Y, int64_t F, int64_t B,
+                                 int R, cudaStream_t st) {
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
     return FMPB_EINVAL;
   }
-  constexpr int RC = 4;
-  const int threads = 256;
-  const int rows = 32;
-  const size_t smem = (size_t)RC * B * sizeof(cd);
-  if (smem > 200 * 1024) {
+  const int RC = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+  if ((size_t)RC * B * sizeof(float4) > 200 * 1024) {
     set_error("block_product: block size %lld too large", (long long)B);
     return FMPB_EINVAL;
   }
-  if (smem > 48 * 1024)
-    FMPB_CUDA(cudaFuncSetAttribute(k_block_product<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
-  for (int r0 = 0; r0 < R; r0 += RC) {
-    FMPB_LAUNCH("block_product_f64", st, k_block_product<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
-    FMPB_CUDA(cudaGetLastError());
+  if (spec_ff) {
+    if (RC == 4) return launch_block_product<4, true>(spec, X, Y, F, B, R, st);
+    if (RC == 2) return launch_block_product<2, true>(spec, X, Y, F, B, R, st);
+    return launch_block_product<1, true>(spec, X, Y, F, B, R, st);
   }
-  return FMPB_OK;
+  if (RC == 4) return launch_block_product<4, false>(spec, X, Y, F, B, R, st);
+  if (RC == 2) return launch_block_product<2, false>(spec, X, Y, F, B, R, st);
+  return launch_block_product<1, false>(spec, X, Y, F, B, R, st);
 }
 
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 * (size_t)s.F * R * B; }
@@ -349,31 +369,29 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
   const int64_t Nc = s.ncells;
-  cd* A = scratch;
-  cd* G = scratch + (size_t)s.F * RB;
-  // forward x: x[r][cz][cy][cx][b] -> A[cz][cy][fx][r][b]
-  FMPB_TRY(dft_axis(x, A, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B, (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0,
-                    false, st));
+  // both halves hold float-float values (16 bytes each, like complex double)
+  float4* A = reinterpret_cast<float4*>(scratch);
+  float4* G = reinterpret_cast<float4*>(scratch + (size_t)s.F * RB);
+  // forward x: x[r][cz][cy][cx][b] (complex double) -> A[cz][cy][fx][r][b]
+  FMPB_TRY((dft_axis<false, true>(x, A, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B, (int64_t)Px * RB, RB, Mx, Px,
+                                  Px, -1, 1.0, false, st)));
   // forward y: A[cz][cy][fx][rb] -> G[cz][fy][fx][rb]
-  FMPB_TRY(dft_axis(A, G, Mz, Px, RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, (int64_t)Py * Px * RB, RB,
-                    (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st));
+  FMPB_TRY((dft_axis<true, true>(A, G, Mz, Px, RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, (int64_t)Py * Px * RB,
+                                 RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st)));
   // forward z: G[cz][fy fx][rb] -> A[fz][fy fx][rb]
-  FMPB_TRY(dft_axis(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz,
-                    -1, 1.0, false, st));
+  FMPB_TRY((dft_axis<true, true>(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz,
+                                 Pz, Pz, -1, 1.0, false, st)));
   // per-frequency block products: A[f][r][b] -> G[f][r][b]
-  if (spec_ff)
-    FMPB_TRY(block_product_ff(reinterpret_cast<const float4*>(spec), A, G, s.F, B, R, st));
-  else
-    FMPB_TRY(block_product(spec, A, G, s.F, B, R, st));
+  FMPB_TRY(block_product(spec, spec_ff, A, G, s.F, B, R, st));
   // inverse z: G[fz][fy fx][rb] -> A[cz][fy fx][rb], cz < Mz
-  FMPB_TRY(dft_axis(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz, Mz, Pz,
-                    +1, 1.0, false, st));
+  FMPB_TRY((dft_axis<true, true>(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz,
+                                 Mz, Pz, +1, 1.0, false, st)));
   // inverse y: A[cz][fy][fx][rb] -> G[cz][cy][fx][rb], cy < My
-  FMPB_TRY(dft_axis(A, G, Mz, Px, RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, (int64_t)My * Px * RB, RB,
-                    (int64_t)Px * RB, Py, My, Py, +1, 1.0, false, st));
-  // inverse x with crop and 1/F: G[cz][cy][fx][r][b] -> y[r][cz][cy][cx][b]
-  FMPB_TRY(dft_axis(G, y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B, (int64_t)Mx * B, B, Px, Mx, Px, +1,
-                    1.0 / (double)s.F, accumulate, st));
+  FMPB_TRY((dft_axis<true, true>(A, G, Mz, Px, RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, (int64_t)My * Px * RB,
+                                 RB, (int64_t)Px * RB, Py, My, Py, +1, 1.0, false, st)));
+  // inverse x with crop and 1/F: G[cz][cy][fx][r][b] -> y[r][cz][cy][cx][b] (complex double)
+  FMPB_TRY((dft_axis<true, false>(G, y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B, (int64_t)Mx * B, B, Px, Mx, Px,
+                                  +1, 1.0 / (double)s.F, accumulate, st)));
   return FMPB_OK;
 }
 
@@ -406,6 +424,8 @@ fmpb_status circulant_spectrum_from_blocks(const CircShape& s, int64_t B, const 
                                                                                        n_off));
   FMPB_CUDA(cudaGetLastError());
   FMPB_TRY(grid_fft_inplace(s, B * B, spec, st));
+  // the building-block API returns the spectrum in complex double
+  FMPB_TRY(spectrum_from_ff(spec, (size_t)s.F * B * B, st));
   FMPB_CUDA(cudaFreeAsync(dslot, st));
   return FMPB_OK;
 }

@@ -57,7 +57,8 @@ fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R
                          cd* out, cudaStream_t st);
 
 // Circulant engine (circulant.cu)
-// In-place FFT over the padded grid of F slots, each holding `inner` values.
+// In-place forward DFT over the padded grid of F slots, each holding `inner`
+// complex doubles; leaves the result as float-float pairs (16 bytes each).
 fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st);
 // y (+)= T x through pruned FFT, block product, pruned inverse FFT.
 // scratch: 2 * F * R * B complex values.
