@@ -196,6 +196,9 @@ static fmpb_status dft_axis(const void* in, void* out, int O1, int O2, int64_t I
     return FMPB_EINVAL;
   }
   if (TI > I) TI = I;
+  // enough CTAs to fill the 152 SMs several times over: shrink the inner
+  // tile (down to 4 values, 64-byte segments) while the grid is small
+  while (TI > 4 && ((I + TI - 1) / TI) * (int64_t)O1 * O2 < 4 * 152) TI /= 2;
   size_t smem = (size_t)(Pin * TI + P) * sizeof(float4);
   if (smem > 48 * 1024)
     FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis_ff<IN_FF, OUT_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -17,25 +17,43 @@
 namespace fmpb {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 64;   // partial sums per (vector, rhs)
+constexpr int RED_BLOCKS = 64;   // upper bound on partial sums per (vector, rhs)
+constexpr int MAX_RESTART = 200;
 
-// partial[(v*R + r)*RED_BLOCKS + blk] = sum over chunk of conj(V_v[r]) w[r]
+// partial[(v*R + r)*gridDim.x + blk] = sum over the block's rows of
+// conj(V_v[r]) w[r]; four independent accumulators per thread keep several
+// loads in flight.
 __global__ void k_dots(const cd* __restrict__ V, int64_t vstride, int nvec, const cd* __restrict__ w, int R,
                        int64_t N, cd* __restrict__ partial, const int* __restrict__ active) {
   const int blk = blockIdx.x, v = blockIdx.y, r = blockIdx.z;
   __shared__ double sre[RED_THREADS], sim[RED_THREADS];
-  double re = 0.0, im = 0.0;
+  double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
   if (active[r]) {
     const cd* a = V + (int64_t)v * vstride + (int64_t)r * N;
     const cd* b = w + (int64_t)r * N;
-    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < N; i += 4 * stride) {
+      cd x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x[u] = a[i + u * stride];
+        y[u] = b[i + u * stride];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        re[u] = fma(x[u].x, y[u].x, fma(x[u].y, y[u].y, re[u]));
+        im[u] = fma(x[u].x, y[u].y, fma(-x[u].y, y[u].x, im[u]));
+      }
+    }
+    for (; i < N; i += stride) {
       cd x = a[i], y = b[i];
-      re = fma(x.x, y.x, fma(x.y, y.y, re));
-      im = fma(x.x, y.y, fma(-x.y, y.x, im));
+      re[0] = fma(x.x, y.x, fma(x.y, y.y, re[0]));
+      im[0] = fma(x.x, y.y, fma(-x.y, y.x, im[0]));
     }
   }
-  sre[threadIdx.x] = re;
-  sim[threadIdx.x] = im;
+  sre[threadIdx.x] = (re[0] + re[1]) + (re[2] + re[3]);
+  sim[threadIdx.x] = (im[0] + im[1]) + (im[2] + im[3]);
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
@@ -57,21 +75,61 @@ __global__ void k_reduce_partials(const cd* __restrict__ partial, int nblk, int 
   out[t] = accumulate ? cadd(out[t], s) : s;
 }
 
-// w[r] -= sum_v V_v[r] h[v*R + r]
+// w[r] -= sum_v V_v[r] h[v*R + r]: each thread owns 4 rows (strided by the
+// grid) and walks the basis 4 vectors at a time, 16 loads in flight; the
+// coefficients of rhs r sit in shared memory.
+constexpr int SUB_ROWS = 4;
 __global__ void k_subtract_projection(const cd* __restrict__ V, int64_t vstride, int nvec,
                                       const cd* __restrict__ h, cd* __restrict__ w, int R, int64_t N,
                                       const int* __restrict__ active) {
   const int r = blockIdx.y;
   if (!active[r]) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    cd acc = w[(int64_t)r * N + i];
-    for (int v = 0; v < nvec; ++v) {
-      cd hv = h[v * R + r];
-      cd a = V[(int64_t)v * vstride + (int64_t)r * N + i];
-      acc.x -= a.x * hv.x - a.y * hv.y;
-      acc.y -= a.x * hv.y + a.y * hv.x;
+  __shared__ cd hs[MAX_RESTART + 1];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) hs[v] = h[v * R + r];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  cd* wr = w + (int64_t)r * N;
+  const cd* Vr = V + (int64_t)r * N;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += SUB_ROWS * stride) {
+    cd acc[SUB_ROWS];
+    bool ok[SUB_ROWS];
+#pragma unroll
+    for (int u = 0; u < SUB_ROWS; ++u) {
+      const int64_t i = i0 + u * stride;
+      ok[u] = i < N;
+      acc[u] = ok[u] ? wr[i] : mkc(0.0, 0.0);
     }
-    w[(int64_t)r * N + i] = acc;
+    int v = 0;
+    for (; v + 3 < nvec; v += 4) {
+      cd a[4][SUB_ROWS];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < SUB_ROWS; ++u)
+          a[q][u] = ok[u] ? Vr[(int64_t)(v + q) * vstride + i0 + u * stride] : mkc(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const cd hv = hs[v + q];
+#pragma unroll
+        for (int u = 0; u < SUB_ROWS; ++u) {
+          acc[u].x -= a[q][u].x * hv.x - a[q][u].y * hv.y;
+          acc[u].y -= a[q][u].x * hv.y + a[q][u].y * hv.x;
+        }
+      }
+    }
+    for (; v < nvec; ++v) {
+      const cd hv = hs[v];
+#pragma unroll
+      for (int u = 0; u < SUB_ROWS; ++u) {
+        if (!ok[u]) continue;
+        const cd a = Vr[(int64_t)v * vstride + i0 + u * stride];
+        acc[u].x -= a.x * hv.x - a.y * hv.y;
+        acc[u].y -= a.x * hv.y + a.y * hv.x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SUB_ROWS; ++u)
+      if (ok[u]) wr[i0 + u * stride] = acc[u];
   }
 }
 
@@ -228,7 +286,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int m = o.restart > 0 ? o.restart : 30;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
-  if (m > 200 || R < 1 || N < 1) {
+  if (m > MAX_RESTART || R < 1 || N < 1) {
     set_error("gmres: restart must be 1..200 and R, N positive");
     return FMPB_EINVAL;
   }
@@ -282,6 +340,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   cd* partial = (cd*)Pb.p;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
+  const unsigned sub_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 1023) / 1024, 152 * 4));
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, N / (RED_THREADS * 16)));
   const unsigned rb = grid_for(R, 64);
 
   // all-active mask for norms of b and of true residuals
@@ -298,8 +358,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   }
 
   auto norms = [&](const cd* X, double* out, double* invout) -> fmpb_status {
-    FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(X, 0, 1, X, R, N, partial, all_active));
-    FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0));
+    FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(X, 0, 1, X, R, N, partial, all_active));
+    FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
     FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, out, invout, R));
     FMPB_CUDA(cudaGetLastError());
     return FMPB_OK;
@@ -336,16 +396,16 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       cd* vn = V + (int64_t)(j + 1) * vstride;
       FMPB_TRY(A(R, vj, vn, st));
       // two passes of classical Gram-Schmidt against v_0..v_j
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, RED_BLOCKS, (j + 1) * R, h2, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, s.active));
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h, 0));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
       // ||w||, normalise
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(RED_BLOCKS, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, RED_BLOCKS, R, nrm2, 0));
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
       FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R));
       FMPB_LAUNCH("scale", st, k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, vn, s.inv, R, N, s.active));
       FMPB_LAUNCH("givens", st, k_givens<<<rb, 64, 0, st>>>(s, h, wnorm, R, m, j, tol));
