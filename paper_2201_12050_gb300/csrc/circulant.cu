@@ -71,18 +71,18 @@ __device__ __forceinline__ float4 split_ff(cd v) {
 }
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // (sh, sl) += a * x for a, x float-float complex; re and im separately.
 __device__ __forceinline__ void ff_cmac(const float4 a, const float4 x, float& rh, float& rl, float& ih, float& il) {
   // hi x hi products with their exact rounding errors
-  const float p1 = a.x * x.x, e1 = fmaf(a.x, x.x, -p1);   // ar xr
-  const float p2 = a.z * x.z, e2 = fmaf(a.z, x.z, -p2);   // ai xi
-  const float p3 = a.x * x.z, e3 = fmaf(a.x, x.z, -p3);   // ar xi
-  const float p4 = a.z * x.x, e4 = fmaf(a.z, x.x, -p4);   // ai xr
+  const float p1 = __fmul_rn(a.x, x.x), e1 = fmaf(a.x, x.x, -p1);   // ar xr
+  const float p2 = __fmul_rn(a.z, x.z), e2 = fmaf(a.z, x.z, -p2);   // ai xi
+  const float p3 = __fmul_rn(a.x, x.z), e3 = fmaf(a.x, x.z, -p3);   // ar xi
+  const float p4 = __fmul_rn(a.z, x.x), e4 = fmaf(a.z, x.x, -p4);   // ai xr
   // cross terms hi x lo + lo x hi
   const float cr = fmaf(a.x, x.y, fmaf(a.y, x.x, -fmaf(a.z, x.w, a.w * x.z)));
   const float ci = fmaf(a.x, x.w, fmaf(a.y, x.z, fmaf(a.z, x.y, a.w * x.x)));
@@ -105,14 +105,14 @@ __device__ __forceinline__ void ff_warp_sum(float& h, float& l) {
     float s, e;
     two_sum_f(h, oh, s, e);
     h = s;
-    l = l + ol + e;
+    l = __fadd_rn(__fadd_rn(l, ol), e);
   }
 }
 
 // Renormalise a float-float pair so that |lo| <= ulp(hi)/2.
 __device__ __forceinline__ float4 ff_norm(float rh, float rl, float ih, float il) {
-  const float a = rh + rl, b = ih + il;
-  return make_float4(a, rl - (a - rh), b, il - (b - ih));
+  const float a = __fadd_rn(rh, rl), b = __fadd_rn(ih, il);
+  return make_float4(a, __fsub_rn(rl, __fsub_rn(a, rh)), b, __fsub_rn(il, __fsub_rn(b, ih)));
 }
 
 __device__ __forceinline__ cd ff_to_cd(const float4 v) {

@@ -75,10 +75,9 @@ __global__ void k_reduce_partials(const cd* __restrict__ partial, int nblk, int 
   out[t] = accumulate ? cadd(out[t], s) : s;
 }
 
-// w[r] -= sum_v V_v[r] h[v*R + r]: each thread owns 4 rows (strided by the
-// grid) and walks the basis 4 vectors at a time, 16 loads in flight; the
-// coefficients of rhs r sit in shared memory.
-constexpr int SUB_ROWS = 4;
+// w[r] -= sum_v V_v[r] h[v*R + r]: one row per thread, the basis walked 8
+// vectors at a time (8 loads in flight); the coefficients of rhs r sit in
+// shared memory.
 __global__ void k_subtract_projection(const cd* __restrict__ V, int64_t vstride, int nvec,
                                       const cd* __restrict__ h, cd* __restrict__ w, int R, int64_t N,
                                       const int* __restrict__ active) {
@@ -90,46 +89,27 @@ __global__ void k_subtract_projection(const cd* __restrict__ V, int64_t vstride,
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   cd* wr = w + (int64_t)r * N;
   const cd* Vr = V + (int64_t)r * N;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += SUB_ROWS * stride) {
-    cd acc[SUB_ROWS];
-    bool ok[SUB_ROWS];
-#pragma unroll
-    for (int u = 0; u < SUB_ROWS; ++u) {
-      const int64_t i = i0 + u * stride;
-      ok[u] = i < N;
-      acc[u] = ok[u] ? wr[i] : mkc(0.0, 0.0);
-    }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    cd acc = wr[i];
     int v = 0;
-    for (; v + 3 < nvec; v += 4) {
-      cd a[4][SUB_ROWS];
+    for (; v + 7 < nvec; v += 8) {
+      cd a[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 8; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
 #pragma unroll
-        for (int u = 0; u < SUB_ROWS; ++u)
-          a[q][u] = ok[u] ? Vr[(int64_t)(v + q) * vstride + i0 + u * stride] : mkc(0.0, 0.0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const cd hv = hs[v + q];
-#pragma unroll
-        for (int u = 0; u < SUB_ROWS; ++u) {
-          acc[u].x -= a[q][u].x * hv.x - a[q][u].y * hv.y;
-          acc[u].y -= a[q][u].x * hv.y + a[q][u].y * hv.x;
-        }
+        acc.x -= a[q].x * hv.x - a[q].y * hv.y;
+        acc.y -= a[q].x * hv.y + a[q].y * hv.x;
       }
     }
     for (; v < nvec; ++v) {
       const cd hv = hs[v];
-#pragma unroll
-      for (int u = 0; u < SUB_ROWS; ++u) {
-        if (!ok[u]) continue;
-        const cd a = Vr[(int64_t)v * vstride + i0 + u * stride];
-        acc[u].x -= a.x * hv.x - a.y * hv.y;
-        acc[u].y -= a.x * hv.y + a.y * hv.x;
-      }
+      const cd a = Vr[(int64_t)v * vstride + i];
+      acc.x -= a.x * hv.x - a.y * hv.y;
+      acc.y -= a.x * hv.y + a.y * hv.x;
     }
-#pragma unroll
-    for (int u = 0; u < SUB_ROWS; ++u)
-      if (ok[u]) wr[i0 + u * stride] = acc[u];
+    wr[i] = acc;
   }
 }
 
@@ -340,7 +320,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   cd* partial = (cd*)Pb.p;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
-  const unsigned sub_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 1023) / 1024, 152 * 4));
+  const unsigned sub_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8));
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, N / (RED_THREADS * 16)));
   const unsigned rb = grid_for(R, 64);
 

@@ -4,8 +4,27 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace fmpb {
+
+// Source-element geometry in float-float for the far-class quadrature.
+struct FfElem {
+  ff w0[3];      // v0 - centroid
+  ff ba[3];      // v1 - v0
+  ff cb[3];      // v2 - v1
+  ff ny[3];      // unit normal
+  ff two_area;
+  float hmax;
+  float pad;
+};
+constexpr int NTAY = 9;   // Taylor terms of cos and sin in the float-float exponential
+struct FfConst {
+  ff s[Q_FAR], t[Q_FAR];
+  ff W[Q_FAR * Q_FAR];    // s_a w_a w_b of the collapsed far rule
+  ff ccos[NTAY], csin[NTAY];
+  ff inv4pi;
+};
 
 // Finite cell grid (Sec. 2.2): counts M[a] along lattice vectors L[a].
 struct CellGrid {
@@ -41,6 +60,9 @@ struct DeviceMesh {
   Elem* el = nullptr;
   QuadRules* qr_dev = nullptr;
   QuadRules qr;
+  FfElem* ffel = nullptr;
+  FfConst* fc_dev = nullptr;
+  FfConst fc;
   double radius = 0.0;   // max |vertex| about the origin (expansion centre)
 };
 

@@ -29,13 +29,13 @@ struct dd {
 };
 __device__ __forceinline__ dd dd_make(double a) { return {a, 0.0}; }
 __device__ __forceinline__ dd quick_two_sum(double a, double b) {
-  double s = a + b;
-  return {s, b - (s - a)};
+  double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
 }
 __device__ __forceinline__ dd two_sum(double a, double b) {
-  double s = a + b;
-  double bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  return {s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
 }
 __device__ __forceinline__ dd dd_add(dd x, dd y) {
   dd s = two_sum(x.hi, y.hi);
@@ -44,13 +44,13 @@ __device__ __forceinline__ dd dd_add(dd x, dd y) {
 }
 __device__ __forceinline__ dd dd_neg(dd x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ dd dd_mul(dd x, dd y) {
-  double p = x.hi * y.hi;
+  double p = __dmul_rn(x.hi, y.hi);
   double e = fma(x.hi, y.hi, -p);
   e += x.hi * y.lo + x.lo * y.hi;
   return quick_two_sum(p, e);
 }
 __device__ __forceinline__ dd dd_mul_d(dd x, double y) {
-  double p = x.hi * y;
+  double p = __dmul_rn(x.hi, y);
   double e = fma(x.hi, y, -p);
   e += x.lo * y;
   return quick_two_sum(p, e);

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "internal.cuh"
 #include "profile.cuh"
+#include "ff.cuh"
 
 namespace fmpb {
 
@@ -184,6 +185,164 @@ __device__ void element_dh(const Elem& E, const double shift[3], const double x[
   }
 }
 
+// ------------------------------------------------- float-float far rule --
+// The far class (d >= 4h, 9 points, about 97 % of all quadrature points) is
+// evaluated in float-float arithmetic on the FP32 pipe.  FP64 keeps the parts
+// that need it: the class decision, e = x - c (c = element centroid) and the
+// reference phase k|e| reduced mod 2 pi.  Per point, with u = y - c,
+//   Delta = |u|^2 - 2 e.u,   r = sqrt(|e|^2 + Delta),   delta = Delta/(|e| + r),
+//   e^{ikr} = e^{ik|e|} e^{ik delta},
+// so only the small phase k delta (|k delta| <= k h) is formed per point;
+// e^{i psi} comes from Taylor series at psi / 2^m (|psi / 2^m| <= 0.75,
+// nine terms) followed by m complex squarings.
+
+// Per-element geometry in float-float (source side, shift free).
+__global__ void k_prepare_ff(const Elem* __restrict__ el, int n, FfElem* __restrict__ fe, const QuadRules* qr,
+                             FfConst* fc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) {
+    const Elem E = el[e];
+    FfElem F;
+    for (int d = 0; d < 3; ++d) {
+      F.w0[d] = ff_from_d(E.v[0][d] - E.c[d]);
+      F.ba[d] = ff_from_d(E.v[1][d] - E.v[0][d]);
+      F.cb[d] = ff_from_d(E.v[2][d] - E.v[1][d]);
+      F.ny[d] = ff_from_d(E.nrm[d]);
+    }
+    F.two_area = ff_from_d(2.0 * E.area);
+    F.hmax = (float)E.hmax;
+    F.pad = 0.f;
+    fe[e] = F;
+  }
+  if (e == 0) {
+    FfConst C;
+    for (int i = 0; i < Q_FAR; ++i) {
+      C.s[i] = ff_from_d(qr->t3[i]);
+      C.t[i] = ff_from_d(qr->t3[i]);
+      for (int j = 0; j < Q_FAR; ++j) C.W[i * Q_FAR + j] = ff_from_d(qr->t3[i] * qr->w3[i] * qr->w3[j]);
+    }
+    double f = 1.0;   // (2k)! and (2k+1)!, exact in FP64 up to 17!
+    for (int k = 0; k < NTAY; ++k) {
+      const double f2k = f;                     // (2k)!
+      const double f2k1 = f * (2 * k + 1);      // (2k+1)!
+      const double sgn = (k & 1) ? -1.0 : 1.0;
+      C.ccos[k] = ff_from_d(sgn / f2k);
+      C.csin[k] = ff_from_d(sgn / f2k1);
+      f = f2k1 * (2 * k + 2);
+    }
+    C.inv4pi = ff_from_d(0.25 / PI);
+    *fc = C;
+  }
+}
+
+__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
+  return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
+
+// e^{i psi} for |psi| <= 0.75 * 2^m
+__device__ __forceinline__ ffc expi_ff(ff psi, int m, const FfConst& C) {
+  const float sc = ldexpf(1.f, -m);
+  const ff p = {psi.h * sc, psi.l * sc};    // exact scaling by a power of two
+  const ff z = ff_mul(p, p);
+  ff c = C.ccos[NTAY - 1], s = C.csin[NTAY - 1];
+#pragma unroll
+  for (int k = NTAY - 2; k >= 0; --k) {
+    c = ff_add(C.ccos[k], ff_mul(z, c));
+    s = ff_add(C.csin[k], ff_mul(z, s));
+  }
+  s = ff_mul(p, s);
+  for (int i = 0; i < m; ++i) {
+    const ff cs = ff_mul(c, s);
+    c = ff_sub(ff_mul(c, c), ff_mul(s, s));
+    s = {2.f * cs.h, 2.f * cs.l};
+  }
+  return {c, s};
+}
+
+// 2 pi split into two doubles (2 pi = TWO_PI_HI + TWO_PI_LO to ~1e-32)
+constexpr double TWO_PI_HI = 6.283185307179586;
+constexpr double TWO_PI_LO = 2.4492935982947064e-16;
+
+// D, H of a far element: e = x - (c + shift) in FP64, r2 = |e|^2, dist = |e|.
+__device__ void far_dh_ff(const FfElem& F, const double e[3], double r2, double dist, const ff nxf[3], double k,
+                          ff kf, const FfConst& C, cd& D, cd& H) {
+  const ff ef[3] = {ff_from_d(e[0]), ff_from_d(e[1]), ff_from_d(e[2])};
+  const ff rho2 = ff_from_d(r2);
+  const ff rho = ff_from_d(dist);
+  const ff dny = ff_dot3(ef, F.ny);           // (x - y).n_y is constant on the flat element
+  const ff enx = ff_dot3(ef, nxf);
+  const ff Cd = ff_mul(dny, C.inv4pi);
+  const ff Cg1 = ff_mul(ff_dot3(nxf, F.ny), C.inv4pi);
+  const ff w0nx = ff_dot3(F.w0, nxf), banx = ff_dot3(F.ba, nxf), cbnx = ff_dot3(F.cb, nxf);
+  // reference phase k|e| reduced to [-pi, pi] in FP64
+  double th = k * dist;
+  const double qn = rint(th * (1.0 / TWO_PI_HI));
+  th = fma(-qn, TWO_PI_HI, th);
+  th = fma(-qn, TWO_PI_LO, th);
+  const ffc Eref = expi_ff(ff_from_d(th), 3, C);
+  int m = 2;
+  const float kh = (float)k * F.hmax;
+  while (kh > 0.75f * (float)(1 << m) && m < 12) ++m;
+  ff Dre = ff_make(0.f), Dim = ff_make(0.f), Hre = ff_make(0.f), Him = ff_make(0.f);
+#pragma unroll 1
+  for (int b = 0; b < Q_FAR; ++b) {
+    ff qb[3];
+    for (int d = 0; d < 3; ++d) qb[d] = ff_add(F.ba[d], ff_mul(C.t[b], F.cb[d]));
+    const ff qnx = ff_add(banx, ff_mul(C.t[b], cbnx));
+#pragma unroll 1
+    for (int a = 0; a < Q_FAR; ++a) {
+      ff u[3];
+      for (int d = 0; d < 3; ++d) u[d] = ff_add(F.w0[d], ff_mul(C.s[a], qb[d]));
+      const ff unx = ff_add(w0nx, ff_mul(C.s[a], qnx));
+      const ff eu = ff_dot3(ef, u);
+      const ff Delta = ff_sub(ff_dot3(u, u), ff{2.f * eu.h, 2.f * eu.l});
+      const ff r = ff_sqrt(ff_add(rho2, Delta));
+      const ff delta = ff_div(Delta, ff_add(rho, r));
+      const ffc ep = expi_ff(ff_mul(kf, delta), m, C);
+      const ffc E = ffc_mul(Eref, ep);
+      const ff ir = ff_rcp(r);
+      const ff ir2 = ff_mul(ir, ir);
+      const ff ir3 = ff_mul(ir2, ir);
+      const ff ir5 = ff_mul(ir3, ir2);
+      const ff kr = ff_mul(kf, r);
+      const ff dnx = ff_sub(enx, unx);
+      // a = e^{ikr}(1 - ikr), b = e^{ikr}(3 - (kr)^2 - 3ikr)
+      const ff are = ff_add(E.re, ff_mul(E.im, kr));
+      const ff aim = ff_sub(E.im, ff_mul(E.re, kr));
+      const ff t3 = ff_sub(ff_make(3.f), ff_mul(kr, kr));
+      const ff kr3 = ff_mul_f(kr, 3.f);
+      const ff bre = ff_add(ff_mul(E.re, t3), ff_mul(E.im, kr3));
+      const ff bim = ff_sub(ff_mul(E.im, t3), ff_mul(E.re, kr3));
+      const ff wgt = ff_mul(F.two_area, C.W[a * Q_FAR + b]);
+      const ff wir3 = ff_mul(wgt, ir3);
+      const ff f = ff_mul(wir3, Cd);
+      const ff g1 = ff_mul(wir3, Cg1);
+      const ff g2 = ff_mul(ff_mul(ff_mul(wgt, ir5), dnx), Cd);
+      Dre = ff_add(Dre, ff_mul(are, f));
+      Dim = ff_add(Dim, ff_mul(aim, f));
+      Hre = ff_add(Hre, ff_sub(ff_mul(are, g1), ff_mul(bre, g2)));
+      Him = ff_add(Him, ff_sub(ff_mul(aim, g1), ff_mul(bim, g2)));
+    }
+  }
+  D = mkc(ff_to_d(Dre), ff_to_d(Dim));
+  H = mkc(ff_to_d(Hre), ff_to_d(Him));
+}
+
+// D, H by class: the far class through far_dh_ff, the near classes in FP64.
+__device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double shift[3], const double x[3],
+                                 const double nx[3], const ff nxf[3], double k, ff kf, const QuadRules& qr,
+                                 const FfConst& C, cd& D, cd& H) {
+  double dc[3];
+  for (int d = 0; d < 3; ++d) dc[d] = x[d] - (E.c[d] + shift[d]);
+  const double r2 = dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2];
+  const double dist = sqrt(r2);
+  if (dist >= FAR_RATIO * E.hmax) {
+    far_dh_ff(F, dc, r2, dist, nxf, k, kf, C, D, H);
+    return;
+  }
+  element_dh(E, shift, x, nx, k, qr, D, H);
+}
+
 // T = -(D + (i/k) H)
 __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
   return mkc(-D.x + H.y / k, -D.y - H.x / k);
@@ -192,9 +351,10 @@ __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
 // out + dest[o] * n * n.  The diagonal of the zero offset is left to
 // k_self_terms.
-__global__ void k_build_blocks(const Elem* __restrict__ el, int n, const double* __restrict__ shifts,
-                               const int64_t* __restrict__ dest, int n_off, int zero_off, cd* __restrict__ out,
-                               double k, QuadRules qr) {
+__global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
+                               const double* __restrict__ shifts, const int64_t* __restrict__ dest, int n_off,
+                               int zero_off, cd* __restrict__ out, double k, QuadRules qr, FfConst C) {
+  const ff kf = ff_from_d(k);
   const size_t nn = (size_t)n * n;
   const size_t total = nn * (size_t)n_off;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -207,9 +367,10 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, int n, const double*
     const Elem& Ti = el[i];
     double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
     double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
+    const ff nxf[3] = {ff_from_d(nx[0]), ff_from_d(nx[1]), ff_from_d(nx[2])};
     double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
     cd D, H;
-    element_dh(el[j], sh, x, nx, k, qr, D, H);
+    element_dh_mixed(el[j], fel[j], sh, x, nx, nxf, k, kf, qr, C, D, H);
     out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
   }
 }
@@ -403,6 +564,8 @@ fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, in
   cudaError_t e = cudaMalloc(&dtris, sizeof(int32_t) * 3 * ntri);
   if (e == cudaSuccess) e = cudaMalloc(&m.el, sizeof(Elem) * ntri);
   if (e == cudaSuccess) e = cudaMalloc(&m.qr_dev, sizeof(QuadRules));
+  if (e == cudaSuccess) e = cudaMalloc(&m.ffel, sizeof(FfElem) * ntri);
+  if (e == cudaSuccess) e = cudaMalloc(&m.fc_dev, sizeof(FfConst));
   if (e == cudaSuccess) e = cudaMemcpyAsync(dverts, verts, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dtris, tris, sizeof(int32_t) * 3 * ntri, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
@@ -410,7 +573,12 @@ fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, in
     FMPB_LAUNCH("gauss_legendre", st, k_gauss_legendre<<<1, 32, 0, st>>>(m.qr_dev));
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) {
+    FMPB_LAUNCH("prepare_ff", st, k_prepare_ff<<<grid_for(ntri, 128), 128, 0, st>>>(m.el, (int)ntri, m.ffel, m.qr_dev, m.fc_dev));
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&m.qr, m.qr_dev, sizeof(QuadRules), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&m.fc, m.fc_dev, sizeof(FfConst), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dverts);
   cudaFree(dtris);
@@ -429,8 +597,12 @@ fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, in
 void free_mesh(DeviceMesh& m) {
   if (m.el) cudaFree(m.el);
   if (m.qr_dev) cudaFree(m.qr_dev);
+  if (m.ffel) cudaFree(m.ffel);
+  if (m.fc_dev) cudaFree(m.fc_dev);
   m.el = nullptr;
   m.qr_dev = nullptr;
+  m.ffel = nullptr;
+  m.fc_dev = nullptr;
 }
 
 fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n_off, const int32_t* offsets,
@@ -454,7 +626,7 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
   if (e == cudaSuccess) {
     const size_t total = (size_t)m.n * m.n * n_off;
     unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
-    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.n, dshift, ddest, n_off, zero_off, out, k, m.qr));
+    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, ddest, n_off, zero_off, out, k, m.qr, m.fc));
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
                                                      k, m.qr));
