@@ -2,7 +2,8 @@
 // (Sec. 4: the systems of Eqs. (toeplitzBEM) and (FMPBEMsystem) are solved by
 // GMRES with a relative residual tolerance).  Every vector, the Hessenberg
 // columns and the Givens rotations live on the device in FP64; the Arnoldi
-// step is two-pass classical Gram-Schmidt.  The host sequences launches and
+// step is classical Gram-Schmidt with a second pass whenever the first one
+// removed more than half of ||w||^2 (Kahan-Parlett "twice is enough").  The host sequences launches and
 // reads one residual estimate per RHS per iteration (the only device to host
 // traffic), and enforces the wall-clock limit between launches: no kernel
 // waits on anything.
@@ -166,68 +167,106 @@ __global__ void k_cycle_start(GmresState s, int R, int m, double tol) {
 
 // Column j of H from the projections h (nvec = j+1) and the norm of w;
 // applies the previous rotations, forms the new one, updates g and the
-// residual estimate.  One thread per rhs.
+// residual estimate.  One warp per rhs: the lanes stage the column and the
+// rotations in shared memory, lane 0 runs the sequential recurrence.
 __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* __restrict__ wnorm, int R, int m,
                          int j, double tol) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R || !s.active[r]) return;
-  cd* col = s.H + ((int64_t)r * m + j) * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h[i * R + r];
-  col[j + 1] = mkc(wnorm[r], 0.0);
-  for (int i = 0; i < j; ++i) {
-    // [c  s; -conj(s) c] applied to (col[i], col[i+1])
-    const double c = s.cs[r * m + i];
-    const cd sn = s.sn[r * m + i];
-    cd a = col[i], b = col[i + 1];
-    col[i] = cadd(cmulr(a, c), cmul(sn, b));
-    col[i + 1] = csub(cmulr(b, c), cmul(cconj(sn), a));
+  const int r = blockIdx.x, lane = threadIdx.x;
+  if (!s.active[r]) return;
+  __shared__ cd col[MAX_RESTART + 1];
+  __shared__ double csv[MAX_RESTART];
+  __shared__ cd snv[MAX_RESTART];
+  for (int i = lane; i <= j; i += 32) col[i] = h[i * R + r];
+  for (int i = lane; i < j; i += 32) {
+    csv[i] = s.cs[r * m + i];
+    snv[i] = s.sn[r * m + i];
   }
-  cd a = col[j], b = col[j + 1];
-  double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
-  double c;
-  cd sn;
-  if (nb == 0.0) {
-    c = 1.0;
-    sn = mkc(0.0, 0.0);
-  } else if (na == 0.0) {
-    c = 0.0;
-    sn = mkc(1.0, 0.0);
-    a = mkc(0.0, 0.0);
-  } else {
-    double t = hypot(na, nb);
-    c = na / t;
-    // sn = (a/|a|) conj(b) / t
-    cd ua = mkc(a.x / na, a.y / na);
-    sn = cmulr(cmul(ua, cconj(b)), 1.0 / t);
+  if (lane == 0) col[j + 1] = mkc(wnorm[r], 0.0);
+  __syncwarp();
+  if (lane == 0) {
+    for (int i = 0; i < j; ++i) {
+      // [c  s; -conj(s) c] applied to (col[i], col[i+1])
+      const double c = csv[i];
+      const cd sn = snv[i];
+      const cd a = col[i], b = col[i + 1];
+      col[i] = cadd(cmulr(a, c), cmul(sn, b));
+      col[i + 1] = csub(cmulr(b, c), cmul(cconj(sn), a));
+    }
+    cd a = col[j], b = col[j + 1];
+    const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+    double c;
+    cd sn;
+    if (nb == 0.0) {
+      c = 1.0;
+      sn = mkc(0.0, 0.0);
+    } else if (na == 0.0) {
+      c = 0.0;
+      sn = mkc(1.0, 0.0);
+      a = mkc(0.0, 0.0);
+    } else {
+      const double t = hypot(na, nb);
+      c = na / t;
+      // sn = (a/|a|) conj(b) / t
+      const cd ua = mkc(a.x / na, a.y / na);
+      sn = cmulr(cmul(ua, cconj(b)), 1.0 / t);
+    }
+    s.cs[r * m + j] = c;
+    s.sn[r * m + j] = sn;
+    col[j] = cadd(cmulr(a, c), cmul(sn, b));
+    col[j + 1] = mkc(0.0, 0.0);
+    cd* g = s.g + r * (m + 1);
+    const cd gj = g[j];
+    g[j] = cmulr(gj, c);
+    g[j + 1] = cmul(mkc(-sn.x, sn.y), gj);   // -conj(sn) g_j
+    s.jcount[r] = j + 1;
+    const double rel = hypot(g[j + 1].x, g[j + 1].y) / s.bnorm[r];
+    s.resid[r] = rel;
+    if (rel <= tol || wnorm[r] == 0.0) s.active[r] = 0;
   }
-  s.cs[r * m + j] = c;
-  s.sn[r * m + j] = sn;
-  col[j] = cadd(cmulr(a, c), cmul(sn, b));
-  col[j + 1] = mkc(0.0, 0.0);
-  cd* g = s.g + r * (m + 1);
-  cd gj = g[j];
-  g[j] = cmulr(gj, c);
-  g[j + 1] = cmul(mkc(-sn.x, sn.y), gj);   // -conj(sn) g_j
-  s.jcount[r] = j + 1;
-  double rel = hypot(g[j + 1].x, g[j + 1].y) / s.bnorm[r];
-  s.resid[r] = rel;
-  if (rel <= tol || wnorm[r] == 0.0) s.active[r] = 0;
+  __syncwarp();
+  cd* Hcol = s.H + ((int64_t)r * m + j) * (m + 1);
+  for (int i = lane; i <= j + 1; i += 32) Hcol[i] = col[i];
 }
 
 // Back substitution H y = g for the jcount[r] completed columns; y into g.
+// One warp per rhs: the inner sums are split over the lanes.
 __global__ void k_backsolve(GmresState s, int R, int m) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+  const int r = blockIdx.x, lane = threadIdx.x;
   const int J = s.jcount[r];
   cd* g = s.g + r * (m + 1);
+  __shared__ cd y[MAX_RESTART + 1];
+  for (int i = lane; i <= m; i += 32) y[i] = i < J ? g[i] : mkc(0.0, 0.0);
+  __syncwarp();
   for (int i = J - 1; i >= 0; --i) {
-    cd acc = g[i];
-    for (int k = i + 1; k < J; ++k) acc = csub(acc, cmul(s.H[((int64_t)r * m + k) * (m + 1) + i], g[k]));
-    cd d = s.H[((int64_t)r * m + i) * (m + 1) + i];
-    double den = d.x * d.x + d.y * d.y;
-    g[i] = den > 0.0 ? mkc((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den) : mkc(0.0, 0.0);
+    double re = 0.0, im = 0.0;
+    for (int k = i + 1 + lane; k < J; k += 32) {
+      const cd hk = s.H[((int64_t)r * m + k) * (m + 1) + i];
+      const cd yk = y[k];
+      re += hk.x * yk.x - hk.y * yk.y;
+      im += hk.x * yk.y + hk.y * yk.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      const cd acc = mkc(y[i].x - re, y[i].y - im);
+      const cd d = s.H[((int64_t)r * m + i) * (m + 1) + i];
+      const double den = d.x * d.x + d.y * d.y;
+      y[i] = den > 0.0 ? mkc((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den) : mkc(0.0, 0.0);
+    }
+    __syncwarp();
   }
-  for (int i = J; i <= m; ++i) g[i] = mkc(0.0, 0.0);
+  for (int i = lane; i <= m; i += 32) g[i] = i < J ? y[i] : mkc(0.0, 0.0);
+}
+
+// Selective reorthogonalisation: need[r] = 1 when the first Gram-Schmidt
+// pass removed more than half of ||w||^2 (Kahan-Parlett "twice is enough").
+__global__ void k_reorth_flag(const cd* __restrict__ before, const cd* __restrict__ after,
+                              const int* __restrict__ active, int* __restrict__ need, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  need[r] = (active[r] && after[r].x < 0.5 * before[r].x) ? 1 : 0;
 }
 
 // x[r] += sum_{i < jcount[r]} V_i[r] y_i[r]
@@ -278,7 +317,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   GmresState s;
   cd *h = nullptr, *h2 = nullptr, *nrm2 = nullptr;
   double *wnorm = nullptr;
-  int *all_active = nullptr, *bad = nullptr;
+  int *all_active = nullptr, *bad = nullptr, *need = nullptr;
   size_t small = 0;
   for (int pass = 0; pass < 2; ++pass) {
     char* base = (char*)Sb.p;
@@ -293,7 +332,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     s.g = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
     h = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
     h2 = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
-    nrm2 = (cd*)take(sizeof(cd) * (size_t)R);
+    nrm2 = (cd*)take(sizeof(cd) * 2 * (size_t)R);
     s.cs = (double*)take(sizeof(double) * (size_t)R * m);
     s.beta = (double*)take(sizeof(double) * R);
     s.inv = (double*)take(sizeof(double) * R);
@@ -303,6 +342,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     s.active = (int*)take(sizeof(int) * R);
     s.jcount = (int*)take(sizeof(int) * R);
     all_active = (int*)take(sizeof(int) * R);
+    need = (int*)take(sizeof(int) * R);
     bad = (int*)take(sizeof(int));
     if (pass == 0) {
       small = off;
@@ -375,20 +415,26 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       cd* vj = V + (int64_t)j * vstride;
       cd* vn = V + (int64_t)(j + 1) * vstride;
       FMPB_TRY(A(R, vj, vn, st));
-      // two passes of classical Gram-Schmidt against v_0..v_j
+      // classical Gram-Schmidt against v_0..v_j, repeated when the first
+      // pass lost more than half of ||w||^2
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2 + R, 0));
       FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h, 0));
       FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
+      FMPB_LAUNCH("reorth_flag", st, k_reorth_flag<<<rb, 64, 0, st>>>(nrm2 + R, nrm2, s.active, need, R));
+      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, s.active));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
       // ||w||, normalise
       FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
       FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R));
       FMPB_LAUNCH("scale", st, k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, vn, s.inv, R, N, s.active));
-      FMPB_LAUNCH("givens", st, k_givens<<<rb, 64, 0, st>>>(s, h, wnorm, R, m, j, tol));
+      FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
       FMPB_CUDA(cudaGetLastError());
       ++total_it;
       for (int r = 0; r < R; ++r)
@@ -405,7 +451,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         break;
       }
     }
-    FMPB_LAUNCH("backsolve", st, k_backsolve<<<rb, 64, 0, st>>>(s, R, m));
+    FMPB_LAUNCH("backsolve", st, k_backsolve<<<R, 32, 0, st>>>(s, R, m));
     FMPB_LAUNCH("update_x", st, k_update_x<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
     FMPB_CUDA(cudaGetLastError());
     if (!any || timed_out || total_it >= maxit) break;
