@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "internal.cuh"
 #include "profile.cuh"
+#include "ff.cuh"
 
 namespace fmpb {
 
@@ -56,67 +57,6 @@ CircShape make_shape(const int M[3]) {
 int64_t offset_slot(const CircShape& s, int dx, int dy, int dz) {
   auto md = [](int d, int P) { return ((d % P) + P) % P; };
   return ((int64_t)md(dz, s.P[2]) * s.P[1] + md(dy, s.P[1])) * s.P[0] + md(dx, s.P[0]);
-}
-
-// ------------------------------------------------ float-float products ----
-// GB300 runs FP64 at 1/58 of its FP32 rate, so the operator keeps its
-// spectrum as float-float pairs (re_hi, re_lo, im_hi, im_lo): the same 16
-// bytes per entry as complex double, hi + lo carrying 48 significand bits.
-// Products use exact FP32 products (fma residual) and two-sum accumulation,
-// giving FP64-level accuracy (about 2^-47 per product) on the FP32 pipe.
-__device__ __forceinline__ float4 split_ff(cd v) {
-  const float rh = __double2float_rn(v.x);
-  const float ih = __double2float_rn(v.y);
-  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
-}
-
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (sh, sl) += a * x for a, x float-float complex; re and im separately.
-__device__ __forceinline__ void ff_cmac(const float4 a, const float4 x, float& rh, float& rl, float& ih, float& il) {
-  // hi x hi products with their exact rounding errors
-  const float p1 = __fmul_rn(a.x, x.x), e1 = fmaf(a.x, x.x, -p1);   // ar xr
-  const float p2 = __fmul_rn(a.z, x.z), e2 = fmaf(a.z, x.z, -p2);   // ai xi
-  const float p3 = __fmul_rn(a.x, x.z), e3 = fmaf(a.x, x.z, -p3);   // ar xi
-  const float p4 = __fmul_rn(a.z, x.x), e4 = fmaf(a.z, x.x, -p4);   // ai xr
-  // cross terms hi x lo + lo x hi
-  const float cr = fmaf(a.x, x.y, fmaf(a.y, x.x, -fmaf(a.z, x.w, a.w * x.z)));
-  const float ci = fmaf(a.x, x.w, fmaf(a.y, x.z, fmaf(a.z, x.y, a.w * x.x)));
-  float d, ed, s, es;
-  two_sum_f(p1, -p2, d, ed);
-  two_sum_f(rh, d, s, es);
-  rh = s;
-  rl += (es + ed) + ((e1 - e2) + cr);
-  two_sum_f(p3, p4, d, ed);
-  two_sum_f(ih, d, s, es);
-  ih = s;
-  il += (es + ed) + ((e3 + e4) + ci);
-}
-
-// warp sum of a float-float value
-__device__ __forceinline__ void ff_warp_sum(float& h, float& l) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-    float s, e;
-    two_sum_f(h, oh, s, e);
-    h = s;
-    l = __fadd_rn(__fadd_rn(l, ol), e);
-  }
-}
-
-// Renormalise a float-float pair so that |lo| <= ulp(hi)/2.
-__device__ __forceinline__ float4 ff_norm(float rh, float rl, float ih, float il) {
-  const float a = __fadd_rn(rh, rl), b = __fadd_rn(ih, il);
-  return make_float4(a, __fsub_rn(rl, __fsub_rn(a, rh)), b, __fsub_rn(il, __fsub_rn(b, ih)));
-}
-
-__device__ __forceinline__ cd ff_to_cd(const float4 v) {
-  return mkc((double)v.x + (double)v.y, (double)v.z + (double)v.w);
 }
 
 // Direct DFT along one axis for the lines (o1, o2, i), float-float arithmetic:
@@ -177,7 +117,7 @@ __global__ void k_dft_axis_ff(const void* in_, void* out_, int O2, int64_t I, in
 }
 
 template <bool IN_FF, bool OUT_FF>
-static fmpb_status dft_axis(const void* in, void* out, int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
+static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
                             int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign, double scale,
                             bool accumulate, cudaStream_t st) {
   if (O1 > 65535 || O2 > 65535) {
@@ -204,7 +144,7 @@ static fmpb_status dft_axis(const void* in, void* out, int O1, int O2, int64_t I
     FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis_ff<IN_FF, OUT_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
-  FMPB_LAUNCH("dft_axis", st, k_dft_axis_ff<IN_FF, OUT_FF><<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P,
+  FMPB_LAUNCH(name, st, k_dft_axis_ff<IN_FF, OUT_FF><<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P,
                                                                            sign, scale, accumulate ? 1 : 0, (int)TI));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
@@ -216,27 +156,27 @@ fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaSt
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   bool ff = false;
   if (Px > 1) {
-    FMPB_TRY((dft_axis<false, true>(grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner, inner, 0,
+    FMPB_TRY((dft_axis<false, true>("dft_spectrum", grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner, inner, 0,
                                     (int64_t)Px * inner, inner, Px, Px, Px, -1, 1.0, false, st)));
     ff = true;
   }
   if (Py > 1) {
     if (ff)
-      FMPB_TRY((dft_axis<true, true>(grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner,
+      FMPB_TRY((dft_axis<true, true>("dft_spectrum", grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner,
                                      (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py, Py, Py, -1, 1.0, false,
                                      st)));
     else
-      FMPB_TRY((dft_axis<false, true>(grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner,
+      FMPB_TRY((dft_axis<false, true>("dft_spectrum", grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner,
                                       (int64_t)Px * inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py,
                                       Py, Py, -1, 1.0, false, st)));
     ff = true;
   }
   if (Pz > 1) {
     if (ff)
-      FMPB_TRY((dft_axis<true, true>(grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
+      FMPB_TRY((dft_axis<true, true>("dft_spectrum", grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
                                      (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st)));
     else
-      FMPB_TRY((dft_axis<false, true>(grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
+      FMPB_TRY((dft_axis<false, true>("dft_spectrum", grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
                                       (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st)));
     ff = true;
   }
@@ -376,24 +316,24 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   float4* A = reinterpret_cast<float4*>(scratch);
   float4* G = reinterpret_cast<float4*>(scratch + (size_t)s.F * RB);
   // forward x: x[r][cz][cy][cx][b] (complex double) -> A[cz][cy][fx][r][b]
-  FMPB_TRY((dft_axis<false, true>(x, A, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B, (int64_t)Px * RB, RB, Mx, Px,
+  FMPB_TRY((dft_axis<false, true>("dft_fwd_x", x, A, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B, (int64_t)Px * RB, RB, Mx, Px,
                                   Px, -1, 1.0, false, st)));
   // forward y: A[cz][cy][fx][rb] -> G[cz][fy][fx][rb]
-  FMPB_TRY((dft_axis<true, true>(A, G, Mz, Px, RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, (int64_t)Py * Px * RB,
+  FMPB_TRY((dft_axis<true, true>("dft_fwd_y", A, G, Mz, Px, RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, (int64_t)Py * Px * RB,
                                  RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st)));
   // forward z: G[cz][fy fx][rb] -> A[fz][fy fx][rb]
-  FMPB_TRY((dft_axis<true, true>(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz,
+  FMPB_TRY((dft_axis<true, true>("dft_fwd_z", G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz,
                                  Pz, Pz, -1, 1.0, false, st)));
   // per-frequency block products: A[f][r][b] -> G[f][r][b]
   FMPB_TRY(block_product(spec, spec_ff, A, G, s.F, B, R, st));
   // inverse z: G[fz][fy fx][rb] -> A[cz][fy fx][rb], cz < Mz
-  FMPB_TRY((dft_axis<true, true>(G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz,
+  FMPB_TRY((dft_axis<true, true>("dft_inv_z", G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz,
                                  Mz, Pz, +1, 1.0, false, st)));
   // inverse y: A[cz][fy][fx][rb] -> G[cz][cy][fx][rb], cy < My
-  FMPB_TRY((dft_axis<true, true>(A, G, Mz, Px, RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, (int64_t)My * Px * RB,
+  FMPB_TRY((dft_axis<true, true>("dft_inv_y", A, G, Mz, Px, RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, (int64_t)My * Px * RB,
                                  RB, (int64_t)Px * RB, Py, My, Py, +1, 1.0, false, st)));
   // inverse x with crop and 1/F: G[cz][cy][fx][r][b] -> y[r][cz][cy][cx][b] (complex double)
-  FMPB_TRY((dft_axis<true, false>(G, y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B, (int64_t)Mx * B, B, Px, Mx, Px,
+  FMPB_TRY((dft_axis<true, false>("dft_inv_x", G, y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B, (int64_t)Mx * B, B, Px, Mx, Px,
                                   +1, 1.0 / (double)s.F, accumulate, st)));
   return FMPB_OK;
 }

@@ -84,4 +84,65 @@ __device__ __forceinline__ ffc ffc_mul(ffc a, ffc b) {
   return {ff_sub(ff_mul(a.re, b.re), ff_mul(a.im, b.im)), ff_add(ff_mul(a.re, b.im), ff_mul(a.im, b.re))};
 }
 
+// ------------------------------------------------ float-float products ----
+// GB300 runs FP64 at 1/58 of its FP32 rate, so the operator keeps its
+// spectrum as float-float pairs (re_hi, re_lo, im_hi, im_lo): the same 16
+// bytes per entry as complex double, hi + lo carrying 48 significand bits.
+// Products use exact FP32 products (fma residual) and two-sum accumulation,
+// giving FP64-level accuracy (about 2^-47 per product) on the FP32 pipe.
+__device__ __forceinline__ float4 split_ff(double2 v) {
+  const float rh = __double2float_rn(v.x);
+  const float ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (sh, sl) += a * x for a, x float-float complex; re and im separately.
+__device__ __forceinline__ void ff_cmac(const float4 a, const float4 x, float& rh, float& rl, float& ih, float& il) {
+  // hi x hi products with their exact rounding errors
+  const float p1 = __fmul_rn(a.x, x.x), e1 = fmaf(a.x, x.x, -p1);   // ar xr
+  const float p2 = __fmul_rn(a.z, x.z), e2 = fmaf(a.z, x.z, -p2);   // ai xi
+  const float p3 = __fmul_rn(a.x, x.z), e3 = fmaf(a.x, x.z, -p3);   // ar xi
+  const float p4 = __fmul_rn(a.z, x.x), e4 = fmaf(a.z, x.x, -p4);   // ai xr
+  // cross terms hi x lo + lo x hi
+  const float cr = fmaf(a.x, x.y, fmaf(a.y, x.x, -fmaf(a.z, x.w, a.w * x.z)));
+  const float ci = fmaf(a.x, x.w, fmaf(a.y, x.z, fmaf(a.z, x.y, a.w * x.x)));
+  float d, ed, s, es;
+  two_sum_f(p1, -p2, d, ed);
+  two_sum_f(rh, d, s, es);
+  rh = s;
+  rl += (es + ed) + ((e1 - e2) + cr);
+  two_sum_f(p3, p4, d, ed);
+  two_sum_f(ih, d, s, es);
+  ih = s;
+  il += (es + ed) + ((e3 + e4) + ci);
+}
+
+// warp sum of a float-float value
+__device__ __forceinline__ void ff_warp_sum(float& h, float& l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum_f(h, oh, s, e);
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, ol), e);
+  }
+}
+
+// Renormalise a float-float pair so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ float4 ff_norm(float rh, float rl, float ih, float il) {
+  const float a = __fadd_rn(rh, rl), b = __fadd_rn(ih, il);
+  return make_float4(a, __fsub_rn(rl, __fsub_rn(a, rh)), b, __fsub_rn(il, __fsub_rn(b, ih)));
+}
+
+__device__ __forceinline__ double2 ff_to_cd(const float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
 }  // namespace fmpb

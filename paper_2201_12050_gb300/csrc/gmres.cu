@@ -14,6 +14,7 @@
 #include "internal.cuh"
 #include "profile.cuh"
 #include "gmres.cuh"
+#include "ff.cuh"
 
 namespace fmpb {
 
@@ -74,54 +75,6 @@ __global__ void k_reduce_partials(const cd* __restrict__ partial, int nblk, int 
   cd s = mkc(0.0, 0.0);
   for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(int64_t)t * nblk + b]);
   out[t] = accumulate ? cadd(out[t], s) : s;
-}
-
-// w[r] -= sum_v V_v[r] h[v*R + r]: one row per thread, the basis walked 8
-// vectors at a time (8 loads in flight); the coefficients of rhs r sit in
-// shared memory.
-__global__ void k_subtract_projection(const cd* __restrict__ V, int64_t vstride, int nvec,
-                                      const cd* __restrict__ h, cd* __restrict__ w, int R, int64_t N,
-                                      const int* __restrict__ active) {
-  const int r = blockIdx.y;
-  if (!active[r]) return;
-  __shared__ cd hs[MAX_RESTART + 1];
-  for (int v = threadIdx.x; v < nvec; v += blockDim.x) hs[v] = h[v * R + r];
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  cd* wr = w + (int64_t)r * N;
-  const cd* Vr = V + (int64_t)r * N;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    cd acc = wr[i];
-    int v = 0;
-    for (; v + 7 < nvec; v += 8) {
-      cd a[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const cd hv = hs[v + q];
-        acc.x -= a[q].x * hv.x - a[q].y * hv.y;
-        acc.y -= a[q].x * hv.y + a[q].y * hv.x;
-      }
-    }
-    for (; v < nvec; ++v) {
-      const cd hv = hs[v];
-      const cd a = Vr[(int64_t)v * vstride + i];
-      acc.x -= a.x * hv.x - a.y * hv.y;
-      acc.y -= a.x * hv.y + a.y * hv.x;
-    }
-    wr[i] = acc;
-  }
-}
-
-// y[r] = x[r] * s[r]  (s real, per rhs; skipped for inactive rhs)
-__global__ void k_scale(const cd* __restrict__ x, cd* __restrict__ y, const double* __restrict__ s, int R,
-                        int64_t N, const int* __restrict__ active) {
-  const int r = blockIdx.y;
-  if (!active[r]) return;
-  const double f = s[r];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    y[(int64_t)r * N + i] = cmulr(x[(int64_t)r * N + i], f);
 }
 
 // y = b - y  (residual from a product)
@@ -269,16 +222,120 @@ __global__ void k_reorth_flag(const cd* __restrict__ before, const cd* __restric
   need[r] = (active[r] && after[r].x < 0.5 * before[r].x) ? 1 : 0;
 }
 
-// x[r] += sum_{i < jcount[r]} V_i[r] y_i[r]
-__global__ void k_update_x(const cd* __restrict__ V, int64_t vstride, GmresState s, cd* __restrict__ x, int R,
-                           int m, int64_t N) {
+// ----------------------------------------------- float-float Krylov basis --
+// The basis vectors are stored as float-float pairs (16 bytes per complex
+// entry, as complex double) and every Gram-Schmidt dot product and update
+// runs in float-float arithmetic on the FP32 pipe (48-bit significands): on
+// GB300 the FP64 pipe would bound these passes at 1/58 of the FP32 rate.
+// Reductions across threads, the Hessenberg matrix, the rotations, the
+// solution update and the true residual stay in FP64.
+
+__device__ __forceinline__ float4 ff_conj(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
+
+// partial[(v*R + r)*gridDim.x + blk] = sum over the block's rows of conj(V_v[r]) w[r]
+__global__ void k_dots_ff(const float4* __restrict__ V, int64_t vstride, int nvec, const float4* __restrict__ w, int R,
+                          int64_t N, cd* __restrict__ partial, const int* __restrict__ active) {
+  const int blk = blockIdx.x, v = blockIdx.y, r = blockIdx.z;
+  __shared__ double sre[RED_THREADS], sim[RED_THREADS];
+  float rh[2] = {0.f, 0.f}, rl[2] = {0.f, 0.f}, ih[2] = {0.f, 0.f}, il[2] = {0.f, 0.f};
+  if (active[r]) {
+    const float4* a = V + (int64_t)v * vstride + (int64_t)r * N;
+    const float4* b = w + (int64_t)r * N;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
+    for (; i + stride < N; i += 2 * stride) {
+      const float4 x0 = a[i], x1 = a[i + stride], y0 = b[i], y1 = b[i + stride];
+      ff_cmac(ff_conj(x0), y0, rh[0], rl[0], ih[0], il[0]);
+      ff_cmac(ff_conj(x1), y1, rh[1], rl[1], ih[1], il[1]);
+    }
+    if (i < N) ff_cmac(ff_conj(a[i]), b[i], rh[0], rl[0], ih[0], il[0]);
+  }
+  sre[threadIdx.x] = ((double)rh[0] + (double)rl[0]) + ((double)rh[1] + (double)rl[1]);
+  sim[threadIdx.x] = ((double)ih[0] + (double)il[0]) + ((double)ih[1] + (double)il[1]);
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) {
+      sre[threadIdx.x] += sre[threadIdx.x + s2];
+      sim[threadIdx.x] += sim[threadIdx.x + s2];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[((int64_t)v * R + r) * gridDim.x + blk] = mkc(sre[0], sim[0]);
+}
+
+// w[r] -= sum_v V_v[r] h[v*R + r], one row per thread, 8 basis vectors in flight
+__global__ void k_subtract_ff(const float4* __restrict__ V, int64_t vstride, int nvec, const cd* __restrict__ h,
+                              float4* __restrict__ w, int R, int64_t N, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  __shared__ float4 hs[MAX_RESTART + 1];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const cd hv = h[v * R + r];
+    hs[v] = split_ff(mkc(-hv.x, -hv.y));
+  }
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float4* wr = w + (int64_t)r * N;
+  const float4* Vr = V + (int64_t)r * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const float4 w0 = wr[i];
+    float rh = w0.x, rl = w0.y, ih = w0.z, il = w0.w;
+    int v = 0;
+    for (; v + 7 < nvec; v += 8) {
+      float4 a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ff_cmac(a[q], hs[v + q], rh, rl, ih, il);
+    }
+    for (; v < nvec; ++v) ff_cmac(Vr[(int64_t)v * vstride + i], hs[v], rh, rl, ih, il);
+    wr[i] = ff_norm(rh, rl, ih, il);
+  }
+}
+
+// v[r] *= s[r] in float-float
+__global__ void k_scale_ff(float4* __restrict__ v, const double* __restrict__ s, int R, int64_t N,
+                           const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  const ff f = ff_from_d(s[r]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = v[(int64_t)r * N + i];
+    const ff re = ff_mul(ff{a.x, a.y}, f), im = ff_mul(ff{a.z, a.w}, f);
+    v[(int64_t)r * N + i] = make_float4(re.h, re.l, im.h, im.l);
+  }
+}
+
+// y[r] = float-float(x[r] * s[r])
+__global__ void k_scale_to_ff(const cd* __restrict__ x, float4* __restrict__ y, const double* __restrict__ s, int R,
+                              int64_t N, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  const double f = s[r];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    y[(int64_t)r * N + i] = split_ff(cmulr(x[(int64_t)r * N + i], f));
+}
+
+__global__ void k_cd_to_ff(const cd* __restrict__ x, float4* __restrict__ y, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = split_ff(x[i]);
+}
+
+__global__ void k_ff_to_cd(const float4* __restrict__ x, cd* __restrict__ y, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = ff_to_cd(x[i]);
+}
+
+// x[r] += sum_{i < jcount[r]} V_i[r] y_i[r]  (FP64 accumulation)
+__global__ void k_update_x_ff(const float4* __restrict__ V, int64_t vstride, GmresState s, cd* __restrict__ x, int R,
+                              int m, int64_t N) {
   const int r = blockIdx.y;
   const int J = s.jcount[r];
   if (J == 0) return;
   const cd* y = s.g + r * (m + 1);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     cd acc = x[(int64_t)r * N + i];
-    for (int v = 0; v < J; ++v) acc = cfma(V[(int64_t)v * vstride + (int64_t)r * N + i], y[v], acc);
+    for (int v = 0; v < J; ++v) acc = cfma(ff_to_cd(V[(int64_t)v * vstride + (int64_t)r * N + i]), y[v], acc);
     x[(int64_t)r * N + i] = acc;
   }
 }
@@ -312,7 +369,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   auto t0 = std::chrono::steady_clock::now();
   const int64_t vstride = (int64_t)R * N;
   // device memory: basis (m+1) R N, work vector R N, small state
-  DevBuf Vb, Wb, Sb, Pb;
+  DevBuf Vb, Wb, Tb, Sb, Pb;
   // control state: carve one allocation; the first pass (base = null) sizes it
   GmresState s;
   cd *h = nullptr, *h2 = nullptr, *nrm2 = nullptr;
@@ -347,7 +404,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     if (pass == 0) {
       small = off;
       if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
-          cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
+          cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess ||
+          cudaMalloc(&Tb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
           cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 1) * R * RED_BLOCKS) != cudaSuccess) {
         cudaGetLastError();
         set_error("gmres: cannot allocate the Krylov basis (%zu bytes)", sizeof(cd) * (size_t)(m + 2) * vstride);
@@ -355,8 +413,9 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       }
     }
   }
-  cd* V = (cd*)Vb.p;
-  cd* W = (cd*)Wb.p;
+  float4* V = (float4*)Vb.p;   // float-float basis
+  cd* W = (cd*)Wb.p;           // product output / residual (FP64)
+  cd* T = (cd*)Tb.p;           // product input (FP64 copy of v_j)
   cd* partial = (cd*)Pb.p;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
@@ -404,7 +463,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     first = false;
     FMPB_TRY(norms(W, s.beta, s.inv));
     FMPB_LAUNCH("cycle_start", st, k_cycle_start<<<rb, 64, 0, st>>>(s, R, m, tol));
-    FMPB_LAUNCH("scale", st, k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active));
+    FMPB_LAUNCH("scale_to_ff", st, k_scale_to_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active));
     FMPB_CUDA(cudaGetLastError());
     FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
     FMPB_CUDA(cudaStreamSynchronize(st));
@@ -412,28 +471,30 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     for (int r = 0; r < R; ++r) any |= hact[r] != 0;
     if (!any) break;
     for (int j = 0; j < m && total_it < maxit; ++j) {
-      cd* vj = V + (int64_t)j * vstride;
-      cd* vn = V + (int64_t)(j + 1) * vstride;
-      FMPB_TRY(A(R, vj, vn, st));
+      float4* vj = V + (int64_t)j * vstride;
+      float4* vn = V + (int64_t)(j + 1) * vstride;
+      FMPB_LAUNCH("ff_to_cd", st, k_ff_to_cd<<<vec_blocks, 256, 0, st>>>(vj, T, vstride));
+      FMPB_TRY(A(R, T, W, st));
+      FMPB_LAUNCH("cd_to_ff", st, k_cd_to_ff<<<vec_blocks, 256, 0, st>>>(W, vn, vstride));
       // classical Gram-Schmidt against v_0..v_j, repeated when the first
       // pass lost more than half of ||w||^2
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2 + R, 0));
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
+      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
       FMPB_LAUNCH("reorth_flag", st, k_reorth_flag<<<rb, 64, 0, st>>>(nrm2 + R, nrm2, s.active, need, R));
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
+      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_projection<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
       // ||w||, normalise
-      FMPB_LAUNCH("dots", st, k_dots<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
       FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R));
-      FMPB_LAUNCH("scale", st, k_scale<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, vn, s.inv, R, N, s.active));
+      FMPB_LAUNCH("scale", st, k_scale_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, s.inv, R, N, s.active));
       FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
       FMPB_CUDA(cudaGetLastError());
       ++total_it;
@@ -452,7 +513,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       }
     }
     FMPB_LAUNCH("backsolve", st, k_backsolve<<<R, 32, 0, st>>>(s, R, m));
-    FMPB_LAUNCH("update_x", st, k_update_x<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
+    FMPB_LAUNCH("update_x", st, k_update_x_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
     FMPB_CUDA(cudaGetLastError());
     if (!any || timed_out || total_it >= maxit) break;
   }
