@@ -88,11 +88,11 @@ struct fmpb_operator {
   int64_t B = 0;
   int dim = 0;
   cd* spec = nullptr;      // F x B x B, float-float pairs (re_hi, re_lo, im_hi, im_lo) per entry
-  cd* S = nullptr;         // n_near x n x n (FMM form)
+  cd* S = nullptr;         // n_near x n x n (FMM form), float-float pairs
   int* near_offs = nullptr;
   int n_near = 0;
-  cd* V0 = nullptr;        // B x n
-  cd* U0 = nullptr;        // n x B
+  cd* V0 = nullptr;        // B x n, float-float pairs
+  cd* U0 = nullptr;        // n x B, float-float pairs
   size_t bytes = 0;
   // scratch, grown on demand (calls on one operator are stream-ordered)
   cd* scratch = nullptr;
@@ -128,13 +128,16 @@ struct fmpb_operator {
     }
     const size_t circ = circulant_scratch_elems(shape, B, R);
     const size_t mom = (size_t)R * Nc * B;
-    FMPB_TRY(ensure_scratch(circ + 2 * mom));
+    const size_t nvec = (size_t)R * Nc * mesh.n;
+    FMPB_TRY(ensure_scratch(circ + 2 * mom + nvec));
     cd* Mom = scratch + circ;
     cd* Loc = Mom + mom;
-    FMPB_TRY(near_apply(S, near_offs, n_near, mesh.n, shape.M, R, x, y, false, st));
-    FMPB_TRY(p2m_apply(V0, mesh.n, (int)B, (int64_t)R * Nc, x, Mom, st));
+    float4* xff = reinterpret_cast<float4*>(Loc + mom);
+    FMPB_TRY(vector_to_ff(x, xff, nvec, st));
+    FMPB_TRY(near_apply(reinterpret_cast<const float4*>(S), near_offs, n_near, mesh.n, shape.M, R, xff, y, false, st));
+    FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0), mesh.n, (int)B, (int64_t)R * Nc, xff, Mom, st));
     FMPB_TRY(circulant_apply(shape, B, spec, R, Mom, Loc, false, scratch, st, true));
-    FMPB_TRY(l2p_apply(U0, mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
+    FMPB_TRY(l2p_apply(reinterpret_cast<const float4*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
     return FMPB_OK;
   }
 };
@@ -256,6 +259,10 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     for (int i = 0; i < op->n_near; ++i) dnear[i] = i;
     s = build_blocks(op->mesh, op->grid, k, op->n_near, near_off.data(), dnear.data(), op->S, st);
     if (s == FMPB_OK) s = multipole_tables(op->mesh, k, nt, op->V0, op->U0, st);
+    // the products read the near blocks and the P2M/L2P tables as float-float pairs
+    if (s == FMPB_OK) s = spectrum_to_ff(op->S, (size_t)op->n_near * n * n, st);
+    if (s == FMPB_OK) s = spectrum_to_ff(op->V0, (size_t)B * n, st);
+    if (s == FMPB_OK) s = spectrum_to_ff(op->U0, (size_t)B * n, st);
     if (s != FMPB_OK) return fail(s);
     const int n_far = (int)(far_off.size() / 3);
     std::vector<double> dvec(3 * (size_t)n_far);

@@ -261,6 +261,17 @@ fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st) {
   return FMPB_OK;
 }
 
+__global__ void k_vec_to_ff(const cd* __restrict__ x, float4* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = split_ff(x[i]);
+}
+
+fmpb_status vector_to_ff(const cd* x, float4* y, size_t n, cudaStream_t st) {
+  FMPB_LAUNCH("to_ff", st, k_vec_to_ff<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(x, y, n));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 static fmpb_status spectrum_from_ff(cd* spec, size_t n, cudaStream_t st) {
   FMPB_LAUNCH("from_ff", st, k_from_ff<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(spec, n));
   FMPB_CUDA(cudaGetLastError());
@@ -312,29 +323,45 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
   const int64_t Nc = s.ncells;
-  // both halves hold float-float values (16 bytes each, like complex double)
-  float4* A = reinterpret_cast<float4*>(scratch);
-  float4* G = reinterpret_cast<float4*>(scratch + (size_t)s.F * RB);
-  // forward x: x[r][cz][cy][cx][b] (complex double) -> A[cz][cy][fx][r][b]
-  FMPB_TRY((dft_axis<false, true>("dft_fwd_x", x, A, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B, (int64_t)Px * RB, RB, Mx, Px,
-                                  Px, -1, 1.0, false, st)));
-  // forward y: A[cz][cy][fx][rb] -> G[cz][fy][fx][rb]
-  FMPB_TRY((dft_axis<true, true>("dft_fwd_y", A, G, Mz, Px, RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, (int64_t)Py * Px * RB,
-                                 RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st)));
-  // forward z: G[cz][fy fx][rb] -> A[fz][fy fx][rb]
-  FMPB_TRY((dft_axis<true, true>("dft_fwd_z", G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz,
-                                 Pz, Pz, -1, 1.0, false, st)));
-  // per-frequency block products: A[f][r][b] -> G[f][r][b]
-  FMPB_TRY(block_product(spec, spec_ff, A, G, s.F, B, R, st));
-  // inverse z: G[fz][fy fx][rb] -> A[cz][fy fx][rb], cz < Mz
-  FMPB_TRY((dft_axis<true, true>("dft_inv_z", G, A, 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz,
-                                 Mz, Pz, +1, 1.0, false, st)));
-  // inverse y: A[cz][fy][fx][rb] -> G[cz][cy][fx][rb], cy < My
-  FMPB_TRY((dft_axis<true, true>("dft_inv_y", A, G, Mz, Px, RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, (int64_t)My * Px * RB,
-                                 RB, (int64_t)Px * RB, Py, My, Py, +1, 1.0, false, st)));
-  // inverse x with crop and 1/F: G[cz][cy][fx][r][b] -> y[r][cz][cy][cx][b] (complex double)
-  FMPB_TRY((dft_axis<true, false>("dft_inv_x", G, y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B, (int64_t)Mx * B, B, Px, Mx, Px,
-                                  +1, 1.0 / (double)s.F, accumulate, st)));
+  // two float-float buffers (16 bytes per value, like complex double); an
+  // axis with a single cell (P = 1) leaves the layout unchanged and is skipped
+  float4* buf[2] = {reinterpret_cast<float4*>(scratch), reinterpret_cast<float4*>(scratch + (size_t)s.F * RB)};
+  int cur = 0;
+  // forward x: x[r][cz][cy][cx][b] (complex double) -> [cz][cy][fx][r][b]
+  FMPB_TRY((dft_axis<false, true>("dft_fwd_x", x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
+                                  (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st)));
+  // forward y: [cz][cy][fx][rb] -> [cz][fy][fx][rb]
+  if (Py > 1) {
+    FMPB_TRY((dft_axis<true, true>("dft_fwd_y", buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)My * Px * RB, RB,
+                                   (int64_t)Px * RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0,
+                                   false, st)));
+    cur = 1 - cur;
+  }
+  // forward z: [cz][fy fx][rb] -> [fz][fy fx][rb]
+  if (Pz > 1) {
+    FMPB_TRY((dft_axis<true, true>("dft_fwd_z", buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB,
+                                   0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz, -1, 1.0, false, st)));
+    cur = 1 - cur;
+  }
+  // per-frequency block products: [f][r][b] -> [f][r][b]
+  FMPB_TRY(block_product(spec, spec_ff, buf[cur], buf[1 - cur], s.F, B, R, st));
+  cur = 1 - cur;
+  // inverse z: [fz][fy fx][rb] -> [cz][fy fx][rb], cz < Mz
+  if (Pz > 1) {
+    FMPB_TRY((dft_axis<true, true>("dft_inv_z", buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB,
+                                   0, RB, (int64_t)Py * Px * RB, Pz, Mz, Pz, +1, 1.0, false, st)));
+    cur = 1 - cur;
+  }
+  // inverse y: [cz][fy][fx][rb] -> [cz][cy][fx][rb], cy < My
+  if (Py > 1) {
+    FMPB_TRY((dft_axis<true, true>("dft_inv_y", buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)Py * Px * RB, RB,
+                                   (int64_t)Px * RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, Py, My, Py, +1, 1.0,
+                                   false, st)));
+    cur = 1 - cur;
+  }
+  // inverse x with crop and 1/F: [cz][cy][fx][r][b] -> y[r][cz][cy][cx][b] (complex double)
+  FMPB_TRY((dft_axis<true, false>("dft_inv_x", buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
+                                  (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, accumulate, st)));
   return FMPB_OK;
 }
 

@@ -89,6 +89,8 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
                             bool accumulate, cd* scratch, cudaStream_t st, bool spec_ff = false);
 // In-place conversion of n complex doubles to float-float pairs (re_hi, re_lo, im_hi, im_lo).
 fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st);
+// Out-of-place conversion of n complex doubles to float-float pairs.
+fmpb_status vector_to_ff(const cd* x, float4* y, size_t n, cudaStream_t st);
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R);
 
 }  // namespace fmpb

@@ -20,6 +20,7 @@
 #include "internal.cuh"
 #include "profile.cuh"
 #include "multipole.cuh"
+#include "ff.cuh"
 
 namespace fmpb {
 
@@ -415,44 +416,44 @@ __global__ void k_m2l_blocks(int nt, double k, const double* __restrict__ dvecs,
 }
 
 // ----------------------------------------------------------- applications --
-// Mom[r][c][q] = sum_j V_0[q][j] p[r][c][j]; one CTA per (r, c) column,
-// p staged in shared memory.
-__global__ void k_p2m_apply(const cd* __restrict__ V0, int n, int B, const cd* __restrict__ p, cd* __restrict__ Mom) {
-  extern __shared__ cd ps[];
+// Mom[r][c][q] = sum_j V_0[q][j] p[r][c][j]: one CTA per (r, c) column, p
+// (float-float) in shared memory, one warp per coefficient row of V_0
+// (float-float); Mom complex double.
+__global__ void k_p2m_apply_ff(const float4* __restrict__ V0, int n, int B, const float4* __restrict__ p,
+                               cd* __restrict__ Mom) {
+  extern __shared__ float4 ps4[];
   const int64_t col = blockIdx.x;   // r * Nc + c
-  const cd* src = p + col * n;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) ps[j] = src[j];
+  const float4* src = p + col * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) ps4[j] = src[j];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int q = warp; q < B; q += nw) {
-    cd acc = mkc(0.0, 0.0);
-    const cd* row = V0 + (size_t)q * n;
-    for (int j = lane; j < n; j += 32) acc = cfma(row[j], ps[j], acc);
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
-    if (lane == 0) Mom[col * B + q] = acc;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4* row = V0 + (size_t)q * n;
+    for (int j = lane; j < n; j += 32) ff_cmac(row[j], ps4[j], rh, rl, ih, il);
+    ff_warp_sum(rh, rl);
+    ff_warp_sum(ih, il);
+    if (lane == 0) Mom[col * B + q] = mkc((double)rh + (double)rl, (double)ih + (double)il);
   }
 }
 
-// y[r][c][i] += sum_q U_0[i][q] Loc[r][c][q]
-__global__ void k_l2p_apply(const cd* __restrict__ U0, int n, int B, const cd* __restrict__ Loc, cd* __restrict__ y) {
-  extern __shared__ cd ls[];
+// y[r][c][i] += sum_q U_0[i][q] Loc[r][c][q]: Loc (complex double) split into
+// float-float in shared memory, one warp per row of U_0 (float-float).
+__global__ void k_l2p_apply_ff(const float4* __restrict__ U0, int n, int B, const cd* __restrict__ Loc,
+                               cd* __restrict__ y) {
+  extern __shared__ float4 ls4[];
   const int64_t col = blockIdx.x;
   const cd* src = Loc + col * B;
-  for (int q = threadIdx.x; q < B; q += blockDim.x) ls[q] = src[q];
+  for (int q = threadIdx.x; q < B; q += blockDim.x) ls4[q] = split_ff(src[q]);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < n; i += nw) {
-    cd acc = mkc(0.0, 0.0);
-    const cd* row = U0 + (size_t)i * B;
-    for (int q = lane; q < B; q += 32) acc = cfma(row[q], ls[q], acc);
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
-    if (lane == 0) y[col * n + i] = cadd(y[col * n + i], acc);
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4* row = U0 + (size_t)i * B;
+    for (int q = lane; q < B; q += 32) ff_cmac(row[q], ls4[q], rh, rl, ih, il);
+    ff_warp_sum(rh, rl);
+    ff_warp_sum(ih, il);
+    if (lane == 0) y[col * n + i] = cadd(y[col * n + i], mkc((double)rh + (double)rl, (double)ih + (double)il));
   }
 }
 
@@ -505,14 +506,16 @@ fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, cons
   return FMPB_OK;
 }
 
-fmpb_status p2m_apply(const cd* V0, int n, int B, int64_t columns, const cd* p, cd* Mom, cudaStream_t st) {
-  FMPB_LAUNCH("p2m_apply", st, k_p2m_apply<<<(unsigned)columns, 256, sizeof(cd) * n, st>>>(V0, n, B, p, Mom));
+fmpb_status p2m_apply(const float4* V0, int n, int B, int64_t columns, const float4* p, cd* Mom, cudaStream_t st) {
+  const size_t smem = sizeof(float4) * n;
+  if (smem > 48 * 1024) FMPB_CUDA(cudaFuncSetAttribute(k_p2m_apply_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FMPB_LAUNCH("p2m_apply", st, k_p2m_apply_ff<<<(unsigned)columns, 256, smem, st>>>(V0, n, B, p, Mom));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
 
-fmpb_status l2p_apply(const cd* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st) {
-  FMPB_LAUNCH("l2p_apply", st, k_l2p_apply<<<(unsigned)columns, 256, sizeof(cd) * B, st>>>(U0, n, B, Loc, y));
+fmpb_status l2p_apply(const float4* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st) {
+  FMPB_LAUNCH("l2p_apply", st, k_l2p_apply_ff<<<(unsigned)columns, 256, sizeof(float4) * B, st>>>(U0, n, B, Loc, y));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }

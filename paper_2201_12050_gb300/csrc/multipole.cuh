@@ -19,7 +19,8 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, int nt, cd* V0, cd* 
 // K(d_o) for n_d translations; block o written at out + dest[o] B B (dest < 0 skipped).
 fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, const int64_t* dest_host, cd* out,
                        cudaStream_t st);
-fmpb_status p2m_apply(const cd* V0, int n, int B, int64_t columns, const cd* p, cd* Mom, cudaStream_t st);
-fmpb_status l2p_apply(const cd* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st);
+// Applications with float-float tables (V0: B x n, U0: n x B) and float-float p.
+fmpb_status p2m_apply(const float4* V0, int n, int B, int64_t columns, const float4* p, cd* Mom, cudaStream_t st);
+fmpb_status l2p_apply(const float4* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st);
 
 }  // namespace fmpb
