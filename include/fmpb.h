@@ -62,7 +62,12 @@ typedef enum {
 } fmpb_status;
 
 typedef enum { FMPB_FORM_AUTO = -1, FMPB_FORM_FMM = 0, FMPB_FORM_PBEM = 1 } fmpb_form;
-typedef enum { FMPB_FP64 = 0, FMPB_FP32 = 1, FMPB_BF16 = 2 } fmpb_precision;
+/* FP64: spectrum and tables as float-float pairs (FP64-class accuracy).
+ * FP32: spectrum in complex FP32 (half the bytes per product).
+ * MIXED: both spectra; fmpb_matvec uses the accurate one and fmpb_solve
+ *        runs GMRES-IR (FP32 inner solves, accurate outer residuals).
+ * BF16 is reserved. */
+typedef enum { FMPB_FP64 = 0, FMPB_FP32 = 1, FMPB_BF16 = 2, FMPB_MIXED = 3 } fmpb_precision;
 
 /* Finite lattice (Sec. 2.2, Fig. PeriodicArray2d): counts[a] cells along
  * lattice vector vectors[a] (metres).  counts[a] = 1 for an unused axis. */
@@ -91,7 +96,7 @@ typedef struct {
                       |d| <= 2 rho is refused (EADMISS). */
   int n_t;         /* truncation number of the FMM form (Eq. (greenFMM)), 1..20;
                       0 = default 8 */
-  int precision;   /* fmpb_precision of the product; FMPB_FP64 only in this version */
+  int precision;   /* fmpb_precision: FMPB_FP64 (default), FMPB_FP32 or FMPB_MIXED */
 } fmpb_operator_opts;
 
 typedef struct {
@@ -106,6 +111,7 @@ typedef struct {
   int64_t F;             /* P[0] P[1] P[2] */
   int32_t n_near;        /* near offsets stored (3^dim) in the FMM form, else 0 */
   size_t bytes_device;   /* device memory held by the operator (tables only) */
+  int32_t precision;     /* fmpb_precision of the stored spectrum(s) */
 } fmpb_operator_info;
 
 /*
@@ -159,21 +165,28 @@ typedef struct {
   int restart;       /* GMRES restart length m, 1..200; 0 selects 30 */
   int maxit;         /* total iteration cap per RHS; 0 selects 1000 */
   int timeout_ms;    /* wall-clock cap for the whole call; 0 = none */
+  double inner_tol;  /* MIXED operators: relative tolerance of each inner FP32
+                        GMRES solve; <= 0 selects 1e-4 */
 } fmpb_solve_opts;
 
 typedef struct {
-  int iters;            /* Arnoldi iterations used */
-  int converged;        /* 1 if the estimated residual met tol */
-  double relres_est;    /* residual estimate from the Givens recursion */
-  double relres_true;   /* ||b - A p|| / ||b|| recomputed with one product */
+  int iters;            /* Arnoldi iterations used (summed over inner solves) */
+  int converged;        /* 1 if the residual met tol */
+  double relres_est;    /* residual estimate (Givens recursion; outer residual for MIXED) */
+  double relres_true;   /* ||b - A p|| / ||b|| recomputed with the accurate operator */
+  int refinements;      /* outer refinement steps (MIXED operators), else 0 */
 } fmpb_solve_info;
 
 /*
  * Solves A p_r = b_r for R right-hand sides by restarted GMRES (Sec. 4)
- * with x0 = 0, no preconditioner, FP64 Arnoldi (two-pass classical
- * Gram-Schmidt) and Givens rotations, all vectors and the Hessenberg data on
- * the device; the host only sequences launches and reads one residual per
- * RHS per iteration.
+ * with x0 = 0 and no preconditioner.  Arnoldi: classical Gram-Schmidt with a
+ * second pass when the first removes more than half of ||w||^2, on a Krylov
+ * basis stored as float-float pairs (48-bit significands, FP32 pipe); Givens
+ * rotations, Hessenberg data, solution update and the true residual in FP64.
+ * All vectors live on the device; the host sequences launches and reads one
+ * convergence flag per RHS per iteration.  MIXED operators run GMRES-IR:
+ * FP32-spectrum inner solves to inner_tol, outer residuals with the accurate
+ * operator, until tol.
  *   b, p   device, R x N; p is overwritten.
  *   opts   may be NULL (defaults); info host, R entries, may be NULL.
  * Returns FMPB_ENOCONV if some RHS missed the tolerance within maxit (p

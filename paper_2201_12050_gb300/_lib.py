@@ -37,17 +37,17 @@ class OperatorInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("N", ctypes.c_int64), ("dim", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("n_t", ctypes.c_int32), ("B", ctypes.c_int64),
                 ("P", ctypes.c_int32 * 3), ("F", ctypes.c_int64), ("n_near", ctypes.c_int32),
-                ("bytes_device", ctypes.c_size_t)]
+                ("bytes_device", ctypes.c_size_t), ("precision", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("timeout_ms", ctypes.c_int)]
+                ("timeout_ms", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("relres_est", ctypes.c_double),
-                ("relres_true", ctypes.c_double)]
+                ("relres_true", ctypes.c_double), ("refinements", ctypes.c_int)]
 
 
 P = ctypes.c_void_p

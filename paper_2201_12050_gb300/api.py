@@ -12,6 +12,8 @@ from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, SolveOpts, S
 
 FORM_AUTO, FORM_FMM, FORM_PBEM = -1, 0, 1
 FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem"}
+FP64, FP32, MIXED = 0, 1, 3
+PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", MIXED: "mixed"}
 
 
 def _stream():
@@ -53,12 +55,12 @@ def _cvec(x, N, name):
 class Operator:
     """fmpb_operator: the tables of one (unit-cell mesh, lattice, k)."""
 
-    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0):
+    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64):
         self._lib = lib()
         v = _host(verts, np.float64)
         t = _host(tris, np.int32)
         self._lat = _lattice(counts, vectors)
-        opts = OperatorOpts(int(form), int(n_t), 0)
+        opts = OperatorOpts(int(form), int(n_t), int(precision))
         h = ctypes.c_void_p()
         check(self._lib.fmpb_operator_create(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(self._lat),
                                              float(k), ctypes.byref(opts), _stream(), ctypes.byref(h)))
@@ -68,6 +70,7 @@ class Operator:
         check(self._lib.fmpb_operator_get_info(self._h, ctypes.byref(info)))
         self.info = {f: (list(getattr(info, f)) if f == "P" else getattr(info, f)) for f, _ in info._fields_}
         self.info["form_name"] = FORM_NAMES[self.info["form"]]
+        self.info["precision_name"] = PRECISION_NAMES.get(self.info["precision"], "?")
         self.N = self.info["N"]
 
     def close(self):
@@ -101,15 +104,16 @@ class Operator:
         check(self._lib.fmpb_matvec(self._h, R, _ptr(x), _ptr(y), _stream()))
         return y
 
-    def solve(self, b, tol=1e-8, restart=30, maxit=1000, timeout_ms=0, out=None, raise_on_noconv=True):
+    def solve(self, b, tol=1e-8, restart=30, maxit=1000, timeout_ms=0, out=None, raise_on_noconv=True,
+              inner_tol=0.0):
         R = _cvec(b, self.N, "b")
         p = out if out is not None else torch.empty_like(b)
-        opts = SolveOpts(float(tol), int(restart), int(maxit), int(timeout_ms))
+        opts = SolveOpts(float(tol), int(restart), int(maxit), int(timeout_ms), float(inner_tol))
         infos = (SolveInfo * R)()
         st = self._lib.fmpb_solve(self._h, R, _ptr(b), _ptr(p), ctypes.byref(opts), ctypes.cast(infos, ctypes.c_void_p),
                                   _stream())
         info = [{"iters": i.iters, "converged": bool(i.converged), "relres_est": i.relres_est,
-                 "relres_true": i.relres_true} for i in infos]
+                 "relres_true": i.relres_true, "refinements": i.refinements} for i in infos]
         if st != 0 and (raise_on_noconv or st not in (-5, -6)):
             check(st)
         return p, info

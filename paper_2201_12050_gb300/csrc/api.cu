@@ -88,6 +88,8 @@ struct fmpb_operator {
   int64_t B = 0;
   int dim = 0;
   cd* spec = nullptr;      // F x B x B, float-float pairs (re_hi, re_lo, im_hi, im_lo) per entry
+  void* spec32 = nullptr;  // F x B x B complex FP32 (FP32 and MIXED operators)
+  int precision = FMPB_FP64;
   cd* S = nullptr;         // n_near x n x n (FMM form), float-float pairs
   int* near_offs = nullptr;
   int n_near = 0;
@@ -102,6 +104,7 @@ struct fmpb_operator {
     cudaDeviceSynchronize();
     free_mesh(mesh);
     cudaFree(spec);
+    cudaFree(spec32);
     cudaFree(S);
     cudaFree(near_offs);
     cudaFree(V0);
@@ -120,11 +123,15 @@ struct fmpb_operator {
     return FMPB_OK;
   }
 
-  fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st) {
+  // low: use the FP32 spectrum of a MIXED operator
+  fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st, bool low = false) {
     const int64_t Nc = shape.ncells;
+    const bool f32 = precision == FMPB_FP32 || (precision == FMPB_MIXED && low);
+    const cd* sp = f32 ? reinterpret_cast<const cd*>(spec32) : spec;
+    const int fmt = f32 ? SPEC_F32 : SPEC_FF;
     if (form == FMPB_FORM_PBEM) {
       FMPB_TRY(ensure_scratch(circulant_scratch_elems(shape, B, R)));
-      return circulant_apply(shape, B, spec, R, x, y, false, scratch, st, true);
+      return circulant_apply(shape, B, sp, R, x, y, false, scratch, st, fmt);
     }
     const size_t circ = circulant_scratch_elems(shape, B, R);
     const size_t mom = (size_t)R * Nc * B;
@@ -136,7 +143,7 @@ struct fmpb_operator {
     FMPB_TRY(vector_to_ff(x, xff, nvec, st));
     FMPB_TRY(near_apply(reinterpret_cast<const float4*>(S), near_offs, n_near, mesh.n, shape.M, R, xff, y, false, st));
     FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0), mesh.n, (int)B, (int64_t)R * Nc, xff, Mom, st));
-    FMPB_TRY(circulant_apply(shape, B, spec, R, Mom, Loc, false, scratch, st, true));
+    FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
     FMPB_TRY(l2p_apply(reinterpret_cast<const float4*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
     return FMPB_OK;
   }
@@ -176,7 +183,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(k > 0.0 && std::isfinite(k), "operator_create: wavenumber must be positive");
   fmpb_operator_opts o = opts ? *opts : fmpb_operator_opts{FMPB_FORM_AUTO, 0, FMPB_FP64};
   CHECK_ARG(o.form >= -1 && o.form <= 1, "operator_create: bad form %d", o.form);
-  CHECK_ARG(o.precision == FMPB_FP64, "operator_create: only FMPB_FP64 products in this version");
+  CHECK_ARG(o.precision == FMPB_FP64 || o.precision == FMPB_FP32 || o.precision == FMPB_MIXED,
+            "operator_create: precision must be FMPB_FP64, FMPB_FP32 or FMPB_MIXED");
   const int nt = o.n_t > 0 ? o.n_t : 8;
   CHECK_ARG(nt >= 1 && nt <= MAX_NT, "operator_create: n_t must be 1..%d", MAX_NT);
   cudaStream_t st = (cudaStream_t)stream;
@@ -277,6 +285,19 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec, st);   // leaves float-float pairs
     if (s != FMPB_OK) return fail(s);
   }
+  op->precision = o.precision;
+  if (o.precision != FMPB_FP64) {
+    const size_t ne = (size_t)sh.F * op->B * op->B;
+    s = dev_alloc(reinterpret_cast<float2**>(&op->spec32), ne, op->bytes);
+    if (s == FMPB_OK) s = spectrum_ff_to_f32(op->spec, op->spec32, ne, st);
+    if (s != FMPB_OK) return fail(s);
+    if (o.precision == FMPB_FP32) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "operator_create"));
+      cudaFree(op->spec);
+      op->spec = nullptr;
+      op->bytes -= sizeof(cd) * ne;
+    }
+  }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "operator_create"));
   *out = op;
@@ -296,6 +317,7 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->F = op->shape.F;
   info->n_near = op->n_near;
   info->bytes_device = op->bytes;
+  info->precision = op->precision;
   return FMPB_OK;
 }
 
@@ -320,10 +342,14 @@ fmpb_status fmpb_solve(const fmpb_operator* op, int R, const fmpb_c64* b, fmpb_c
   CHECK_ARG(op && b && p, "solve: NULL argument");
   CHECK_ARG(R >= 1 && R <= 4096, "solve: R out of range");
   CHECK_ARG((const void*)b != (const void*)p, "solve: b and p must not alias");
-  fmpb_solve_opts o = opts ? *opts : fmpb_solve_opts{0.0, 0, 0, 0};
+  fmpb_solve_opts o = opts ? *opts : fmpb_solve_opts{0.0, 0, 0, 0, 0.0};
   fmpb_operator* mop = const_cast<fmpb_operator*>(op);
   MatvecFn A = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st); };
   const int64_t N = (int64_t)op->mesh.n * op->shape.ncells;
+  if (op->precision == FMPB_MIXED) {
+    MatvecFn Alow = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st, true); };
+    return gmres_refined(A, Alow, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+  }
   return gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
 }
 

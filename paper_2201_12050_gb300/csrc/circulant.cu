@@ -278,6 +278,97 @@ static fmpb_status spectrum_from_ff(cd* spec, size_t n, cudaStream_t st) {
   return FMPB_OK;
 }
 
+// Y_f = Lambda_f X_f with Lambda_f in complex FP32 (mixed-precision operator):
+// X_f (float-float) is rounded to FP32 in shared memory, products and sums
+// are FP32, Y_f is written as float-float with a zero low part.  8-byte
+// spectrum entries halve the bytes streamed per product.
+template <int RC>
+__global__ void __launch_bounds__(256) k_block_product_f32(const float2* __restrict__ spec, const float4* __restrict__ X,
+                                                           float4* __restrict__ Y, int64_t B, int R, int r0,
+                                                           int rows_per_cta) {
+  extern __shared__ float2 xs2[];   // RC x B
+  const int64_t f = blockIdx.y;
+  const int64_t RB = (int64_t)R * B;
+  const float4* Xf = X + f * RB + (int64_t)r0 * B;
+  const int rc = min(RC, R - r0);
+  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) {
+    const float4 v = Xf[e];
+    xs2[e] = make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int64_t bend = min(B, (int64_t)(blockIdx.x + 1) * rows_per_cta);
+  for (int64_t b = (int64_t)blockIdx.x * rows_per_cta + warp; b < bend; b += nwarps) {
+    float re[RC], im[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) re[r] = im[r] = 0.f;
+    const float2* row = spec + (f * B + b) * B;
+    int64_t bp = lane;
+    for (; bp + 224 < B; bp += 256) {
+      float2 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcs(row + bp + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+          if (r < rc) {
+            const float2 x = xs2[r * B + bp + 32 * u];
+            re[r] = fmaf(a[u].x, x.x, fmaf(-a[u].y, x.y, re[r]));
+            im[r] = fmaf(a[u].x, x.y, fmaf(a[u].y, x.x, im[r]));
+          }
+    }
+    for (; bp < B; bp += 32) {
+      const float2 a = __ldcs(row + bp);
+#pragma unroll
+      for (int r = 0; r < RC; ++r)
+        if (r < rc) {
+          const float2 x = xs2[r * B + bp];
+          re[r] = fmaf(a.x, x.x, fmaf(-a.y, x.y, re[r]));
+          im[r] = fmaf(a.x, x.y, fmaf(a.y, x.x, im[r]));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+      for (int o = 16; o > 0; o >>= 1) {
+        re[r] += __shfl_xor_sync(0xffffffffu, re[r], o);
+        im[r] += __shfl_xor_sync(0xffffffffu, im[r], o);
+      }
+      if (lane == 0 && r < rc) Y[f * RB + (int64_t)(r0 + r) * B + b] = make_float4(re[r], 0.f, im[r], 0.f);
+    }
+  }
+}
+
+template <int RC>
+static fmpb_status launch_block_product_f32(const float2* spec, const float4* X, float4* Y, int64_t F, int64_t B,
+                                            int R, cudaStream_t st) {
+  const int threads = 256, rows = 32;
+  const size_t smem = (size_t)RC * B * sizeof(float2);
+  if (smem > 48 * 1024)
+    FMPB_CUDA(cudaFuncSetAttribute(k_block_product_f32<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
+  for (int r0 = 0; r0 < R; r0 += RC) {
+    FMPB_LAUNCH("block_product_f32", st, k_block_product_f32<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
+    FMPB_CUDA(cudaGetLastError());
+  }
+  return FMPB_OK;
+}
+
+// float-float spectrum (16 bytes per entry) -> complex FP32 (8 bytes)
+__global__ void k_ff_to_f32(const float4* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    out[i] = make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
+  }
+}
+
+fmpb_status spectrum_ff_to_f32(const cd* in, void* out, size_t n, cudaStream_t st) {
+  FMPB_LAUNCH("to_f32", st, k_ff_to_f32<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(reinterpret_cast<const float4*>(in), reinterpret_cast<float2*>(out), n));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 template <int RC, bool SPEC_FF>
 static fmpb_status launch_block_product(const void* spec, const float4* X, float4* Y, int64_t F, int64_t B, int R,
                                         cudaStream_t st) {
@@ -294,8 +385,8 @@ static fmpb_status launch_block_product(const void* spec, const float4* X, float
   return FMPB_OK;
 }
 
-static fmpb_status block_product(const void* spec, bool spec_ff, const float4* X, float4* Y, int64_t F, int64_t B,
-                                 int R, cudaStream_t st) {
+static fmpb_status block_product(const void* spec, int spec_format, const float4* X, float4* Y, int64_t F,
+                                 int64_t B, int R, cudaStream_t st) {
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
     return FMPB_EINVAL;
@@ -305,7 +396,13 @@ static fmpb_status block_product(const void* spec, bool spec_ff, const float4* X
     set_error("block_product: block size %lld too large", (long long)B);
     return FMPB_EINVAL;
   }
-  if (spec_ff) {
+  if (spec_format == SPEC_F32) {
+    const float2* sp = reinterpret_cast<const float2*>(spec);
+    if (RC == 4) return launch_block_product_f32<4>(sp, X, Y, F, B, R, st);
+    if (RC == 2) return launch_block_product_f32<2>(sp, X, Y, F, B, R, st);
+    return launch_block_product_f32<1>(sp, X, Y, F, B, R, st);
+  }
+  if (spec_format == SPEC_FF) {
     if (RC == 4) return launch_block_product<4, true>(spec, X, Y, F, B, R, st);
     if (RC == 2) return launch_block_product<2, true>(spec, X, Y, F, B, R, st);
     return launch_block_product<1, true>(spec, X, Y, F, B, R, st);
@@ -318,7 +415,7 @@ static fmpb_status block_product(const void* spec, bool spec_ff, const float4* X
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 * (size_t)s.F * R * B; }
 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
-                            bool accumulate, cd* scratch, cudaStream_t st, bool spec_ff) {
+                            bool accumulate, cd* scratch, cudaStream_t st, int spec_format) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
@@ -344,7 +441,7 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
     cur = 1 - cur;
   }
   // per-frequency block products: [f][r][b] -> [f][r][b]
-  FMPB_TRY(block_product(spec, spec_ff, buf[cur], buf[1 - cur], s.F, B, R, st));
+  FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st));
   cur = 1 - cur;
   // inverse z: [fz][fy fx][rb] -> [cz][fy fx][rb], cz < Mz
   if (Pz > 1) {

@@ -536,6 +536,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       info[r].converged = conv ? 1 : 0;
       info[r].relres_est = hest[r];
       info[r].relres_true = rel;
+      info[r].refinements = 0;
     }
   }
   if (timed_out) {
@@ -544,6 +545,159 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   }
   if (!all_conv) {
     set_error("gmres: tolerance %.3g not reached within %d iterations", tol, maxit);
+    return FMPB_ENOCONV;
+  }
+  return FMPB_OK;
+}
+
+}  // namespace fmpb
+
+namespace fmpb {
+
+// r = b - r for rhs not yet converged, r = 0 for converged ones
+__global__ void k_outer_residual(const cd* __restrict__ b, cd* __restrict__ r, const int* __restrict__ done, int R,
+                                 int64_t N, int from_product) {
+  const int rr = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = (int64_t)rr * N + i;
+    r[k] = done[rr] ? mkc(0.0, 0.0) : (from_product ? csub(b[k], r[k]) : b[k]);
+  }
+}
+
+__global__ void k_axpy(cd* __restrict__ x, const cd* __restrict__ d, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = cadd(x[i], d[i]);
+}
+
+__global__ void k_norm2_partial(const cd* __restrict__ v, int64_t N, double* __restrict__ out) {
+  const int r = blockIdx.y;
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const cd a = v[(int64_t)r * N + i];
+    acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(int64_t)r * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// Mixed-precision iterative refinement (GMRES-IR): the residual
+// r = b - A x is formed with the accurate operator, the correction equation
+// A_low d = r is solved by GMRES with the low-precision operator to the
+// relative tolerance inner_tol, and x += d, until ||r|| / ||b|| <= tol.
+fmpb_status gmres_refined(const MatvecFn& A, const MatvecFn& Alow, int R, int64_t N, const cd* b, cd* x,
+                          const fmpb_solve_opts& o, fmpb_solve_info* info, cudaStream_t st) {
+  const double tol = o.tol > 0 ? o.tol : 1e-8;
+  const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+  const int maxit = o.maxit > 0 ? o.maxit : 1000;
+  const int64_t total = (int64_t)R * N;
+  auto t0 = std::chrono::steady_clock::now();
+  cd *r = nullptr, *d = nullptr;
+  double* part = nullptr;
+  int* done = nullptr;
+  const unsigned nbk = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 64));
+  struct Free {
+    void* p[4];
+    ~Free() {
+      for (void* q : p)
+        if (q) cudaFree(q);
+    }
+  } fr{{nullptr, nullptr, nullptr, nullptr}};
+  if (cudaMalloc(&r, sizeof(cd) * total) != cudaSuccess || cudaMalloc(&d, sizeof(cd) * total) != cudaSuccess ||
+      cudaMalloc(&part, sizeof(double) * R * nbk) != cudaSuccess || cudaMalloc(&done, sizeof(int) * R) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("gmres_refined: cannot allocate work vectors");
+    return FMPB_ENOMEM;
+  }
+  fr.p[0] = r;
+  fr.p[1] = d;
+  fr.p[2] = part;
+  fr.p[3] = done;
+  const unsigned vb = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
+  std::vector<double> hp((size_t)R * nbk), bn(R), rn(R);
+  std::vector<int> hdone(R, 0), iters(R, 0);
+  auto norms = [&](const cd* v, std::vector<double>& out) -> fmpb_status {
+    FMPB_LAUNCH("norm2", st, k_norm2_partial<<<dim3(nbk, R), 256, 0, st>>>(v, N, part));
+    FMPB_CUDA(cudaGetLastError());
+    FMPB_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * R * nbk, cudaMemcpyDeviceToHost, st));
+    FMPB_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < R; ++q) {
+      double s = 0.0;
+      for (unsigned k = 0; k < nbk; ++k) s += hp[(size_t)q * nbk + k];
+      out[q] = sqrt(s);
+    }
+    return FMPB_OK;
+  };
+  FMPB_TRY(norms(b, bn));
+  for (int q = 0; q < R; ++q)
+    if (!std::isfinite(bn[q])) {
+      set_error("gmres_refined: the right-hand side holds NaN or Inf");
+      return FMPB_ENAN;
+    }
+  FMPB_CUDA(cudaMemsetAsync(x, 0, sizeof(cd) * total, st));
+  int refinements = 0, total_it = 0;
+  std::vector<double> rel(R, 1.0);
+  fmpb_status last = FMPB_OK;
+  for (int ref = 0;; ++ref) {
+    FMPB_CUDA(cudaMemcpyAsync(done, hdone.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+    if (ref > 0) FMPB_TRY(A(R, x, r, st));
+    FMPB_LAUNCH("outer_residual", st, k_outer_residual<<<dim3(vb, R), 256, 0, st>>>(b, r, done, R, N, ref > 0 ? 1 : 0));
+    FMPB_CUDA(cudaGetLastError());
+    FMPB_TRY(norms(r, rn));
+    bool all = true;
+    for (int q = 0; q < R; ++q) {
+      if (!hdone[q]) rel[q] = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
+      if (rel[q] <= tol) hdone[q] = 1;
+      all &= hdone[q] != 0;
+    }
+    if (all || total_it >= maxit) break;
+    if (o.timeout_ms > 0 &&
+        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+            o.timeout_ms) {
+      set_error("gmres_refined: wall-clock limit of %d ms reached", o.timeout_ms);
+      last = FMPB_ETIMEOUT;
+      break;
+    }
+    if (hdone != std::vector<int>(R, 0)) {
+      FMPB_CUDA(cudaMemcpyAsync(done, hdone.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+      FMPB_LAUNCH("outer_residual", st, k_outer_residual<<<dim3(vb, R), 256, 0, st>>>(r, r, done, R, N, 0));
+    }
+    fmpb_solve_opts inner = o;
+    inner.tol = inner_tol;
+    inner.maxit = maxit - total_it;
+    std::vector<fmpb_solve_info> ii(R);
+    fmpb_status s = gmres_solve(Alow, R, N, r, d, inner, ii.data(), st);
+    if (s != FMPB_OK && s != FMPB_ENOCONV && s != FMPB_ETIMEOUT) return s;
+    int it_max = 0;
+    for (int q = 0; q < R; ++q) {
+      iters[q] += ii[q].iters;
+      it_max = std::max(it_max, ii[q].iters);
+    }
+    total_it += std::max(1, it_max);
+    FMPB_LAUNCH("axpy", st, k_axpy<<<vb, 256, 0, st>>>(x, d, total));
+    FMPB_CUDA(cudaGetLastError());
+    ++refinements;
+  }
+  bool all_conv = true;
+  for (int q = 0; q < R; ++q) {
+    const bool conv = rel[q] <= tol;
+    all_conv &= conv;
+    if (info) {
+      info[q].iters = iters[q];
+      info[q].converged = conv ? 1 : 0;
+      info[q].relres_est = rel[q];
+      info[q].relres_true = rel[q];
+      info[q].refinements = refinements;
+    }
+  }
+  if (last != FMPB_OK) return last;
+  if (!all_conv) {
+    set_error("gmres_refined: tolerance %.3g not reached within %d inner iterations", tol, maxit);
     return FMPB_ENOCONV;
   }
   return FMPB_OK;

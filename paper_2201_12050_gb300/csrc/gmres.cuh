@@ -11,5 +11,8 @@ typedef std::function<fmpb_status(int R, const cd* x, cd* y, cudaStream_t st)> M
 
 fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
                         fmpb_solve_info* info, cudaStream_t st);
+// GMRES-IR: accurate residuals with A, corrections by GMRES with Alow.
+fmpb_status gmres_refined(const MatvecFn& A, const MatvecFn& Alow, int R, int64_t N, const cd* b, cd* x,
+                          const fmpb_solve_opts& o, fmpb_solve_info* info, cudaStream_t st);
 
 }  // namespace fmpb

@@ -84,9 +84,14 @@ fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R
 fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st);
 // y (+)= T x through pruned FFT, block product, pruned inverse FFT.
 // scratch: 2 * F * R * B complex values.
-// spec_ff: spectrum stored as float-float pairs (see spectrum_to_ff), else complex double.
+// Storage formats of a spectrum: complex double, float-float pairs (16 bytes,
+// FP64-class accuracy) or complex FP32 (8 bytes, the low-precision half of the
+// mixed-precision operator).
+enum SpecFormat { SPEC_CD = 0, SPEC_FF = 1, SPEC_F32 = 2 };
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
-                            bool accumulate, cd* scratch, cudaStream_t st, bool spec_ff = false);
+                            bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD);
+// float-float spectrum -> complex FP32 (out has n float2 entries)
+fmpb_status spectrum_ff_to_f32(const cd* in, void* out, size_t n, cudaStream_t st);
 // In-place conversion of n complex doubles to float-float pairs (re_hi, re_lo, im_hi, im_lo).
 fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st);
 // Out-of-place conversion of n complex doubles to float-float pairs.

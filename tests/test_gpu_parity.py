@@ -294,3 +294,42 @@ def test_sphere_array_full_size_sampled_rows():
                 loc += fmm.m2l_block(np.asarray(delta, dtype=float) @ L, k, nt) @ Mom[cj]
         ref = acc + U0[i] @ loc
         assert abs(y[c * n + i] - ref) <= 1e-11 * abs(ref), (c, i)
+
+
+# ---------------------------------------------------------- mixed precision ---
+
+def test_fp32_operator_products_and_mixed_refinement():
+    """FP32 spectrum: products within 1e-5 of the FP64 oracle; MIXED operator:
+    GMRES-IR (FP32 inner solves, accurate outer residuals) reaches the FP64
+    tolerance and the FP64 solution."""
+    v, t = icosphere(1, 0.2)
+    counts, lattice, k = (4, 3, 1), np.diag([0.5, 0.45, 1.0]), 4.0
+    x = random_complex_vectors(31, 2, int(np.prod(counts)) * len(t))
+    A = bem.dense_matrix(v, t, lattice, counts, k)
+    ref = x @ A.T
+    op32 = gb.Operator(v, t, counts, lattice, k, form=gb.FORM_PBEM, precision=gb.FP32)
+    assert op32.info["precision_name"] == "fp32"
+    y32 = op32.matvec(_dev(x)).cpu().numpy()
+    err32 = _rel(y32, ref)
+    assert 1e-9 < err32 < 1e-5
+    opm = gb.Operator(v, t, counts, lattice, k, form=gb.FORM_PBEM, precision=gb.MIXED)
+    ym = opm.matvec(_dev(x)).cpu().numpy()
+    assert _rel(ym, ref) < 1e-12              # MIXED products use the accurate spectrum
+    b = opm.rhs_plane_wave([[0.6, 0.8, 0.0]])
+    p, info = opm.solve(b, tol=1e-10, restart=30, inner_tol=1e-4)
+    assert info[0]["converged"] and info[0]["refinements"] >= 2 and info[0]["relres_true"] <= 1e-10
+    pref = np.linalg.solve(A, b.cpu().numpy()[0])
+    assert _rel(p.cpu().numpy()[0], pref) < 1e-8
+    p32, info32 = op32.solve(op32.rhs_plane_wave([[0.6, 0.8, 0.0]]), tol=1e-5, restart=30)
+    assert _rel(p32.cpu().numpy()[0], pref) < 1e-3
+
+
+def test_fmm_fp32_operator_products():
+    w = WORKLOADS["sphere_row_4"]
+    v, t = w.mesh()
+    k = w.wavenumbers[0]
+    op = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM, n_t=w.n_t, precision=gb.FP32)
+    x = random_complex_vectors(32, 1, op.N)
+    y = op.matvec(_dev(x)).cpu().numpy()
+    ref = fmm.fmm_matvec_explicit(bem.CellMesh(v, t), w.lattice, w.counts, k, w.n_t, x)
+    assert _rel(y, ref) < 1e-5
