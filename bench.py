@@ -274,13 +274,16 @@ def run_ours(args):
 
 
 def mixed_section(gb, torch, stream, args, w, v, t, sols, fp64_ms_per_step, world, rank):
-    """The same frequency steps with (a) the MIXED operator (FP32 + float-float
-    spectra, GMRES-IR to the same 1e-8 tolerance) and (b) the FP32 operator at
-    the paper's GMRES tolerance 1e-4.  Errors are relative L2 against the FP64
-    solution of the same step (which itself matches the FP64 oracle)."""
+    """The same frequency steps solved at equal accuracy by the plain FP64
+    operator and by the FP32-spectrum operator (both to relative residual
+    1e-5, about 1e-4 solution error on this crystal), plus the MIXED operator
+    (FP32 + float-float spectra, GMRES-IR to the headline 1e-8).  Errors are
+    relative L2 against the FP64 solution of the same step at 1e-8 (which is
+    itself checked against the FP64 oracle by the parity tests)."""
     ks, d, nf = w.wavenumbers, w.directions, len(w.wavenumbers)
     out = {}
-    for name, prec, tol in (("mixed_ir_tol1e-8", gb.MIXED, TOL), ("fp32_tol1e-4", gb.FP32, 1e-4)):
+    for name, prec, tol in (("fp64_tol1e-5", gb.FP64, 1e-5), ("fp32_tol1e-5", gb.FP32, 1e-5),
+                            ("mixed_ir_tol1e-8", gb.MIXED, TOL)):
         errs, iters, refs = [], [], []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
