@@ -59,6 +59,23 @@ def dist_env():
     return rank, world, local
 
 
+def frequency_index(step, world, rank, nf):
+    """Frequency of a step on a rank: the ranks of a replica run interleave the
+    sweep, so N ranks cover N different frequencies per step (weak scaling)."""
+    return (step * world + rank) % nf
+
+
+def reduce_max_ms(ms, world, device="cpu"):
+    """Slowest rank's time (the job's time) via an all-reduce MAX."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def config_block(w, extra=None):
     cfg = {
         "workload": "sonic_crystal_3x20: 3x20 rigid capped cylinders r=0.15 h=3.0, lattice 0.4 m, "
@@ -145,7 +162,7 @@ def run_ours(args):
     nf = len(ks)
 
     def step(i):
-        k = ks[(i * world + rank) % nf]
+        k = ks[frequency_index(i, world, rank, nf)]
         op = gb.Operator(v, t, w.counts, w.lattice, k)
         b = op.rhs_plane_wave(d)
         p, info = op.solve(b, tol=TOL, restart=RESTART, maxit=MAXIT, raise_on_noconv=False)
@@ -175,7 +192,7 @@ def run_ours(args):
         iters.append(info[0]["iters"])
         relres.append(info[0]["relres_true"])
         conv.append(info[0]["converged"])
-        sols[(args.warmup + i) * world + rank] = p
+        sols[frequency_index(args.warmup + i, world, rank, nf)] = p
         op.close()
     e1.record(stream)
     barrier()
@@ -184,11 +201,7 @@ def run_ours(args):
     launches = gb.kernel_launches() - launches0
     prof = gb.profile_summary()
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max_ms(ms, world, "cuda")
     value = args.steps * world / (ms / 1e3)
 
     # product throughput on one operator (100 Hz), and the block-product roofline
@@ -225,7 +238,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     h2d = d2h = 0
     for i in range(e2e_steps):
-        k = ks[(i * world + rank) % nf]
+        k = ks[frequency_index(i, world, rank, nf)]
         op2 = gb.Operator(v, t, w.counts, w.lattice, k)
         b = op2.rhs_plane_wave(d)
         p, info = op2.solve(b, tol=TOL, restart=RESTART, maxit=MAXIT, raise_on_noconv=False)
@@ -289,8 +302,8 @@ def mixed_section(gb, torch, stream, args, w, v, t, sols, fp64_ms_per_step, worl
         torch.cuda.synchronize()
         e0.record(stream)
         for i in range(args.steps):
-            key = (args.warmup + i) * world + rank
-            op = gb.Operator(v, t, w.counts, w.lattice, ks[key % nf], precision=prec)
+            key = frequency_index(args.warmup + i, world, rank, nf)
+            op = gb.Operator(v, t, w.counts, w.lattice, ks[key], precision=prec)
             b = op.rhs_plane_wave(d)
             p, info = op.solve(b, tol=tol, restart=RESTART, maxit=MAXIT, raise_on_noconv=False, inner_tol=1e-4)
             ref = sols[key]
