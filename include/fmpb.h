@@ -293,6 +293,79 @@ fmpb_status fmpb_circulant_apply_static(const int32_t counts[3], int64_t B, cons
                                         const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Serving: a request loop over many (mesh, lattice, k) problems.
+ *
+ * Requests (a unit-cell mesh, a lattice, a wavenumber and R incident plane
+ * waves) are queued and served by two worker threads, each with its own
+ * CUDA stream, so that batches overlap on the device.  Operators are kept
+ * resident per (mesh, lattice, k, form, precision) in a cache with LRU
+ * eviction.  A request is admitted when its operator and solve workspace fit
+ * in the HBM budget (after evicting idle operators).  Queued requests that
+ * share an operator are merged into one multi-RHS solve (continuous
+ * batching: new arrivals join the next batch while others run).  Each RHS
+ * runs its own Krylov iteration, so a result does not depend on what else
+ * was batched with it.  The paper has no serving layer; this is the systems
+ * pattern around its solver.
+ * ---------------------------------------------------------------------- */
+typedef struct fmpb_server fmpb_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* 0 = 80% of the device memory free at creation */
+  int max_batch_rhs;         /* right-hand sides merged into one solve; 0 = 64 */
+  int cache_entries;         /* resident operators kept; 0 = 8 */
+  int precision;             /* fmpb_precision of the operators the server builds */
+  double tol;                /* GMRES relative tolerance; <= 0 selects 1e-8 */
+  int restart;               /* GMRES restart; 0 = 200 */
+  int maxit;                 /* iteration cap; 0 = 3000 */
+} fmpb_server_opts;
+
+typedef struct {
+  const double *verts;       /* host, nv x 3, copied at submit */
+  int64_t nv;
+  const int32_t *tris;       /* host, ntri x 3, copied at submit */
+  int64_t ntri;
+  fmpb_lattice lattice;
+  double k;
+  int form;                  /* fmpb_form */
+  int n_t;                   /* FMM truncation number; 0 = 8 */
+  int R;                     /* plane waves, 1..64 */
+  const double *dirs;        /* host, R x 3 unit vectors, copied at submit */
+  const fmpb_c64 *amps;      /* host, R amplitudes or NULL (all 1), copied at submit */
+} fmpb_request;
+
+typedef struct {
+  fmpb_status status;        /* of this request only */
+  int R;
+  int iters_max;             /* largest GMRES iteration count among its RHS */
+  double relres_true_max;    /* largest true relative residual among its RHS */
+  int cache_hit;             /* 1 if its operator was resident when it started */
+  int batched_with;          /* requests in the same solve, itself included */
+  double queue_ms, build_ms, solve_ms, latency_ms;   /* submit -> completion */
+} fmpb_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, cache_hits, batches;
+  double p50_ms, p99_ms, mean_ms;         /* latency over completed requests */
+  double solves_per_s;                    /* completed requests / (last completion - first submit) */
+  size_t hbm_in_use, hbm_high_water;      /* resident operators + running workspaces */
+} fmpb_server_stats;
+
+/* Creates the server on the current device.  opts may be NULL. */
+fmpb_status fmpb_server_create(const fmpb_server_opts *opts, fmpb_server **out);
+/*
+ * Queues a request.  p_out (host, R x N complex, N = ntri * cells) receives
+ * the surface pressure; it must stay valid until fmpb_server_wait returns for
+ * this ticket.  Returns at once; EINVAL on malformed requests.
+ */
+fmpb_status fmpb_server_submit(fmpb_server *srv, const fmpb_request *req, fmpb_c64 *p_out, uint64_t *ticket);
+/* Waits (bounded by timeout_ms; <= 0 waits without limit) for a ticket and
+ * fills *res.  ETIMEOUT if still running.  A ticket can be waited once. */
+fmpb_status fmpb_server_wait(fmpb_server *srv, uint64_t ticket, int timeout_ms, fmpb_result *res);
+fmpb_status fmpb_server_get_stats(fmpb_server *srv, fmpb_server_stats *stats);
+/* Finishes queued work, stops the workers, frees every cached operator. */
+void fmpb_server_destroy(fmpb_server *srv);
+
+/* ------------------------------------------------------------------------
  * Telemetry (no counterpart in the paper; it reports wall-clock times of
  * assembly and products only, Sec. 4).
  * ---------------------------------------------------------------------- */

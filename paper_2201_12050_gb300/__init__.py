@@ -7,11 +7,11 @@ Every step runs in the CUDA library ``libfmpb.so`` (C ABI in
 device memory and streams.
 """
 from ._lib import FmpbError, FmpbLibraryMissing, lib
-from .api import (Operator, build_blocks, multipole_tables, m2l_blocks, circulant_shape,
+from .api import (Operator, Server, build_blocks, multipole_tables, m2l_blocks, circulant_shape,
                   circulant_spectrum, circulant_apply, kernel_launches, profile_enable, profile_reset,
                   profile_summary, FORM_AUTO, FORM_FMM, FORM_PBEM, FP64, FP32, MIXED)
 
-__all__ = ["Operator", "build_blocks", "multipole_tables", "m2l_blocks", "circulant_shape",
+__all__ = ["Operator", "Server", "build_blocks", "multipole_tables", "m2l_blocks", "circulant_shape",
            "circulant_spectrum", "circulant_apply", "kernel_launches", "profile_enable",
            "profile_reset", "profile_summary", "FmpbError", "FmpbLibraryMissing", "lib",
            "FORM_AUTO", "FORM_FMM", "FORM_PBEM", "FP64", "FP32", "MIXED"]

@@ -50,6 +50,31 @@ class SolveInfo(ctypes.Structure):
                 ("relres_true", ctypes.c_double), ("refinements", ctypes.c_int)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_rhs", ctypes.c_int), ("cache_entries", ctypes.c_int),
+                ("precision", ctypes.c_int), ("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("nv", ctypes.c_int64), ("tris", ctypes.c_void_p), ("ntri", ctypes.c_int64),
+                ("lattice", Lattice), ("k", ctypes.c_double), ("form", ctypes.c_int), ("n_t", ctypes.c_int),
+                ("R", ctypes.c_int), ("dirs", ctypes.c_void_p), ("amps", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("R", ctypes.c_int), ("iters_max", ctypes.c_int),
+                ("relres_true_max", ctypes.c_double), ("cache_hit", ctypes.c_int), ("batched_with", ctypes.c_int),
+                ("queue_ms", ctypes.c_double), ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cache_hits", ctypes.c_int64), ("batches", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
+                ("hbm_in_use", ctypes.c_size_t), ("hbm_high_water", ctypes.c_size_t)]
+
+
 P = ctypes.c_void_p
 I32 = ctypes.c_int32
 I64 = ctypes.c_int64
@@ -75,6 +100,11 @@ SIGNATURES = {
     "fmpb_circulant_spectrum": (INT, [P, I64, P, P, P]),
     "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_apply_static": (INT, [P, I64, P, INT, P, P, INT, P]),
+    "fmpb_server_create": (INT, [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]),
+    "fmpb_server_submit": (INT, [P, ctypes.POINTER(Request), P, ctypes.POINTER(ctypes.c_uint64)]),
+    "fmpb_server_wait": (INT, [P, ctypes.c_uint64, INT, ctypes.POINTER(Result)]),
+    "fmpb_server_get_stats": (INT, [P, ctypes.POINTER(ServerStats)]),
+    "fmpb_server_destroy": (None, [P]),
     "fmpb_kernel_launches": (ctypes.c_uint64, []),
     "fmpb_profile_enable": (None, [INT]),
     "fmpb_profile_reset": (INT, []),

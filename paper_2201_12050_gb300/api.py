@@ -8,7 +8,8 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, SolveOpts, SolveInfo, FmpbError)
+from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, SolveOpts, SolveInfo, FmpbError, ServerOpts,
+                   Request, Result, ServerStats, STATUS)
 
 FORM_AUTO, FORM_FMM, FORM_PBEM = -1, 0, 1
 FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem"}
@@ -213,3 +214,64 @@ def profile_summary() -> dict:
     buf = ctypes.create_string_buffer(1 << 16)
     check(lib().fmpb_profile_summary(buf, len(buf)))
     return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+class Server:
+    """fmpb_server: queued solves of many (mesh, lattice, k) problems."""
+
+    def __init__(self, hbm_budget_bytes=0, max_batch_rhs=64, cache_entries=8, precision=FP64, tol=1e-8,
+                 restart=200, maxit=3000):
+        self._lib = lib()
+        o = ServerOpts(int(hbm_budget_bytes), int(max_batch_rhs), int(cache_entries), int(precision), float(tol),
+                       int(restart), int(maxit))
+        h = ctypes.c_void_p()
+        check(self._lib.fmpb_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._pending = {}
+
+    def submit(self, verts, tris, counts, vectors, k, dirs, amps=None, form=FORM_AUTO, n_t=0):
+        """Queues a request; returns a ticket.  The result array is kept alive here."""
+        v = _host(verts, np.float64)
+        t = _host(tris, np.int32)
+        d = _host(dirs, np.float64).reshape(-1, 3)
+        R = len(d)
+        a = None if amps is None else _host(np.asarray(amps, dtype=np.complex128).reshape(R), np.complex128)
+        ncell = int(np.prod(list(counts) + [1] * (3 - len(counts))))
+        out = np.zeros((R, len(t) * ncell), dtype=np.complex128)
+        req = Request(_ptr(v), len(v), _ptr(t), len(t), _lattice(counts, vectors), float(k), int(form), int(n_t), R,
+                      _ptr(d), None if a is None else _ptr(a))
+        tk = ctypes.c_uint64()
+        check(self._lib.fmpb_server_submit(self._h, ctypes.byref(req), _ptr(out), ctypes.byref(tk)))
+        self._pending[tk.value] = (out, v, t, d, a)
+        return tk.value
+
+    def wait(self, ticket, timeout_ms=0):
+        """(result dict, surface pressure R x N numpy array)."""
+        r = Result()
+        check(self._lib.fmpb_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r)))
+        out = self._pending.pop(ticket)[0]
+        res = {f: getattr(r, f) for f, _ in r._fields_}
+        res["status_name"] = STATUS.get(res["status"], str(res["status"]))
+        return res, out
+
+    def stats(self):
+        s = ServerStats()
+        check(self._lib.fmpb_server_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmpb_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

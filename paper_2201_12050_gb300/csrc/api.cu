@@ -75,6 +75,81 @@ static fmpb_status dev_alloc(T** p, size_t count, size_t& bytes) {
 
 }  // namespace fmpb
 
+
+namespace fmpb {
+
+// Offsets of the (2M-1)^d block Toeplitz pattern (delta_x fastest) split into
+// near (|delta|_inf <= 1) and far, and the form to build: AUTO picks FMM when
+// the nearest far translation is at least 3 cell radii (two-centre expansion
+// ratio 2 rho / |d| <= 2/3), else PBEM; FMM forced with |d| <= 2 rho is refused.
+fmpb_status decide_form(const CellGrid& g, double rho, int requested, int* form, std::vector<int32_t>* all_off,
+                        std::vector<int32_t>* near_off, std::vector<int32_t>* far_off) {
+  double dmin = 1e300;
+  for (int dz = 1 - g.M[2]; dz < g.M[2]; ++dz)
+    for (int dy = 1 - g.M[1]; dy < g.M[1]; ++dy)
+      for (int dx = 1 - g.M[0]; dx < g.M[0]; ++dx) {
+        const int32_t dl[3] = {dx, dy, dz};
+        const bool near = abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1;
+        if (all_off) all_off->insert(all_off->end(), dl, dl + 3);
+        std::vector<int32_t>* dst = near ? near_off : far_off;
+        if (dst) dst->insert(dst->end(), dl, dl + 3);
+        if (!near) {
+          double d2 = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            const double v = dx * g.L[0][c] + dy * g.L[1][c] + dz * g.L[2][c];
+            d2 += v * v;
+          }
+          dmin = fmin(dmin, sqrt(d2));
+        }
+      }
+  int f = requested;
+  if (f == FMPB_FORM_AUTO) f = (dmin >= 3.0 * rho) ? FMPB_FORM_FMM : FMPB_FORM_PBEM;
+  if (f == FMPB_FORM_FMM && !(dmin > 2.0 * rho)) {
+    set_error("operator_create: FMM form not admissible (nearest far cell at %.4g, cell radius %.4g)", dmin, rho);
+    return FMPB_EADMISS;
+  }
+  *form = f;
+  return FMPB_OK;
+}
+
+// Form, circulant block size and spectrum length, and the device bytes an
+// operator will hold, computed on the host without building it (admission).
+fmpb_status plan_operator(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                          const fmpb_lattice* lattice, const fmpb_operator_opts* opts, int* form, int64_t* B,
+                          int64_t* F, size_t* bytes) {
+  CellGrid g;
+  FMPB_TRY(make_grid(lattice, g));
+  double rho = 0.0;
+  for (int64_t t = 0; t < 3 * ntri; ++t) {
+    const int32_t v = tris[t];
+    if (v < 0 || v >= nv) {
+      set_error("plan: triangle index out of range");
+      return FMPB_EMESH;
+    }
+    const double* p = verts + 3 * v;
+    rho = fmax(rho, sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]));
+  }
+  FMPB_TRY(decide_form(g, rho, opts->form, form, nullptr, nullptr, nullptr));
+  const CircShape sh = make_shape(g.M);
+  const int nt = opts->n_t > 0 ? opts->n_t : 8;
+  const int64_t n = ntri;
+  const int64_t b = *form == FMPB_FORM_PBEM ? n : (int64_t)(nt + 1) * (nt + 1);
+  const int dim = (g.M[0] > 1) + (g.M[1] > 1) + (g.M[2] > 1);
+  int nnear = 1;
+  for (int i = 0; i < dim; ++i) nnear *= 3;
+  size_t per = 16;   // float-float spectrum
+  if (opts->precision == FMPB_FP32) per = 8;
+  if (opts->precision == FMPB_MIXED) per = 24;
+  size_t total = per * (size_t)sh.F * b * b;
+  if (*form == FMPB_FORM_FMM) total += 16 * ((size_t)nnear * n * n + 2 * (size_t)b * n);
+  *B = b;
+  *F = sh.F;
+  *bytes = total;
+  return FMPB_OK;
+}
+
+}  // namespace fmpb
+
 using namespace fmpb;
 
 struct fmpb_operator {
@@ -207,33 +282,10 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   const CircShape& sh = op->shape;
   op->dim = (sh.M[0] > 1) + (sh.M[1] > 1) + (sh.M[2] > 1);
   const int n = op->mesh.n;
-  // admissibility of the cell-as-box FMM: every far translation must exceed
-  // three cell radii (two-centre convergence ratio 2 rho / |d| <= 2/3)
-  double dmin = 1e300;
   std::vector<int32_t> all_off, far_off, near_off;
-  for (int dz = 1 - sh.M[2]; dz < sh.M[2]; ++dz)
-    for (int dy = 1 - sh.M[1]; dy < sh.M[1]; ++dy)
-      for (int dx = 1 - sh.M[0]; dx < sh.M[0]; ++dx) {
-        int32_t dl[3] = {dx, dy, dz};
-        all_off.insert(all_off.end(), dl, dl + 3);
-        bool near = abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1;
-        (near ? near_off : far_off).insert((near ? near_off : far_off).end(), dl, dl + 3);
-        if (!near) {
-          double d2 = 0.0;
-          for (int c = 0; c < 3; ++c) {
-            double v = dx * op->grid.L[0][c] + dy * op->grid.L[1][c] + dz * op->grid.L[2][c];
-            d2 += v * v;
-          }
-          dmin = fmin(dmin, sqrt(d2));
-        }
-      }
-  const double rho = op->mesh.radius;
-  int form = o.form;
-  if (form == FMPB_FORM_AUTO) form = (dmin >= 3.0 * rho) ? FMPB_FORM_FMM : FMPB_FORM_PBEM;
-  if (form == FMPB_FORM_FMM && !(dmin > 2.0 * rho)) {
-    set_error("operator_create: FMM form not admissible (nearest far cell at %.4g, cell radius %.4g)", dmin, rho);
-    return fail(FMPB_EADMISS);
-  }
+  int form = 0;
+  s = decide_form(op->grid, op->mesh.radius, o.form, &form, &all_off, &near_off, &far_off);
+  if (s != FMPB_OK) return fail(s);
   op->form = form;
   if (form == FMPB_FORM_PBEM) {
     op->B = n;

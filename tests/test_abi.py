@@ -53,3 +53,14 @@ def test_argument_errors_are_statuses_not_crashes(L):
     assert st == -1 and b"wavenumber" in L.fmpb_last_error()
     assert L.fmpb_matvec(None, 1, None, None, None) == -1
     L.fmpb_operator_destroy(None)
+
+
+def test_server_reports_missing_device_as_status(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    from paper_2201_12050_gb300._lib import ServerOpts
+    h = ctypes.c_void_p()
+    st = L.fmpb_server_create(ctypes.byref(ServerOpts()), ctypes.byref(h))
+    assert st in (-8, -2) and not h.value
+    assert L.fmpb_server_submit(None, None, None, None) == -1
