@@ -257,6 +257,7 @@ def run_ours(args):
     roof = dominant_roofline(dom, prof, w, v, t, args.steps, hbm_peak, peaks, bp_gbs)
 
     fmm = fmm_section(gb, torch, stream) if rank == 0 else None
+    serving = serving_section(gb) if rank == 0 else None
     mixed = mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
 
     out = {
@@ -276,6 +277,7 @@ def run_ours(args):
                      "bytes_device": info_op["bytes_device"]},
         "fmm_workload": fmm,
         "mixed": mixed,
+        "serving": serving,
     }
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, v, t, iters)
@@ -284,6 +286,38 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serving_section(gb, n_sample=24):
+    """The serving loop on a bounded sample of the seeded request stream
+    (Poisson arrivals at 50 req/s, grids 4x4..64x8, 100-2000 Hz, 1-16 plane
+    waves): the first n_sample sphere-cell requests, submitted at their arrival
+    times.  Sphere cells use the FMM form with n_t = ceil(1.5 k rho) + 4."""
+    from workloads import serving_stream, icosphere
+    sv, stri = icosphere(2, 0.2)
+    reqs = [r for r in serving_stream(400) if r["cell"] == "sphere"][:n_sample]
+    t0 = time.perf_counter()
+    with gb.Server(max_batch_rhs=64, tol=TOL, restart=RESTART, maxit=MAXIT) as srv:
+        tickets = []
+        base = reqs[0]["t"]
+        for r in reqs:
+            delay = (r["t"] - base) - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            nt = int(min(20, max(6, math.ceil(1.5 * r["k"] * 0.2) + 4)))
+            tickets.append(srv.submit(sv, stri, r["counts"], r["lattice"], r["k"], r["dirs"], form=gb.FORM_FMM,
+                                      n_t=nt))
+        results = [srv.wait(tk)[0] for tk in tickets]
+        st = srv.stats()
+    wall = time.perf_counter() - t0
+    ok = [x for x in results if x["status_name"] == "FMPB_OK"]
+    return {"sample": f"first {n_sample} sphere-cell requests of the seeded 50 req/s stream",
+            "offered_req_per_s": (len(reqs) - 1) / (reqs[-1]["t"] - base) if len(reqs) > 1 else None,
+            "achieved_solves_per_s": len(ok) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "completed": st["completed"], "failed": st["failed"],
+            "batches": st["batches"], "cache_hits": st["cache_hits"],
+            "hbm_high_water_bytes": st["hbm_high_water"],
+            "iters_max": max(x["iters_max"] for x in results), "relres_true_max": max(x["relres_true_max"] for x in results)}
 
 
 def mixed_section(gb, torch, stream, args, w, v, t, sols, fp64_ms_per_step, world, rank):

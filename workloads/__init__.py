@@ -8,10 +8,10 @@ inputs without sharing any of the method's code.
 """
 from .meshes import icosphere, capped_cylinder, cube, mesh_signed_volume
 from .rng import PCG32, random_complex_vectors
-from .configs import WORKLOADS, Workload, fibonacci_directions, SPEED_OF_SOUND
+from .configs import WORKLOADS, Workload, fibonacci_directions, SPEED_OF_SOUND, serving_stream
 
 __all__ = [
     "icosphere", "capped_cylinder", "cube", "mesh_signed_volume",
     "PCG32", "random_complex_vectors",
-    "WORKLOADS", "Workload", "fibonacci_directions", "SPEED_OF_SOUND",
+    "WORKLOADS", "Workload", "fibonacci_directions", "SPEED_OF_SOUND", "serving_stream",
 ]

@@ -99,3 +99,30 @@ WORKLOADS = {
         notes="16x16x4 rigid cubes edge 0.3 m in 0.5 m cells, 432 triangles per cell, N=442,368",
     ),
 }
+
+
+def serving_stream(n_requests: int, seed: int = _SEED + 4, rate_hz: float = 50.0):
+    """Seeded request stream of the serving workload: Poisson arrivals at
+    rate_hz, cell grids uniform from 4x4 to 64x8 of the capped-cylinder cell
+    or the sphere cell, frequencies uniform in 100-2000 Hz, 1-16 incident
+    plane waves with directions uniform on the sphere.  Returns a list of dicts
+    (arrival time s, cell name, counts, lattice, k, directions)."""
+    from .rng import PCG32
+    g = PCG32(seed)
+    u = lambda: g.uniform(1)[0]
+    out, t = [], 0.0
+    for _ in range(n_requests):
+        t += -np.log(1.0 - u()) / rate_hz
+        cell = "cylinder" if u() < 0.5 else "sphere"
+        mx = 4 + int(u() * 61)
+        my = 4 + int(u() * 5)
+        f = 100.0 + 1900.0 * u()
+        R = 1 + int(u() * 16)
+        z = 2.0 * g.uniform(R) - 1.0
+        ph = 2.0 * np.pi * g.uniform(R)
+        rho = np.sqrt(1.0 - z * z)
+        dirs = np.stack([rho * np.cos(ph), rho * np.sin(ph), z], axis=1)
+        lattice = np.diag([0.4, 0.4, 3.0]) if cell == "cylinder" else np.diag([1.0, 1.0, 1.0])
+        out.append({"t": t, "cell": cell, "counts": (mx, my, 1), "lattice": lattice,
+                    "k": 2.0 * np.pi * f / SPEED_OF_SOUND, "freq_hz": f, "dirs": dirs})
+    return out
