@@ -215,6 +215,16 @@ struct fmpb_operator {
     cd* Mom = scratch + circ;
     cd* Loc = Mom + mom;
     float4* xff = reinterpret_cast<float4*>(Loc + mom);
+    if (precision == FMPB_FP32) {
+      float2* x32 = reinterpret_cast<float2*>(Loc + mom);
+      FMPB_TRY(vector_to_f32(x, x32, nvec, st));
+      FMPB_TRY(near_apply_f32(reinterpret_cast<const float2*>(S), near_offs, n_near, mesh.n, shape.M, R, x32, y, false,
+                              st));
+      FMPB_TRY(p2m_apply_f32(reinterpret_cast<const float2*>(V0), mesh.n, (int)B, (int64_t)R * Nc, x32, Mom, st));
+      FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
+      FMPB_TRY(l2p_apply_f32(reinterpret_cast<const float2*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
+      return FMPB_OK;
+    }
     FMPB_TRY(vector_to_ff(x, xff, nvec, st));
     FMPB_TRY(near_apply(reinterpret_cast<const float4*>(S), near_offs, n_near, mesh.n, shape.M, R, xff, y, false, st));
     FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0), mesh.n, (int)B, (int64_t)R * Nc, xff, Mom, st));
@@ -319,10 +329,28 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     for (int i = 0; i < op->n_near; ++i) dnear[i] = i;
     s = build_blocks(op->mesh, op->grid, k, op->n_near, near_off.data(), dnear.data(), op->S, st);
     if (s == FMPB_OK) s = multipole_tables(op->mesh, k, nt, op->V0, op->U0, st);
-    // the products read the near blocks and the P2M/L2P tables as float-float pairs
-    if (s == FMPB_OK) s = spectrum_to_ff(op->S, (size_t)op->n_near * n * n, st);
-    if (s == FMPB_OK) s = spectrum_to_ff(op->V0, (size_t)B * n, st);
-    if (s == FMPB_OK) s = spectrum_to_ff(op->U0, (size_t)B * n, st);
+    // the products read the near blocks and the P2M/L2P tables as float-float
+    // pairs, or as complex FP32 for FP32 operators (8 bytes per entry)
+    if (o.precision == FMPB_FP32) {
+      for (cd** t : {&op->S, &op->V0, &op->U0}) {
+        const size_t ne = (t == &op->S) ? (size_t)op->n_near * n * n : (size_t)B * n;
+        float2* f32 = nullptr;
+        if (s == FMPB_OK) s = dev_alloc(&f32, ne, op->bytes);
+        if (s == FMPB_OK) s = vector_to_f32(*t, f32, ne, st);
+        if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tables");
+        if (s == FMPB_OK) {
+          cudaFree(*t);
+          op->bytes -= sizeof(cd) * ne;
+          *t = reinterpret_cast<cd*>(f32);
+        } else if (f32) {
+          cudaFree(f32);
+        }
+      }
+    } else {
+      if (s == FMPB_OK) s = spectrum_to_ff(op->S, (size_t)op->n_near * n * n, st);
+      if (s == FMPB_OK) s = spectrum_to_ff(op->V0, (size_t)B * n, st);
+      if (s == FMPB_OK) s = spectrum_to_ff(op->U0, (size_t)B * n, st);
+    }
     if (s != FMPB_OK) return fail(s);
     const int n_far = (int)(far_off.size() / 3);
     std::vector<double> dvec(3 * (size_t)n_far);

@@ -266,6 +266,17 @@ __global__ void k_vec_to_ff(const cd* __restrict__ x, float4* __restrict__ y, si
     y[i] = split_ff(x[i]);
 }
 
+__global__ void k_vec_to_f32(const cd* __restrict__ x, float2* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
+fmpb_status vector_to_f32(const cd* x, float2* y, size_t n, cudaStream_t st) {
+  FMPB_LAUNCH("to_f32", st, k_vec_to_f32<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(x, y, n));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 fmpb_status vector_to_ff(const cd* x, float4* y, size_t n, cudaStream_t st) {
   FMPB_LAUNCH("to_ff", st, k_vec_to_ff<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(x, y, n));
   FMPB_CUDA(cudaGetLastError());
@@ -385,12 +396,110 @@ static fmpb_status launch_block_product(const void* spec, const float4* X, float
   return FMPB_OK;
 }
 
+// Many right-hand sides: Y_f[r][b] = sum_k X_f[r][k] Lambda_f[b][k] as a
+// tiled GEMM per frequency.  A CTA owns 32 rows b x 32 right-hand sides r and
+// walks k in slices of 16 through shared memory; each thread accumulates 2 x 2
+// outputs.  The r-tile index is the fastest grid dimension, so the CTAs that
+// share a spectrum tile run together and reuse it from L2.  FF: float-float
+// spectrum and arithmetic; otherwise complex FP32 spectrum and FP32 FMAs.
+constexpr int BPT_B = 32, BPT_R = 32, BPT_K = 16;
+template <bool FF>
+__global__ void __launch_bounds__(256) k_block_product_tiled(const void* __restrict__ spec_,
+                                                             const float4* __restrict__ X, float4* __restrict__ Y,
+                                                             int64_t B, int R) {
+  __shared__ float4 Ls[BPT_B][BPT_K + 1];
+  __shared__ float4 Xs[BPT_K][BPT_R + 1];
+  const int64_t f = blockIdx.y;
+  const int r0 = blockIdx.x * BPT_R;
+  const int64_t b0 = (int64_t)blockIdx.z * BPT_B;
+  const int64_t RB = (int64_t)R * B;
+  const float4* Xf = X + f * RB;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float rh[2][2], rl[2][2], ih[2][2], il[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) rh[a][b] = rl[a][b] = ih[a][b] = il[a][b] = 0.f;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t k0 = 0; k0 < B; k0 += BPT_K) {
+    for (int e = threadIdx.x; e < BPT_B * BPT_K; e += blockDim.x) {
+      const int bb = e / BPT_K, kk = e - bb * BPT_K;
+      const int64_t b = b0 + bb, k = k0 + kk;
+      float4 v = zero;
+      if (b < B && k < B) {
+        const int64_t idx = (f * B + b) * B + k;
+        if (FF) {
+          v = __ldcs(reinterpret_cast<const float4*>(spec_) + idx);
+        } else {
+          const float2 s = __ldcs(reinterpret_cast<const float2*>(spec_) + idx);
+          v = make_float4(s.x, 0.f, s.y, 0.f);
+        }
+      }
+      Ls[bb][kk] = v;
+    }
+    for (int e = threadIdx.x; e < BPT_R * BPT_K; e += blockDim.x) {
+      const int rr = e / BPT_K, kk = e - rr * BPT_K;
+      const int r = r0 + rr;
+      const int64_t k = k0 + kk;
+      Xs[kk][rr] = (r < R && k < B) ? Xf[(int64_t)r * B + k] : zero;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BPT_K; ++kk) {
+      const float4 l0 = Ls[ty][kk], l1 = Ls[ty + 16][kk];
+      const float4 x0 = Xs[kk][tx], x1 = Xs[kk][tx + 16];
+      if (FF) {
+        ff_cmac(l0, x0, rh[0][0], rl[0][0], ih[0][0], il[0][0]);
+        ff_cmac(l0, x1, rh[0][1], rl[0][1], ih[0][1], il[0][1]);
+        ff_cmac(l1, x0, rh[1][0], rl[1][0], ih[1][0], il[1][0]);
+        ff_cmac(l1, x1, rh[1][1], rl[1][1], ih[1][1], il[1][1]);
+      } else {
+        const float4* ls[2] = {&l0, &l1};
+        const float4* xs[2] = {&x0, &x1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const float lr = ls[a]->x, li = ls[a]->z;
+            const float xr = xs[b]->x + xs[b]->y, xi = xs[b]->z + xs[b]->w;
+            rh[a][b] = fmaf(lr, xr, fmaf(-li, xi, rh[a][b]));
+            ih[a][b] = fmaf(lr, xi, fmaf(li, xr, ih[a][b]));
+          }
+      }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int64_t row = b0 + ty + 16 * a;
+      const int r = r0 + tx + 16 * b;
+      if (row < B && r < R)
+        Y[f * RB + (int64_t)r * B + row] =
+            FF ? ff_norm(rh[a][b], rl[a][b], ih[a][b], il[a][b]) : make_float4(rh[a][b], 0.f, ih[a][b], 0.f);
+    }
+}
+
+template <bool FF>
+static fmpb_status launch_block_product_tiled(const void* spec, const float4* X, float4* Y, int64_t F, int64_t B,
+                                              int R, cudaStream_t st) {
+  const int64_t btiles = (B + BPT_B - 1) / BPT_B;
+  if (btiles > 65535) {
+    set_error("block_product: block size %lld too large", (long long)B);
+    return FMPB_EINVAL;
+  }
+  dim3 grid((unsigned)((R + BPT_R - 1) / BPT_R), (unsigned)F, (unsigned)btiles);
+  FMPB_LAUNCH(FF ? "block_product_tiled" : "block_product_tiled_f32", st, k_block_product_tiled<FF><<<grid, 256, 0, st>>>(spec, X, Y, B, R));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 static fmpb_status block_product(const void* spec, int spec_format, const float4* X, float4* Y, int64_t F,
                                  int64_t B, int R, cudaStream_t st) {
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
     return FMPB_EINVAL;
   }
+  // many right-hand sides: one tiled pass over the spectrum
+  if (R >= 8 && spec_format == SPEC_FF) return launch_block_product_tiled<true>(spec, X, Y, F, B, R, st);
+  if (R >= 8 && spec_format == SPEC_F32) return launch_block_product_tiled<false>(spec, X, Y, F, B, R, st);
   const int RC = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
   if ((size_t)RC * B * sizeof(float4) > 200 * 1024) {
     set_error("block_product: block size %lld too large", (long long)B);

@@ -96,6 +96,8 @@ fmpb_status spectrum_ff_to_f32(const cd* in, void* out, size_t n, cudaStream_t s
 fmpb_status spectrum_to_ff(cd* spec, size_t n, cudaStream_t st);
 // Out-of-place conversion of n complex doubles to float-float pairs.
 fmpb_status vector_to_ff(const cd* x, float4* y, size_t n, cudaStream_t st);
+// Out-of-place rounding of n complex doubles to complex FP32.
+fmpb_status vector_to_f32(const cd* x, float2* y, size_t n, cudaStream_t st);
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R);
 
 }  // namespace fmpb

@@ -457,6 +457,55 @@ __global__ void k_l2p_apply_ff(const float4* __restrict__ U0, int n, int B, cons
   }
 }
 
+// FP32 operators: V_0, U_0 and p complex FP32.
+__global__ void k_p2m_apply_f32(const float2* __restrict__ V0, int n, int B, const float2* __restrict__ p,
+                                cd* __restrict__ Mom) {
+  extern __shared__ float2 ps2[];
+  const int64_t col = blockIdx.x;
+  const float2* src = p + col * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) ps2[j] = src[j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < B; q += nw) {
+    float re = 0.f, im = 0.f;
+    const float2* row = V0 + (size_t)q * n;
+    for (int j = lane; j < n; j += 32) {
+      const float2 a = row[j], b = ps2[j];
+      re = fmaf(a.x, b.x, fmaf(-a.y, b.y, re));
+      im = fmaf(a.x, b.y, fmaf(a.y, b.x, im));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) Mom[col * B + q] = mkc(re, im);
+  }
+}
+
+__global__ void k_l2p_apply_f32(const float2* __restrict__ U0, int n, int B, const cd* __restrict__ Loc,
+                                cd* __restrict__ y) {
+  extern __shared__ float2 ls2[];
+  const int64_t col = blockIdx.x;
+  const cd* src = Loc + col * B;
+  for (int q = threadIdx.x; q < B; q += blockDim.x) ls2[q] = make_float2((float)src[q].x, (float)src[q].y);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw) {
+    float re = 0.f, im = 0.f;
+    const float2* row = U0 + (size_t)i * B;
+    for (int q = lane; q < B; q += 32) {
+      const float2 a = row[q], b = ls2[q];
+      re = fmaf(a.x, b.x, fmaf(-a.y, b.y, re));
+      im = fmaf(a.x, b.y, fmaf(a.y, b.x, im));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) y[col * n + i] = cadd(y[col * n + i], mkc(re, im));
+  }
+}
+
 // ------------------------------------------------------------- host side --
 fmpb_status multipole_tables(const DeviceMesh& m, double k, int nt, cd* V0, cd* U0, cudaStream_t st) {
   if (nt < 1 || nt > MAX_NT) {
@@ -516,6 +565,22 @@ fmpb_status p2m_apply(const float4* V0, int n, int B, int64_t columns, const flo
 
 fmpb_status l2p_apply(const float4* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st) {
   FMPB_LAUNCH("l2p_apply", st, k_l2p_apply_ff<<<(unsigned)columns, 256, sizeof(float4) * B, st>>>(U0, n, B, Loc, y));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+}  // namespace fmpb
+
+namespace fmpb {
+
+fmpb_status p2m_apply_f32(const float2* V0, int n, int B, int64_t columns, const float2* p, cd* Mom, cudaStream_t st) {
+  FMPB_LAUNCH("p2m_apply_f32", st, k_p2m_apply_f32<<<(unsigned)columns, 256, sizeof(float2) * n, st>>>(V0, n, B, p, Mom));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+fmpb_status l2p_apply_f32(const float2* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st) {
+  FMPB_LAUNCH("l2p_apply_f32", st, k_l2p_apply_f32<<<(unsigned)columns, 256, sizeof(float2) * B, st>>>(U0, n, B, Loc, y));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }

@@ -23,4 +23,8 @@ fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, cons
 fmpb_status p2m_apply(const float4* V0, int n, int B, int64_t columns, const float4* p, cd* Mom, cudaStream_t st);
 fmpb_status l2p_apply(const float4* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st);
 
+// FP32 operators: complex FP32 tables and p.
+fmpb_status p2m_apply_f32(const float2* V0, int n, int B, int64_t columns, const float2* p, cd* Mom, cudaStream_t st);
+fmpb_status l2p_apply_f32(const float2* U0, int n, int B, int64_t columns, const cd* Loc, cd* y, cudaStream_t st);
+
 }  // namespace fmpb

@@ -86,6 +86,83 @@ __global__ void __launch_bounds__(256) k_near_apply_ff(const float4* __restrict_
     }
 }
 
+// FP32 operators: S and p complex FP32 (float2), FP32 FMAs, same tiling.
+__global__ void __launch_bounds__(256) k_near_apply_f32(const float2* __restrict__ S, const int* __restrict__ offs,
+                                                        int n_near, int n, int Mx, int My, int Mz,
+                                                        const float2* __restrict__ p, cd* __restrict__ y,
+                                                        int accumulate) {
+  __shared__ float2 Ss[NT_I][NT_J + 1];
+  __shared__ float2 Ps[NT_J][NT_C + 1];
+  const int r = blockIdx.z;
+  const int i0 = blockIdx.y * NT_I;
+  const int c0 = blockIdx.x * NT_C;
+  const int Nc = Mx * My * Mz;
+  const int64_t N = (int64_t)Nc * n;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float re[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, im[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const float2* pr = p + (int64_t)r * N;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int o = 0; o < n_near; ++o) {
+    const int dx = offs[3 * o], dy = offs[3 * o + 1], dz = offs[3 * o + 2];
+    const float2* So = S + (size_t)o * n * n;
+    for (int j0 = 0; j0 < n; j0 += NT_J) {
+      for (int e = threadIdx.x; e < NT_I * NT_J; e += blockDim.x) {
+        const int ii = e / NT_J, jj = e - ii * NT_J;
+        const int i = i0 + ii, j = j0 + jj;
+        Ss[ii][jj] = (i < n && j < n) ? So[(size_t)i * n + j] : zero;
+      }
+      for (int e = threadIdx.x; e < NT_J * NT_C; e += blockDim.x) {
+        const int cc = e / NT_J, jj = e - cc * NT_J;
+        const int c = c0 + cc, j = j0 + jj;
+        float2 v = zero;
+        if (c < Nc && j < n) {
+          const int cx = c % Mx, cy = (c / Mx) % My, cz = c / (Mx * My);
+          const int sx = cx - dx, sy = cy - dy, sz = cz - dz;
+          if (sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz)
+            v = pr[((int64_t)(sz * My + sy) * Mx + sx) * n + j];
+        }
+        Ps[jj][cc] = v;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int jj = 0; jj < NT_J; ++jj) {
+        const float2 s[2] = {Ss[ty][jj], Ss[ty + 16][jj]};
+        const float2 q[2] = {Ps[jj][tx], Ps[jj][tx + 16]};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            re[a][b] = fmaf(s[a].x, q[b].x, fmaf(-s[a].y, q[b].y, re[a][b]));
+            im[a][b] = fmaf(s[a].x, q[b].y, fmaf(s[a].y, q[b].x, im[a][b]));
+          }
+      }
+      __syncthreads();
+    }
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + ty + 16 * a, c = c0 + tx + 16 * b;
+      if (i < n && c < Nc) {
+        cd* d = y + (int64_t)r * N + (int64_t)c * n + i;
+        const cd v = mkc((double)re[a][b], (double)im[a][b]);
+        *d = accumulate ? cadd(*d, v) : v;
+      }
+    }
+}
+
+fmpb_status near_apply_f32(const float2* S, const int* offs_dev, int n_near, int n, const int M[3], int R,
+                           const float2* p, cd* y, bool accumulate, cudaStream_t st) {
+  const int Nc = M[0] * M[1] * M[2];
+  if (R > 65535) {
+    set_error("near_apply: too many right-hand sides");
+    return FMPB_EINVAL;
+  }
+  dim3 grid((unsigned)((Nc + NT_C - 1) / NT_C), (unsigned)((n + NT_I - 1) / NT_I), (unsigned)R);
+  FMPB_LAUNCH("near_apply_f32", st, k_near_apply_f32<<<grid, 256, 0, st>>>(S, offs_dev, n_near, n, M[0], M[1], M[2], p, y, accumulate ? 1 : 0));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 fmpb_status near_apply(const float4* S, const int* offs_dev, int n_near, int n, const int M[3], int R, const float4* p,
                        cd* y, bool accumulate, cudaStream_t st) {
   const int Nc = M[0] * M[1] * M[2];

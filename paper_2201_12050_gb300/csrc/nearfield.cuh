@@ -9,4 +9,8 @@ namespace fmpb {
 fmpb_status near_apply(const float4* S, const int* offs_dev, int n_near, int n, const int M[3], int R, const float4* p,
                        cd* y, bool accumulate, cudaStream_t st);
 
+// FP32 operators: S and p complex FP32.
+fmpb_status near_apply_f32(const float2* S, const int* offs_dev, int n_near, int n, const int M[3], int R,
+                           const float2* p, cd* y, bool accumulate, cudaStream_t st);
+
 }  // namespace fmpb

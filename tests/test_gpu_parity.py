@@ -333,3 +333,28 @@ def test_fmm_fp32_operator_products():
     y = op.matvec(_dev(x)).cpu().numpy()
     ref = fmm.fmm_matvec_explicit(bem.CellMesh(v, t), w.lattice, w.counts, k, w.n_t, x)
     assert _rel(y, ref) < 1e-5
+
+
+@pytest.mark.parametrize("R", [9, 35])
+def test_many_rhs_products_match_oracle(R):
+    """R >= 8 takes the tiled per-frequency GEMM (one pass over the spectrum)."""
+    v, t = icosphere(1, 0.2)
+    counts, lattice, k = (3, 2, 1), np.diag([0.5, 0.6, 1.0]), 3.0
+    A = bem.dense_matrix(v, t, lattice, counts, k)
+    x = random_complex_vectors(40 + R, R, A.shape[0])
+    ref = x @ A.T
+    op = gb.Operator(v, t, counts, lattice, k, form=gb.FORM_PBEM)
+    assert _rel(op.matvec(_dev(x)).cpu().numpy(), ref) < 1e-12
+    op32 = gb.Operator(v, t, counts, lattice, k, form=gb.FORM_PBEM, precision=gb.FP32)
+    assert _rel(op32.matvec(_dev(x)).cpu().numpy(), ref) < 1e-5
+
+
+def test_fmm_fp32_many_rhs_products():
+    v, t = icosphere(1, 0.2)
+    counts, lattice, k, nt = (5, 4, 1), np.diag([0.6, 0.6, 1.0]), 4.0, 5
+    x = random_complex_vectors(50, 10, int(np.prod(counts)) * len(t))
+    ref = fmm.fmm_matvec_explicit(bem.CellMesh(v, t), lattice, counts, k, nt, x)
+    op = gb.Operator(v, t, counts, lattice, k, form=gb.FORM_FMM, n_t=nt, precision=gb.FP32)
+    assert _rel(op.matvec(_dev(x)).cpu().numpy(), ref) < 1e-5
+    op64 = gb.Operator(v, t, counts, lattice, k, form=gb.FORM_FMM, n_t=nt)
+    assert _rel(op64.matvec(_dev(x)).cpu().numpy(), ref) < 1e-12
