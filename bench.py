@@ -47,8 +47,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile-case", default=None, choices=["product", "build"],
-                    help="small case for kernel captures: 3x8 cylinders (1.8 GB spectrum), 500 Hz")
+    ap.add_argument("--profile-case", default=None, choices=["product", "build", "near", "batch"],
+                    help="small case for kernel captures: product/build = 3x8 cylinders (1.8 GB spectrum) at "
+                         "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, FP32")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="skip the FMM, mixed-precision, serving and batching sections")
     return ap.parse_args()
 
 
@@ -603,10 +606,32 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """3 x 8 cylinders at 500 Hz (PBEM form, P = 5 x 16, spectrum 1.84 GB, larger
-    than L2): one operator build, then 4 products.  Prints one JSON line."""
+    """Small cases for kernel captures (inputs larger than L2, a few GB at most):
+    product/build: 3 x 8 cylinders at 500 Hz (PBEM, spectrum 1.84 GB), one build
+    and 4 products; near: the 32 x 32 sphere array (FMM form), one build and 3
+    products; batch: 8 x 8 x 4 cubes, FP32 FMM operator, 3 products of 64
+    right-hand sides.  Prints one JSON line."""
     import torch
     import paper_2201_12050_gb300 as gb
+    if args.profile_case in ("near", "batch"):
+        if args.profile_case == "near":
+            w2 = WORKLOADS["sphere_array_32x32"]
+            v2, t2 = w2.mesh()
+            op = gb.Operator(v2, t2, w2.counts, w2.lattice, w2.wavenumbers[0], form=gb.FORM_FMM, n_t=w2.n_t)
+            x = torch.as_tensor(random_complex_vectors(w2.rhs_seed, 1, op.N), device="cuda")
+        else:
+            w2 = WORKLOADS["cube_lattice_16x16x4"]
+            v2, t2 = w2.mesh()
+            op = gb.Operator(v2, t2, (8, 8, 4), w2.lattice, w2.wavenumbers[3], form=gb.FORM_FMM, n_t=12,
+                             precision=gb.FP32)
+            x = op.rhs_plane_wave(w2.directions)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.matvec(x, out=y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "N": op.N, "R": x.shape[0], "B": op.info["B"],
+                          "F": op.info["F"], "y_norm": float(torch.linalg.vector_norm(y))}))
+        return
     w = WORKLOADS[WORKLOAD]
     v, t = w.mesh()
     k = 2 * math.pi * 500.0 / SPEED_OF_SOUND
