@@ -259,10 +259,12 @@ def run_ours(args):
     total_prof = sum(v_[1] for v_ in prof.values())
     roof = dominant_roofline(dom, prof, w, v, t, args.steps, hbm_peak, peaks, bp_gbs)
 
-    fmm = fmm_section(gb, torch, stream) if rank == 0 else None
-    serving = serving_section(gb) if rank == 0 else None
-    batching = batching_section(gb, torch, stream) if rank == 0 else None
-    mixed = mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
+    sections = rank == 0 and not args.only_headline
+    fmm = fmm_section(gb, torch, stream) if sections else None
+    serving = serving_section(gb) if sections else None
+    batching = batching_section(gb, torch, stream) if sections else None
+    mixed = (mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
+             if not args.only_headline else None)
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

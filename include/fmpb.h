@@ -64,9 +64,16 @@ typedef enum {
 typedef enum { FMPB_FORM_AUTO = -1, FMPB_FORM_FMM = 0, FMPB_FORM_PBEM = 1 } fmpb_form;
 /* FP64: spectrum and tables as float-float pairs (FP64-class accuracy).
  * FP32: spectrum in complex FP32 (half the bytes per product).
+ * BF16: FMM form only.  Near-field blocks and P2M/L2P tables rounded to
+ *       BF16 (FP64 -> FP32 -> BF16, nearest even each time) and applied on
+ *       the tensor cores with FP32 accumulation (see fmpb_offset_gemm_bf16);
+ *       the input vector is rounded the same way per product.  M2L spectrum
+ *       in complex FP32.  Relative error of a product about 1e-3.
  * MIXED: both spectra; fmpb_matvec uses the accurate one and fmpb_solve
- *        runs GMRES-IR (FP32 inner solves, accurate outer residuals).
- * BF16 is reserved. */
+ *        runs GMRES-IR (inner solves on the FP32 spectrum, accurate outer
+ *        residuals).  In the FMM form the inner products also run the near
+ *        field, P2M and L2P on the tensor cores as BF16 does, and the operator
+ *        keeps both the float-float and the BF16 tables. */
 typedef enum { FMPB_FP64 = 0, FMPB_FP32 = 1, FMPB_BF16 = 2, FMPB_MIXED = 3 } fmpb_precision;
 
 /* Finite lattice (Sec. 2.2, Fig. PeriodicArray2d): counts[a] cells along
@@ -96,7 +103,8 @@ typedef struct {
                       |d| <= 2 rho is refused (EADMISS). */
   int n_t;         /* truncation number of the FMM form (Eq. (greenFMM)), 1..20;
                       0 = default 8 */
-  int precision;   /* fmpb_precision: FMPB_FP64 (default), FMPB_FP32 or FMPB_MIXED */
+  int precision;   /* fmpb_precision: FMPB_FP64 (default), FMPB_FP32, FMPB_BF16
+                      (FMM form only) or FMPB_MIXED */
 } fmpb_operator_opts;
 
 typedef struct {
@@ -198,6 +206,17 @@ fmpb_status fmpb_solve(const fmpb_operator *op, int R, const fmpb_c64 *b, fmpb_c
                        const fmpb_solve_opts *opts, fmpb_solve_info *info, void *stream);
 
 /*
+ * Synchronises the stream and reports whether any tensor-core product of
+ * this operator (BF16 precision) gave up waiting for its MMAs since the
+ * operator was built: every such wait is bounded (about one second), and a
+ * kernel that gives up skips its output, frees its tensor memory and raises
+ * a flag instead of hanging.  Returns FMPB_OK, or FMPB_ECUDA when the flag
+ * is set (every product since then is invalid).  fmpb_solve runs this check
+ * itself before returning.
+ */
+fmpb_status fmpb_operator_check(const fmpb_operator *op, void *stream);
+
+/*
  * Total pressure at field points in the fluid (Eq. (cbie) with c(x) = 1):
  * p(x) = p_inc(x) + sum_j int_{E_j} dG/dn_y(x, y) dA_y p_j over every
  * element of every cell (direct sum).
@@ -241,6 +260,30 @@ fmpb_status fmpb_multipole_tables(const double *verts, int64_t nv, const int32_t
  */
 fmpb_status fmpb_m2l_blocks(double k, int n_t, int n_d, const double *dvecs, fmpb_c64 *out,
                             void *stream);
+
+/*
+ * Offset-indexed complex block products on the tensor cores, the form shared
+ * by the near field (Sec. 3.2: y_c = sum_delta S_delta p_{c - delta}) and by
+ * P2M / L2P (Sec. 3.5, one offset delta = 0):
+ *   y[r][c] (+)= sum_o T_o x[r][c - delta_o]
+ * for every right-hand side r < R and cell c of the counts[0] x counts[1] x
+ * counts[2] grid (cell index (c_z counts[1] + c_y) counts[0] + c_x); terms
+ * whose source cell c - delta_o lies outside the grid are skipped.
+ *   offsets  host, n_off x 3 int32 (delta_x, delta_y, delta_z), 1 <= n_off <= 27.
+ *   T        device, n_off x m x k complex blocks, row-major.
+ *   x        device, R x n_cells x k;   y device, R x n_cells x m.
+ *   accumulate  0: y = result;  1: y += result.
+ * Arithmetic: T and x are rounded to BF16 (FP64 -> FP32 -> BF16, nearest
+ * even at each step); the products run on the tensor cores (tcgen05, complex
+ * numbers as 2 x 2 real blocks) with FP32 accumulation; y is complex double.
+ * So the result equals the exact product of the rounded inputs up to FP32
+ * accumulation error.  Allocates its BF16 copies of T and x per call and
+ * synchronises the stream.  FMPB_ECUDA if a bounded wait in the kernel gave
+ * up (see fmpb_operator_check).
+ */
+fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t *offsets,
+                                  int64_t m, int64_t k, const fmpb_c64 *T, int R, const fmpb_c64 *x,
+                                  fmpb_c64 *y, int accumulate, void *stream);
 
 /*
  * Padded circulant lengths P_a (smallest 2,3,5,7-smooth integer >= 2 M_a - 1,

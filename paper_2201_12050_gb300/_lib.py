@@ -92,10 +92,12 @@ SIGNATURES = {
     "fmpb_rhs_plane_wave": (INT, [P, INT, P, P, P, P]),
     "fmpb_matvec": (INT, [P, INT, P, P, P]),
     "fmpb_solve": (INT, [P, INT, P, P, ctypes.POINTER(SolveOpts), P, P]),
+    "fmpb_operator_check": (INT, [P, P]),
     "fmpb_field": (INT, [P, INT, P, P, P, I64, P, P, P]),
     "fmpb_build_blocks": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, INT, P, P, P]),
     "fmpb_multipole_tables": (INT, [P, I64, P, I64, D, INT, P, P, P]),
     "fmpb_m2l_blocks": (INT, [D, INT, INT, P, P, P]),
+    "fmpb_offset_gemm_bf16": (INT, [P, INT, P, I64, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_shape": (INT, [P, P, P]),
     "fmpb_circulant_spectrum": (INT, [P, I64, P, P, P]),
     "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),

@@ -13,8 +13,8 @@ from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, SolveOpts, S
 
 FORM_AUTO, FORM_FMM, FORM_PBEM = -1, 0, 1
 FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem"}
-FP64, FP32, MIXED = 0, 1, 3
-PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", MIXED: "mixed"}
+FP64, FP32, BF16, MIXED = 0, 1, 2, 3
+PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", BF16: "bf16", MIXED: "mixed"}
 
 
 def _stream():
@@ -119,6 +119,10 @@ class Operator:
             check(st)
         return p, info
 
+    def check(self):
+        """fmpb_operator_check: raises FmpbError if a tensor-core wait of this operator gave up."""
+        check(self._lib.fmpb_operator_check(self._h, _stream()))
+
     def field(self, p, dirs, pts, amps=None):
         R = _cvec(p, self.N, "p")
         d = _host(dirs, np.float64).reshape(R, 3)
@@ -164,6 +168,21 @@ def m2l_blocks(k, n_t, dvecs):
     out = torch.empty((len(d), B, B), dtype=torch.complex128, device="cuda")
     check(lib().fmpb_m2l_blocks(float(k), int(n_t), len(d), _ptr(d), _ptr(out), _stream()))
     return out
+
+
+def offset_gemm_bf16(counts, offsets, T, x, out=None, accumulate=False):
+    """fmpb_offset_gemm_bf16: y[r, c] (+)= sum_o T[o] x[r, c - delta_o] on the tensor cores.
+
+    T: (n_off, m, k) complex128 CUDA; x: (R, n_cells * k); returns (R, n_cells * m)."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    off = _host(offsets, np.int32).reshape(-1, 3)
+    n_off, m, k = T.shape
+    ncell = int(np.prod(c))
+    R = _cvec(x, ncell * k, "x")
+    y = out if out is not None else torch.empty((R, ncell * m), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_offset_gemm_bf16(_ptr(c), int(n_off), _ptr(off), int(m), int(k), _ptr(T.contiguous()), R,
+                                      _ptr(x), _ptr(y), 1 if accumulate else 0, _stream()))
+    return y
 
 
 def circulant_shape(counts):

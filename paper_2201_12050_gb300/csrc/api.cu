@@ -11,6 +11,7 @@
 #include "multipole.cuh"
 #include "nearfield.cuh"
 #include "gmres.cuh"
+#include "tc_gemm.cuh"
 
 namespace fmpb {
 
@@ -138,10 +139,15 @@ fmpb_status plan_operator(const double* verts, int64_t nv, const int32_t* tris, 
   int nnear = 1;
   for (int i = 0; i < dim; ++i) nnear *= 3;
   size_t per = 16;   // float-float spectrum
-  if (opts->precision == FMPB_FP32) per = 8;
+  if (opts->precision == FMPB_FP32 || opts->precision == FMPB_BF16) per = 8;
   if (opts->precision == FMPB_MIXED) per = 24;
   size_t total = per * (size_t)sh.F * b * b;
-  if (*form == FMPB_FORM_FMM) total += 16 * ((size_t)nnear * n * n + 2 * (size_t)b * n);
+  const size_t tc_bytes = 2 * ((size_t)nnear * tc_rows(n) * tc_depth(n) + (size_t)tc_rows(b) * tc_depth(n) +
+                               (size_t)tc_rows(n) * tc_depth(b));
+  if (*form == FMPB_FORM_FMM && opts->precision == FMPB_BF16)
+    total += tc_bytes;
+  else if (*form == FMPB_FORM_FMM)
+    total += 16 * ((size_t)nnear * n * n + 2 * (size_t)b * n) + (opts->precision == FMPB_MIXED ? tc_bytes : 0);
   *B = b;
   *F = sh.F;
   *bytes = total;
@@ -170,6 +176,12 @@ struct fmpb_operator {
   int n_near = 0;
   cd* V0 = nullptr;        // B x n, float-float pairs
   cd* U0 = nullptr;        // n x B, float-float pairs
+  // BF16 operators: S, V_0, U_0 as realified BF16 tiles for the tensor cores
+  __nv_bfloat16* Sb = nullptr;    // n_near x tc_rows(n) x tc_depth(n)
+  __nv_bfloat16* V0b = nullptr;   // tc_rows(B) x tc_depth(n)
+  __nv_bfloat16* U0b = nullptr;   // tc_rows(n) x tc_depth(B)
+  TcOffsets near_tc{};
+  unsigned* tc_err = nullptr;     // set by a tensor-core kernel whose wait gave up
   size_t bytes = 0;
   // scratch, grown on demand (calls on one operator are stream-ordered)
   cd* scratch = nullptr;
@@ -184,6 +196,10 @@ struct fmpb_operator {
     cudaFree(near_offs);
     cudaFree(V0);
     cudaFree(U0);
+    cudaFree(Sb);
+    cudaFree(V0b);
+    cudaFree(U0b);
+    cudaFree(tc_err);
     cudaFree(scratch);
   }
 
@@ -198,10 +214,11 @@ struct fmpb_operator {
     return FMPB_OK;
   }
 
-  // low: use the FP32 spectrum of a MIXED operator
+  // low: the inner product of a MIXED operator (FP32 spectrum; in the FMM form
+  // also the BF16 tensor-core near field, P2M and L2P)
   fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st, bool low = false) {
     const int64_t Nc = shape.ncells;
-    const bool f32 = precision == FMPB_FP32 || (precision == FMPB_MIXED && low);
+    const bool f32 = precision == FMPB_FP32 || precision == FMPB_BF16 || (precision == FMPB_MIXED && low);
     const cd* sp = f32 ? reinterpret_cast<const cd*>(spec32) : spec;
     const int fmt = f32 ? SPEC_F32 : SPEC_FF;
     if (form == FMPB_FORM_PBEM) {
@@ -215,6 +232,25 @@ struct fmpb_operator {
     cd* Mom = scratch + circ;
     cd* Loc = Mom + mom;
     float4* xff = reinterpret_cast<float4*>(Loc + mom);
+    if (precision == FMPB_BF16 || (precision == FMPB_MIXED && low)) {
+      const int n = mesh.n;
+      const size_t xb_elems = (size_t)R * Nc * tc_depth(n), lb_elems = (size_t)R * Nc * tc_depth(B);
+      const size_t extra = (2 * (xb_elems + lb_elems) + sizeof(cd) - 1) / sizeof(cd);
+      FMPB_TRY(ensure_scratch(circ + 2 * mom + extra));
+      Mom = scratch + circ;
+      Loc = Mom + mom;
+      __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(Loc + mom);
+      __nv_bfloat16* lb = xb + xb_elems;
+      TcOffsets zero{};
+      zero.n = 1;
+      FMPB_TRY(tc_rows_to_bf16(x, (int64_t)R * Nc, n, xb, st));
+      FMPB_TRY(tc_offset_gemm(Sb, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st));
+      FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
+      FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
+      FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
+      FMPB_TRY(tc_offset_gemm(U0b, zero, n, B, shape.M, R, lb, y, true, tc_err, st));
+      return FMPB_OK;
+    }
     if (precision == FMPB_FP32) {
       float2* x32 = reinterpret_cast<float2*>(Loc + mom);
       FMPB_TRY(vector_to_f32(x, x32, nvec, st));
@@ -268,8 +304,9 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(k > 0.0 && std::isfinite(k), "operator_create: wavenumber must be positive");
   fmpb_operator_opts o = opts ? *opts : fmpb_operator_opts{FMPB_FORM_AUTO, 0, FMPB_FP64};
   CHECK_ARG(o.form >= -1 && o.form <= 1, "operator_create: bad form %d", o.form);
-  CHECK_ARG(o.precision == FMPB_FP64 || o.precision == FMPB_FP32 || o.precision == FMPB_MIXED,
-            "operator_create: precision must be FMPB_FP64, FMPB_FP32 or FMPB_MIXED");
+  CHECK_ARG(o.precision == FMPB_FP64 || o.precision == FMPB_FP32 || o.precision == FMPB_BF16 ||
+                o.precision == FMPB_MIXED,
+            "operator_create: precision must be FMPB_FP64, FMPB_FP32, FMPB_BF16 or FMPB_MIXED");
   const int nt = o.n_t > 0 ? o.n_t : 8;
   CHECK_ARG(nt >= 1 && nt <= MAX_NT, "operator_create: n_t must be 1..%d", MAX_NT);
   cudaStream_t st = (cudaStream_t)stream;
@@ -296,6 +333,11 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   int form = 0;
   s = decide_form(op->grid, op->mesh.radius, o.form, &form, &all_off, &near_off, &far_off);
   if (s != FMPB_OK) return fail(s);
+  if (form == FMPB_FORM_PBEM && o.precision == FMPB_BF16) {
+    set_error("operator_create: BF16 runs the near-field, P2M and L2P products of the FMM form on the tensor cores; "
+              "this lattice needs the PBEM form, which has none (use FMPB_FP32 or FMPB_MIXED)");
+    return fail(FMPB_EINVAL);
+  }
   op->form = form;
   if (form == FMPB_FORM_PBEM) {
     op->B = n;
@@ -331,7 +373,32 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     if (s == FMPB_OK) s = multipole_tables(op->mesh, k, nt, op->V0, op->U0, st);
     // the products read the near blocks and the P2M/L2P tables as float-float
     // pairs, or as complex FP32 for FP32 operators (8 bytes per entry)
-    if (o.precision == FMPB_FP32) {
+    if (o.precision == FMPB_BF16 || o.precision == FMPB_MIXED) {
+      if (s == FMPB_OK) s = dev_alloc(&op->Sb, (size_t)op->n_near * tc_rows(n) * tc_depth(n), op->bytes);
+      if (s == FMPB_OK) s = dev_alloc(&op->V0b, (size_t)tc_rows(B) * tc_depth(n), op->bytes);
+      if (s == FMPB_OK) s = dev_alloc(&op->U0b, (size_t)tc_rows(n) * tc_depth(B), op->bytes);
+      if (s == FMPB_OK) s = dev_alloc(&op->tc_err, 1, op->bytes);
+      if (s == FMPB_OK && cudaMemsetAsync(op->tc_err, 0, sizeof(unsigned), st) != cudaSuccess)
+        s = cuda_status(cudaGetLastError(), "memset");
+      if (s == FMPB_OK) s = tc_realify(op->S, op->n_near, n, n, op->Sb, st);
+      if (s == FMPB_OK) s = tc_realify(op->V0, 1, B, n, op->V0b, st);
+      if (s == FMPB_OK) s = tc_realify(op->U0, 1, n, B, op->U0b, st);
+      if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tables");
+      if (s == FMPB_OK) {
+        op->near_tc.n = op->n_near;
+        for (int i = 0; i < op->n_near; ++i)
+          for (int c = 0; c < 3; ++c) op->near_tc.d[i][c] = near_off[3 * i + c];
+      }
+    }
+    if (o.precision == FMPB_BF16) {
+      if (s == FMPB_OK) {
+        for (cd** t : {&op->S, &op->V0, &op->U0}) {
+          cudaFree(*t);
+          *t = nullptr;
+        }
+        op->bytes -= sizeof(cd) * ((size_t)op->n_near * n * n + 2 * (size_t)B * n);
+      }
+    } else if (o.precision == FMPB_FP32) {
       for (cd** t : {&op->S, &op->V0, &op->U0}) {
         const size_t ne = (t == &op->S) ? (size_t)op->n_near * n * n : (size_t)B * n;
         float2* f32 = nullptr;
@@ -371,7 +438,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     s = dev_alloc(reinterpret_cast<float2**>(&op->spec32), ne, op->bytes);
     if (s == FMPB_OK) s = spectrum_ff_to_f32(op->spec, op->spec32, ne, st);
     if (s != FMPB_OK) return fail(s);
-    if (o.precision == FMPB_FP32) {
+    if (o.precision == FMPB_FP32 || o.precision == FMPB_BF16) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "operator_create"));
       cudaFree(op->spec);
       op->spec = nullptr;
@@ -426,11 +493,31 @@ fmpb_status fmpb_solve(const fmpb_operator* op, int R, const fmpb_c64* b, fmpb_c
   fmpb_operator* mop = const_cast<fmpb_operator*>(op);
   MatvecFn A = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st); };
   const int64_t N = (int64_t)op->mesh.n * op->shape.ncells;
+  fmpb_status s;
   if (op->precision == FMPB_MIXED) {
     MatvecFn Alow = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st, true); };
-    return gmres_refined(A, Alow, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+    s = gmres_refined(A, Alow, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+  } else {
+    s = gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
   }
-  return gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+  if (s != FMPB_OK && s != FMPB_ENOCONV) return s;
+  const fmpb_status c = fmpb_operator_check(op, stream);
+  return c != FMPB_OK ? c : s;
+}
+
+fmpb_status fmpb_operator_check(const fmpb_operator* op, void* stream) {
+  CHECK_ARG(op, "operator_check: NULL operator");
+  cudaStream_t st = (cudaStream_t)stream;
+  FMPB_CUDA(cudaStreamSynchronize(st));
+  if (!op->tc_err) return FMPB_OK;
+  unsigned flag = 0;
+  FMPB_CUDA(cudaMemcpyAsync(&flag, op->tc_err, sizeof(flag), cudaMemcpyDeviceToHost, st));
+  FMPB_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    set_error("a tensor-core product gave up waiting for its MMAs (results of this operator are invalid)");
+    return FMPB_ECUDA;
+  }
+  return FMPB_OK;
 }
 
 fmpb_status fmpb_field(const fmpb_operator* op, int R, const fmpb_c64* p, const double* dirs, const fmpb_c64* amps,
@@ -493,6 +580,54 @@ fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fm
     M[a] = counts[a];
   }
   return circulant_spectrum_from_blocks(make_shape(M), B, (const cd*)blocks, (cd*)spec, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
+                                  const fmpb_c64* T, int R, const fmpb_c64* x, fmpb_c64* y, int accumulate,
+                                  void* stream) {
+  CHECK_ARG(counts && offsets && T && x && y, "offset_gemm_bf16: NULL argument");
+  CHECK_ARG(n_off >= 1 && n_off <= TC_MAX_OFF, "offset_gemm_bf16: n_off must be 1..%d", TC_MAX_OFF);
+  CHECK_ARG(m >= 1 && m <= (1 << 20) && k >= 1 && k <= (1 << 20), "offset_gemm_bf16: m or k out of range");
+  CHECK_ARG(R >= 1 && R <= 4096, "offset_gemm_bf16: R out of range");
+  CHECK_ARG((const void*)x != (const void*)y, "offset_gemm_bf16: x and y must not alias");
+  int M[3];
+  int64_t Nc = 1;
+  for (int a = 0; a < 3; ++a) {
+    CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "offset_gemm_bf16: count out of range");
+    M[a] = counts[a];
+    Nc *= M[a];
+  }
+  TcOffsets offs{};
+  offs.n = n_off;
+  for (int i = 0; i < n_off; ++i)
+    for (int c = 0; c < 3; ++c) offs.d[i][c] = offsets[3 * i + c];
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t a_elems = (size_t)n_off * tc_rows(m) * tc_depth(k);
+  const size_t x_elems = (size_t)R * Nc * tc_depth(k);
+  __nv_bfloat16 *Ab = nullptr, *Xb = nullptr;
+  unsigned* err = nullptr;
+  size_t bytes = 0;
+  fmpb_status s = dev_alloc(&Ab, a_elems, bytes);
+  if (s == FMPB_OK) s = dev_alloc(&Xb, x_elems, bytes);
+  if (s == FMPB_OK) s = dev_alloc(&err, 1, bytes);
+  if (s == FMPB_OK && cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "memset");
+  if (s == FMPB_OK) s = tc_realify((const cd*)T, n_off, m, k, Ab, st);
+  if (s == FMPB_OK) s = tc_rows_to_bf16((const cd*)x, (int64_t)R * Nc, k, Xb, st);
+  if (s == FMPB_OK) s = tc_offset_gemm(Ab, offs, m, k, M, R, Xb, (cd*)y, accumulate != 0, err, st);
+  unsigned flag = 0;
+  if (s == FMPB_OK && cudaMemcpyAsync(&flag, err, sizeof(flag), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "offset_gemm_bf16");
+  if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "offset_gemm_bf16");
+  if (s == FMPB_OK && flag) {
+    set_error("offset_gemm_bf16: a tensor-core wait gave up");
+    s = FMPB_ECUDA;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(Ab);
+  cudaFree(Xb);
+  cudaFree(err);
+  return s;
 }
 
 fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R, const fmpb_c64* x,

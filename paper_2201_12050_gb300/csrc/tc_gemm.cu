@@ -1,0 +1,363 @@
+// Offset-indexed complex block products on the 5th-generation tensor cores.
+//
+// The near field of the FMPBEM (Sec. 3.2: y_c = sum_delta S_delta p_{c-delta})
+// and the P2M / L2P steps shared by all cells (Sec. 3.5: M_c = V_0 p_c,
+// y_c += U_0 L_c) are the same operation: for every cell c and right-hand
+// side r, a sum over cell offsets delta of a complex block times the vector
+// of the source cell c - delta.  Seen from all cells at once, each offset is
+// one dense GEMM whose columns are the (cell, rhs) pairs, so with many
+// right-hand sides this is where the method becomes tensor-core work.
+//
+// Arithmetic: BF16 inputs, FP32 accumulation (tcgen05.mma kind::f16).  A
+// complex product is carried as the real product of the interleaved 2 x 2
+// representation [[re, -im], [im, re]], so one real GEMM of twice the size
+// gives real and imaginary parts in adjacent accumulator rows.
+//
+// Kernel structure (one CTA per 128 x 256 output tile, 256 threads):
+//   - all threads stage A (128 x 64) and B (256 x 64) tiles with cp.async into
+//     a 4-deep ring of shared-memory stages, in the no-swizzle K-major layout
+//     of 8-row x 16-byte core matrices; B rows of source cells outside the
+//     grid are zero-filled by the copy itself (source size 0);
+//   - one thread issues four 128 x 256 x 16 MMAs per stage into a 256-column
+//     FP32 accumulator in tensor memory and commits them to the stage's
+//     mbarrier, which releases the stage for the next copy;
+//   - after the last commit the eight warps read the accumulator back with
+//     tcgen05.ld (each warp its 32-lane quarter, half of the columns) and
+//     write or add complex-double output with coalesced stores.
+// Every wait is bounded (one second of wall time); a wait that gives up sets
+// an error word for the host, and the CTA still drains its copies and frees
+// its tensor memory before it returns.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "profile.cuh"
+#include "tc_gemm.cuh"
+
+namespace fmpb {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 256;
+constexpr int TC_BK = 64;
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 256;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_BAR_BYTES = 64;   // TC_STAGES mbarriers + the tensor-memory address
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + TC_BAR_BYTES;
+constexpr uint64_t TC_WAIT_NS = 1000000000ull;
+
+// Core-matrix strides of the no-swizzle K-major layout: the 16-byte rows of
+// one 8 x 8 core matrix are contiguous (128 bytes), core matrices adjacent in
+// K are 128 bytes apart and those adjacent in M (or N) TC_BK / 8 * 128 bytes.
+constexpr uint32_t TC_LBO = 128;
+constexpr uint32_t TC_SBO = (TC_BK / 8) * 128;
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B in BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N / 8 in bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t TC_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading
+// byte offset / 16 (16-29), stride byte offset / 16 (32-45), the fixed
+// version field 1 (46-47), base offset 0, no swizzling (61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// Make this thread's completed generic-proxy writes to shared memory visible
+// to the tensor cores, which read their operands through the async proxy.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Waits for the completion of the phase with the given parity; false after TC_WAIT_NS.
+__device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > TC_WAIT_NS) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// D (tensor memory) = A B (+ D if accumulate), one 128 x 256 x 16 step.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+// The mbarrier receives one arrival when all MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+// 16 consecutive FP32 columns of this thread's accumulator lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_offset_gemm(const __nv_bfloat16* __restrict__ A, int64_t a_stride, int Kp,
+                     const __nv_bfloat16* __restrict__ X, cd* __restrict__ y, int m, int64_t ncols, int Mx, int My,
+                     int Mz, TcOffsets offs, int accumulate, unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+  const uint32_t sbase = smem_u32(smem);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_BM;
+  const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
+  const int Nc = Mx * My * Mz;
+
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), TC_BN);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // This thread's copies: the 16-byte chunk q = tid + 256 t of a stage sits
+  // at byte 16 q, i.e. row ((q >> 6) << 3) + (q & 7) and K chunk (q >> 3) & 7.
+  const int kc = (tid >> 3) & 7;
+  const int rlo = (tid >> 6) * 8 + (tid & 7);   // row for t = 0; t adds 32 rows
+  // B rows: column j = n0 + row of the output; its cell coordinates
+  int64_t bj[TC_BN / 32];
+  int bx[TC_BN / 32], by[TC_BN / 32], bz[TC_BN / 32];
+#pragma unroll
+  for (int t = 0; t < TC_BN / 32; ++t) {
+    const int64_t j = n0 + rlo + 32 * t;
+    bj[t] = j < ncols ? j : -1;
+    const int c = (int)(j % Nc);
+    bx[t] = c % Mx;
+    by[t] = (c / Mx) % My;
+    bz[t] = c / (Mx * My);
+  }
+  const int kt_per_off = Kp / TC_BK;
+  const int KT = offs.n * kt_per_off;
+
+  auto load_stage = [&](int it, int s) {
+    const int o = it / kt_per_off;
+    const int k0 = (it - o * kt_per_off) * TC_BK + kc * 8;
+    const int dx = offs.d[o][0], dy = offs.d[o][1], dz = offs.d[o][2];
+    const int64_t dlin = ((int64_t)dz * My + dy) * Mx + dx;
+    const uint32_t sa = sbase + s * TC_STAGE_BYTES + tid * 16;
+    const uint32_t sb = sa + TC_A_BYTES;
+    const __nv_bfloat16* arow = A + o * a_stride + (int64_t)(m0 + rlo) * Kp + k0;
+#pragma unroll
+    for (int t = 0; t < TC_BM / 32; ++t) cp_async16(sa + t * 4096, arow + (int64_t)(32 * t) * Kp, 16);
+#pragma unroll
+    for (int t = 0; t < TC_BN / 32; ++t) {
+      const int sx = bx[t] - dx, sy = by[t] - dy, sz = bz[t] - dz;
+      const bool ok = bj[t] >= 0 && sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz;
+      const __nv_bfloat16* src = ok ? X + (bj[t] - dlin) * Kp + k0 : X;
+      cp_async16(sb + t * 4096, src, ok ? 16 : 0);
+    }
+  };
+
+  bool bad = false;
+#pragma unroll 1
+  for (int s = 0; s < TC_STAGES - 1; ++s) {
+    if (s < KT) load_stage(s, s);
+    cp_async_commit();
+  }
+  int kt = 0;
+#pragma unroll 1
+  for (; kt < KT; ++kt) {
+    const int s = kt % TC_STAGES;
+    cp_async_wait<TC_STAGES - 2>();
+    fence_proxy_async();
+    if (__syncthreads_or(bad)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = sbase + s * TC_STAGE_BYTES, b0 = a0 + TC_A_BYTES;
+#pragma unroll
+      for (int q = 0; q < TC_BK / 16; ++q) tc_mma(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), (kt | q) != 0);
+      tc_commit(smem_u32(&bars[s]));
+    }
+    const int nk = kt + TC_STAGES - 1;
+    if (nk < KT) {
+      // stage nk % TC_STAGES was last read by the MMAs of step kt - 1
+      if (kt >= 1) bad = !mbar_wait_bounded(smem_u32(&bars[(kt - 1) % TC_STAGES]), ((kt - 1) / TC_STAGES) & 1);
+      if (!bad) load_stage(nk, nk % TC_STAGES);
+    }
+    cp_async_commit();
+  }
+  const int last = kt - 1;   // MMAs were issued for steps 0 .. last
+  bool ok = true;
+  if (last >= 0) ok = mbar_wait_bounded(smem_u32(&bars[last % TC_STAGES]), (last / TC_STAGES) & 1);
+  cp_async_wait<0>();
+  ok = !__syncthreads_or(!ok || bad || last != KT - 1);
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 1u);
+  } else {
+    tc_fence_after();
+    const int quarter = warp & 3;
+    const int64_t gm = (int64_t)m0 + quarter * 32 + lane;   // accumulator lane = realified output row
+    const bool row_ok = gm < 2 * (int64_t)m;
+    const int64_t i = gm >> 1;
+    const int part = (int)(gm & 1);
+    const int cbase = (warp >> 2) * (TC_BN / 2);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN / 2; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + c0), v);
+      if (row_ok) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int64_t j = n0 + cbase + c0 + t;
+          if (j < ncols) {
+            double* d = reinterpret_cast<double*>(y + j * m + i) + part;
+            *d = accumulate ? *d + (double)v[t] : (double)v[t];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TC_BN);
+}
+
+__device__ __forceinline__ __nv_bfloat16 to_bf16(double v) { return __float2bfloat16_rn(__double2float_rn(v)); }
+
+__global__ void k_tc_realify(const cd* __restrict__ T, int64_t m, int64_t k, int64_t Mh, int64_t Kh, int64_t total,
+                             __nv_bfloat162* __restrict__ A) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t per = Mh * Kh;
+  const int64_t o = idx / per, rem = idx - o * per;
+  const int64_t i = rem / Kh, j = rem - i * Kh;
+  cd v = mkc(0.0, 0.0);
+  if (i < m && j < k) v = T[(o * m + i) * k + j];
+  const __nv_bfloat16 re = to_bf16(v.x), im = to_bf16(v.y), nim = to_bf16(-v.y);
+  // rows 2i and 2i+1 of the realified block, each Kp = 2 Kh values (Kh pairs)
+  __nv_bfloat162* base = A + o * (2 * Mh) * Kh;
+  __nv_bfloat162 top, bot;
+  top.x = re;
+  top.y = nim;
+  bot.x = im;
+  bot.y = re;
+  base[(2 * i) * Kh + j] = top;
+  base[(2 * i + 1) * Kh + j] = bot;
+}
+
+__global__ void k_tc_rows_to_bf16(const cd* __restrict__ x, int64_t k, int64_t Kh, int64_t total,
+                                  __nv_bfloat162* __restrict__ X) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t rho = idx / Kh, j = idx - rho * Kh;
+  cd v = mkc(0.0, 0.0);
+  if (j < k) v = x[rho * k + j];
+  __nv_bfloat162 p;
+  p.x = to_bf16(v.x);
+  p.y = to_bf16(v.y);
+  X[idx] = p;
+}
+
+}  // namespace
+
+fmpb_status tc_realify(const cd* T, int n_off, int64_t m, int64_t k, __nv_bfloat16* A, cudaStream_t st) {
+  const int64_t Mh = tc_rows(m) / 2, Kh = tc_depth(k) / 2;
+  const int64_t total = (int64_t)n_off * Mh * Kh;
+  FMPB_LAUNCH("tc_realify", st,
+              k_tc_realify<<<grid_for((size_t)total, 256), 256, 0, st>>>(T, m, k, Mh, Kh, total,
+                                                                          reinterpret_cast<__nv_bfloat162*>(A)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+fmpb_status tc_rows_to_bf16(const cd* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
+  const int64_t Kh = tc_depth(k) / 2;
+  const int64_t total = rows * Kh;
+  if (total == 0) return FMPB_OK;
+  FMPB_LAUNCH("tc_to_bf16", st,
+              k_tc_rows_to_bf16<<<grid_for((size_t)total, 256), 256, 0, st>>>(
+                  x, k, Kh, total, reinterpret_cast<__nv_bfloat162*>(X)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
+                           const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st) {
+  const int64_t Mp = tc_rows(m), Kp = tc_depth(k);
+  const int64_t Nc = (int64_t)M[0] * M[1] * M[2];
+  const int64_t ncols = Nc * R;
+  if (offs.n < 1 || offs.n > TC_MAX_OFF || m < 1 || k < 1 || R < 1 || Nc < 1) {
+    set_error("tc_offset_gemm: bad shape (offsets %d, m %lld, k %lld, R %d)", offs.n, (long long)m, (long long)k, R);
+    return FMPB_EINVAL;
+  }
+  const int64_t ntiles = (ncols + TC_BN - 1) / TC_BN;
+  if (ntiles > 65535 || Kp > (1 << 24) || Nc > (1 << 30)) {
+    set_error("tc_offset_gemm: %lld columns exceed the launch limit", (long long)ncols);
+    return FMPB_EINVAL;
+  }
+  FMPB_CUDA(cudaFuncSetAttribute(k_tc_offset_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  dim3 grid((unsigned)(Mp / TC_BM), (unsigned)ntiles);
+  FMPB_LAUNCH("tc_gemm", st,
+              k_tc_offset_gemm<<<grid, TC_THREADS, TC_SMEM, st>>>(A, Mp * Kp, (int)Kp, X, y, (int)m, ncols, M[0],
+                                                                  M[1], M[2], offs, accumulate ? 1 : 0, err));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+}  // namespace fmpb

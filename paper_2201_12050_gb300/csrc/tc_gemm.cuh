@@ -1,0 +1,40 @@
+// Offset-indexed complex block products on the tensor cores (tc_gemm.cu).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace fmpb {
+
+// Up to 3^3 cell offsets per product (the near stencil of a 3-D lattice).
+constexpr int TC_MAX_OFF = 27;
+struct TcOffsets {
+  int n;
+  int d[TC_MAX_OFF][3];
+};
+
+// Shapes of the realified operands of a complex m x k block.
+//   Mp = 2 m rounded up to 128 (tile rows), Kp = 2 k rounded up to 64 (tile depth).
+inline int64_t tc_rows(int64_t m) { return (2 * m + 127) / 128 * 128; }
+inline int64_t tc_depth(int64_t k) { return (2 * k + 63) / 64 * 64; }
+
+// A (n_off x Mp x Kp BF16) from n_off complex blocks (m x k each), as the
+// real matrix of the complex product with rows and columns interleaved:
+//   A[2i][2j] = Re T_ij, A[2i][2j+1] = -Im T_ij, A[2i+1][2j] = Im T_ij, A[2i+1][2j+1] = Re T_ij,
+// zero outside 2m x 2k.  Values are rounded FP64 -> FP32 -> BF16, each to nearest even.
+fmpb_status tc_realify(const cd* T, int n_off, int64_t m, int64_t k, __nv_bfloat16* A, cudaStream_t st);
+
+// X (rows x Kp BF16): row rho holds (Re x_rho0, Im x_rho0, Re x_rho1, ...) of
+// the complex row x + rho k, zero-padded to Kp; same rounding as tc_realify.
+fmpb_status tc_rows_to_bf16(const cd* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st);
+
+// y[(r Nc + c) m + i] (+)= sum_o sum_j T_o[i][j] x[(r Nc + c - delta_o) k + j]
+// for every right-hand side r < R and cell c of the M[0] x M[1] x M[2] grid;
+// source cells c - delta_o outside the grid contribute nothing.  A and X as
+// produced by tc_realify / tc_rows_to_bf16; FP32 accumulation in tensor
+// memory; y complex double.  err: device word, set non-zero (never cleared
+// here) if a wait inside the kernel gave up.
+fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
+                           const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st);
+
+}  // namespace fmpb
