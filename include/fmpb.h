@@ -312,6 +312,23 @@ fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_
                                  const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
 
 /*
+ * The product of fmpb_circulant_apply with the per-frequency products
+ * Y_f = Lambda_f X_f on the tensor cores (tcgen05, BF16 inputs, FP32
+ * accumulation): Lambda_f and X_f are rounded to BF16 (Lambda: FP64 -> FP32 ->
+ * BF16; X_f: its float-float DFT value -> FP32 -> BF16, nearest even at each
+ * step); the pruned forward and inverse DFTs run in float-float as in
+ * fmpb_circulant_apply.  The result equals the exact circulant product with
+ * the rounded Lambda_f and X_f up to FP32 accumulation.  This is how BF16
+ * operators (and the inner solves of MIXED operators in the FMM form) apply
+ * their M2L translations.  Same arguments and layouts as
+ * fmpb_circulant_apply; F must not exceed 65,535.  Allocates its BF16 copy of
+ * the spectrum and its scratch per call, synchronises the stream; FMPB_ECUDA
+ * if a bounded wait of the tensor-core kernel gave up.
+ */
+fmpb_status fmpb_circulant_apply_bf16(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
+                                      const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
+
+/*
  * Same product as fmpb_circulant_apply, for callers that cannot allocate
  * device memory during the call (for example a program whose device memory
  * belongs to another runtime's pool, or a latency-bound loop that cannot

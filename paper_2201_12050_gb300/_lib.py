@@ -102,6 +102,7 @@ SIGNATURES = {
     "fmpb_circulant_spectrum": (INT, [P, I64, P, P, P]),
     "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_apply_static": (INT, [P, I64, P, INT, P, P, INT, P]),
+    "fmpb_circulant_apply_bf16": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_server_create": (INT, [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]),
     "fmpb_server_submit": (INT, [P, ctypes.POINTER(Request), P, ctypes.POINTER(ctypes.c_uint64)]),
     "fmpb_server_wait": (INT, [P, ctypes.c_uint64, INT, ctypes.POINTER(Result)]),

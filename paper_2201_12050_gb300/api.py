@@ -214,6 +214,18 @@ def circulant_apply(counts, spec, x, out=None, accumulate=False):
     return y
 
 
+def circulant_apply_bf16(counts, spec, x, out=None, accumulate=False):
+    """fmpb_circulant_apply_bf16: the circulant product with BF16 tensor-core frequency products."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    B = spec.shape[-1]
+    ncell = int(np.prod(c))
+    R = _cvec(x, ncell * B, "x")
+    y = out if out is not None else torch.empty_like(x)
+    check(lib().fmpb_circulant_apply_bf16(_ptr(c), B, _ptr(spec.contiguous()), R, _ptr(x), _ptr(y),
+                                          1 if accumulate else 0, _stream()))
+    return y
+
+
 def kernel_launches() -> int:
     """fmpb_kernel_launches: kernels launched by the library in this process."""
     return int(lib().fmpb_kernel_launches())

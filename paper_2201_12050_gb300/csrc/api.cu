@@ -139,9 +139,13 @@ fmpb_status plan_operator(const double* verts, int64_t nv, const int32_t* tris, 
   int nnear = 1;
   for (int i = 0; i < dim; ++i) nnear *= 3;
   size_t per = 16;   // float-float spectrum
-  if (opts->precision == FMPB_FP32 || opts->precision == FMPB_BF16) per = 8;
-  if (opts->precision == FMPB_MIXED) per = 24;
+  if (opts->precision == FMPB_FP32) per = 8;
+  if (opts->precision == FMPB_MIXED && *form == FMPB_FORM_PBEM) per = 24;
   size_t total = per * (size_t)sh.F * b * b;
+  // realified BF16 spectrum of BF16 operators and of MIXED operators in the FMM form
+  const size_t spec_bf16 = 2 * (size_t)sh.F * tc_rows(b) * tc_depth(b);
+  if (*form == FMPB_FORM_FMM && opts->precision == FMPB_BF16) total = spec_bf16;
+  if (*form == FMPB_FORM_FMM && opts->precision == FMPB_MIXED) total += spec_bf16;
   const size_t tc_bytes = 2 * ((size_t)nnear * tc_rows(n) * tc_depth(n) + (size_t)tc_rows(b) * tc_depth(n) +
                                (size_t)tc_rows(n) * tc_depth(b));
   if (*form == FMPB_FORM_FMM && opts->precision == FMPB_BF16)
@@ -169,7 +173,8 @@ struct fmpb_operator {
   int64_t B = 0;
   int dim = 0;
   cd* spec = nullptr;      // F x B x B, float-float pairs (re_hi, re_lo, im_hi, im_lo) per entry
-  void* spec32 = nullptr;  // F x B x B complex FP32 (FP32 and MIXED operators)
+  void* spec32 = nullptr;  // F x B x B complex FP32 (FP32 operators, MIXED in the PBEM form)
+  __nv_bfloat16* specb = nullptr;  // F x tc_rows(B) x tc_depth(B) realified BF16 (BF16, MIXED FMM)
   int precision = FMPB_FP64;
   cd* S = nullptr;         // n_near x n x n (FMM form), float-float pairs
   int* near_offs = nullptr;
@@ -192,6 +197,7 @@ struct fmpb_operator {
     free_mesh(mesh);
     cudaFree(spec);
     cudaFree(spec32);
+    cudaFree(specb);
     cudaFree(S);
     cudaFree(near_offs);
     cudaFree(V0);
@@ -214,11 +220,11 @@ struct fmpb_operator {
     return FMPB_OK;
   }
 
-  // low: the inner product of a MIXED operator (FP32 spectrum; in the FMM form
-  // also the BF16 tensor-core near field, P2M and L2P)
+  // low: the inner product of a MIXED operator (PBEM form: the FP32 spectrum;
+  // FMM form: the BF16 tensor-core path of BF16 operators)
   fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st, bool low = false) {
     const int64_t Nc = shape.ncells;
-    const bool f32 = precision == FMPB_FP32 || precision == FMPB_BF16 || (precision == FMPB_MIXED && low);
+    const bool f32 = precision == FMPB_FP32 || (precision == FMPB_MIXED && low);
     const cd* sp = f32 ? reinterpret_cast<const cd*>(spec32) : spec;
     const int fmt = f32 ? SPEC_F32 : SPEC_FF;
     if (form == FMPB_FORM_PBEM) {
@@ -235,18 +241,21 @@ struct fmpb_operator {
     if (precision == FMPB_BF16 || (precision == FMPB_MIXED && low)) {
       const int n = mesh.n;
       const size_t xb_elems = (size_t)R * Nc * tc_depth(n), lb_elems = (size_t)R * Nc * tc_depth(B);
-      const size_t extra = (2 * (xb_elems + lb_elems) + sizeof(cd) - 1) / sizeof(cd);
+      const size_t fb_elems = (size_t)shape.F * R * tc_depth(B);
+      const size_t extra = (2 * (xb_elems + lb_elems + fb_elems) + sizeof(cd) - 1) / sizeof(cd);
       FMPB_TRY(ensure_scratch(circ + 2 * mom + extra));
       Mom = scratch + circ;
       Loc = Mom + mom;
       __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(Loc + mom);
       __nv_bfloat16* lb = xb + xb_elems;
+      __nv_bfloat16* fb = lb + lb_elems;
       TcOffsets zero{};
       zero.n = 1;
       FMPB_TRY(tc_rows_to_bf16(x, (int64_t)R * Nc, n, xb, st));
       FMPB_TRY(tc_offset_gemm(Sb, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st));
       FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
-      FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
+      FMPB_TRY(circulant_apply(shape, B, reinterpret_cast<const cd*>(specb), R, Mom, Loc, false, scratch, st,
+                               SPEC_BF16, fb, tc_err));
       FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
       FMPB_TRY(tc_offset_gemm(U0b, zero, n, B, shape.M, R, lb, y, true, tc_err, st));
       return FMPB_OK;
@@ -433,17 +442,25 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     if (s != FMPB_OK) return fail(s);
   }
   op->precision = o.precision;
-  if (o.precision != FMPB_FP64) {
-    const size_t ne = (size_t)sh.F * op->B * op->B;
+  const size_t ne = (size_t)sh.F * op->B * op->B;
+  const bool want32 = o.precision == FMPB_FP32 || (o.precision == FMPB_MIXED && form == FMPB_FORM_PBEM);
+  const bool wantb = o.precision == FMPB_BF16 || (o.precision == FMPB_MIXED && form == FMPB_FORM_FMM);
+  if (want32) {
     s = dev_alloc(reinterpret_cast<float2**>(&op->spec32), ne, op->bytes);
     if (s == FMPB_OK) s = spectrum_ff_to_f32(op->spec, op->spec32, ne, st);
     if (s != FMPB_OK) return fail(s);
-    if (o.precision == FMPB_FP32 || o.precision == FMPB_BF16) {
-      if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "operator_create"));
-      cudaFree(op->spec);
-      op->spec = nullptr;
-      op->bytes -= sizeof(cd) * ne;
-    }
+  }
+  if (wantb) {
+    s = dev_alloc(&op->specb, (size_t)sh.F * tc_rows(op->B) * tc_depth(op->B), op->bytes);
+    if (s == FMPB_OK)
+      s = tc_realify_ff(reinterpret_cast<const float4*>(op->spec), (int)sh.F, op->B, op->B, op->specb, st);
+    if (s != FMPB_OK) return fail(s);
+  }
+  if (o.precision == FMPB_FP32 || o.precision == FMPB_BF16) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "operator_create"));
+    cudaFree(op->spec);
+    op->spec = nullptr;
+    op->bytes -= sizeof(cd) * ne;
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "operator_create"));
@@ -626,6 +643,50 @@ fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int3
   cudaStreamSynchronize(st);
   cudaFree(Ab);
   cudaFree(Xb);
+  cudaFree(err);
+  return s;
+}
+
+fmpb_status fmpb_circulant_apply_bf16(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R,
+                                     const fmpb_c64* x, fmpb_c64* y, int accumulate, void* stream) {
+  CHECK_ARG(counts && spec && x && y && B >= 1 && B <= (1 << 20), "circulant_apply_bf16: bad arguments");
+  CHECK_ARG(R >= 1 && R <= 4096, "circulant_apply_bf16: R out of range");
+  CHECK_ARG((const void*)x != (const void*)y, "circulant_apply_bf16: x and y must not alias");
+  int M[3];
+  for (int a = 0; a < 3; ++a) {
+    CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "circulant_apply_bf16: count out of range");
+    M[a] = counts[a];
+  }
+  const CircShape sh = make_shape(M);
+  CHECK_ARG(sh.F <= 65535, "circulant_apply_bf16: %lld frequencies exceed the launch limit", (long long)sh.F);
+  cudaStream_t st = (cudaStream_t)stream;
+  __nv_bfloat16 *Ab = nullptr, *rows = nullptr;
+  cd* scratch = nullptr;
+  unsigned* err = nullptr;
+  size_t bytes = 0;
+  fmpb_status s = dev_alloc(&Ab, (size_t)sh.F * tc_rows(B) * tc_depth(B), bytes);
+  if (s == FMPB_OK) s = dev_alloc(&rows, (size_t)sh.F * R * tc_depth(B), bytes);
+  if (s == FMPB_OK) s = dev_alloc(&scratch, circulant_scratch_elems(sh, B, R), bytes);
+  if (s == FMPB_OK) s = dev_alloc(&err, 1, bytes);
+  if (s == FMPB_OK && cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "memset");
+  if (s == FMPB_OK) s = tc_realify((const cd*)spec, (int)sh.F, B, B, Ab, st);
+  if (s == FMPB_OK)
+    s = circulant_apply(sh, B, reinterpret_cast<const cd*>(Ab), R, (const cd*)x, (cd*)y, accumulate != 0, scratch,
+                        st, SPEC_BF16, rows, err);
+  unsigned flag = 0;
+  if (s == FMPB_OK && cudaMemcpyAsync(&flag, err, sizeof(flag), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "circulant_apply_bf16");
+  if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "circulant_apply_bf16");
+  if (s == FMPB_OK && flag) {
+    set_error("circulant_apply_bf16: a tensor-core wait gave up");
+    s = FMPB_ECUDA;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(Ab);
+  cudaFree(rows);
+  cudaFree(scratch);
   cudaFree(err);
   return s;
 }

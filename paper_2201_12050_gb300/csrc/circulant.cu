@@ -27,6 +27,7 @@
 #include "internal.cuh"
 #include "profile.cuh"
 #include "ff.cuh"
+#include "tc_gemm.cuh"
 
 namespace fmpb {
 
@@ -492,10 +493,20 @@ static fmpb_status launch_block_product_tiled(const void* spec, const float4* X,
 }
 
 static fmpb_status block_product(const void* spec, int spec_format, const float4* X, float4* Y, int64_t F,
-                                 int64_t B, int R, cudaStream_t st) {
+                                 int64_t B, int R, cudaStream_t st, void* tc_rows, unsigned* tc_err) {
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
     return FMPB_EINVAL;
+  }
+  // BF16 spectrum: every frequency's product on the tensor cores
+  if (spec_format == SPEC_BF16) {
+    if (!tc_rows || !tc_err) {
+      set_error("block_product: BF16 spectrum without tensor-core scratch");
+      return FMPB_EINVAL;
+    }
+    __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tc_rows);
+    FMPB_TRY(tc_rows_from_ff(X, F * R, B, rows, st));
+    return tc_freq_gemm(reinterpret_cast<const __nv_bfloat16*>(spec), F, B, R, rows, Y, tc_err, st);
   }
   // many right-hand sides: one tiled pass over the spectrum
   if (R >= 8 && spec_format == SPEC_FF) return launch_block_product_tiled<true>(spec, X, Y, F, B, R, st);
@@ -524,7 +535,8 @@ static fmpb_status block_product(const void* spec, int spec_format, const float4
 size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 * (size_t)s.F * R * B; }
 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
-                            bool accumulate, cd* scratch, cudaStream_t st, int spec_format) {
+                            bool accumulate, cd* scratch, cudaStream_t st, int spec_format, void* tc_rows,
+                            unsigned* tc_err) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
@@ -550,7 +562,7 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
     cur = 1 - cur;
   }
   // per-frequency block products: [f][r][b] -> [f][r][b]
-  FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st));
+  FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st, tc_rows, tc_err));
   cur = 1 - cur;
   // inverse z: [fz][fy fx][rb] -> [cz][fy fx][rb], cz < Mz
   if (Pz > 1) {

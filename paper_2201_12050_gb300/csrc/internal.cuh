@@ -87,9 +87,13 @@ fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaSt
 // Storage formats of a spectrum: complex double, float-float pairs (16 bytes,
 // FP64-class accuracy) or complex FP32 (8 bytes, the low-precision half of the
 // mixed-precision operator).
-enum SpecFormat { SPEC_CD = 0, SPEC_FF = 1, SPEC_F32 = 2 };
+// SPEC_BF16: the spectrum as realified BF16 tiles (tc_realify_ff layout),
+// applied on the tensor cores; needs tc_rows (F R tc_depth(B) BF16 values of
+// scratch) and the error word tc_err of the tensor-core kernels.
+enum SpecFormat { SPEC_CD = 0, SPEC_FF = 1, SPEC_F32 = 2, SPEC_BF16 = 3 };
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
-                            bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD);
+                            bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD,
+                            void* tc_rows = nullptr, unsigned* tc_err = nullptr);
 // float-float spectrum -> complex FP32 (out has n float2 entries)
 fmpb_status spectrum_ff_to_f32(const cd* in, void* out, size_t n, cudaStream_t st);
 // In-place conversion of n complex doubles to float-float pairs (re_hi, re_lo, im_hi, im_lo).

@@ -13,8 +13,13 @@
 // representation [[re, -im], [im, re]], so one real GEMM of twice the size
 // gives real and imaginary parts in adjacent accumulator rows.
 //
-// Kernel structure (one CTA per 128 x 256 output tile, 256 threads):
-//   - all threads stage A (128 x 64) and B (256 x 64) tiles with cp.async into
+// The per-frequency block products of the circulant engine (Sec. 2.4:
+// Y_f = Lambda_f X_f for every padded-grid frequency f) are the other dense
+// complex GEMMs of the method once many right-hand sides share the spectrum;
+// the same kernel runs them with A = Lambda_f chosen by the frequency.
+//
+// Kernel structure (one CTA per 128 x BN output tile, BN = 32..256, 256 threads):
+//   - all threads stage A (128 x 64) and B (BN x 64) tiles with cp.async into
 //     a 4-deep ring of shared-memory stages, in the no-swizzle K-major layout
 //     of 8-row x 16-byte core matrices; B rows of source cells outside the
 //     grid are zero-filled by the copy itself (source size 0);
@@ -39,15 +44,22 @@ namespace fmpb {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BN = 256;
 constexpr int TC_BK = 64;
 constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 256;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
-constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;
-constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr int TC_BAR_BYTES = 64;   // TC_STAGES mbarriers + the tensor-memory address
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + TC_BAR_BYTES;
+template <int BN>
+struct TcTile {
+  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
+  static constexpr int SMEM = TC_STAGES * STAGE_BYTES + TC_BAR_BYTES;
+  // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A
+  // and B in BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
+  // N / 8 in bits 17-22, M / 16 in bits 24-28.
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+};
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;
 
 // Core-matrix strides of the no-swizzle K-major layout: the 16-byte rows of
@@ -55,12 +67,6 @@ constexpr uint64_t TC_WAIT_NS = 1000000000ull;
 // K are 128 bytes apart and those adjacent in M (or N) TC_BK / 8 * 128 bytes.
 constexpr uint32_t TC_LBO = 128;
 constexpr uint32_t TC_SBO = (TC_BK / 8) * 128;
-
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
-// B in BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N / 8 in bits 17-22, M / 16 in bits 24-28.
-constexpr uint32_t TC_IDESC =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -123,12 +129,13 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// D (tensor memory) = A B (+ D if accumulate), one 128 x 256 x 16 step.
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+// D (tensor memory) = A B (+ D if accumulate), one 128 x N x 16 step.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 // The mbarrier receives one arrival when all MMAs issued so far by this thread have completed.
@@ -150,17 +157,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two ways of choosing the operands of one output tile:
+//   OFFSET: columns j = r Nc + c (rhs r, cell c), A_o shared by all columns,
+//           B row of column j for offset o = x row of the source cell
+//           c - delta_o (zero outside the grid); K runs over offsets x depth.
+//   FREQ:   blockIdx.y = frequency f with its own A_f, columns j = r < R,
+//           B row of column j = x row f R + r; K runs over the depth.
+template <int BN, bool FREQ>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_offset_gemm(const __nv_bfloat16* __restrict__ A, int64_t a_stride, int Kp,
-                     const __nv_bfloat16* __restrict__ X, cd* __restrict__ y, int m, int64_t ncols, int Mx, int My,
-                     int Mz, TcOffsets offs, int accumulate, unsigned* err) {
+    k_tc_gemm(const __nv_bfloat16* __restrict__ A, int64_t a_stride, int Kp, const __nv_bfloat16* __restrict__ X,
+              void* __restrict__ y_, int m, int64_t ncols, int Mx, int My, int Mz, TcOffsets offs, int accumulate,
+              unsigned* err) {
+  using Tile = TcTile<BN>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * Tile::STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * TC_BM;
-  const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
+  const int64_t n0 = (int64_t)(FREQ ? blockIdx.z : blockIdx.y) * BN;
+  const int64_t f = FREQ ? (int64_t)blockIdx.y : 0;
   const int Nc = Mx * My * Mz;
 
   if (tid == 0) {
@@ -168,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
-    tmem_alloc(smem_u32(tmem_slot), TC_BN);
+    tmem_alloc(smem_u32(tmem_slot), BN);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -180,37 +196,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // at byte 16 q, i.e. row ((q >> 6) << 3) + (q & 7) and K chunk (q >> 3) & 7.
   const int kc = (tid >> 3) & 7;
   const int rlo = (tid >> 6) * 8 + (tid & 7);   // row for t = 0; t adds 32 rows
-  // B rows: column j = n0 + row of the output; its cell coordinates
-  int64_t bj[TC_BN / 32];
-  int bx[TC_BN / 32], by[TC_BN / 32], bz[TC_BN / 32];
+  constexpr int NB = BN / 32;                   // B chunks per thread and stage
+  int64_t bj[NB];
+  int bx[NB], by[NB], bz[NB];
 #pragma unroll
-  for (int t = 0; t < TC_BN / 32; ++t) {
+  for (int t = 0; t < NB; ++t) {
     const int64_t j = n0 + rlo + 32 * t;
     bj[t] = j < ncols ? j : -1;
-    const int c = (int)(j % Nc);
+    const int c = FREQ ? 0 : (int)(j % Nc);
     bx[t] = c % Mx;
     by[t] = (c / Mx) % My;
     bz[t] = c / (Mx * My);
   }
   const int kt_per_off = Kp / TC_BK;
-  const int KT = offs.n * kt_per_off;
+  const int KT = (FREQ ? 1 : offs.n) * kt_per_off;
+  const __nv_bfloat16* Af = A + f * a_stride;
 
   auto load_stage = [&](int it, int s) {
-    const int o = it / kt_per_off;
+    const int o = FREQ ? 0 : it / kt_per_off;
     const int k0 = (it - o * kt_per_off) * TC_BK + kc * 8;
-    const int dx = offs.d[o][0], dy = offs.d[o][1], dz = offs.d[o][2];
-    const int64_t dlin = ((int64_t)dz * My + dy) * Mx + dx;
-    const uint32_t sa = sbase + s * TC_STAGE_BYTES + tid * 16;
+    const uint32_t sa = sbase + s * Tile::STAGE_BYTES + tid * 16;
     const uint32_t sb = sa + TC_A_BYTES;
-    const __nv_bfloat16* arow = A + o * a_stride + (int64_t)(m0 + rlo) * Kp + k0;
+    const __nv_bfloat16* arow = Af + o * a_stride + (int64_t)(m0 + rlo) * Kp + k0;
 #pragma unroll
     for (int t = 0; t < TC_BM / 32; ++t) cp_async16(sa + t * 4096, arow + (int64_t)(32 * t) * Kp, 16);
+    if (FREQ) {
 #pragma unroll
-    for (int t = 0; t < TC_BN / 32; ++t) {
-      const int sx = bx[t] - dx, sy = by[t] - dy, sz = bz[t] - dz;
-      const bool ok = bj[t] >= 0 && sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz;
-      const __nv_bfloat16* src = ok ? X + (bj[t] - dlin) * Kp + k0 : X;
-      cp_async16(sb + t * 4096, src, ok ? 16 : 0);
+      for (int t = 0; t < NB; ++t) {
+        const bool ok = bj[t] >= 0;
+        cp_async16(sb + t * 4096, ok ? X + (f * ncols + bj[t]) * Kp + k0 : X, ok ? 16 : 0);
+      }
+    } else {
+      const int dx = offs.d[o][0], dy = offs.d[o][1], dz = offs.d[o][2];
+      const int64_t dlin = ((int64_t)dz * My + dy) * Mx + dx;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const int sx = bx[t] - dx, sy = by[t] - dy, sz = bz[t] - dz;
+        const bool ok = bj[t] >= 0 && sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz;
+        const __nv_bfloat16* src = ok ? X + (bj[t] - dlin) * Kp + k0 : X;
+        cp_async16(sb + t * 4096, src, ok ? 16 : 0);
+      }
     }
   };
 
@@ -229,9 +254,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (__syncthreads_or(bad)) break;
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = sbase + s * TC_STAGE_BYTES, b0 = a0 + TC_A_BYTES;
+      const uint32_t a0 = sbase + s * Tile::STAGE_BYTES, b0 = a0 + TC_A_BYTES;
 #pragma unroll
-      for (int q = 0; q < TC_BK / 16; ++q) tc_mma(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), (kt | q) != 0);
+      for (int q = 0; q < TC_BK / 16; ++q)
+        tc_mma(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), Tile::IDESC, (kt | q) != 0);
       tc_commit(smem_u32(&bars[s]));
     }
     const int nk = kt + TC_STAGES - 1;
@@ -256,9 +282,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool row_ok = gm < 2 * (int64_t)m;
     const int64_t i = gm >> 1;
     const int part = (int)(gm & 1);
-    const int cbase = (warp >> 2) * (TC_BN / 2);
+    const int cbase = (warp >> 2) * (BN / 2);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN / 2; c0 += 16) {
+    for (int c0 = 0; c0 < BN / 2; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + c0), v);
       if (row_ok) {
@@ -266,8 +292,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = 0; t < 16; ++t) {
           const int64_t j = n0 + cbase + c0 + t;
           if (j < ncols) {
-            double* d = reinterpret_cast<double*>(y + j * m + i) + part;
-            *d = accumulate ? *d + (double)v[t] : (double)v[t];
+            if (FREQ) {
+              // float-float output (hi = FP32 sum, lo = 0), the circulant scratch format
+              float2* d = reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ncols + j) * m + i) + part;
+              *d = make_float2(v[t], 0.f);
+            } else {
+              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + j * m + i) + part;
+              *d = accumulate ? *d + (double)v[t] : (double)v[t];
+            }
           }
         }
       }
@@ -275,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TC_BN);
+  if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
 __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) { return __float2bfloat16_rn(__double2float_rn(v)); }
@@ -314,6 +346,59 @@ __global__ void k_tc_rows_to_bf16(const cd* __restrict__ x, int64_t k, int64_t K
   X[idx] = p;
 }
 
+// Float-float (float4: re_hi, re_lo, im_hi, im_lo) sources: the value is
+// hi + lo, whose FP32 rounding is hi for normalised pairs.
+__device__ __forceinline__ __nv_bfloat16 ff_to_bf16(float hi, float lo) {
+  return __float2bfloat16_rn(__double2float_rn((double)hi + (double)lo));
+}
+
+__global__ void k_tc_realify_ff(const float4* __restrict__ T, int64_t m, int64_t k, int64_t Mh, int64_t Kh,
+                                int64_t total, __nv_bfloat162* __restrict__ A) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t per = Mh * Kh;
+  const int64_t o = idx / per, rem = idx - o * per;
+  const int64_t i = rem / Kh, j = rem - i * Kh;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < m && j < k) v = T[(o * m + i) * k + j];
+  const __nv_bfloat16 re = ff_to_bf16(v.x, v.y), im = ff_to_bf16(v.z, v.w), nim = ff_to_bf16(-v.z, -v.w);
+  __nv_bfloat162* base = A + o * (2 * Mh) * Kh;
+  __nv_bfloat162 top, bot;
+  top.x = re;
+  top.y = nim;
+  bot.x = im;
+  bot.y = re;
+  base[(2 * i) * Kh + j] = top;
+  base[(2 * i + 1) * Kh + j] = bot;
+}
+
+__global__ void k_tc_rows_from_ff(const float4* __restrict__ x, int64_t k, int64_t Kh, int64_t total,
+                                  __nv_bfloat162* __restrict__ X) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t rho = idx / Kh, j = idx - rho * Kh;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (j < k) v = x[rho * k + j];
+  __nv_bfloat162 p;
+  p.x = ff_to_bf16(v.x, v.y);
+  p.y = ff_to_bf16(v.z, v.w);
+  X[idx] = p;
+}
+
+template <int BN, bool FREQ>
+fmpb_status launch_tc(dim3 grid, const __nv_bfloat16* A, int64_t a_stride, int64_t Kp, const __nv_bfloat16* X,
+                      void* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs, bool accumulate,
+                      unsigned* err, cudaStream_t st) {
+  using Tile = TcTile<BN>;
+  FMPB_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, FREQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile::SMEM));
+  FMPB_LAUNCH(FREQ ? "tc_block_product" : "tc_gemm", st,
+              (k_tc_gemm<BN, FREQ><<<grid, TC_THREADS, Tile::SMEM, st>>>(A, a_stride, (int)Kp, X, y, (int)m, ncols,
+                                                                          M[0], M[1], M[2], offs,
+                                                                          accumulate ? 1 : 0, err)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 }  // namespace
 
 fmpb_status tc_realify(const cd* T, int n_off, int64_t m, int64_t k, __nv_bfloat16* A, cudaStream_t st) {
@@ -337,6 +422,27 @@ fmpb_status tc_rows_to_bf16(const cd* x, int64_t rows, int64_t k, __nv_bfloat16*
   return FMPB_OK;
 }
 
+fmpb_status tc_realify_ff(const float4* T, int n_off, int64_t m, int64_t k, __nv_bfloat16* A, cudaStream_t st) {
+  const int64_t Mh = tc_rows(m) / 2, Kh = tc_depth(k) / 2;
+  const int64_t total = (int64_t)n_off * Mh * Kh;
+  FMPB_LAUNCH("tc_realify", st,
+              k_tc_realify_ff<<<grid_for((size_t)total, 256), 256, 0, st>>>(T, m, k, Mh, Kh, total,
+                                                                             reinterpret_cast<__nv_bfloat162*>(A)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+fmpb_status tc_rows_from_ff(const float4* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
+  const int64_t Kh = tc_depth(k) / 2;
+  const int64_t total = rows * Kh;
+  if (total == 0) return FMPB_OK;
+  FMPB_LAUNCH("tc_to_bf16", st,
+              k_tc_rows_from_ff<<<grid_for((size_t)total, 256), 256, 0, st>>>(
+                  x, k, Kh, total, reinterpret_cast<__nv_bfloat162*>(X)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
                            const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st) {
   const int64_t Mp = tc_rows(m), Kp = tc_depth(k);
@@ -346,18 +452,37 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
     set_error("tc_offset_gemm: bad shape (offsets %d, m %lld, k %lld, R %d)", offs.n, (long long)m, (long long)k, R);
     return FMPB_EINVAL;
   }
-  const int64_t ntiles = (ncols + TC_BN - 1) / TC_BN;
-  if (ntiles > 65535 || Kp > (1 << 24) || Nc > (1 << 30)) {
+  constexpr int BN = 256;
+  const int64_t ntiles = (ncols + BN - 1) / BN;
+  if (ntiles > 65535 || Mp / TC_BM > 65535 || Kp > (1 << 24) || Nc > (1 << 30)) {
     set_error("tc_offset_gemm: %lld columns exceed the launch limit", (long long)ncols);
     return FMPB_EINVAL;
   }
-  FMPB_CUDA(cudaFuncSetAttribute(k_tc_offset_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   dim3 grid((unsigned)(Mp / TC_BM), (unsigned)ntiles);
-  FMPB_LAUNCH("tc_gemm", st,
-              k_tc_offset_gemm<<<grid, TC_THREADS, TC_SMEM, st>>>(A, Mp * Kp, (int)Kp, X, y, (int)m, ncols, M[0],
-                                                                  M[1], M[2], offs, accumulate ? 1 : 0, err));
-  FMPB_CUDA(cudaGetLastError());
-  return FMPB_OK;
+  return launch_tc<BN, false>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+}
+
+fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, float4* Y,
+                         unsigned* err, cudaStream_t st) {
+  const int64_t Mp = tc_rows(B), Kp = tc_depth(B);
+  if (F < 1 || F > 65535 || B < 1 || R < 1 || Mp / TC_BM > 65535 || Kp > (1 << 24)) {
+    set_error("tc_freq_gemm: bad shape (F %lld, B %lld, R %d)", (long long)F, (long long)B, R);
+    return FMPB_EINVAL;
+  }
+  const TcOffsets none{};
+  const int M[3] = {1, 1, 1};
+  const int BN = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
+  dim3 grid((unsigned)(Mp / TC_BM), (unsigned)F, (unsigned)((R + BN - 1) / BN));
+  if (grid.z > 65535) {
+    set_error("tc_freq_gemm: too many right-hand sides");
+    return FMPB_EINVAL;
+  }
+  switch (BN) {
+    case 32: return launch_tc<32, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    case 64: return launch_tc<64, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    case 128: return launch_tc<128, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    default: return launch_tc<256, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+  }
 }
 
 }  // namespace fmpb

@@ -8,6 +8,12 @@ terms (K <= 6,000 below, so 1e-5 in the L2 norm is a safe bound).  The
 rounding is emulated bit-exactly on the host (round-to-nearest-even on the
 FP32 bit pattern).
 
+fmpb_circulant_apply_bf16 runs the per-frequency products Lambda_f X_f of the
+circulant engine on the tensor cores; it is pinned against numpy's FFT of the
+zero-padded grid, the same BF16 rounding of Lambda_f and X_f, the FP64
+product and the inverse FFT with crop (an arbitrary spectrum defines a valid
+circulant product, so random spectra serve).
+
 The BF16 operator is checked against the oracle's explicit FMM operator:
 two roundings of relative size <= 2^-8 per product term give a product
 error of a few 1e-3, so the bound is 1e-2 (and at least 1e-4, to show the
@@ -105,6 +111,25 @@ def test_offset_gemm_accumulates_and_skips_cells_outside_the_grid():
     assert _rel(y, ref) < 1e-5
     only_outside = gb.offset_gemm_bf16(counts, [(4, 0, 0)], _dev(T[:1]), _dev(x)).cpu().numpy()
     assert np.abs(only_outside).max() == 0.0
+
+
+@pytest.mark.parametrize("counts,B,R", [((3, 4, 1), 40, 70), ((2, 3, 2), 81, 5), ((5, 1, 1), 169, 64),
+                                          ((2, 2, 1), 30, 300)])
+def test_circulant_bf16_equals_rounded_frequency_products(counts, B, R):
+    rng = np.random.default_rng(B + R)
+    P, F = gb.circulant_shape(counts)
+    Mx, My, Mz = counts
+    Px, Py, Pz = P
+    spec = rng.standard_normal((F, B, B)) + 1j * rng.standard_normal((F, B, B))
+    x = random_complex_vectors(B + R, R, Mx * My * Mz * B)
+    y = gb.circulant_apply_bf16(counts, _dev(spec), _dev(x)).cpu().numpy()
+    xg = np.zeros((R, Pz, Py, Px, B), dtype=np.complex128)
+    xg[:, :Mz, :My, :Mx, :] = x.reshape(R, Mz, My, Mx, B)
+    X = np.fft.fftn(xg, axes=(1, 2, 3)).reshape(R, F, B)
+    Yf = np.einsum("fij,rfj->rfi", _cbf16(spec), _cbf16(X))
+    ref = np.fft.ifftn(Yf.reshape(R, Pz, Py, Px, B), axes=(1, 2, 3))[:, :Mz, :My, :Mx, :].reshape(R, -1)
+    err = _rel(y, ref)
+    assert err < 1e-5, err
 
 
 @pytest.mark.parametrize("name,level,nt,counts", [
