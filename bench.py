@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-case", default=None, choices=["product", "build", "near", "batch"],
                     help="small case for kernel captures: product/build = 3x8 cylinders (1.8 GB spectrum) at "
-                         "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, FP32")
+                         "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, BF16")
     ap.add_argument("--only-headline", action="store_true",
                     help="skip the FMM, mixed-precision, serving and batching sections")
     return ap.parse_args()
@@ -295,53 +295,130 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _near_pairs(M):
+    """Target/source cell pairs of the 3^d near stencil on an M grid."""
+    pairs = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if (M[2] == 1 and dz) or (M[1] == 1 and dy):
+                    continue
+                pairs += max(0, M[0] - abs(dx)) * max(0, M[1] - abs(dy)) * max(0, M[2] - abs(dz))
+    return pairs
+
+
+def _tc_rows(m):
+    return (2 * m + 127) // 128 * 128
+
+
+def _tc_depth(k):
+    return (2 * k + 63) // 64 * 64
+
+
 def batching_section(gb, torch, stream, freq_index=3, n_t=12):
     """Batched right-hand sides on the 3-D cube lattice: 16 x 16 x 4 rigid cubes
-    (432 triangles each, N = 442,368), FMM form, FP32 operator, the 64
-    spherical-Fibonacci incidence directions solved as one 64-RHS GMRES(30)
-    at one frequency of the 200-1600 Hz sweep (the full workload repeats this
-    for 8 frequencies).  Reports the 64-RHS product and the solve."""
+    (432 triangles each, N = 442,368), FMM form, the 64 spherical-Fibonacci
+    incidence directions solved as one 64-RHS GMRES(30) at one frequency of the
+    200-1600 Hz sweep (the full workload repeats this for 8 frequencies).
+
+    The batched forms run on the tensor cores: the BF16 operator (near field,
+    P2M, L2P and the per-frequency M2L products as BF16 x BF16 -> FP32 tcgen05
+    GEMMs) solved to 1e-3, and the MIXED operator (the same BF16 products in
+    the inner GMRES, float-float outer residuals) solved to 1e-5.  The FP32 and
+    FP64 (float-float) 64-RHS products are timed beside them; a 64-RHS FP64
+    solve is not run (about 466 x 0.62 s)."""
     w = WORKLOADS["cube_lattice_16x16x4"]
     v, t = w.mesh()
     k = w.wavenumbers[freq_index]
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    b0, b1 = ev(), ev()
-    b0.record(stream)
-    op = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM, n_t=n_t, precision=gb.FP32)
-    b1.record(stream)
-    torch.cuda.synchronize()
-    build_ms = b0.elapsed_time(b1)
     R = len(w.directions)
-    b = op.rhs_plane_wave(w.directions)
-    y = torch.empty_like(b)
-    op.matvec(b, out=y)
-    torch.cuda.synchronize()
-    gb.profile_reset()
-    gb.profile_enable(True)
-    m0, m1 = ev(), ev()
-    m0.record(stream)
-    for _ in range(3):
+    n = len(t)
+    peaks = measured_peaks()
+
+    def build(prec):
+        torch.cuda.synchronize()
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        op = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM, n_t=n_t, precision=prec)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        return op, b0.elapsed_time(b1)
+
+    def products(op, b, reps):
+        y = torch.empty_like(b)
         op.matvec(b, out=y)
-    m1.record(stream)
-    torch.cuda.synchronize()
-    gb.profile_enable(False)
-    mv_ms = m0.elapsed_time(m1) / 3
-    prof = gb.profile_summary()
-    s0, s1 = ev(), ev()
-    s0.record(stream)
-    p, info = op.solve(b, tol=1e-5, restart=30, maxit=2000, raise_on_noconv=False)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    solve_ms = s0.elapsed_time(s1)
-    out = {"workload": f"cube_lattice_16x16x4: N={op.N}, FMM form n_t={n_t} (B={op.info['B']}, P={op.info['P']}), "
-                       f"FP32 operator, {R} RHS at {k * SPEED_OF_SOUND / (2 * math.pi):.0f} Hz, GMRES(30) tol 1e-5",
-           "build_ms": build_ms, "matvec_64rhs_ms": mv_ms, "rhs_products_per_s": R * 1e3 / mv_ms,
-           "matvec_kernels_ms": {k_: v_[1] / 3 for k_, v_ in prof.items()},
-           "solve_ms": solve_ms, "solves_per_s_incl_build": R * 1e3 / (solve_ms + build_ms),
-           "iters_max": max(i["iters"] for i in info), "relres_true_max": max(i["relres_true"] for i in info),
-           "operator_bytes": op.info["bytes_device"]}
+        torch.cuda.synchronize()
+        gb.profile_reset()
+        gb.profile_enable(True)
+        m0, m1 = ev(), ev()
+        m0.record(stream)
+        for _ in range(reps):
+            op.matvec(b, out=y)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        gb.profile_enable(False)
+        return m0.elapsed_time(m1) / reps, {k_: v_[1] / reps for k_, v_ in gb.profile_summary().items()}, \
+            {k_: v_ for k_, v_ in gb.profile_summary().items()}
+
+    def solve(op, b, **kw):
+        s0, s1 = ev(), ev()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        p, info = op.solve(b, raise_on_noconv=False, **kw)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        op.check()
+        return s0.elapsed_time(s1), p, info
+
+    out = {"workload": f"cube_lattice_16x16x4: N={16 * 16 * 4 * n}, FMM form n_t={n_t}, {R} RHS at "
+                       f"{k * SPEED_OF_SOUND / (2 * math.pi):.0f} Hz, GMRES(30)"}
+    # BF16 tensor-core operator
+    op, build_ms = build(gb.BF16)
+    B = op.info["B"]
+    b = op.rhs_plane_wave(w.directions)
+    mv_ms, kern, raw = products(op, b, 3)
+    nc = int(np.prod(w.counts))
+    pairs = _near_pairs(w.counts)
+    near_alg = 8.0 * pairs * n * n * R                       # complex MACs of the near field x 8
+    issued = 2.0 * (_tc_rows(n) * _tc_depth(n) * 27 + _tc_rows(B) * _tc_depth(n) + _tc_rows(n) * _tc_depth(B)) * nc * R
+    tc_launches, tc_ms = raw.get("tc_gemm", (3, float("nan")))
+    bp_launches, bp_ms = raw.get("tc_block_product", (3, float("nan")))
+    F = op.info["F"]
+    bp_issued = 2.0 * _tc_rows(B) * _tc_depth(B) * F * max(R, 32)
+    s_ms, pb, info = solve(op, b, tol=1e-3, restart=30, maxit=2000)
+    bf16_peak = peaks.get("bf16_tflops") or 1900.0
+    out["bf16"] = {"build_ms": build_ms, "matvec_64rhs_ms": mv_ms, "rhs_products_per_s": R * 1e3 / mv_ms,
+                   "matvec_kernels_ms": kern,
+                   "tc_gemm": {"ms_per_matvec": tc_ms / 3, "launches_per_matvec": tc_launches / 3, "issued_tflops":
+                               issued / (tc_ms / 3 / 1e3) / 1e12, "near_algorithmic_tflops":
+                               near_alg / (tc_ms / 3 / 1e3) / 1e12, "peak_bf16_tflops": bf16_peak,
+                               "frac_issued": issued / (tc_ms / 3 / 1e3) / 1e12 / bf16_peak,
+                               "peak_source": "measured bf16_tflops" if peaks.get("bf16_tflops") else "fallback"},
+                   "tc_block_product": {"ms_per_matvec": bp_ms / 3,
+                                        "issued_tflops": bp_issued / (bp_ms / 3 / 1e3) / 1e12,
+                                        "spectrum_bytes": 2 * F * _tc_rows(B) * _tc_depth(B)},
+                   "solve_tol1e-3": {"ms": s_ms, "solves_per_s_incl_build": R * 1e3 / (s_ms + build_ms),
+                                     "iters_max": max(i["iters"] for i in info),
+                                     "relres_true_max": max(i["relres_true"] for i in info)},
+                   "operator_bytes": op.info["bytes_device"]}
     op.close()
+    # MIXED: BF16 inner products, float-float outer residuals
+    op, build_ms = build(gb.MIXED)
+    s_ms, pm, info = solve(op, b, tol=1e-5, restart=30, maxit=3000, inner_tol=1e-2)
+    out["mixed"] = {"build_ms": build_ms, "solve_tol1e-5": {
+        "ms": s_ms, "solves_per_s_incl_build": R * 1e3 / (s_ms + build_ms),
+        "iters_max": max(i["iters"] for i in info), "refinements_max": max(i["refinements"] for i in info),
+        "relres_true_max": max(i["relres_true"] for i in info)}, "operator_bytes": op.info["bytes_device"]}
+    out["bf16"]["solve_tol1e-3"]["rel_err_vs_mixed_solution"] = float(
+        torch.linalg.vector_norm(pb - pm) / torch.linalg.vector_norm(pm))
+    op.close()
+    # FP32 and FP64 (float-float) products of the same 64 right-hand sides
+    for name, prec, reps in (("fp32", gb.FP32, 2), ("fp64", gb.FP64, 1)):
+        op, build_ms = build(prec)
+        mv_ms, kern, _ = products(op, b, reps)
+        out[name] = {"build_ms": build_ms, "matvec_64rhs_ms": mv_ms, "matvec_kernels_ms": kern}
+        op.close()
+    out["speedup_bf16_product_vs_fp64"] = out["fp64"]["matvec_64rhs_ms"] / out["bf16"]["matvec_64rhs_ms"]
     return out
 
 
@@ -472,7 +549,65 @@ def fmm_section(gb, torch, stream):
            "solve": {"ms": solve_ms, "iters": info[0]["iters"], "relres_true": info[0]["relres_true"],
                      "solves_per_s_incl_build": 1e3 / (solve_ms + build_ms)},
            "operator_bytes": op.info["bytes_device"]}
+    out["precision"] = precision_section(gb, torch, stream, w, v, t, k, op, x, y, p, solve_ms, build_ms)
     op.close()
+    return out
+
+
+def precision_section(gb, torch, stream, w, v, t, k, op64, x, y64, p64, fp64_solve_ms, fp64_build_ms):
+    """The 32 x 32 sphere array in every precision of the library, against the
+    FP64 (float-float) operator, whose products match the FP64 oracle to 1e-12:
+    FP32 (near field, P2M, L2P and M2L spectrum in complex FP32), BF16 (all of
+    them as BF16 x BF16 -> FP32 tensor-core GEMMs) and MIXED (GMRES-IR: BF16
+    inner solves, float-float outer residuals).  Products at 1 and 16
+    right-hand sides; solves of the +x plane wave, errors relative (L2) to the
+    FP64 solution at 1e-8."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    x16 = torch.as_tensor(random_complex_vectors(w.rhs_seed + 1, 16, op64.N), device="cuda")
+    y16 = op64.matvec(x16)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, c = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            r = fn()
+        c.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(c) / reps, r
+
+    out = {"fp64": {"matvec_ms_R1": timed(lambda: op64.matvec(x), 5)[0],
+                    "matvec_ms_R16": timed(lambda: op64.matvec(x16), 3)[0],
+                    "solve_tol1e-8": {"ms": fp64_solve_ms, "solves_per_s_incl_build":
+                                      1e3 / (fp64_solve_ms + fp64_build_ms)}}}
+    b = op64.rhs_plane_wave(w.directions)
+    for name, prec, tol, inner in (("fp32", gb.FP32, 1e-5, 0.0), ("bf16", gb.BF16, 1e-3, 0.0),
+                                   ("mixed", gb.MIXED, 1e-8, 1e-2)):
+        torch.cuda.synchronize()
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        op = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM, n_t=w.n_t, precision=prec)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        build_ms = b0.elapsed_time(b1)
+        r = {"build_ms": build_ms}
+        if prec != gb.MIXED:
+            ms1, y1 = timed(lambda: op.matvec(x), 5)
+            ms16, yy = timed(lambda: op.matvec(x16), 3)
+            r.update({"matvec_ms_R1": ms1, "matvec_ms_R16": ms16, "product_rel_err_vs_fp64": max(rel(y1, y64),
+                                                                                                   rel(yy, y16))})
+        op.solve(b, tol=tol, restart=RESTART, maxit=MAXIT, raise_on_noconv=False, inner_tol=inner)
+        ms, (p, info) = timed(lambda: op.solve(b, tol=tol, restart=RESTART, maxit=MAXIT, raise_on_noconv=False,
+                                               inner_tol=inner), 2)
+        op.check()
+        r[f"solve_tol{tol:.0e}"] = {"ms": ms, "solves_per_s_incl_build": 1e3 / (ms + build_ms),
+                                   "iters": info[0]["iters"], "refinements": info[0]["refinements"],
+                                   "relres_true": info[0]["relres_true"], "rel_err_vs_fp64_solution": rel(p, p64),
+                                   "speedup_vs_fp64_solve": (fp64_solve_ms + fp64_build_ms) / (ms + build_ms)}
+        out[name] = r
+        op.close()
     return out
 
 
@@ -611,8 +746,8 @@ def run_profile_case(args):
     """Small cases for kernel captures (inputs larger than L2, a few GB at most):
     product/build: 3 x 8 cylinders at 500 Hz (PBEM, spectrum 1.84 GB), one build
     and 4 products; near: the 32 x 32 sphere array (FMM form), one build and 3
-    products; batch: 8 x 8 x 4 cubes, FP32 FMM operator, 3 products of 64
-    right-hand sides.  Prints one JSON line."""
+    products; batch: 8 x 8 x 4 cubes, BF16 (tensor-core) FMM operator, 3 products
+    of 64 right-hand sides.  Prints one JSON line."""
     import torch
     import paper_2201_12050_gb300 as gb
     if args.profile_case in ("near", "batch"):
@@ -625,7 +760,7 @@ def run_profile_case(args):
             w2 = WORKLOADS["cube_lattice_16x16x4"]
             v2, t2 = w2.mesh()
             op = gb.Operator(v2, t2, (8, 8, 4), w2.lattice, w2.wavenumbers[3], form=gb.FORM_FMM, n_t=12,
-                             precision=gb.FP32)
+                             precision=gb.BF16)
             x = op.rhs_plane_wave(w2.directions)
         y = torch.empty_like(x)
         for _ in range(3):
