@@ -170,7 +170,7 @@ fmpb_status fmpb_matvec(const fmpb_operator *op, int R, const fmpb_c64 *x, fmpb_
 
 typedef struct {
   double tol;        /* relative residual ||b - A p|| / ||b||; <= 0 selects 1e-8 */
-  int restart;       /* GMRES restart length m, 1..200; 0 selects 30 */
+  int restart;       /* GMRES restart length m, 1..1000; 0 selects 30 */
   int maxit;         /* total iteration cap per RHS; 0 selects 1000 */
   int timeout_ms;    /* wall-clock cap for the whole call; 0 = none */
   double inner_tol;  /* MIXED operators: relative tolerance of each inner FP32

@@ -20,7 +20,7 @@ namespace fmpb {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 64;   // upper bound on partial sums per (vector, rhs)
-constexpr int MAX_RESTART = 200;
+constexpr int MAX_RESTART = 1000;
 
 // partial[(v*R + r)*gridDim.x + blk] = sum over the block's rows of
 // conj(V_v[r]) w[r]; four independent accumulators per thread keep several
@@ -77,6 +77,24 @@ __global__ void k_reduce_partials(const cd* __restrict__ partial, int nblk, int 
   out[t] = accumulate ? cadd(out[t], s) : s;
 }
 
+// The same sums with one warp per output, for long partial lists: lane l
+// adds partials l, l + 32, ..., then a fixed shuffle tree (deterministic).
+__global__ void k_reduce_partials_warp(const cd* __restrict__ partial, int nblk, int count, cd* __restrict__ out) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= count) return;
+  double re = 0.0, im = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    const cd v = partial[(int64_t)t * nblk + b];
+    re += v.x;
+    im += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) out[t] = mkc(re, im);
+}
+
 // y = b - y  (residual from a product)
 __global__ void k_residual(const cd* __restrict__ b, cd* __restrict__ y, int64_t total) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
@@ -95,6 +113,7 @@ struct GmresState {
   double* resid;   // R: current residual estimate / ||b||
   int* active;     // R
   int* jcount;     // R: Arnoldi columns completed this cycle
+  int* iters;      // R: Arnoldi steps taken while active (whole solve)
 };
 
 // Norms: sqrt(real(dot)) from the reduced dots.
@@ -121,32 +140,48 @@ __global__ void k_cycle_start(GmresState s, int R, int m, double tol) {
 // Column j of H from the projections h (nvec = j+1) and the norm of w;
 // applies the previous rotations, forms the new one, updates g and the
 // residual estimate.  One warp per rhs: the lanes stage the column and the
-// rotations in shared memory, lane 0 runs the sequential recurrence.
+// rotations in shared memory as float-float values, lane 0 runs the
+// sequential recurrence in float-float arithmetic on the FP32 pipe (GB300's
+// FP64 latency would make this chain of up to 1,000 dependent rotations the
+// slowest step of an iteration), and the new rotation, g and the residual
+// estimate are formed in FP64.
+__device__ __forceinline__ ffc ffc_from_cd(cd v) { return {ff_from_d(v.x), ff_from_d(v.y)}; }
+__device__ __forceinline__ cd ffc_to_cd(ffc v) { return mkc(ff_to_d(v.re), ff_to_d(v.im)); }
+__device__ __forceinline__ ffc ffc_add(ffc a, ffc b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ __forceinline__ ffc ffc_sub(ffc a, ffc b) { return {ff_sub(a.re, b.re), ff_sub(a.im, b.im)}; }
+__device__ __forceinline__ ffc ffc_scale(ffc a, ff c) { return {ff_mul(a.re, c), ff_mul(a.im, c)}; }
+__device__ __forceinline__ ffc ffc_conj(ffc a) { return {a.re, ff_neg(a.im)}; }
+
 __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* __restrict__ wnorm, int R, int m,
                          int j, double tol) {
   const int r = blockIdx.x, lane = threadIdx.x;
   if (!s.active[r]) return;
-  __shared__ cd col[MAX_RESTART + 1];
-  __shared__ double csv[MAX_RESTART];
-  __shared__ cd snv[MAX_RESTART];
-  for (int i = lane; i <= j; i += 32) col[i] = h[i * R + r];
+  if (lane == 0) s.iters[r] += 1;
+  __shared__ ffc col[MAX_RESTART + 1];
+  __shared__ ff csv[MAX_RESTART];
+  __shared__ ffc snv[MAX_RESTART];
+  for (int i = lane; i <= j; i += 32) col[i] = ffc_from_cd(h[i * R + r]);
   for (int i = lane; i < j; i += 32) {
-    csv[i] = s.cs[r * m + i];
-    snv[i] = s.sn[r * m + i];
+    csv[i] = ff_from_d(s.cs[r * m + i]);
+    snv[i] = ffc_from_cd(s.sn[r * m + i]);
   }
-  if (lane == 0) col[j + 1] = mkc(wnorm[r], 0.0);
   __syncwarp();
+  __shared__ cd top;
   if (lane == 0) {
+    // [c  s; -conj(s) c] applied to (col[i], col[i+1]) for i < j; the entry
+    // carried from one rotation to the next stays in registers
+    ffc a = col[0];
+#pragma unroll 4
     for (int i = 0; i < j; ++i) {
-      // [c  s; -conj(s) c] applied to (col[i], col[i+1])
-      const double c = csv[i];
-      const cd sn = snv[i];
-      const cd a = col[i], b = col[i + 1];
-      col[i] = cadd(cmulr(a, c), cmul(sn, b));
-      col[i + 1] = csub(cmulr(b, c), cmul(cconj(sn), a));
+      const ff c = csv[i];
+      const ffc sn = snv[i];
+      const ffc b = col[i + 1];
+      col[i] = ffc_add(ffc_scale(a, c), ffc_mul(sn, b));
+      a = ffc_sub(ffc_scale(b, c), ffc_mul(ffc_conj(sn), a));
     }
-    cd a = col[j], b = col[j + 1];
-    const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+    cd ad = ffc_to_cd(a);
+    const cd b = mkc(wnorm[r], 0.0);
+    const double na = hypot(ad.x, ad.y), nb = hypot(b.x, b.y);
     double c;
     cd sn;
     if (nb == 0.0) {
@@ -155,18 +190,17 @@ __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* _
     } else if (na == 0.0) {
       c = 0.0;
       sn = mkc(1.0, 0.0);
-      a = mkc(0.0, 0.0);
+      ad = mkc(0.0, 0.0);
     } else {
       const double t = hypot(na, nb);
       c = na / t;
       // sn = (a/|a|) conj(b) / t
-      const cd ua = mkc(a.x / na, a.y / na);
+      const cd ua = mkc(ad.x / na, ad.y / na);
       sn = cmulr(cmul(ua, cconj(b)), 1.0 / t);
     }
     s.cs[r * m + j] = c;
     s.sn[r * m + j] = sn;
-    col[j] = cadd(cmulr(a, c), cmul(sn, b));
-    col[j + 1] = mkc(0.0, 0.0);
+    top = cadd(cmulr(ad, c), cmul(sn, b));
     cd* g = s.g + r * (m + 1);
     const cd gj = g[j];
     g[j] = cmulr(gj, c);
@@ -178,7 +212,11 @@ __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* _
   }
   __syncwarp();
   cd* Hcol = s.H + ((int64_t)r * m + j) * (m + 1);
-  for (int i = lane; i <= j + 1; i += 32) Hcol[i] = col[i];
+  for (int i = lane; i < j; i += 32) Hcol[i] = ffc_to_cd(col[i]);
+  if (lane == 0) {
+    Hcol[j] = top;
+    Hcol[j + 1] = mkc(0.0, 0.0);
+  }
 }
 
 // Back substitution H y = g for the jcount[r] completed columns; y into g.
@@ -232,65 +270,141 @@ __global__ void k_reorth_flag(const cd* __restrict__ before, const cd* __restric
 
 __device__ __forceinline__ float4 ff_conj(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
 
-// partial[(v*R + r)*gridDim.x + blk] = sum over the block's rows of conj(V_v[r]) w[r]
-__global__ void k_dots_ff(const float4* __restrict__ V, int64_t vstride, int nvec, const float4* __restrict__ w, int R,
-                          int64_t N, cd* __restrict__ partial, const int* __restrict__ active) {
-  const int blk = blockIdx.x, v = blockIdx.y, r = blockIdx.z;
-  __shared__ double sre[RED_THREADS], sim[RED_THREADS];
-  float rh[2] = {0.f, 0.f}, rl[2] = {0.f, 0.f}, ih[2] = {0.f, 0.f}, il[2] = {0.f, 0.f};
+// partial[(v*R + r)*gridDim.x + blk] = sum over the block's rows of conj(V_v[r]) w[r],
+// for DOT_VB basis vectors per CTA (v = blockIdx.y *
+// DOT_VB + q, q < DOT_VB, v < nvec): each row of w is loaded once for all of
+// them.  Per-thread sums are reduced across the warp in float-float (FP32
+// pipe; GB300's FP64 pipe would bound this step), then across the warps in
+// FP64, in a fixed order (deterministic).
+constexpr int DOT_VB = 4;
+__global__ void __launch_bounds__(RED_THREADS) k_dots_ff4(const float4* __restrict__ V, int64_t vstride, int nvec,
+                                                          const float4* __restrict__ w, int R, int64_t N,
+                                                          cd* __restrict__ partial, const int* __restrict__ active) {
+  const int blk = blockIdx.x, v0 = blockIdx.y * DOT_VB, r = blockIdx.z;
+  const int nq = min(DOT_VB, nvec - v0);
+  float rh[DOT_VB], rl[DOT_VB], ih[DOT_VB], il[DOT_VB];
+#pragma unroll
+  for (int q = 0; q < DOT_VB; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
   if (active[r]) {
-    const float4* a = V + (int64_t)v * vstride + (int64_t)r * N;
+    const float4* a = V + (int64_t)v0 * vstride + (int64_t)r * N;
     const float4* b = w + (int64_t)r * N;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    for (; i + stride < N; i += 2 * stride) {
-      const float4 x0 = a[i], x1 = a[i + stride], y0 = b[i], y1 = b[i + stride];
-      ff_cmac(ff_conj(x0), y0, rh[0], rl[0], ih[0], il[0]);
-      ff_cmac(ff_conj(x1), y1, rh[1], rl[1], ih[1], il[1]);
+    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < N; i += stride) {
+      const float4 y = b[i];
+      float4 x[DOT_VB];
+#pragma unroll
+      for (int q = 0; q < DOT_VB; ++q) x[q] = q < nq ? a[(int64_t)q * vstride + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < DOT_VB; ++q) ff_cmac(ff_conj(x[q]), y, rh[q], rl[q], ih[q], il[q]);
     }
-    if (i < N) ff_cmac(ff_conj(a[i]), b[i], rh[0], rl[0], ih[0], il[0]);
   }
-  sre[threadIdx.x] = ((double)rh[0] + (double)rl[0]) + ((double)rh[1] + (double)rl[1]);
-  sim[threadIdx.x] = ((double)ih[0] + (double)il[0]) + ((double)ih[1] + (double)il[1]);
+  __shared__ float4 sh[RED_THREADS / 32][DOT_VB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < DOT_VB; ++q) {
+    ff_warp_sum(rh[q], rl[q]);
+    ff_warp_sum(ih[q], il[q]);
+    if (lane == 0) sh[warp][q] = make_float4(rh[q], rl[q], ih[q], il[q]);
+  }
   __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
-    if (threadIdx.x < s2) {
-      sre[threadIdx.x] += sre[threadIdx.x + s2];
-      sim[threadIdx.x] += sim[threadIdx.x + s2];
+  if (threadIdx.x < nq) {
+    const int q = threadIdx.x;
+    double re = 0.0, im = 0.0;
+    for (int u = 0; u < RED_THREADS / 32; ++u) {
+      const float4 t = sh[u][q];
+      re += (double)t.x + (double)t.y;
+      im += (double)t.z + (double)t.w;
     }
-    __syncthreads();
+    partial[((int64_t)(v0 + q) * R + r) * gridDim.x + blk] = mkc(re, im);
   }
-  if (threadIdx.x == 0) partial[((int64_t)v * R + r) * gridDim.x + blk] = mkc(sre[0], sim[0]);
 }
 
-// w[r] -= sum_v V_v[r] h[v*R + r], one row per thread, 8 basis vectors in flight
-__global__ void k_subtract_ff(const float4* __restrict__ V, int64_t vstride, int nvec, const cd* __restrict__ h,
-                              float4* __restrict__ w, int R, int64_t N, const int* __restrict__ active) {
+// w[r] -= sum_v V_v[r] h[v*R + r].  A CTA of 256 threads covers SUB_ROWS =
+// 128 rows; the two halves of the CTA take the two halves of the basis for
+// the same rows (twice the loads in flight of one thread per row), 8 basis
+// vectors in flight each, and are combined in shared memory in a fixed
+// order.  Also writes the CTA's share of ||w[r]||^2 after the update to
+// pnorm[r * gridDim.x + blockIdx.x] (FP64, reduced in a fixed order), zero
+// for a right-hand side that is not active.
+constexpr int SUB_ROWS = 128;
+__global__ void __launch_bounds__(2 * SUB_ROWS) k_subtract_ff(const float4* __restrict__ V, int64_t vstride, int nvec,
+                                                              const cd* __restrict__ h, float4* __restrict__ w, int R,
+                                                              int64_t N, const int* __restrict__ active,
+                                                              cd* __restrict__ pnorm) {
   const int r = blockIdx.y;
-  if (!active[r]) return;
+  if (!active[r]) {
+    if (threadIdx.x == 0) pnorm[(int64_t)r * gridDim.x + blockIdx.x] = mkc(0.0, 0.0);
+    return;
+  }
   __shared__ float4 hs[MAX_RESTART + 1];
+  __shared__ float4 other[SUB_ROWS];
+  __shared__ double red[2 * SUB_ROWS / 32];
   for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
     const cd hv = h[v * R + r];
     hs[v] = split_ff(mkc(-hv.x, -hv.y));
   }
+  const int row = threadIdx.x & (SUB_ROWS - 1), half = threadIdx.x / SUB_ROWS;
+  const int nh = (nvec + 1) / 2;
+  const int vb = half ? nh : 0, ve = half ? nvec : nh;
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   float4* wr = w + (int64_t)r * N;
   const float4* Vr = V + (int64_t)r * N;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const float4 w0 = wr[i];
-    float rh = w0.x, rl = w0.y, ih = w0.z, il = w0.w;
-    int v = 0;
-    for (; v + 7 < nvec; v += 8) {
-      float4 a[8];
+  double acc = 0.0;
+  for (int64_t base = (int64_t)blockIdx.x * SUB_ROWS; base < N; base += (int64_t)gridDim.x * SUB_ROWS) {
+    const int64_t i = base + row;
+    const bool ok = i < N;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    if (ok) {
+      if (!half) {
+        const float4 w0 = wr[i];
+        rh = w0.x;
+        rl = w0.y;
+        ih = w0.z;
+        il = w0.w;
+      }
+      int v = vb;
+      for (; v + 7 < ve; v += 8) {
+        float4 a[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
+        for (int q = 0; q < 8; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ff_cmac(a[q], hs[v + q], rh, rl, ih, il);
+        for (int q = 0; q < 8; ++q) ff_cmac(a[q], hs[v + q], rh, rl, ih, il);
+      }
+      for (; v < ve; ++v) ff_cmac(Vr[(int64_t)v * vstride + i], hs[v], rh, rl, ih, il);
     }
-    for (; v < nvec; ++v) ff_cmac(Vr[(int64_t)v * vstride + i], hs[v], rh, rl, ih, il);
-    wr[i] = ff_norm(rh, rl, ih, il);
+    if (half) other[row] = make_float4(rh, rl, ih, il);
+    __syncthreads();
+    if (!half && ok) {
+      const float4 o = other[row];
+      float s1, e1, s2, e2;
+      two_sum_f(rh, o.x, s1, e1);
+      two_sum_f(ih, o.z, s2, e2);
+      const float4 out = ff_norm(s1, (rl + o.y) + e1, s2, (il + o.w) + e2);
+      wr[i] = out;
+      const double re = (double)out.x + (double)out.y, im = (double)out.z + (double)out.w;
+      acc = fma(re, re, fma(im, im, acc));
+    }
+    __syncthreads();
   }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < 2 * SUB_ROWS / 32; ++u) t += red[u];
+    pnorm[(int64_t)r * gridDim.x + blockIdx.x] = mkc(t, 0.0);
+  }
+}
+
+// ||w||^2 of the last Gram-Schmidt pass each right-hand side ran (the second
+// where need[r]), its square root and inverse.
+__global__ void k_sqrt_select(const cd* __restrict__ first, const cd* __restrict__ second,
+                              const int* __restrict__ need, double* __restrict__ out, double* __restrict__ inv, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const double v = sqrt(fmax((need[r] ? second[r] : first[r]).x, 0.0));
+  out[r] = v;
+  inv[r] = v > 0.0 ? 1.0 / v : 0.0;
 }
 
 // v[r] *= s[r] in float-float
@@ -348,6 +462,19 @@ __global__ void k_finite_check(const cd* __restrict__ b, int64_t total, int* __r
   }
 }
 
+// Iterations to enqueue before the host reads the convergence flags again:
+// half of the iterations still needed at the residual contraction rate seen
+// since the last look (1 to 32), so that a solve overshoots its convergence
+// by a few iterations at most while most host round trips disappear.
+static int next_block(double last, double cur, int since, double tol) {
+  if (!(last > 0.0) || !(cur > 0.0) || since < 1) return 4;
+  if (cur >= last) return 16;   // stagnating within the cycle
+  const double rate = std::pow(cur / last, 1.0 / since);
+  const double need = std::log(tol / cur) / std::log(rate);
+  if (!(need > 0.0)) return 1;
+  return (int)std::max(1.0, std::min(32.0, std::floor(0.5 * need)));
+}
+
 namespace {
 struct DevBuf {
   void* p = nullptr;
@@ -363,7 +490,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   const int m = o.restart > 0 ? o.restart : 30;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
   if (m > MAX_RESTART || R < 1 || N < 1) {
-    set_error("gmres: restart must be 1..200 and R, N positive");
+    set_error("gmres: restart must be 1..%d and R, N positive", MAX_RESTART);
     return FMPB_EINVAL;
   }
   auto t0 = std::chrono::steady_clock::now();
@@ -372,7 +499,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   DevBuf Vb, Wb, Tb, Sb, Pb;
   // control state: carve one allocation; the first pass (base = null) sizes it
   GmresState s;
-  cd *h = nullptr, *h2 = nullptr, *nrm2 = nullptr;
+  cd *h = nullptr, *h2 = nullptr, *nrm2 = nullptr, *pnorm = nullptr;
   double *wnorm = nullptr;
   int *all_active = nullptr, *bad = nullptr, *need = nullptr;
   size_t small = 0;
@@ -387,9 +514,10 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     s.H = (cd*)take(sizeof(cd) * (size_t)R * (m + 1) * m);
     s.sn = (cd*)take(sizeof(cd) * (size_t)R * m);
     s.g = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
-    h = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+    h = (cd*)take(sizeof(cd) * (size_t)R * (m + 2));
     h2 = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
     nrm2 = (cd*)take(sizeof(cd) * 2 * (size_t)R);
+    pnorm = (cd*)take(sizeof(cd) * (size_t)R * 152 * 8);
     s.cs = (double*)take(sizeof(double) * (size_t)R * m);
     s.beta = (double*)take(sizeof(double) * R);
     s.inv = (double*)take(sizeof(double) * R);
@@ -398,6 +526,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     wnorm = (double*)take(sizeof(double) * R);
     s.active = (int*)take(sizeof(int) * R);
     s.jcount = (int*)take(sizeof(int) * R);
+    s.iters = (int*)take(sizeof(int) * R);
     all_active = (int*)take(sizeof(int) * R);
     need = (int*)take(sizeof(int) * R);
     bad = (int*)take(sizeof(int));
@@ -406,7 +535,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
           cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess ||
           cudaMalloc(&Tb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
-          cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 1) * R * RED_BLOCKS) != cudaSuccess) {
+          cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 2) * R * RED_BLOCKS) != cudaSuccess) {
         cudaGetLastError();
         set_error("gmres: cannot allocate the Krylov basis (%zu bytes)", sizeof(cd) * (size_t)(m + 2) * vstride);
         return FMPB_ENOMEM;
@@ -419,8 +548,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   cd* partial = (cd*)Pb.p;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
-  const unsigned sub_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8));
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, N / (RED_THREADS * 16)));
+  const unsigned sub_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + SUB_ROWS - 1) / SUB_ROWS, 152 * 8));
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, N / (RED_THREADS * 8)));
   const unsigned rb = grid_for(R, 64);
 
   // all-active mask for norms of b and of true residuals
@@ -446,8 +575,9 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
 
   FMPB_TRY(norms(b, s.bnorm, nullptr));
   FMPB_CUDA(cudaMemsetAsync(x, 0, sizeof(cd) * vstride, st));
+  FMPB_CUDA(cudaMemsetAsync(s.iters, 0, sizeof(int) * R, st));
 
-  std::vector<double> hres(R), hbn(R);
+  std::vector<double> hres(R), hbn(R), hest(R);
   std::vector<int> hact(R), iters(R, 0);
   int total_it = 0;
   bool timed_out = false;
@@ -470,6 +600,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     bool any = false;
     for (int r = 0; r < R; ++r) any |= hact[r] != 0;
     if (!any) break;
+    int block = 4, since = 0;
+    double last_res = -1.0;
     for (int j = 0; j < m && total_it < maxit; ++j) {
       float4* vj = V + (int64_t)j * vstride;
       float4* vn = V + (int64_t)(j + 1) * vstride;
@@ -477,33 +609,39 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       FMPB_TRY(A(R, T, W, st));
       FMPB_LAUNCH("cd_to_ff", st, k_cd_to_ff<<<vec_blocks, 256, 0, st>>>(W, vn, vstride));
       // classical Gram-Schmidt against v_0..v_j, repeated when the first
-      // pass lost more than half of ||w||^2
-      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2 + R, 0));
-      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active));
-      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
-      FMPB_LAUNCH("reorth_flag", st, k_reorth_flag<<<rb, 64, 0, st>>>(nrm2 + R, nrm2, s.active, need, R));
-      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, j + 1, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
+      // pass lost more than half of ||w||^2.  w sits in slot j + 1 of the
+      // basis, so one launch over slots 0..j+1 gives the projections h_0..h_j
+      // and ||w||^2 (entry j + 1).
+      FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vn, R, N, partial, s.active));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active, pnorm));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials_warp<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, R, nrm2));
+      FMPB_LAUNCH("reorth_flag", st, k_reorth_flag<<<rb, 64, 0, st>>>(h + (int64_t)(j + 1) * R, nrm2, s.active, need, R));
+      FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (j + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need));
+      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need, pnorm));
+      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials_warp<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, R, nrm2 + R));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
       // ||w||, normalise
-      FMPB_LAUNCH("dots", st, k_dots_ff<<<dim3(nb, 1, R), RED_THREADS, 0, st>>>(vn, 0, 1, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for(R, 64), 64, 0, st>>>(partial, nb, R, nrm2, 0));
-      FMPB_LAUNCH("sqrt_real", st, k_sqrt_real<<<rb, 64, 0, st>>>(nrm2, wnorm, s.inv, R));
+      FMPB_LAUNCH("sqrt_real", st, k_sqrt_select<<<rb, 64, 0, st>>>(nrm2, nrm2 + R, need, wnorm, s.inv, R));
       FMPB_LAUNCH("scale", st, k_scale_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, s.inv, R, N, s.active));
       FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
       FMPB_CUDA(cudaGetLastError());
       ++total_it;
-      for (int r = 0; r < R; ++r)
-        if (hact[r]) iters[r]++;
+      // The host looks at the convergence flags only every `block`
+      // iterations; in between it keeps enqueueing, and the Arnoldi kernels
+      // of converged right-hand sides return at once (device-side flags).
+      if (++since < block && j + 1 < m && total_it < maxit) continue;
       FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+      FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
       FMPB_CUDA(cudaStreamSynchronize(st));
       any = false;
-      for (int r = 0; r < R; ++r) any |= hact[r] != 0;
+      double cur = 0.0;
+      for (int r = 0; r < R; ++r)
+        if (hact[r]) {
+          any = true;
+          cur = std::max(cur, hest[r]);
+        }
       if (!any) break;
       if (o.timeout_ms > 0 &&
           std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
@@ -511,6 +649,9 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         timed_out = true;
         break;
       }
+      block = next_block(last_res, cur, since, tol);
+      last_res = cur;
+      since = 0;
     }
     FMPB_LAUNCH("backsolve", st, k_backsolve<<<R, 32, 0, st>>>(s, R, m));
     FMPB_LAUNCH("update_x", st, k_update_x_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
@@ -523,8 +664,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   FMPB_TRY(norms(W, s.beta, nullptr));
   FMPB_CUDA(cudaMemcpyAsync(hres.data(), s.beta, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   FMPB_CUDA(cudaMemcpyAsync(hbn.data(), s.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-  std::vector<double> hest(R);
   FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  FMPB_CUDA(cudaMemcpyAsync(iters.data(), s.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
   FMPB_CUDA(cudaStreamSynchronize(st));
   bool all_conv = true;
   for (int r = 0; r < R; ++r) {

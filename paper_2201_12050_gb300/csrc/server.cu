@@ -323,8 +323,8 @@ fmpb_status fmpb_server_create(const fmpb_server_opts* opts, fmpb_server** out) 
   if (o.restart <= 0) o.restart = 200;
   if (o.maxit <= 0) o.maxit = 3000;
   if (o.tol <= 0) o.tol = 1e-8;
-  if (o.max_batch_rhs > 4096 || o.restart > 200) {
-    set_error("server_create: max_batch_rhs <= 4096 and restart <= 200");
+  if (o.max_batch_rhs > 4096 || o.restart > 1000) {
+    set_error("server_create: max_batch_rhs <= 4096 and restart <= 1000");
     return FMPB_EINVAL;
   }
   if (o.precision != FMPB_FP64 && o.precision != FMPB_FP32 && o.precision != FMPB_MIXED) {

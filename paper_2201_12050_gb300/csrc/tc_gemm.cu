@@ -23,7 +23,7 @@
 //     a 4-deep ring of shared-memory stages, in the no-swizzle K-major layout
 //     of 8-row x 16-byte core matrices; B rows of source cells outside the
 //     grid are zero-filled by the copy itself (source size 0);
-//   - one thread issues four 128 x 256 x 16 MMAs per stage into a 256-column
+//   - one thread issues four 128 x BN x 16 MMAs per stage into a BN-column
 //     FP32 accumulator in tensor memory and commits them to the stage's
 //     mbarrier, which releases the stage for the next copy;
 //   - after the last commit the eight warps read the accumulator back with
