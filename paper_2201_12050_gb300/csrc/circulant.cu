@@ -129,8 +129,11 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
     set_error("dft_axis: scaling and accumulation need complex-double output");
     return FMPB_EINVAL;
   }
+  // inner tile: up to 256 values (one per thread) so that long lines, such
+  // as the operator's block columns, run in few CTAs that each amortise their
+  // twiddle table; shrunk to the shared-memory budget and to fill the GPU
   const size_t budget = 96 * 1024;
-  int64_t TI = 32;
+  int64_t TI = 256;
   while (TI > 1 && (size_t)(Pin * TI + P) * sizeof(float4) > budget) TI /= 2;
   if ((size_t)(Pin * TI + P) * sizeof(float4) > 200 * 1024) {
     set_error("dft_axis: axis length %d too large", P);

@@ -141,11 +141,11 @@ __device__ __forceinline__ void integrate_collapsed(const double a[3], const dou
     ba[d] = b[d] - a[d];
     cb[d] = cc[d] - b[d];
   }
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < Q; ++i) {
     const double s = t[i];
     const double ws = two_area * s * w[i];
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < Q; ++j) {
       double y[3];
       for (int d = 0; d < 3; ++d) y[d] = a[d] + s * (ba[d] + t[j] * cb[d]);
@@ -154,8 +154,11 @@ __device__ __forceinline__ void integrate_collapsed(const double a[3], const dou
   }
 }
 
-// D, H of element E (translated by shift) seen from (x, nx), by class.
-__device__ void element_dh(const Elem& E, const double shift[3], const double x[3], const double nx[3],
+// D, H of element E (translated by shift) seen from (x, nx), by class.  Kept
+// out of line with rolled loops: the quadrature kernel's code must stay small
+// enough for the instruction cache, and these classes are a few per cent of
+// the points.
+__device__ __noinline__ void element_dh(const Elem& E, const double shift[3], const double x[3], const double nx[3],
                            double k, const QuadRules& qr, cd& D, cd& H) {
   double v[3][3];
   for (int a = 0; a < 3; ++a)
@@ -367,7 +370,9 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
     const Elem& Ti = el[i];
     double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
     double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
-    const ff nxf[3] = {ff_from_d(nx[0]), ff_from_d(nx[1]), ff_from_d(nx[2])};
+    // the target normal in float-float is the element's own (prepared once)
+    const FfElem& Fi = fel[i];
+    const ff nxf[3] = {Fi.ny[0], Fi.ny[1], Fi.ny[2]};
     double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
     cd D, H;
     element_dh_mixed(el[j], fel[j], sh, x, nx, nxf, k, kf, qr, C, D, H);
