@@ -617,9 +617,9 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active, pnorm));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials_warp<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, R, nrm2));
       FMPB_LAUNCH("reorth_flag", st, k_reorth_flag<<<rb, 64, 0, st>>>(h + (int64_t)(j + 1) * R, nrm2, s.active, need, R));
-      FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (j + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
+      FMPB_LAUNCH("dots_reorth", st, k_dots_ff4<<<dim3(nb, (j + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need, pnorm));
+      FMPB_LAUNCH("subtract_reorth", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need, pnorm));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials_warp<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, R, nrm2 + R));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
       // ||w||, normalise

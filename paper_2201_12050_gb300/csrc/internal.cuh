@@ -14,6 +14,7 @@ struct FfElem {
   ff ba[3];      // v1 - v0
   ff cb[3];      // v2 - v1
   ff ny[3];      // unit normal
+  ff c[3];       // centroid (collocation point of a target element)
   ff two_area;
   float hmax;
   float pad;

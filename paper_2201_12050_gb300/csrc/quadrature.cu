@@ -211,6 +211,7 @@ __global__ void k_prepare_ff(const Elem* __restrict__ el, int n, FfElem* __restr
       F.ba[d] = ff_from_d(E.v[1][d] - E.v[0][d]);
       F.cb[d] = ff_from_d(E.v[2][d] - E.v[1][d]);
       F.ny[d] = ff_from_d(E.nrm[d]);
+      F.c[d] = ff_from_d(E.c[d]);
     }
     F.two_area = ff_from_d(2.0 * E.area);
     F.hmax = (float)E.hmax;
@@ -266,12 +267,13 @@ __device__ __forceinline__ ffc expi_ff(ff psi, int m, const FfConst& C) {
 constexpr double TWO_PI_HI = 6.283185307179586;
 constexpr double TWO_PI_LO = 2.4492935982947064e-16;
 
-// D, H of a far element: e = x - (c + shift) in FP64, r2 = |e|^2, dist = |e|.
-__device__ void far_dh_ff(const FfElem& F, const double e[3], double r2, double dist, const ff nxf[3], double k,
-                          ff kf, const FfConst& C, cd& D, cd& H) {
-  const ff ef[3] = {ff_from_d(e[0]), ff_from_d(e[1]), ff_from_d(e[2])};
-  const ff rho2 = ff_from_d(r2);
-  const ff rho = ff_from_d(dist);
+// D, H of a far element.  ef = x - (c + shift) in float-float (formed on the
+// FP32 pipe from float-float centroids and shift; about 1e-13 relative to
+// |e| >= 4 h), dist = |e| in FP64 for the reference phase.
+__device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff nxf[3], double k, ff kf,
+                          const FfConst& C, cd& D, cd& H) {
+  const ff rho2 = ff_dot3(ef, ef);
+  const ff rho = ff_sqrt(rho2);
   const ff dny = ff_dot3(ef, F.ny);           // (x - y).n_y is constant on the flat element
   const ff enx = ff_dot3(ef, nxf);
   const ff Cd = ff_mul(dny, C.inv4pi);
@@ -332,15 +334,17 @@ __device__ void far_dh_ff(const FfElem& F, const double e[3], double r2, double 
 }
 
 // D, H by class: the far class through far_dh_ff, the near classes in FP64.
-__device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double shift[3], const double x[3],
-                                 const double nx[3], const ff nxf[3], double k, ff kf, const QuadRules& qr,
-                                 const FfConst& C, cd& D, cd& H) {
+__device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double shift[3], const ff shf[3],
+                                 const double x[3], const ff xf[3], const double nx[3], const ff nxf[3], double k,
+                                 ff kf, const QuadRules& qr, const FfConst& C, cd& D, cd& H) {
   double dc[3];
   for (int d = 0; d < 3; ++d) dc[d] = x[d] - (E.c[d] + shift[d]);
   const double r2 = dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2];
   const double dist = sqrt(r2);
   if (dist >= FAR_RATIO * E.hmax) {
-    far_dh_ff(F, dc, r2, dist, nxf, k, kf, C, D, H);
+    const ff ef[3] = {ff_sub(ff_sub(xf[0], F.c[0]), shf[0]), ff_sub(ff_sub(xf[1], F.c[1]), shf[1]),
+                      ff_sub(ff_sub(xf[2], F.c[2]), shf[2])};
+    far_dh_ff(F, ef, dist, nxf, k, kf, C, D, H);
     return;
   }
   element_dh(E, shift, x, nx, k, qr, D, H);
@@ -355,7 +359,8 @@ __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
 // out + dest[o] * n * n.  The diagonal of the zero offset is left to
 // k_self_terms.
 __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
-                               const double* __restrict__ shifts, const int64_t* __restrict__ dest, int n_off,
+                               const double* __restrict__ shifts, const ff* __restrict__ shiftf,
+                               const int64_t* __restrict__ dest, int n_off,
                                int zero_off, cd* __restrict__ out, double k, QuadRules qr, FfConst C) {
   const ff kf = ff_from_d(k);
   const size_t nn = (size_t)n * n;
@@ -373,9 +378,11 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
     // the target normal in float-float is the element's own (prepared once)
     const FfElem& Fi = fel[i];
     const ff nxf[3] = {Fi.ny[0], Fi.ny[1], Fi.ny[2]};
+    const ff xf[3] = {Fi.c[0], Fi.c[1], Fi.c[2]};
     double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
+    const ff shf[3] = {shiftf[3 * o], shiftf[3 * o + 1], shiftf[3 * o + 2]};
     cd D, H;
-    element_dh_mixed(el[j], fel[j], sh, x, nx, nxf, k, kf, qr, C, D, H);
+    element_dh_mixed(el[j], fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H);
     out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
   }
 }
@@ -621,17 +628,27 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
     for (int d = 0; d < 3; ++d)
       shifts[3 * o + d] = -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
   }
+  // the same shifts as float-float pairs (hi = nearest float, lo = nearest float of the rest)
+  std::vector<ff> shiftf(3 * (size_t)n_off);
+  for (size_t q = 0; q < shiftf.size(); ++q) {
+    const float hi = (float)shifts[q];
+    shiftf[q] = ff{hi, (float)(shifts[q] - (double)hi)};
+  }
   double* dshift = nullptr;
+  ff* dshiftf = nullptr;
   int64_t* ddest = nullptr;
   FMPB_CUDA(cudaMalloc(&dshift, sizeof(double) * 3 * n_off));
   cudaError_t e = cudaMalloc(&ddest, sizeof(int64_t) * n_off);
+  if (e == cudaSuccess) e = cudaMalloc(&dshiftf, sizeof(ff) * 3 * n_off);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dshift, shifts.data(), sizeof(double) * 3 * n_off, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dshiftf, shiftf.data(), sizeof(ff) * 3 * n_off, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ddest, dest_host, sizeof(int64_t) * n_off, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     const size_t total = (size_t)m.n * m.n * n_off;
     unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
-    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, ddest, n_off, zero_off, out, k, m.qr, m.fc));
+    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, m.qr, m.fc));
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
                                                      k, m.qr));
@@ -639,6 +656,7 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dshift);
+  cudaFree(dshiftf);
   cudaFree(ddest);
   if (e != cudaSuccess) return cuda_status(e, "build_blocks");
   return FMPB_OK;
