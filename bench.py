@@ -404,7 +404,10 @@ def batching_section(gb, torch, stream, freq_index=3, n_t=12):
                    "solve_tol1e-3": {"ms": s_ms, "solves_per_s_incl_build": R * 1e3 / (s_ms + build_ms),
                                      "iters_max": max(i["iters"] for i in info),
                                      "relres_true_max": max(i["relres_true"] for i in info)},
-                   "operator_bytes": op.info["bytes_device"]}
+                   "operator_bytes": op.info["bytes_device"],
+                   "tc_tiles_chosen": [{k_: e[k_] for k_ in ("m", "k", "columns", "offsets", "rows_per_cta",
+                                                              "columns_per_cta", "ms")}
+                                       for e in gb.tuning_summary() if e["columns"] == nc * R]}
     op.close()
     # MIXED: BF16 inner products, float-float outer residuals
     op, build_ms = build(gb.MIXED)

@@ -442,6 +442,22 @@ fmpb_status fmpb_profile_reset(void);
  * EINVAL if buf is too small. */
 fmpb_status fmpb_profile_summary(char *buf, size_t len);
 
+/* Writes a JSON list of the tile shapes the tensor-core autotuner chose:
+ * the first product of each shape (device, rows m, depth k, columns,
+ * offsets) times the tile variants (128 or 256 output rows and 128 or 256
+ * output columns per CTA) on the caller's stream and keeps the fastest;
+ * every entry lists the chosen tile and the time of each variant (ms, in
+ * the order 128x256, 256x256, 256x128, 128x128).  EINVAL if buf is too
+ * small. */
+fmpb_status fmpb_tuning_summary(char *buf, size_t len);
+
+/* Forces one tile variant of the tensor-core offset GEMM for all later
+ * products in this process (0: 128x256, 1: 256x256, 2: 256x128,
+ * 3: 128x128 output rows x columns per CTA), or restores autotuning (-1).
+ * For tests and tuning studies; the variants give the same results up to
+ * FP32 accumulation order.  EINVAL outside -1..3. */
+fmpb_status fmpb_set_tile_variant(int variant);
+
 #ifdef __cplusplus
 }
 #endif

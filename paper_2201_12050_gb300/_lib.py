@@ -112,6 +112,8 @@ SIGNATURES = {
     "fmpb_profile_enable": (None, [INT]),
     "fmpb_profile_reset": (INT, []),
     "fmpb_profile_summary": (INT, [ctypes.c_char_p, ctypes.c_size_t]),
+    "fmpb_tuning_summary": (INT, [ctypes.c_char_p, ctypes.c_size_t]),
+    "fmpb_set_tile_variant": (INT, [INT]),
 }
 
 _lib = None

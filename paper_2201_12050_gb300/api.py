@@ -247,6 +247,19 @@ def profile_summary() -> dict:
     return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
 
+def set_tile_variant(variant: int):
+    """fmpb_set_tile_variant: force a tensor-core tile variant (0..3) or autotune (-1)."""
+    check(lib().fmpb_set_tile_variant(int(variant)))
+
+
+def tuning_summary() -> list:
+    """fmpb_tuning_summary: tile shapes chosen by the tensor-core autotuner."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib().fmpb_tuning_summary(buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
 class Server:
     """fmpb_server: queued solves of many (mesh, lattice, k) problems."""
 

@@ -599,6 +599,17 @@ fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fm
   return circulant_spectrum_from_blocks(make_shape(M), B, (const cd*)blocks, (cd*)spec, (cudaStream_t)stream);
 }
 
+fmpb_status fmpb_tuning_summary(char* buf, size_t len) {
+  CHECK_ARG(buf && len >= 3, "tuning_summary: buffer too small");
+  std::string out;
+  FMPB_TRY(tc_tuning_summary(out));
+  CHECK_ARG(out.size() + 1 <= len, "tuning_summary: buffer of %zu bytes too small (%zu needed)", len, out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return FMPB_OK;
+}
+
+fmpb_status fmpb_set_tile_variant(int variant) { return tc_force_variant(variant); }
+
 fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
                                   const fmpb_c64* T, int R, const fmpb_c64* x, fmpb_c64* y, int accumulate,
                                   void* stream) {

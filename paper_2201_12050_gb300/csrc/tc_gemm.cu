@@ -34,6 +34,12 @@
 // its tensor memory before it returns.
 #include <cuda_bf16.h>
 
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
 #include "common.cuh"
 #include "internal.cuh"
 #include "profile.cuh"
@@ -49,11 +55,18 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 256;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 constexpr int TC_BAR_BYTES = 64;   // TC_STAGES mbarriers + the tensor-memory address
-template <int BN>
+// BN output columns and MT x 128 output rows per CTA (MT accumulators of BN
+// tensor-memory columns each); as many stages as fit (at most TC_STAGES).
+template <int BN, int MT>
 struct TcTile {
+  static constexpr int A_BYTES = MT * TC_A_BYTES;
   static constexpr int B_BYTES = BN * TC_BK * 2;
-  static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
-  static constexpr int SMEM = TC_STAGES * STAGE_BYTES + TC_BAR_BYTES;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int FIT = (227 * 1024 - TC_BAR_BYTES) / STAGE_BYTES;
+  static constexpr int STAGES = FIT < TC_STAGES ? FIT : TC_STAGES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + TC_BAR_BYTES;
+  static constexpr int TMEM_COLS = MT * BN;
+  static_assert(STAGES >= 3, "tile too large for the shared-memory ring");
   // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A
   // and B in BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
   // N / 8 in bits 17-22, M / 16 in bits 24-28.
@@ -163,28 +176,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 //           c - delta_o (zero outside the grid); K runs over offsets x depth.
 //   FREQ:   blockIdx.y = frequency f with its own A_f, columns j = r < R,
 //           B row of column j = x row f R + r; K runs over the depth.
-template <int BN, bool FREQ>
+//   MT = 2: a CTA owns 256 output rows in two accumulators and uses each B
+//           tile it copies for both (half the B traffic per flop); the last
+//           row tile of an odd count runs its second half empty.
+template <int BN, bool FREQ, int MT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __nv_bfloat16* __restrict__ A, int64_t a_stride, int Kp, const __nv_bfloat16* __restrict__ X,
               void* __restrict__ y_, int m, int64_t ncols, int Mx, int My, int Mz, TcOffsets offs, int accumulate,
               unsigned* err) {
-  using Tile = TcTile<BN>;
+  using Tile = TcTile<BN, MT>;
+  constexpr int NS = Tile::STAGES;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * Tile::STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * Tile::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NS);
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TC_BM;
+  const int m0 = blockIdx.x * TC_BM * MT;
+  const int64_t Mp = a_stride / Kp;
+  const bool two = MT == 2 && m0 + TC_BM < Mp;   // second row half present
   const int64_t n0 = (int64_t)(FREQ ? blockIdx.z : blockIdx.y) * BN;
   const int64_t f = FREQ ? (int64_t)blockIdx.y : 0;
   const int Nc = Mx * My * Mz;
 
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
-    tmem_alloc(smem_u32(tmem_slot), BN);
+    tmem_alloc(smem_u32(tmem_slot), Tile::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -216,10 +235,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int o = FREQ ? 0 : it / kt_per_off;
     const int k0 = (it - o * kt_per_off) * TC_BK + kc * 8;
     const uint32_t sa = sbase + s * Tile::STAGE_BYTES + tid * 16;
-    const uint32_t sb = sa + TC_A_BYTES;
+    const uint32_t sb = sa + Tile::A_BYTES;
     const __nv_bfloat16* arow = Af + o * a_stride + (int64_t)(m0 + rlo) * Kp + k0;
 #pragma unroll
-    for (int t = 0; t < TC_BM / 32; ++t) cp_async16(sa + t * 4096, arow + (int64_t)(32 * t) * Kp, 16);
+    for (int t = 0; t < MT * TC_BM / 32; ++t)
+      if (t < TC_BM / 32 || two) cp_async16(sa + t * 4096, arow + (int64_t)(32 * t) * Kp, 16);
     if (FREQ) {
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
@@ -241,52 +261,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   bool bad = false;
 #pragma unroll 1
-  for (int s = 0; s < TC_STAGES - 1; ++s) {
+  for (int s = 0; s < NS - 1; ++s) {
     if (s < KT) load_stage(s, s);
     cp_async_commit();
   }
   int kt = 0;
 #pragma unroll 1
   for (; kt < KT; ++kt) {
-    const int s = kt % TC_STAGES;
-    cp_async_wait<TC_STAGES - 2>();
+    const int s = kt % NS;
+    cp_async_wait<NS - 2>();
     fence_proxy_async();
     if (__syncthreads_or(bad)) break;
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = sbase + s * Tile::STAGE_BYTES, b0 = a0 + TC_A_BYTES;
+      const uint32_t a0 = sbase + s * Tile::STAGE_BYTES, b0 = a0 + Tile::A_BYTES;
 #pragma unroll
-      for (int q = 0; q < TC_BK / 16; ++q)
+      for (int q = 0; q < TC_BK / 16; ++q) {
         tc_mma(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), Tile::IDESC, (kt | q) != 0);
+        if (two)   // rows 128..255 of the stage, second accumulator
+          tc_mma(tmem + BN, smem_desc(a0 + TC_A_BYTES + 256 * q), smem_desc(b0 + 256 * q), Tile::IDESC,
+                 (kt | q) != 0);
+      }
       tc_commit(smem_u32(&bars[s]));
     }
-    const int nk = kt + TC_STAGES - 1;
+    const int nk = kt + NS - 1;
     if (nk < KT) {
-      // stage nk % TC_STAGES was last read by the MMAs of step kt - 1
-      if (kt >= 1) bad = !mbar_wait_bounded(smem_u32(&bars[(kt - 1) % TC_STAGES]), ((kt - 1) / TC_STAGES) & 1);
-      if (!bad) load_stage(nk, nk % TC_STAGES);
+      // stage nk % NS was last read by the MMAs of step kt - 1
+      if (kt >= 1) bad = !mbar_wait_bounded(smem_u32(&bars[(kt - 1) % NS]), ((kt - 1) / NS) & 1);
+      if (!bad) load_stage(nk, nk % NS);
     }
     cp_async_commit();
   }
   const int last = kt - 1;   // MMAs were issued for steps 0 .. last
   bool ok = true;
-  if (last >= 0) ok = mbar_wait_bounded(smem_u32(&bars[last % TC_STAGES]), (last / TC_STAGES) & 1);
+  if (last >= 0) ok = mbar_wait_bounded(smem_u32(&bars[last % NS]), (last / NS) & 1);
   cp_async_wait<0>();
   ok = !__syncthreads_or(!ok || bad || last != KT - 1);
   if (!ok) {
     if (tid == 0) atomicOr(err, 1u);
   } else {
     tc_fence_after();
-    const int quarter = warp & 3;
-    const int64_t gm = (int64_t)m0 + quarter * 32 + lane;   // accumulator lane = realified output row
+    // MT = 1: warps 0-3 and 4-7 read the two column halves of the accumulator;
+    // MT = 2: warps 0-3 read accumulator 0 (rows 0..127), warps 4-7 accumulator 1
+    const int quarter = warp & 3, half = warp >> 2;
+    const int64_t gm = (int64_t)m0 + (MT == 2 ? half * TC_BM : 0) + quarter * 32 + lane;
     const bool row_ok = gm < 2 * (int64_t)m;
     const int64_t i = gm >> 1;
     const int part = (int)(gm & 1);
-    const int cbase = (warp >> 2) * (BN / 2);
+    const int cbase = MT == 2 ? 0 : half * (BN / 2);
+    const int ncol = MT == 2 ? ((half == 0 || two) ? BN : 0) : BN / 2;
+    const uint32_t tcol = MT == 2 ? (uint32_t)(half * BN) : (uint32_t)cbase;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + c0), v);
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + tcol + (uint32_t)c0, v);
       if (row_ok) {
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
@@ -307,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, BN);
+  if (warp == 0) tmem_dealloc(tmem, Tile::TMEM_COLS);
 }
 
 __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) { return __float2bfloat16_rn(__double2float_rn(v)); }
@@ -385,17 +413,112 @@ __global__ void k_tc_rows_from_ff(const float4* __restrict__ x, int64_t k, int64
   X[idx] = p;
 }
 
-template <int BN, bool FREQ>
+template <int BN, bool FREQ, int MT>
 fmpb_status launch_tc(dim3 grid, const __nv_bfloat16* A, int64_t a_stride, int64_t Kp, const __nv_bfloat16* X,
                       void* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs, bool accumulate,
                       unsigned* err, cudaStream_t st) {
-  using Tile = TcTile<BN>;
-  FMPB_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, FREQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile::SMEM));
+  using Tile = TcTile<BN, MT>;
+  FMPB_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, FREQ, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile::SMEM));
   FMPB_LAUNCH(FREQ ? "tc_block_product" : "tc_gemm", st,
-              (k_tc_gemm<BN, FREQ><<<grid, TC_THREADS, Tile::SMEM, st>>>(A, a_stride, (int)Kp, X, y, (int)m, ncols,
-                                                                          M[0], M[1], M[2], offs,
-                                                                          accumulate ? 1 : 0, err)));
+              (k_tc_gemm<BN, FREQ, MT><<<grid, TC_THREADS, Tile::SMEM, st>>>(A, a_stride, (int)Kp, X, y, (int)m,
+                                                                              ncols, M[0], M[1], M[2], offs,
+                                                                              accumulate ? 1 : 0, err)));
   FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+// Tile variants of the offset GEMM: (row tiles per CTA, output columns per CTA).
+struct TcVariant {
+  int mt, bn;
+};
+constexpr TcVariant TC_VARIANTS[] = {{1, 256}, {2, 256}, {2, 128}, {1, 128}};
+constexpr int TC_NVARIANTS = sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]);
+
+fmpb_status launch_offset_variant(int v, const __nv_bfloat16* A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
+                                  cd* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs,
+                                  bool accumulate, unsigned* err, cudaStream_t st) {
+  const TcVariant t = TC_VARIANTS[v];
+  const int64_t rows = (int64_t)TC_BM * t.mt;
+  const int64_t ntiles = (ncols + t.bn - 1) / t.bn;
+  if (ntiles > 65535) {
+    set_error("tc_offset_gemm: %lld columns exceed the launch limit", (long long)ncols);
+    return FMPB_EINVAL;
+  }
+  dim3 grid((unsigned)((Mp + rows - 1) / rows), (unsigned)ntiles);
+  switch (v) {
+    case 0: return launch_tc<256, false, 1>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+    case 1: return launch_tc<256, false, 2>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+    case 2: return launch_tc<128, false, 2>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+    default: return launch_tc<128, false, 1>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+  }
+}
+
+// Autotuner of the offset GEMM: the first call of a shape (device, m, k,
+// columns, offsets) times every variant on the caller's stream with CUDA
+// events (after one untimed launch each) and keeps the fastest; later calls
+// of the shape launch it directly.  The variants compute the same sums in the
+// same order (they only assign output tiles to CTAs differently).  Tuning runs
+// of an accumulating call write into a scratch output, so the caller's y
+// receives the product exactly once.
+struct TuneKey {
+  int dev;
+  int64_t m, k, ncols;
+  int noff;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, m, k, ncols, noff) < std::tie(o.dev, o.m, o.k, o.ncols, o.noff);
+  }
+};
+struct TuneEntry {
+  int variant;
+  float ms[TC_NVARIANTS];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+int g_forced_variant = -1;   // >= 0: fmpb_set_tile_variant override
+
+fmpb_status tune_offset_gemm(const TuneKey& key, const __nv_bfloat16* A, int64_t Mp, int64_t Kp,
+                             const __nv_bfloat16* X, cd* y, int64_t m, int64_t ncols, const int M[3],
+                             const TcOffsets& offs, bool accumulate, unsigned* err, cudaStream_t st, int* chosen) {
+  cd* out = y;
+  cd* scratch = nullptr;
+  if (accumulate) {
+    FMPB_CUDA(cudaMalloc(&scratch, sizeof(cd) * (size_t)ncols * m));
+    out = scratch;
+  }
+  TuneEntry e{};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  fmpb_status s = FMPB_OK;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "tune events");
+  float best = 1e30f;
+  int bestv = 0;
+  for (int v = 0; v < TC_NVARIANTS && s == FMPB_OK; ++v) {
+    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, offs, false, err, st);
+    if (s == FMPB_OK && cudaEventRecord(t0, st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tune");
+    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, offs, false, err, st);
+    if (s == FMPB_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
+      s = cuda_status(cudaGetLastError(), "tune");
+    float ms = 0.f;
+    if (s == FMPB_OK && cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tune");
+    e.ms[v] = ms;
+    if (s == FMPB_OK && ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (scratch) {
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+  }
+  if (s != FMPB_OK) return s;
+  e.variant = bestv;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = e;
+  }
+  *chosen = bestv;
   return FMPB_OK;
 }
 
@@ -452,14 +575,62 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
     set_error("tc_offset_gemm: bad shape (offsets %d, m %lld, k %lld, R %d)", offs.n, (long long)m, (long long)k, R);
     return FMPB_EINVAL;
   }
-  constexpr int BN = 256;
-  const int64_t ntiles = (ncols + BN - 1) / BN;
-  if (ntiles > 65535 || Mp / TC_BM > 65535 || Kp > (1 << 24) || Nc > (1 << 30)) {
+  if ((ncols + 127) / 128 > 65535 || Mp / TC_BM > 65535 || Kp > (1 << 24) || Nc > (1 << 30)) {
     set_error("tc_offset_gemm: %lld columns exceed the launch limit", (long long)ncols);
     return FMPB_EINVAL;
   }
-  dim3 grid((unsigned)(Mp / TC_BM), (unsigned)ntiles);
-  return launch_tc<BN, false>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+  int dev = 0;
+  FMPB_CUDA(cudaGetDevice(&dev));
+  const TuneKey key{dev, m, k, ncols, offs.n};
+  int v = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (g_forced_variant >= 0)
+      v = g_forced_variant;
+    else if (it != g_tune.end())
+      v = it->second.variant;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FMPB_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (v < 0 && cap == cudaStreamCaptureStatusNone)
+    FMPB_TRY(tune_offset_gemm(key, A, Mp, Kp, X, y, m, ncols, M, offs, accumulate, err, st, &v));
+  if (v < 0) v = 0;   // no tuning inside a stream capture
+  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+}
+
+fmpb_status tc_force_variant(int v) {
+  if (v < -1 || v >= TC_NVARIANTS) {
+    set_error("set_tile_variant: variant %d outside -1..%d", v, TC_NVARIANTS - 1);
+    return FMPB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_forced_variant = v;
+  return FMPB_OK;
+}
+
+fmpb_status tc_tuning_summary(std::string& out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  out = "[";
+  bool first = true;
+  char buf[512];
+  for (const auto& kv : g_tune) {
+    const TcVariant t = TC_VARIANTS[kv.second.variant];
+    int n = snprintf(buf, sizeof(buf),
+                     "%s{\"kernel\": \"tc_gemm\", \"device\": %d, \"m\": %lld, \"k\": %lld, \"columns\": %lld, "
+                     "\"offsets\": %d, \"rows_per_cta\": %d, \"columns_per_cta\": %d, \"ms\": [",
+                     first ? "" : ", ", kv.first.dev, (long long)kv.first.m, (long long)kv.first.k,
+                     (long long)kv.first.ncols, kv.first.noff, TC_BM * t.mt, t.bn);
+    out.append(buf, n);
+    for (int v = 0; v < TC_NVARIANTS; ++v) {
+      n = snprintf(buf, sizeof(buf), "%s%.4f", v ? ", " : "", kv.second.ms[v]);
+      out.append(buf, n);
+    }
+    out += "]}";
+    first = false;
+  }
+  out += "]";
+  return FMPB_OK;
 }
 
 fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, float4* Y,
@@ -478,10 +649,10 @@ fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, co
     return FMPB_EINVAL;
   }
   switch (BN) {
-    case 32: return launch_tc<32, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
-    case 64: return launch_tc<64, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
-    case 128: return launch_tc<128, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
-    default: return launch_tc<256, true>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    case 32: return launch_tc<32, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    case 64: return launch_tc<64, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    case 128: return launch_tc<128, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    default: return launch_tc<256, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
   }
 }
 

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace fmpb {
@@ -48,5 +50,10 @@ fmpb_status tc_rows_from_ff(const float4* x, int64_t rows, int64_t k, __nv_bfloa
 // [f][r][b] (hi = FP32 accumulator, lo = 0).
 fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, float4* Y,
                          unsigned* err, cudaStream_t st);
+
+// JSON list of the tile variants the offset-GEMM autotuner chose so far.
+fmpb_status tc_tuning_summary(std::string& out);
+// Forces tile variant v (0..3) of the offset GEMM, or autotuning (-1).
+fmpb_status tc_force_variant(int v);
 
 }  // namespace fmpb

@@ -84,13 +84,21 @@ OFF27 = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0
 OFF9 = [(dx, dy, 0) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
 
 
+@pytest.fixture
+def tile_variant(request):
+    gb.set_tile_variant(request.param)
+    yield request.param
+    gb.set_tile_variant(-1)
+
+
+@pytest.mark.parametrize("tile_variant", [-1, 0, 1, 2, 3], indirect=True)
 @pytest.mark.parametrize("counts,offsets,m,k,R", [
     ((5, 4, 3), OFF27, 20, 20, 3),          # one ragged tile in M, N and K
-    ((16, 12, 1), OFF9, 300, 150, 2),       # 5 M tiles, 2 N tiles, 45 K steps (ring wraps)
+    ((16, 12, 1), OFF9, 300, 150, 2),       # 5 M tiles (odd: a half-empty 256-row tile), 2 N tiles, 45 K steps
     ((7, 1, 1), [(0, 0, 0)], 81, 320, 5),   # P2M shape, one offset
     ((3, 3, 2), [(0, 0, 0)], 100, 49, 40),  # L2P shape, ragged depth
 ])
-def test_offset_gemm_equals_product_of_rounded_inputs(counts, offsets, m, k, R):
+def test_offset_gemm_equals_product_of_rounded_inputs(counts, offsets, m, k, R, tile_variant):
     T, x = _case(7 + m + k, counts, offsets, m, k, R)
     y = gb.offset_gemm_bf16(counts, offsets, _dev(T), _dev(x)).cpu().numpy()
     ref = _reference(counts, offsets, _cbf16(T), _cbf16(x))
@@ -101,7 +109,18 @@ def test_offset_gemm_equals_product_of_rounded_inputs(counts, offsets, m, k, R):
     assert _rel(y, exact) > 10 * err
 
 
-def test_offset_gemm_accumulates_and_skips_cells_outside_the_grid():
+def test_autotuner_records_its_choice():
+    T, x = _case(5, (6, 5, 1), OFF9, 64, 40, 3)
+    gb.offset_gemm_bf16((6, 5, 1), OFF9, _dev(T), _dev(x))
+    entries = [e for e in gb.tuning_summary() if (e["m"], e["k"], e["columns"], e["offsets"]) == (64, 40, 90, 9)]
+    assert len(entries) == 1
+    e = entries[0]
+    assert e["rows_per_cta"] in (128, 256) and e["columns_per_cta"] in (128, 256) and len(e["ms"]) == 4
+    assert all(t > 0 for t in e["ms"])
+
+
+@pytest.mark.parametrize("tile_variant", [0, 1, 2, 3], indirect=True)
+def test_offset_gemm_accumulates_and_skips_cells_outside_the_grid(tile_variant):
     counts, m, k, R = (4, 3, 2), 33, 17, 2
     offsets = [(1, 0, 0), (-1, 1, 1), (0, 0, -1), (2, 0, 0)]   # the last has sources only for c_x >= 2
     T, x = _case(99, counts, offsets, m, k, R)
