@@ -357,11 +357,16 @@ __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
 
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
 // out + dest[o] * n * n.  The diagonal of the zero offset is left to
-// k_self_terms.
+// k_self_terms.  Far-class entries are computed here; near and very-near
+// entries (a fraction of a per cent) are appended to near_list for
+// k_near_entries, which gives each of them a whole warp, or computed here
+// when the list is full.
 __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
                                const double* __restrict__ shifts, const ff* __restrict__ shiftf,
                                const int64_t* __restrict__ dest, int n_off,
-                               int zero_off, cd* __restrict__ out, double k, QuadRules qr, FfConst C) {
+                               int zero_off, cd* __restrict__ out, double k, QuadRules qr, FfConst C,
+                               unsigned long long* __restrict__ near_list, unsigned long long* __restrict__ near_count,
+                               unsigned long long near_cap) {
   const ff kf = ff_from_d(k);
   const size_t nn = (size_t)n * n;
   const size_t total = nn * (size_t)n_off;
@@ -381,9 +386,103 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
     const ff xf[3] = {Fi.c[0], Fi.c[1], Fi.c[2]};
     double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
     const ff shf[3] = {shiftf[3 * o], shiftf[3 * o + 1], shiftf[3 * o + 2]};
+    const Elem& Ej = el[j];
+    double dc[3];
+    for (int d = 0; d < 3; ++d) dc[d] = x[d] - (Ej.c[d] + sh[d]);
+    const double dist = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
+    if (dist < FAR_RATIO * Ej.hmax && near_list) {
+      const unsigned long long slot = atomicAdd(near_count, 1ull);
+      if (slot < near_cap) {
+        near_list[slot] = idx;
+        continue;
+      }
+    }
     cd D, H;
-    element_dh_mixed(el[j], fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H);
+    element_dh_mixed(Ej, fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H);
     out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
+  }
+}
+
+// Near and very-near entries listed by k_build_blocks, one warp per entry:
+// the lanes share the 64 points of the 8 x 8 collapsed rule (near) or the
+// 256 points of the rule on the four midpoint children (very near), in FP64,
+// and the sums are reduced across the warp in a fixed order.
+__global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ el, int n,
+                                                      const double* __restrict__ shifts,
+                                                      const int64_t* __restrict__ dest,
+                                                      const unsigned long long* __restrict__ list,
+                                                      const unsigned long long* __restrict__ count,
+                                                      unsigned long long cap, cd* __restrict__ out, double k,
+                                                      QuadRules qr) {
+  const size_t nn = (size_t)n * n;
+  const unsigned long long total = min(*count, cap);
+  const int lane = threadIdx.x & 31;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long w = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
+       w += nwarps) {
+    const size_t idx = list[w];
+    const int o = (int)(idx / nn);
+    const size_t rem = idx - (size_t)o * nn;
+    const int i = (int)(rem / n);
+    const int j = (int)(rem - (size_t)i * n);
+    const Elem& Ti = el[i];
+    const Elem& E = el[j];
+    const double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
+    const double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
+    const double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
+    double v[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) v[a][d] = E.v[a][d] + sh[d];
+    double dc[3];
+    for (int d = 0; d < 3; ++d) dc[d] = x[d] - (E.c[d] + sh[d]);
+    const double dist = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
+    const bool very = dist < NEAR_RATIO * E.hmax;
+    const int npts = very ? 4 * Q_NEAR * Q_NEAR : Q_NEAR * Q_NEAR;
+    cd D = mkc(0.0, 0.0), H = mkc(0.0, 0.0);
+    for (int p = lane; p < npts; p += 32) {
+      const int child = p / (Q_NEAR * Q_NEAR), q = p - child * Q_NEAR * Q_NEAR;
+      const int ia = q / Q_NEAR, ib = q - ia * Q_NEAR;
+      // triangle (A, Bv, Cv): the element, or child `child` in the order
+      // (v0, m01, m20), (m01, v1, m12), (m20, m12, v2), (m01, m12, m20)
+      double A[3], Bv[3], Cv[3], two_area = 2.0 * E.area;
+      for (int d = 0; d < 3; ++d) {
+        const double m01 = 0.5 * (v[0][d] + v[1][d]), m12 = 0.5 * (v[1][d] + v[2][d]),
+                     m20 = 0.5 * (v[2][d] + v[0][d]);
+        if (!very) {
+          A[d] = v[0][d];
+          Bv[d] = v[1][d];
+          Cv[d] = v[2][d];
+        } else if (child == 0) {
+          A[d] = v[0][d];
+          Bv[d] = m01;
+          Cv[d] = m20;
+        } else if (child == 1) {
+          A[d] = m01;
+          Bv[d] = v[1][d];
+          Cv[d] = m12;
+        } else if (child == 2) {
+          A[d] = m20;
+          Bv[d] = m12;
+          Cv[d] = v[2][d];
+        } else {
+          A[d] = m01;
+          Bv[d] = m12;
+          Cv[d] = m20;
+        }
+      }
+      if (very) two_area *= 0.25;
+      const double sv = qr.t8[ia], tv = qr.t8[ib];
+      double y[3];
+      for (int d = 0; d < 3; ++d) y[d] = A[d] + sv * ((Bv[d] - A[d]) + tv * (Cv[d] - Bv[d]));
+      kernel_point(x, nx, y, E.nrm, two_area * sv * qr.w8[ia] * qr.w8[ib], k, D, H);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      D.x += __shfl_xor_sync(0xffffffffu, D.x, off);
+      D.y += __shfl_xor_sync(0xffffffffu, D.y, off);
+      H.x += __shfl_xor_sync(0xffffffffu, H.x, off);
+      H.y += __shfl_xor_sync(0xffffffffu, H.y, off);
+    }
+    if (lane == 0) out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
   }
 }
 
@@ -645,10 +744,18 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dshiftf, shiftf.data(), sizeof(ff) * 3 * n_off, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ddest, dest_host, sizeof(int64_t) * n_off, cudaMemcpyHostToDevice, st);
+  // list of near and very-near entries for k_near_entries (entries beyond
+  // its capacity are computed by k_build_blocks itself)
+  const size_t total = (size_t)m.n * m.n * n_off;
+  const unsigned long long near_cap = (unsigned long long)std::min<size_t>(total, (size_t)8 << 20);
+  unsigned long long* near_list = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&near_list, sizeof(unsigned long long) * (near_cap + 1));
+  unsigned long long* near_count = near_list ? near_list + near_cap : nullptr;
+  if (e == cudaSuccess) e = cudaMemsetAsync(near_count, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
-    const size_t total = (size_t)m.n * m.n * n_off;
     unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
-    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, m.qr, m.fc));
+    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, m.qr, m.fc, near_list, near_count, near_cap));
+    FMPB_LAUNCH("build_near", st, k_near_entries<<<152 * 16, 256, 0, st>>>(m.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, m.qr));
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
                                                      k, m.qr));
@@ -658,6 +765,7 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
   cudaFree(dshift);
   cudaFree(dshiftf);
   cudaFree(ddest);
+  cudaFree(near_list);
   if (e != cudaSuccess) return cuda_status(e, "build_blocks");
   return FMPB_OK;
 }
