@@ -220,6 +220,14 @@ struct fmpb_operator {
     return FMPB_OK;
   }
 
+  // The PBEM-form product of an FP64 operator on float-float vectors.
+  bool has_ff_matvec() const { return form == FMPB_FORM_PBEM && spec != nullptr; }
+  fmpb_status matvec_ff(int R, const float4* x, float4* y, cudaStream_t st) {
+    FMPB_TRY(ensure_scratch(circulant_scratch_elems(shape, B, R)));
+    return circulant_apply(shape, B, spec, R, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), false,
+                           scratch, st, SPEC_FF, nullptr, nullptr, true);
+  }
+
   // low: the inner product of a MIXED operator (PBEM form: the FP32 spectrum;
   // FMM form: the BF16 tensor-core path of BF16 operators)
   fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st, bool low = false) {
@@ -515,7 +523,11 @@ fmpb_status fmpb_solve(const fmpb_operator* op, int R, const fmpb_c64* b, fmpb_c
     MatvecFn Alow = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st, true); };
     s = gmres_refined(A, Alow, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
   } else {
-    s = gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+    const MatvecFfFn Aff = [mop](int r, const float4* x, float4* y, cudaStream_t st) {
+      return mop->matvec_ff(r, x, y, st);
+    };
+    s = gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream,
+                    mop->has_ff_matvec() && op->precision == FMPB_FP64 ? &Aff : nullptr);
   }
   if (s != FMPB_OK && s != FMPB_ENOCONV) return s;
   const fmpb_status c = fmpb_operator_check(op, stream);

@@ -108,7 +108,13 @@ __global__ void k_dft_axis_ff(const void* in_, void* out_, int O2, int64_t I, in
     }
     const int64_t o = base_out + f * bf + ii;
     if (OUT_FF) {
-      reinterpret_cast<float4*>(out_)[o] = ff_norm(rh, rl, ih, il);
+      float4 v = ff_norm(rh, rl, ih, il);
+      if (scale != 1.0) {   // float-float product with the float-float scale
+        const ff sc = ff_from_d(scale);
+        const ff re = ff_mul(ff{v.x, v.y}, sc), im = ff_mul(ff{v.z, v.w}, sc);
+        v = make_float4(re.h, re.l, im.h, im.l);
+      }
+      reinterpret_cast<float4*>(out_)[o] = v;
     } else {
       cd v = mkc(((double)rh + (double)rl) * scale, ((double)ih + (double)il) * scale);
       cd* d = reinterpret_cast<cd*>(out_) + o;
@@ -125,8 +131,8 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
     set_error("dft_axis: line grid %d x %d exceeds the launch limits", O1, O2);
     return FMPB_EINVAL;
   }
-  if (OUT_FF && (scale != 1.0 || accumulate)) {
-    set_error("dft_axis: scaling and accumulation need complex-double output");
+  if (OUT_FF && accumulate) {
+    set_error("dft_axis: accumulation needs complex-double output");
     return FMPB_EINVAL;
   }
   // inner tile: up to 256 values (one per thread) so that long lines, such
@@ -539,7 +545,7 @@ size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 
 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format, void* tc_rows,
-                            unsigned* tc_err) {
+                            unsigned* tc_err, bool ff_io) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
@@ -549,8 +555,12 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   float4* buf[2] = {reinterpret_cast<float4*>(scratch), reinterpret_cast<float4*>(scratch + (size_t)s.F * RB)};
   int cur = 0;
   // forward x: x[r][cz][cy][cx][b] (complex double) -> [cz][cy][fx][r][b]
-  FMPB_TRY((dft_axis<false, true>("dft_fwd_x", x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
-                                  (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st)));
+  if (ff_io)
+    FMPB_TRY((dft_axis<true, true>("dft_fwd_x", x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
+                                   (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st)));
+  else
+    FMPB_TRY((dft_axis<false, true>("dft_fwd_x", x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
+                                    (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st)));
   // forward y: [cz][cy][fx][rb] -> [cz][fy][fx][rb]
   if (Py > 1) {
     FMPB_TRY((dft_axis<true, true>("dft_fwd_y", buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)My * Px * RB, RB,
@@ -581,8 +591,12 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
     cur = 1 - cur;
   }
   // inverse x with crop and 1/F: [cz][cy][fx][r][b] -> y[r][cz][cy][cx][b] (complex double)
-  FMPB_TRY((dft_axis<true, false>("dft_inv_x", buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
-                                  (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, accumulate, st)));
+  if (ff_io)
+    FMPB_TRY((dft_axis<true, true>("dft_inv_x", buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
+                                   (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, false, st)));
+  else
+    FMPB_TRY((dft_axis<true, false>("dft_inv_x", buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
+                                    (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, accumulate, st)));
   return FMPB_OK;
 }
 

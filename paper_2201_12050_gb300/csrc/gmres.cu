@@ -77,24 +77,6 @@ __global__ void k_reduce_partials(const cd* __restrict__ partial, int nblk, int 
   out[t] = accumulate ? cadd(out[t], s) : s;
 }
 
-// The same sums with one warp per output, for long partial lists: lane l
-// adds partials l, l + 32, ..., then a fixed shuffle tree (deterministic).
-__global__ void k_reduce_partials_warp(const cd* __restrict__ partial, int nblk, int count, cd* __restrict__ out) {
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (t >= count) return;
-  double re = 0.0, im = 0.0;
-  for (int b = lane; b < nblk; b += 32) {
-    const cd v = partial[(int64_t)t * nblk + b];
-    re += v.x;
-    im += v.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    re += __shfl_xor_sync(0xffffffffu, re, o);
-    im += __shfl_xor_sync(0xffffffffu, im, o);
-  }
-  if (lane == 0) out[t] = mkc(re, im);
-}
-
 // y = b - y  (residual from a product)
 __global__ void k_residual(const cd* __restrict__ b, cd* __restrict__ y, int64_t total) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
@@ -251,15 +233,6 @@ __global__ void k_backsolve(GmresState s, int R, int m) {
   for (int i = lane; i <= m; i += 32) g[i] = i < J ? y[i] : mkc(0.0, 0.0);
 }
 
-// Selective reorthogonalisation: need[r] = 1 when the first Gram-Schmidt
-// pass removed more than half of ||w||^2 (Kahan-Parlett "twice is enough").
-__global__ void k_reorth_flag(const cd* __restrict__ before, const cd* __restrict__ after,
-                              const int* __restrict__ active, int* __restrict__ need, int R) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  need[r] = (active[r] && after[r].x < 0.5 * before[r].x) ? 1 : 0;
-}
-
 // ----------------------------------------------- float-float Krylov basis --
 // The basis vectors are stored as float-float pairs (16 bytes per complex
 // entry, as complex double) and every Gram-Schmidt dot product and update
@@ -396,15 +369,45 @@ __global__ void __launch_bounds__(2 * SUB_ROWS) k_subtract_ff(const float4* __re
   }
 }
 
-// ||w||^2 of the last Gram-Schmidt pass each right-hand side ran (the second
-// where need[r]), its square root and inverse.
-__global__ void k_sqrt_select(const cd* __restrict__ first, const cd* __restrict__ second,
-                              const int* __restrict__ need, double* __restrict__ out, double* __restrict__ inv, int R) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// Warp-parallel fixed-order sum of the nblk norm partials of rhs r.
+__device__ __forceinline__ double warp_norm_sum(const cd* __restrict__ pnorm, int nblk, int r, int lane) {
+  double t = 0.0;
+  for (int b = lane; b < nblk; b += 32) t += pnorm[(int64_t)r * nblk + b].x;
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// After the first Gram-Schmidt pass, one warp per rhs: ||w'||^2 from the
+// subtract's partials, and need[r] = 1 when the pass removed more than half
+// of ||w||^2 (before = ||w||^2 from the projection dots).
+__global__ void k_norm_flag(const cd* __restrict__ pnorm, int nblk, const cd* __restrict__ before,
+                            const int* __restrict__ active, cd* __restrict__ after, int* __restrict__ need, int R) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (r >= R) return;
-  const double v = sqrt(fmax((need[r] ? second[r] : first[r]).x, 0.0));
-  out[r] = v;
-  inv[r] = v > 0.0 ? 1.0 / v : 0.0;
+  const double a = warp_norm_sum(pnorm, nblk, r, lane);
+  if (lane == 0) {
+    after[r] = mkc(a, 0.0);
+    need[r] = (active[r] && a < 0.5 * before[r].x) ? 1 : 0;
+  }
+}
+
+// End of the Gram-Schmidt step, one warp per rhs: where the second pass ran,
+// h += h2 and ||w||^2 from its partials; then ||w|| and 1 / ||w||.
+__global__ void k_finish(const cd* __restrict__ pnorm, int nblk, const cd* __restrict__ first,
+                         const int* __restrict__ need, const cd* __restrict__ h2, cd* __restrict__ h, int nvec,
+                         double* __restrict__ wnorm, double* __restrict__ inv, int R) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= R) return;
+  double w2 = first[r].x;
+  if (need[r]) {
+    w2 = warp_norm_sum(pnorm, nblk, r, lane);
+    for (int v = lane; v < nvec; v += 32) h[v * R + r] = cadd(h[v * R + r], h2[v * R + r]);
+  }
+  if (lane == 0) {
+    const double v = sqrt(fmax(w2, 0.0));
+    wnorm[r] = v;
+    inv[r] = v > 0.0 ? 1.0 / v : 0.0;
+  }
 }
 
 // v[r] *= s[r] in float-float
@@ -485,7 +488,7 @@ struct DevBuf {
 }  // namespace
 
 fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
-                        fmpb_solve_info* info, cudaStream_t st) {
+                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff) {
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int m = o.restart > 0 ? o.restart : 30;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
@@ -605,9 +608,13 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     for (int j = 0; j < m && total_it < maxit; ++j) {
       float4* vj = V + (int64_t)j * vstride;
       float4* vn = V + (int64_t)(j + 1) * vstride;
-      FMPB_LAUNCH("ff_to_cd", st, k_ff_to_cd<<<vec_blocks, 256, 0, st>>>(vj, T, vstride));
-      FMPB_TRY(A(R, T, W, st));
-      FMPB_LAUNCH("cd_to_ff", st, k_cd_to_ff<<<vec_blocks, 256, 0, st>>>(W, vn, vstride));
+      if (Aff) {
+        FMPB_TRY((*Aff)(R, vj, vn, st));
+      } else {
+        FMPB_LAUNCH("ff_to_cd", st, k_ff_to_cd<<<vec_blocks, 256, 0, st>>>(vj, T, vstride));
+        FMPB_TRY(A(R, T, W, st));
+        FMPB_LAUNCH("cd_to_ff", st, k_cd_to_ff<<<vec_blocks, 256, 0, st>>>(W, vn, vstride));
+      }
       // classical Gram-Schmidt against v_0..v_j, repeated when the first
       // pass lost more than half of ||w||^2.  w sits in slot j + 1 of the
       // basis, so one launch over slots 0..j+1 gives the projections h_0..h_j
@@ -615,15 +622,12 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vn, R, N, partial, s.active));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
       FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active, pnorm));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials_warp<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, R, nrm2));
-      FMPB_LAUNCH("reorth_flag", st, k_reorth_flag<<<rb, 64, 0, st>>>(h + (int64_t)(j + 1) * R, nrm2, s.active, need, R));
+      FMPB_LAUNCH("reorth_flag", st, k_norm_flag<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, h + (int64_t)(j + 1) * R, s.active, nrm2, need, R));
       FMPB_LAUNCH("dots_reorth", st, k_dots_ff4<<<dim3(nb, (j + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
       FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
       FMPB_LAUNCH("subtract_reorth", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need, pnorm));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials_warp<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, R, nrm2 + R));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(h2, 1, (j + 1) * R, h, 1));
-      // ||w||, normalise
-      FMPB_LAUNCH("sqrt_real", st, k_sqrt_select<<<rb, 64, 0, st>>>(nrm2, nrm2 + R, need, wnorm, s.inv, R));
+      // h += h2 and ||w|| where the second pass ran; normalise
+      FMPB_LAUNCH("sqrt_real", st, k_finish<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, nrm2, need, h2, h, j + 1, wnorm, s.inv, R));
       FMPB_LAUNCH("scale", st, k_scale_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, s.inv, R, N, s.active));
       FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
       FMPB_CUDA(cudaGetLastError());

@@ -8,9 +8,12 @@ namespace fmpb {
 
 // y = A x for R stacked vectors of length N on stream st.
 typedef std::function<fmpb_status(int R, const cd* x, cd* y, cudaStream_t st)> MatvecFn;
+// The same product on float-float vectors (float4 per value), where the
+// operator has one; it saves the conversions around every Arnoldi product.
+typedef std::function<fmpb_status(int R, const float4* x, float4* y, cudaStream_t st)> MatvecFfFn;
 
 fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
-                        fmpb_solve_info* info, cudaStream_t st);
+                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff = nullptr);
 // GMRES-IR: accurate residuals with A, corrections by GMRES with Alow.
 fmpb_status gmres_refined(const MatvecFn& A, const MatvecFn& Alow, int R, int64_t N, const cd* b, cd* x,
                           const fmpb_solve_opts& o, fmpb_solve_info* info, cudaStream_t st);

@@ -94,7 +94,9 @@ fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaSt
 enum SpecFormat { SPEC_CD = 0, SPEC_FF = 1, SPEC_F32 = 2, SPEC_BF16 = 3 };
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD,
-                            void* tc_rows = nullptr, unsigned* tc_err = nullptr);
+                            void* tc_rows = nullptr, unsigned* tc_err = nullptr, bool ff_io = false);
+// ff_io: x and y are float-float vectors (float4 per value, passed as cd*;
+// same 16 bytes) instead of complex double; accumulate must be false.
 // float-float spectrum -> complex FP32 (out has n float2 entries)
 fmpb_status spectrum_ff_to_f32(const cd* in, void* out, size_t n, cudaStream_t st);
 // In-place conversion of n complex doubles to float-float pairs (re_hi, re_lo, im_hi, im_lo).
