@@ -133,6 +133,11 @@ __device__ __forceinline__ ffc ffc_add(ffc a, ffc b) { return {ff_add(a.re, b.re
 __device__ __forceinline__ ffc ffc_sub(ffc a, ffc b) { return {ff_sub(a.re, b.re), ff_sub(a.im, b.im)}; }
 __device__ __forceinline__ ffc ffc_scale(ffc a, ff c) { return {ff_mul(a.re, c), ff_mul(a.im, c)}; }
 __device__ __forceinline__ ffc ffc_conj(ffc a) { return {a.re, ff_neg(a.im)}; }
+__device__ __forceinline__ ffc ffc_neg(ffc a) { return {ff_neg(a.re), ff_neg(a.im)}; }
+__device__ __forceinline__ ffc ffc_shfl_up(ffc a, int off) {
+  return {{__shfl_up_sync(0xffffffffu, a.re.h, off), __shfl_up_sync(0xffffffffu, a.re.l, off)},
+          {__shfl_up_sync(0xffffffffu, a.im.h, off), __shfl_up_sync(0xffffffffu, a.im.l, off)}};
+}
 
 __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* __restrict__ wnorm, int R, int m,
                          int j, double tol) {
@@ -148,20 +153,47 @@ __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* _
     snv[i] = ffc_from_cd(s.sn[r * m + i]);
   }
   __syncwarp();
-  __shared__ cd top;
-  if (lane == 0) {
-    // [c  s; -conj(s) c] applied to (col[i], col[i+1]) for i < j; the entry
-    // carried from one rotation to the next stays in registers
-    ffc a = col[0];
-#pragma unroll 4
-    for (int i = 0; i < j; ++i) {
+  // [c  s; -conj(s) c] applied to (a_i, h_{i+1}) for i < j, a_0 = h_0: the
+  // rotated entry is c_i a_i + s_i h_{i+1} and the carried one
+  // a_{i+1} = -conj(s_i) a_i + c_i h_{i+1}, an affine recurrence.  Each lane
+  // composes the maps of one chunk of ceil(j/32) rotations, a shuffle scan
+  // gives every lane the value entering its chunk, and each lane then
+  // rotates its chunk: sequential depth about 2 j / 32 + 5 instead of j.
+  cd* Hcol = s.H + ((int64_t)r * m + j) * (m + 1);
+  __shared__ ffc carry;
+  {
+    const int L = (j + 31) / 32;
+    const int i0 = min(j, lane * L), i1 = min(j, i0 + L);
+    const ffc one = {ff_make(1.f), ff_make(0.f)}, zero = {ff_make(0.f), ff_make(0.f)};
+    ffc al = one, be = zero;   // chunk map z -> al z + be
+    for (int i = i0; i < i1; ++i) {
+      const ffc ai = ffc_neg(ffc_conj(snv[i]));
+      be = ffc_add(ffc_mul(ai, be), ffc_scale(col[i + 1], csv[i]));
+      al = ffc_mul(ai, al);
+    }
+    for (int off = 1; off < 32; off <<= 1) {   // inclusive scan: later map after earlier
+      const ffc pa = ffc_shfl_up(al, off), pb = ffc_shfl_up(be, off);
+      if (lane >= off) {
+        be = ffc_add(ffc_mul(al, pb), be);
+        al = ffc_mul(al, pa);
+      }
+    }
+    const ffc pa = ffc_shfl_up(al, 1), pb = ffc_shfl_up(be, 1);
+    const ffc a0 = col[0];
+    ffc a = lane == 0 ? a0 : ffc_add(ffc_mul(pa, a0), pb);
+    for (int i = i0; i < i1; ++i) {
       const ff c = csv[i];
       const ffc sn = snv[i];
       const ffc b = col[i + 1];
-      col[i] = ffc_add(ffc_scale(a, c), ffc_mul(sn, b));
+      Hcol[i] = ffc_to_cd(ffc_add(ffc_scale(a, c), ffc_mul(sn, b)));
       a = ffc_sub(ffc_scale(b, c), ffc_mul(ffc_conj(sn), a));
     }
-    cd ad = ffc_to_cd(a);
+    if ((i0 < i1 && i1 == j) || (j == 0 && lane == 0)) carry = a;
+  }
+  __syncwarp();
+  __shared__ cd top;
+  if (lane == 0) {
+    cd ad = ffc_to_cd(carry);
     const cd b = mkc(wnorm[r], 0.0);
     const double na = hypot(ad.x, ad.y), nb = hypot(b.x, b.y);
     double c;
@@ -193,8 +225,6 @@ __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* _
     if (rel <= tol || wnorm[r] == 0.0) s.active[r] = 0;
   }
   __syncwarp();
-  cd* Hcol = s.H + ((int64_t)r * m + j) * (m + 1);
-  for (int i = lane; i < j; i += 32) Hcol[i] = ffc_to_cd(col[i]);
   if (lane == 0) {
     Hcol[j] = top;
     Hcol[j + 1] = mkc(0.0, 0.0);
