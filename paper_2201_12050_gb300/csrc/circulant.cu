@@ -67,10 +67,15 @@ int64_t offset_slot(const CircShape& s, int dx, int dy, int dz) {
 // buffer can change format in place.  A CTA loads one (o1, o2) line group
 // for TI consecutive inner indices into shared memory before writing, so the
 // call may run in place when in and out use the same strides.
+// P1 > 0 selects the two-factor (Cooley-Tukey) form for P = P1 P2: with
+// n = P2 n1 + n2 and f = k1 + P1 k2,
+//   Y[n2][k1] = w^{n2 k1} sum_{n1} in[P2 n1 + n2] w^{P2 n1 k1}   (P2 DFTs of length P1),
+//   out[k1 + P1 k2] = sum_{n2} Y[n2][k1] w^{P1 n2 k2}           (P1 DFTs of length P2),
+// P1 Pin + P + Pout P2 products per line instead of Pout Pin.
 template <bool IN_FF, bool OUT_FF>
 __global__ void k_dft_axis_ff(const void* in_, void* out_, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj,
                               int64_t b1, int64_t b2, int64_t bf, int Pin, int Pout, int P, int sign, double scale,
-                              int accumulate, int TI) {
+                              int accumulate, int TI, int P1) {
   extern __shared__ float4 smf[];
   float4* tw = smf;          // P twiddles (float-float)
   float4* tile = smf + P;    // Pin x TI
@@ -95,16 +100,47 @@ __global__ void k_dft_axis_ff(const void* in_, void* out_, int O2, int64_t I, in
     tile[e] = v;
   }
   __syncthreads();
+  const int P2 = P1 > 0 ? P / P1 : 0;
+  float4* Y = tile + Pin * TI;   // two-factor form: P x TI intermediate values
+  if (P1 > 0) {
+    for (int e = threadIdx.x; e < P * TI; e += blockDim.x) {
+      const int q = e / TI, ii = e - q * TI;   // q = n2 P1 + k1
+      const int n2 = q / P1, k1 = q - n2 * P1;
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      const int step = (P2 * k1) % P;
+      int idx = 0;
+      for (int n = n2; n < Pin; n += P2) {
+        ff_cmac(tw[idx], tile[n * TI + ii], rh, rl, ih, il);
+        idx += step;
+        if (idx >= P) idx -= P;
+      }
+      float ar = 0.f, al = 0.f, ai = 0.f, ail = 0.f;
+      ff_cmac(tw[(n2 * k1) % P], ff_norm(rh, rl, ih, il), ar, al, ai, ail);
+      Y[e] = ff_norm(ar, al, ai, ail);
+    }
+    __syncthreads();
+  }
   const int64_t base_out = o1 * b1 + o2 * b2 + i0;
   for (int e = threadIdx.x; e < Pout * TI; e += blockDim.x) {
     const int f = e / TI, ii = e - f * TI;
     if (i0 + ii >= I) continue;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    int idx = 0;
-    for (int j = 0; j < Pin; ++j) {
-      ff_cmac(tw[idx], tile[j * TI + ii], rh, rl, ih, il);
-      idx += f;
-      if (idx >= P) idx -= P;
+    if (P1 > 0) {
+      const int k1 = f % P1, k2 = f / P1;
+      const int step = (P1 * k2) % P;
+      int idx = 0;
+      for (int n2 = 0; n2 < P2; ++n2) {
+        ff_cmac(tw[idx], Y[(n2 * P1 + k1) * TI + ii], rh, rl, ih, il);
+        idx += step;
+        if (idx >= P) idx -= P;
+      }
+    } else {
+      int idx = 0;
+      for (int j = 0; j < Pin; ++j) {
+        ff_cmac(tw[idx], tile[j * TI + ii], rh, rl, ih, il);
+        idx += f;
+        if (idx >= P) idx -= P;
+      }
     }
     const int64_t o = base_out + f * bf + ii;
     if (OUT_FF) {
@@ -138,10 +174,27 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
   // inner tile: up to 256 values (one per thread) so that long lines, such
   // as the operator's block columns, run in few CTAs that each amortise their
   // twiddle table; shrunk to the shared-memory budget and to fill the GPU
+  // two-factor form when it saves at least a fifth of the products
+  int P1 = 0;
+  {
+    const int64_t direct = (int64_t)Pout * Pin;
+    int64_t best = direct;
+    for (int a = 2; a * 2 <= P; ++a) {
+      if (P % a) continue;
+      const int b = P / a;
+      const int64_t cost = (int64_t)a * Pin + P + (int64_t)Pout * b;
+      if (cost < best) {
+        best = cost;
+        P1 = a;
+      }
+    }
+    if (5 * best > 4 * direct) P1 = 0;
+  }
+  const int per_ti = Pin + (P1 > 0 ? P : 0);   // shared float4 values per inner index
   const size_t budget = 96 * 1024;
   int64_t TI = 256;
-  while (TI > 1 && (size_t)(Pin * TI + P) * sizeof(float4) > budget) TI /= 2;
-  if ((size_t)(Pin * TI + P) * sizeof(float4) > 200 * 1024) {
+  while (TI > 1 && (size_t)(per_ti * TI + P) * sizeof(float4) > budget) TI /= 2;
+  if ((size_t)(per_ti * TI + P) * sizeof(float4) > 200 * 1024) {
     set_error("dft_axis: axis length %d too large", P);
     return FMPB_EINVAL;
   }
@@ -149,13 +202,13 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
   // enough CTAs to fill the 152 SMs several times over: shrink the inner
   // tile (down to 4 values, 64-byte segments) while the grid is small
   while (TI > 4 && ((I + TI - 1) / TI) * (int64_t)O1 * O2 < 4 * 152) TI /= 2;
-  size_t smem = (size_t)(Pin * TI + P) * sizeof(float4);
+  size_t smem = (size_t)(per_ti * TI + P) * sizeof(float4);
   if (smem > 48 * 1024)
     FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis_ff<IN_FF, OUT_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
   FMPB_LAUNCH(name, st, k_dft_axis_ff<IN_FF, OUT_FF><<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P,
-                                                                           sign, scale, accumulate ? 1 : 0, (int)TI));
+                                                                           sign, scale, accumulate ? 1 : 0, (int)TI, P1));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
