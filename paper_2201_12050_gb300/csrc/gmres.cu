@@ -440,6 +440,230 @@ __global__ void k_finish(const cd* __restrict__ pnorm, int nblk, const cd* __res
   }
 }
 
+// ------------------------------------- delayed reorthogonalisation (DCGS2) --
+// Classical Gram-Schmidt with the second (reorthogonalising) pass of step
+// j - 1 folded into the projections of step j, so that a step reads the basis
+// twice instead of four times.  State at step j: q_0..q_{j-1} orthonormal in
+// slots 0..j-1, the pending vector p (the product of step j - 1 projected
+// once, not normalised) in slot j, and the first-pass coefficients s_prev of
+// column j - 1.  With z = A p in slot j + 1:
+//   t = Q^H p, b = Q^H z, pp = p^H p, pz = p^H z           (one dots pass)
+//   beta = sqrt(pp - |t|^2),  q_j = (p - Q t) / beta
+//   column j - 1 of H: s_prev + t, subdiagonal beta
+//   c = [b ; (pz - t^H b) / beta] = Q_{j+1}^H z
+//   next pending (z - Q_{j+1} c) / beta,  its first-pass coefficients
+//   s = (c - H t) / beta  (H: the raw Hessenberg columns 0..j-1)
+// (A q_j = (z - A Q t) / beta and A Q = Q_{j+1} H.)
+
+// partial sums of conj(V_v) p and conj(V_v) z (v < nvec), DOT_VB vectors per
+// CTA, both targets from each loaded basis row
+__global__ void __launch_bounds__(RED_THREADS) k_dots2_ff(const float4* __restrict__ V, int64_t vstride, int nvec,
+                                                          const float4* __restrict__ p, const float4* __restrict__ z,
+                                                          int R, int64_t N, cd* __restrict__ part_p,
+                                                          cd* __restrict__ part_z, const int* __restrict__ active) {
+  const int blk = blockIdx.x, v0 = blockIdx.y * DOT_VB, r = blockIdx.z;
+  const int nq = min(DOT_VB, nvec - v0);
+  float ph[DOT_VB], pl[DOT_VB], pih[DOT_VB], pil[DOT_VB];
+  float zh[DOT_VB], zl[DOT_VB], zih[DOT_VB], zil[DOT_VB];
+#pragma unroll
+  for (int q = 0; q < DOT_VB; ++q) ph[q] = pl[q] = pih[q] = pil[q] = zh[q] = zl[q] = zih[q] = zil[q] = 0.f;
+  if (active[r]) {
+    const float4* a = V + (int64_t)v0 * vstride + (int64_t)r * N;
+    const float4* pr = p + (int64_t)r * N;
+    const float4* zr = z + (int64_t)r * N;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < N; i += stride) {
+      const float4 yp = pr[i], yz = zr[i];
+      float4 x[DOT_VB];
+#pragma unroll
+      for (int q = 0; q < DOT_VB; ++q) x[q] = q < nq ? a[(int64_t)q * vstride + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < DOT_VB; ++q) {
+        const float4 cx = ff_conj(x[q]);
+        ff_cmac(cx, yp, ph[q], pl[q], pih[q], pil[q]);
+        ff_cmac(cx, yz, zh[q], zl[q], zih[q], zil[q]);
+      }
+    }
+  }
+  __shared__ float4 sh[2][RED_THREADS / 32][DOT_VB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < DOT_VB; ++q) {
+    ff_warp_sum(ph[q], pl[q]);
+    ff_warp_sum(pih[q], pil[q]);
+    ff_warp_sum(zh[q], zl[q]);
+    ff_warp_sum(zih[q], zil[q]);
+    if (lane == 0) {
+      sh[0][warp][q] = make_float4(ph[q], pl[q], pih[q], pil[q]);
+      sh[1][warp][q] = make_float4(zh[q], zl[q], zih[q], zil[q]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * nq) {
+    const int tgt = threadIdx.x / nq, q = threadIdx.x - tgt * nq;
+    double re = 0.0, im = 0.0;
+    for (int u = 0; u < RED_THREADS / 32; ++u) {
+      const float4 t = sh[tgt][u][q];
+      re += (double)t.x + (double)t.y;
+      im += (double)t.z + (double)t.w;
+    }
+    cd* out = tgt ? part_z : part_p;
+    out[((int64_t)(v0 + q) * R + r) * gridDim.x + blk] = mkc(re, im);
+  }
+}
+
+// One warp per rhs: beta, the final column j - 1 (hc, raw copy in Hraw,
+// subdiagonal in wnorm) and the update coefficients c.  t = hA[0..j-1],
+// pp = hA[j], b = hB[0..j-1], pz = hB[j].
+__global__ void k_dcgs_coef(GmresState s, const cd* __restrict__ hA, const cd* __restrict__ hB,
+                            const cd* __restrict__ sprev, cd* __restrict__ hc, cd* __restrict__ cbuf,
+                            cd* __restrict__ Hraw, double* __restrict__ wnorm, int R, int m, int j) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= R || !s.active[r]) return;
+  double tt = 0.0, tbr = 0.0, tbi = 0.0;
+  for (int v = lane; v < j; v += 32) {
+    const cd t = hA[v * R + r], b = hB[v * R + r];
+    tt = fma(t.x, t.x, fma(t.y, t.y, tt));
+    tbr = fma(t.x, b.x, fma(t.y, b.y, tbr));   // conj(t) b
+    tbi = fma(t.x, b.y, fma(-t.y, b.x, tbi));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tt += __shfl_xor_sync(0xffffffffu, tt, o);
+    tbr += __shfl_xor_sync(0xffffffffu, tbr, o);
+    tbi += __shfl_xor_sync(0xffffffffu, tbi, o);
+  }
+  const double b2 = hA[j * R + r].x - tt;
+  const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  cd* Hc = Hraw + ((int64_t)r * m + (j > 0 ? j - 1 : 0)) * (m + 1);
+  for (int v = lane; v < j; v += 32) {
+    const cd val = cadd(sprev[v * R + r], hA[v * R + r]);
+    hc[v * R + r] = val;
+    Hc[v] = val;
+    cbuf[v * R + r] = hB[v * R + r];
+  }
+  if (lane == 0) {
+    if (j > 0) {
+      Hc[j] = mkc(beta, 0.0);
+      wnorm[r] = beta;
+    }
+    const cd pz = hB[j * R + r];
+    cbuf[j * R + r] = cmulr(mkc(pz.x - tbr, pz.y - tbi), inv);
+    s.inv[r] = inv;
+  }
+}
+
+// s_new[i] = (c_i - sum_{v < j} H[i][v] t_v) / beta for rows i <= j (the
+// first-pass coefficients of the new pending column), one warp per row.
+__global__ void k_hess_t(const int* __restrict__ active, const cd* __restrict__ Hraw, const cd* __restrict__ hA,
+                         const cd* __restrict__ cbuf, const double* __restrict__ inv, cd* __restrict__ sprev, int R,
+                         int m, int j) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int r = blockIdx.y;
+  if (i > j || !active[r]) return;
+  double gr = 0.0, gi = 0.0;
+  for (int v = max(0, i - 1) + lane; v < j; v += 32) {
+    const cd hv = Hraw[((int64_t)r * m + v) * (m + 1) + i], t = hA[v * R + r];
+    gr = fma(hv.x, t.x, fma(-hv.y, t.y, gr));
+    gi = fma(hv.x, t.y, fma(hv.y, t.x, gi));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+  }
+  if (lane == 0) {
+    const cd c = cbuf[i * R + r];
+    sprev[i * R + r] = cmulr(mkc(c.x - gr, c.y - gi), inv[r]);
+  }
+}
+
+// q_j = (p - Q t) / beta into slot j and the next pending vector
+// (z - Q c_{0..j-1} - q_j c_j) / beta into slot j + 1, in one pass over
+// q_0..q_{j-1} (two products per loaded basis row).  The two halves of a CTA
+// take the two halves of the basis for the same rows and are combined in
+// shared memory in a fixed order.
+__global__ void __launch_bounds__(2 * SUB_ROWS) k_update2_ff(float4* __restrict__ V, int64_t vstride, int j,
+                                                             const cd* __restrict__ hA, const cd* __restrict__ cbuf,
+                                                             const double* __restrict__ inv, int R, int64_t N,
+                                                             const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  __shared__ float4 ts[MAX_RESTART], cs[MAX_RESTART];
+  __shared__ float4 op[SUB_ROWS], oz[SUB_ROWS];
+  for (int v = threadIdx.x; v < j; v += blockDim.x) {
+    const cd t = hA[v * R + r], c = cbuf[v * R + r];
+    ts[v] = split_ff(mkc(-t.x, -t.y));
+    cs[v] = split_ff(mkc(-c.x, -c.y));
+  }
+  const ff invf = ff_from_d(inv[r]);
+  const cd cj = cbuf[j * R + r];
+  const float4 mcj = split_ff(mkc(-cj.x, -cj.y));
+  const int row = threadIdx.x & (SUB_ROWS - 1), half = threadIdx.x / SUB_ROWS;
+  const int nh = (j + 1) / 2;
+  const int vb = half ? nh : 0, ve = half ? j : nh;
+  __syncthreads();
+  float4* P = V + (int64_t)j * vstride + (int64_t)r * N;
+  float4* Z = V + (int64_t)(j + 1) * vstride + (int64_t)r * N;
+  const float4* Vr = V + (int64_t)r * N;
+  for (int64_t base = (int64_t)blockIdx.x * SUB_ROWS; base < N; base += (int64_t)gridDim.x * SUB_ROWS) {
+    const int64_t i = base + row;
+    const bool ok = i < N;
+    float ph = 0.f, pl = 0.f, pih = 0.f, pil = 0.f, zh = 0.f, zl = 0.f, zih = 0.f, zil = 0.f;
+    if (ok) {
+      if (!half) {
+        const float4 p0 = P[i], z0 = Z[i];
+        ph = p0.x;
+        pl = p0.y;
+        pih = p0.z;
+        pil = p0.w;
+        zh = z0.x;
+        zl = z0.y;
+        zih = z0.z;
+        zil = z0.w;
+      }
+      int v = vb;
+      for (; v + 3 < ve; v += 4) {
+        float4 a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ff_cmac(a[q], ts[v + q], ph, pl, pih, pil);
+          ff_cmac(a[q], cs[v + q], zh, zl, zih, zil);
+        }
+      }
+      for (; v < ve; ++v) {
+        const float4 a = Vr[(int64_t)v * vstride + i];
+        ff_cmac(a, ts[v], ph, pl, pih, pil);
+        ff_cmac(a, cs[v], zh, zl, zih, zil);
+      }
+    }
+    if (half) {
+      op[row] = make_float4(ph, pl, pih, pil);
+      oz[row] = make_float4(zh, zl, zih, zil);
+    }
+    __syncthreads();
+    if (!half && ok) {
+      float s1, e1, s2, e2;
+      const float4 a = op[row], b = oz[row];
+      two_sum_f(ph, a.x, s1, e1);
+      two_sum_f(pih, a.z, s2, e2);
+      const float4 pv = ff_norm(s1, (pl + a.y) + e1, s2, (pil + a.w) + e2);
+      const ff qre = ff_mul(ff{pv.x, pv.y}, invf), qim = ff_mul(ff{pv.z, pv.w}, invf);
+      const float4 q = make_float4(qre.h, qre.l, qim.h, qim.l);
+      two_sum_f(zh, b.x, s1, e1);
+      two_sum_f(zih, b.z, s2, e2);
+      float wh = s1, wl = (zl + b.y) + e1, wih = s2, wil = (zil + b.w) + e2;
+      ff_cmac(q, mcj, wh, wl, wih, wil);
+      const float4 wv = ff_norm(wh, wl, wih, wil);
+      const ff wre = ff_mul(ff{wv.x, wv.y}, invf), wim = ff_mul(ff{wv.z, wv.w}, invf);
+      P[i] = q;
+      Z[i] = make_float4(wre.h, wre.l, wim.h, wim.l);
+    }
+    __syncthreads();
+  }
+}
+
 // v[r] *= s[r] in float-float
 __global__ void k_scale_ff(float4* __restrict__ v, const double* __restrict__ s, int R, int64_t N,
                            const int* __restrict__ active) {
@@ -533,6 +757,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   // control state: carve one allocation; the first pass (base = null) sizes it
   GmresState s;
   cd *h = nullptr, *h2 = nullptr, *nrm2 = nullptr, *pnorm = nullptr;
+  cd *hB = nullptr, *sprev = nullptr, *cbuf = nullptr, *hc = nullptr;
   double *wnorm = nullptr;
   int *all_active = nullptr, *bad = nullptr, *need = nullptr;
   size_t small = 0;
@@ -550,6 +775,10 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     h = (cd*)take(sizeof(cd) * (size_t)R * (m + 2));
     h2 = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
     nrm2 = (cd*)take(sizeof(cd) * 2 * (size_t)R);
+    hB = (cd*)take(sizeof(cd) * (size_t)R * (m + 2));
+    sprev = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+    cbuf = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
+    hc = (cd*)take(sizeof(cd) * (size_t)R * (m + 1));
     pnorm = (cd*)take(sizeof(cd) * (size_t)R * 152 * 8);
     s.cs = (double*)take(sizeof(double) * (size_t)R * m);
     s.beta = (double*)take(sizeof(double) * R);
@@ -568,7 +797,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
           cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess ||
           cudaMalloc(&Tb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
-          cudaMalloc(&Pb.p, sizeof(cd) * (size_t)(m + 2) * R * RED_BLOCKS) != cudaSuccess) {
+          cudaMalloc(&Pb.p, 2 * sizeof(cd) * (size_t)(m + 2) * R * RED_BLOCKS) != cudaSuccess) {
         cudaGetLastError();
         set_error("gmres: cannot allocate the Krylov basis (%zu bytes)", sizeof(cd) * (size_t)(m + 2) * vstride);
         return FMPB_ENOMEM;
@@ -579,6 +808,16 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   cd* W = (cd*)Wb.p;           // product output / residual (FP64)
   cd* T = (cd*)Tb.p;           // product input (FP64 copy of v_j)
   cd* partial = (cd*)Pb.p;
+  cd* partial2 = partial + (size_t)(m + 2) * R * RED_BLOCKS;
+  // delayed reorthogonalisation (one basis read less per pass) where the
+  // operator multiplies float-float vectors, with the raw Hessenberg columns
+  // kept for the H t corrections
+  DevBuf Hb;
+  const size_t hraw_bytes = sizeof(cd) * (size_t)R * m * (m + 1);
+  const bool dcgs2 = Aff != nullptr && hraw_bytes <= ((size_t)1 << 30) &&
+                     cudaMalloc(&Hb.p, hraw_bytes) == cudaSuccess;
+  if (!dcgs2) cudaGetLastError();
+  cd* Hraw = (cd*)Hb.p;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
   const unsigned sub_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + SUB_ROWS - 1) / SUB_ROWS, 152 * 8));
@@ -635,57 +874,108 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     if (!any) break;
     int block = 4, since = 0;
     double last_res = -1.0;
-    for (int j = 0; j < m && total_it < maxit; ++j) {
-      float4* vj = V + (int64_t)j * vstride;
-      float4* vn = V + (int64_t)(j + 1) * vstride;
-      if (Aff) {
+    if (dcgs2) {
+      int jdone = 0;
+      for (int j = 0; j < m && total_it < maxit; ++j) {
+        float4* vj = V + (int64_t)j * vstride;       // pending p
+        float4* vn = V + (int64_t)(j + 1) * vstride; // z = A p
         FMPB_TRY((*Aff)(R, vj, vn, st));
-      } else {
-        FMPB_LAUNCH("ff_to_cd", st, k_ff_to_cd<<<vec_blocks, 256, 0, st>>>(vj, T, vstride));
-        FMPB_TRY(A(R, T, W, st));
-        FMPB_LAUNCH("cd_to_ff", st, k_cd_to_ff<<<vec_blocks, 256, 0, st>>>(W, vn, vstride));
-      }
-      // classical Gram-Schmidt against v_0..v_j, repeated when the first
-      // pass lost more than half of ||w||^2.  w sits in slot j + 1 of the
-      // basis, so one launch over slots 0..j+1 gives the projections h_0..h_j
-      // and ||w||^2 (entry j + 1).
-      FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vn, R, N, partial, s.active));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
-      FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active, pnorm));
-      FMPB_LAUNCH("reorth_flag", st, k_norm_flag<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, h + (int64_t)(j + 1) * R, s.active, nrm2, need, R));
-      FMPB_LAUNCH("dots_reorth", st, k_dots_ff4<<<dim3(nb, (j + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
-      FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
-      FMPB_LAUNCH("subtract_reorth", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need, pnorm));
-      // h += h2 and ||w|| where the second pass ran; normalise
-      FMPB_LAUNCH("sqrt_real", st, k_finish<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, nrm2, need, h2, h, j + 1, wnorm, s.inv, R));
-      FMPB_LAUNCH("scale", st, k_scale_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, s.inv, R, N, s.active));
-      FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
-      FMPB_CUDA(cudaGetLastError());
-      ++total_it;
-      // The host looks at the convergence flags only every `block`
-      // iterations; in between it keeps enqueueing, and the Arnoldi kernels
-      // of converged right-hand sides return at once (device-side flags).
-      if (++since < block && j + 1 < m && total_it < maxit) continue;
-      FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-      FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-      FMPB_CUDA(cudaStreamSynchronize(st));
-      any = false;
-      double cur = 0.0;
-      for (int r = 0; r < R; ++r)
-        if (hact[r]) {
-          any = true;
-          cur = std::max(cur, hest[r]);
+        jdone = j + 1;
+        FMPB_LAUNCH("dots", st, k_dots2_ff<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb, (j + 1) * R, hB, 0));
+        FMPB_LAUNCH("reorth_flag", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
+        FMPB_LAUNCH("sqrt_real", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
+        FMPB_LAUNCH("subtract_projection", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
+        if (j >= 1) FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, j - 1, tol));
+        FMPB_CUDA(cudaGetLastError());
+        ++total_it;
+        // The host looks at the convergence flags only every `block`
+        // iterations; in between it keeps enqueueing, and the Arnoldi kernels
+        // of converged right-hand sides return at once (device-side flags).
+        if (++since < block && j + 1 < m && total_it < maxit) continue;
+        FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+        FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        FMPB_CUDA(cudaStreamSynchronize(st));
+        any = false;
+        double cur = 0.0;
+        for (int r = 0; r < R; ++r)
+          if (hact[r]) {
+            any = true;
+            cur = std::max(cur, hest[r]);
+          }
+        if (!any) break;
+        if (o.timeout_ms > 0 &&
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+                o.timeout_ms) {
+          timed_out = true;
+          break;
         }
-      if (!any) break;
-      if (o.timeout_ms > 0 &&
-          std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
-              o.timeout_ms) {
-        timed_out = true;
-        break;
+        block = next_block(last_res, cur, since, tol);
+        last_res = cur;
+        since = 0;
       }
-      block = next_block(last_res, cur, since, tol);
-      last_res = cur;
-      since = 0;
+      // finish the pending column (a full cycle, or the iteration limit)
+      if (any && jdone > 0) {
+        FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((jdone + 1) * R, 64), 64, 0, st>>>(partial, nb, (jdone + 1) * R, h, 0));
+        FMPB_LAUNCH("reorth_flag", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
+        FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, jdone - 1, tol));
+        FMPB_CUDA(cudaGetLastError());
+      }
+    } else {
+      for (int j = 0; j < m && total_it < maxit; ++j) {
+        float4* vj = V + (int64_t)j * vstride;
+        float4* vn = V + (int64_t)(j + 1) * vstride;
+        if (Aff) {
+          FMPB_TRY((*Aff)(R, vj, vn, st));
+        } else {
+          FMPB_LAUNCH("ff_to_cd", st, k_ff_to_cd<<<vec_blocks, 256, 0, st>>>(vj, T, vstride));
+          FMPB_TRY(A(R, T, W, st));
+          FMPB_LAUNCH("cd_to_ff", st, k_cd_to_ff<<<vec_blocks, 256, 0, st>>>(W, vn, vstride));
+        }
+        // classical Gram-Schmidt against v_0..v_j, repeated when the first
+        // pass lost more than half of ||w||^2.  w sits in slot j + 1 of the
+        // basis, so one launch over slots 0..j+1 gives the projections h_0..h_j
+        // and ||w||^2 (entry j + 1).
+        FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vn, R, N, partial, s.active));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
+        FMPB_LAUNCH("subtract_projection", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h, vn, R, N, s.active, pnorm));
+        FMPB_LAUNCH("reorth_flag", st, k_norm_flag<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, h + (int64_t)(j + 1) * R, s.active, nrm2, need, R));
+        FMPB_LAUNCH("dots_reorth", st, k_dots_ff4<<<dim3(nb, (j + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 1, vn, R, N, partial, need));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial, nb, (j + 1) * R, h2, 0));
+        FMPB_LAUNCH("subtract_reorth", st, k_subtract_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j + 1, h2, vn, R, N, need, pnorm));
+        // h += h2 and ||w|| where the second pass ran; normalise
+        FMPB_LAUNCH("sqrt_real", st, k_finish<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, nrm2, need, h2, h, j + 1, wnorm, s.inv, R));
+        FMPB_LAUNCH("scale", st, k_scale_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, s.inv, R, N, s.active));
+        FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
+        FMPB_CUDA(cudaGetLastError());
+        ++total_it;
+        // The host looks at the convergence flags only every `block`
+        // iterations; in between it keeps enqueueing, and the Arnoldi kernels
+        // of converged right-hand sides return at once (device-side flags).
+        if (++since < block && j + 1 < m && total_it < maxit) continue;
+        FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+        FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        FMPB_CUDA(cudaStreamSynchronize(st));
+        any = false;
+        double cur = 0.0;
+        for (int r = 0; r < R; ++r)
+          if (hact[r]) {
+            any = true;
+            cur = std::max(cur, hest[r]);
+          }
+        if (!any) break;
+        if (o.timeout_ms > 0 &&
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+                o.timeout_ms) {
+          timed_out = true;
+          break;
+        }
+        block = next_block(last_res, cur, since, tol);
+        last_res = cur;
+        since = 0;
+      }
     }
     FMPB_LAUNCH("backsolve", st, k_backsolve<<<R, 32, 0, st>>>(s, R, m));
     FMPB_LAUNCH("update_x", st, k_update_x_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
