@@ -881,12 +881,12 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         float4* vn = V + (int64_t)(j + 1) * vstride; // z = A p
         FMPB_TRY((*Aff)(R, vj, vn, st));
         jdone = j + 1;
-        FMPB_LAUNCH("dots", st, k_dots2_ff<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
+        FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb, (j + 1) * R, hB, 0));
-        FMPB_LAUNCH("reorth_flag", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
-        FMPB_LAUNCH("sqrt_real", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
-        FMPB_LAUNCH("subtract_projection", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
+        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
+        FMPB_LAUNCH("dcgs2_hess_t", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
+        FMPB_LAUNCH("update_dcgs2", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
         if (j >= 1) FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, j - 1, tol));
         FMPB_CUDA(cudaGetLastError());
         ++total_it;
@@ -919,7 +919,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       if (any && jdone > 0) {
         FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((jdone + 1) * R, 64), 64, 0, st>>>(partial, nb, (jdone + 1) * R, h, 0));
-        FMPB_LAUNCH("reorth_flag", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
+        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
         FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, jdone - 1, tol));
         FMPB_CUDA(cudaGetLastError());
       }
