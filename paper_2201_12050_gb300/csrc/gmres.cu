@@ -455,18 +455,20 @@ __global__ void k_finish(const cd* __restrict__ pnorm, int nblk, const cd* __res
 //   s = (c - H t) / beta  (H: the raw Hessenberg columns 0..j-1)
 // (A q_j = (z - A Q t) / beta and A Q = Q_{j+1} H.)
 
-// partial sums of conj(V_v) p and conj(V_v) z (v < nvec), DOT_VB vectors per
-// CTA, both targets from each loaded basis row
+// partial sums of conj(V_v) p and conj(V_v) z (v < nvec), DOT2_VB vectors per
+// CTA, both targets from each loaded basis row (two vectors per CTA keep the
+// registers low enough for four CTAs per SM)
+constexpr int DOT2_VB = 2;
 __global__ void __launch_bounds__(RED_THREADS) k_dots2_ff(const float4* __restrict__ V, int64_t vstride, int nvec,
                                                           const float4* __restrict__ p, const float4* __restrict__ z,
                                                           int R, int64_t N, cd* __restrict__ part_p,
                                                           cd* __restrict__ part_z, const int* __restrict__ active) {
-  const int blk = blockIdx.x, v0 = blockIdx.y * DOT_VB, r = blockIdx.z;
-  const int nq = min(DOT_VB, nvec - v0);
-  float ph[DOT_VB], pl[DOT_VB], pih[DOT_VB], pil[DOT_VB];
-  float zh[DOT_VB], zl[DOT_VB], zih[DOT_VB], zil[DOT_VB];
+  const int blk = blockIdx.x, v0 = blockIdx.y * DOT2_VB, r = blockIdx.z;
+  const int nq = min(DOT2_VB, nvec - v0);
+  float ph[DOT2_VB], pl[DOT2_VB], pih[DOT2_VB], pil[DOT2_VB];
+  float zh[DOT2_VB], zl[DOT2_VB], zih[DOT2_VB], zil[DOT2_VB];
 #pragma unroll
-  for (int q = 0; q < DOT_VB; ++q) ph[q] = pl[q] = pih[q] = pil[q] = zh[q] = zl[q] = zih[q] = zil[q] = 0.f;
+  for (int q = 0; q < DOT2_VB; ++q) ph[q] = pl[q] = pih[q] = pil[q] = zh[q] = zl[q] = zih[q] = zil[q] = 0.f;
   if (active[r]) {
     const float4* a = V + (int64_t)v0 * vstride + (int64_t)r * N;
     const float4* pr = p + (int64_t)r * N;
@@ -474,21 +476,21 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots2_ff(const float4* __restri
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < N; i += stride) {
       const float4 yp = pr[i], yz = zr[i];
-      float4 x[DOT_VB];
+      float4 x[DOT2_VB];
 #pragma unroll
-      for (int q = 0; q < DOT_VB; ++q) x[q] = q < nq ? a[(int64_t)q * vstride + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < DOT2_VB; ++q) x[q] = q < nq ? a[(int64_t)q * vstride + i] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < DOT_VB; ++q) {
+      for (int q = 0; q < DOT2_VB; ++q) {
         const float4 cx = ff_conj(x[q]);
         ff_cmac(cx, yp, ph[q], pl[q], pih[q], pil[q]);
         ff_cmac(cx, yz, zh[q], zl[q], zih[q], zil[q]);
       }
     }
   }
-  __shared__ float4 sh[2][RED_THREADS / 32][DOT_VB];
+  __shared__ float4 sh[2][RED_THREADS / 32][DOT2_VB];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < DOT_VB; ++q) {
+  for (int q = 0; q < DOT2_VB; ++q) {
     ff_warp_sum(ph[q], pl[q]);
     ff_warp_sum(pih[q], pil[q]);
     ff_warp_sum(zh[q], zl[q]);
@@ -881,7 +883,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         float4* vn = V + (int64_t)(j + 1) * vstride; // z = A p
         FMPB_TRY((*Aff)(R, vj, vn, st));
         jdone = j + 1;
-        FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb, (j + 2 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
+        FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb, (j + 2 + DOT2_VB - 1) / DOT2_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb, (j + 1) * R, hB, 0));
         FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
