@@ -1,8 +1,9 @@
-"""Burton-Miller collocation BEM for a rigid boundary (Sec. 2.1), constant
-flat-triangle elements, and its multilevel block Toeplitz form for finite
-periodic arrays (Sec. 2.2).  Oracle code: test infrastructure only.
+"""Burton-Miller collocation BEM (Sec. 2.1), constant flat-triangle elements,
+for a rigid boundary or a uniform admittance, and its multilevel block
+Toeplitz form for finite periodic arrays (Sec. 2.2).  Oracle code: test
+infrastructure only.
 
-Equation solved (Eq. (bm) with dp/dn = 0, Eq. (admittance) with beta = 0).
+Equation solved (Eq. (bm) with Eq. (admittance); beta = 0 is the rigid case).
 The paper's normal points out of the fluid (that is the orientation under
 which its CBIE, Eq. (cbie), follows from Green's identity and gives
 c = 1/2 for p = p_inc = 1 at k -> 0).  Meshes here carry normals n_m into the
@@ -13,6 +14,14 @@ reads
     b = -alpha = i/k   (alpha = -i/k, the coupling of Eq. (bm)),
 with G = e^{ikr}/(4 pi r) (Eq. (green3dFull)).  The matrix entry is
 A_ij = 1/2 delta_ij - (D_ij + b H_ij).
+
+Admittance (Eq. (admittance)): dp/dn = i k beta p with the paper's normal n,
+i.e. dp/dn_m = -i k beta p in mesh normals.  The dp/dn terms of Eq. (bm),
+(alpha/2) dp/dn(x) - int [G + alpha dG/dn(x)] dp/dn dA, then add
+    A_ij += (beta/2) delta_ij - i k beta (S_ij + b K_ij),
+    S_ij = int_{E_j} G dA_y,   K_ij = int_{E_j} dG/dn_m(x) dA_y,
+(alpha i k beta / 2 = beta / 2 and alpha dG/dn = b dG/dn_m), the matrix
+H - G Y of Eq. (matrixBEM) with a uniform normalised admittance beta.
 
 Quadrature (the paper names the element type only, Eq. (matrixBEM)); the
 rule below is part of the operator's definition and the GPU library
@@ -28,7 +37,10 @@ generates the same rule from the same description:
       self       j == i (x_i on E_i) : D = 0 (flat panel); H = finite part
                  (1/4pi)[ fp int r^-3 dA  +  int (e^{ikr}(1-ikr) - 1) r^-3 dA ],
                  the first in closed form -sum_edges (t_b/|b-x| - t_a/|a-x|)/h_e,
-                 the second on the three children (x, v_a, v_b) with apex x, q = 8.
+                 the second on the three children (x, v_a, v_b) with apex x, q = 8;
+                 S = (1/4pi)[ int r^-1 dA + int (e^{ikr} - 1) r^-1 dA ], the first in
+                 closed form sum_edges h_e ln((t_b + |b-x|)/(t_a + |a-x|)), the second
+                 on the same three children; K = 0 (flat panel).
 """
 import numpy as np
 
@@ -121,6 +133,19 @@ def kernel_hyp(x, nx, y, ny, k):
     return e * ((1.0 - ikr) * r * r * nn - (3.0 - 3.0 * ikr - (k * r) ** 2) * dnx * dny) / (4 * np.pi * r ** 5)
 
 
+def kernel_slp(x, y, k):
+    """G = e^{ikr} / (4 pi r)."""
+    r = np.linalg.norm(x - y, axis=-1)
+    return np.exp(1j * k * r) / (4 * np.pi * r)
+
+
+def kernel_adlp(x, nx, y, k):
+    """dG/dn_x = e^{ikr}(ikr - 1) ((x-y).n_x) / (4 pi r^3)."""
+    d = x - y
+    r = np.linalg.norm(d, axis=-1)
+    return np.exp(1j * k * r) * (1j * k * r - 1.0) * np.einsum("...i,...i->...", d, nx) / (4 * np.pi * r ** 3)
+
+
 def _sin_minus_xcos(x):
     """sin x - x cos x without cancellation (series below 0.5)."""
     x = np.asarray(x, dtype=np.float64)
@@ -164,6 +189,38 @@ def self_hyp(tri_v, k):
     return (fp + rem) / (4 * np.pi)
 
 
+def inv_r_integral(tri_v, x):
+    """Closed form of int_T 1/|x - y| dA_y for x in the plane of T and inside
+    it: in polar coordinates about x the integral is int R(theta) dtheta, and
+    each edge (foot of the perpendicular at distance h, coordinates t along
+    the edge) gives h ln((t_b + |b - x|) / (t_a + |a - x|))."""
+    total = 0.0
+    for e in range(3):
+        a, b = tri_v[e], tri_v[(e + 1) % 3]
+        eh = (b - a) / np.linalg.norm(b - a)
+        ta, tb = np.dot(a - x, eh), np.dot(b - x, eh)
+        he = np.linalg.norm((a - x) - ta * eh)
+        total += he * np.log((tb + np.linalg.norm(b - x)) / (ta + np.linalg.norm(a - x)))
+    return total
+
+
+def self_slp(tri_v, k):
+    """Integral of G over the flat element tri_v for x at its centroid: the
+    1/r part in closed form (polar coordinates about x: each edge contributes
+    h ln((t_b + |b-x|)/(t_a + |a-x|))), the bounded remainder
+    (e^{ikr} - 1)/r by polar quadrature on the three children (x, a, b)."""
+    x = tri_v.mean(axis=0)
+    closed = inv_r_integral(tri_v, x)
+    rem = 0.0 + 0.0j
+    for e in range(3):
+        a, b = tri_v[e], tri_v[(e + 1) % 3]
+        pts, w = collapsed_rule(x, a, b, Q_SELF)
+        r = np.linalg.norm(pts - x, axis=-1)
+        kr = k * r
+        rem += np.sum(w * (-2.0 * np.sin(0.5 * kr) ** 2 + 1j * np.sin(kr)) / r)   # (e^{ikr} - 1)/r
+    return (closed + rem) / (4 * np.pi)
+
+
 # ----------------------------------------------------- operator entries -----
 
 def classify(x, cen, hmax):
@@ -174,9 +231,9 @@ def classify(x, cen, hmax):
     return cls
 
 
-def pair_integrals(xs, nxs, tri_v, k, cls_code):
-    """D and H integrals for pairs (xs[p], nxs[p]) x element tri_v[p] (all of
-    one class), vectorised over pairs."""
+def pair_integrals(xs, nxs, tri_v, k, cls_code, with_sk=False):
+    """D and H integrals (and S, K when with_sk) for pairs (xs[p], nxs[p]) x
+    element tri_v[p] (all of one class), vectorised over pairs."""
     name = {0: "far", 1: "near", 2: "verynear"}[cls_code]
     pts, w = element_rule(tri_v, name)
     cr = np.cross(tri_v[:, 1] - tri_v[:, 0], tri_v[:, 2] - tri_v[:, 0])
@@ -186,12 +243,17 @@ def pair_integrals(xs, nxs, tri_v, k, cls_code):
     NY = ny[:, None, :]
     D = np.sum(w * kernel_dlp(X, NX, pts, NY, k), axis=1)
     H = np.sum(w * kernel_hyp(X, NX, pts, NY, k), axis=1)
-    return D, H
+    if not with_sk:
+        return D, H
+    S = np.sum(w * kernel_slp(X, pts, k), axis=1)
+    K = np.sum(w * kernel_adlp(X, NX, pts, k), axis=1)
+    return D, H, S, K
 
 
-def dh_block(tgt: CellMesh, src_v, k, self_pairs=None, chunk=200000):
+def dh_block(tgt: CellMesh, src_v, k, self_pairs=None, chunk=200000, with_sk=False):
     """D and H matrices (n_t x n_s) for collocation points of ``tgt`` and source
-    elements with vertex coordinates ``src_v`` (n_s x 3 x 3, already placed).
+    elements with vertex coordinates ``src_v`` (n_s x 3 x 3, already placed),
+    and S, K as well when with_sk.
     ``self_pairs``: boolean n_t x n_s mask of pairs (i, j) with x_i on E_j."""
     nt_, ns = tgt.n, len(src_v)
     cen = src_v.mean(axis=1)
@@ -203,16 +265,25 @@ def dh_block(tgt: CellMesh, src_v, k, self_pairs=None, chunk=200000):
         cls[self_pairs] = 3
     D = np.zeros((nt_, ns), dtype=complex)
     H = np.zeros((nt_, ns), dtype=complex)
+    S = np.zeros((nt_, ns), dtype=complex)
+    K = np.zeros((nt_, ns), dtype=complex)
     for c in (0, 1, 2):
         ii, jj = np.nonzero(cls == c)
         for s in range(0, len(ii), chunk):
             i, j = ii[s:s + chunk], jj[s:s + chunk]
-            d, h = pair_integrals(tgt.centroid[i], tgt.normal[i], src_v[j], k, c)
-            D[i, j] = d
-            H[i, j] = h
+            out = pair_integrals(tgt.centroid[i], tgt.normal[i], src_v[j], k, c, with_sk)
+            D[i, j] = out[0]
+            H[i, j] = out[1]
+            if with_sk:
+                S[i, j] = out[2]
+                K[i, j] = out[3]
     ii, jj = np.nonzero(cls == 3)
     for i, j in zip(ii, jj):
         H[i, j] = self_hyp(src_v[j], k)
+        if with_sk:
+            S[i, j] = self_slp(src_v[j], k)          # K = 0 on the flat panel
+    if with_sk:
+        return D, H, S, K
     return D, H
 
 
@@ -221,17 +292,31 @@ def coupling(k):
     return 1j / k
 
 
-def toeplitz_block(cell: CellMesh, lattice, delta, k):
+def _entries(D, H, S, K, k, beta):
+    """-(D + b H) - i k beta (S + b K) (without the diagonal terms)."""
+    b = coupling(k)
+    T = -(D + b * H)
+    if beta != 0:
+        T = T - 1j * k * beta * (S + b * K)
+    return T
+
+
+def toeplitz_block(cell: CellMesh, lattice, delta, k, beta=0.0):
     """T_delta (Eq. (blockToeplizMatrix), Sec. 2.2): target cell at the origin,
     source cell displaced by -delta . lattice.  Entry (i, j) is the matrix
-    entry of collocation point i against element j."""
+    entry of collocation point i against element j; beta = uniform
+    normalised admittance (0: rigid)."""
     shift = -np.asarray(delta, dtype=np.float64) @ np.asarray(lattice, dtype=np.float64)
     src_v = cell.v + shift[None, None, :]
     selfp = np.eye(cell.n, dtype=bool) if not np.any(delta) else None
-    D, H = dh_block(cell, src_v, k, self_pairs=selfp)
-    T = -(D + coupling(k) * H)
+    if beta == 0:
+        D, H = dh_block(cell, src_v, k, self_pairs=selfp)
+        S = K = None
+    else:
+        D, H, S, K = dh_block(cell, src_v, k, self_pairs=selfp, with_sk=True)
+    T = _entries(D, H, S, K, k, beta)
     if selfp is not None:
-        T += 0.5 * np.eye(cell.n)
+        T += (0.5 + 0.5 * beta) * np.eye(cell.n)
     return T
 
 
@@ -252,14 +337,18 @@ def assemble_full_mesh(verts, tris, lattice, counts):
     return np.concatenate(V), np.concatenate(T)
 
 
-def dense_matrix(verts, tris, lattice, counts, k):
+def dense_matrix(verts, tris, lattice, counts, k, beta=0.0):
     """The conventional dense BM collocation matrix (Eq. (matrixBEM)) of the
     whole array, assembled pair by pair over the full mesh with no use of the
-    periodic structure."""
+    periodic structure; beta = uniform normalised admittance (0: rigid)."""
     V, T = assemble_full_mesh(verts, tris, lattice, counts)
     m = CellMesh(V, T)
-    D, H = dh_block(m, m.v, k, self_pairs=np.eye(m.n, dtype=bool))
-    return 0.5 * np.eye(m.n) - (D + coupling(k) * H)
+    if beta == 0:
+        D, H = dh_block(m, m.v, k, self_pairs=np.eye(m.n, dtype=bool))
+        S = K = None
+    else:
+        D, H, S, K = dh_block(m, m.v, k, self_pairs=np.eye(m.n, dtype=bool), with_sk=True)
+    return (0.5 + 0.5 * beta) * np.eye(m.n) + _entries(D, H, S, K, k, beta)
 
 
 def all_offsets(counts):

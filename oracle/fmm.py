@@ -43,12 +43,20 @@ def far_rule_points(cell: CellMesh):
     return collapsed_rule(v[:, 0], v[:, 1], v[:, 2], Q_FAR)
 
 
-def p2m_table(cell: CellMesh, k: float, nt: int):
-    """V_0 (B x n): moments of each element's unit density (Eq. (p2m))."""
+def p2m_table(cell: CellMesh, k: float, nt: int, beta=0.0):
+    """V_0 (B x n): moments of each element's unit density (Eq. (p2m)).  With
+    a uniform admittance beta the single-layer source term of Eq. (bm),
+    i k beta int G dA, adds i k beta int conj(I_q)(y - y_c) dA (the target
+    side, U_0, is the same operator 1 + b d/dn_x for both layers)."""
     pts, w = far_rule_points(cell)
     g = sp.grad_regular_table(nt, pts, k)               # B x n x 9 x 3
     dIdn = np.einsum("bnqi,ni->bnq", g, cell.normal)    # d I / dn_m
-    return np.sum(np.conj(dIdn) * w[None], axis=2)       # conj(dI/dn) = d conj(I)/dn
+    V = np.sum(np.conj(dIdn) * w[None], axis=2)          # conj(dI/dn) = d conj(I)/dn
+    if beta != 0:
+        n9 = pts.shape[0] * pts.shape[1]
+        I = sp.wave_table(nt, pts.reshape(n9, 3), k, "I").reshape(-1, pts.shape[0], pts.shape[1])
+        V = V + 1j * k * beta * np.sum(np.conj(I) * w[None], axis=2)
+    return V
 
 
 def l2p_table(cell: CellMesh, k: float, nt: int):
@@ -121,7 +129,7 @@ def m2l_block_by_projection(dvec, k: float, nt: int, rho0: float, nq: int = 48):
 
 
 def fmm_matvec_explicit(cell: CellMesh, lattice, counts, k, nt, p, near_blocks=None,
-                        V0=None, U0=None):
+                        V0=None, U0=None, beta=0.0):
     """Explicit, unconvolved FMPBEM product (Eq. (2dPeriodicFMM)):
     y_c = sum_{near c'} S_{c-c'} p_{c'} + U_0 sum_{far c'} K((c-c').a) V_0 p_{c'},
     looping over every cell pair -- no FFT, no circulant embedding."""
@@ -133,7 +141,7 @@ def fmm_matvec_explicit(cell: CellMesh, lattice, counts, k, nt, p, near_blocks=N
     P = p.reshape(R, len(cells), n)
     if near_blocks is None:
         near_blocks = {}
-    V0 = p2m_table(cell, k, nt) if V0 is None else V0
+    V0 = p2m_table(cell, k, nt, beta) if V0 is None else V0
     U0 = l2p_table(cell, k, nt) if U0 is None else U0
     Mom = P @ V0.T                                       # R x Nc x B
     Y = np.zeros((R, len(cells), n), dtype=complex)
@@ -144,7 +152,7 @@ def fmm_matvec_explicit(cell: CellMesh, lattice, counts, k, nt, p, near_blocks=N
             delta = tuple(a - b for a, b in zip(c, cp))
             if max(abs(x) for x in delta) <= 1:
                 if delta not in near_blocks:
-                    near_blocks[delta] = toeplitz_block(cell, L, delta, k)
+                    near_blocks[delta] = toeplitz_block(cell, L, delta, k, beta)
                 Y[:, ci] += P[:, cj] @ near_blocks[delta].T
             else:
                 if delta not in Kcache:
