@@ -394,9 +394,11 @@ def plane_wave_rhs(cell: CellMesh, lattice, counts, k, direction, amp=1.0):
     return np.concatenate(out)
 
 
-def field_points(verts, tris, lattice, counts, k, p, points, direction, amp=1.0):
+def field_points(verts, tris, lattice, counts, k, p, points, direction, amp=1.0, beta=0.0):
     """Total pressure in the fluid (Eq. (cbie) with c = 1):
-    p(x) = p_inc(x) + sum_j D(x, E_j) p_j  (mesh normals)."""
+    p(x) = p_inc(x) + sum_j D(x, E_j) p_j  (mesh normals).  With a uniform
+    admittance the single-layer term -G dp/dn_m of Eq. (cbie), with
+    dp/dn_m = -i k beta p (Eq. (admittance)), adds i k beta S(x, E_j) p_j."""
     V, T = assemble_full_mesh(verts, tris, lattice, counts)
     m = CellMesh(V, T)
     pts = np.asarray(points, dtype=np.float64)
@@ -408,6 +410,11 @@ def field_points(verts, tris, lattice, counts, k, p, points, direction, amp=1.0)
         ii, jj = np.nonzero(cls == c)
         if len(ii) == 0:
             continue
-        d, _ = pair_integrals(pts[ii], dummy_n[ii] + np.array([0, 0, 1.0]), m.v[jj], k, c)
+        nz = dummy_n[ii] + np.array([0, 0, 1.0])
+        if beta == 0:
+            d, _ = pair_integrals(pts[ii], nz, m.v[jj], k, c)
+        else:
+            d, _, sl, _ = pair_integrals(pts[ii], nz, m.v[jj], k, c, with_sk=True)
+            d = d + 1j * k * beta * sl
         np.add.at(out, ii, d * p[jj])
     return out

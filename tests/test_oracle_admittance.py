@@ -118,3 +118,39 @@ def test_fmm_with_admittance_converges_to_exact_blocks():
     errs = [np.linalg.norm(fmm.fmm_matvec_explicit(cell, lat, counts, k, nt, x, beta=beta) - exact)
             / np.linalg.norm(exact) for nt in (2, 4, 8)]
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6, errs
+
+
+def _impedance_sphere_total(k, a, beta, pts, nmax=40):
+    """Total pressure outside the sphere: sum_n (2n+1) i^n [j_n(kr) + A_n h_n(kr)] P_n(cos theta),
+    A_n = -(j_n'(ka) + i beta j_n(ka)) / (h_n'(ka) + i beta h_n(ka)) from dp/dr = -i k beta p at r = a."""
+    from oracle.special import sph_jn, sph_jn_deriv
+    r = np.linalg.norm(pts, axis=1)
+    ct = pts[:, 0] / r
+    ka = k * a
+    out = np.zeros(len(pts), dtype=complex)
+    for n in range(nmax):
+        An = -(sph_jn_deriv(n, ka) + 1j * beta * sph_jn(n, ka)) / (sph_hn_deriv(n, ka) + 1j * beta * sph_hn(n, ka))
+        out += (2 * n + 1) * 1j ** n * (sph_jn(n, k * r) + An * sph_hn(n, k * r)) * eval_legendre(n, ct)
+    return out
+
+
+@pytest.mark.parametrize("k,beta", [(3.0, 0.6 + 0.4j), (6.0, 1.0)])
+def test_impedance_sphere_field_points_against_analytic_series(k, beta):
+    # the exterior field of the collocation solution: the single layer that
+    # the admittance adds (i k beta S p) is needed to reach the series
+    v, t = icosphere(3, 0.2)
+    cell = bem.CellMesh(v, t)
+    A = bem.toeplitz_block(cell, np.eye(3), (0, 0, 0), k, beta)
+    b = bem.plane_wave_rhs(cell, np.eye(3), (1, 1, 1), k, [1.0, 0.0, 0.0])
+    p = np.linalg.solve(A, b)
+    rng = np.random.default_rng(9)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    pts = np.vstack([0.3 * dirs, 0.6 * dirs])
+    ref = _impedance_sphere_total(k, 0.2, beta, pts)
+    got = bem.field_points(v, t, np.eye(3), (1, 1, 1), k, p, pts, [1.0, 0.0, 0.0], beta=beta)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 0.01, err
+    # dropping the admittance single layer misses the series by far more
+    no_s = bem.field_points(v, t, np.eye(3), (1, 1, 1), k, p, pts, [1.0, 0.0, 0.0])
+    assert np.linalg.norm(no_s - ref) / np.linalg.norm(ref) > 5 * err
