@@ -267,6 +267,7 @@ def run_ours(args):
     fmm = fmm_section(gb, torch, stream) if sections else None
     serving = serving_section(gb) if sections else None
     batching = batching_section(gb, torch, stream) if sections else None
+    admittance = admittance_section(gb, torch, stream, w, v, t) if sections else None
     mixed = (mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
              if not args.only_headline else None)
 
@@ -289,6 +290,7 @@ def run_ours(args):
         "mixed": mixed,
         "serving": serving,
         "batching": batching,
+        "admittance": admittance,
     }
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, v, t, iters)
@@ -558,6 +560,56 @@ def fmm_section(gb, torch, stream):
            "operator_bytes": op.info["bytes_device"]}
     out["precision"] = precision_section(gb, torch, stream, w, v, t, k, op, x, y, p, solve_ms, build_ms)
     op.close()
+    return out
+
+
+def admittance_section(gb, torch, stream, w, v, t, beta=0.4 + 0.2j, freq_index=3):
+    """The headline sonic crystal with an absorbing surface of uniform
+    normalised admittance beta (Eq. (admittance)) against the rigid one at the
+    same frequency: operator build (the quadrature kernels now also integrate
+    G and dG/dn_x), the product, and a plane-wave solve to 1e-8."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    k = w.wavenumbers[freq_index]
+    out = {"workload": f"{WORKLOAD} at k = {k:.4f}, beta = {beta}", "beta": [beta.real, beta.imag]}
+    x = torch.as_tensor(random_complex_vectors(w.rhs_seed, 1, len(t) * int(np.prod(w.counts))), device="cuda")
+    pts = quadrature_points(w, v, t)
+    for name, b in (("rigid", 0.0), ("admittance", beta)):
+        torch.cuda.synchronize()
+        gb.profile_reset()
+        gb.profile_enable(True)
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        op = gb.Operator(v, t, w.counts, w.lattice, k, beta=b)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        gb.profile_enable(False)
+        build_ms = b0.elapsed_time(b1)
+        bprof = gb.profile_summary()
+        y = op.matvec(x)
+        torch.cuda.synchronize()
+        m0, m1 = ev(), ev()
+        m0.record(stream)
+        for _ in range(10):
+            op.matvec(x, out=y)
+        m1.record(stream)
+        rhs = op.rhs_plane_wave(w.directions)
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        p, info = op.solve(rhs, tol=TOL, restart=RESTART, maxit=MAXIT, raise_on_noconv=False)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        quad = "build_blocks_adm" if b else "build_blocks"
+        qms = bprof.get(quad, (1, float("nan")))[1]
+        out[name] = {"build_ms": build_ms, "build_kernels_ms": {k_: v_[1] for k_, v_ in bprof.items()},
+                     "quadrature_points_per_s": pts / (qms / 1e3),
+                     "matvec_ms": m0.elapsed_time(m1) / 10, "solve_ms": s0.elapsed_time(s1),
+                     "iters": info[0]["iters"], "relres_true": info[0]["relres_true"],
+                     "converged": info[0]["converged"],
+                     "solves_per_s_incl_build": 1e3 / (build_ms + s0.elapsed_time(s1))}
+        op.close()
+    r, a = out["rigid"], out["admittance"]
+    out["quadrature_kernel_time_ratio"] = (a["build_kernels_ms"].get("build_blocks_adm", float("nan"))
+                                           / r["build_kernels_ms"].get("build_blocks", float("nan")))
     return out
 
 

@@ -105,6 +105,15 @@ typedef struct {
                       0 = default 8 */
   int precision;   /* fmpb_precision: FMPB_FP64 (default), FMPB_FP32, FMPB_BF16
                       (FMM form only) or FMPB_MIXED */
+  /* Uniform normalised surface admittance beta = beta_re + i beta_im
+   * (Eq. (admittance): dp/dn = i k beta p with n out of the fluid, i.e.
+   * dp/dn_m = -i k beta p with the mesh normal); 0 + 0i (the value of a
+   * zero-initialised struct) is the rigid surface.  The matrix gains
+   * (beta/2) delta_ij - i k beta (S_ij + (i/k) K_ij) with S = int G and
+   * K = int dG/dn_x (Eq. (bm), Eq. (matrixBEM)); the FMM form adds
+   * i k beta int conj(I) dA to the P2M table. */
+  double beta_re;
+  double beta_im;
 } fmpb_operator_opts;
 
 typedef struct {
@@ -120,6 +129,8 @@ typedef struct {
   int32_t n_near;        /* near offsets stored (3^dim) in the FMM form, else 0 */
   size_t bytes_device;   /* device memory held by the operator (tables only) */
   int32_t precision;     /* fmpb_precision of the stored spectrum(s) */
+  double beta_re;        /* surface admittance the operator was built with */
+  double beta_im;
 } fmpb_operator_info;
 
 /*
@@ -219,7 +230,8 @@ fmpb_status fmpb_operator_check(const fmpb_operator *op, void *stream);
 /*
  * Total pressure at field points in the fluid (Eq. (cbie) with c(x) = 1):
  * p(x) = p_inc(x) + sum_j int_{E_j} dG/dn_y(x, y) dA_y p_j over every
- * element of every cell (direct sum).
+ * element of every cell (direct sum); an operator built with an admittance
+ * beta adds i k beta int_{E_j} G(x, y) dA_y p_j (dp/dn_m = -i k beta p).
  *   p     device, R x N surface pressure.   dirs, amps as in fmpb_rhs_plane_wave.
  *   pts   device, npts x 3 points (must not lie on an element).
  *   out   device, R x npts.
@@ -244,6 +256,18 @@ fmpb_status fmpb_field(const fmpb_operator *op, int R, const fmpb_c64 *p, const 
 fmpb_status fmpb_build_blocks(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
                               const fmpb_lattice *lattice, double k, int n_off,
                               const int32_t *offsets, fmpb_c64 *out, void *stream);
+/*
+ * The same blocks for a surface of uniform normalised admittance beta
+ * (Eq. (admittance) in Eq. (bm)); fmpb_build_blocks is beta = 0:
+ *   T_delta[i][j] += [delta = 0, i = j] beta/2 - i k beta int_{E_j} (G + (i/k) dG/dn_x).
+ * The self term's int G is the closed form of int 1/r plus the polar rule on
+ * (e^{ikr} - 1)/r; its int dG/dn_x vanishes on the flat element.
+ * Errors: as fmpb_build_blocks, and EINVAL for a non-finite beta.
+ */
+fmpb_status fmpb_build_blocks_admittance(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                                         const fmpb_lattice *lattice, double k, double beta_re,
+                                         double beta_im, int n_off, const int32_t *offsets,
+                                         fmpb_c64 *out, void *stream);
 
 /*
  * P2M table V_0 (B x n, Eq. (p2m)) and L2P table U_0 (n x B, Eq. (l2p) and
@@ -253,6 +277,13 @@ fmpb_status fmpb_build_blocks(const double *verts, int64_t nv, const int32_t *tr
 fmpb_status fmpb_multipole_tables(const double *verts, int64_t nv, const int32_t *tris,
                                   int64_t ntri, double k, int n_t, fmpb_c64 *V0, fmpb_c64 *U0,
                                   void *stream);
+/* The same tables for a surface of uniform normalised admittance beta:
+ * V_0[q][j] += i k beta int_{E_j} conj(I_q) dA (the single layer that the
+ * admittance adds to Eq. (p2m)); U_0 is unchanged.  beta = 0 is
+ * fmpb_multipole_tables. */
+fmpb_status fmpb_multipole_tables_admittance(const double *verts, int64_t nv, const int32_t *tris,
+                                             int64_t ntri, double k, double beta_re, double beta_im,
+                                             int n_t, fmpb_c64 *V0, fmpb_c64 *U0, void *stream);
 
 /*
  * M2L blocks K(d) (B x B each, Eqs. (m2l), (wigner)) for n_d translation

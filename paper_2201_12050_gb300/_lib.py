@@ -30,14 +30,16 @@ class Lattice(ctypes.Structure):
 
 
 class OperatorOpts(ctypes.Structure):
-    _fields_ = [("form", ctypes.c_int), ("n_t", ctypes.c_int), ("precision", ctypes.c_int)]
+    _fields_ = [("form", ctypes.c_int), ("n_t", ctypes.c_int), ("precision", ctypes.c_int),
+                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double)]
 
 
 class OperatorInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("N", ctypes.c_int64), ("dim", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("n_t", ctypes.c_int32), ("B", ctypes.c_int64),
                 ("P", ctypes.c_int32 * 3), ("F", ctypes.c_int64), ("n_near", ctypes.c_int32),
-                ("bytes_device", ctypes.c_size_t), ("precision", ctypes.c_int32)]
+                ("bytes_device", ctypes.c_size_t), ("precision", ctypes.c_int32),
+                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -96,6 +98,8 @@ SIGNATURES = {
     "fmpb_field": (INT, [P, INT, P, P, P, I64, P, P, P]),
     "fmpb_build_blocks": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, INT, P, P, P]),
     "fmpb_multipole_tables": (INT, [P, I64, P, I64, D, INT, P, P, P]),
+    "fmpb_build_blocks_admittance": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
+    "fmpb_multipole_tables_admittance": (INT, [P, I64, P, I64, D, D, D, INT, P, P, P]),
     "fmpb_m2l_blocks": (INT, [D, INT, INT, P, P, P]),
     "fmpb_offset_gemm_bf16": (INT, [P, INT, P, I64, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_shape": (INT, [P, P, P]),

@@ -54,14 +54,16 @@ def _cvec(x, N, name):
 
 
 class Operator:
-    """fmpb_operator: the tables of one (unit-cell mesh, lattice, k)."""
+    """fmpb_operator: the tables of one (unit-cell mesh, lattice, k); beta is
+    the surface's uniform normalised admittance (0: rigid)."""
 
-    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64):
+    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64, beta=0.0):
         self._lib = lib()
         v = _host(verts, np.float64)
         t = _host(tris, np.int32)
         self._lat = _lattice(counts, vectors)
-        opts = OperatorOpts(int(form), int(n_t), int(precision))
+        beta = complex(beta)
+        opts = OperatorOpts(int(form), int(n_t), int(precision), beta.real, beta.imag)
         h = ctypes.c_void_p()
         check(self._lib.fmpb_operator_create(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(self._lat),
                                              float(k), ctypes.byref(opts), _stream(), ctypes.byref(h)))
@@ -147,6 +149,32 @@ def build_blocks(verts, tris, counts, vectors, k, offsets):
     check(lib().fmpb_build_blocks(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k), len(off), _ptr(off),
                                   _ptr(out), _stream()))
     return out
+
+
+def build_blocks_admittance(verts, tris, counts, vectors, k, beta, offsets):
+    """fmpb_build_blocks_admittance: T_delta of a surface of admittance beta."""
+    v = _host(verts, np.float64)
+    t = _host(tris, np.int32)
+    off = _host(offsets, np.int32).reshape(-1, 3)
+    lat = _lattice(counts, vectors)
+    beta = complex(beta)
+    out = torch.empty((len(off), len(t), len(t)), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_build_blocks_admittance(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k),
+                                             beta.real, beta.imag, len(off), _ptr(off), _ptr(out), _stream()))
+    return out
+
+
+def multipole_tables_admittance(verts, tris, k, beta, n_t):
+    """fmpb_multipole_tables_admittance: (V_0, U_0) of a surface of admittance beta."""
+    v = _host(verts, np.float64)
+    t = _host(tris, np.int32)
+    B = (n_t + 1) ** 2
+    beta = complex(beta)
+    V0 = torch.empty((B, len(t)), dtype=torch.complex128, device="cuda")
+    U0 = torch.empty((len(t), B), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_multipole_tables_admittance(_ptr(v), len(v), _ptr(t), len(t), float(k), beta.real, beta.imag,
+                                                 int(n_t), _ptr(V0), _ptr(U0), _stream()))
+    return V0, U0
 
 
 def multipole_tables(verts, tris, k, n_t):

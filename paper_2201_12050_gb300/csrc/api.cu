@@ -168,6 +168,7 @@ struct fmpb_operator {
   CellGrid grid;
   CircShape shape;
   double k = 0.0;
+  cd beta = {0.0, 0.0};     // uniform normalised admittance (0: rigid)
   int form = FMPB_FORM_PBEM;
   int nt = 0;
   int64_t B = 0;
@@ -326,6 +327,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
             "operator_create: precision must be FMPB_FP64, FMPB_FP32, FMPB_BF16 or FMPB_MIXED");
   const int nt = o.n_t > 0 ? o.n_t : 8;
   CHECK_ARG(nt >= 1 && nt <= MAX_NT, "operator_create: n_t must be 1..%d", MAX_NT);
+  CHECK_ARG(std::isfinite(o.beta_re) && std::isfinite(o.beta_im), "operator_create: admittance must be finite");
+  const cd beta = mkc(o.beta_re, o.beta_im);
   cudaStream_t st = (cudaStream_t)stream;
   fmpb_operator* op = new (std::nothrow) fmpb_operator();
   if (!op) {
@@ -338,6 +341,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   };
   cudaGetDevice(&op->device);
   op->k = k;
+  op->beta = beta;
   fmpb_status s = make_grid(lattice, op->grid);
   if (s != FMPB_OK) return fail(s);
   s = upload_mesh(verts, nv, tris, ntri, op->mesh, st);
@@ -365,7 +369,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     const int n_off = (int)(all_off.size() / 3);
     std::vector<int64_t> dest(n_off);
     for (int i = 0; i < n_off; ++i) dest[i] = offset_slot(sh, all_off[3 * i], all_off[3 * i + 1], all_off[3 * i + 2]);
-    s = build_blocks(op->mesh, op->grid, k, n_off, all_off.data(), dest.data(), op->spec, st);
+    s = build_blocks(op->mesh, op->grid, k, beta, n_off, all_off.data(), dest.data(), op->spec, st);
     if (s != FMPB_OK) return fail(s);
     s = grid_fft_inplace(sh, (int64_t)n * n, op->spec, st);   // leaves float-float pairs
     if (s != FMPB_OK) return fail(s);
@@ -386,8 +390,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
       return fail(cuda_status(cudaGetLastError(), "operator_create copies"));
     std::vector<int64_t> dnear(op->n_near);
     for (int i = 0; i < op->n_near; ++i) dnear[i] = i;
-    s = build_blocks(op->mesh, op->grid, k, op->n_near, near_off.data(), dnear.data(), op->S, st);
-    if (s == FMPB_OK) s = multipole_tables(op->mesh, k, nt, op->V0, op->U0, st);
+    s = build_blocks(op->mesh, op->grid, k, beta, op->n_near, near_off.data(), dnear.data(), op->S, st);
+    if (s == FMPB_OK) s = multipole_tables(op->mesh, k, beta, nt, op->V0, op->U0, st);
     // the products read the near blocks and the P2M/L2P tables as float-float
     // pairs, or as complex FP32 for FP32 operators (8 bytes per entry)
     if (o.precision == FMPB_BF16 || o.precision == FMPB_MIXED) {
@@ -490,6 +494,8 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->n_near = op->n_near;
   info->bytes_device = op->bytes;
   info->precision = op->precision;
+  info->beta_re = op->beta.x;
+  info->beta_im = op->beta.y;
   return FMPB_OK;
 }
 
@@ -553,15 +559,22 @@ fmpb_status fmpb_field(const fmpb_operator* op, int R, const fmpb_c64* p, const 
                        int64_t npts, const double* pts, fmpb_c64* out, void* stream) {
   CHECK_ARG(op && p && dirs && pts && out, "field: NULL argument");
   CHECK_ARG(R >= 1 && R <= 65535 && npts >= 1, "field: R or npts out of range");
-  return field_points(op->mesh, op->grid, op->k, R, (const cd*)p, dirs, amps, npts, pts, (cd*)out,
+  return field_points(op->mesh, op->grid, op->k, op->beta, R, (const cd*)p, dirs, amps, npts, pts, (cd*)out,
                       (cudaStream_t)stream);
 }
 
 fmpb_status fmpb_build_blocks(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
                               const fmpb_lattice* lattice, double k, int n_off, const int32_t* offsets, fmpb_c64* out,
                               void* stream) {
+  return fmpb_build_blocks_admittance(verts, nv, tris, ntri, lattice, k, 0.0, 0.0, n_off, offsets, out, stream);
+}
+
+fmpb_status fmpb_build_blocks_admittance(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                         const fmpb_lattice* lattice, double k, double beta_re, double beta_im,
+                                         int n_off, const int32_t* offsets, fmpb_c64* out, void* stream) {
   CHECK_ARG(offsets && out && n_off >= 1, "build_blocks: bad offsets or output");
   CHECK_ARG(k > 0.0 && std::isfinite(k), "build_blocks: wavenumber must be positive");
+  CHECK_ARG(std::isfinite(beta_re) && std::isfinite(beta_im), "build_blocks: admittance must be finite");
   CellGrid g;
   FMPB_TRY(make_grid(lattice, g));
   DeviceMesh m;
@@ -569,19 +582,26 @@ fmpb_status fmpb_build_blocks(const double* verts, int64_t nv, const int32_t* tr
   FMPB_TRY(upload_mesh(verts, nv, tris, ntri, m, st));
   std::vector<int64_t> dest(n_off);
   for (int i = 0; i < n_off; ++i) dest[i] = i;
-  fmpb_status s = build_blocks(m, g, k, n_off, offsets, dest.data(), (cd*)out, st);
+  fmpb_status s = build_blocks(m, g, k, mkc(beta_re, beta_im), n_off, offsets, dest.data(), (cd*)out, st);
   free_mesh(m);
   return s;
 }
 
 fmpb_status fmpb_multipole_tables(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, double k,
                                   int n_t, fmpb_c64* V0, fmpb_c64* U0, void* stream) {
+  return fmpb_multipole_tables_admittance(verts, nv, tris, ntri, k, 0.0, 0.0, n_t, V0, U0, stream);
+}
+
+fmpb_status fmpb_multipole_tables_admittance(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                             double k, double beta_re, double beta_im, int n_t, fmpb_c64* V0,
+                                             fmpb_c64* U0, void* stream) {
   CHECK_ARG(k > 0.0 && std::isfinite(k), "multipole_tables: wavenumber must be positive");
+  CHECK_ARG(std::isfinite(beta_re) && std::isfinite(beta_im), "multipole_tables: admittance must be finite");
   CHECK_ARG(n_t >= 1 && n_t <= MAX_NT, "multipole_tables: n_t must be 1..%d", MAX_NT);
   DeviceMesh m;
   cudaStream_t st = (cudaStream_t)stream;
   FMPB_TRY(upload_mesh(verts, nv, tris, ntri, m, st));
-  fmpb_status s = multipole_tables(m, k, n_t, (cd*)V0, (cd*)U0, st);
+  fmpb_status s = multipole_tables(m, k, mkc(beta_re, beta_im), n_t, (cd*)V0, (cd*)U0, st);
   if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "multipole_tables");
   free_mesh(m);
   return s;

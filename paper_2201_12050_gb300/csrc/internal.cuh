@@ -71,11 +71,12 @@ fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, in
                         cudaStream_t st);
 void free_mesh(DeviceMesh& m);
 // Builds n_off collocation blocks; block o is written at out + dest[o] * n * n.
-fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n_off, const int32_t* offsets,
-                         const int64_t* dest_host, cd* out, cudaStream_t st);
+// beta: uniform normalised admittance of the surface (0: rigid).
+fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                         const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);
 fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int R, const double* dirs_host,
                            const fmpb_c64* amps_host, cd* b, cudaStream_t st);
-fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R, const cd* surf,
+fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
                          const double* dirs_host, const fmpb_c64* amps_host, int64_t npts, const double* pts,
                          cd* out, cudaStream_t st);
 

@@ -305,7 +305,7 @@ __device__ void wave_eval(int nt, const WaveSetup& w, int q, const double nrm[3]
 // ---------------------------------------------------------------- tables --
 // V_0[q][j]: far rule (collapsed Gauss-Legendre 3x3, apex v0) on element j.
 // One CTA per element, one thread per coefficient.
-__global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k, QuadRules qr,
+__global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k, cd beta, QuadRules qr,
                             cd* __restrict__ V0) {
   __shared__ WaveSetup ws;
   const int j = blockIdx.x;
@@ -313,6 +313,7 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
   const int B = (nt + 1) * (nt + 1);
   const int q = threadIdx.x;
   cd acc = mkc(0.0, 0.0);
+  const cd ikb = mkc(-k * beta.y, k * beta.x);   // i k beta
   const double two_area = 2.0 * E.area;
   for (int a = 0; a < Q_FAR; ++a) {
     const double s = qr.t3[a];
@@ -326,10 +327,12 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
       }
       __syncthreads();
       if (q < B) {
-        cd dI;
-        wave_eval(nt, ws, q, E.nrm, k, nullptr, &dI);
+        cd I, dI;
+        wave_eval(nt, ws, q, E.nrm, k, &I, &dI);
         const double w = two_area * s * qr.w3[a] * qr.w3[b];
-        acc = cadd(acc, cmulr(cconj(dI), w));
+        // conj(dI/dn) (double layer) + i k beta conj(I) (admittance single layer)
+        const cd src = cadd(cconj(dI), cmul(ikb, cconj(I)));
+        acc = cadd(acc, cmulr(src, w));
       }
     }
   }
@@ -507,14 +510,14 @@ __global__ void k_l2p_apply_f32(const float2* __restrict__ U0, int n, int B, con
 }
 
 // ------------------------------------------------------------- host side --
-fmpb_status multipole_tables(const DeviceMesh& m, double k, int nt, cd* V0, cd* U0, cudaStream_t st) {
+fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd* V0, cd* U0, cudaStream_t st) {
   if (nt < 1 || nt > MAX_NT) {
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
-  if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, m.qr, V0));
+  if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, V0));
   if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, U0));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;

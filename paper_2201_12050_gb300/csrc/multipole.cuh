@@ -15,7 +15,8 @@ __host__ __device__ __forceinline__ void q_to_nm(int q, int& n, int& m) {
   m = q - n * (n + 1);
 }
 
-fmpb_status multipole_tables(const DeviceMesh& m, double k, int nt, cd* V0, cd* U0, cudaStream_t st);
+// beta: uniform normalised admittance (adds i k beta int conj(I) dA to V0).
+fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd* V0, cd* U0, cudaStream_t st);
 // K(d_o) for n_d translations; block o written at out + dest[o] B B (dest < 0 skipped).
 fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, const int64_t* dest_host, cd* out,
                        cudaStream_t st);

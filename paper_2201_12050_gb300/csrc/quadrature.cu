@@ -102,9 +102,12 @@ __global__ void k_gauss_legendre(QuadRules* qr) {
 }
 
 // ------------------------------------------------------------- kernels ----
-// Accumulates w*dG/dn_y into D and w*d2G/dn_x dn_y into H at one point.
-__device__ __forceinline__ void kernel_point(const double x[3], const double nx[3], const double y[3],
-                                             const double ny[3], double w, double k, cd& D, cd& H) {
+// Accumulates w*dG/dn_y into D and w*d2G/dn_x dn_y into H at one point, and
+// with SK also w*G into S and w*dG/dn_x into K (admittance boundaries).
+template <bool SK>
+__device__ __forceinline__ void kernel_point4(const double x[3], const double nx[3], const double y[3],
+                                              const double ny[3], double w, double k, cd& D, cd& H, cd& S,
+                                              cd& K) {
   const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
   const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
   const double r = sqrt(r2);
@@ -129,13 +132,27 @@ __device__ __forceinline__ void kernel_point(const double x[3], const double nx[
   const double g2 = w * dnx * dny * ir3 * ir * ir * inv4pi;
   H.x += a_re * g1 - b_re * g2;
   H.y += a_im * g1 - b_im * g2;
+  if (SK) {
+    // G = e^{ikr} / (4 pi r),  dG/dn_x = -e^{ikr}(1 - ikr) ((x-y).n_x) / (4 pi r^3)
+    const double gs = w * ir * inv4pi;
+    S.x = fma(c, gs, S.x);
+    S.y = fma(s, gs, S.y);
+    const double gk = -w * dnx * ir3 * inv4pi;
+    K.x = fma(a_re, gk, K.x);
+    K.y = fma(a_im, gk, K.y);
+  }
+}
+__device__ __forceinline__ void kernel_point(const double x[3], const double nx[3], const double y[3],
+                                             const double ny[3], double w, double k, cd& D, cd& H) {
+  cd S, K;
+  kernel_point4<false>(x, nx, y, ny, w, k, D, H, S, K);
 }
 
-template <int Q>
+template <int Q, bool SK>
 __device__ __forceinline__ void integrate_collapsed(const double a[3], const double b[3], const double cc[3],
                                                     double two_area, const double* t, const double* w,
                                                     const double x[3], const double nx[3], const double ny[3],
-                                                    double k, cd& D, cd& H) {
+                                                    double k, cd& D, cd& H, cd& S, cd& K) {
   double ba[3], cb[3];
   for (int d = 0; d < 3; ++d) {
     ba[d] = b[d] - a[d];
@@ -149,7 +166,7 @@ __device__ __forceinline__ void integrate_collapsed(const double a[3], const dou
     for (int j = 0; j < Q; ++j) {
       double y[3];
       for (int d = 0; d < 3; ++d) y[d] = a[d] + s * (ba[d] + t[j] * cb[d]);
-      kernel_point(x, nx, y, ny, ws * w[j], k, D, H);
+      kernel_point4<SK>(x, nx, y, ny, ws * w[j], k, D, H, S, K);
     }
   }
 }
@@ -158,8 +175,9 @@ __device__ __forceinline__ void integrate_collapsed(const double a[3], const dou
 // out of line with rolled loops: the quadrature kernel's code must stay small
 // enough for the instruction cache, and these classes are a few per cent of
 // the points.
-__device__ __noinline__ void element_dh(const Elem& E, const double shift[3], const double x[3], const double nx[3],
-                           double k, const QuadRules& qr, cd& D, cd& H) {
+template <bool SK>
+__device__ void element_dh_t(const Elem& E, const double shift[3], const double x[3], const double nx[3],
+                             double k, const QuadRules& qr, cd& D, cd& H, cd& S, cd& K) {
   double v[3][3];
   for (int a = 0; a < 3; ++a)
     for (int d = 0; d < 3; ++d) v[a][d] = E.v[a][d] + shift[d];
@@ -169,10 +187,12 @@ __device__ __noinline__ void element_dh(const Elem& E, const double shift[3], co
   const double two_area = 2.0 * E.area;
   D = mkc(0.0, 0.0);
   H = mkc(0.0, 0.0);
+  S = mkc(0.0, 0.0);
+  K = mkc(0.0, 0.0);
   if (dist >= FAR_RATIO * E.hmax) {
-    integrate_collapsed<Q_FAR>(v[0], v[1], v[2], two_area, qr.t3, qr.w3, x, nx, E.nrm, k, D, H);
+    integrate_collapsed<Q_FAR, SK>(v[0], v[1], v[2], two_area, qr.t3, qr.w3, x, nx, E.nrm, k, D, H, S, K);
   } else if (dist >= NEAR_RATIO * E.hmax) {
-    integrate_collapsed<Q_NEAR>(v[0], v[1], v[2], two_area, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+    integrate_collapsed<Q_NEAR, SK>(v[0], v[1], v[2], two_area, qr.t8, qr.w8, x, nx, E.nrm, k, D, H, S, K);
   } else {
     double m01[3], m12[3], m20[3];
     for (int d = 0; d < 3; ++d) {
@@ -181,11 +201,21 @@ __device__ __noinline__ void element_dh(const Elem& E, const double shift[3], co
       m20[d] = 0.5 * (v[2][d] + v[0][d]);
     }
     const double ta = 0.25 * two_area;
-    integrate_collapsed<Q_NEAR>(v[0], m01, m20, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
-    integrate_collapsed<Q_NEAR>(m01, v[1], m12, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
-    integrate_collapsed<Q_NEAR>(m20, m12, v[2], ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
-    integrate_collapsed<Q_NEAR>(m01, m12, m20, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H);
+    integrate_collapsed<Q_NEAR, SK>(v[0], m01, m20, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H, S, K);
+    integrate_collapsed<Q_NEAR, SK>(m01, v[1], m12, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H, S, K);
+    integrate_collapsed<Q_NEAR, SK>(m20, m12, v[2], ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H, S, K);
+    integrate_collapsed<Q_NEAR, SK>(m01, m12, m20, ta, qr.t8, qr.w8, x, nx, E.nrm, k, D, H, S, K);
   }
+}
+__device__ __noinline__ void element_dh(const Elem& E, const double shift[3], const double x[3], const double nx[3],
+                                        double k, const QuadRules& qr, cd& D, cd& H) {
+  cd S, K;
+  element_dh_t<false>(E, shift, x, nx, k, qr, D, H, S, K);
+}
+__device__ __noinline__ void element_dhsk(const Elem& E, const double shift[3], const double x[3],
+                                          const double nx[3], double k, const QuadRules& qr, cd& D, cd& H, cd& S,
+                                          cd& K) {
+  element_dh_t<true>(E, shift, x, nx, k, qr, D, H, S, K);
 }
 
 // ------------------------------------------------- float-float far rule --
@@ -267,11 +297,13 @@ __device__ __forceinline__ ffc expi_ff(ff psi, int m, const FfConst& C) {
 constexpr double TWO_PI_HI = 6.283185307179586;
 constexpr double TWO_PI_LO = 2.4492935982947064e-16;
 
-// D, H of a far element.  ef = x - (c + shift) in float-float (formed on the
-// FP32 pipe from float-float centroids and shift; about 1e-13 relative to
-// |e| >= 4 h), dist = |e| in FP64 for the reference phase.
+// D, H (and with SK also S, K) of a far element.  ef = x - (c + shift) in
+// float-float (formed on the FP32 pipe from float-float centroids and shift;
+// about 1e-13 relative to |e| >= 4 h), dist = |e| in FP64 for the reference
+// phase.
+template <bool SK>
 __device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff nxf[3], double k, ff kf,
-                          const FfConst& C, cd& D, cd& H) {
+                          const FfConst& C, cd& D, cd& H, cd& S, cd& K) {
   const ff rho2 = ff_dot3(ef, ef);
   const ff rho = ff_sqrt(rho2);
   const ff dny = ff_dot3(ef, F.ny);           // (x - y).n_y is constant on the flat element
@@ -289,6 +321,7 @@ __device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff
   const float kh = (float)k * F.hmax;
   while (kh > 0.75f * (float)(1 << m) && m < 12) ++m;
   ff Dre = ff_make(0.f), Dim = ff_make(0.f), Hre = ff_make(0.f), Him = ff_make(0.f);
+  ff Sre = ff_make(0.f), Sim = ff_make(0.f), Kre = ff_make(0.f), Kim = ff_make(0.f);
 #pragma unroll 1
   for (int b = 0; b < Q_FAR; ++b) {
     ff qb[3];
@@ -327,16 +360,30 @@ __device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff
       Dim = ff_add(Dim, ff_mul(aim, f));
       Hre = ff_add(Hre, ff_sub(ff_mul(are, g1), ff_mul(bre, g2)));
       Him = ff_add(Him, ff_sub(ff_mul(aim, g1), ff_mul(bim, g2)));
+      if (SK) {
+        // G = e^{ikr}/(4 pi r),  dG/dn_x = -a ((x-y).n_x)/(4 pi r^3)
+        const ff gs = ff_mul(ff_mul(wgt, ir), C.inv4pi);
+        Sre = ff_add(Sre, ff_mul(E.re, gs));
+        Sim = ff_add(Sim, ff_mul(E.im, gs));
+        const ff gk = ff_mul(ff_mul(wir3, dnx), C.inv4pi);
+        Kre = ff_sub(Kre, ff_mul(are, gk));
+        Kim = ff_sub(Kim, ff_mul(aim, gk));
+      }
     }
   }
   D = mkc(ff_to_d(Dre), ff_to_d(Dim));
   H = mkc(ff_to_d(Hre), ff_to_d(Him));
+  if (SK) {
+    S = mkc(ff_to_d(Sre), ff_to_d(Sim));
+    K = mkc(ff_to_d(Kre), ff_to_d(Kim));
+  }
 }
 
-// D, H by class: the far class through far_dh_ff, the near classes in FP64.
+// D, H (S, K) by class: the far class through far_dh_ff, the near classes in FP64.
+template <bool SK>
 __device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double shift[3], const ff shf[3],
                                  const double x[3], const ff xf[3], const double nx[3], const ff nxf[3], double k,
-                                 ff kf, const QuadRules& qr, const FfConst& C, cd& D, cd& H) {
+                                 ff kf, const QuadRules& qr, const FfConst& C, cd& D, cd& H, cd& S, cd& K) {
   double dc[3];
   for (int d = 0; d < 3; ++d) dc[d] = x[d] - (E.c[d] + shift[d]);
   const double r2 = dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2];
@@ -344,15 +391,26 @@ __device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double sh
   if (dist >= FAR_RATIO * E.hmax) {
     const ff ef[3] = {ff_sub(ff_sub(xf[0], F.c[0]), shf[0]), ff_sub(ff_sub(xf[1], F.c[1]), shf[1]),
                       ff_sub(ff_sub(xf[2], F.c[2]), shf[2])};
-    far_dh_ff(F, ef, dist, nxf, k, kf, C, D, H);
+    far_dh_ff<SK>(F, ef, dist, nxf, k, kf, C, D, H, S, K);
     return;
   }
-  element_dh(E, shift, x, nx, k, qr, D, H);
+  if (SK)
+    element_dhsk(E, shift, x, nx, k, qr, D, H, S, K);
+  else
+    element_dh(E, shift, x, nx, k, qr, D, H);
 }
 
 // T = -(D + (i/k) H)
 __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
   return mkc(-D.x + H.y / k, -D.y - H.x / k);
+}
+
+// T = -(D + b H) - i k beta (S + b K), b = i/k: the admittance condition
+// dp/dn_m = -i k beta p turns the dp/dn terms of the Burton-Miller equation
+// into -i k beta S + beta K.
+__device__ __forceinline__ cd bm_entry_adm(cd D, cd H, cd S, cd K, double k, cd beta) {
+  const cd t = mkc(K.x + k * S.y, K.y - k * S.x);   // K - i k S
+  return cadd(bm_entry(D, H, k), cmul(beta, t));
 }
 
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
@@ -361,10 +419,11 @@ __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
 // entries (a fraction of a per cent) are appended to near_list for
 // k_near_entries, which gives each of them a whole warp, or computed here
 // when the list is full.
+template <bool SK>
 __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
                                const double* __restrict__ shifts, const ff* __restrict__ shiftf,
                                const int64_t* __restrict__ dest, int n_off,
-                               int zero_off, cd* __restrict__ out, double k, QuadRules qr, FfConst C,
+                               int zero_off, cd* __restrict__ out, double k, cd beta, QuadRules qr, FfConst C,
                                unsigned long long* __restrict__ near_list, unsigned long long* __restrict__ near_count,
                                unsigned long long near_cap) {
   const ff kf = ff_from_d(k);
@@ -397,9 +456,9 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
         continue;
       }
     }
-    cd D, H;
-    element_dh_mixed(Ej, fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H);
-    out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
+    cd D, H, S, K;
+    element_dh_mixed<SK>(Ej, fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H, S, K);
+    out[(size_t)dest[o] * nn + rem] = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
   }
 }
 
@@ -407,13 +466,14 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
 // the lanes share the 64 points of the 8 x 8 collapsed rule (near) or the
 // 256 points of the rule on the four midpoint children (very near), in FP64,
 // and the sums are reduced across the warp in a fixed order.
+template <bool SK>
 __global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ el, int n,
                                                       const double* __restrict__ shifts,
                                                       const int64_t* __restrict__ dest,
                                                       const unsigned long long* __restrict__ list,
                                                       const unsigned long long* __restrict__ count,
                                                       unsigned long long cap, cd* __restrict__ out, double k,
-                                                      QuadRules qr) {
+                                                      cd beta, QuadRules qr) {
   const size_t nn = (size_t)n * n;
   const unsigned long long total = min(*count, cap);
   const int lane = threadIdx.x & 31;
@@ -438,7 +498,7 @@ __global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ e
     const double dist = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
     const bool very = dist < NEAR_RATIO * E.hmax;
     const int npts = very ? 4 * Q_NEAR * Q_NEAR : Q_NEAR * Q_NEAR;
-    cd D = mkc(0.0, 0.0), H = mkc(0.0, 0.0);
+    cd D = mkc(0.0, 0.0), H = mkc(0.0, 0.0), S = mkc(0.0, 0.0), K = mkc(0.0, 0.0);
     for (int p = lane; p < npts; p += 32) {
       const int child = p / (Q_NEAR * Q_NEAR), q = p - child * Q_NEAR * Q_NEAR;
       const int ia = q / Q_NEAR, ib = q - ia * Q_NEAR;
@@ -474,15 +534,21 @@ __global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ e
       const double sv = qr.t8[ia], tv = qr.t8[ib];
       double y[3];
       for (int d = 0; d < 3; ++d) y[d] = A[d] + sv * ((Bv[d] - A[d]) + tv * (Cv[d] - Bv[d]));
-      kernel_point(x, nx, y, E.nrm, two_area * sv * qr.w8[ia] * qr.w8[ib], k, D, H);
+      kernel_point4<SK>(x, nx, y, E.nrm, two_area * sv * qr.w8[ia] * qr.w8[ib], k, D, H, S, K);
     }
     for (int off = 16; off > 0; off >>= 1) {
       D.x += __shfl_xor_sync(0xffffffffu, D.x, off);
       D.y += __shfl_xor_sync(0xffffffffu, D.y, off);
       H.x += __shfl_xor_sync(0xffffffffu, H.x, off);
       H.y += __shfl_xor_sync(0xffffffffu, H.y, off);
+      if (SK) {
+        S.x += __shfl_xor_sync(0xffffffffu, S.x, off);
+        S.y += __shfl_xor_sync(0xffffffffu, S.y, off);
+        K.x += __shfl_xor_sync(0xffffffffu, K.x, off);
+        K.y += __shfl_xor_sync(0xffffffffu, K.y, off);
+      }
     }
-    if (lane == 0) out[(size_t)dest[o] * nn + rem] = bm_entry(D, H, k);
+    if (lane == 0) out[(size_t)dest[o] * nn + rem] = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
   }
 }
 
@@ -506,14 +572,19 @@ __device__ double sin_minus_xcos(double x) {
 }
 
 // Self term of element i (x_i at its centroid, on the flat panel):
-// D_ii = 0, H_ii = (1/4pi)[fp int r^-3 + int (e^{ikr}(1-ikr) - 1) r^-3].
-__global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict__ block0, double k,
+// D_ii = 0, H_ii = (1/4pi)[fp int r^-3 + int (e^{ikr}(1-ikr) - 1) r^-3];
+// with an admittance (beta != 0) also K_ii = 0 and
+// S_ii = (1/4pi)[int 1/r + int (e^{ikr} - 1)/r], the 1/r part in closed form
+// (polar coordinates about x: an edge at distance h with end coordinates
+// t_a, t_b along it gives h ln((t_b + |b - x|)/(t_a + |a - x|))).
+__global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict__ block0, double k, cd beta,
                              QuadRules qr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Elem& E = el[i];
   const double* x = E.c;
-  double fp = 0.0;
+  const bool adm = beta.x != 0.0 || beta.y != 0.0;
+  double fp = 0.0, invr = 0.0;
   for (int e = 0; e < 3; ++e) {
     const double* a = E.v[e];
     const double* b = E.v[(e + 1) % 3];
@@ -534,8 +605,9 @@ __global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict_
     double ra = sqrt(am[0] * am[0] + am[1] * am[1] + am[2] * am[2]);
     double rb = sqrt(bm[0] * bm[0] + bm[1] * bm[1] + bm[2] * bm[2]);
     fp -= (tb / rb - ta / ra) / he;
+    invr += he * log((tb + rb) / (ta + ra));
   }
-  double rem_re = 0.0, rem_im = 0.0;
+  double rem_re = 0.0, rem_im = 0.0, srem_re = 0.0, srem_im = 0.0;
   for (int e = 0; e < 3; ++e) {
     const double* a = E.v[e];
     const double* b = E.v[(e + 1) % 3];
@@ -559,18 +631,30 @@ __global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict_
         double r = sqrt(dx * dx + dy * dy + dz * dz);
         double kr = k * r;
         double sh = sin(0.5 * kr);
-        double re = -2.0 * sh * sh + kr * sin(kr);   // cos kr + kr sin kr - 1
+        const double skr = sin(kr);
+        double re = -2.0 * sh * sh + kr * skr;       // cos kr + kr sin kr - 1
         double im = sin_minus_xcos(kr);              // sin kr - kr cos kr
         double wr = ws * qr.w8[q] / (r * r * r);
         rem_re += wr * re;
         rem_im += wr * im;
+        if (adm) {
+          const double w1 = ws * qr.w8[q] / r;       // (e^{ikr} - 1)/r
+          srem_re += w1 * (-2.0 * sh * sh);
+          srem_im += w1 * skr;
+        }
       }
     }
   }
   const double inv4pi = 0.25 / PI;
   cd H = mkc((fp + rem_re) * inv4pi, rem_im * inv4pi);
   // 1/2 - (i/k) H
-  block0[(size_t)i * n + i] = mkc(0.5 + H.y / k, -H.x / k);
+  cd t = mkc(0.5 + H.y / k, -H.x / k);
+  if (adm) {
+    // + beta (1/2 - i k S)
+    const cd S = mkc((invr + srem_re) * inv4pi, srem_im * inv4pi);
+    t = cadd(t, cmul(beta, mkc(0.5 + k * S.y, -k * S.x)));
+  }
+  block0[(size_t)i * n + i] = t;
 }
 
 // ------------------------------------------------------- right-hand side --
@@ -604,10 +688,14 @@ __global__ void k_rhs_plane_wave(const Elem* __restrict__ el, int n, CellGrid g,
 
 // ---------------------------------------------------------- field points --
 // out[r][p] = p_inc,r(x_p) + sum_{c, j} D(x_p, E_j + pos_c) surf[r][c*n + j]
-__global__ void k_field(const Elem* __restrict__ el, int n, CellGrid g, double k, int R,
+// p(x) = p_inc(x) + sum_j (D(x, E_j) + i k beta S(x, E_j)) p_j: with an
+// admittance the single layer of dp/dn_m = -i k beta p joins the double layer.
+__global__ void k_field(const Elem* __restrict__ el, int n, CellGrid g, double k, cd beta, int R,
                         const double* __restrict__ dirs, const cd* __restrict__ amps,
                         const cd* __restrict__ surf, int64_t npts, const double* __restrict__ pts,
                         cd* __restrict__ out, QuadRules qr) {
+  const bool adm = beta.x != 0.0 || beta.y != 0.0;
+  const cd ikb = mkc(-k * beta.y, k * beta.x);
   const size_t total = (size_t)npts * R;
   const size_t N = (size_t)n * g.ncells;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -625,8 +713,13 @@ __global__ void k_field(const Elem* __restrict__ el, int n, CellGrid g, double k
       double pos[3];
       g.cell_position(c, pos);
       for (int j = 0; j < n; ++j) {
-        cd D, H;
-        element_dh(el[j], pos, x, nx, k, qr, D, H);
+        cd D, H, S, K;
+        if (adm) {
+          element_dhsk(el[j], pos, x, nx, k, qr, D, H, S, K);
+          D = cfma(ikb, S, D);
+        } else {
+          element_dh(el[j], pos, x, nx, k, qr, D, H);
+        }
         acc = cfma(D, surf[(size_t)r * N + (size_t)c * n + j], acc);
       }
     }
@@ -716,8 +809,8 @@ void free_mesh(DeviceMesh& m) {
   m.fc_dev = nullptr;
 }
 
-fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n_off, const int32_t* offsets,
-                         const int64_t* dest_host, cd* out, cudaStream_t st) {
+fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                         const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st) {
   // shifts: -delta . lattice
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
@@ -754,11 +847,16 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, int n
   if (e == cudaSuccess) e = cudaMemsetAsync(near_count, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
     unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
-    FMPB_LAUNCH("build_blocks", st, k_build_blocks<<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, m.qr, m.fc, near_list, near_count, near_cap));
-    FMPB_LAUNCH("build_near", st, k_near_entries<<<152 * 16, 256, 0, st>>>(m.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, m.qr));
+    if (beta.x == 0.0 && beta.y == 0.0) {
+      FMPB_LAUNCH("build_blocks", st, k_build_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, m.qr, m.fc, near_list, near_count, near_cap));
+      FMPB_LAUNCH("build_near", st, k_near_entries<false><<<152 * 16, 256, 0, st>>>(m.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, m.qr));
+    } else {
+      FMPB_LAUNCH("build_blocks_adm", st, k_build_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, m.qr, m.fc, near_list, near_count, near_cap));
+      FMPB_LAUNCH("build_near_adm", st, k_near_entries<true><<<152 * 16, 256, 0, st>>>(m.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, m.qr));
+    }
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
-                                                     k, m.qr));
+                                                     k, beta, m.qr));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -801,7 +899,7 @@ fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int
   return FMPB_OK;
 }
 
-fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R, const cd* surf,
+fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
                          const double* dirs_host, const fmpb_c64* amps_host, int64_t npts, const double* pts,
                          cd* out, cudaStream_t st) {
   std::vector<double> dirs(dirs_host, dirs_host + 3 * (size_t)R);
@@ -814,7 +912,7 @@ fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, int R
   FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
   const size_t total = (size_t)npts * R;
-  FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, m.n, g, k, R, ddirs, damps,
+  FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, m.n, g, k, beta, R, ddirs, damps,
                                                                              surf, npts, pts, out, m.qr));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(ddirs, st));
