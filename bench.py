@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile-case", default=None, choices=["product", "build", "near", "batch", "gmres"],
+    ap.add_argument("--profile-case", default=None,
+                    choices=["product", "build", "near", "batch", "gmres", "barrier", "admittance"],
                     help="small case for kernel captures: product/build = 3x8 cylinders (1.8 GB spectrum) at "
                          "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, BF16; gmres = 320 "
                          "Arnoldi steps of the full crystal at 300 Hz")
@@ -268,6 +269,7 @@ def run_ours(args):
     serving = serving_section(gb) if sections else None
     batching = batching_section(gb, torch, stream) if sections else None
     admittance = admittance_section(gb, torch, stream, w, v, t) if sections else None
+    halfspace = halfspace_section(gb, torch, stream) if sections else None
     mixed = (mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
              if not args.only_headline else None)
 
@@ -291,6 +293,7 @@ def run_ours(args):
         "serving": serving,
         "batching": batching,
         "admittance": admittance,
+        "halfspace": halfspace,
     }
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, v, t, iters)
@@ -613,6 +616,68 @@ def admittance_section(gb, torch, stream, w, v, t, beta=0.4 + 0.2j, freq_index=3
     return out
 
 
+def halfspace_section(gb, torch, stream, freq_indices=(1, 3)):
+    """The cylinder sound barrier of the paper's barrier study on a sound-hard
+    ground (Sec. 2.3, Sec. 3.4): 3 x 25 x 5 cells, N = 126,000, the image part
+    block Hankel along z, two monopoles.  FMM form (n_t = 10) at 200 Hz and at
+    the first Bragg frequency 428.75 Hz; PBEM form (two spectra, 8 GB) at
+    200 Hz, and the relative difference of the two solutions (the FMM
+    truncation error on this workload)."""
+    w = WORKLOADS["barrier_cylinders_3x25x5"]
+    v, t = w.mesh()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    inc = [("monopole", pos, amp) for pos, amp in w.monopoles]
+    out = {"workload": w.notes + "; monopoles " + str(list(w.monopoles))}
+    sols = {}
+    for form, fi in [("fmm", freq_indices[0]), ("fmm", freq_indices[1]), ("pbem", freq_indices[0])]:
+        k = w.wavenumbers[fi]
+        torch.cuda.synchronize()
+        gb.profile_reset()
+        gb.profile_enable(True)
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        op = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM if form == "fmm" else gb.FORM_PBEM,
+                         n_t=w.n_t, plane=w.plane)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        gb.profile_enable(False)
+        build_ms = b0.elapsed_time(b1)
+        bprof = gb.profile_summary()
+        x = torch.as_tensor(random_complex_vectors(w.rhs_seed, 1, op.N), device="cuda")
+        y = op.matvec(x)
+        torch.cuda.synchronize()
+        gb.profile_reset()
+        gb.profile_enable(True)
+        m0, m1 = ev(), ev()
+        m0.record(stream)
+        for _ in range(10):
+            op.matvec(x, out=y)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        gb.profile_enable(False)
+        mprof = gb.profile_summary()
+        rhs = op.rhs_incident(inc)
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        p, info = op.solve(rhs, tol=TOL, restart=SHORT_RESTART, maxit=MAXIT, raise_on_noconv=False)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        solve_ms = s0.elapsed_time(s1)
+        sols[(form, fi)] = p
+        out[f"{form}_{w.wavenumbers[fi] * SPEED_OF_SOUND / (2 * np.pi):.2f}Hz"] = {
+            "k": k, "build_ms": build_ms, "build_kernels_ms": {k_: v_[1] for k_, v_ in bprof.items()},
+            "matvec_ms": m0.elapsed_time(m1) / 10,
+            "matvec_kernels_ms": {k_: v_[1] / 10 for k_, v_ in mprof.items()},
+            "solve_ms": solve_ms, "iters": [i["iters"] for i in info],
+            "relres_true": [i["relres_true"] for i in info], "converged": all(i["converged"] for i in info),
+            "solves_per_s_incl_build": len(inc) * 1e3 / (build_ms + solve_ms),
+            "operator_bytes": op.info["bytes_device"], "n_near_image": op.info["n_near_image"]}
+        op.close()
+    a, b = sols[("fmm", freq_indices[0])], sols[("pbem", freq_indices[0])]
+    out["fmm_vs_pbem_solution_rel_diff"] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    return out
+
+
 def precision_section(gb, torch, stream, w, v, t, k, op64, x, y64, p64, fp64_solve_ms, fp64_build_ms):
     """The 32 x 32 sphere array in every precision of the library, against the
     FP64 (float-float) operator, whose products match the FP64 oracle to 1e-12:
@@ -806,7 +871,10 @@ def run_profile_case(args):
     product/build: 3 x 8 cylinders at 500 Hz (PBEM, spectrum 1.84 GB), one build
     and 4 products; near: the 32 x 32 sphere array (FMM form), one build and 3
     products; batch: 8 x 8 x 4 cubes, BF16 (tensor-core) FMM operator, 3 products
-    of 64 right-hand sides.  Prints one JSON line."""
+    of 64 right-hand sides; barrier: the half-space cylinder barrier (FMM form,
+    block Hankel image part), one build and 3 products; admittance: the 3 x 8
+    cylinders at 500 Hz with beta = 0.4 + 0.2i, one build.  Prints one JSON
+    line."""
     import torch
     import paper_2201_12050_gb300 as gb
     if args.profile_case == "gmres":
@@ -819,6 +887,26 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "gmres", "N": op.N, "iters": info[0]["iters"],
                           "relres_est": info[0]["relres_est"]}))
+        return
+    if args.profile_case == "barrier":
+        w2 = WORKLOADS["barrier_cylinders_3x25x5"]
+        v2, t2 = w2.mesh()
+        op = gb.Operator(v2, t2, w2.counts, w2.lattice, w2.wavenumbers[3], n_t=w2.n_t, plane=w2.plane)
+        x = torch.as_tensor(random_complex_vectors(w2.rhs_seed, 1, op.N), device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.matvec(x, out=y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "barrier", "N": op.N, "form": op.info["form_name"], "B": op.info["B"],
+                          "F": op.info["F"], "n_near_image": op.info["n_near_image"],
+                          "y_norm": float(torch.linalg.vector_norm(y))}))
+        return
+    if args.profile_case == "admittance":
+        w = WORKLOADS[WORKLOAD]
+        v, t = w.mesh()
+        op = gb.Operator(v, t, (3, 8, 1), w.lattice, 2 * math.pi * 500.0 / SPEED_OF_SOUND, beta=0.4 + 0.2j)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "admittance", "N": op.N, "F": op.info["F"]}))
         return
     if args.profile_case in ("near", "batch"):
         if args.profile_case == "near":

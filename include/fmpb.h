@@ -76,6 +76,17 @@ typedef enum { FMPB_FORM_AUTO = -1, FMPB_FORM_FMM = 0, FMPB_FORM_PBEM = 1 } fmpb
  *        keeps both the float-float and the BF16 tables. */
 typedef enum { FMPB_FP64 = 0, FMPB_FP32 = 1, FMPB_BF16 = 2, FMPB_MIXED = 3 } fmpb_precision;
 
+/* Incident fields: a plane wave amp e^{i k d.x} (Eq. (planewave); vec = unit
+ * direction d) or a monopole amp e^{i k r}/r, r = |x - x_s| (vec = source
+ * position x_s; amp is the pressure amplitude at 1 m; the source must not
+ * lie on the surface). */
+typedef enum { FMPB_INC_PLANE = 0, FMPB_INC_MONOPOLE = 1 } fmpb_incident_kind;
+typedef struct {
+  int32_t kind;      /* fmpb_incident_kind */
+  double vec[3];
+  fmpb_c64 amp;
+} fmpb_incident;
+
 /* Finite lattice (Sec. 2.2, Fig. PeriodicArray2d): counts[a] cells along
  * lattice vector vectors[a] (metres).  counts[a] = 1 for an unused axis. */
 typedef struct {
@@ -114,6 +125,25 @@ typedef struct {
    * i k beta int conj(I) dA to the P2M table. */
   double beta_re;
   double beta_im;
+  /* Half-space (Sec. 2.3, Eq. (green3dHalf)): halfspace = 1 replaces G by
+   * G_h(x, y) = G(x, y) + R_p G(x, y^), y^ the mirror image of y in the plane
+   * {x : x[plane_axis] = plane_offset}; 0 (zero-initialised) is full space.
+   * Every lattice axis with more than one cell must be parallel to the plane
+   * or perpendicular to it (at most one); a perpendicular axis makes the image
+   * part a block Hankel matrix (Eq. (blockToeplizMatrixSymmetry)), applied as
+   * the block Toeplitz product of the cell-reversed vector (Sec. 2.4).  The
+   * mesh of every cell must lie on one side of the plane (touching allowed).
+   * The image part is stored beside the full-space one (PBEM form with a
+   * perpendicular axis: a second spectrum; FMM form: image near blocks, a
+   * P2M table of the mirrored cell and a second M2L spectrum, Eq.
+   * (2dPeriodicFMM_halfspace)); PBEM with the lattice parallel to the plane
+   * adds the image blocks to the one block Toeplitz pattern.  Precisions
+   * FP64, FP32, and MIXED in the PBEM form. */
+  int32_t halfspace;
+  int32_t plane_axis;   /* 0, 1, 2 */
+  double plane_offset;
+  double Rp_re;         /* reflection coefficient R_p (1: rigid plane, -1: soft) */
+  double Rp_im;
 } fmpb_operator_opts;
 
 typedef struct {
@@ -131,6 +161,10 @@ typedef struct {
   int32_t precision;     /* fmpb_precision of the stored spectrum(s) */
   double beta_re;        /* surface admittance the operator was built with */
   double beta_im;
+  int32_t halfspace;     /* 1 for a half-space operator */
+  int32_t hankel_axis;   /* lattice axis perpendicular to the plane, -1 if none */
+  int32_t n_near_image;  /* image offsets evaluated exactly (FMM form), else 0 */
+  int32_t image_separate;/* 1 if the image part has its own tables and products */
 } fmpb_operator_info;
 
 /*
@@ -170,6 +204,14 @@ void fmpb_operator_destroy(fmpb_operator *op);
  */
 fmpb_status fmpb_rhs_plane_wave(const fmpb_operator *op, int R, const double *dirs,
                                 const fmpb_c64 *amps, fmpb_c64 *b, void *stream);
+/*
+ * Right-hand sides of R incident fields of any kind (fmpb_incident, host
+ * array of R), with their images R_p p_inc(M x) for a half-space operator:
+ * b_r(x_i) = p_inc(x_i) + (i/k) dp_inc/dn(x_i).  fmpb_rhs_plane_wave is the
+ * plane-wave case.   b device, R x N.
+ */
+fmpb_status fmpb_rhs_incident(const fmpb_operator *op, int R, const fmpb_incident *inc, fmpb_c64 *b,
+                              void *stream);
 
 /*
  * y = A x for R vectors at once, A the collocation operator of the chosen
@@ -239,6 +281,11 @@ fmpb_status fmpb_operator_check(const fmpb_operator *op, void *stream);
 fmpb_status fmpb_field(const fmpb_operator *op, int R, const fmpb_c64 *p, const double *dirs,
                        const fmpb_c64 *amps, int64_t npts, const double *pts, fmpb_c64 *out,
                        void *stream);
+/* fmpb_field for incident fields of any kind (host array of R); for a
+ * half-space operator the sums include R_p times the mirrored elements and
+ * the incident fields their images. */
+fmpb_status fmpb_field_incident(const fmpb_operator *op, int R, const fmpb_c64 *p, const fmpb_incident *inc,
+                                int64_t npts, const double *pts, fmpb_c64 *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * Building blocks (the same kernels the operator uses), for callers that

@@ -31,7 +31,17 @@ class Lattice(ctypes.Structure):
 
 class OperatorOpts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("n_t", ctypes.c_int), ("precision", ctypes.c_int),
-                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double)]
+                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
+                ("halfspace", ctypes.c_int32), ("plane_axis", ctypes.c_int32), ("plane_offset", ctypes.c_double),
+                ("Rp_re", ctypes.c_double), ("Rp_im", ctypes.c_double)]
+
+
+class C64(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class Incident(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("vec", ctypes.c_double * 3), ("amp", C64)]
 
 
 class OperatorInfo(ctypes.Structure):
@@ -39,7 +49,9 @@ class OperatorInfo(ctypes.Structure):
                 ("form", ctypes.c_int32), ("n_t", ctypes.c_int32), ("B", ctypes.c_int64),
                 ("P", ctypes.c_int32 * 3), ("F", ctypes.c_int64), ("n_near", ctypes.c_int32),
                 ("bytes_device", ctypes.c_size_t), ("precision", ctypes.c_int32),
-                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double)]
+                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
+                ("halfspace", ctypes.c_int32), ("hankel_axis", ctypes.c_int32), ("n_near_image", ctypes.c_int32),
+                ("image_separate", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -98,6 +110,8 @@ SIGNATURES = {
     "fmpb_field": (INT, [P, INT, P, P, P, I64, P, P, P]),
     "fmpb_build_blocks": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, INT, P, P, P]),
     "fmpb_multipole_tables": (INT, [P, I64, P, I64, D, INT, P, P, P]),
+    "fmpb_rhs_incident": (INT, [P, INT, P, P, P]),
+    "fmpb_field_incident": (INT, [P, INT, P, P, I64, P, P, P]),
     "fmpb_build_blocks_admittance": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
     "fmpb_multipole_tables_admittance": (INT, [P, I64, P, I64, D, D, D, INT, P, P, P]),
     "fmpb_m2l_blocks": (INT, [D, INT, INT, P, P, P]),

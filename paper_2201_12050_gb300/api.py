@@ -8,7 +8,7 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, SolveOpts, SolveInfo, FmpbError, ServerOpts,
+from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, Incident, C64, SolveOpts, SolveInfo, FmpbError, ServerOpts,
                    Request, Result, ServerStats, STATUS)
 
 FORM_AUTO, FORM_FMM, FORM_PBEM = -1, 0, 1
@@ -55,15 +55,22 @@ def _cvec(x, N, name):
 
 class Operator:
     """fmpb_operator: the tables of one (unit-cell mesh, lattice, k); beta is
-    the surface's uniform normalised admittance (0: rigid)."""
+    the surface's uniform normalised admittance (0: rigid); plane =
+    (axis, offset, R_p) makes it a half-space operator (None: full space)."""
 
-    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64, beta=0.0):
+    def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64, beta=0.0,
+                 plane=None):
         self._lib = lib()
         v = _host(verts, np.float64)
         t = _host(tris, np.int32)
         self._lat = _lattice(counts, vectors)
         beta = complex(beta)
         opts = OperatorOpts(int(form), int(n_t), int(precision), beta.real, beta.imag)
+        if plane is not None:
+            axis, offset, Rp = plane
+            Rp = complex(Rp)
+            opts.halfspace, opts.plane_axis, opts.plane_offset = 1, int(axis), float(offset)
+            opts.Rp_re, opts.Rp_im = Rp.real, Rp.imag
         h = ctypes.c_void_p()
         check(self._lib.fmpb_operator_create(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(self._lat),
                                              float(k), ctypes.byref(opts), _stream(), ctypes.byref(h)))
@@ -100,6 +107,30 @@ class Operator:
         b = out if out is not None else torch.empty((R, self.N), dtype=torch.complex128, device="cuda")
         check(self._lib.fmpb_rhs_plane_wave(self._h, R, _ptr(d), None if a is None else _ptr(a), _ptr(b), _stream()))
         return b
+
+    def rhs_incident(self, incidents, out=None):
+        """fmpb_rhs_incident: incidents = [(kind, vec, amp)], kind "plane"
+        (vec = unit direction) or "monopole" (vec = source position)."""
+        inc = _incidents(incidents)
+        R = len(inc)
+        b = out if out is not None else torch.empty((R, self.N), dtype=torch.complex128, device="cuda")
+        check(self._lib.fmpb_rhs_incident(self._h, R, ctypes.cast(inc, ctypes.c_void_p), _ptr(b), _stream()))
+        return b
+
+    def field_incident(self, p, incidents, pts):
+        """fmpb_field_incident: total pressure at pts for incident fields of any kind."""
+        R = _cvec(p, self.N, "p")
+        inc = _incidents(incidents)
+        if len(inc) != R:
+            raise ValueError("one incident field per right-hand side")
+        if not (isinstance(pts, torch.Tensor) and pts.is_cuda and pts.dtype == torch.float64):
+            pts = torch.as_tensor(np.asarray(pts, dtype=np.float64), device="cuda")
+        pts = pts.contiguous()
+        npts = pts.numel() // 3
+        out = torch.empty((R, npts), dtype=torch.complex128, device="cuda")
+        check(self._lib.fmpb_field_incident(self._h, R, _ptr(p), ctypes.cast(inc, ctypes.c_void_p), npts, _ptr(pts),
+                                            _ptr(out), _stream()))
+        return out
 
     def matvec(self, x, out=None):
         R = _cvec(x, self.N, "x")
@@ -149,6 +180,18 @@ def build_blocks(verts, tris, counts, vectors, k, offsets):
     check(lib().fmpb_build_blocks(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k), len(off), _ptr(off),
                                   _ptr(out), _stream()))
     return out
+
+
+def _incidents(incidents):
+    kinds = {"plane": 0, "monopole": 1}
+    arr = (Incident * len(incidents))()
+    for i, (kind, vec, amp) in enumerate(incidents):
+        a = complex(amp)
+        arr[i].kind = kinds[kind]
+        for d in range(3):
+            arr[i].vec[d] = float(vec[d])
+        arr[i].amp = C64(a.real, a.imag)
+    return arr
 
 
 def build_blocks_admittance(verts, tris, counts, vectors, k, beta, offsets):

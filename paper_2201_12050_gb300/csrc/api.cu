@@ -188,6 +188,17 @@ struct fmpb_operator {
   __nv_bfloat16* U0b = nullptr;   // tc_rows(n) x tc_depth(B)
   TcOffsets near_tc{};
   unsigned* tc_err = nullptr;     // set by a tensor-core kernel whose wait gave up
+  // half-space image part (Sec. 2.3, Sec. 3.4)
+  PlaneDev plane{0, 0, 0.0, {0.0, 0.0}};
+  int hankel = -1;                // lattice axis perpendicular to the plane
+  bool img_sep = false;           // image part with its own tables and products
+  DeviceMesh refl;                // reflected unit cell (R v, reversed winding)
+  cd* spec_img = nullptr;         // image spectrum (PBEM blocks or FMM M2L), float-float
+  void* spec32_img = nullptr;     // the same in complex FP32
+  cd* S_img = nullptr;            // n_near_img x n x n image near blocks (FMM)
+  int* near_offs_img = nullptr;
+  int n_near_img = 0;
+  cd* V0_img = nullptr;           // R_p x P2M table of the reflected cell (FMM)
   size_t bytes = 0;
   // scratch, grown on demand (calls on one operator are stream-ordered)
   cd* scratch = nullptr;
@@ -208,6 +219,12 @@ struct fmpb_operator {
     cudaFree(U0b);
     cudaFree(tc_err);
     cudaFree(scratch);
+    free_mesh(refl);
+    cudaFree(spec_img);
+    cudaFree(spec32_img);
+    cudaFree(S_img);
+    cudaFree(near_offs_img);
+    cudaFree(V0_img);
   }
 
   fmpb_status ensure_scratch(size_t elems) {
@@ -222,7 +239,7 @@ struct fmpb_operator {
   }
 
   // The PBEM-form product of an FP64 operator on float-float vectors.
-  bool has_ff_matvec() const { return form == FMPB_FORM_PBEM && spec != nullptr; }
+  bool has_ff_matvec() const { return form == FMPB_FORM_PBEM && spec != nullptr && !img_sep; }
   fmpb_status matvec_ff(int R, const float4* x, float4* y, cudaStream_t st) {
     FMPB_TRY(ensure_scratch(circulant_scratch_elems(shape, B, R)));
     return circulant_apply(shape, B, spec, R, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), false,
@@ -237,13 +254,22 @@ struct fmpb_operator {
     const cd* sp = f32 ? reinterpret_cast<const cd*>(spec32) : spec;
     const int fmt = f32 ? SPEC_F32 : SPEC_FF;
     if (form == FMPB_FORM_PBEM) {
-      FMPB_TRY(ensure_scratch(circulant_scratch_elems(shape, B, R)));
-      return circulant_apply(shape, B, sp, R, x, y, false, scratch, st, fmt);
+      const size_t circ = circulant_scratch_elems(shape, B, R);
+      FMPB_TRY(ensure_scratch(circ + (img_sep ? (size_t)R * Nc * B : 0)));
+      FMPB_TRY(circulant_apply(shape, B, sp, R, x, y, false, scratch, st, fmt));
+      if (img_sep) {
+        // the block Hankel image part: (T^ P)(P x) (Sec. 2.4)
+        cd* q = scratch + circ;
+        FMPB_TRY(reverse_cells(x, q, sizeof(cd), R, shape.M, mesh.n, hankel, st));
+        const cd* spi = f32 ? reinterpret_cast<const cd*>(spec32_img) : spec_img;
+        FMPB_TRY(circulant_apply(shape, B, spi, R, q, y, true, scratch, st, fmt));
+      }
+      return FMPB_OK;
     }
     const size_t circ = circulant_scratch_elems(shape, B, R);
     const size_t mom = (size_t)R * Nc * B;
     const size_t nvec = (size_t)R * Nc * mesh.n;
-    FMPB_TRY(ensure_scratch(circ + 2 * mom + nvec));
+    FMPB_TRY(ensure_scratch(circ + 2 * mom + (img_sep ? 2 : 1) * nvec));
     cd* Mom = scratch + circ;
     cd* Loc = Mom + mom;
     float4* xff = reinterpret_cast<float4*>(Loc + mom);
@@ -269,6 +295,10 @@ struct fmpb_operator {
       FMPB_TRY(tc_offset_gemm(U0b, zero, n, B, shape.M, R, lb, y, true, tc_err, st));
       return FMPB_OK;
     }
+    // the image part of a half-space operator (Eq. (2dPeriodicFMM_halfspace)):
+    // near blocks S^ and P2M table V^ of the mirrored cell act on q = P x, its
+    // M2L spectrum adds to the same local expansions (U^ = U)
+    const cd* spi = f32 ? reinterpret_cast<const cd*>(spec32_img) : spec_img;
     if (precision == FMPB_FP32) {
       float2* x32 = reinterpret_cast<float2*>(Loc + mom);
       FMPB_TRY(vector_to_f32(x, x32, nvec, st));
@@ -276,6 +306,17 @@ struct fmpb_operator {
                               st));
       FMPB_TRY(p2m_apply_f32(reinterpret_cast<const float2*>(V0), mesh.n, (int)B, (int64_t)R * Nc, x32, Mom, st));
       FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
+      if (img_sep) {
+        float2* q32 = x32;
+        if (hankel >= 0) {
+          q32 = x32 + nvec;
+          FMPB_TRY(reverse_cells(x32, q32, sizeof(float2), R, shape.M, mesh.n, hankel, st));
+        }
+        FMPB_TRY(near_apply_f32(reinterpret_cast<const float2*>(S_img), near_offs_img, n_near_img, mesh.n, shape.M, R,
+                                q32, y, true, st));
+        FMPB_TRY(p2m_apply_f32(reinterpret_cast<const float2*>(V0_img), mesh.n, (int)B, (int64_t)R * Nc, q32, Mom, st));
+        FMPB_TRY(circulant_apply(shape, B, spi, R, Mom, Loc, true, scratch, st, fmt));
+      }
       FMPB_TRY(l2p_apply_f32(reinterpret_cast<const float2*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
       return FMPB_OK;
     }
@@ -283,6 +324,17 @@ struct fmpb_operator {
     FMPB_TRY(near_apply(reinterpret_cast<const float4*>(S), near_offs, n_near, mesh.n, shape.M, R, xff, y, false, st));
     FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0), mesh.n, (int)B, (int64_t)R * Nc, xff, Mom, st));
     FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
+    if (img_sep) {
+      float4* qff = xff;
+      if (hankel >= 0) {
+        qff = xff + nvec;
+        FMPB_TRY(reverse_cells(xff, qff, sizeof(float4), R, shape.M, mesh.n, hankel, st));
+      }
+      FMPB_TRY(near_apply(reinterpret_cast<const float4*>(S_img), near_offs_img, n_near_img, mesh.n, shape.M, R, qff, y,
+                          true, st));
+      FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0_img), mesh.n, (int)B, (int64_t)R * Nc, qff, Mom, st));
+      FMPB_TRY(circulant_apply(shape, B, spi, R, Mom, Loc, true, scratch, st, fmt));
+    }
     FMPB_TRY(l2p_apply(reinterpret_cast<const float4*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
     return FMPB_OK;
   }
@@ -295,6 +347,107 @@ struct fmpb_operator {
       return FMPB_EINVAL;         \
     }                             \
   } while (0)
+
+namespace fmpb {
+
+// Half-space set-up (Sec. 2.3): checks the plane and the role of every
+// lattice axis (parallel to the plane, or perpendicular to it: at most one),
+// checks that every cell lies on one side of the plane, and uploads the
+// reflected unit cell (R v, reversed winding, so that its element normals are
+// R n and the quadrature rules apply unchanged).
+static fmpb_status setup_halfspace(fmpb_operator* op, const fmpb_operator_opts& o, const double* verts, int64_t nv,
+                                   const int32_t* tris, int64_t ntri, cudaStream_t st) {
+  const int ax = o.plane_axis;
+  if (ax < 0 || ax > 2 || !std::isfinite(o.plane_offset) || !std::isfinite(o.Rp_re) || !std::isfinite(o.Rp_im)) {
+    set_error("operator_create: half-space needs plane_axis 0..2 and finite plane_offset, R_p");
+    return FMPB_EINVAL;
+  }
+  const CellGrid& g = op->grid;
+  int h = -1;
+  for (int a = 0; a < 3; ++a) {
+    if (g.M[a] <= 1) continue;
+    const double n = sqrt(g.L[a][0] * g.L[a][0] + g.L[a][1] * g.L[a][1] + g.L[a][2] * g.L[a][2]);
+    const double along = fabs(g.L[a][ax]);
+    if (along <= 1e-12 * n) continue;
+    if (fabs(along - n) <= 1e-12 * n && h < 0) {
+      h = a;
+      continue;
+    }
+    set_error("operator_create: lattice vector %d is neither parallel nor perpendicular to the plane "
+              "(or a second perpendicular axis)", a);
+    return FMPB_EINVAL;
+  }
+  // extent of the cells' positions along the plane normal (corners of the grid)
+  double pmin = 1e300, pmax = -1e300;
+  for (int corner = 0; corner < 8; ++corner) {
+    double p = 0.0;
+    for (int a = 0; a < 3; ++a) p += ((corner >> a) & 1) * (g.M[a] - 1) * g.L[a][ax];
+    pmin = fmin(pmin, p);
+    pmax = fmax(pmax, p);
+  }
+  double vmin = 1e300, vmax = -1e300, cmin = 1e300, cmax = -1e300, scale = fabs(o.plane_offset);
+  for (int64_t v = 0; v < nv; ++v) {
+    vmin = fmin(vmin, verts[3 * v + ax]);
+    vmax = fmax(vmax, verts[3 * v + ax]);
+    scale = fmax(scale, fabs(verts[3 * v + ax]));
+  }
+  for (int64_t t = 0; t < ntri; ++t) {
+    const double c = (verts[3 * tris[3 * t] + ax] + verts[3 * tris[3 * t + 1] + ax] + verts[3 * tris[3 * t + 2] + ax]) / 3.0;
+    cmin = fmin(cmin, c);
+    cmax = fmax(cmax, c);
+  }
+  scale = fmax(scale, fmax(fabs(pmin), fabs(pmax)));
+  const double tol = 1e-12 * scale;
+  const bool above = vmin + pmin - o.plane_offset >= -tol && cmin + pmin - o.plane_offset > tol;
+  const bool below = vmax + pmax - o.plane_offset <= tol && cmax + pmax - o.plane_offset < -tol;
+  if (!above && !below) {
+    set_error("operator_create: the cells do not lie on one side of the plane x[%d] = %.6g", ax, o.plane_offset);
+    return FMPB_EMESH;
+  }
+  std::vector<double> rv(verts, verts + 3 * nv);
+  for (int64_t v = 0; v < nv; ++v) rv[3 * v + ax] = -rv[3 * v + ax];
+  std::vector<int32_t> rt(3 * ntri);
+  for (int64_t t = 0; t < ntri; ++t) {
+    rt[3 * t] = tris[3 * t];
+    rt[3 * t + 1] = tris[3 * t + 2];
+    rt[3 * t + 2] = tris[3 * t + 1];
+  }
+  FMPB_TRY(upload_mesh(rv.data(), nv, rt.data(), ntri, op->refl, st));
+  op->plane = PlaneDev{1, ax, o.plane_offset, mkc(o.Rp_re, o.Rp_im)};
+  op->hankel = h;
+  return FMPB_OK;
+}
+
+// shift(delta~) = -delta~ . L - (M_h - 1) L_h + 2 offset e: where the
+// reflected unit cell sits for the image block delta~ (x_c - y^_c = -shift).
+static std::vector<double> image_shifts(const fmpb_operator* op, const std::vector<int32_t>& offs) {
+  const CellGrid& g = op->grid;
+  const size_t n = offs.size() / 3;
+  std::vector<double> sh(3 * n);
+  for (size_t o = 0; o < n; ++o)
+    for (int d = 0; d < 3; ++d) {
+      double v = 0.0;
+      for (int a = 0; a < 3; ++a) v -= offs[3 * o + a] * g.L[a][d];
+      if (op->hankel >= 0) v -= (g.M[op->hankel] - 1) * g.L[op->hankel][d];
+      if (d == op->plane.axis) v += 2.0 * op->plane.offset;
+      sh[3 * o + d] = v;
+    }
+  return sh;
+}
+
+// r of the mirrored admissibility criterion: the longest lattice vector
+// among the axes with more than one cell.
+static double image_r(const CellGrid& g) {
+  double r = 0.0, rall = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double n = sqrt(g.L[a][0] * g.L[a][0] + g.L[a][1] * g.L[a][1] + g.L[a][2] * g.L[a][2]);
+    rall = fmax(rall, n);
+    if (g.M[a] > 1) r = fmax(r, n);
+  }
+  return r > 0.0 ? r : rall;
+}
+
+}  // namespace fmpb
 
 extern "C" {
 
@@ -359,6 +512,40 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
               "this lattice needs the PBEM form, which has none (use FMPB_FP32 or FMPB_MIXED)");
     return fail(FMPB_EINVAL);
   }
+  // half-space: the image offsets delta~ over the same pattern; in the FMM
+  // form those whose mirrored cell is within 2 r (Eq. (admissibilityMirror))
+  // are near, the others must admit the expansion about the mirrored centre
+  std::vector<int32_t> near_img, far_img;
+  std::vector<double> far_img_t;
+  if (o.halfspace) {
+    s = setup_halfspace(op, o, verts, nv, tris, ntri, st);
+    if (s != FMPB_OK) return fail(s);
+    const std::vector<double> shifts = image_shifts(op, all_off);
+    const double r2 = 2.0 * image_r(op->grid) * (1.0 - 1e-9);
+    double dmin_img = 1e300;
+    for (size_t i = 0; i < all_off.size() / 3; ++i) {
+      const double* t = &shifts[3 * i];
+      const double d = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+      std::vector<int32_t>& dst = d < r2 ? near_img : far_img;
+      dst.insert(dst.end(), &all_off[3 * i], &all_off[3 * i] + 3);
+      if (d >= r2) {
+        for (int c = 0; c < 3; ++c) far_img_t.push_back(-t[c]);
+        dmin_img = fmin(dmin_img, d);
+      }
+    }
+    const double rho = op->mesh.radius;
+    if (o.form == FMPB_FORM_AUTO && form == FMPB_FORM_FMM && !(dmin_img >= 3.0 * rho)) form = FMPB_FORM_PBEM;
+    if (o.form == FMPB_FORM_FMM && !(dmin_img > 2.0 * rho)) {
+      set_error("operator_create: FMM form not admissible for the mirrored cells (nearest far image at %.4g, "
+                "cell radius %.4g)", dmin_img, rho);
+      return fail(FMPB_EADMISS);
+    }
+    if (o.precision == FMPB_BF16 || (o.precision == FMPB_MIXED && form == FMPB_FORM_FMM)) {
+      set_error("operator_create: half-space operators run FMPB_FP64, FMPB_FP32 or (PBEM form) FMPB_MIXED");
+      return fail(FMPB_EINVAL);
+    }
+    op->img_sep = form == FMPB_FORM_FMM || op->hankel >= 0;
+  }
   op->form = form;
   if (form == FMPB_FORM_PBEM) {
     op->B = n;
@@ -371,6 +558,23 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     for (int i = 0; i < n_off; ++i) dest[i] = offset_slot(sh, all_off[3 * i], all_off[3 * i + 1], all_off[3 * i + 2]);
     s = build_blocks(op->mesh, op->grid, k, beta, n_off, all_off.data(), dest.data(), op->spec, st);
     if (s != FMPB_OK) return fail(s);
+    if (op->plane.on) {
+      // image blocks R_p T^(delta~): added to the same pattern when the
+      // lattice is parallel to the plane, else a second (block Hankel) spectrum
+      const std::vector<double> shifts = image_shifts(op, all_off);
+      cd* dst = op->spec;
+      if (op->img_sep) {
+        s = dev_alloc(&op->spec_img, elems, op->bytes);
+        if (s != FMPB_OK) return fail(s);
+        if (cudaMemsetAsync(op->spec_img, 0, sizeof(cd) * elems, st) != cudaSuccess)
+          return fail(cuda_status(cudaGetLastError(), "memset"));
+        dst = op->spec_img;
+      }
+      const ImageBlocks ib{&op->refl, shifts.data(), op->plane.Rp, !op->img_sep};
+      s = build_blocks(op->mesh, op->grid, k, beta, n_off, all_off.data(), dest.data(), dst, st, &ib);
+      if (s == FMPB_OK && op->img_sep) s = grid_fft_inplace(sh, (int64_t)n * n, op->spec_img, st);
+      if (s != FMPB_OK) return fail(s);
+    }
     s = grid_fft_inplace(sh, (int64_t)n * n, op->spec, st);   // leaves float-float pairs
     if (s != FMPB_OK) return fail(s);
   } else {
@@ -452,6 +656,54 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     s = m2l_blocks(nt, k, n_far, dvec.data(), dfar.data(), op->spec, st);
     if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec, st);   // leaves float-float pairs
     if (s != FMPB_OK) return fail(s);
+    if (op->img_sep) {
+      // image part (Eq. (2dPeriodicFMM_halfspace)): R_p S^ at the near image
+      // offsets, V^ = R_p x the P2M table of the reflected cell, and the M2L
+      // blocks of the translations x_c - y^_c of the far image offsets
+      op->n_near_img = (int)(near_img.size() / 3);
+      const std::vector<double> shn = image_shifts(op, near_img);
+      std::vector<int64_t> dn(op->n_near_img);
+      for (int i = 0; i < op->n_near_img; ++i) dn[i] = i;
+      s = dev_alloc(&op->S_img, (size_t)op->n_near_img * n * n, op->bytes);
+      if (s == FMPB_OK) s = dev_alloc(&op->near_offs_img, near_img.size(), op->bytes);
+      if (s == FMPB_OK) s = dev_alloc(&op->V0_img, (size_t)B * n, op->bytes);
+      if (s == FMPB_OK) s = dev_alloc(&op->spec_img, (size_t)sh.F * B * B, op->bytes);
+      if (s != FMPB_OK) return fail(s);
+      if ((near_img.size() && cudaMemcpyAsync(op->near_offs_img, near_img.data(), sizeof(int) * near_img.size(),
+                                              cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+          cudaMemsetAsync(op->spec_img, 0, sizeof(cd) * (size_t)sh.F * B * B, st) != cudaSuccess)
+        return fail(cuda_status(cudaGetLastError(), "operator_create copies"));
+      const ImageBlocks ib{&op->refl, shn.data(), op->plane.Rp, false};
+      if (op->n_near_img > 0)
+        s = build_blocks(op->mesh, op->grid, k, beta, op->n_near_img, near_img.data(), dn.data(), op->S_img, st, &ib);
+      if (s == FMPB_OK) s = multipole_tables(op->refl, k, beta, nt, op->V0_img, nullptr, st);
+      if (s == FMPB_OK) s = scale_inplace(op->V0_img, (size_t)B * n, op->plane.Rp, st);
+      const int n_far_img = (int)(far_img.size() / 3);
+      std::vector<int64_t> dfi(n_far_img);
+      for (int i = 0; i < n_far_img; ++i) dfi[i] = offset_slot(sh, far_img[3 * i], far_img[3 * i + 1], far_img[3 * i + 2]);
+      if (s == FMPB_OK && n_far_img > 0) s = m2l_blocks(nt, k, n_far_img, far_img_t.data(), dfi.data(), op->spec_img, st);
+      if (s == FMPB_OK) s = grid_fft_inplace(sh, B * B, op->spec_img, st);
+      if (o.precision == FMPB_FP32) {
+        for (cd** t : {&op->S_img, &op->V0_img}) {
+          const size_t ne = (t == &op->S_img) ? (size_t)op->n_near_img * n * n : (size_t)B * n;
+          float2* f32 = nullptr;
+          if (s == FMPB_OK) s = dev_alloc(&f32, ne, op->bytes);
+          if (s == FMPB_OK) s = vector_to_f32(*t, f32, ne, st);
+          if (s == FMPB_OK && cudaStreamSynchronize(st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tables");
+          if (s == FMPB_OK) {
+            cudaFree(*t);
+            op->bytes -= sizeof(cd) * ne;
+            *t = reinterpret_cast<cd*>(f32);
+          } else if (f32) {
+            cudaFree(f32);
+          }
+        }
+      } else {
+        if (s == FMPB_OK) s = spectrum_to_ff(op->S_img, (size_t)op->n_near_img * n * n, st);
+        if (s == FMPB_OK) s = spectrum_to_ff(op->V0_img, (size_t)B * n, st);
+      }
+      if (s != FMPB_OK) return fail(s);
+    }
   }
   op->precision = o.precision;
   const size_t ne = (size_t)sh.F * op->B * op->B;
@@ -460,6 +712,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   if (want32) {
     s = dev_alloc(reinterpret_cast<float2**>(&op->spec32), ne, op->bytes);
     if (s == FMPB_OK) s = spectrum_ff_to_f32(op->spec, op->spec32, ne, st);
+    if (s == FMPB_OK && op->spec_img) s = dev_alloc(reinterpret_cast<float2**>(&op->spec32_img), ne, op->bytes);
+    if (s == FMPB_OK && op->spec_img) s = spectrum_ff_to_f32(op->spec_img, op->spec32_img, ne, st);
     if (s != FMPB_OK) return fail(s);
   }
   if (wantb) {
@@ -473,6 +727,11 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     cudaFree(op->spec);
     op->spec = nullptr;
     op->bytes -= sizeof(cd) * ne;
+    if (op->spec_img) {
+      cudaFree(op->spec_img);
+      op->spec_img = nullptr;
+      op->bytes -= sizeof(cd) * ne;
+    }
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "operator_create"));
@@ -496,6 +755,10 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->precision = op->precision;
   info->beta_re = op->beta.x;
   info->beta_im = op->beta.y;
+  info->halfspace = op->plane.on;
+  info->hankel_axis = op->hankel;
+  info->n_near_image = op->n_near_img;
+  info->image_separate = op->img_sep ? 1 : 0;
   return FMPB_OK;
 }
 
@@ -505,7 +768,19 @@ fmpb_status fmpb_rhs_plane_wave(const fmpb_operator* op, int R, const double* di
                                 fmpb_c64* b, void* stream) {
   CHECK_ARG(op && dirs && b, "rhs_plane_wave: NULL argument");
   CHECK_ARG(R >= 1 && R <= 65535, "rhs_plane_wave: R out of range");
-  return rhs_plane_wave(op->mesh, op->grid, op->k, R, dirs, amps, (cd*)b, (cudaStream_t)stream);
+  std::vector<fmpb_incident> inc(R);
+  for (int r = 0; r < R; ++r) {
+    inc[r].kind = FMPB_INC_PLANE;
+    for (int d = 0; d < 3; ++d) inc[r].vec[d] = dirs[3 * r + d];
+    inc[r].amp = amps ? amps[r] : fmpb_c64{1.0, 0.0};
+  }
+  return rhs_incident(op->mesh, op->grid, op->k, R, inc.data(), op->plane, (cd*)b, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_rhs_incident(const fmpb_operator* op, int R, const fmpb_incident* inc, fmpb_c64* b, void* stream) {
+  CHECK_ARG(op && inc && b, "rhs_incident: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 65535, "rhs_incident: R out of range");
+  return rhs_incident(op->mesh, op->grid, op->k, R, inc, op->plane, (cd*)b, (cudaStream_t)stream);
 }
 
 fmpb_status fmpb_matvec(const fmpb_operator* op, int R, const fmpb_c64* x, fmpb_c64* y, void* stream) {
@@ -559,8 +834,21 @@ fmpb_status fmpb_field(const fmpb_operator* op, int R, const fmpb_c64* p, const 
                        int64_t npts, const double* pts, fmpb_c64* out, void* stream) {
   CHECK_ARG(op && p && dirs && pts && out, "field: NULL argument");
   CHECK_ARG(R >= 1 && R <= 65535 && npts >= 1, "field: R or npts out of range");
-  return field_points(op->mesh, op->grid, op->k, op->beta, R, (const cd*)p, dirs, amps, npts, pts, (cd*)out,
-                      (cudaStream_t)stream);
+  std::vector<fmpb_incident> inc(R);
+  for (int r = 0; r < R; ++r) {
+    inc[r].kind = FMPB_INC_PLANE;
+    for (int d = 0; d < 3; ++d) inc[r].vec[d] = dirs[3 * r + d];
+    inc[r].amp = amps ? amps[r] : fmpb_c64{1.0, 0.0};
+  }
+  return fmpb_field_incident(op, R, p, inc.data(), npts, pts, out, stream);
+}
+
+fmpb_status fmpb_field_incident(const fmpb_operator* op, int R, const fmpb_c64* p, const fmpb_incident* inc,
+                                int64_t npts, const double* pts, fmpb_c64* out, void* stream) {
+  CHECK_ARG(op && p && inc && pts && out, "field: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 65535 && npts >= 1, "field: R or npts out of range");
+  return field_incident(op->mesh, op->plane.on ? &op->refl : nullptr, op->grid, op->k, op->beta, op->plane, R,
+                        (const cd*)p, inc, npts, pts, (cd*)out, (cudaStream_t)stream);
 }
 
 fmpb_status fmpb_build_blocks(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,

@@ -653,6 +653,54 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   return FMPB_OK;
 }
 
+// out[r][c][i] = in[r][P c][i]: the cells of every right-hand side reversed
+// along lattice axis h (the permutation P of the block Hankel image part of a
+// half-space operator, Sec. 2.4).  in and out do not overlap.
+template <typename T>
+__global__ void k_reverse_cells(const T* __restrict__ in, T* __restrict__ out, int64_t total, int n, int Mx, int My,
+                                int Mz, int h) {
+  const int64_t Nc = (int64_t)Mx * My * Mz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n);
+    const int64_t rc = idx / n;
+    const int c = (int)(rc % Nc);
+    const int64_t r = rc / Nc;
+    int cx = c % Mx, cy = (c / Mx) % My, cz = c / (Mx * My);
+    if (h == 0) cx = Mx - 1 - cx;
+    if (h == 1) cy = My - 1 - cy;
+    if (h == 2) cz = Mz - 1 - cz;
+    out[idx] = in[(r * Nc + ((int64_t)cz * My + cy) * Mx + cx) * n + i];
+  }
+}
+
+fmpb_status reverse_cells(const void* in, void* out, size_t elem_bytes, int R, const int M[3], int n, int h,
+                          cudaStream_t st) {
+  if (h < 0 || h > 2 || (elem_bytes != 8 && elem_bytes != 16)) {
+    set_error("reverse_cells: bad axis or element size");
+    return FMPB_EINVAL;
+  }
+  const int64_t total = (int64_t)R * M[0] * M[1] * M[2] * n;
+  const unsigned grid = (unsigned)std::min<int64_t>(grid_for(total, 256), 152 * 32);
+  if (elem_bytes == 16)
+    FMPB_LAUNCH("reverse_cells", st, k_reverse_cells<float4><<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(in), reinterpret_cast<float4*>(out), total, n, M[0], M[1], M[2], h));
+  else
+    FMPB_LAUNCH("reverse_cells", st, k_reverse_cells<float2><<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), total, n, M[0], M[1], M[2], h));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+__global__ void k_scale_cd(cd* __restrict__ a, size_t n, cd s) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a[i] = cmul(s, a[i]);
+}
+
+fmpb_status scale_inplace(cd* a, size_t n, cd s, cudaStream_t st) {
+  FMPB_LAUNCH("scale", st, k_scale_cd<<<std::min<size_t>(grid_for(n, 256), 152 * 32), 256, 0, st>>>(a, n, s));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 // Scatter blocks given in offset order (delta_x fastest, 1-M..M-1) into the
 // zeroed padded grid.
 __global__ void k_scatter_offsets(const cd* __restrict__ blocks, cd* __restrict__ grid, int64_t BB,

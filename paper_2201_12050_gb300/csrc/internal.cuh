@@ -70,15 +70,48 @@ struct DeviceMesh {
 fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, DeviceMesh& m,
                         cudaStream_t st);
 void free_mesh(DeviceMesh& m);
+// Image blocks of a half-space operator (Sec. 2.3): per offset the shift of
+// the reflected unit cell (3 doubles, host), the factor R_p, and whether the
+// entries are added to out (the full-space blocks of the same pattern).
+struct ImageBlocks {
+  const DeviceMesh* source;   // the reflected unit cell (elements); targets stay in m
+  const double* shifts;
+  cd scale;
+  bool accumulate;
+};
 // Builds n_off collocation blocks; block o is written at out + dest[o] * n * n.
-// beta: uniform normalised admittance of the surface (0: rigid).
+// beta: uniform normalised admittance of the surface (0: rigid).  img: the
+// image blocks of m's collocation points against the reflected cell (no self
+// terms), else the full-space blocks at shifts -delta . lattice.
 fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
-                         const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);
-fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int R, const double* dirs_host,
-                           const fmpb_c64* amps_host, cd* b, cudaStream_t st);
-fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
-                         const double* dirs_host, const fmpb_c64* amps_host, int64_t npts, const double* pts,
-                         cd* out, cudaStream_t st);
+                         const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
+                         const ImageBlocks* img = nullptr);
+
+// One incident field on the device (kind 0: plane wave, v = direction;
+// kind 1: monopole, v = source position) and the symmetry plane of a
+// half-space operator (on = 0: full space).
+struct IncDev {
+  int kind;
+  double v[3];
+  cd amp;
+};
+struct PlaneDev {
+  int on;
+  int axis;
+  double offset;
+  cd Rp;
+};
+fmpb_status rhs_incident(const DeviceMesh& m, const CellGrid& g, double k, int R, const fmpb_incident* inc,
+                         const PlaneDev& pl, cd* b, cudaStream_t st);
+fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const CellGrid& g, double k, cd beta,
+                           const PlaneDev& pl, int R, const cd* surf, const fmpb_incident* inc, int64_t npts,
+                           const double* pts, cd* out, cudaStream_t st);
+
+// P x: cells reversed along lattice axis h for every right-hand side (16- or
+// 8-byte elements, n per cell); a * s in place.
+fmpb_status reverse_cells(const void* in, void* out, size_t elem_bytes, int R, const int M[3], int n, int h,
+                          cudaStream_t st);
+fmpb_status scale_inplace(cd* a, size_t n, cd s, cudaStream_t st);
 
 // Circulant engine (circulant.cu)
 // In-place forward DFT over the padded grid of F slots, each holding `inner`

@@ -413,6 +413,18 @@ __device__ __forceinline__ cd bm_entry_adm(cd D, cd H, cd S, cd K, double k, cd 
   return cadd(bm_entry(D, H, k), cmul(beta, t));
 }
 
+// How a block kernel stores an entry: out = v, or out (+)= scale v (image
+// blocks of a half-space operator: R_p times the entries, added to the
+// full-space blocks when both share one block Toeplitz pattern).
+struct BlockWrite {
+  cd scale;
+  int scaled, accumulate;
+  __device__ __forceinline__ void put(cd* dst, cd v) const {
+    if (scaled) v = cmul(scale, v);
+    *dst = accumulate ? cadd(*dst, v) : v;
+  }
+};
+
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
 // out + dest[o] * n * n.  The diagonal of the zero offset is left to
 // k_self_terms.  Far-class entries are computed here; near and very-near
@@ -420,12 +432,13 @@ __device__ __forceinline__ cd bm_entry_adm(cd D, cd H, cd S, cd K, double k, cd 
 // k_near_entries, which gives each of them a whole warp, or computed here
 // when the list is full.
 template <bool SK>
-__global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
+__global__ void k_build_blocks(const Elem* __restrict__ tel, const FfElem* __restrict__ tfel,
+                               const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
                                const double* __restrict__ shifts, const ff* __restrict__ shiftf,
                                const int64_t* __restrict__ dest, int n_off,
-                               int zero_off, cd* __restrict__ out, double k, cd beta, QuadRules qr, FfConst C,
-                               unsigned long long* __restrict__ near_list, unsigned long long* __restrict__ near_count,
-                               unsigned long long near_cap) {
+                               int zero_off, cd* __restrict__ out, double k, cd beta, BlockWrite bw, QuadRules qr,
+                               FfConst C, unsigned long long* __restrict__ near_list,
+                               unsigned long long* __restrict__ near_count, unsigned long long near_cap) {
   const ff kf = ff_from_d(k);
   const size_t nn = (size_t)n * n;
   const size_t total = nn * (size_t)n_off;
@@ -436,11 +449,11 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
     const int i = (int)(rem / n);
     const int j = (int)(rem - (size_t)i * n);
     if (o == zero_off && i == j) continue;
-    const Elem& Ti = el[i];
+    const Elem& Ti = tel[i];
     double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
     double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
     // the target normal in float-float is the element's own (prepared once)
-    const FfElem& Fi = fel[i];
+    const FfElem& Fi = tfel[i];
     const ff nxf[3] = {Fi.ny[0], Fi.ny[1], Fi.ny[2]};
     const ff xf[3] = {Fi.c[0], Fi.c[1], Fi.c[2]};
     double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
@@ -458,7 +471,7 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
     }
     cd D, H, S, K;
     element_dh_mixed<SK>(Ej, fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H, S, K);
-    out[(size_t)dest[o] * nn + rem] = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
+    bw.put(out + (size_t)dest[o] * nn + rem, SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k));
   }
 }
 
@@ -467,13 +480,13 @@ __global__ void k_build_blocks(const Elem* __restrict__ el, const FfElem* __rest
 // 256 points of the rule on the four midpoint children (very near), in FP64,
 // and the sums are reduced across the warp in a fixed order.
 template <bool SK>
-__global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ el, int n,
+__global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ tel, const Elem* __restrict__ el, int n,
                                                       const double* __restrict__ shifts,
                                                       const int64_t* __restrict__ dest,
                                                       const unsigned long long* __restrict__ list,
                                                       const unsigned long long* __restrict__ count,
                                                       unsigned long long cap, cd* __restrict__ out, double k,
-                                                      cd beta, QuadRules qr) {
+                                                      cd beta, BlockWrite bw, QuadRules qr) {
   const size_t nn = (size_t)n * n;
   const unsigned long long total = min(*count, cap);
   const int lane = threadIdx.x & 31;
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ e
     const size_t rem = idx - (size_t)o * nn;
     const int i = (int)(rem / n);
     const int j = (int)(rem - (size_t)i * n);
-    const Elem& Ti = el[i];
+    const Elem& Ti = tel[i];
     const Elem& E = el[j];
     const double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
     const double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ e
         K.y += __shfl_xor_sync(0xffffffffu, K.y, off);
       }
     }
-    if (lane == 0) out[(size_t)dest[o] * nn + rem] = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
+    if (lane == 0) bw.put(out + (size_t)dest[o] * nn + rem, SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k));
   }
 }
 
@@ -658,9 +671,58 @@ __global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict_
 }
 
 // ------------------------------------------------------- right-hand side --
-__global__ void k_rhs_plane_wave(const Elem* __restrict__ el, int n, CellGrid g, double k, int R,
-                                 const double* __restrict__ dirs, const cd* __restrict__ amps,
-                                 cd* __restrict__ b) {
+// p_inc and dp_inc/dn at x (normal nrm) of one incident field: a plane wave
+// amp e^{ik d.x} (Eq. (planewave)) or a monopole amp e^{ikr}/r, r = |x - x_s|.
+__device__ void incident_free(const IncDev& in, const double x[3], const double nrm[3], double k, cd& p, cd& dp) {
+  if (in.kind == 0) {
+    double ph = 0.0, dn = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      ph += in.v[d] * x[d];
+      dn += in.v[d] * nrm[d];
+    }
+    double s, c;
+    sincos(k * ph, &s, &c);
+    p = cmul(in.amp, mkc(c, s));
+    dp = cmul(mkc(0.0, k * dn), p);   // i k (d.n) p
+    return;
+  }
+  double rv[3], r2 = 0.0, rn = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    rv[d] = x[d] - in.v[d];
+    r2 += rv[d] * rv[d];
+    rn += rv[d] * nrm[d];
+  }
+  const double r = sqrt(r2);
+  double s, c;
+  sincos(k * r, &s, &c);
+  p = cmulr(cmul(in.amp, mkc(c, s)), 1.0 / r);
+  // d/dn e^{ikr}/r = e^{ikr}/r (ikr - 1)/r (r_vec . n)/r
+  dp = cmul(p, mkc(-rn / r2, k * rn / r));
+}
+
+// With a plane, the image R_p p_inc(M x): its normal derivative along n is the
+// derivative of p_inc at M x along R n.
+__device__ void incident_at(const IncDev& in, const PlaneDev& pl, const double x[3], const double nrm[3], double k,
+                            cd& p, cd& dp) {
+  incident_free(in, x, nrm, k, p, dp);
+  if (pl.on) {
+    double xm[3], nm[3];
+    for (int d = 0; d < 3; ++d) {
+      xm[d] = x[d];
+      nm[d] = nrm[d];
+    }
+    xm[pl.axis] = 2.0 * pl.offset - x[pl.axis];
+    nm[pl.axis] = -nrm[pl.axis];
+    cd pi, dpi;
+    incident_free(in, xm, nm, k, pi, dpi);
+    p = cfma(pl.Rp, pi, p);
+    dp = cfma(pl.Rp, dpi, dp);
+  }
+}
+
+// b_r(x_i) = p_inc(x_i) + (i/k) dp_inc/dn(x_i) at every collocation point.
+__global__ void k_rhs_incident(const Elem* __restrict__ el, int n, CellGrid g, double k, int R,
+                               const IncDev* __restrict__ inc, PlaneDev pl, cd* __restrict__ b) {
   const size_t N = (size_t)n * g.ncells;
   const size_t total = N * R;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -669,31 +731,26 @@ __global__ void k_rhs_plane_wave(const Elem* __restrict__ el, int n, CellGrid g,
     const size_t gi = idx - (size_t)r * N;
     const int c = (int)(gi / n);
     const int i = (int)(gi - (size_t)c * n);
-    double pos[3];
-    g.cell_position(c, pos);
+    double x[3];
+    g.cell_position(c, x);
     const Elem& E = el[i];
-    const double* dv = dirs + 3 * r;
-    double ph = 0.0, dn = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      ph += dv[d] * (E.c[d] + pos[d]);
-      dn += dv[d] * E.nrm[d];
-    }
-    double s, co;
-    sincos(k * ph, &s, &co);
-    cd pinc = cmul(amps[r], mkc(co, s));
-    // p_inc + (i/k) * i k (d.n) p_inc = p_inc (1 - d.n)
-    b[idx] = cmulr(pinc, 1.0 - dn);
+    for (int d = 0; d < 3; ++d) x[d] += E.c[d];
+    cd p, dp;
+    incident_at(inc[r], pl, x, E.nrm, k, p, dp);
+    b[idx] = mkc(p.x - dp.y / k, p.y + dp.x / k);   // p + (i/k) dp
   }
 }
 
 // ---------------------------------------------------------- field points --
-// out[r][p] = p_inc,r(x_p) + sum_{c, j} D(x_p, E_j + pos_c) surf[r][c*n + j]
-// p(x) = p_inc(x) + sum_j (D(x, E_j) + i k beta S(x, E_j)) p_j: with an
-// admittance the single layer of dp/dn_m = -i k beta p joins the double layer.
-__global__ void k_field(const Elem* __restrict__ el, int n, CellGrid g, double k, cd beta, int R,
-                        const double* __restrict__ dirs, const cd* __restrict__ amps,
-                        const cd* __restrict__ surf, int64_t npts, const double* __restrict__ pts,
-                        cd* __restrict__ out, QuadRules qr) {
+// out[r][p] = p_inc,r(x_p) + sum_{c, j} (D + i k beta S)(x_p, E_j + pos_c) surf[r][c*n + j]
+// (Eq. (cbie) with c = 1; with an admittance the single layer of
+// dp/dn_m = -i k beta p joins the double layer), and for a half-space
+// operator R_p times the same sum over the mirrored elements: refl holds the
+// reflected unit cell (R v, reversed winding), placed for cell c at
+// R pos_c + 2 offset e.
+__global__ void k_field(const Elem* __restrict__ el, const Elem* __restrict__ refl, int n, CellGrid g, double k,
+                        cd beta, PlaneDev pl, int R, const IncDev* __restrict__ inc, const cd* __restrict__ surf,
+                        int64_t npts, const double* __restrict__ pts, cd* __restrict__ out, QuadRules qr) {
   const bool adm = beta.x != 0.0 || beta.y != 0.0;
   const cd ikb = mkc(-k * beta.y, k * beta.x);
   const size_t total = (size_t)npts * R;
@@ -704,24 +761,29 @@ __global__ void k_field(const Elem* __restrict__ el, int n, CellGrid g, double k
     const int64_t p = (int64_t)(idx - (size_t)r * npts);
     double x[3] = {pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]};
     double nx[3] = {0.0, 0.0, 1.0};
-    const double* dv = dirs + 3 * r;
-    double ph = dv[0] * x[0] + dv[1] * x[1] + dv[2] * x[2];
-    double s, co;
-    sincos(k * ph, &s, &co);
-    cd acc = cmul(amps[r], mkc(co, s));
-    for (int c = 0; c < g.ncells; ++c) {
-      double pos[3];
-      g.cell_position(c, pos);
-      for (int j = 0; j < n; ++j) {
-        cd D, H, S, K;
-        if (adm) {
-          element_dhsk(el[j], pos, x, nx, k, qr, D, H, S, K);
-          D = cfma(ikb, S, D);
-        } else {
-          element_dh(el[j], pos, x, nx, k, qr, D, H);
+    cd acc, dummy;
+    incident_at(inc[r], pl, x, nx, k, acc, dummy);
+    for (int side = 0; side < (pl.on ? 2 : 1); ++side) {
+      const Elem* els = side ? refl : el;
+      cd sum = mkc(0.0, 0.0);
+      for (int c = 0; c < g.ncells; ++c) {
+        double pos[3];
+        g.cell_position(c, pos);
+        if (side) {
+          pos[pl.axis] = 2.0 * pl.offset - pos[pl.axis];
         }
-        acc = cfma(D, surf[(size_t)r * N + (size_t)c * n + j], acc);
+        for (int j = 0; j < n; ++j) {
+          cd D, H, S, K;
+          if (adm) {
+            element_dhsk(els[j], pos, x, nx, k, qr, D, H, S, K);
+            D = cfma(ikb, S, D);
+          } else {
+            element_dh(els[j], pos, x, nx, k, qr, D, H);
+          }
+          sum = cfma(D, surf[(size_t)r * N + (size_t)c * n + j], sum);
+        }
       }
+      acc = side ? cfma(pl.Rp, sum, acc) : cadd(acc, sum);
     }
     out[idx] = acc;
   }
@@ -810,15 +872,25 @@ void free_mesh(DeviceMesh& m) {
 }
 
 fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
-                         const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st) {
-  // shifts: -delta . lattice
+                         const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
+                         const ImageBlocks* img) {
+  // shifts: -delta . lattice, or the image shifts given by the caller
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
   for (int o = 0; o < n_off; ++o) {
     const int32_t* dl = offsets + 3 * o;
-    if (dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
+    if (!img && dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
     for (int d = 0; d < 3; ++d)
-      shifts[3 * o + d] = -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
+      shifts[3 * o + d] = img ? img->shifts[3 * o + d]
+                              : -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
+  }
+  BlockWrite bw{mkc(1.0, 0.0), 0, 0};
+  if (img) bw = BlockWrite{img->scale, 1, img->accumulate ? 1 : 0};
+  // collocation points from m, elements from the reflected cell for images
+  const DeviceMesh& src = img ? *img->source : m;
+  if (src.n != m.n) {
+    set_error("build_blocks: source and target cells differ in size");
+    return FMPB_EINVAL;
   }
   // the same shifts as float-float pairs (hi = nearest float, lo = nearest float of the rest)
   std::vector<ff> shiftf(3 * (size_t)n_off);
@@ -848,11 +920,11 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
   if (e == cudaSuccess) {
     unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
     if (beta.x == 0.0 && beta.y == 0.0) {
-      FMPB_LAUNCH("build_blocks", st, k_build_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, m.qr, m.fc, near_list, near_count, near_cap));
-      FMPB_LAUNCH("build_near", st, k_near_entries<false><<<152 * 16, 256, 0, st>>>(m.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, m.qr));
+      FMPB_LAUNCH("build_blocks", st, k_build_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.ffel, src.el, src.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, bw, m.qr, m.fc, near_list, near_count, near_cap));
+      FMPB_LAUNCH("build_near", st, k_near_entries<false><<<152 * 16, 256, 0, st>>>(m.el, src.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw, m.qr));
     } else {
-      FMPB_LAUNCH("build_blocks_adm", st, k_build_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, m.qr, m.fc, near_list, near_count, near_cap));
-      FMPB_LAUNCH("build_near_adm", st, k_near_entries<true><<<152 * 16, 256, 0, st>>>(m.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, m.qr));
+      FMPB_LAUNCH("build_blocks_adm", st, k_build_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.ffel, src.el, src.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, bw, m.qr, m.fc, near_list, near_count, near_cap));
+      FMPB_LAUNCH("build_near_adm", st, k_near_entries<true><<<152 * 16, 256, 0, st>>>(m.el, src.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw, m.qr));
     }
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
@@ -868,55 +940,62 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
   return FMPB_OK;
 }
 
-fmpb_status rhs_plane_wave(const DeviceMesh& m, const CellGrid& g, double k, int R, const double* dirs_host,
-                           const fmpb_c64* amps_host, cd* b, cudaStream_t st) {
-  std::vector<double> dirs(3 * (size_t)R);
-  std::vector<cd> amps(R);
+static fmpb_status upload_incident(int R, const fmpb_incident* inc, double k, IncDev** out, cudaStream_t st) {
+  std::vector<IncDev> h(R);
   for (int r = 0; r < R; ++r) {
+    const fmpb_incident& a = inc[r];
+    if (a.kind != FMPB_INC_PLANE && a.kind != FMPB_INC_MONOPOLE) {
+      set_error("incident field %d: unknown kind %d", r, a.kind);
+      return FMPB_EINVAL;
+    }
     double nrm = 0.0;
     for (int d = 0; d < 3; ++d) {
-      dirs[3 * r + d] = dirs_host[3 * r + d];
-      nrm += dirs[3 * r + d] * dirs[3 * r + d];
+      if (!std::isfinite(a.vec[d])) {
+        set_error("incident field %d: vector not finite", r);
+        return FMPB_EINVAL;
+      }
+      h[r].v[d] = a.vec[d];
+      nrm += a.vec[d] * a.vec[d];
     }
-    if (!(fabs(nrm - 1.0) < 1e-6)) {
+    if (a.kind == FMPB_INC_PLANE && !(fabs(nrm - 1.0) < 1e-6)) {
       set_error("rhs: direction %d is not a unit vector", r);
       return FMPB_EINVAL;
     }
-    amps[r] = amps_host ? mkc(amps_host[r].re, amps_host[r].im) : mkc(1.0, 0.0);
+    h[r].kind = a.kind;
+    h[r].amp = mkc(a.amp.re, a.amp.im);
   }
-  double* ddirs = nullptr;
-  cd* damps = nullptr;
-  FMPB_CUDA(cudaMallocAsync(&ddirs, sizeof(double) * 3 * R, st));
-  FMPB_CUDA(cudaMallocAsync(&damps, sizeof(cd) * R, st));
-  FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
-  FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
-  const size_t total = (size_t)m.n * g.ncells * R;
-  FMPB_LAUNCH("rhs_plane_wave", st, k_rhs_plane_wave<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(m.el, m.n, g, k, R, ddirs,
-                                                                                      damps, b));
-  FMPB_CUDA(cudaGetLastError());
-  FMPB_CUDA(cudaFreeAsync(ddirs, st));
-  FMPB_CUDA(cudaFreeAsync(damps, st));
+  (void)k;
+  IncDev* d = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&d, sizeof(IncDev) * R, st));
+  FMPB_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(IncDev) * R, cudaMemcpyHostToDevice, st));
+  *out = d;
   return FMPB_OK;
 }
 
-fmpb_status field_points(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
-                         const double* dirs_host, const fmpb_c64* amps_host, int64_t npts, const double* pts,
-                         cd* out, cudaStream_t st) {
-  std::vector<double> dirs(dirs_host, dirs_host + 3 * (size_t)R);
-  std::vector<cd> amps(R);
-  for (int r = 0; r < R; ++r) amps[r] = amps_host ? mkc(amps_host[r].re, amps_host[r].im) : mkc(1.0, 0.0);
-  double* ddirs = nullptr;
-  cd* damps = nullptr;
-  FMPB_CUDA(cudaMallocAsync(&ddirs, sizeof(double) * 3 * R, st));
-  FMPB_CUDA(cudaMallocAsync(&damps, sizeof(cd) * R, st));
-  FMPB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
-  FMPB_CUDA(cudaMemcpyAsync(damps, amps.data(), sizeof(cd) * R, cudaMemcpyHostToDevice, st));
-  const size_t total = (size_t)npts * R;
-  FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, m.n, g, k, beta, R, ddirs, damps,
-                                                                             surf, npts, pts, out, m.qr));
+fmpb_status rhs_incident(const DeviceMesh& m, const CellGrid& g, double k, int R, const fmpb_incident* inc,
+                         const PlaneDev& pl, cd* b, cudaStream_t st) {
+  IncDev* dinc = nullptr;
+  FMPB_TRY(upload_incident(R, inc, k, &dinc, st));
+  const size_t total = (size_t)m.n * g.ncells * R;
+  FMPB_LAUNCH("rhs_incident", st, k_rhs_incident<<<std::min<size_t>(grid_for(total, 256), 152 * 32), 256, 0, st>>>(m.el, m.n, g, k, R, dinc, pl, b));
   FMPB_CUDA(cudaGetLastError());
-  FMPB_CUDA(cudaFreeAsync(ddirs, st));
-  FMPB_CUDA(cudaFreeAsync(damps, st));
+  FMPB_CUDA(cudaFreeAsync(dinc, st));
+  return FMPB_OK;
+}
+
+fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const CellGrid& g, double k, cd beta,
+                           const PlaneDev& pl, int R, const cd* surf, const fmpb_incident* inc, int64_t npts,
+                           const double* pts, cd* out, cudaStream_t st) {
+  if (pl.on && !refl) {
+    set_error("field: half-space operator without its reflected cell");
+    return FMPB_EINVAL;
+  }
+  IncDev* dinc = nullptr;
+  FMPB_TRY(upload_incident(R, inc, k, &dinc, st));
+  const size_t total = (size_t)npts * R;
+  FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, pl.on ? refl->el : m.el, m.n, g, k, beta, pl, R, dinc, surf, npts, pts, out, m.qr));
+  FMPB_CUDA(cudaGetLastError());
+  FMPB_CUDA(cudaFreeAsync(dinc, st));
   return FMPB_OK;
 }
 

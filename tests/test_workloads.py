@@ -39,10 +39,20 @@ def test_pcg32_reference_stream_and_vectors():
 
 def test_workload_sizes():
     sizes = {"sphere_row_4": 1280, "sonic_crystal_3x20": 72000,
-             "sphere_array_32x32": 327680, "cube_lattice_16x16x4": 442368}
+             "sphere_array_32x32": 327680, "cube_lattice_16x16x4": 442368,
+             "barrier_cylinders_3x25x5": 126000}
     for name, N in sizes.items():
         w = WORKLOADS[name]
         v, t = w.mesh()
         assert len(t) * int(np.prod(w.counts)) == N
+    # the barrier's open cylinder segments: normals radially outward, cells
+    # stacked without gaps from the ground plane z = -0.2 upwards
+    w = WORKLOADS["barrier_cylinders_3x25x5"]
+    v, t = w.mesh()
+    tri = v[t]
+    nrm = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    cen = tri.mean(axis=1)
+    assert (np.einsum("ij,ij->i", nrm[:, :2], cen[:, :2]) > 0).all()
+    assert v[:, 2].min() == w.plane[1] and v[:, 2].max() - v[:, 2].min() == w.lattice[2, 2]
     d = fibonacci_directions(64)
     assert np.allclose(np.linalg.norm(d, axis=1), 1.0) and abs(d.mean(0)).max() < 0.05

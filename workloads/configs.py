@@ -11,7 +11,7 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .meshes import icosphere, capped_cylinder, cube
+from .meshes import icosphere, capped_cylinder, cube, open_cylinder
 
 SPEED_OF_SOUND = 343.0
 
@@ -28,6 +28,8 @@ class Workload:
     pbem_form: bool = False                # every offset dense (cells too tall for the FMM)
     n_t: int = 0                           # truncation number (0 = not an FMM workload)
     notes: str = ""
+    plane: tuple = None                    # (axis, offset, R_p) of a half-space workload
+    monopoles: tuple = ()                  # ((x, y, z), amplitude at 1 m) incident monopoles
 
     @property
     def dim(self) -> int:
@@ -97,6 +99,24 @@ WORKLOADS = {
         rhs_seed=_SEED + 3,
         n_t=12,
         notes="16x16x4 rigid cubes edge 0.3 m in 0.5 m cells, 432 triangles per cell, N=442,368",
+    ),
+    # the cylinder sound barrier of the paper's barrier study: 3 x 25 rigid
+    # cylinders r = 0.1 m, 2 m high, on a sound-hard ground, as cells of
+    # 0.4 m stacked 5 high (the z axis is perpendicular to the ground: block
+    # Hankel image part); two monopoles 1 m above the ground
+    "barrier_cylinders_3x25x5": Workload(
+        name="barrier_cylinders_3x25x5",
+        make_mesh=lambda: open_cylinder(0.1, 0.4, 12, 14),
+        counts=(3, 25, 5),
+        lattice=np.diag([0.4, 0.4, 0.4]),
+        wavenumbers=_freqs_to_k([100.0, 200.0, 300.0, 428.75, 500.0]),
+        directions=np.array([[1.0, 0.0, 0.0]]),
+        rhs_seed=_SEED + 5,
+        n_t=10,
+        notes="3x25x5 cells of open cylinder segments r=0.1 m h=0.4 m, lattice 0.4 m, ground z=0 (R_p=1), "
+              "336 triangles per cell, N=126,000",
+        plane=(2, -0.2, 1.0),
+        monopoles=(((-4.0, 6.5, 0.8), 2.0), ((-4.0, 3.5, 0.8), 1.0)),
     ),
 }
 

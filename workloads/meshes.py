@@ -100,6 +100,31 @@ def capped_cylinder(radius: float, height: float, n_around: int = 20, n_rows: in
     return verts, tris.astype(np.int32)
 
 
+def open_cylinder(radius: float, height: float, n_around: int = 12, n_rows: int = 14):
+    """Mantle of a cylinder along z, centred on the origin, without caps (a
+    unit cell of a column of stacked cells): ``n_around`` segments by
+    ``n_rows`` rows of quads split into two triangles, wound so that the
+    normals point radially outward (336 triangles with the defaults)."""
+    ang = 2.0 * np.pi * np.arange(n_around) / n_around
+    zs = np.linspace(-height / 2.0, height / 2.0, n_rows + 1)
+    verts = np.array([(radius * np.cos(a), radius * np.sin(a), z) for z in zs for a in ang], dtype=np.float64)
+    tris = []
+    for r in range(n_rows):
+        for s in range(n_around):
+            a = r * n_around + s
+            b = r * n_around + (s + 1) % n_around
+            c = (r + 1) * n_around + s
+            d = (r + 1) * n_around + (s + 1) % n_around
+            tris += [(a, b, d), (a, d, c)]
+    tris = np.array(tris, dtype=np.int64)
+    v = verts[tris]
+    nrm = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    cen = v.mean(axis=1)
+    flip = np.einsum("ij,ij->i", nrm[:, :2], cen[:, :2]) < 0
+    tris[flip] = tris[flip][:, [0, 2, 1]]
+    return verts, tris.astype(np.int32)
+
+
 def cube(edge: float, n_per_edge: int = 6):
     """Axis-aligned cube centred on the origin, each face an
     ``n_per_edge`` x ``n_per_edge`` grid of squares split into two triangles
