@@ -883,9 +883,14 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         float4* vn = V + (int64_t)(j + 1) * vstride; // z = A p
         FMPB_TRY((*Aff)(R, vj, vn, st));
         jdone = j + 1;
-        FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb, (j + 2 + DOT2_VB - 1) / DOT2_VB, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
-        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb, (j + 2) * R, h, 0));
-        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb, (j + 1) * R, hB, 0));
+        // row blocks per vector group: about two waves of CTAs in total, so
+        // that a long basis gives each thread many rows and the per-CTA
+        // reduction is amortised (a short one keeps up to nb row blocks)
+        const int vg = (j + 2 + DOT2_VB - 1) / DOT2_VB;
+        const int nb2 = std::max(1, std::min(nb, (152 * 4 * 2 + vg * R - 1) / (vg * R)));
+        FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb2, (j + 2) * R, h, 0));
+        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb2, (j + 1) * R, hB, 0));
         FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
         FMPB_LAUNCH("dcgs2_hess_t", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
         FMPB_LAUNCH("update_dcgs2", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
