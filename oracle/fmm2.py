@@ -121,9 +121,13 @@ def regular_translation(bvec, k, nt, rho=None, nq=None):
     int I_q(rho u + b) conj(Y_q'(u)) dOmega."""
     coeffs = sp.coeff_list(nt)
     if rho is None:
-        rho = max(np.linalg.norm(bvec), 1.0 / k)
+        # the division by j_n'(k rho) amplifies quadrature rounding: take the
+        # k rho in [1.5, 8] that keeps min_n |j_n(k rho)| largest
+        grid = np.linspace(1.5, 8.0, 27)
+        score = [min(abs(sp.sph_jn(n, x)) for n in range(nt + 1)) for x in grid]
+        rho = grid[int(np.argmax(score))] / k
     if nq is None:
-        nq = 2 * nt + 24
+        nq = 2 * nt + 24 + int(k * np.linalg.norm(bvec))
     x, wx = np.polynomial.legendre.leggauss(nq)
     nphi = 2 * nq
     phi = 2 * np.pi * np.arange(nphi) / nphi

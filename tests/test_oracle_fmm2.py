@@ -49,7 +49,7 @@ def test_regular_translation_equals_the_3j_form():
             for qj, (n2, m2) in enumerate(coeffs):
                 C[qj, sp.coeff_index(n, -m)] = (-1) ** (m % 2) * (2 * n + 1) / (2 * n2 + 1) * K[qi, qj]
         R = fmm2.regular_translation(np.asarray(b), k, nt)
-        assert np.abs(C - R).max() < 1e-9 * np.abs(R).max()
+        assert np.abs(C - R).max() < 1e-12 * np.abs(R).max()
 
 
 def test_m2m_and_l2l_converge_to_direct_expansions():
