@@ -313,6 +313,7 @@ def run_ours(args):
     batching = batching_section(gb, torch, stream) if sections else None
     admittance = admittance_section(gb, torch, stream, w, v, t) if sections else None
     halfspace = halfspace_section(gb, torch, stream) if sections else None
+    fmm2 = fmm2_section(gb, torch, stream) if sections else None
     mixed = (mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
              if not args.only_headline else None)
 
@@ -340,6 +341,7 @@ def run_ours(args):
         "batching": batching,
         "admittance": admittance,
         "halfspace": halfspace,
+        "fmm2": fmm2,
     }
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, v, t, iters)
@@ -667,6 +669,66 @@ def admittance_section(gb, torch, stream, w, v, t, beta=0.4 + 0.2j, freq_index=3
     r, a = out["rigid"], out["admittance"]
     out["quadrature_kernel_time_ratio"] = (a["build_kernels_ms"].get("build_blocks_adm", float("nan"))
                                            / r["build_kernels_ms"].get("build_blocks", float("nan")))
+    return out
+
+
+def fmm2_section(gb, torch, stream, n_t_near=6):
+    """FMPBEM2 (Sec. 3.3) against the single-level FMM form on large unit
+    cells: 5 x 10 spheres of 5,120 triangles (N = 256,000, n_t = 8, k = 4).
+    The FMM form stores 9 exact near blocks of 5,120 x 5,120; FMPBEM2 keeps
+    only the entries of leaf pairs that are not well separated and runs the
+    rest of the near field as a multilevel FMM (n_t,near = 6).  Build,
+    product, plane-wave solve to 1e-8, device bytes, and the differences of
+    the FMPBEM2 product and solution from the FMM form's."""
+    w = WORKLOADS["sphere_array_5x10_fine"]
+    v, t = w.mesh()
+    k = w.wavenumbers[0]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": w.notes}
+    x = torch.as_tensor(random_complex_vectors(w.rhs_seed, 1, len(t) * int(np.prod(w.counts))), device="cuda")
+    res = {}
+    for name, form in (("fmm", gb.FORM_FMM), ("fmm2", gb.FORM_FMM2)):
+        torch.cuda.synchronize()
+        gb.profile_reset()
+        gb.profile_enable(True)
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        op = gb.Operator(v, t, w.counts, w.lattice, k, form=form, n_t=w.n_t, n_t_near=n_t_near)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        gb.profile_enable(False)
+        build_ms = b0.elapsed_time(b1)
+        bprof = gb.profile_summary()
+        y = op.matvec(x)
+        torch.cuda.synchronize()
+        gb.profile_reset()
+        gb.profile_enable(True)
+        m0, m1 = ev(), ev()
+        m0.record(stream)
+        for _ in range(5):
+            op.matvec(x, out=y)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        gb.profile_enable(False)
+        mprof = gb.profile_summary()
+        rhs = op.rhs_plane_wave(w.directions)
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        p, info = op.solve(rhs, tol=TOL, restart=SHORT_RESTART, maxit=MAXIT, raise_on_noconv=False)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = (y.clone(), p)
+        out[name] = {"build_ms": build_ms, "build_kernels_ms": {k_: v_[1] for k_, v_ in bprof.items()},
+                     "matvec_ms": m0.elapsed_time(m1) / 5,
+                     "matvec_kernels_ms": {k_: v_[1] / 5 for k_, v_ in mprof.items()},
+                     "solve_ms": s0.elapsed_time(s1), "iters": info[0]["iters"],
+                     "relres_true": info[0]["relres_true"], "converged": info[0]["converged"],
+                     "operator_bytes": op.info["bytes_device"], "near_levels": op.info["near_levels"],
+                     "n_m2l_near": op.info["n_m2l_near"], "n_p2p_near": op.info["n_p2p_near"]}
+        op.close()
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    out["fmm2_vs_fmm_product_rel_diff"] = rel(res["fmm2"][0], res["fmm"][0])
+    out["fmm2_vs_fmm_solution_rel_diff"] = rel(res["fmm2"][1], res["fmm"][1])
     return out
 
 

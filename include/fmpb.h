@@ -61,7 +61,9 @@ typedef enum {
   FMPB_ECUDA = -8      /* a CUDA runtime call failed */
 } fmpb_status;
 
-typedef enum { FMPB_FORM_AUTO = -1, FMPB_FORM_FMM = 0, FMPB_FORM_PBEM = 1 } fmpb_form;
+/* FMPB_FORM_FMM2: the FMM form with every unique near block approximated by
+ * a multilevel FMM over an octree of the unit cell (FMPBEM2, Sec. 3.3). */
+typedef enum { FMPB_FORM_AUTO = -1, FMPB_FORM_FMM = 0, FMPB_FORM_PBEM = 1, FMPB_FORM_FMM2 = 2 } fmpb_form;
 /* FP64: spectrum and tables as float-float pairs (FP64-class accuracy).
  * FP32: spectrum in complex FP32 (half the bytes per product).
  * BF16: FMM form only.  Near-field blocks and P2M/L2P tables rounded to
@@ -144,6 +146,15 @@ typedef struct {
   double plane_offset;
   double Rp_re;         /* reflection coefficient R_p (1: rigid plane, -1: soft) */
   double Rp_im;
+  /* FMPBEM2 form (FMPB_FORM_FMM2, FP64, full space): truncation number
+   * n_t,near of the multilevel near field (0: 6) and the depth of the cell's
+   * octree (0: the shallowest with at most 32 elements per leaf on average).
+   * The root is the cube on the centroids' bounding box; boxes of a level are
+   * well separated at centre distance >= 3 x their largest centre-to-vertex
+   * distance (Eq. (admissibility)); pairs that never are keep their exact
+   * entries (P2P). */
+  int32_t n_t_near;
+  int32_t near_levels;
 } fmpb_operator_opts;
 
 typedef struct {
@@ -165,6 +176,9 @@ typedef struct {
   int32_t hankel_axis;   /* lattice axis perpendicular to the plane, -1 if none */
   int32_t n_near_image;  /* image offsets evaluated exactly (FMM form), else 0 */
   int32_t image_separate;/* 1 if the image part has its own tables and products */
+  int32_t near_levels;   /* FMPBEM2: octree depth, else 0 */
+  int64_t n_m2l_near;    /* FMPBEM2: M2L pairs over all near offsets */
+  int64_t n_p2p_near;    /* FMPBEM2: exact entries kept */
 } fmpb_operator_info;
 
 /*

@@ -33,7 +33,8 @@ class OperatorOpts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("n_t", ctypes.c_int), ("precision", ctypes.c_int),
                 ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
                 ("halfspace", ctypes.c_int32), ("plane_axis", ctypes.c_int32), ("plane_offset", ctypes.c_double),
-                ("Rp_re", ctypes.c_double), ("Rp_im", ctypes.c_double)]
+                ("Rp_re", ctypes.c_double), ("Rp_im", ctypes.c_double),
+                ("n_t_near", ctypes.c_int32), ("near_levels", ctypes.c_int32)]
 
 
 class C64(ctypes.Structure):
@@ -51,7 +52,8 @@ class OperatorInfo(ctypes.Structure):
                 ("bytes_device", ctypes.c_size_t), ("precision", ctypes.c_int32),
                 ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
                 ("halfspace", ctypes.c_int32), ("hankel_axis", ctypes.c_int32), ("n_near_image", ctypes.c_int32),
-                ("image_separate", ctypes.c_int32)]
+                ("image_separate", ctypes.c_int32), ("near_levels", ctypes.c_int32),
+                ("n_m2l_near", ctypes.c_int64), ("n_p2p_near", ctypes.c_int64)]
 
 
 class SolveOpts(ctypes.Structure):

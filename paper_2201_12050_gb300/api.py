@@ -11,8 +11,8 @@ import torch
 from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, Incident, C64, SolveOpts, SolveInfo, FmpbError, ServerOpts,
                    Request, Result, ServerStats, STATUS)
 
-FORM_AUTO, FORM_FMM, FORM_PBEM = -1, 0, 1
-FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem"}
+FORM_AUTO, FORM_FMM, FORM_PBEM, FORM_FMM2 = -1, 0, 1, 2
+FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem", FORM_FMM2: "fmm2"}
 FP64, FP32, BF16, MIXED = 0, 1, 2, 3
 PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", BF16: "bf16", MIXED: "mixed"}
 
@@ -59,13 +59,14 @@ class Operator:
     (axis, offset, R_p) makes it a half-space operator (None: full space)."""
 
     def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64, beta=0.0,
-                 plane=None):
+                 plane=None, n_t_near=0, near_levels=0):
         self._lib = lib()
         v = _host(verts, np.float64)
         t = _host(tris, np.int32)
         self._lat = _lattice(counts, vectors)
         beta = complex(beta)
         opts = OperatorOpts(int(form), int(n_t), int(precision), beta.real, beta.imag)
+        opts.n_t_near, opts.near_levels = int(n_t_near), int(near_levels)
         if plane is not None:
             axis, offset, Rp = plane
             Rp = complex(Rp)

@@ -12,6 +12,7 @@
 #include "nearfield.cuh"
 #include "gmres.cuh"
 #include "tc_gemm.cuh"
+#include "fmm2.cuh"
 
 namespace fmpb {
 
@@ -105,7 +106,7 @@ fmpb_status decide_form(const CellGrid& g, double rho, int requested, int* form,
       }
   int f = requested;
   if (f == FMPB_FORM_AUTO) f = (dmin >= 3.0 * rho) ? FMPB_FORM_FMM : FMPB_FORM_PBEM;
-  if (f == FMPB_FORM_FMM && !(dmin > 2.0 * rho)) {
+  if ((f == FMPB_FORM_FMM || f == FMPB_FORM_FMM2) && !(dmin > 2.0 * rho)) {
     set_error("operator_create: FMM form not admissible (nearest far cell at %.4g, cell radius %.4g)", dmin, rho);
     return FMPB_EADMISS;
   }
@@ -199,6 +200,7 @@ struct fmpb_operator {
   int* near_offs_img = nullptr;
   int n_near_img = 0;
   cd* V0_img = nullptr;           // R_p x P2M table of the reflected cell (FMM)
+  Near2* near2 = nullptr;         // multilevel near field (FMPBEM2 form)
   size_t bytes = 0;
   // scratch, grown on demand (calls on one operator are stream-ordered)
   cd* scratch = nullptr;
@@ -225,6 +227,7 @@ struct fmpb_operator {
     cudaFree(S_img);
     cudaFree(near_offs_img);
     cudaFree(V0_img);
+    delete near2;
   }
 
   fmpb_status ensure_scratch(size_t elems) {
@@ -269,6 +272,20 @@ struct fmpb_operator {
     const size_t circ = circulant_scratch_elems(shape, B, R);
     const size_t mom = (size_t)R * Nc * B;
     const size_t nvec = (size_t)R * Nc * mesh.n;
+    if (near2) {
+      // FMPBEM2: the multilevel near field in FP64, then the cell-level far field
+      const size_t n2 = near2_scratch_elems(*near2, (int64_t)R * Nc);
+      FMPB_TRY(ensure_scratch(circ + 2 * mom + nvec + n2));
+      cd* Mom2 = scratch + circ;
+      cd* Loc2 = Mom2 + mom;
+      float4* xf2 = reinterpret_cast<float4*>(Loc2 + mom);
+      FMPB_TRY(near2_apply(*near2, shape.M, R, x, y, reinterpret_cast<cd*>(xf2 + nvec), st));
+      FMPB_TRY(vector_to_ff(x, xf2, nvec, st));
+      FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0), mesh.n, (int)B, (int64_t)R * Nc, xf2, Mom2, st));
+      FMPB_TRY(circulant_apply(shape, B, spec, R, Mom2, Loc2, false, scratch, st, SPEC_FF));
+      FMPB_TRY(l2p_apply(reinterpret_cast<const float4*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc2, y, st));
+      return FMPB_OK;
+    }
     FMPB_TRY(ensure_scratch(circ + 2 * mom + (img_sep ? 2 : 1) * nvec));
     cd* Mom = scratch + circ;
     cd* Loc = Mom + mom;
@@ -474,7 +491,11 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(out, "operator_create: out is NULL");
   CHECK_ARG(k > 0.0 && std::isfinite(k), "operator_create: wavenumber must be positive");
   fmpb_operator_opts o = opts ? *opts : fmpb_operator_opts{FMPB_FORM_AUTO, 0, FMPB_FP64};
-  CHECK_ARG(o.form >= -1 && o.form <= 1, "operator_create: bad form %d", o.form);
+  CHECK_ARG(o.form >= -1 && o.form <= 2, "operator_create: bad form %d", o.form);
+  CHECK_ARG(o.form != FMPB_FORM_FMM2 || (o.precision == FMPB_FP64 && !o.halfspace),
+            "operator_create: the FMPBEM2 form runs FMPB_FP64 in full space");
+  CHECK_ARG(o.n_t_near >= 0 && o.n_t_near <= MAX_NT && o.near_levels >= 0 && o.near_levels <= 10,
+            "operator_create: n_t_near must be 0..%d and near_levels 0..10", MAX_NT);
   CHECK_ARG(o.precision == FMPB_FP64 || o.precision == FMPB_FP32 || o.precision == FMPB_BF16 ||
                 o.precision == FMPB_MIXED,
             "operator_create: precision must be FMPB_FP64, FMPB_FP32, FMPB_BF16 or FMPB_MIXED");
@@ -581,7 +602,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
     op->nt = nt;
     op->B = (int64_t)(nt + 1) * (nt + 1);
     const int64_t B = op->B;
-    op->n_near = (int)(near_off.size() / 3);
+    op->n_near = form == FMPB_FORM_FMM2 ? 0 : (int)(near_off.size() / 3);
     s = dev_alloc(&op->S, (size_t)op->n_near * n * n, op->bytes);
     if (s == FMPB_OK) s = dev_alloc(&op->near_offs, near_off.size(), op->bytes);
     if (s == FMPB_OK) s = dev_alloc(&op->V0, (size_t)B * n, op->bytes);
@@ -594,7 +615,16 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
       return fail(cuda_status(cudaGetLastError(), "operator_create copies"));
     std::vector<int64_t> dnear(op->n_near);
     for (int i = 0; i < op->n_near; ++i) dnear[i] = i;
-    s = build_blocks(op->mesh, op->grid, k, beta, op->n_near, near_off.data(), dnear.data(), op->S, st);
+    if (form == FMPB_FORM_FMM2) {
+      // FMPBEM2 (Sec. 3.3): the near blocks as a multilevel FMM over the cell's octree
+      op->near2 = new (std::nothrow) Near2();
+      if (!op->near2) return fail(FMPB_ENOMEM);
+      s = near2_build(op->mesh, op->grid, verts, tris, k, beta, o.near_levels, o.n_t_near > 0 ? o.n_t_near : 6,
+                      near_off, *op->near2, st);
+      op->bytes += op->near2->bytes;
+    } else {
+      s = build_blocks(op->mesh, op->grid, k, beta, op->n_near, near_off.data(), dnear.data(), op->S, st);
+    }
     if (s == FMPB_OK) s = multipole_tables(op->mesh, k, beta, nt, op->V0, op->U0, st);
     // the products read the near blocks and the P2M/L2P tables as float-float
     // pairs, or as complex FP32 for FP32 operators (8 bytes per entry)
@@ -639,7 +669,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
         }
       }
     } else {
-      if (s == FMPB_OK) s = spectrum_to_ff(op->S, (size_t)op->n_near * n * n, st);
+      if (s == FMPB_OK && op->n_near > 0) s = spectrum_to_ff(op->S, (size_t)op->n_near * n * n, st);
       if (s == FMPB_OK) s = spectrum_to_ff(op->V0, (size_t)B * n, st);
       if (s == FMPB_OK) s = spectrum_to_ff(op->U0, (size_t)B * n, st);
     }
@@ -759,6 +789,9 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->hankel_axis = op->hankel;
   info->n_near_image = op->n_near_img;
   info->image_separate = op->img_sep ? 1 : 0;
+  info->near_levels = op->near2 ? op->near2->L : 0;
+  info->n_m2l_near = op->near2 ? op->near2->n_m2l : 0;
+  info->n_p2p_near = op->near2 ? op->near2->n_p2p : 0;
   return FMPB_OK;
 }
 

@@ -87,6 +87,14 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
                          const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
                          const ImageBlocks* img = nullptr);
 
+// Listed entries of n_off blocks (list: device, count indices
+// (o n + i) n + j, o indexing offsets), written to out[e]; self_slot (device,
+// n entries, -1 where absent): the position in out of entry (i, i) of the
+// zero offset, filled with the singular self term.
+fmpb_status build_entries(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                          const int32_t* offsets, const int64_t* list, int64_t count, const int64_t* self_slot,
+                          cd* out, cudaStream_t st);
+
 // One incident field on the device (kind 0: plane wave, v = direction;
 // kind 1: monopole, v = source position) and the symmetry plane of a
 // half-space operator (on = 0: full space).

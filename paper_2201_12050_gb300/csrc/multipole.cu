@@ -306,7 +306,7 @@ __device__ void wave_eval(int nt, const WaveSetup& w, int q, const double nrm[3]
 // V_0[q][j]: far rule (collapsed Gauss-Legendre 3x3, apex v0) on element j.
 // One CTA per element, one thread per coefficient.
 __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k, cd beta, QuadRules qr,
-                            cd* __restrict__ V0) {
+                            const double* __restrict__ centres, cd* __restrict__ V0) {
   __shared__ WaveSetup ws;
   const int j = blockIdx.x;
   const Elem& E = el[j];
@@ -322,7 +322,8 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
       if (threadIdx.x == 0) {
         double y[3];
         for (int d = 0; d < 3; ++d)
-          y[d] = E.v[0][d] + s * ((E.v[1][d] - E.v[0][d]) + qr.t3[b] * (E.v[2][d] - E.v[1][d]));
+          y[d] = E.v[0][d] + s * ((E.v[1][d] - E.v[0][d]) + qr.t3[b] * (E.v[2][d] - E.v[1][d])) -
+                 (centres ? centres[3 * j + d] : 0.0);
         wave_setup(nt, y, k, &ws);
       }
       __syncthreads();
@@ -340,12 +341,17 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
 }
 
 // U_0[i][q] at the collocation points; one CTA per element.
-__global__ void k_l2p_table(const Elem* __restrict__ el, int n, int nt, double k, cd* __restrict__ U0) {
+__global__ void k_l2p_table(const Elem* __restrict__ el, int n, int nt, double k, const double* __restrict__ centres,
+                            cd* __restrict__ U0) {
   __shared__ WaveSetup ws;
   const int i = blockIdx.x;
   const Elem& E = el[i];
   const int B = (nt + 1) * (nt + 1);
-  if (threadIdx.x == 0) wave_setup(nt, E.c, k, &ws);
+  if (threadIdx.x == 0) {
+    double x[3];
+    for (int d = 0; d < 3; ++d) x[d] = E.c[d] - (centres ? centres[3 * i + d] : 0.0);
+    wave_setup(nt, x, k, &ws);
+  }
   __syncthreads();
   const int q = threadIdx.x;
   if (q >= B) return;
@@ -361,9 +367,10 @@ __global__ void k_l2p_table(const Elem* __restrict__ el, int n, int nt, double k
 
 // O_l^mu(d) for l <= 2 nt into shared memory, then K(d)[q][q'] for every
 // pair.  One CTA per translation; block o is written at out + dest[o] B B
-// (dest < 0: skipped).
+// (dest < 0: skipped).  regular: the same table with I_l = j_l Y_l in place
+// of O_l = h_l Y_l (the coefficients of the regular addition theorem).
 __global__ void k_m2l_blocks(int nt, double k, const double* __restrict__ dvecs, const int64_t* __restrict__ dest,
-                             const double* __restrict__ W3, cd* __restrict__ out) {
+                             const double* __restrict__ W3, cd* __restrict__ out, int regular) {
   extern __shared__ double smem[];
   const int L = 2 * nt;
   cd* Osh = (cd*)smem;                               // (L+1)^2
@@ -389,7 +396,7 @@ __global__ void k_m2l_blocks(int nt, double k, const double* __restrict__ dvecs,
     q_to_nm(e, l, m);
     const cd ph = eimphi(m, ang[0], ang[1]);
     const double Y = ynorm(l, m) * Psh[l * (L + 1) + abs(m)];
-    Osh[e] = cmul(mkc(jb[l], yb[l]), cmulr(ph, Y));
+    Osh[e] = cmul(mkc(jb[l], regular ? 0.0 : yb[l]), cmulr(ph, Y));
   }
   __syncthreads();
   const int B = (nt + 1) * (nt + 1);
@@ -510,15 +517,16 @@ __global__ void k_l2p_apply_f32(const float2* __restrict__ U0, int n, int B, con
 }
 
 // ------------------------------------------------------------- host side --
-fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd* V0, cd* U0, cudaStream_t st) {
+fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd* V0, cd* U0, cudaStream_t st,
+                             const double* centres) {
   if (nt < 1 || nt > MAX_NT) {
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
-  if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, V0));
-  if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, U0));
+  if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));
+  if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, centres, U0));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -535,7 +543,7 @@ fmpb_status wigner_table(int nt, double** W3out, cudaStream_t st) {
 }
 
 fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, const int64_t* dest_host, cd* out,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool regular) {
   if (nt < 1 || nt > MAX_NT) {
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
@@ -550,7 +558,7 @@ fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, cons
   FMPB_CUDA(cudaMemcpyAsync(dd_, dvecs_host, sizeof(double) * 3 * n_d, cudaMemcpyHostToDevice, st));
   FMPB_CUDA(cudaMemcpyAsync(dst, dest_host, sizeof(int64_t) * n_d, cudaMemcpyHostToDevice, st));
   const size_t smem = 3 * sizeof(double) * (2 * nt + 1) * (2 * nt + 1);
-  FMPB_LAUNCH("m2l_blocks", st, k_m2l_blocks<<<n_d, 256, smem, st>>>(nt, k, dd_, dst, W3, out));
+  FMPB_LAUNCH("m2l_blocks", st, k_m2l_blocks<<<n_d, 256, smem, st>>>(nt, k, dd_, dst, W3, out, regular ? 1 : 0));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(dd_, st));
   FMPB_CUDA(cudaFreeAsync(dst, st));

@@ -565,6 +565,39 @@ __global__ void __launch_bounds__(256) k_near_entries(const Elem* __restrict__ t
   }
 }
 
+// Listed entries (o, i, j) of n_off blocks (idx = (o n + i) n + j), written
+// to out[e]: the exact entries a multilevel near field keeps (its P2P pairs).
+// Same classes and arithmetic as k_build_blocks; near and very-near entries
+// in FP64 in the thread itself.  The self entry of the zero offset is left
+// to k_self_terms.
+template <bool SK>
+__global__ void k_build_entries(const Elem* __restrict__ el, const FfElem* __restrict__ fel, int n,
+                                const double* __restrict__ shifts, const ff* __restrict__ shiftf, int zero_off,
+                                const int64_t* __restrict__ list, int64_t count, cd* __restrict__ out, double k,
+                                cd beta, QuadRules qr, FfConst C) {
+  const ff kf = ff_from_d(k);
+  const size_t nn = (size_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const size_t idx = (size_t)list[e];
+    const int o = (int)(idx / nn);
+    const size_t rem = idx - (size_t)o * nn;
+    const int i = (int)(rem / n);
+    const int j = (int)(rem - (size_t)i * n);
+    if (o == zero_off && i == j) continue;
+    const Elem& Ti = el[i];
+    double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
+    double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
+    const FfElem& Fi = fel[i];
+    const ff nxf[3] = {Fi.ny[0], Fi.ny[1], Fi.ny[2]};
+    const ff xf[3] = {Fi.c[0], Fi.c[1], Fi.c[2]};
+    double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
+    const ff shf[3] = {shiftf[3 * o], shiftf[3 * o + 1], shiftf[3 * o + 2]};
+    cd D, H, S, K;
+    element_dh_mixed<SK>(el[j], fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H, S, K);
+    out[e] = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
+  }
+}
+
 // sin x - x cos x without cancellation: series for |x| < 0.5.
 __device__ double sin_minus_xcos(double x) {
   if (fabs(x) < 0.5) {
@@ -591,7 +624,7 @@ __device__ double sin_minus_xcos(double x) {
 // (polar coordinates about x: an edge at distance h with end coordinates
 // t_a, t_b along it gives h ln((t_b + |b - x|)/(t_a + |a - x|))).
 __global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict__ block0, double k, cd beta,
-                             QuadRules qr) {
+                             QuadRules qr, const int64_t* __restrict__ slot) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Elem& E = el[i];
@@ -667,7 +700,11 @@ __global__ void k_self_terms(const Elem* __restrict__ el, int n, cd* __restrict_
     const cd S = mkc((invr + srem_re) * inv4pi, srem_im * inv4pi);
     t = cadd(t, cmul(beta, mkc(0.5 + k * S.y, -k * S.x)));
   }
-  block0[(size_t)i * n + i] = t;
+  if (slot) {
+    if (slot[i] >= 0) block0[slot[i]] = t;   // listed entries: the slot of (i, i)
+  } else {
+    block0[(size_t)i * n + i] = t;
+  }
 }
 
 // ------------------------------------------------------- right-hand side --
@@ -928,7 +965,7 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
     }
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
-                                                     k, beta, m.qr));
+                                                     k, beta, m.qr, nullptr));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -937,6 +974,42 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
   cudaFree(ddest);
   cudaFree(near_list);
   if (e != cudaSuccess) return cuda_status(e, "build_blocks");
+  return FMPB_OK;
+}
+
+fmpb_status build_entries(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                          const int32_t* offsets, const int64_t* list, int64_t count, const int64_t* self_slot,
+                          cd* out, cudaStream_t st) {
+  std::vector<double> shifts(3 * (size_t)n_off);
+  int zero_off = -1;
+  for (int o = 0; o < n_off; ++o) {
+    const int32_t* dl = offsets + 3 * o;
+    if (dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
+    for (int d = 0; d < 3; ++d) shifts[3 * o + d] = -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
+  }
+  std::vector<ff> shiftf(3 * (size_t)n_off);
+  for (size_t q = 0; q < shiftf.size(); ++q) {
+    const float hi = (float)shifts[q];
+    shiftf[q] = ff{hi, (float)(shifts[q] - (double)hi)};
+  }
+  double* dshift = nullptr;
+  ff* dshiftf = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&dshift, sizeof(double) * 3 * n_off, st));
+  FMPB_CUDA(cudaMallocAsync(&dshiftf, sizeof(ff) * 3 * n_off, st));
+  FMPB_CUDA(cudaMemcpyAsync(dshift, shifts.data(), sizeof(double) * 3 * n_off, cudaMemcpyHostToDevice, st));
+  FMPB_CUDA(cudaMemcpyAsync(dshiftf, shiftf.data(), sizeof(ff) * 3 * n_off, cudaMemcpyHostToDevice, st));
+  if (count > 0) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((count + 127) / 128, 152 * 64);
+    if (beta.x == 0.0 && beta.y == 0.0)
+      FMPB_LAUNCH("build_entries", st, k_build_entries<false><<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, zero_off, list, count, out, k, beta, m.qr, m.fc));
+    else
+      FMPB_LAUNCH("build_entries_adm", st, k_build_entries<true><<<blocks, 128, 0, st>>>(m.el, m.ffel, m.n, dshift, dshiftf, zero_off, list, count, out, k, beta, m.qr, m.fc));
+  }
+  if (zero_off >= 0 && self_slot)
+    FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out, k, beta, m.qr, self_slot));
+  FMPB_CUDA(cudaGetLastError());
+  FMPB_CUDA(cudaFreeAsync(dshift, st));
+  FMPB_CUDA(cudaFreeAsync(dshiftf, st));
   return FMPB_OK;
 }
 

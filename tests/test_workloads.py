@@ -40,7 +40,7 @@ def test_pcg32_reference_stream_and_vectors():
 def test_workload_sizes():
     sizes = {"sphere_row_4": 1280, "sonic_crystal_3x20": 72000,
              "sphere_array_32x32": 327680, "cube_lattice_16x16x4": 442368,
-             "barrier_cylinders_3x25x5": 126000}
+             "barrier_cylinders_3x25x5": 126000, "sphere_array_5x10_fine": 256000}
     for name, N in sizes.items():
         w = WORKLOADS[name]
         v, t = w.mesh()

@@ -100,6 +100,19 @@ WORKLOADS = {
         n_t=12,
         notes="16x16x4 rigid cubes edge 0.3 m in 0.5 m cells, 432 triangles per cell, N=442,368",
     ),
+    # large unit cells (the h-refinement study of the sphere array): 5 x 10
+    # spheres of 5,120 triangles each, for the multilevel near field (FMPBEM2)
+    "sphere_array_5x10_fine": Workload(
+        name="sphere_array_5x10_fine",
+        make_mesh=lambda: icosphere(4, 0.2),
+        counts=(5, 10, 1),
+        lattice=np.diag([0.6, 0.6, 1.0]),
+        wavenumbers=[4.0],
+        directions=np.array([[1.0, 0.0, 0.0]]),
+        rhs_seed=_SEED + 6,
+        n_t=8,
+        notes="5x10 rigid spheres r=0.2 m, lattice 0.6 m, 5,120 triangles per cell, N=256,000, k=4",
+    ),
     # the cylinder sound barrier of the paper's barrier study: 3 x 25 rigid
     # cylinders r = 0.1 m, 2 m high, on a sound-hard ground, as cells of
     # 0.4 m stacked 5 high (the z axis is perpendicular to the ground: block
