@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-case", default=None,
-                    choices=["product", "build", "near", "batch", "gmres", "barrier", "admittance"],
+                    choices=["product", "build", "near", "batch", "gmres", "barrier", "admittance", "fmm2"],
                     help="small case for kernel captures: product/build = 3x8 cylinders (1.8 GB spectrum) at "
                          "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, BF16; gmres = 320 "
                          "Arnoldi steps of the full crystal at 300 Hz")
@@ -988,7 +988,8 @@ def run_profile_case(args):
     and 4 products; near: the 32 x 32 sphere array (FMM form), one build and 3
     products; batch: 8 x 8 x 4 cubes, BF16 (tensor-core) FMM operator, 3 products
     of 64 right-hand sides; barrier: the half-space cylinder barrier (FMM form,
-    block Hankel image part), one build and 3 products; admittance: the 3 x 8
+    block Hankel image part), one build and 3 products; fmm2: the 5 x 10 fine
+    spheres in the FMPBEM2 form, one build and 3 products; admittance: the 3 x 8
     cylinders at 500 Hz with beta = 0.4 + 0.2i, one build.  Prints one JSON
     line."""
     import torch
@@ -1015,6 +1016,20 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "barrier", "N": op.N, "form": op.info["form_name"], "B": op.info["B"],
                           "F": op.info["F"], "n_near_image": op.info["n_near_image"],
+                          "y_norm": float(torch.linalg.vector_norm(y))}))
+        return
+    if args.profile_case == "fmm2":
+        w2 = WORKLOADS["sphere_array_5x10_fine"]
+        v2, t2 = w2.mesh()
+        op = gb.Operator(v2, t2, w2.counts, w2.lattice, w2.wavenumbers[0], form=gb.FORM_FMM2, n_t=w2.n_t,
+                         n_t_near=6)
+        x = torch.as_tensor(random_complex_vectors(w2.rhs_seed, 1, op.N), device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.matvec(x, out=y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "fmm2", "N": op.N, "near_levels": op.info["near_levels"],
+                          "n_m2l_near": op.info["n_m2l_near"], "n_p2p_near": op.info["n_p2p_near"],
                           "y_norm": float(torch.linalg.vector_norm(y))}))
         return
     if args.profile_case == "admittance":
