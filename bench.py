@@ -854,7 +854,7 @@ def precision_section(gb, torch, stream, w, v, t, k, op64, x, y64, p64, fp64_sol
 
 
 QUAD_POINTS = {0: 9, 1: 64, 2: 256}
-FLOPS_PER_POINT = 80      # FP64 operations of one kernel evaluation
+FLOPS_PER_POINT = 80      # FP64-equivalent operations of one kernel evaluation (D and H at one point)
 
 
 def quadrature_points(w, v, t):
