@@ -307,6 +307,18 @@ fmpb_status fmpb_field_incident(const fmpb_operator *op, int R, const fmpb_c64 *
  * ---------------------------------------------------------------------- */
 
 /*
+ * Host-side plan of the FMPBEM2 near field (FMPB_FORM_FMM2, Sec. 3.3), with
+ * no device work: the octree depth used (near_levels 0 = automatic), the M2L
+ * pairs over all near offsets of the lattice, the exact entries kept for
+ * the leaf pairs that are never well separated, and the distinct M2L
+ * translations.  n_t_near only validates (0 = 6).  Errors: EINVAL.
+ */
+fmpb_status fmpb_near2_plan_counts(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                                   const fmpb_lattice *lattice, int near_levels, int n_t_near,
+                                   int32_t *levels_out, int64_t *n_m2l, int64_t *n_p2p,
+                                   int64_t *n_translations);
+
+/*
  * Collocation blocks T_delta of Eq. (blockToeplizMatrix) (Sec. 2.2): entry
  * (i, j) couples collocation point i of the cell at the origin with
  * triangle j of the cell displaced by -delta . lattice vectors:

@@ -195,6 +195,19 @@ def _incidents(incidents):
     return arr
 
 
+def near2_plan_counts(verts, tris, counts, vectors, near_levels=0, n_t_near=0):
+    """fmpb_near2_plan_counts (host only): (levels, M2L pairs, exact entries, translations)."""
+    v = _host(verts, np.float64)
+    t = _host(tris, np.int32)
+    lat = _lattice(counts, vectors)
+    lv = ctypes.c_int32()
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().fmpb_near2_plan_counts(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), int(near_levels),
+                                       int(n_t_near), ctypes.byref(lv), ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(c)))
+    return lv.value, a.value, b.value, c.value
+
+
 def build_blocks_admittance(verts, tris, counts, vectors, k, beta, offsets):
     """fmpb_build_blocks_admittance: T_delta of a surface of admittance beta."""
     v = _host(verts, np.float64)

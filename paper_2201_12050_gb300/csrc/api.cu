@@ -884,6 +884,31 @@ fmpb_status fmpb_field_incident(const fmpb_operator* op, int R, const fmpb_c64* 
                         (const cd*)p, inc, npts, pts, (cd*)out, (cudaStream_t)stream);
 }
 
+fmpb_status fmpb_near2_plan_counts(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                   const fmpb_lattice* lattice, int near_levels, int n_t_near, int32_t* levels_out,
+                                   int64_t* n_m2l, int64_t* n_p2p, int64_t* n_translations) {
+  CHECK_ARG(verts && tris && nv >= 3 && ntri >= 1 && ntri <= (1 << 20), "near2_plan: bad mesh");
+  CHECK_ARG(levels_out && n_m2l && n_p2p && n_translations, "near2_plan: NULL output");
+  CHECK_ARG(near_levels >= 0 && near_levels <= 10, "near2_plan: near_levels must be 0..10");
+  for (int64_t e = 0; e < 3 * ntri; ++e)
+    CHECK_ARG(tris[e] >= 0 && tris[e] < nv, "near2_plan: triangle index out of range");
+  CellGrid g;
+  FMPB_TRY(make_grid(lattice, g));
+  std::vector<int32_t> near_off;
+  for (int dz = 1 - g.M[2]; dz < g.M[2]; ++dz)
+    for (int dy = 1 - g.M[1]; dy < g.M[1]; ++dy)
+      for (int dx = 1 - g.M[0]; dx < g.M[0]; ++dx)
+        if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) near_off.insert(near_off.end(), {dx, dy, dz});
+  Near2 t;
+  Near2Host h;
+  FMPB_TRY(near2_plan(verts, tris, (int)ntri, g, near_levels, n_t_near > 0 ? n_t_near : 6, near_off, t, h));
+  *levels_out = t.L;
+  *n_m2l = t.n_m2l;
+  *n_p2p = t.n_p2p;
+  *n_translations = t.n_k;
+  return FMPB_OK;
+}
+
 fmpb_status fmpb_build_blocks(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
                               const fmpb_lattice* lattice, double k, int n_off, const int32_t* offsets, fmpb_c64* out,
                               void* stream) {

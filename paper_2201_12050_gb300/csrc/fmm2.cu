@@ -224,10 +224,8 @@ static fmpb_status upload(T** dst, const std::vector<T>& h, size_t& bytes, cudaS
   return FMPB_OK;
 }
 
-fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* verts, const int32_t* tris, double k,
-                        cd beta, int levels, int nt_near, const std::vector<int32_t>& near_off, Near2& t,
-                        cudaStream_t st) {
-  const int n = m.n;
+fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const CellGrid& g, int levels, int nt_near,
+                       const std::vector<int32_t>& near_off, Near2& t, Near2Host& h) {
   if (nt_near < 1 || nt_near > MAX_NT) {
     set_error("FMPBEM2: n_t,near must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
@@ -279,7 +277,6 @@ fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* ve
   t.B = (nt_near + 1) * (nt_near + 1);
   t.n = n;
   t.n_off = (int)(near_off.size() / 3);
-  const int B = t.B;
   // boxes of every level, ordered by (z, y, x); radius rho_l
   std::vector<std::map<Key, int>> index(L + 1);
   std::vector<std::vector<Key>> keys(L + 1);
@@ -419,6 +416,42 @@ fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* ve
     pstart[i + 1] = (int64_t)plist.size();
   }
   t.n_p2p = (int64_t)plist.size();
+  h.parent = std::move(parent);
+  h.octant = std::move(octant);
+  h.cstart = std::move(cstart);
+  h.cidx = std::move(cidx);
+  h.lstart = std::move(lstart);
+  h.lelems = std::move(lelems);
+  h.elem_leaf = std::move(elem_leaf);
+  h.lcen = std::move(lcen);
+  h.mstart = std::move(mstart);
+  h.msrc = std::move(msrc);
+  h.moff = std::move(moff);
+  h.mk = std::move(mk);
+  h.dvecs = std::move(dvecs);
+  h.pstart = std::move(pstart);
+  h.plist = std::move(plist);
+  h.pj = std::move(pj);
+  h.poff = std::move(poff);
+  h.self_slot = std::move(self_slot);
+  h.e0 = e0;
+  return FMPB_OK;
+}
+
+fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* verts, const int32_t* tris, double k,
+                        cd beta, int levels, int nt_near, const std::vector<int32_t>& near_off, Near2& t,
+                        cudaStream_t st) {
+  const int n = m.n;
+  Near2Host h;
+  FMPB_TRY(near2_plan(verts, tris, n, g, levels, nt_near, near_off, t, h));
+  const int L = t.L, B = t.B;
+  const double e0 = h.e0;
+  const auto &parent = h.parent, &octant = h.octant, &cstart = h.cstart, &cidx = h.cidx, &lstart = h.lstart,
+             &lelems = h.lelems, &elem_leaf = h.elem_leaf, &mstart = h.mstart, &msrc = h.msrc, &moff = h.moff,
+             &mk = h.mk, &pj = h.pj, &poff = h.poff;
+  const auto& lcen = h.lcen;
+  const auto& dvecs = h.dvecs;
+  const auto &pstart = h.pstart, &plist = h.plist, &self_slot = h.self_slot;
   // device structure
   size_t& by = t.bytes;
   FMPB_TRY(upload(&t.parent, parent, by, st));

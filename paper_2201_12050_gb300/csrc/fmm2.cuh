@@ -41,6 +41,17 @@ struct Near2 {
   ~Near2();
 };
 
+// Host half of the build: the octree, the interaction lists and the exact
+// entries' indices (no CUDA call).  Fills the scalar fields and `base` of t.
+struct Near2Host {
+  std::vector<int> parent, octant, cstart, cidx, lstart, lelems, elem_leaf, mstart, msrc, moff, mk, pj, poff;
+  std::vector<double> lcen, dvecs;
+  std::vector<int64_t> pstart, plist, self_slot;
+  double e0 = 0.0;
+};
+fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const CellGrid& g, int levels, int nt_near,
+                       const std::vector<int32_t>& near_off, Near2& t, Near2Host& h);
+
 // Builds the tree, the interaction lists of every near offset and the device
 // tables (Sec. 3.3, Eqs. (m2m), (m2l), (l2l)).  verts/tris: the host mesh;
 // levels: octree depth L >= 0 (0 picks the depth giving about 32 elements
