@@ -307,6 +307,19 @@ fmpb_status fmpb_field_incident(const fmpb_operator *op, int R, const fmpb_c64 *
  * ---------------------------------------------------------------------- */
 
 /*
+ * Host-side plan of a half-space operator (no device work): the lattice axis
+ * perpendicular to the plane {x : x[plane_axis] = plane_offset} (-1 if
+ * none), the image offsets whose mirrored cell is within 2 r of the target
+ * cell (evaluated exactly in the FMM form, Eq. (admissibilityMirror)) and
+ * the smallest distance to a farther mirrored cell (1e300 if none).
+ * Errors: EINVAL (bad plane or a lattice axis neither parallel nor
+ * perpendicular to the plane), EMESH (cells on both sides of the plane).
+ */
+fmpb_status fmpb_halfspace_plan(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                                const fmpb_lattice *lattice, int plane_axis, double plane_offset,
+                                int32_t *hankel_axis, int32_t *n_near_image, double *dmin_far_image);
+
+/*
  * Host-side plan of the FMPBEM2 near field (FMPB_FORM_FMM2, Sec. 3.3), with
  * no device work: the octree depth used (near_levels 0 = automatic), the M2L
  * pairs over all near offsets of the lattice, the exact entries kept for

@@ -195,6 +195,17 @@ def _incidents(incidents):
     return arr
 
 
+def halfspace_plan(verts, tris, counts, vectors, plane_axis, plane_offset):
+    """fmpb_halfspace_plan (host only): (perpendicular axis, near image offsets, nearest far image)."""
+    v = _host(verts, np.float64)
+    t = _host(tris, np.int32)
+    lat = _lattice(counts, vectors)
+    h, nn, dmin = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    check(lib().fmpb_halfspace_plan(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), int(plane_axis),
+                                    float(plane_offset), ctypes.byref(h), ctypes.byref(nn), ctypes.byref(dmin)))
+    return h.value, nn.value, dmin.value
+
+
 def near2_plan_counts(verts, tris, counts, vectors, near_levels=0, n_t_near=0):
     """fmpb_near2_plan_counts (host only): (levels, M2L pairs, exact entries, translations)."""
     v = _host(verts, np.float64)

@@ -372,14 +372,13 @@ namespace fmpb {
 // checks that every cell lies on one side of the plane, and uploads the
 // reflected unit cell (R v, reversed winding, so that its element normals are
 // R n and the quadrature rules apply unchanged).
-static fmpb_status setup_halfspace(fmpb_operator* op, const fmpb_operator_opts& o, const double* verts, int64_t nv,
-                                   const int32_t* tris, int64_t ntri, cudaStream_t st) {
+static fmpb_status halfspace_check(const CellGrid& g, const fmpb_operator_opts& o, const double* verts, int64_t nv,
+                                   const int32_t* tris, int64_t ntri, int* hankel) {
   const int ax = o.plane_axis;
   if (ax < 0 || ax > 2 || !std::isfinite(o.plane_offset) || !std::isfinite(o.Rp_re) || !std::isfinite(o.Rp_im)) {
     set_error("operator_create: half-space needs plane_axis 0..2 and finite plane_offset, R_p");
     return FMPB_EINVAL;
   }
-  const CellGrid& g = op->grid;
   int h = -1;
   for (int a = 0; a < 3; ++a) {
     if (g.M[a] <= 1) continue;
@@ -421,6 +420,15 @@ static fmpb_status setup_halfspace(fmpb_operator* op, const fmpb_operator_opts& 
     set_error("operator_create: the cells do not lie on one side of the plane x[%d] = %.6g", ax, o.plane_offset);
     return FMPB_EMESH;
   }
+  *hankel = h;
+  return FMPB_OK;
+}
+
+static fmpb_status setup_halfspace(fmpb_operator* op, const fmpb_operator_opts& o, const double* verts, int64_t nv,
+                                   const int32_t* tris, int64_t ntri, cudaStream_t st) {
+  int h = -1;
+  FMPB_TRY(halfspace_check(op->grid, o, verts, nv, tris, ntri, &h));
+  const int ax = o.plane_axis;
   std::vector<double> rv(verts, verts + 3 * nv);
   for (int64_t v = 0; v < nv; ++v) rv[3 * v + ax] = -rv[3 * v + ax];
   std::vector<int32_t> rt(3 * ntri);
@@ -437,19 +445,22 @@ static fmpb_status setup_halfspace(fmpb_operator* op, const fmpb_operator_opts& 
 
 // shift(delta~) = -delta~ . L - (M_h - 1) L_h + 2 offset e: where the
 // reflected unit cell sits for the image block delta~ (x_c - y^_c = -shift).
-static std::vector<double> image_shifts(const fmpb_operator* op, const std::vector<int32_t>& offs) {
-  const CellGrid& g = op->grid;
+static std::vector<double> image_shifts(const CellGrid& g, int hankel, int axis, double offset,
+                                        const std::vector<int32_t>& offs) {
   const size_t n = offs.size() / 3;
   std::vector<double> sh(3 * n);
   for (size_t o = 0; o < n; ++o)
     for (int d = 0; d < 3; ++d) {
       double v = 0.0;
       for (int a = 0; a < 3; ++a) v -= offs[3 * o + a] * g.L[a][d];
-      if (op->hankel >= 0) v -= (g.M[op->hankel] - 1) * g.L[op->hankel][d];
-      if (d == op->plane.axis) v += 2.0 * op->plane.offset;
+      if (hankel >= 0) v -= (g.M[hankel] - 1) * g.L[hankel][d];
+      if (d == axis) v += 2.0 * offset;
       sh[3 * o + d] = v;
     }
   return sh;
+}
+static std::vector<double> image_shifts(const fmpb_operator* op, const std::vector<int32_t>& offs) {
+  return image_shifts(op->grid, op->hankel, op->plane.axis, op->plane.offset, offs);
 }
 
 // r of the mirrored admissibility criterion: the longest lattice vector
@@ -882,6 +893,43 @@ fmpb_status fmpb_field_incident(const fmpb_operator* op, int R, const fmpb_c64* 
   CHECK_ARG(R >= 1 && R <= 65535 && npts >= 1, "field: R or npts out of range");
   return field_incident(op->mesh, op->plane.on ? &op->refl : nullptr, op->grid, op->k, op->beta, op->plane, R,
                         (const cd*)p, inc, npts, pts, (cd*)out, (cudaStream_t)stream);
+}
+
+fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                const fmpb_lattice* lattice, int plane_axis, double plane_offset,
+                                int32_t* hankel_axis, int32_t* n_near_image, double* dmin_far_image) {
+  CHECK_ARG(verts && tris && nv >= 3 && ntri >= 1, "halfspace_plan: bad mesh");
+  CHECK_ARG(hankel_axis && n_near_image && dmin_far_image, "halfspace_plan: NULL output");
+  for (int64_t e = 0; e < 3 * ntri; ++e)
+    CHECK_ARG(tris[e] >= 0 && tris[e] < nv, "halfspace_plan: triangle index out of range");
+  CellGrid g;
+  FMPB_TRY(make_grid(lattice, g));
+  fmpb_operator_opts o{};
+  o.halfspace = 1;
+  o.plane_axis = plane_axis;
+  o.plane_offset = plane_offset;
+  o.Rp_re = 1.0;
+  int h = -1;
+  FMPB_TRY(halfspace_check(g, o, verts, nv, tris, ntri, &h));
+  std::vector<int32_t> offs;
+  for (int dz = 1 - g.M[2]; dz < g.M[2]; ++dz)
+    for (int dy = 1 - g.M[1]; dy < g.M[1]; ++dy)
+      for (int dx = 1 - g.M[0]; dx < g.M[0]; ++dx) offs.insert(offs.end(), {dx, dy, dz});
+  const std::vector<double> sh = image_shifts(g, h, plane_axis, plane_offset, offs);
+  const double r2 = 2.0 * image_r(g) * (1.0 - 1e-9);
+  int near = 0;
+  double dmin = 1e300;
+  for (size_t i = 0; i < offs.size() / 3; ++i) {
+    const double d = sqrt(sh[3 * i] * sh[3 * i] + sh[3 * i + 1] * sh[3 * i + 1] + sh[3 * i + 2] * sh[3 * i + 2]);
+    if (d < r2)
+      ++near;
+    else
+      dmin = fmin(dmin, d);
+  }
+  *hankel_axis = h;
+  *n_near_image = near;
+  *dmin_far_image = dmin;
+  return FMPB_OK;
 }
 
 fmpb_status fmpb_near2_plan_counts(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
