@@ -55,6 +55,8 @@ class Octree:
         lo, hi = cen.min(axis=0), cen.max(axis=0)
         self.c0 = 0.5 * (lo + hi)
         self.e0 = (hi - lo).max() * (1.0 + 1e-9)
+        if not self.e0 > 0.0:
+            self.e0 = 1.0          # all centroids at one point: one box at every level
         self.L = int(levels)
         self.corner = self.c0 - 0.5 * self.e0
         self.boxes = []          # per level: sorted list of occupied box keys (ix, iy, iz)

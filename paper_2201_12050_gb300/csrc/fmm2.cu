@@ -245,6 +245,7 @@ fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const Ce
     e0 = std::max(e0, hi[d] - lo[d]);
   }
   e0 *= 1.0 + 1e-9;
+  if (!(e0 > 0.0)) e0 = 1.0;   // all centroids at one point: a single box at every level
   for (int d = 0; d < 3; ++d) corner[d] = c0[d] - 0.5 * e0;
   using Key = std::tuple<int, int, int>;
   auto key_of = [&](int l, int j) {

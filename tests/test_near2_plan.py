@@ -50,6 +50,13 @@ def test_plan_counts_match_the_oracle_lists(mesh, counts, lattice, levels):
     assert (n_m2l, n_p2p, n_k) == _oracle_counts(v, t, counts, lattice, lv)
 
 
+def test_single_element_cell_is_one_box_per_level():
+    v = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0], [0.0, 0.1, 0.0]])
+    t = np.array([[0, 1, 2]], dtype=np.int32)
+    lv, n_m2l, n_p2p, n_k = gb.near2_plan_counts(v, t, (3, 1, 1), np.diag([0.5, 1.0, 1.0]), near_levels=2)
+    assert lv == 2 and (n_m2l, n_p2p, n_k) == _oracle_counts(v, t, (3, 1, 1), np.diag([0.5, 1.0, 1.0]), 2)
+
+
 def test_plan_rejects_bad_arguments():
     v, t = icosphere(0, 0.2)
     with pytest.raises(gb.FmpbError):
