@@ -279,8 +279,8 @@ struct fmpb_operator {
       cd* Mom2 = scratch + circ;
       cd* Loc2 = Mom2 + mom;
       float4* xf2 = reinterpret_cast<float4*>(Loc2 + mom);
-      FMPB_TRY(near2_apply(*near2, shape.M, R, x, y, reinterpret_cast<cd*>(xf2 + nvec), st));
       FMPB_TRY(vector_to_ff(x, xf2, nvec, st));
+      FMPB_TRY(near2_apply(*near2, shape.M, R, x, xf2, y, reinterpret_cast<cd*>(xf2 + nvec), st));
       FMPB_TRY(p2m_apply(reinterpret_cast<const float4*>(V0), mesh.n, (int)B, (int64_t)R * Nc, xf2, Mom2, st));
       FMPB_TRY(circulant_apply(shape, B, spec, R, Mom2, Loc2, false, scratch, st, SPEC_FF));
       FMPB_TRY(l2p_apply(reinterpret_cast<const float4*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc2, y, st));

@@ -154,12 +154,13 @@ __global__ void k_near2_l2l(const cd* __restrict__ T, const int* __restrict__ pa
   }
 }
 
-// y[col][i] = sum_q U[i][q] Loc[col][leaf(i)][q] + sum of the exact entries of row i
+// y[col][i] = sum_q U[i][q] Loc[col][leaf(i)][q] + sum of the exact entries of
+// row i; the exact entries and x as float-float pairs (FP32 pipe)
 __global__ void k_near2_l2p_p2p(const cd* __restrict__ U, const int* __restrict__ elem_leaf,
                                 const int64_t* __restrict__ p2p_start, const int* __restrict__ p2p_j,
-                                const int* __restrict__ p2p_off, const cd* __restrict__ p2p_val,
+                                const int* __restrict__ p2p_off, const float4* __restrict__ p2p_val,
                                 const int* __restrict__ offs, int n, int nbox, int B, int Mx, int My, int Mz,
-                                int64_t columns, const cd* __restrict__ Loc, const cd* __restrict__ x,
+                                int64_t columns, const cd* __restrict__ Loc, const float4* __restrict__ xff,
                                 cd* __restrict__ y) {
   const int64_t Nc = (int64_t)Mx * My * Mz;
   const int64_t total = columns * n;
@@ -173,14 +174,15 @@ __global__ void k_near2_l2p_p2p(const cd* __restrict__ U, const int* __restrict_
     const int64_t r = col / Nc;
     const int c = (int)(col - r * Nc);
     const int cx = c % Mx, cy = (c / Mx) % My, cz = c / (Mx * My);
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     for (int64_t p = p2p_start[i]; p < p2p_start[i + 1]; ++p) {
       const int* d = offs + 3 * p2p_off[p];
       const int sx = cx - d[0], sy = cy - d[1], sz = cz - d[2];
       if (sx < 0 || sx >= Mx || sy < 0 || sy >= My || sz < 0 || sz >= Mz) continue;
       const int64_t scol = r * Nc + ((int64_t)sz * My + sy) * Mx + sx;
-      acc = cfma(p2p_val[p], x[scol * n + p2p_j[p]], acc);
+      ff_cmac(p2p_val[p], xff[scol * n + p2p_j[p]], rh, rl, ih, il);
     }
-    y[e] = acc;
+    y[e] = cadd(acc, mkc((double)rh + (double)rl, (double)ih + (double)il));
   }
 }
 
@@ -190,7 +192,8 @@ static unsigned grid_of(int64_t total) {
 
 size_t near2_scratch_elems(const Near2& t, int64_t columns) { return 2 * (size_t)columns * t.nbox * t.B; }
 
-fmpb_status near2_apply(const Near2& t, const int M[3], int R, const cd* x, cd* y, cd* scratch, cudaStream_t st) {
+fmpb_status near2_apply(const Near2& t, const int M[3], int R, const cd* x, const float4* xff, cd* y, cd* scratch,
+                        cudaStream_t st) {
   const int64_t columns = (int64_t)R * M[0] * M[1] * M[2];
   const int B = t.B;
   cd* Mom = scratch;
@@ -209,7 +212,7 @@ fmpb_status near2_apply(const Near2& t, const int M[3], int R, const cd* x, cd* 
     const int nb = t.base[l + 2] - t.base[l + 1];
     FMPB_LAUNCH("near2_l2l", st, k_near2_l2l<<<grid_of(columns * nb * B), 256, 0, st>>>(t.Tl2l + (size_t)l * 8 * B * B, t.parent, t.octant, t.base[l + 1], nb, t.nbox, B, columns, Loc));
   }
-  FMPB_LAUNCH("near2_l2p_p2p", st, k_near2_l2p_p2p<<<grid_of(columns * t.n), 256, 0, st>>>(t.U, t.elem_leaf, t.p2p_start, t.p2p_j, t.p2p_off, t.p2p_val, t.offs, t.n, t.nbox, B, M[0], M[1], M[2], columns, Loc, x, y));
+  FMPB_LAUNCH("near2_l2p_p2p", st, k_near2_l2p_p2p<<<grid_of(columns * t.n), 256, 0, st>>>(t.U, t.elem_leaf, t.p2p_start, t.p2p_j, t.p2p_off, reinterpret_cast<const float4*>(t.p2p_val), t.offs, t.n, t.nbox, B, M[0], M[1], M[2], columns, Loc, xff, y));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -521,6 +524,7 @@ fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* ve
     FMPB_CUDA(cudaMemcpyAsync(dlist, plist.data(), sizeof(int64_t) * t.n_p2p, cudaMemcpyHostToDevice, st));
     FMPB_CUDA(cudaMemcpyAsync(dslot, self_slot.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
     FMPB_TRY(build_entries(m, g, k, beta, t.n_off, near_off.data(), dlist, t.n_p2p, dslot, t.p2p_val, st));
+    FMPB_TRY(spectrum_to_ff(t.p2p_val, (size_t)t.n_p2p, st));   // read as float-float pairs
     FMPB_CUDA(cudaFreeAsync(dlist, st));
     FMPB_CUDA(cudaFreeAsync(dslot, st));
   }

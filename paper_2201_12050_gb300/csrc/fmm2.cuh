@@ -34,7 +34,7 @@ struct Near2 {
   int64_t* p2p_start = nullptr;       // [n + 1] CSR by target element
   int* p2p_j = nullptr;               // source element
   int* p2p_off = nullptr;             // near offset index
-  cd* p2p_val = nullptr;              // exact entries
+  cd* p2p_val = nullptr;              // exact entries (float-float pairs)
   int64_t n_p2p = 0;
   int* offs = nullptr;                // n_off x 3 near offsets
   size_t bytes = 0;
@@ -61,8 +61,10 @@ fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* ve
                         cudaStream_t st);
 
 // y (=) sum_delta S~_delta x_{c - delta} for R right-hand sides (complex
-// double, cell-major); scratch: near2_scratch_elems complex values.
+// double, cell-major; xff: the same vector as float-float pairs); scratch:
+// near2_scratch_elems complex values.
 size_t near2_scratch_elems(const Near2& t, int64_t columns);
-fmpb_status near2_apply(const Near2& t, const int M[3], int R, const cd* x, cd* y, cd* scratch, cudaStream_t st);
+fmpb_status near2_apply(const Near2& t, const int M[3], int R, const cd* x, const float4* xff, cd* y, cd* scratch,
+                        cudaStream_t st);
 
 }  // namespace fmpb
