@@ -312,3 +312,26 @@ def fmm_image_matvec_explicit(cell: bem.CellMesh, lattice, counts, k, nt, plane:
                 Lc += Mom[:, cj] @ cache[key].T
         Y[:, ci] += Lc @ U0.T
     return Y.reshape(R, -1)
+
+
+# ----------------------------------------------------------- insertion loss --
+
+def insertion_loss_from_fields(p_inc, p_tot):
+    """Eq. (insertionloss): IL = 20 log10(sum_i |p_inc(x_i)| / sum_i |p(x_i)|)
+    over the observation points, p_inc and p the fields of all sources
+    together (arrays over the points)."""
+    return 20.0 * np.log10(np.sum(np.abs(p_inc)) / np.sum(np.abs(p_tot)))
+
+
+def insertion_loss(verts, tris, lattice, counts, k, P, points, incidents, plane: Plane = None, beta=0.0):
+    """IL of the solutions P (R x N, one row per incident field of
+    `incidents` = [(kind, vec, amp)]) at the observation points: the sources
+    act together, so the fields of the R right-hand sides are summed."""
+    pts = np.asarray(points, dtype=np.float64)
+    nz = np.zeros_like(pts) + np.array([0.0, 0.0, 1.0])
+    tot = np.zeros(len(pts), dtype=complex)
+    inc = np.zeros(len(pts), dtype=complex)
+    for r, (kind, vec, amp) in enumerate(incidents):
+        tot += field_points(verts, tris, lattice, counts, k, P[r], pts, kind, vec, amp, plane, beta)
+        inc += incident(pts, nz, k, kind, vec, amp, plane)[0]
+    return insertion_loss_from_fields(inc, tot)
