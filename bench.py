@@ -738,9 +738,10 @@ def halfspace_section(gb, torch, stream, freq_indices=(1, 3)):
     """The cylinder sound barrier of the paper's barrier study on a sound-hard
     ground (Sec. 2.3, Sec. 3.4): 3 x 25 x 5 cells, N = 126,000, the image part
     block Hankel along z, two monopoles.  FMM form (n_t = 10) at 200 Hz and at
-    the first Bragg frequency 428.75 Hz; PBEM form (two spectra, 8 GB) at
-    200 Hz, and the relative difference of the two solutions (the FMM
-    truncation error on this workload)."""
+    the first Bragg frequency 428.75 Hz, with the insertion loss over 3200
+    observation points; PBEM form (two spectra, 8 GB) at 200 Hz, and the
+    relative difference of the two solutions (the FMM truncation error on
+    this workload)."""
     w = WORKLOADS["barrier_cylinders_3x25x5"]
     v, t = w.mesh()
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -782,7 +783,19 @@ def halfspace_section(gb, torch, stream, freq_indices=(1, 3)):
         torch.cuda.synchronize()
         solve_ms = s0.elapsed_time(s1)
         sols[(form, fi)] = p
+        il = il_ms = None
+        if form == "fmm":
+            # Eq. (insertionloss) over 40 x 80 = 3200 points behind the barrier, 1 m above the ground
+            gx, gy = np.meshgrid(np.linspace(2.0, 6.0, 40), np.linspace(0.0, 9.6, 80), indexing="ij")
+            obs = np.column_stack([gx.ravel(), gy.ravel(), np.full(gx.size, 0.8)])
+            i0, i1 = ev(), ev()
+            i0.record(stream)
+            il = op.insertion_loss(p, inc, obs)
+            i1.record(stream)
+            torch.cuda.synchronize()
+            il_ms = i0.elapsed_time(i1)
         out[f"{form}_{w.wavenumbers[fi] * SPEED_OF_SOUND / (2 * np.pi):.2f}Hz"] = {
+            "insertion_loss_db": il, "insertion_loss_ms": il_ms,
             "k": k, "build_ms": build_ms, "build_kernels_ms": {k_: v_[1] for k_, v_ in bprof.items()},
             "matvec_ms": m0.elapsed_time(m1) / 10,
             "matvec_kernels_ms": {k_: v_[1] / 10 for k_, v_ in mprof.items()},

@@ -301,6 +301,16 @@ fmpb_status fmpb_field(const fmpb_operator *op, int R, const fmpb_c64 *p, const 
 fmpb_status fmpb_field_incident(const fmpb_operator *op, int R, const fmpb_c64 *p, const fmpb_incident *inc,
                                 int64_t npts, const double *pts, fmpb_c64 *out, void *stream);
 
+/*
+ * Insertion loss of Eq. (insertionloss) at npts observation points:
+ * IL = 20 log10(sum_i |p_inc(x_i)| / sum_i |p(x_i)|), the R incident fields
+ * (host array) and their solutions p (device, R x N) acting together; p_inc
+ * and p include the images of a half-space operator.   pts device, npts x 3;
+ * *il host, in dB.  Errors: EINVAL (sizes, or a total field that vanishes).
+ */
+fmpb_status fmpb_insertion_loss(const fmpb_operator *op, int R, const fmpb_c64 *p, const fmpb_incident *inc,
+                                int64_t npts, const double *pts, double *il, void *stream);
+
 /* ------------------------------------------------------------------------
  * Building blocks (the same kernels the operator uses), for callers that
  * assemble their own products and for table-level checks.

@@ -133,6 +133,20 @@ class Operator:
                                             _ptr(out), _stream()))
         return out
 
+    def insertion_loss(self, p, incidents, pts):
+        """fmpb_insertion_loss: Eq. (insertionloss) in dB for the solutions p of the incident fields."""
+        R = _cvec(p, self.N, "p")
+        inc = _incidents(incidents)
+        if len(inc) != R:
+            raise ValueError("one incident field per right-hand side")
+        if not (isinstance(pts, torch.Tensor) and pts.is_cuda and pts.dtype == torch.float64):
+            pts = torch.as_tensor(np.asarray(pts, dtype=np.float64), device="cuda")
+        pts = pts.contiguous()
+        il = ctypes.c_double()
+        check(self._lib.fmpb_insertion_loss(self._h, R, _ptr(p), ctypes.cast(inc, ctypes.c_void_p), pts.numel() // 3,
+                                            _ptr(pts), ctypes.byref(il), _stream()))
+        return il.value
+
     def matvec(self, x, out=None):
         R = _cvec(x, self.N, "x")
         y = out if out is not None else torch.empty_like(x)

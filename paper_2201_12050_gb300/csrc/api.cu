@@ -895,6 +895,14 @@ fmpb_status fmpb_field_incident(const fmpb_operator* op, int R, const fmpb_c64* 
                         (const cd*)p, inc, npts, pts, (cd*)out, (cudaStream_t)stream);
 }
 
+fmpb_status fmpb_insertion_loss(const fmpb_operator* op, int R, const fmpb_c64* p, const fmpb_incident* inc,
+                                int64_t npts, const double* pts, double* il, void* stream) {
+  CHECK_ARG(op && p && inc && pts && il, "insertion_loss: NULL argument");
+  CHECK_ARG(R >= 1 && R <= 65535 && npts >= 1, "insertion_loss: R or npts out of range");
+  return insertion_loss(op->mesh, op->plane.on ? &op->refl : nullptr, op->grid, op->k, op->beta, op->plane, R,
+                        (const cd*)p, inc, npts, pts, il, (cudaStream_t)stream);
+}
+
 fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
                                 const fmpb_lattice* lattice, int plane_axis, double plane_offset,
                                 int32_t* hankel_axis, int32_t* n_near_image, double* dmin_far_image) {

@@ -114,6 +114,10 @@ fmpb_status rhs_incident(const DeviceMesh& m, const CellGrid& g, double k, int R
 fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const CellGrid& g, double k, cd beta,
                            const PlaneDev& pl, int R, const cd* surf, const fmpb_incident* inc, int64_t npts,
                            const double* pts, cd* out, cudaStream_t st);
+// Eq. (insertionloss) over the points for the R solutions surf together.
+fmpb_status insertion_loss(const DeviceMesh& m, const DeviceMesh* refl, const CellGrid& g, double k, cd beta,
+                           const PlaneDev& pl, int R, const cd* surf, const fmpb_incident* inc, int64_t npts,
+                           const double* pts, double* il, cudaStream_t st);
 
 // P x: cells reversed along lattice axis h for every right-hand side (16- or
 // 8-byte elements, n per cell); a * s in place.

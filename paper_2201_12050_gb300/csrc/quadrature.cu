@@ -826,6 +826,55 @@ __global__ void k_field(const Elem* __restrict__ el, const Elem* __restrict__ re
   }
 }
 
+// ---------------------------------------------------------- insertion loss --
+// Incident field alone at the points (with its image for a half-space
+// operator), out[r][p].
+__global__ void k_incident_points(const IncDev* __restrict__ inc, PlaneDev pl, double k, int R, int64_t npts,
+                                  const double* __restrict__ pts, cd* __restrict__ out) {
+  const int64_t total = (int64_t)npts * R;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / npts);
+    const int64_t p = idx - (int64_t)r * npts;
+    const double x[3] = {pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]};
+    const double nx[3] = {0.0, 0.0, 1.0};
+    cd v, dv;
+    incident_at(inc[r], pl, x, nx, k, v, dv);
+    out[idx] = v;
+  }
+}
+
+// sums[0] = sum_p |sum_r inc[r][p]|, sums[1] = sum_p |sum_r tot[r][p]| in one
+// CTA (fixed order: deterministic).
+__global__ void k_il_sums(const cd* __restrict__ inc, const cd* __restrict__ tot, int R, int64_t npts,
+                          double* __restrict__ sums) {
+  __shared__ double a[256], b[256];
+  double sa = 0.0, sb = 0.0;
+  for (int64_t p = threadIdx.x; p < npts; p += blockDim.x) {
+    cd ci = mkc(0.0, 0.0), ct = mkc(0.0, 0.0);
+    for (int r = 0; r < R; ++r) {
+      ci = cadd(ci, inc[(int64_t)r * npts + p]);
+      ct = cadd(ct, tot[(int64_t)r * npts + p]);
+    }
+    sa += hypot(ci.x, ci.y);
+    sb += hypot(ct.x, ct.y);
+  }
+  a[threadIdx.x] = sa;
+  b[threadIdx.x] = sb;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      a[threadIdx.x] += a[threadIdx.x + s];
+      b[threadIdx.x] += b[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[0] = a[0];
+    sums[1] = b[0];
+  }
+}
+
 // ------------------------------------------------------------ host side --
 fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, DeviceMesh& m,
                         cudaStream_t st) {
@@ -1069,6 +1118,37 @@ fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const Ce
   FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, pl.on ? refl->el : m.el, m.n, g, k, beta, pl, R, dinc, surf, npts, pts, out, m.qr));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(dinc, st));
+  return FMPB_OK;
+}
+
+fmpb_status insertion_loss(const DeviceMesh& m, const DeviceMesh* refl, const CellGrid& g, double k, cd beta,
+                           const PlaneDev& pl, int R, const cd* surf, const fmpb_incident* inc, int64_t npts,
+                           const double* pts, double* il, cudaStream_t st) {
+  cd* tot = nullptr;
+  cd* incv = nullptr;
+  double* sums = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&tot, sizeof(cd) * (size_t)R * npts, st));
+  FMPB_CUDA(cudaMallocAsync(&incv, sizeof(cd) * (size_t)R * npts, st));
+  FMPB_CUDA(cudaMallocAsync(&sums, sizeof(double) * 2, st));
+  FMPB_TRY(field_incident(m, refl, g, k, beta, pl, R, surf, inc, npts, pts, tot, st));
+  IncDev* dinc = nullptr;
+  FMPB_TRY(upload_incident(R, inc, k, &dinc, st));
+  const int64_t total = (int64_t)npts * R;
+  FMPB_LAUNCH("incident_points", st, k_incident_points<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, st>>>(dinc, pl, k, R, npts, pts, incv));
+  FMPB_LAUNCH("il_sums", st, k_il_sums<<<1, 256, 0, st>>>(incv, tot, R, npts, sums));
+  FMPB_CUDA(cudaGetLastError());
+  double h[2] = {0.0, 0.0};
+  FMPB_CUDA(cudaMemcpyAsync(h, sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  FMPB_CUDA(cudaFreeAsync(dinc, st));
+  FMPB_CUDA(cudaFreeAsync(tot, st));
+  FMPB_CUDA(cudaFreeAsync(incv, st));
+  FMPB_CUDA(cudaFreeAsync(sums, st));
+  FMPB_CUDA(cudaStreamSynchronize(st));
+  if (!(h[1] > 0.0)) {
+    set_error("insertion_loss: the total field vanishes at every point");
+    return FMPB_EINVAL;
+  }
+  *il = 20.0 * log10(h[0] / h[1]);
   return FMPB_OK;
 }
 

@@ -232,3 +232,20 @@ def test_barrier_full_size_sampled_rows():
                 loc += K(("i", delta), -hs.image_shift(L, counts, pl, delta)) @ Momh[cj]
         ref = acc + U0[i] @ loc
         assert abs(y[c * n + i] - ref) <= 1e-11 * abs(ref), (c, i)
+
+
+def test_insertion_loss_matches_oracle():
+    counts, L, plane, h = CASES["perpendicular"]
+    v, t = icosphere(1, 0.2)
+    k = 2.5
+    op = gb.Operator(v, t, counts, L, k, form=gb.FORM_PBEM, plane=plane)
+    inc = [("monopole", [-2.0, 0.4, 0.5], 2.0), ("monopole", [-2.0, -0.6, 0.5], 1.0)]
+    b = op.rhs_incident(inc)
+    p, info = op.solve(b, tol=1e-10, restart=80)
+    rng = np.random.default_rng(8)
+    pts = np.column_stack([rng.uniform(1.0, 2.0, 40), rng.uniform(-0.5, 0.5, 40), rng.uniform(0.0, 1.0, 40)])
+    il = op.insertion_loss(p, inc, pts)
+    ref = hs.insertion_loss(v, t, L, counts, k, p.cpu().numpy(), pts, inc, hs.Plane(*plane))
+    assert abs(il - ref) < 1e-9
+    # no surface response: the total field is the incident field
+    assert abs(op.insertion_loss(torch.zeros_like(p), inc, pts)) < 1e-12
