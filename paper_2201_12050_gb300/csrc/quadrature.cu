@@ -785,44 +785,60 @@ __global__ void k_rhs_incident(const Elem* __restrict__ el, int n, CellGrid g, d
 // operator R_p times the same sum over the mirrored elements: refl holds the
 // reflected unit cell (R v, reversed winding), placed for cell c at
 // R pos_c + 2 offset e.
-__global__ void k_field(const Elem* __restrict__ el, const Elem* __restrict__ refl, int n, CellGrid g, double k,
-                        cd beta, PlaneDev pl, int R, const IncDev* __restrict__ inc, const cd* __restrict__ surf,
-                        int64_t npts, const double* __restrict__ pts, cd* __restrict__ out, QuadRules qr) {
+__global__ void __launch_bounds__(256) k_field(const Elem* __restrict__ el, const Elem* __restrict__ refl, int n,
+                                               CellGrid g, double k, cd beta, PlaneDev pl, int R,
+                                               const IncDev* __restrict__ inc, const cd* __restrict__ surf,
+                                               int64_t npts, const double* __restrict__ pts, cd* __restrict__ out,
+                                               QuadRules qr) {
+  // one CTA per (rhs, point): the threads split the elements of every cell
+  // (and their images) and the partial sums are reduced in a fixed order
+  __shared__ double sre[256], sim[256];
   const bool adm = beta.x != 0.0 || beta.y != 0.0;
   const cd ikb = mkc(-k * beta.y, k * beta.x);
-  const size_t total = (size_t)npts * R;
+  const int64_t total = (int64_t)npts * R;
   const size_t N = (size_t)n * g.ncells;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
+  const int64_t items = (int64_t)g.ncells * n;
+  for (int64_t idx = blockIdx.x; idx < total; idx += gridDim.x) {
     const int r = (int)(idx / npts);
-    const int64_t p = (int64_t)(idx - (size_t)r * npts);
+    const int64_t p = idx - (int64_t)r * npts;
     double x[3] = {pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]};
     double nx[3] = {0.0, 0.0, 1.0};
-    cd acc, dummy;
-    incident_at(inc[r], pl, x, nx, k, acc, dummy);
-    for (int side = 0; side < (pl.on ? 2 : 1); ++side) {
-      const Elem* els = side ? refl : el;
-      cd sum = mkc(0.0, 0.0);
-      for (int c = 0; c < g.ncells; ++c) {
-        double pos[3];
-        g.cell_position(c, pos);
-        if (side) {
-          pos[pl.axis] = 2.0 * pl.offset - pos[pl.axis];
+    cd part = mkc(0.0, 0.0);
+    for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+      const int c = (int)(it / n), j = (int)(it - (int64_t)c * n);
+      const cd pj = surf[(size_t)r * N + (size_t)c * n + j];
+      double pos[3];
+      g.cell_position(c, pos);
+      for (int side = 0; side < (pl.on ? 2 : 1); ++side) {
+        const Elem* els = side ? refl : el;
+        if (side) pos[pl.axis] = 2.0 * pl.offset - pos[pl.axis];
+        cd D, H, S, K;
+        if (adm) {
+          element_dhsk(els[j], pos, x, nx, k, qr, D, H, S, K);
+          D = cfma(ikb, S, D);
+        } else {
+          element_dh(els[j], pos, x, nx, k, qr, D, H);
         }
-        for (int j = 0; j < n; ++j) {
-          cd D, H, S, K;
-          if (adm) {
-            element_dhsk(els[j], pos, x, nx, k, qr, D, H, S, K);
-            D = cfma(ikb, S, D);
-          } else {
-            element_dh(els[j], pos, x, nx, k, qr, D, H);
-          }
-          sum = cfma(D, surf[(size_t)r * N + (size_t)c * n + j], sum);
-        }
+        const cd v = cmul(D, pj);
+        part = side ? cfma(pl.Rp, v, part) : cadd(part, v);
       }
-      acc = side ? cfma(pl.Rp, sum, acc) : cadd(acc, sum);
     }
-    out[idx] = acc;
+    sre[threadIdx.x] = part.x;
+    sim[threadIdx.x] = part.y;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+        sre[threadIdx.x] += sre[threadIdx.x + s];
+        sim[threadIdx.x] += sim[threadIdx.x + s];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      cd acc, dummy;
+      incident_at(inc[r], pl, x, nx, k, acc, dummy);
+      out[idx] = cadd(acc, mkc(sre[0], sim[0]));
+    }
+    __syncthreads();
   }
 }
 
@@ -1115,7 +1131,7 @@ fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const Ce
   IncDev* dinc = nullptr;
   FMPB_TRY(upload_incident(R, inc, k, &dinc, st));
   const size_t total = (size_t)npts * R;
-  FMPB_LAUNCH("field", st, k_field<<<std::min<size_t>(grid_for(total, 128), 152 * 16), 128, 0, st>>>(m.el, pl.on ? refl->el : m.el, m.n, g, k, beta, pl, R, dinc, surf, npts, pts, out, m.qr));
+  FMPB_LAUNCH("field", st, k_field<<<(unsigned)std::min<size_t>(total, 152 * 16), 256, 0, st>>>(m.el, pl.on ? refl->el : m.el, m.n, g, k, beta, pl, R, dinc, surf, npts, pts, out, m.qr));
   FMPB_CUDA(cudaGetLastError());
   FMPB_CUDA(cudaFreeAsync(dinc, st));
   return FMPB_OK;
