@@ -125,6 +125,51 @@ def open_cylinder(radius: float, height: float, n_around: int = 12, n_rows: int 
     return verts, tris.astype(np.int32)
 
 
+def quad9_sphere(m: int, radius: float):
+    """Sphere of 6 m^2 nine-node quadratic quadrilaterals: each face of the
+    cube [-1, 1]^3 split into m x m squares, the (2m + 1)^2 nodes of a face
+    projected radially onto the sphere (shared nodes merged).  Returns
+    (nodes, elements): elements (6 m^2 x 9) list their nodes in a 3 x 3 grid,
+    node (i, j) at 3 j + i with i along xi and j along eta, oriented so that
+    d y/d xi x d y/d eta points out of the sphere."""
+    index, nodes, elems = {}, [], []
+
+    def node(p):
+        q = np.asarray(p, dtype=np.float64)
+        q = q / np.linalg.norm(q) * radius
+        key = tuple(np.round(q / radius * 1e9).astype(np.int64))
+        if key not in index:
+            index[key] = len(nodes)
+            nodes.append(q)
+        return index[key]
+
+    g = np.linspace(-1.0, 1.0, 2 * m + 1)
+    for axis in range(3):
+        for sign in (-1.0, 1.0):
+            a1, a2 = [d for d in range(3) if d != axis]
+            for ey in range(m):
+                for ex in range(m):
+                    ids = []
+                    for j in range(3):
+                        for i in range(3):
+                            p = np.zeros(3)
+                            p[axis] = sign
+                            p[a1] = g[2 * ex + i]
+                            p[a2] = g[2 * ey + j]
+                            ids.append(node(p))
+                    elems.append(ids)
+    nodes = np.array(nodes)
+    elems = np.array(elems, dtype=np.int64)
+    # orientation from the corner diagonals (the centre normal of the map)
+    y = nodes[elems]
+    dxi = y[:, 5] - y[:, 3]
+    deta = y[:, 7] - y[:, 1]
+    flip = np.einsum("ij,ij->i", np.cross(dxi, deta), y[:, 4]) < 0
+    order = np.array([2, 1, 0, 5, 4, 3, 8, 7, 6])    # xi -> -xi
+    elems[flip] = elems[flip][:, order]
+    return nodes, elems.astype(np.int32)
+
+
 def cube(edge: float, n_per_edge: int = 6):
     """Axis-aligned cube centred on the origin, each face an
     ``n_per_edge`` x ``n_per_edge`` grid of squares split into two triangles
