@@ -82,6 +82,12 @@ typedef enum { FMPB_FP64 = 0, FMPB_FP32 = 1, FMPB_BF16 = 2, FMPB_MIXED = 3 } fmp
  * direction d) or a monopole amp e^{i k r}/r, r = |x - x_s| (vec = source
  * position x_s; amp is the pressure amplitude at 1 m; the source must not
  * lie on the surface). */
+/* Boundary elements (Sec. 2.1): flat three-node triangles, or the paper's
+ * nine-node quadratic quadrilaterals.  Both carry one constant pressure per
+ * element, collocated at the centroid (triangle) or at the parameter centre
+ * y(0, 0) (quadrilateral). */
+typedef enum { FMPB_ELEM_TRI3 = 0, FMPB_ELEM_QUAD9 = 1 } fmpb_element;
+
 typedef enum { FMPB_INC_PLANE = 0, FMPB_INC_MONOPOLE = 1 } fmpb_incident_kind;
 typedef struct {
   int32_t kind;      /* fmpb_incident_kind */
@@ -155,6 +161,13 @@ typedef struct {
    * entries (P2P). */
   int32_t n_t_near;
   int32_t near_levels;
+  /* fmpb_element of the mesh (0, zero-initialised: flat triangles).  With
+   * FMPB_ELEM_QUAD9 `tris` holds ntri x 9 node indices per element (node
+   * (i, j) of its 3 x 3 grid at 3 j + i, i along xi, parameter values -1, 0,
+   * 1; y_xi x y_eta into the fluid) and the operator is built in the PBEM
+   * form, full space, FP64, FP32 or MIXED; the field-point calls take
+   * triangles only. */
+  int32_t element;
 } fmpb_operator_opts;
 
 typedef struct {
@@ -179,6 +192,7 @@ typedef struct {
   int32_t near_levels;   /* FMPBEM2: octree depth, else 0 */
   int64_t n_m2l_near;    /* FMPBEM2: M2L pairs over all near offsets */
   int64_t n_p2p_near;    /* FMPBEM2: exact entries kept */
+  int32_t element;       /* fmpb_element of the mesh */
 } fmpb_operator_info;
 
 /*
@@ -186,7 +200,8 @@ typedef struct {
  *   verts  host, nv x 3 doubles: unit-cell vertex coordinates (metres).  The
  *          mesh origin is the cell's expansion centre.
  *   tris   host, ntri x 3 int32: vertex indices of each flat triangle, wound
- *          so that (v1-v0) x (v2-v0) points from the body into the fluid.
+ *          so that (v1-v0) x (v2-v0) points from the body into the fluid
+ *          (ntri x 9 node indices with opts->element = FMPB_ELEM_QUAD9).
  *   k      wavenumber omega/c > 0 (Eq. (helmholtz)).
  *   opts   may be NULL (AUTO form, n_t = 8, FP64).
  * Builds, all on the device: element geometry and quadrature rules; the
@@ -364,6 +379,28 @@ fmpb_status fmpb_build_blocks_admittance(const double *verts, int64_t nv, const 
                                          const fmpb_lattice *lattice, double k, double beta_re,
                                          double beta_im, int n_off, const int32_t *offsets,
                                          fmpb_c64 *out, void *stream);
+
+/*
+ * The blocks T_delta of fmpb_build_blocks_admittance on nine-node quadratic
+ * quadrilaterals (Sec. 2.1, Eq. (matrixBEM)) with one constant pressure per
+ * element collocated at its centre y(0, 0):
+ *   nodes   host, nn x 3 doubles.
+ *   elems   host, n x 9 int32 node indices (node (i, j) of the element's 3 x 3
+ *           grid at 3 j + i, i along xi, parameter values -1, 0, 1;
+ *           y_xi x y_eta points into the fluid).
+ *   out     device, n_off x n x n, row-major per block.
+ * Regular entries by class of d = |x_i - y_j(0, 0)| against the longest
+ * chord h_j between adjacent corners: d >= 4 h: 4 x 4 Gauss-Legendre;
+ * 1.5 h <= d < 4 h: 8 x 8; closer: 8 x 8 on each parameter quarter.  Self
+ * entries: polar coordinates about the centre (four triangles, 16 x 16
+ * Gauss-Legendre each); D, S, K directly and H as the Hadamard finite part
+ * from the Laurent expansion of the integrand in the polar radius.
+ * Errors: EINVAL (sizes, k <= 0, non-finite beta), EMESH (node index out of
+ * range, non-finite node, vanishing Jacobian), ENOMEM, ECUDA.
+ */
+fmpb_status fmpb_build_blocks_q9(const double *nodes, int64_t nn, const int32_t *elems, int64_t n,
+                                 const fmpb_lattice *lattice, double k, double beta_re, double beta_im,
+                                 int n_off, const int32_t *offsets, fmpb_c64 *out, void *stream);
 
 /*
  * P2M table V_0 (B x n, Eq. (p2m)) and L2P table U_0 (n x B, Eq. (l2p) and

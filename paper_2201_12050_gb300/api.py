@@ -14,6 +14,7 @@ from ._lib import (lib, check, Lattice, OperatorOpts, OperatorInfo, Incident, C6
 FORM_AUTO, FORM_FMM, FORM_PBEM, FORM_FMM2 = -1, 0, 1, 2
 FORM_NAMES = {FORM_FMM: "fmm", FORM_PBEM: "pbem", FORM_FMM2: "fmm2"}
 FP64, FP32, BF16, MIXED = 0, 1, 2, 3
+ELEM_TRI3, ELEM_QUAD9 = 0, 1
 PRECISION_NAMES = {FP64: "fp64", FP32: "fp32", BF16: "bf16", MIXED: "mixed"}
 
 
@@ -56,7 +57,8 @@ def _cvec(x, N, name):
 class Operator:
     """fmpb_operator: the tables of one (unit-cell mesh, lattice, k); beta is
     the surface's uniform normalised admittance (0: rigid); plane =
-    (axis, offset, R_p) makes it a half-space operator (None: full space)."""
+    (axis, offset, R_p) makes it a half-space operator (None: full space).
+    tris with nine columns are nine-node quadrilaterals (FMPB_ELEM_QUAD9)."""
 
     def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64, beta=0.0,
                  plane=None, n_t_near=0, near_levels=0):
@@ -67,6 +69,8 @@ class Operator:
         beta = complex(beta)
         opts = OperatorOpts(int(form), int(n_t), int(precision), beta.real, beta.imag)
         opts.n_t_near, opts.near_levels = int(n_t_near), int(near_levels)
+        if t.ndim == 2 and t.shape[1] == 9:
+            opts.element = ELEM_QUAD9
         if plane is not None:
             axis, offset, Rp = plane
             Rp = complex(Rp)
@@ -243,6 +247,19 @@ def build_blocks_admittance(verts, tris, counts, vectors, k, beta, offsets):
     out = torch.empty((len(off), len(t), len(t)), dtype=torch.complex128, device="cuda")
     check(lib().fmpb_build_blocks_admittance(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k),
                                              beta.real, beta.imag, len(off), _ptr(off), _ptr(out), _stream()))
+    return out
+
+
+def build_blocks_q9(nodes, elems, counts, vectors, k, offsets, beta=0.0):
+    """fmpb_build_blocks_q9: T_delta on nine-node quadrilaterals (elems n x 9)."""
+    v = _host(nodes, np.float64)
+    t = _host(elems, np.int32).reshape(-1, 9)
+    off = _host(offsets, np.int32).reshape(-1, 3)
+    lat = _lattice(counts, vectors)
+    beta = complex(beta)
+    out = torch.empty((len(off), len(t), len(t)), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_build_blocks_q9(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k), beta.real,
+                                     beta.imag, len(off), _ptr(off), _ptr(out), _stream()))
     return out
 
 

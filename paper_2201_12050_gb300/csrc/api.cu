@@ -513,6 +513,12 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   const int nt = o.n_t > 0 ? o.n_t : 8;
   CHECK_ARG(nt >= 1 && nt <= MAX_NT, "operator_create: n_t must be 1..%d", MAX_NT);
   CHECK_ARG(std::isfinite(o.beta_re) && std::isfinite(o.beta_im), "operator_create: admittance must be finite");
+  CHECK_ARG(o.element == FMPB_ELEM_TRI3 || o.element == FMPB_ELEM_QUAD9,
+            "operator_create: element must be FMPB_ELEM_TRI3 or FMPB_ELEM_QUAD9");
+  const bool quad9 = o.element == FMPB_ELEM_QUAD9;
+  CHECK_ARG(!quad9 || ((o.form == FMPB_FORM_AUTO || o.form == FMPB_FORM_PBEM) && !o.halfspace &&
+                       o.precision != FMPB_BF16),
+            "operator_create: nine-node quadrilaterals run the PBEM form in full space (FP64, FP32 or MIXED)");
   const cd beta = mkc(o.beta_re, o.beta_im);
   cudaStream_t st = (cudaStream_t)stream;
   fmpb_operator* op = new (std::nothrow) fmpb_operator();
@@ -529,7 +535,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   op->beta = beta;
   fmpb_status s = make_grid(lattice, op->grid);
   if (s != FMPB_OK) return fail(s);
-  s = upload_mesh(verts, nv, tris, ntri, op->mesh, st);
+  s = quad9 ? upload_mesh_q9(verts, nv, tris, ntri, op->mesh, st) : upload_mesh(verts, nv, tris, ntri, op->mesh, st);
   if (s != FMPB_OK) return fail(s);
   op->shape = make_shape(op->grid.M);
   const CircShape& sh = op->shape;
@@ -537,7 +543,7 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   const int n = op->mesh.n;
   std::vector<int32_t> all_off, far_off, near_off;
   int form = 0;
-  s = decide_form(op->grid, op->mesh.radius, o.form, &form, &all_off, &near_off, &far_off);
+  s = decide_form(op->grid, op->mesh.radius, quad9 ? FMPB_FORM_PBEM : o.form, &form, &all_off, &near_off, &far_off);
   if (s != FMPB_OK) return fail(s);
   if (form == FMPB_FORM_PBEM && o.precision == FMPB_BF16) {
     set_error("operator_create: BF16 runs the near-field, P2M and L2P products of the FMM form on the tensor cores; "
@@ -803,6 +809,7 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->near_levels = op->near2 ? op->near2->L : 0;
   info->n_m2l_near = op->near2 ? op->near2->n_m2l : 0;
   info->n_p2p_near = op->near2 ? op->near2->n_p2p : 0;
+  info->element = op->mesh.nodes == 9 ? FMPB_ELEM_QUAD9 : FMPB_ELEM_TRI3;
   return FMPB_OK;
 }
 
@@ -985,6 +992,26 @@ fmpb_status fmpb_build_blocks_admittance(const double* verts, int64_t nv, const 
   std::vector<int64_t> dest(n_off);
   for (int i = 0; i < n_off; ++i) dest[i] = i;
   fmpb_status s = build_blocks(m, g, k, mkc(beta_re, beta_im), n_off, offsets, dest.data(), (cd*)out, st);
+  free_mesh(m);
+  return s;
+}
+
+fmpb_status fmpb_build_blocks_q9(const double* nodes, int64_t nn, const int32_t* elems, int64_t n,
+                                 const fmpb_lattice* lattice, double k, double beta_re, double beta_im, int n_off,
+                                 const int32_t* offsets, fmpb_c64* out, void* stream) {
+  CHECK_ARG(offsets && out && n_off >= 1, "build_blocks_q9: bad offsets or output");
+  CHECK_ARG(k > 0.0 && std::isfinite(k), "build_blocks_q9: wavenumber must be positive");
+  CHECK_ARG(std::isfinite(beta_re) && std::isfinite(beta_im), "build_blocks_q9: admittance must be finite");
+  CellGrid g;
+  FMPB_TRY(make_grid(lattice, g));
+  DeviceMesh m;
+  cudaStream_t st = (cudaStream_t)stream;
+  fmpb_status s = upload_mesh_q9(nodes, nn, elems, n, m, st);
+  if (s == FMPB_OK) {
+    std::vector<int64_t> dest(n_off);
+    for (int i = 0; i < n_off; ++i) dest[i] = i;
+    s = build_blocks_q9(m, g, k, mkc(beta_re, beta_im), n_off, offsets, dest.data(), (cd*)out, st);
+  }
   free_mesh(m);
   return s;
 }

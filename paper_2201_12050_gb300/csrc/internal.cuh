@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "ff.cuh"
+#include "quad9.cuh"
 
 namespace fmpb {
 
@@ -25,6 +26,35 @@ struct FfConst {
   ff W[Q_FAR * Q_FAR];    // s_a w_a w_b of the collapsed far rule
   ff ccos[NTAY], csin[NTAY];
   ff inv4pi;
+};
+
+// Gauss-Legendre node i (ascending) and weight of order q on [0, 1]
+// (Newton's method on P_q).
+__host__ __device__ void gl_node(int q, int i, double* t, double* w);
+
+// T = -(D + (i/k) H)
+__host__ __device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
+  return mkc(-D.x + H.y / k, -D.y - H.x / k);
+}
+
+// T = -(D + b H) - i k beta (S + b K), b = i/k: the admittance condition
+// dp/dn_m = -i k beta p turns the dp/dn terms of the Burton-Miller equation
+// into -i k beta S + beta K.
+__host__ __device__ __forceinline__ cd bm_entry_adm(cd D, cd H, cd S, cd K, double k, cd beta) {
+  const cd t = mkc(K.x + k * S.y, K.y - k * S.x);   // K - i k S
+  return cadd(bm_entry(D, H, k), cmul(beta, t));
+}
+
+// How a block kernel stores an entry: out = v, or out (+)= scale v (image
+// blocks of a half-space operator: R_p times the entries, added to the
+// full-space blocks when both share one block Toeplitz pattern).
+struct BlockWrite {
+  cd scale;
+  int scaled, accumulate;
+  __device__ __forceinline__ void put(cd* dst, cd v) const {
+    if (scaled) v = cmul(scale, v);
+    *dst = accumulate ? cadd(*dst, v) : v;
+  }
 };
 
 // Finite cell grid (Sec. 2.2): counts M[a] along lattice vectors L[a].
@@ -65,11 +95,30 @@ struct DeviceMesh {
   FfConst* fc_dev = nullptr;
   FfConst fc;
   double radius = 0.0;   // max |vertex| about the origin (expansion centre)
+  // Nine-node quadrilaterals (nodes = 9; el then holds each element's centre,
+  // normal, chord and area for the collocation points): the elements and
+  // their class-rule points, the far rule point-major and field-major
+  // (q9_far[(p 7 + f) n + e], f: y, n_y, w|J|) for coalesced loads across
+  // source elements, the near and very-near rules element-major
+  // (q9_near[(e 320 + p) 8 + f]) for a warp sharing one element.
+  int nodes = 3;
+  Q9Elem* q9 = nullptr;
+  double* q9_far = nullptr;
+  double* q9_near = nullptr;
+  Q9Rules q9r;
 };
 
 fmpb_status upload_mesh(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, DeviceMesh& m,
                         cudaStream_t st);
 void free_mesh(DeviceMesh& m);
+// Nine-node quadrilateral mesh: nodes nn x 3, elems n x 9 node indices
+// (node (i, j) of the element's 3 x 3 grid at 3 j + i, i along xi,
+// y_xi x y_eta into the fluid).
+fmpb_status upload_mesh_q9(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, DeviceMesh& m,
+                           cudaStream_t st);
+// build_blocks for a nine-node mesh (full space only).
+fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                            const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);
 // Image blocks of a half-space operator (Sec. 2.3): per offset the shift of
 // the reflected unit cell (3 doubles, host), the factor R_p, and whether the
 // entries are added to out (the full-space blocks of the same pattern).

@@ -523,6 +523,10 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
+  if (m.nodes != 3) {
+    set_error("multipole_tables: the expansion tables take flat triangles");
+    return FMPB_EINVAL;
+  }
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
   if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));

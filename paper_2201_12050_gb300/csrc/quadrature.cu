@@ -67,7 +67,7 @@ __global__ void k_prepare_elements(const double* __restrict__ verts, const int32
 
 // Gauss-Legendre nodes/weights on [0,1] by Newton's method on P_q (three-term
 // recurrence), one thread per node.
-__device__ void gl_node(int q, int i, double* t, double* w) {
+__host__ __device__ void gl_node(int q, int i, double* t, double* w) {
   double x = cos(PI * (i + 0.75) / (q + 0.5));
   double p0 = 1.0, p1 = x, dp = 1.0;
   for (int it = 0; it < 100; ++it) {
@@ -399,31 +399,6 @@ __device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double sh
   else
     element_dh(E, shift, x, nx, k, qr, D, H);
 }
-
-// T = -(D + (i/k) H)
-__device__ __forceinline__ cd bm_entry(cd D, cd H, double k) {
-  return mkc(-D.x + H.y / k, -D.y - H.x / k);
-}
-
-// T = -(D + b H) - i k beta (S + b K), b = i/k: the admittance condition
-// dp/dn_m = -i k beta p turns the dp/dn terms of the Burton-Miller equation
-// into -i k beta S + beta K.
-__device__ __forceinline__ cd bm_entry_adm(cd D, cd H, cd S, cd K, double k, cd beta) {
-  const cd t = mkc(K.x + k * S.y, K.y - k * S.x);   // K - i k S
-  return cadd(bm_entry(D, H, k), cmul(beta, t));
-}
-
-// How a block kernel stores an entry: out = v, or out (+)= scale v (image
-// blocks of a half-space operator: R_p times the entries, added to the
-// full-space blocks when both share one block Toeplitz pattern).
-struct BlockWrite {
-  cd scale;
-  int scaled, accumulate;
-  __device__ __forceinline__ void put(cd* dst, cd v) const {
-    if (scaled) v = cmul(scale, v);
-    *dst = accumulate ? cadd(*dst, v) : v;
-  }
-};
 
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
 // out + dest[o] * n * n.  The diagonal of the zero offset is left to
@@ -967,15 +942,28 @@ void free_mesh(DeviceMesh& m) {
   if (m.qr_dev) cudaFree(m.qr_dev);
   if (m.ffel) cudaFree(m.ffel);
   if (m.fc_dev) cudaFree(m.fc_dev);
+  if (m.q9) cudaFree(m.q9);
+  if (m.q9_far) cudaFree(m.q9_far);
+  if (m.q9_near) cudaFree(m.q9_near);
   m.el = nullptr;
   m.qr_dev = nullptr;
   m.ffel = nullptr;
   m.fc_dev = nullptr;
+  m.q9 = nullptr;
+  m.q9_far = nullptr;
+  m.q9_near = nullptr;
 }
 
 fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                          const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
                          const ImageBlocks* img) {
+  if (m.nodes == 9) {
+    if (img) {
+      set_error("build_blocks: half-space image blocks take flat triangles");
+      return FMPB_EINVAL;
+    }
+    return build_blocks_q9(m, g, k, beta, n_off, offsets, dest_host, out, st);
+  }
   // shifts: -delta . lattice, or the image shifts given by the caller
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
@@ -1045,6 +1033,10 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
 fmpb_status build_entries(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                           const int32_t* offsets, const int64_t* list, int64_t count, const int64_t* self_slot,
                           cd* out, cudaStream_t st) {
+  if (m.nodes != 3) {
+    set_error("build_entries: listed entries take flat triangles");
+    return FMPB_EINVAL;
+  }
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
   for (int o = 0; o < n_off; ++o) {
@@ -1126,6 +1118,10 @@ fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const Ce
                            const double* pts, cd* out, cudaStream_t st) {
   if (pl.on && !refl) {
     set_error("field: half-space operator without its reflected cell");
+    return FMPB_EINVAL;
+  }
+  if (m.nodes != 3) {
+    set_error("field: field points take flat triangles");
     return FMPB_EINVAL;
   }
   IncDev* dinc = nullptr;

@@ -11,7 +11,7 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .meshes import icosphere, capped_cylinder, cube, open_cylinder
+from .meshes import icosphere, capped_cylinder, cube, open_cylinder, quad9_sphere
 
 SPEED_OF_SOUND = 343.0
 
@@ -112,6 +112,21 @@ WORKLOADS = {
         rhs_seed=_SEED + 6,
         n_t=8,
         notes="5x10 rigid spheres r=0.2 m, lattice 0.6 m, 5,120 triangles per cell, N=256,000, k=4",
+    ),
+    # the paper's first scattering example on its own element family: 5 x 5
+    # rigid spheres r = 0.1 m at 0.35 m, each of 600 nine-node quadratic
+    # quadrilaterals (40 over the circumference), N = 15,000, 500 Hz, plane
+    # wave along x
+    "sphere_array_5x5_q9": Workload(
+        name="sphere_array_5x5_q9",
+        make_mesh=lambda: quad9_sphere(10, 0.1),
+        counts=(5, 5, 1),
+        lattice=np.diag([0.35, 0.35, 1.0]),
+        wavenumbers=_freqs_to_k([100.0, 500.0]),
+        directions=np.array([[1.0, 0.0, 0.0]]),
+        rhs_seed=_SEED + 7,
+        pbem_form=True,
+        notes="5x5 rigid spheres r=0.1 m, lattice 0.35 m, 600 nine-node quadrilaterals per cell, N=15,000",
     ),
     # the cylinder sound barrier of the paper's barrier study: 3 x 25 rigid
     # cylinders r = 0.1 m, 2 m high, on a sound-hard ground, as cells of
