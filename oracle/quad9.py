@@ -41,7 +41,8 @@ Integrals of element j seen from (x, n_x), with the kernels of bem.py
 """
 import numpy as np
 
-from . import bem
+from . import bem, fmm
+from . import special as sp
 
 Q_FAR4 = 4
 Q_NEAR8 = 8
@@ -263,3 +264,31 @@ def toeplitz_block(cell: Q9Mesh, lattice, delta, k, beta=0.0):
     if selfp is not None:
         T += (0.5 + 0.5 * beta) * np.eye(cell.n)
     return T
+
+
+# ------------------------------------------------------------ FMM tables --
+
+def p2m_table(mesh: Q9Mesh, k, nt, beta=0.0):
+    """V_0 (B x n) of Eq. (p2m) on the curved elements: the far-class rule
+    (4 x 4 Gauss-Legendre) with the normal of each point, about the cell
+    origin.  With an admittance the single-layer source term adds
+    i k beta int conj(I_q) dA, as on flat triangles (fmm.p2m_table).  The
+    L2P table needs only the collocation points and their normals:
+    fmm.l2p_table(mesh, k, nt)."""
+    y, ny, w = _batch_rule(mesh.Y, "far")                # n x 16 x 3, n x 16 x 3, n x 16
+    g = sp.grad_regular_table(nt, y, k)                   # B x n x 16 x 3
+    dIdn = np.einsum("bnqi,nqi->bnq", g, ny)
+    V = np.sum(np.conj(dIdn) * w[None], axis=2)
+    if beta != 0:
+        I = sp.wave_table(nt, y.reshape(-1, 3), k, "I").reshape(-1, *w.shape)
+        V = V + 1j * k * beta * np.sum(np.conj(I) * w[None], axis=2)
+    return V
+
+
+def fmm_matvec_explicit(mesh: Q9Mesh, lattice, counts, k, nt, p, beta=0.0):
+    """The FMPBEM product (Eq. (2dPeriodicFMM)) on a Q9 cell, every cell
+    pair explicitly: near blocks (|delta|_inf <= 1) from toeplitz_block,
+    far pairs through U_0 K(delta) V_0."""
+    near = {d: toeplitz_block(mesh, lattice, d, k, beta) for d in bem.near_offsets(counts)}
+    return fmm.fmm_matvec_explicit(mesh, lattice, counts, k, nt, p, near_blocks=near,
+                                   V0=p2m_table(mesh, k, nt, beta), U0=fmm.l2p_table(mesh, k, nt), beta=beta)

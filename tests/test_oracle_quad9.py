@@ -133,3 +133,24 @@ def test_periodic_blocks_equal_the_dense_matrix_of_the_array():
             # the translated node coordinates differ by rounding, which the
             # finite part of the self term amplifies to about 1e-11
             assert np.abs(A[ci * n:(ci + 1) * n, cj * n:(cj + 1) * n] - T).max() <= 1e-10 * np.abs(T).max()
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.3 + 0.2j])
+def test_fmm_product_on_q9_cells_tends_to_the_exact_operator(beta):
+    # the far cells' blocks use the same 4 x 4 rule as the P2M table, so the
+    # FMPBEM product converges to the exact block Toeplitz product to
+    # rounding; the centre's normal in place of each point's stalls it at
+    # 6e-5, a missing conjugate or admittance term far higher
+    nodes, el = quad9_sphere(2, 0.2)
+    cell = quad9.Q9Mesh(nodes, el)
+    L, counts, k = np.eye(3), (4, 1, 1), 2.0
+    blocks = {d: quad9.toeplitz_block(cell, L, d, k, beta) for d in bem.all_offsets(counts)}
+    rng = np.random.default_rng(7)
+    p = rng.standard_normal(cell.n * 4) + 1j * rng.standard_normal(cell.n * 4)
+    y_exact = bem.toeplitz_matvec(blocks, counts, p)[0]
+    errs = []
+    for nt in (2, 4, 6, 8, 10, 12):
+        y = quad9.fmm_matvec_explicit(cell, L, counts, k, nt, p, beta)[0]
+        errs.append(np.linalg.norm(y - y_exact) / np.linalg.norm(y_exact))
+    assert all(b < 0.05 * a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-13, errs
