@@ -164,8 +164,10 @@ typedef struct {
   /* fmpb_element of the mesh (0, zero-initialised: flat triangles).  With
    * FMPB_ELEM_QUAD9 `tris` holds ntri x 9 node indices per element (node
    * (i, j) of its 3 x 3 grid at 3 j + i, i along xi, parameter values -1, 0,
-   * 1; y_xi x y_eta into the fluid) and the operator is built in the PBEM
-   * form, full space, FP64, FP32 or MIXED; the field-point calls take
+   * 1; y_xi x y_eta into the fluid).  Such operators run in full space, in
+   * the PBEM form (FP64, FP32 or MIXED; AUTO picks it) or the FMM form
+   * (FP64 or FP32; its P2M table integrates each element with the 4 x 4
+   * far-class rule and each point's normal); the field-point calls take
    * triangles only. */
   int32_t element;
 } fmpb_operator_opts;

@@ -516,9 +516,10 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(o.element == FMPB_ELEM_TRI3 || o.element == FMPB_ELEM_QUAD9,
             "operator_create: element must be FMPB_ELEM_TRI3 or FMPB_ELEM_QUAD9");
   const bool quad9 = o.element == FMPB_ELEM_QUAD9;
-  CHECK_ARG(!quad9 || ((o.form == FMPB_FORM_AUTO || o.form == FMPB_FORM_PBEM) && !o.halfspace &&
-                       o.precision != FMPB_BF16),
-            "operator_create: nine-node quadrilaterals run the PBEM form in full space (FP64, FP32 or MIXED)");
+  CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && !o.halfspace && o.precision != FMPB_BF16 &&
+                       !(o.form == FMPB_FORM_FMM && o.precision == FMPB_MIXED)),
+            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED) or the FMM form "
+            "(FP64 or FP32), in full space");
   const cd beta = mkc(o.beta_re, o.beta_im);
   cudaStream_t st = (cudaStream_t)stream;
   fmpb_operator* op = new (std::nothrow) fmpb_operator();
@@ -543,7 +544,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   const int n = op->mesh.n;
   std::vector<int32_t> all_off, far_off, near_off;
   int form = 0;
-  s = decide_form(op->grid, op->mesh.radius, quad9 ? FMPB_FORM_PBEM : o.form, &form, &all_off, &near_off, &far_off);
+  s = decide_form(op->grid, op->mesh.radius, quad9 && o.form == FMPB_FORM_AUTO ? FMPB_FORM_PBEM : o.form, &form,
+                  &all_off, &near_off, &far_off);
   if (s != FMPB_OK) return fail(s);
   if (form == FMPB_FORM_PBEM && o.precision == FMPB_BF16) {
     set_error("operator_create: BF16 runs the near-field, P2M and L2P products of the FMM form on the tensor cores; "

@@ -340,6 +340,37 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
   if (q < B) V0[(size_t)q * n + j] = acc;
 }
 
+// V_0[q][j] of a nine-node quadrilateral mesh: the far-class rule (4 x 4
+// points, each with its own normal and weight w|J|) from the point-major
+// table far_tab[(p 7 + f) n + j] (f: y, n_y, w|J|).  One CTA per element.
+__global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt, double k, cd beta,
+                               cd* __restrict__ V0) {
+  __shared__ WaveSetup ws;
+  const int j = blockIdx.x;
+  const int B = (nt + 1) * (nt + 1);
+  const int q = threadIdx.x;
+  const size_t sn = (size_t)n;
+  cd acc = mkc(0.0, 0.0);
+  const cd ikb = mkc(-k * beta.y, k * beta.x);   // i k beta
+  for (int p = 0; p < Q9_FAR; ++p) {
+    const double* t = far_tab + (size_t)p * 7 * sn + j;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double y[3] = {t[0], t[sn], t[2 * sn]};
+      wave_setup(nt, y, k, &ws);
+    }
+    __syncthreads();
+    if (q < B) {
+      const double ny[3] = {t[3 * sn], t[4 * sn], t[5 * sn]};
+      cd I, dI;
+      wave_eval(nt, ws, q, ny, k, &I, &dI);
+      const cd src = cadd(cconj(dI), cmul(ikb, cconj(I)));
+      acc = cadd(acc, cmulr(src, t[6 * sn]));
+    }
+  }
+  if (q < B) V0[(size_t)q * n + j] = acc;
+}
+
 // U_0[i][q] at the collocation points; one CTA per element.
 __global__ void k_l2p_table(const Elem* __restrict__ el, int n, int nt, double k, const double* __restrict__ centres,
                             cd* __restrict__ U0) {
@@ -523,13 +554,16 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
-  if (m.nodes != 3) {
-    set_error("multipole_tables: the expansion tables take flat triangles");
+  if (m.nodes == 9 && centres) {
+    set_error("multipole_tables: per-element expansion centres take flat triangles");
     return FMPB_EINVAL;
   }
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
-  if (V0) FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));
+  if (V0 && m.nodes == 9)
+    FMPB_LAUNCH("p2m_table_q9", st, k_p2m_table_q9<<<m.n, threads, 0, st>>>(m.q9_far, m.n, nt, k, beta, V0));
+  else if (V0)
+    FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));
   if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, centres, U0));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;

@@ -94,6 +94,35 @@ def test_q9_reduced_precision_products():
         assert float(torch.linalg.vector_norm(yp - y64) / torch.linalg.vector_norm(y64)) < 1e-5, prec
 
 
+@pytest.mark.parametrize("beta", [0.0, 0.3 + 0.2j])
+def test_q9_fmm_matvec_equals_explicit_oracle(beta):
+    # FMPBEM on the curved elements: near blocks from the Q9 quadrature, the
+    # P2M table over the 4 x 4 far rule with each point's normal
+    nodes, el = quad9_sphere(2, 0.2)
+    L, counts, k, nt = np.eye(3), (4, 1, 1), 2.0, 6
+    op = gb.Operator(nodes, el, counts, L, k, form=gb.FORM_FMM, n_t=nt, beta=beta)
+    assert op.info["form_name"] == "fmm" and op.info["element"] == gb.ELEM_QUAD9
+    x = random_complex_vectors(53, 2, op.N)
+    y = op.matvec(_dev(x)).cpu().numpy()
+    ref = quad9.fmm_matvec_explicit(quad9.Q9Mesh(nodes, el), L, counts, k, nt, x, beta)
+    assert _rel(y, ref) < 1e-10
+    op32 = gb.Operator(nodes, el, counts, L, k, form=gb.FORM_FMM, n_t=nt, beta=beta, precision=gb.FP32)
+    assert _rel(op32.matvec(_dev(x)).cpu().numpy(), y) < 1e-5
+
+
+def test_q9_fmm_solve_tends_to_the_pbem_solve():
+    nodes, el = quad9_sphere(2, 0.2)
+    L, counts, k = np.eye(3), (5, 2, 1), 2.0
+    sols = {}
+    for name, form, nt in (("pbem", gb.FORM_PBEM, 0), ("fmm", gb.FORM_FMM, 10)):
+        op = gb.Operator(nodes, el, counts, L, k, form=form, n_t=nt)
+        b = op.rhs_plane_wave([[1.0, 0.0, 0.0]])
+        p, info = op.solve(b, tol=1e-11)
+        assert info[0]["converged"]
+        sols[name] = p
+    assert float(torch.linalg.vector_norm(sols["fmm"] - sols["pbem"]) / torch.linalg.vector_norm(sols["pbem"])) < 1e-9
+
+
 def _series(ka, ct, nmax=40):
     return sum((2 * n + 1) * 1j ** n * (1j / ka ** 2) / sph_hn_deriv(n, ka) * eval_legendre(n, ct)
                for n in range(nmax))
@@ -118,7 +147,9 @@ def test_q9_argument_errors():
     nodes, el = quad9_sphere(1, 0.2)
     counts = (2, 1, 1)
     with pytest.raises(gb.FmpbError):
-        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM)
+        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM2)
+    with pytest.raises(gb.FmpbError):
+        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM, precision=gb.MIXED)
     with pytest.raises(gb.FmpbError):
         gb.Operator(nodes, el, counts, LATTICE, 2.0, plane=(2, -0.3, 1.0))
     with pytest.raises(gb.FmpbError):
