@@ -1,0 +1,276 @@
+"""Burton-Miller collocation on nine-node quadratic quadrilaterals with
+discontinuous pressure of order 0, 1 or 2 (the paper's discontinuous
+Lagrange pressure of variable order, Sec. 2.1 and Eq. (matrixBEM)).  Oracle
+code: test infrastructure only.
+
+Pressure on element f: p(y) = sum_b N_b(xi, eta) p_{f,b}, with nodes inside
+the element (discontinuous: no node on an edge), collocated at the nodes
+x_{f,a} = y_f(xi_a, eta_a) with the normal there:
+  * order 0: one node at (0, 0), N = 1 (quad9.py's element);
+  * order 1: 2 x 2 nodes at (+-s1, +-s1), s1 = 1/sqrt(3), bilinear Lagrange;
+  * order 2: the eight-node serendipity element on [-s2, s2]^2,
+    s2 = sqrt(3/5), nodes at the corners and side midpoints of that square.
+The dof counts of the paper's h-study (8 pressure dofs per quadratic
+element) fix the eight-node form of order 2; the node positions are not
+printed and are taken at the Gauss-Legendre points of the matching order.
+
+Entries (mesh normals into the fluid, b = i/k):
+  A[(e,a),(f,b)] = 1/2 (1 + beta) [(e,a) = (f,b)]
+                   - int_{E_f} N_b [dG/dn_y + b d2G/dn_x dn_y] dA
+                   - i k beta int_{E_f} N_b [G + b dG/dn_x] dA,
+x = x_{e,a}.  The 1/2 free term needs p smooth at x, which the
+discontinuous element gives.
+
+Rules.  Regular pairs by d = |x - y_f(0, 0)| against the longest corner
+chord h_f: far d >= 4 h: 4 x 4 Gauss-Legendre; near 1.5 h <= d < 4 h: 8 x 8;
+very near: 8 x 8 on each of 2 x 2 (order 0, quad9.py's rule), 4 x 4 (order
+1) or 8 x 8 (order 2) parameter sub-squares: the collocation points of the
+higher orders lie closer to the element edges (s2 puts them 0.11 h from the
+neighbour), and these subdivisions keep the closed-surface identities at
+about 1e-8 for every order.
+Self pairs (x on E_f): polar coordinates about (xi_a, eta_a), the square cut
+into four triangles with apex there, Q_SELF-point Gauss-Legendre in theta on
+each triangle's angle range and in rho on [0, rho_hat(theta)], Q_SELF = 16
+for order 0 (quad9.py's rule) and 24 for orders 1 and 2, whose off-centre
+apex leaves thin triangles towards the nearest side.  D, S, K
+directly; H as the Hadamard finite part with a spherical exclusion.  With
+F = H |J| rho = F_-2/rho^2 + F_-1/rho + O(1) (quad9.py, now at (xi_a, eta_a))
+and N_b = N_b0 + rho N_b1(theta) + O(rho^2) (N_b0 = N_b(xi_a, eta_a),
+N_b1 = grad N_b . (cos, sin)), the product G = F N_b has
+  G_-2 = F_-2 N_b0,   G_-1 = F_-1 N_b0 + F_-2 N_b1,
+and the finite part is
+  int_theta int_0^rho_hat (G - G_-2/rho^2 - G_-1/rho) drho dtheta
+  + int_theta [G_-1 ln(rho_hat beta) + G_-2 ((A.B)/beta^2 - 1/rho_hat)] dtheta;
+G_-1 is odd under theta -> theta + pi, so the ln(eps) part vanishes.  Away
+from the centre the (A.B) and ln terms do not cancel.
+"""
+import numpy as np
+
+from . import bem, quad9
+
+S1 = 1.0 / np.sqrt(3.0)
+S2 = np.sqrt(3.0 / 5.0)
+Q_SELF = (16, 24, 24)     # self-rule order by pressure order (16: quad9.py's rule)
+
+
+class PressureBasis:
+    """Discontinuous pressure shape functions of one order on [-1, 1]^2."""
+
+    def __init__(self, order: int):
+        if order not in (0, 1, 2):
+            raise ValueError("pressure order must be 0, 1 or 2")
+        self.order = order
+        if order == 0:
+            self.nodes = np.zeros((1, 2))
+        elif order == 1:
+            self.nodes = np.array([[-S1, -S1], [S1, -S1], [-S1, S1], [S1, S1]])
+        else:
+            u = np.array([[-1, -1], [0, -1], [1, -1], [1, 0], [1, 1], [0, 1], [-1, 1], [-1, 0]], dtype=float)
+            self.nodes = S2 * u
+        self.nb = len(self.nodes)
+
+    def eval(self, xi, eta):
+        """N (nb, ...) and grad N (nb, 2, ...) with respect to (xi, eta)."""
+        xi, eta = np.broadcast_arrays(np.asarray(xi, dtype=float), np.asarray(eta, dtype=float))
+        if self.order == 0:
+            N = np.ones((1,) + xi.shape)
+            return N, np.zeros((1, 2) + xi.shape)
+        if self.order == 1:
+            l = [(S1 - xi) / (2 * S1), (S1 + xi) / (2 * S1)]
+            m = [(S1 - eta) / (2 * S1), (S1 + eta) / (2 * S1)]
+            dl = [-np.ones_like(xi) / (2 * S1), np.ones_like(xi) / (2 * S1)]
+            dm = [-np.ones_like(eta) / (2 * S1), np.ones_like(eta) / (2 * S1)]
+            N, G = [], []
+            for j in range(2):
+                for i in range(2):
+                    N.append(l[i] * m[j])
+                    G.append(np.stack([dl[i] * m[j], l[i] * dm[j]]))
+            return np.stack(N), np.stack(G)
+        u, v = xi / S2, eta / S2
+        N, G = [], []
+        for ua, va in self.nodes / S2:
+            if ua != 0 and va != 0:
+                N.append(0.25 * (1 + u * ua) * (1 + v * va) * (u * ua + v * va - 1))
+                du = 0.25 * ua * (1 + v * va) * (2 * u * ua + v * va)
+                dv = 0.25 * va * (1 + u * ua) * (u * ua + 2 * v * va)
+            elif ua == 0:
+                N.append(0.5 * (1 - u * u) * (1 + v * va))
+                du = -u * (1 + v * va)
+                dv = 0.5 * va * (1 - u * u)
+            else:
+                N.append(0.5 * (1 + u * ua) * (1 - v * v))
+                du = 0.5 * ua * (1 - v * v)
+                dv = -v * (1 + u * ua)
+            G.append(np.stack([du / S2, dv / S2]))
+        return np.stack(N), np.stack(G)
+
+
+class OrderMesh:
+    """A Q9 mesh with a pressure basis: collocation points and normals of
+    every (element, node), dof index e * nb + a."""
+
+    def __init__(self, nodes, elems, order):
+        self.geo = quad9.Q9Mesh(nodes, elems)
+        self.basis = PressureBasis(order)
+        self.n = self.geo.n
+        self.nb = self.basis.nb
+        nd = self.basis.nodes
+        y, yx, ye = quad9._batch_geometry(self.geo.Y, nd[:, 0], nd[:, 1])
+        J = np.cross(yx, ye)
+        self.points = y.reshape(-1, 3)
+        self.normals = (J / np.linalg.norm(J, axis=-1, keepdims=True)).reshape(-1, 3)
+
+
+def _rule(cls, order):
+    if cls == 0:
+        return quad9.tensor_rule(quad9.Q_FAR4)
+    if cls == 1:
+        return quad9.tensor_rule(quad9.Q_NEAR8)
+    parts = (2, 4, 8)[order]
+    edges = np.linspace(-1.0, 1.0, parts + 1)
+    rules = [quad9.tensor_rule(quad9.Q_NEAR8, (edges[i], edges[i + 1], edges[j], edges[j + 1]))
+             for j in range(parts) for i in range(parts)]
+    return tuple(np.concatenate([r[q] for r in rules]) for q in range(3))
+
+
+def _polar_rule(xa, ea, q):
+    """theta nodes, weights, rho_hat(theta) of the four triangles about
+    (xa, ea), and the rho nodes/weights on [0, 1]."""
+    corners = [(1.0, -1.0), (1.0, 1.0), (-1.0, 1.0), (-1.0, -1.0)]
+    ang = [np.arctan2(cy - ea, cx - xa) for cx, cy in corners]
+    for i in range(1, 4):
+        while ang[i] <= ang[i - 1]:
+            ang[i] += 2 * np.pi
+    ang.append(ang[0] + 2 * np.pi)
+    ths, wts, rh = [], [], []
+    for side in range(4):
+        t, w = quad9._gauss(q, ang[side], ang[side + 1])
+        c, s = np.cos(t), np.sin(t)
+        rhat = [(1.0 - xa) / c, (1.0 - ea) / s, (-1.0 - xa) / c, (-1.0 - ea) / s][side]
+        ths.append(t)
+        wts.append(w)
+        rh.append(rhat)
+    u, wu = quad9._gauss(q, 0.0, 1.0)
+    return np.concatenate(ths), np.concatenate(wts), np.concatenate(rh), u, wu
+
+
+def self_integrals(Y, basis: PressureBasis, a, k, q=None):
+    """D, H (finite part), S, K (each nb values: one per source shape N_b)
+    of element Y at its own collocation node a; q: self-rule order (default
+    Q_SELF[order])."""
+    q = Q_SELF[basis.order] if q is None else q
+    xa, ea = basis.nodes[a]
+    th, wth, rhat, u, wu = _polar_rule(xa, ea, q)
+    c, s = np.cos(th), np.sin(th)
+    y0, yx, ye, yxx, yxe, yee = quad9.geometry(Y, xa, ea)
+    Jv = np.cross(yx, ye)
+    J0 = np.linalg.norm(Jv)
+    nx = Jv / J0
+    rho = rhat[:, None] * u[None, :]
+    xi, eta = xa + rho * c[:, None], ea + rho * s[:, None]
+    y, yxi, yeta = quad9.geometry(Y, xi, eta)[:3]
+    J = np.cross(yxi, yeta)
+    dJ = np.linalg.norm(J, axis=-1)
+    ny = J / dJ[..., None]
+    x = np.broadcast_to(y0, y.shape)
+    nxb = np.broadcast_to(nx, y.shape)
+    N, _ = basis.eval(xi, eta)                                     # nb x T x U
+    N0, G0 = basis.eval(np.array(xa), np.array(ea))                # nb, nb x 2
+    wgt = (wth[:, None] * wu[None, :] * rhat[:, None]) * rho * dJ
+    kd = bem.kernel_dlp(x, nxb, y, ny, k)
+    ks = bem.kernel_slp(x, y, k)
+    kk = bem.kernel_adlp(x, nxb, y, k)
+    D = np.einsum("btu,tu->b", N, wgt * kd)
+    S = np.einsum("btu,tu->b", N, wgt * ks)
+    K = np.einsum("btu,tu->b", N, wgt * kk)
+    A = yx[None, :] * c[:, None] + ye[None, :] * s[:, None]
+    Bv = 0.5 * (yxx[None, :] * (c * c)[:, None] + 2 * yxe[None, :] * (c * s)[:, None] + yee[None, :] * (s * s)[:, None])
+    beta = np.linalg.norm(A, axis=1)
+    AB = np.einsum("ti,ti->t", A, Bv)
+    Jx = np.cross(yxx, ye) + np.cross(yx, yxe)
+    Je = np.cross(yxe, ye) + np.cross(yx, yee)
+    J1 = (Jv[None, :] * (Jx[None, :] * c[:, None] + Je[None, :] * s[:, None])).sum(axis=1) / J0
+    Fm2 = J0 / (4 * np.pi * beta ** 3)
+    Fm1 = (J1 - 3 * J0 * AB / beta ** 2) / (4 * np.pi * beta ** 3)
+    Nb0 = N0.reshape(-1)                                           # nb
+    Nb1 = G0[:, 0].reshape(-1, 1) * c[None, :] + G0[:, 1].reshape(-1, 1) * s[None, :]   # nb x T
+    Gm2 = Fm2[None, :] * Nb0[:, None]
+    Gm1 = Fm1[None, :] * Nb0[:, None] + Fm2[None, :] * Nb1
+    F = bem.kernel_hyp(x, nxb, y, ny, k) * dJ * rho                # T x U
+    G = N * F[None]
+    inner = np.sum(wu[None, None, :] * rhat[None, :, None]
+                   * (G - Gm2[:, :, None] / rho[None] ** 2 - Gm1[:, :, None] / rho[None]), axis=2)
+    H = np.sum(wth[None, :] * (inner + Gm1 * np.log(rhat * beta)[None, :]
+                               + Gm2 * (AB / beta ** 2 - 1 / rhat)[None, :]), axis=1)
+    return D, H, S, K
+
+
+def dhsk_block(tgt: OrderMesh, src_Y, k, self_same=False, chunk=2000):
+    """D, H, S, K ((n nb) x (n_s nb)) of tgt's collocation points against
+    the elements src_Y (placed); self_same: src_Y is tgt's own cell at its
+    own place, so that a point's own element takes the self rule."""
+    nb = tgt.nb
+    basis = tgt.basis
+    ns = len(src_Y)
+    ycen = src_Y[:, 4]
+    c = src_Y[:, [0, 2, 8, 6]]
+    hmax = np.max(np.linalg.norm(c - np.roll(c, 1, axis=1), axis=2), axis=1)
+    X, NX = tgt.points, tgt.normals
+    cls = bem.classify(X[:, None, :], ycen[None], hmax[None])     # (n nb) x ns
+    if self_same:
+        for e in range(tgt.n):
+            cls[e * nb:(e + 1) * nb, e] = 3
+    out = [np.zeros((len(X), ns * nb), dtype=complex) for _ in range(4)]
+    for cc in (0, 1, 2):
+        xi, eta, w = _rule(cc, basis.order)
+        N, _ = basis.eval(xi, eta)                                # nb x P
+        Nq, Nx, Ne = quad9.shape(xi, eta)[:3]
+        ii, jj = np.nonzero(cls == cc)
+        for s0 in range(0, len(ii), chunk):
+            i, j = ii[s0:s0 + chunk], jj[s0:s0 + chunk]
+            Yb = src_Y[j]
+            y = np.einsum("ap,qad->qpd", Nq, Yb)
+            yx = np.einsum("ap,qad->qpd", Nx, Yb)
+            ye = np.einsum("ap,qad->qpd", Ne, Yb)
+            J = np.cross(yx, ye)
+            dJ = np.linalg.norm(J, axis=-1)
+            ny = J / dJ[..., None]
+            wq = w[None, :] * dJ
+            x = X[i][:, None, :]
+            nx = NX[i][:, None, :]
+            vals = (wq * bem.kernel_dlp(x, nx, y, ny, k), wq * bem.kernel_hyp(x, nx, y, ny, k),
+                    wq * bem.kernel_slp(x, y, k), wq * bem.kernel_adlp(x, nx, y, k))
+            for o, v in zip(out, vals):
+                ent = v @ N.T                                      # pairs x nb
+                for b in range(nb):
+                    o[i, j * nb + b] = ent[:, b]
+    for r, f in zip(*np.nonzero(cls == 3)):
+        a = r - f * nb
+        for o, v in zip(out, self_integrals(src_Y[f], basis, a, k)):
+            o[r, f * nb:(f + 1) * nb] = v
+    return out
+
+
+def dense_matrix(nodes, elems, order, k, beta=0.0):
+    """Collocation matrix of Eq. (bm) on one mesh (dof e nb + a)."""
+    m = OrderMesh(nodes, elems, order)
+    D, H, S, K = dhsk_block(m, m.geo.Y, k, self_same=True)
+    return (0.5 + 0.5 * beta) * np.eye(m.n * m.nb) + bem._entries(D, H, S, K, k, beta)
+
+
+def plane_wave_rhs(mesh: OrderMesh, k, direction, amp=1.0):
+    d = np.asarray(direction, dtype=np.float64)
+    pinc = amp * np.exp(1j * k * (mesh.points @ d))
+    return pinc + bem.coupling(k) * 1j * k * (mesh.normals @ d) * pinc
+
+
+def toeplitz_block(cell: OrderMesh, lattice, delta, k, beta=0.0):
+    """T_delta (Eq. (blockToeplizMatrix)): the cell's collocation points
+    against its elements displaced by -delta . lattice."""
+    shift = -np.asarray(delta, dtype=np.float64) @ np.asarray(lattice, dtype=np.float64)
+    same = not np.any(delta)
+    D, H, S, K = dhsk_block(cell, cell.geo.Y + shift[None, None, :], k, self_same=same)
+    T = bem._entries(D, H, S, K, k, beta)
+    if same:
+        T += (0.5 + 0.5 * beta) * np.eye(cell.n * cell.nb)
+    return T

@@ -1,0 +1,191 @@
+"""Pins of the oracle's nine-node quadrilaterals with discontinuous pressure of
+order 0, 1 and 2 (the paper's variable-order pressure):
+
+* shape functions: nodal interpolation, partition of unity, reproduction of
+  the bilinear (order 1) and eight-node serendipity (order 2) polynomial
+  spaces, gradients against central differences;
+* order 0 is the constant element of quad9.py, entry for entry;
+* the closed-surface flux and hypersingular row sums (the constant density);
+* on a flat element with a non-affine map, the finite part of each shape
+  function at each off-centre node equals an independent decomposition:
+  N_b(x) times the polygon closed form, grad N_b(x) . (the principal value
+  of (y - x)/r^3, an edge sum of int ds/r), and the bounded remainder by a
+  96-point collapsed rule in physical space;
+* Green's identities for a linear harmonic field on a closed Q9 sphere
+  (non-constant densities on curved elements): the representation error of
+  order 1 and the hypersingular error of order 2 fall with refinement at
+  their orders; dropping the gradient term of the Laurent coefficient leaves
+  the row sums intact but stalls the hypersingular identity near 0.3;
+* the analytic rigid sphere, where order 2 is more accurate per unknown;
+* the periodic blocks equal the dense matrix of the whole array.
+"""
+import numpy as np
+import pytest
+from scipy.special import eval_legendre
+
+from oracle import bem, quad9, quad9_order as qo
+from oracle.special import sph_hn_deriv
+from workloads import quad9_sphere
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_pressure_basis(order):
+    b = qo.PressureBasis(order)
+    assert b.nb == (1, 4, 8)[order]
+    N, _ = b.eval(b.nodes[:, 0], b.nodes[:, 1])
+    assert np.allclose(N, np.eye(b.nb), atol=1e-14)
+    rng = np.random.default_rng(3)
+    xi, eta = rng.uniform(-1, 1, 9), rng.uniform(-1, 1, 9)
+    N, G = b.eval(xi, eta)
+    assert np.allclose(N.sum(axis=0), 1.0, atol=1e-14)
+    # reproduction of the element's polynomial space from nodal values
+    space = {0: [lambda x, y: 1 + 0 * x],
+             1: [lambda x, y: 1 + 0 * x, lambda x, y: x, lambda x, y: y, lambda x, y: x * y],
+             2: [lambda x, y: 1 + 0 * x, lambda x, y: x, lambda x, y: y, lambda x, y: x * x, lambda x, y: x * y,
+                 lambda x, y: y * y, lambda x, y: x * x * y, lambda x, y: x * y * y]}[order]
+    for f in space:
+        assert np.allclose(f(b.nodes[:, 0], b.nodes[:, 1]) @ N, f(xi, eta), atol=1e-13)
+    h = 1e-6
+    for d, (a, c) in enumerate(((h, 0.0), (0.0, h))):
+        fd = (b.eval(xi + a, eta + c)[0] - b.eval(xi - a, eta - c)[0]) / (2 * h)
+        assert np.abs(fd - G[:, d]).max() < 1e-8
+
+
+def test_order_zero_is_the_constant_element():
+    nodes, el = quad9_sphere(2, 0.2)
+    A0 = qo.dense_matrix(nodes, el, 0, 3.0, 0.3 + 0.2j)
+    Aq = quad9.dense_matrix(nodes, el, 3.0, 0.3 + 0.2j)
+    assert np.abs(A0 - Aq).max() <= 1e-14 * np.abs(Aq).max()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_closed_surface_identities(order):
+    nodes, el = quad9_sphere(2, 0.2)
+    mesh = qo.OrderMesh(nodes, el, order)
+    D, H, S, K = qo.dhsk_block(mesh, mesh.geo.Y, 1e-3, self_same=True)
+    assert np.abs(D.sum(axis=1) + 0.5).max() < 5e-8
+    assert np.abs(H.sum(axis=1)).max() < 1e-8 * np.abs(H).max()
+
+
+def _flat_q9(a, b, c, d):
+    Y = []
+    for eta in (-1.0, 0.0, 1.0):
+        for xi in (-1.0, 0.0, 1.0):
+            w = np.array([(1 - xi) * (1 - eta), (1 + xi) * (1 - eta), (1 + xi) * (1 + eta), (1 - xi) * (1 + eta)]) / 4
+            Y.append(w[0] * a + w[1] * b + w[2] * c + w[3] * d)
+    return np.array(Y)
+
+
+def _inverse_map(Y, pts):
+    """(xi, eta) of points of a flat element by Newton's method."""
+    xi, eta = np.zeros(len(pts)), np.zeros(len(pts))
+    for _ in range(30):
+        y, yx, ye = quad9.geometry(Y, xi, eta)[:3]
+        M = np.stack([yx, ye], axis=-1)
+        step = np.linalg.solve(np.einsum("pdi,pdj->pij", M, M),
+                               np.einsum("pdi,pd->pi", M, pts - y)[..., None])[..., 0]
+        xi, eta = xi + step[:, 0], eta + step[:, 1]
+    return xi, eta
+
+
+@pytest.mark.parametrize("order,k", [(1, 0.5), (2, 4.0)])
+def test_flat_element_finite_part_with_the_gradient_term(order, k):
+    corners = [np.array(p) for p in ([0.0, 0.0, 0.0], [0.11, 0.01, 0.0], [0.13, 0.09, 0.0], [-0.01, 0.1, 0.0])]
+    Y = _flat_q9(*corners)
+    basis = qo.PressureBasis(order)
+    nrm = np.cross(corners[1] - corners[0], corners[2] - corners[0])
+    nrm /= np.linalg.norm(nrm)
+    for a in range(basis.nb):
+        D, H, S, K = qo.self_integrals(Y, basis, a, k)
+        xa, ea = basis.nodes[a]
+        x, yx, ye = quad9.geometry(Y, xa, ea)[:3]
+        N0, G0 = basis.eval(np.array(xa), np.array(ea))
+        N0, G0 = N0.reshape(-1), G0.reshape(-1, 2)
+        M = np.stack([yx, ye], axis=-1)
+        gy = (M @ np.linalg.inv(M.T @ M) @ G0.T).T          # in-plane gradients of N_b at x
+        fp, pv, invr = 0.0, np.zeros(3), 0.0
+        for e in range(4):
+            p, q = corners[e], corners[(e + 1) % 4]
+            eh = (q - p) / np.linalg.norm(q - p)
+            ta, tb = np.dot(p - x, eh), np.dot(q - x, eh)
+            he = np.linalg.norm((p - x) - ta * eh)
+            ra, rb = np.linalg.norm(p - x), np.linalg.norm(q - x)
+            fp -= (tb / rb - ta / ra) / he                   # finite part of int r^-3
+            line = np.log((tb + rb) / (ta + ra))             # int ds / r along the edge
+            pv -= np.cross(eh, nrm) * line                   # PV int (y - x) / r^3 = -sum nu int ds/r
+            invr += he * line                                # int 1/r
+        rem_h = np.zeros(basis.nb, dtype=complex)
+        rem_s = np.zeros(basis.nb, dtype=complex)
+        for e in range(4):
+            pts, w = bem.collapsed_rule(x, corners[e], corners[(e + 1) % 4], 96)
+            Nb, _ = basis.eval(*_inverse_map(Y, pts))
+            r = np.linalg.norm(pts - x, axis=-1)
+            lin = N0[:, None] + gy @ (pts - x).T
+            rem_h += (Nb - lin) @ (w / r ** 3) + Nb @ (w * (np.exp(1j * k * r) * (1 - 1j * k * r) - 1) / r ** 3)
+            rem_s += (Nb - N0[:, None]) @ (w / r) + Nb @ (w * (np.exp(1j * k * r) - 1) / r)
+        Href = (N0 * fp + gy @ pv + rem_h) / (4 * np.pi)
+        Sref = (N0 * invr + rem_s) / (4 * np.pi)
+        assert np.abs(D).max() < 1e-14 and np.abs(K).max() < 1e-14
+        assert np.abs(H - Href).max() < 2e-9 * np.abs(Href).max(), a
+        # S integrates directly (no subtraction): 24 nodes per direction
+        # leave about 1e-8 of quadrature error on the thin triangle towards
+        # the nearest side
+        assert np.abs(S - Sref).max() < 5e-8 * np.abs(Sref).max(), a
+
+
+def _green_errors(order, m, k=1e-4):
+    nodes, el = quad9_sphere(m, 0.2)
+    mesh = qo.OrderMesh(nodes, el, order)
+    D, H, S, K = qo.dhsk_block(mesh, mesh.geo.Y, k, self_same=True)
+    g = np.array([1.0, 0.5, -0.3])
+    u, dudn = mesh.points @ g, mesh.normals @ g
+    rep = D @ u - S @ dudn + 0.5 * u            # -u/2 = D u - S du/dn
+    hyp = H @ u - K @ dudn + 0.5 * dudn         # -(du/dn_x)/2 = H u - K du/dn
+    return np.abs(rep).max() / np.abs(u).max(), np.abs(hyp).max() / np.abs(dudn).max()
+
+
+def test_green_identities_with_a_linear_harmonic_field():
+    r2, _ = _green_errors(1, 2)
+    r3, _ = _green_errors(1, 3)
+    assert r2 < 2e-3 and r3 < 0.4 * r2              # O(h^3) for the bilinear density
+    _, h2 = _green_errors(2, 2)
+    _, h3 = _green_errors(2, 3)
+    assert h2 < 6e-3 and h3 < 0.45 * h2             # O(h^2): the quadratic density through H
+
+
+def _series(ka, ct, nmax=40):
+    return sum((2 * n + 1) * 1j ** n * (1j / ka ** 2) / sph_hn_deriv(n, ka) * eval_legendre(n, ct)
+               for n in range(nmax))
+
+
+def _sphere_error(order, m, k=2.0, a=0.2):
+    nodes, el = quad9_sphere(m, a)
+    mesh = qo.OrderMesh(nodes, el, order)
+    p = np.linalg.solve(qo.dense_matrix(nodes, el, order, k), qo.plane_wave_rhs(mesh, k, [1.0, 0.0, 0.0]))
+    pa = _series(k * a, mesh.points[:, 0] / np.linalg.norm(mesh.points, axis=1))
+    return np.linalg.norm(p - pa) / np.linalg.norm(pa), len(p)
+
+
+def test_rigid_sphere_quadratic_pressure_per_unknown():
+    e2, n2 = _sphere_error(2, 1)       # 6 elements x 8 nodes
+    e0, n0 = _sphere_error(0, 3)       # 54 elements x 1 node
+    assert n2 < n0 and e2 < 0.5 * e0 and e2 < 4e-3, (e2, e0)
+
+
+def test_periodic_blocks_equal_the_dense_matrix_of_the_array():
+    nodes, el = quad9_sphere(1, 0.2)
+    cell = qo.OrderMesh(nodes, el, 1)
+    L, counts, k, beta = np.diag([0.5, 0.55, 1.0]), (2, 1, 1), 3.0, 0.3 + 0.2j
+    cells = bem.lattice_cells(counts)
+    allN = np.concatenate([nodes + np.asarray(c, float) @ L for c in cells])
+    allE = np.concatenate([el + i * len(nodes) for i in range(len(cells))])
+    A = qo.dense_matrix(allN, allE, 1, k, beta)
+    n = cell.n * cell.nb
+    for ci, c in enumerate(cells):
+        for cj, cp in enumerate(cells):
+            d = tuple(x - y for x, y in zip(c, cp))
+            T = qo.toeplitz_block(cell, L, d, k, beta)
+            # translated node coordinates differ by rounding, which the
+            # finite part amplifies by (rho_hat / rho_min)^2 (the thin
+            # triangles of off-centre nodes reach rho_min of about 5e-4)
+            assert np.abs(A[ci * n:(ci + 1) * n, cj * n:(cj + 1) * n] - T).max() <= 5e-9 * np.abs(T).max()
