@@ -170,6 +170,12 @@ typedef struct {
    * far-class rule and each point's normal); the field-point calls take
    * triangles only. */
   int32_t element;
+  /* Order of the discontinuous pressure on FMPB_ELEM_QUAD9 elements (0,
+   * zero-initialised: one constant per element at its centre; 1: 2 x 2 nodes
+   * at +-1/sqrt(3), bilinear; 2: the eight-node serendipity element on
+   * [-sqrt(3/5), sqrt(3/5)]^2), collocated at the nodes with dof e nb + a.
+   * Orders 1 and 2 run the PBEM form (FP64, FP32 or MIXED). */
+  int32_t pressure_order;
 } fmpb_operator_opts;
 
 typedef struct {
@@ -195,6 +201,7 @@ typedef struct {
   int64_t n_m2l_near;    /* FMPBEM2: M2L pairs over all near offsets */
   int64_t n_p2p_near;    /* FMPBEM2: exact entries kept */
   int32_t element;       /* fmpb_element of the mesh */
+  int32_t pressure_order;/* pressure order of FMPB_ELEM_QUAD9 elements (n = elements x nodes) */
 } fmpb_operator_info;
 
 /*
@@ -403,6 +410,23 @@ fmpb_status fmpb_build_blocks_admittance(const double *verts, int64_t nv, const 
 fmpb_status fmpb_build_blocks_q9(const double *nodes, int64_t nn, const int32_t *elems, int64_t n,
                                  const fmpb_lattice *lattice, double k, double beta_re, double beta_im,
                                  int n_off, const int32_t *offsets, fmpb_c64 *out, void *stream);
+
+/*
+ * fmpb_build_blocks_q9 with discontinuous pressure of order 1 or 2 (see
+ * fmpb_operator_opts.pressure_order): N = n nb dofs per cell (nb = 4 or 8),
+ * dof e nb + a collocated at node a of element e, column f nb + b weighted
+ * by shape N_b.
+ *   out     device, n_off x N x N, row-major per block.
+ * Rules: regular classes as fmpb_build_blocks_q9 but the very-near one on
+ * 4 x 4 (order 1) or 8 x 8 (order 2) parameter sub-squares of 8 x 8 points;
+ * the element's own entries of a node by a 24 x 24 polar rule about the node
+ * with the finite part of N_b H (the shape function's gradient enters the
+ * 1/rho coefficient).
+ * Errors: as fmpb_build_blocks_q9, and EINVAL for another order.
+ */
+fmpb_status fmpb_build_blocks_q9p(const double *nodes, int64_t nn, const int32_t *elems, int64_t n, int order,
+                                  const fmpb_lattice *lattice, double k, double beta_re, double beta_im,
+                                  int n_off, const int32_t *offsets, fmpb_c64 *out, void *stream);
 
 /*
  * P2M table V_0 (B x n, Eq. (p2m)) and L2P table U_0 (n x B, Eq. (l2p) and

@@ -34,7 +34,8 @@ class OperatorOpts(ctypes.Structure):
                 ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
                 ("halfspace", ctypes.c_int32), ("plane_axis", ctypes.c_int32), ("plane_offset", ctypes.c_double),
                 ("Rp_re", ctypes.c_double), ("Rp_im", ctypes.c_double),
-                ("n_t_near", ctypes.c_int32), ("near_levels", ctypes.c_int32), ("element", ctypes.c_int32)]
+                ("n_t_near", ctypes.c_int32), ("near_levels", ctypes.c_int32), ("element", ctypes.c_int32),
+                ("pressure_order", ctypes.c_int32)]
 
 
 class C64(ctypes.Structure):
@@ -53,7 +54,8 @@ class OperatorInfo(ctypes.Structure):
                 ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
                 ("halfspace", ctypes.c_int32), ("hankel_axis", ctypes.c_int32), ("n_near_image", ctypes.c_int32),
                 ("image_separate", ctypes.c_int32), ("near_levels", ctypes.c_int32),
-                ("n_m2l_near", ctypes.c_int64), ("n_p2p_near", ctypes.c_int64), ("element", ctypes.c_int32)]
+                ("n_m2l_near", ctypes.c_int64), ("n_p2p_near", ctypes.c_int64), ("element", ctypes.c_int32),
+                ("pressure_order", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -120,6 +122,7 @@ SIGNATURES = {
     "fmpb_build_blocks_admittance": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
     "fmpb_multipole_tables_admittance": (INT, [P, I64, P, I64, D, D, D, INT, P, P, P]),
     "fmpb_build_blocks_q9": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
+    "fmpb_build_blocks_q9p": (INT, [P, I64, P, I64, INT, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
     "fmpb_m2l_blocks": (INT, [D, INT, INT, P, P, P]),
     "fmpb_offset_gemm_bf16": (INT, [P, INT, P, I64, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_shape": (INT, [P, P, P]),

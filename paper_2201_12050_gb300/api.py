@@ -58,10 +58,11 @@ class Operator:
     """fmpb_operator: the tables of one (unit-cell mesh, lattice, k); beta is
     the surface's uniform normalised admittance (0: rigid); plane =
     (axis, offset, R_p) makes it a half-space operator (None: full space).
-    tris with nine columns are nine-node quadrilaterals (FMPB_ELEM_QUAD9)."""
+    tris with nine columns are nine-node quadrilaterals (FMPB_ELEM_QUAD9),
+    whose discontinuous pressure has order pressure_order (0, 1 or 2)."""
 
     def __init__(self, verts, tris, counts, vectors, k, form=FORM_AUTO, n_t=0, precision=FP64, beta=0.0,
-                 plane=None, n_t_near=0, near_levels=0):
+                 plane=None, n_t_near=0, near_levels=0, pressure_order=0):
         self._lib = lib()
         v = _host(verts, np.float64)
         t = _host(tris, np.int32)
@@ -71,6 +72,7 @@ class Operator:
         opts.n_t_near, opts.near_levels = int(n_t_near), int(near_levels)
         if t.ndim == 2 and t.shape[1] == 9:
             opts.element = ELEM_QUAD9
+        opts.pressure_order = int(pressure_order)
         if plane is not None:
             axis, offset, Rp = plane
             Rp = complex(Rp)
@@ -250,16 +252,24 @@ def build_blocks_admittance(verts, tris, counts, vectors, k, beta, offsets):
     return out
 
 
-def build_blocks_q9(nodes, elems, counts, vectors, k, offsets, beta=0.0):
-    """fmpb_build_blocks_q9: T_delta on nine-node quadrilaterals (elems n x 9)."""
+def build_blocks_q9(nodes, elems, counts, vectors, k, offsets, beta=0.0, pressure_order=0):
+    """fmpb_build_blocks_q9 (pressure_order 0) or fmpb_build_blocks_q9p (1, 2):
+    T_delta on nine-node quadrilaterals (elems n x 9), (n_off, N, N) with
+    N = n x (1, 4, 8)[pressure_order]."""
     v = _host(nodes, np.float64)
     t = _host(elems, np.int32).reshape(-1, 9)
     off = _host(offsets, np.int32).reshape(-1, 3)
     lat = _lattice(counts, vectors)
     beta = complex(beta)
-    out = torch.empty((len(off), len(t), len(t)), dtype=torch.complex128, device="cuda")
-    check(lib().fmpb_build_blocks_q9(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k), beta.real,
-                                     beta.imag, len(off), _ptr(off), _ptr(out), _stream()))
+    order = int(pressure_order)
+    N = len(t) * {0: 1, 1: 4, 2: 8}.get(order, 1)
+    out = torch.empty((len(off), N, N), dtype=torch.complex128, device="cuda")
+    if order == 0:
+        check(lib().fmpb_build_blocks_q9(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), float(k), beta.real,
+                                         beta.imag, len(off), _ptr(off), _ptr(out), _stream()))
+    else:
+        check(lib().fmpb_build_blocks_q9p(_ptr(v), len(v), _ptr(t), len(t), order, ctypes.byref(lat), float(k),
+                                          beta.real, beta.imag, len(off), _ptr(off), _ptr(out), _stream()))
     return out
 
 

@@ -516,6 +516,9 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(o.element == FMPB_ELEM_TRI3 || o.element == FMPB_ELEM_QUAD9,
             "operator_create: element must be FMPB_ELEM_TRI3 or FMPB_ELEM_QUAD9");
   const bool quad9 = o.element == FMPB_ELEM_QUAD9;
+  CHECK_ARG(o.pressure_order == 0 || (quad9 && (o.pressure_order == 1 || o.pressure_order == 2) &&
+                                      (o.form == FMPB_FORM_AUTO || o.form == FMPB_FORM_PBEM)),
+            "operator_create: pressure of order 1 or 2 takes FMPB_ELEM_QUAD9 elements and the PBEM form");
   CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && !o.halfspace && o.precision != FMPB_BF16 &&
                        !(o.form == FMPB_FORM_FMM && o.precision == FMPB_MIXED)),
             "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED) or the FMM form "
@@ -536,7 +539,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   op->beta = beta;
   fmpb_status s = make_grid(lattice, op->grid);
   if (s != FMPB_OK) return fail(s);
-  s = quad9 ? upload_mesh_q9(verts, nv, tris, ntri, op->mesh, st) : upload_mesh(verts, nv, tris, ntri, op->mesh, st);
+  s = quad9 ? upload_mesh_q9p(verts, nv, tris, ntri, o.pressure_order, op->mesh, st)
+            : upload_mesh(verts, nv, tris, ntri, op->mesh, st);
   if (s != FMPB_OK) return fail(s);
   op->shape = make_shape(op->grid.M);
   const CircShape& sh = op->shape;
@@ -812,6 +816,7 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->n_m2l_near = op->near2 ? op->near2->n_m2l : 0;
   info->n_p2p_near = op->near2 ? op->near2->n_p2p : 0;
   info->element = op->mesh.nodes == 9 ? FMPB_ELEM_QUAD9 : FMPB_ELEM_TRI3;
+  info->pressure_order = op->mesh.q9_order;
   return FMPB_OK;
 }
 
@@ -1013,6 +1018,27 @@ fmpb_status fmpb_build_blocks_q9(const double* nodes, int64_t nn, const int32_t*
     std::vector<int64_t> dest(n_off);
     for (int i = 0; i < n_off; ++i) dest[i] = i;
     s = build_blocks_q9(m, g, k, mkc(beta_re, beta_im), n_off, offsets, dest.data(), (cd*)out, st);
+  }
+  free_mesh(m);
+  return s;
+}
+
+fmpb_status fmpb_build_blocks_q9p(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, int order,
+                                  const fmpb_lattice* lattice, double k, double beta_re, double beta_im, int n_off,
+                                  const int32_t* offsets, fmpb_c64* out, void* stream) {
+  CHECK_ARG(offsets && out && n_off >= 1, "build_blocks_q9p: bad offsets or output");
+  CHECK_ARG(order == 1 || order == 2, "build_blocks_q9p: pressure order must be 1 or 2");
+  CHECK_ARG(k > 0.0 && std::isfinite(k), "build_blocks_q9p: wavenumber must be positive");
+  CHECK_ARG(std::isfinite(beta_re) && std::isfinite(beta_im), "build_blocks_q9p: admittance must be finite");
+  CellGrid g;
+  FMPB_TRY(make_grid(lattice, g));
+  DeviceMesh m;
+  cudaStream_t st = (cudaStream_t)stream;
+  fmpb_status s = upload_mesh_q9p(nodes, nn, elems, n, order, m, st);
+  if (s == FMPB_OK) {
+    std::vector<int64_t> dest(n_off);
+    for (int i = 0; i < n_off; ++i) dest[i] = i;
+    s = build_blocks_q9p(m, g, k, mkc(beta_re, beta_im), n_off, offsets, dest.data(), (cd*)out, st);
   }
   free_mesh(m);
   return s;

@@ -101,7 +101,12 @@ struct DeviceMesh {
   // (q9_far[(p 7 + f) n + e], f: y, n_y, w|J|) for coalesced loads across
   // source elements, the near and very-near rules element-major
   // (q9_near[(e 320 + p) 8 + f]) for a warp sharing one element.
+  // With pressure of order q9_order = 1 or 2 (nb = 4 or 8 nodes per element)
+  // n counts the q9_ne nb dofs (dof e nb + a) and el holds each dof's
+  // collocation point and normal.
   int nodes = 3;
+  int q9_order = 0;
+  int q9_ne = 0;
   Q9Elem* q9 = nullptr;
   double* q9_far = nullptr;
   double* q9_near = nullptr;
@@ -116,6 +121,11 @@ void free_mesh(DeviceMesh& m);
 // y_xi x y_eta into the fluid).
 fmpb_status upload_mesh_q9(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, DeviceMesh& m,
                            cudaStream_t st);
+// The same with discontinuous pressure of order 1 or 2 (quad9p.cu).
+fmpb_status upload_mesh_q9p(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, int order,
+                            DeviceMesh& m, cudaStream_t st);
+fmpb_status build_blocks_q9p(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);
 // build_blocks for a nine-node mesh (full space only).
 fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);

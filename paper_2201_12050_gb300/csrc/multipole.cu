@@ -554,6 +554,10 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
+  if (m.nodes == 9 && m.q9_order > 0) {
+    set_error("multipole_tables: pressure of order 1 or 2 runs the PBEM form only");
+    return FMPB_EINVAL;
+  }
   if (m.nodes == 9 && centres) {
     set_error("multipole_tables: per-element expansion centres take flat triangles");
     return FMPB_EINVAL;

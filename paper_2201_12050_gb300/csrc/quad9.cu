@@ -214,6 +214,7 @@ static Q9Rules q9_rules() {
   for (int i = 0; i < 4; ++i) gl_node(4, i, &R.t4[i], &R.w4[i]);
   for (int i = 0; i < 8; ++i) gl_node(8, i, &R.t8[i], &R.w8[i]);
   for (int i = 0; i < 16; ++i) gl_node(16, i, &R.t16[i], &R.w16[i]);
+  for (int i = 0; i < 24; ++i) gl_node(24, i, &R.t24[i], &R.w24[i]);
   return R;
 }
 
@@ -280,6 +281,7 @@ fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd
     set_error("build_blocks_q9: not a nine-node mesh");
     return FMPB_EINVAL;
   }
+  if (m.q9_order > 0) return build_blocks_q9p(m, g, k, beta, n_off, offsets, dest_host, out, st);
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
   for (int o = 0; o < n_off; ++o) {

@@ -40,9 +40,10 @@ constexpr int Q9_NEAR_TAB = Q9_NEAR + Q9_VNEAR;
 constexpr int Q9_THETA = 64;       // angular nodes of the self rule (4 sides x 16)
 constexpr int Q9_RHO = 16;         // radial nodes per angular node
 
-// Gauss-Legendre nodes t (ascending) and weights w on [0, 1].
+// Gauss-Legendre nodes t (ascending) and weights w on [0, 1] (the 24-point
+// rule serves the self terms of pressure of order 1 and 2).
 struct Q9Rules {
-  double t4[4], w4[4], t8[8], w8[8], t16[16], w16[16];
+  double t4[4], w4[4], t8[8], w8[8], t16[16], w16[16], t24[24], w24[24];
 };
 
 struct Q9Elem {
