@@ -274,3 +274,44 @@ def toeplitz_block(cell: OrderMesh, lattice, delta, k, beta=0.0):
     if same:
         T += (0.5 + 0.5 * beta) * np.eye(cell.n * cell.nb)
     return T
+
+
+# ------------------------------------------------------------ FMM tables --
+
+class _Colloc:
+    """The collocation points of an OrderMesh under the names fmm.l2p_table reads."""
+
+    def __init__(self, mesh: OrderMesh):
+        self.centroid, self.normal = mesh.points, mesh.normals
+
+
+def p2m_table(mesh: OrderMesh, k, nt, beta=0.0):
+    """V_0 (B x n nb) of Eq. (p2m) with the pressure shapes: column f nb + b
+    integrates N_b conj(dI_q/dn_y) (+ i k beta N_b conj(I_q)) over element f
+    with the far-class rule (4 x 4 Gauss-Legendre), each point's normal."""
+    xi, eta, w0 = quad9.tensor_rule(quad9.Q_FAR4)
+    y, ny, w = quad9._batch_rule(mesh.geo.Y, "far")        # n x 16 x 3, n x 16 x 3, n x 16
+    N, _ = mesh.basis.eval(xi, eta)                          # nb x 16
+    from . import special as sp
+    g = sp.grad_regular_table(nt, y, k)                      # B x n x 16 x 3
+    src = np.conj(np.einsum("bnqi,nqi->bnq", g, ny))
+    if beta != 0:
+        I = sp.wave_table(nt, y.reshape(-1, 3), k, "I").reshape(-1, *w.shape)
+        src = src + 1j * k * beta * np.conj(I)
+    V = np.einsum("bnq,nq,cq->bnc", src, w, N)               # B x n x nb
+    return V.reshape(V.shape[0], -1)
+
+
+def fmm_matvec_explicit(mesh: OrderMesh, lattice, counts, k, nt, p, beta=0.0):
+    """The FMPBEM product (Eq. (2dPeriodicFMM)) on a cell with pressure of
+    any order, every cell pair explicitly: near blocks (|delta|_inf <= 1)
+    from toeplitz_block, far pairs through U_0 K(delta) V_0."""
+    from . import fmm
+    near = {d: toeplitz_block(mesh, lattice, d, k, beta) for d in bem.near_offsets(counts)}
+
+    class _Cell:
+        n = mesh.n * mesh.nb
+
+    return fmm.fmm_matvec_explicit(_Cell(), lattice, counts, k, nt, p, near_blocks=near,
+                                   V0=p2m_table(mesh, k, nt, beta), U0=fmm.l2p_table(_Colloc(mesh), k, nt),
+                                   beta=beta)

@@ -189,3 +189,29 @@ def test_periodic_blocks_equal_the_dense_matrix_of_the_array():
             # finite part amplifies by (rho_hat / rho_min)^2 (the thin
             # triangles of off-centre nodes reach rho_min of about 5e-4)
             assert np.abs(A[ci * n:(ci + 1) * n, cj * n:(cj + 1) * n] - T).max() <= 5e-9 * np.abs(T).max()
+
+
+@pytest.mark.parametrize("order,beta", [(1, 0.0), (2, 0.3 + 0.2j)])
+def test_fmm_product_tends_to_the_exact_operator(order, beta):
+    # the far cells' blocks use the same 4 x 4 rule as the P2M table, so the
+    # FMPBEM product converges to the exact block Toeplitz product to
+    # rounding; shape functions taken at the element centre instead of each
+    # point stall it at 1e-3
+    nodes, el = quad9_sphere(1, 0.2)
+    cell = qo.OrderMesh(nodes, el, order)
+    L, counts, k = np.eye(3), (4, 1, 1), 2.0
+    blocks = {d: qo.toeplitz_block(cell, L, d, k, beta) for d in bem.all_offsets(counts)}
+    rng = np.random.default_rng(7)
+    N = cell.n * cell.nb * 4
+    p = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    y_exact = bem.toeplitz_matvec(blocks, counts, p)[0]
+    errs = [np.linalg.norm(qo.fmm_matvec_explicit(cell, L, counts, k, nt, p, beta)[0] - y_exact)
+            / np.linalg.norm(y_exact) for nt in (4, 8, 12)]
+    assert errs[1] < 1e-3 * errs[0] and errs[2] < 1e-13, errs
+
+
+def test_order_zero_p2m_is_the_constant_elements():
+    nodes, el = quad9_sphere(1, 0.2)
+    V = qo.p2m_table(qo.OrderMesh(nodes, el, 0), 2.0, 6, 0.3j)
+    Vq = quad9.p2m_table(quad9.Q9Mesh(nodes, el), 2.0, 6, 0.3j)
+    assert np.abs(V - Vq).max() <= 1e-14 * np.abs(Vq).max()
