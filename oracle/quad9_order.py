@@ -315,3 +315,28 @@ def fmm_matvec_explicit(mesh: OrderMesh, lattice, counts, k, nt, p, beta=0.0):
     return fmm.fmm_matvec_explicit(_Cell(), lattice, counts, k, nt, p, near_blocks=near,
                                    V0=p2m_table(mesh, k, nt, beta), U0=fmm.l2p_table(_Colloc(mesh), k, nt),
                                    beta=beta)
+
+
+# ---------------------------------------------------------- field points --
+
+def field_points(nodes, elems, order, lattice, counts, k, p, points, direction, amp=1.0, beta=0.0):
+    """Total pressure in the fluid (Eq. (cbie) with c = 1) from the surface
+    pressure p (dof (c n + e) nb + a over the cells of the array):
+      p(x) = p_inc(x) + sum_{f,b} int_{E_f} N_b [dG/dn_y + i k beta G] dA p_{f,b},
+    the single layer of dp/dn_m = -i k beta p joining the double layer with an
+    admittance; the same class rules as the collocation points, by the
+    distance of x to each element's centre."""
+    from types import SimpleNamespace
+    L = np.asarray(lattice, dtype=np.float64)
+    nodes = np.asarray(nodes, dtype=np.float64)
+    cells = bem.lattice_cells(counts)
+    allN = np.concatenate([nodes + np.asarray(c, dtype=np.float64) @ L for c in cells])
+    allE = np.concatenate([np.asarray(elems) + i * len(nodes) for i in range(len(cells))])
+    Y = allN[allE]
+    basis = PressureBasis(order)
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    tgt = SimpleNamespace(points=pts, normals=np.tile([0.0, 0.0, 1.0], (len(pts), 1)), basis=basis,
+                          nb=basis.nb, n=0)
+    D, _, S, _ = dhsk_block(tgt, Y, k)
+    out = amp * np.exp(1j * k * (pts @ np.asarray(direction, dtype=np.float64)))
+    return out + (D + 1j * k * beta * S) @ np.asarray(p)

@@ -215,3 +215,38 @@ def test_order_zero_p2m_is_the_constant_elements():
     V = qo.p2m_table(qo.OrderMesh(nodes, el, 0), 2.0, 6, 0.3j)
     Vq = quad9.p2m_table(quad9.Q9Mesh(nodes, el), 2.0, 6, 0.3j)
     assert np.abs(V - Vq).max() <= 1e-14 * np.abs(Vq).max()
+
+
+def _impedance_sphere_total(k, a, beta, pts, nmax=40):
+    """sum_n (2n+1) i^n [j_n(kr) + A_n h_n(kr)] P_n(cos theta) outside the sphere,
+    A_n = -(j_n'(ka) + i beta j_n(ka)) / (h_n'(ka) + i beta h_n(ka)) (dp/dr = -i k beta p at r = a)."""
+    from oracle.special import sph_jn, sph_jn_deriv, sph_hn
+    r = np.linalg.norm(pts, axis=1)
+    ct = pts[:, 0] / r
+    ka = k * a
+    out = np.zeros(len(pts), dtype=complex)
+    for n in range(nmax):
+        An = -(sph_jn_deriv(n, ka) + 1j * beta * sph_jn(n, ka)) / (sph_hn_deriv(n, ka) + 1j * beta * sph_hn(n, ka))
+        out += (2 * n + 1) * 1j ** n * (sph_jn(n, k * r) + An * sph_hn(n, k * r)) * eval_legendre(n, ct)
+    return out
+
+
+@pytest.mark.parametrize("order,m,beta", [(1, 2, 0.0), (2, 1, 0.6 + 0.4j)])
+def test_field_points_against_the_analytic_sphere(order, m, beta):
+    k = 3.0
+    nodes, el = quad9_sphere(m, 0.2)
+    mesh = qo.OrderMesh(nodes, el, order)
+    p = np.linalg.solve(qo.toeplitz_block(mesh, np.eye(3), (0, 0, 0), k, beta),
+                        qo.plane_wave_rhs(mesh, k, [1.0, 0.0, 0.0]))
+    rng = np.random.default_rng(9)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    pts = np.vstack([0.3 * dirs, 0.6 * dirs])
+    ref = _impedance_sphere_total(k, 0.2, beta, pts)
+    got = qo.field_points(nodes, el, order, np.eye(3), (1, 1, 1), k, p, pts, [1.0, 0.0, 0.0], beta=beta)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 5e-3, err
+    if beta != 0:
+        # the admittance single layer is needed to reach the series
+        no_s = qo.field_points(nodes, el, order, np.eye(3), (1, 1, 1), k, p, pts, [1.0, 0.0, 0.0])
+        assert np.linalg.norm(no_s - ref) / np.linalg.norm(ref) > 5 * err
