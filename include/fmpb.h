@@ -167,8 +167,8 @@ typedef struct {
    * 1; y_xi x y_eta into the fluid).  Such operators run in full space, in
    * the PBEM form (FP64, FP32 or MIXED; AUTO picks it) or the FMM form
    * (FP64 or FP32; its P2M table integrates each element with the 4 x 4
-   * far-class rule and each point's normal); the field-point calls take
-   * triangles only. */
+   * far-class rule and each point's normal).  Field points and the
+   * insertion loss take every pressure order (full space). */
   int32_t element;
   /* Order of the discontinuous pressure on FMPB_ELEM_QUAD9 elements (0,
    * zero-initialised: one constant per element at its centre; 1: 2 x 2 nodes

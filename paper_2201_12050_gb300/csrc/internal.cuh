@@ -126,6 +126,10 @@ fmpb_status upload_mesh_q9p(const double* nodes, int64_t nn, const int32_t* elem
                             DeviceMesh& m, cudaStream_t st);
 fmpb_status build_blocks_q9p(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                              const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);
+// out[r][p] += the scattered pressure of the surface solution surf at the
+// points (nine-node meshes of any pressure order; full space).
+fmpb_status field_scattered_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
+                               int64_t npts, const double* pts, cd* out, cudaStream_t st);
 // build_blocks for a nine-node mesh (full space only).
 fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);

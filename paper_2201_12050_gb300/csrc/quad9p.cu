@@ -213,7 +213,66 @@ __global__ void __launch_bounds__(256) k_q9p_self(const Q9Elem* __restrict__ q9,
     }
 }
 
+// Scattered pressure at field points added to out[r][p] (which holds the
+// incident field): one CTA per (rhs, point), the threads split the (cell,
+// element) items, the partial sums are reduced in a fixed order.
+template <bool SK>
+__global__ void __launch_bounds__(256) k_field_q9(const Q9Elem* __restrict__ q9, int ne, int order, CellGrid g,
+                                                  double k, cd beta, int R, const cd* __restrict__ surf,
+                                                  int64_t npts, const double* __restrict__ pts, cd* __restrict__ out,
+                                                  Q9Rules Rq) {
+  __shared__ double sre[256], sim[256];
+  const int nb = order == 0 ? 1 : q9p_basis(order).nb;
+  const size_t N = (size_t)ne * nb * g.ncells;
+  const cd ikb = mkc(-k * beta.y, k * beta.x);
+  const int64_t total = npts * R;
+  const int64_t items = (int64_t)g.ncells * ne;
+  for (int64_t idx = blockIdx.x; idx < total; idx += gridDim.x) {
+    const int r = (int)(idx / npts);
+    const int64_t p = idx - (int64_t)r * npts;
+    const double x[3] = {pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]};
+    cd part = mkc(0.0, 0.0);
+    for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+      const int c = (int)(it / ne), f = (int)(it - (int64_t)c * ne);
+      double pos[3];
+      g.cell_position(c, pos);
+      const Q9Elem& F = q9[f];
+      const cd* pd = surf + (size_t)r * N + ((size_t)c * ne + f) * nb;
+      part = cadd(part, q9_field_element<SK>(F.Y, F.c, F.hmax, order, Rq, x, pos, k, ikb, pd));
+    }
+    sre[threadIdx.x] = part.x;
+    sim[threadIdx.x] = part.y;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+        sre[threadIdx.x] += sre[threadIdx.x + s];
+        sim[threadIdx.x] += sim[threadIdx.x + s];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[idx] = cadd(out[idx], mkc(sre[0], sim[0]));
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ host side --
+fmpb_status field_scattered_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
+                               int64_t npts, const double* pts, cd* out, cudaStream_t st) {
+  if (m.nodes != 9 || !m.q9) {
+    set_error("field: not a nine-node mesh");
+    return FMPB_EINVAL;
+  }
+  const int64_t total = npts * R;
+  if (total <= 0) return FMPB_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>(total, 152 * 16);
+  if (beta.x == 0.0 && beta.y == 0.0)
+    FMPB_LAUNCH("field_q9", st, k_field_q9<false><<<blocks, 256, 0, st>>>(m.q9, m.q9_ne, m.q9_order, g, k, beta, R, surf, npts, pts, out, m.q9r));
+  else
+    FMPB_LAUNCH("field_q9_adm", st, k_field_q9<true><<<blocks, 256, 0, st>>>(m.q9, m.q9_ne, m.q9_order, g, k, beta, R, surf, npts, pts, out, m.q9r));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 fmpb_status upload_mesh_q9p(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, int order,
                             DeviceMesh& m, cudaStream_t st) {
   if (order < 0 || order > 2) {

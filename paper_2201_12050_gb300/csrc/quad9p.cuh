@@ -150,6 +150,53 @@ __host__ __device__ inline void q9p_near_sum(const double Y[9][3], const Q9Basis
   }
 }
 
+// Contribution of one element (nodes Y, centre cen, chord hmax; translated
+// by sh) to the pressure at a field point x: int (dG/dn_y + i k beta G) p dA
+// with p = sum_b N_b pd[b] (order 0: p = pd[0]), by the class rules of the
+// collocation points (order 0: quarters for the very-near class; orders 1, 2:
+// their sub-squares).  ikb = i k beta; SK: with the single layer.
+template <bool SK>
+__host__ __device__ inline cd q9_field_element(const double Y[9][3], const double cen[3], double hmax, int order,
+                                               const Q9Rules& R, const double x[3], const double sh[3], double k,
+                                               cd ikb, const cd* pd) {
+  double dc[3];
+  for (int d = 0; d < 3; ++d) dc[d] = x[d] - (cen[d] + sh[d]);
+  const double dist = sqrt(q9_dot(dc, dc));
+  const int cls = dist >= FAR_RATIO * hmax ? 0 : dist >= NEAR_RATIO * hmax ? 1 : 2;
+  const int parts = order == 0 ? 2 : order == 1 ? 4 : 8;
+  const int npts = cls == 0 ? Q9_FAR : cls == 1 ? Q9_NEAR : 64 * parts * parts;
+  const Q9Basis B = q9p_basis(order == 0 ? 1 : order);
+  double am[9][3];
+  q9_monomials(Y, am);
+  const double nz[3] = {0.0, 0.0, 1.0};   // the integrands used here do not read n_x
+  cd acc = mkc(0.0, 0.0);
+  for (int p = 0; p < npts; ++p) {
+    double xi, eta, w;
+    if (cls == 2 && order > 0)
+      q9p_vnear_point(R, parts, p, &xi, &eta, &w);
+    else
+      q9_rule_point(R, cls, p, &xi, &eta, &w);
+    double y[3], yx[3], ye[3], J[3];
+    q9_eval(am, xi, eta, y, yx, ye);
+    q9_cross(yx, ye, J);
+    const double dJ = sqrt(q9_dot(J, J));
+    const double ny[3] = {J[0] / dJ, J[1] / dJ, J[2] / dJ};
+    const double dv[3] = {x[0] - (y[0] + sh[0]), x[1] - (y[1] + sh[1]), x[2] - (y[2] + sh[2])};
+    cd Dp = mkc(0.0, 0.0), Hp = mkc(0.0, 0.0), Sp = mkc(0.0, 0.0), Kp = mkc(0.0, 0.0);
+    q9_kernels<SK>(dv, nz, ny, w * dJ, k, Dp, Hp, Sp, Kp);
+    cd dens = pd[0];
+    if (order > 0) {
+      double N[Q9P_MAXNB];
+      q9p_shape(B, xi, eta, N, nullptr);
+      dens = mkc(0.0, 0.0);
+      for (int b = 0; b < B.nb; ++b) dens = cadd(dens, cmulr(pd[b], N[b]));
+    }
+    const cd g = SK ? cfma(ikb, Sp, Dp) : Dp;
+    acc = cfma(g, dens, acc);
+  }
+  return acc;
+}
+
 // Monomial coefficients of the map about (xa, ea): y(xa + u, ea + v) =
 // sum_{p,q} b[3 q + p] u^p v^q, from those about the centre.
 __host__ __device__ inline void q9p_shift_monomials(const double a[9][3], double xa, double ea, double b[9][3]) {

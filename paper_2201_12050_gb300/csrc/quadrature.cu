@@ -1120,9 +1120,20 @@ fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const Ce
     set_error("field: half-space operator without its reflected cell");
     return FMPB_EINVAL;
   }
-  if (m.nodes != 3) {
-    set_error("field: field points take flat triangles");
-    return FMPB_EINVAL;
+  if (m.nodes == 9) {
+    // nine-node quadrilaterals: the incident field, then the scattered part added
+    if (pl.on) {
+      set_error("field: nine-node quadrilaterals run in full space");
+      return FMPB_EINVAL;
+    }
+    IncDev* dq = nullptr;
+    FMPB_TRY(upload_incident(R, inc, k, &dq, st));
+    const int64_t tq = (int64_t)npts * R;
+    FMPB_LAUNCH("incident_points", st, k_incident_points<<<(unsigned)std::min<int64_t>((tq + 255) / 256, 152 * 32), 256, 0, st>>>(dq, pl, k, R, npts, pts, out));
+    FMPB_CUDA(cudaGetLastError());
+    FMPB_TRY(field_scattered_q9(m, g, k, beta, R, surf, npts, pts, out, st));
+    FMPB_CUDA(cudaFreeAsync(dq, st));
+    return FMPB_OK;
   }
   IncDev* dinc = nullptr;
   FMPB_TRY(upload_incident(R, inc, k, &dinc, st));
