@@ -174,7 +174,8 @@ typedef struct {
    * zero-initialised: one constant per element at its centre; 1: 2 x 2 nodes
    * at +-1/sqrt(3), bilinear; 2: the eight-node serendipity element on
    * [-sqrt(3/5), sqrt(3/5)]^2), collocated at the nodes with dof e nb + a.
-   * Orders 1 and 2 run the PBEM form (FP64, FP32 or MIXED). */
+   * Every order runs the PBEM and FMM forms of FMPB_ELEM_QUAD9 (the P2M table
+   * weights the far rule by each shape N_b). */
   int32_t pressure_order;
 } fmpb_operator_opts;
 

@@ -516,9 +516,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(o.element == FMPB_ELEM_TRI3 || o.element == FMPB_ELEM_QUAD9,
             "operator_create: element must be FMPB_ELEM_TRI3 or FMPB_ELEM_QUAD9");
   const bool quad9 = o.element == FMPB_ELEM_QUAD9;
-  CHECK_ARG(o.pressure_order == 0 || (quad9 && (o.pressure_order == 1 || o.pressure_order == 2) &&
-                                      (o.form == FMPB_FORM_AUTO || o.form == FMPB_FORM_PBEM)),
-            "operator_create: pressure of order 1 or 2 takes FMPB_ELEM_QUAD9 elements and the PBEM form");
+  CHECK_ARG(o.pressure_order == 0 || (quad9 && (o.pressure_order == 1 || o.pressure_order == 2)),
+            "operator_create: pressure of order 1 or 2 takes FMPB_ELEM_QUAD9 elements");
   CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && !o.halfspace && o.precision != FMPB_BF16 &&
                        !(o.form == FMPB_FORM_FMM && o.precision == FMPB_MIXED)),
             "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED) or the FMM form "

@@ -21,6 +21,7 @@
 #include "profile.cuh"
 #include "multipole.cuh"
 #include "ff.cuh"
+#include "quad9p.cuh"
 
 namespace fmpb {
 
@@ -371,6 +372,42 @@ __global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt
   if (q < B) V0[(size_t)q * n + j] = acc;
 }
 
+// V_0[q][f nb + b] with discontinuous pressure of order 1 or 2: the far rule
+// of element f weighted by each shape N_b.  One CTA per element.
+__global__ void k_p2m_table_q9p(const double* __restrict__ far_tab, int ne, int order, int nt, double k, cd beta,
+                                Q9Rules R, cd* __restrict__ V0) {
+  __shared__ WaveSetup ws;
+  const Q9Basis Bs = q9p_basis(order);
+  const int f = blockIdx.x;
+  const int B = (nt + 1) * (nt + 1);
+  const int q = threadIdx.x;
+  const size_t sn = (size_t)ne, N = (size_t)ne * Bs.nb;
+  cd acc[Q9P_MAXNB];
+  for (int b = 0; b < Q9P_MAXNB; ++b) acc[b] = mkc(0.0, 0.0);
+  const cd ikb = mkc(-k * beta.y, k * beta.x);   // i k beta
+  for (int p = 0; p < Q9_FAR; ++p) {
+    const double* t = far_tab + (size_t)p * 7 * sn + f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double y[3] = {t[0], t[sn], t[2 * sn]};
+      wave_setup(nt, y, k, &ws);
+    }
+    __syncthreads();
+    if (q < B) {
+      const double ny[3] = {t[3 * sn], t[4 * sn], t[5 * sn]};
+      cd I, dI;
+      wave_eval(nt, ws, q, ny, k, &I, &dI);
+      const cd src = cadd(cconj(dI), cmul(ikb, cconj(I)));
+      double xi, eta, w, Nv[Q9P_MAXNB];
+      q9_rule_point(R, 0, p, &xi, &eta, &w);
+      q9p_shape(Bs, xi, eta, Nv, nullptr);
+      for (int b = 0; b < Bs.nb; ++b) acc[b] = cadd(acc[b], cmulr(src, t[6 * sn] * Nv[b]));
+    }
+  }
+  if (q < B)
+    for (int b = 0; b < Bs.nb; ++b) V0[(size_t)q * N + (size_t)f * Bs.nb + b] = acc[b];
+}
+
 // U_0[i][q] at the collocation points; one CTA per element.
 __global__ void k_l2p_table(const Elem* __restrict__ el, int n, int nt, double k, const double* __restrict__ centres,
                             cd* __restrict__ U0) {
@@ -554,17 +591,15 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
-  if (m.nodes == 9 && m.q9_order > 0) {
-    set_error("multipole_tables: pressure of order 1 or 2 runs the PBEM form only");
-    return FMPB_EINVAL;
-  }
   if (m.nodes == 9 && centres) {
     set_error("multipole_tables: per-element expansion centres take flat triangles");
     return FMPB_EINVAL;
   }
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
-  if (V0 && m.nodes == 9)
+  if (V0 && m.nodes == 9 && m.q9_order > 0)
+    FMPB_LAUNCH("p2m_table_q9p", st, k_p2m_table_q9p<<<m.q9_ne, threads, 0, st>>>(m.q9_far, m.q9_ne, m.q9_order, nt, k, beta, m.q9r, V0));
+  else if (V0 && m.nodes == 9)
     FMPB_LAUNCH("p2m_table_q9", st, k_p2m_table_q9<<<m.n, threads, 0, st>>>(m.q9_far, m.n, nt, k, beta, V0));
   else if (V0)
     FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));

@@ -162,9 +162,9 @@ def test_q9_argument_errors():
     flat[0, :] = flat[0, 0]      # all nine nodes on one point: no Jacobian
     with pytest.raises(gb.FmpbError, match="EMESH"):
         gb.build_blocks_q9(nodes, flat, counts, LATTICE, 2.0, [[0, 0, 0]])
-    # refused before any device work: pressure of order 1, 2 with the FMM
-    # form, and an order that does not exist
+    # refused before any device work: pressure of order 1, 2 with the
+    # FMPBEM2 form, and an order that does not exist
     with pytest.raises(gb.FmpbError):
-        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM, pressure_order=1)
+        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM2, pressure_order=1)
     with pytest.raises(gb.FmpbError):
         gb.Operator(nodes, el, counts, LATTICE, 2.0, pressure_order=3)
