@@ -340,3 +340,65 @@ def field_points(nodes, elems, order, lattice, counts, k, p, points, direction, 
     D, _, S, _ = dhsk_block(tgt, Y, k)
     out = amp * np.exp(1j * k * (pts @ np.asarray(direction, dtype=np.float64)))
     return out + (D + 1j * k * beta * S) @ np.asarray(p)
+
+
+# ------------------------------------------------------------- half-space --
+# Eq. (green3dHalf): G_h(x, y) = G(x, y) + R_p G(x, y^).  The image
+# integrals over element E_f are integrals over y^ = M y(xi, eta) with the
+# normal R n(xi, eta) and the same area element and shapes N_b(xi, eta).  The
+# mirrored nodes are kept in their order, so that the shapes keep their
+# parameters; the Jacobian of the mirrored map is then -R J (a reflection
+# reverses orientation), so the computed normal is -R n and the terms linear
+# in n_y (D and H) change sign, while S and K (dG/dn_x) do not.  Shifts,
+# lattice roles and the block Hankel part are those of halfspace.py.
+
+def _image_entries(tgt, src_Y_mirrored, k, beta, Rp):
+    D, H, S, K = dhsk_block(tgt, src_Y_mirrored, k)
+    return Rp * bem._entries(-D, -H, S, K, k, beta)
+
+
+def image_block(cell: OrderMesh, lattice, counts, plane, dt, k, beta=0.0):
+    """T^(delta~): R_p times the entries of the cell's collocation points
+    against the reflected unit cell (R Y) shifted by shift(delta~)."""
+    from . import halfspace
+    src = plane.reflect(cell.geo.Y) + halfspace.image_shift(lattice, counts, plane, dt)[None, None, :]
+    return _image_entries(cell, src, k, beta, plane.Rp)
+
+
+def dense_matrix_halfspace(nodes, elems, order, lattice, counts, k, plane, beta=0.0):
+    """The dense collocation matrix of the whole array with G_h, pair by pair
+    over the array and its mirror image, without any structure."""
+    L = np.asarray(lattice, dtype=np.float64)
+    cells = bem.lattice_cells(counts)
+    nodes = np.asarray(nodes, dtype=np.float64)
+    allN = np.concatenate([nodes + np.asarray(c, dtype=np.float64) @ L for c in cells])
+    allE = np.concatenate([np.asarray(elems) + i * len(nodes) for i in range(len(cells))])
+    m = OrderMesh(allN, allE, order)
+    A = dense_matrix(allN, allE, order, k, beta)
+    return A + _image_entries(m, plane.mirror(m.geo.Y), k, beta, plane.Rp)
+
+
+def structured_matvec_halfspace(cell: OrderMesh, lattice, counts, k, plane, p, beta=0.0):
+    """(T + T^) p as two block Toeplitz products (Sec. 2.4): T p, and
+    (T^ P)(P p) with the cells reversed along the axis perpendicular to the
+    plane (none: P = identity)."""
+    from . import halfspace
+    p = np.atleast_2d(p)
+    h = halfspace.hankel_axis(lattice, counts, plane)
+    blocks = {d: toeplitz_block(cell, lattice, d, k, beta) for d in bem.all_offsets(counts)}
+    image = {d: image_block(cell, lattice, counts, plane, d, k, beta) for d in bem.all_offsets(counts)}
+    return (bem.toeplitz_matvec(blocks, counts, p)
+            + bem.toeplitz_matvec(image, counts, halfspace.reverse_cells(p, counts, h)))
+
+
+def incident_with_image(mesh: OrderMesh, k, direction, plane, amp=1.0):
+    """b = p_inc + b dp_inc/dn at the collocation points for the plane wave
+    amp e^{i k d.x} with its image R_p p_inc(M x)."""
+    d = np.asarray(direction, dtype=np.float64)
+    X, Nn = mesh.points, mesh.normals
+    p1 = amp * np.exp(1j * k * (X @ d))
+    dp1 = 1j * k * (Nn @ d) * p1
+    Xm, Nm = plane.mirror(X), plane.reflect(Nn)
+    p2 = amp * np.exp(1j * k * (Xm @ d))
+    dp2 = 1j * k * (Nm @ d) * p2
+    return (p1 + plane.Rp * p2) + bem.coupling(k) * (dp1 + plane.Rp * dp2)

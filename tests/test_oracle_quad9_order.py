@@ -250,3 +250,42 @@ def test_field_points_against_the_analytic_sphere(order, m, beta):
         # the admittance single layer is needed to reach the series
         no_s = qo.field_points(nodes, el, order, np.eye(3), (1, 1, 1), k, p, pts, [1.0, 0.0, 0.0])
         assert np.linalg.norm(no_s - ref) / np.linalg.norm(ref) > 5 * err
+
+
+@pytest.mark.parametrize("order,m", [(0, 2), (1, 2), (2, 1)])
+def test_halfspace_image_method(order, m):
+    # a sphere above a rigid plane (R_p = 1) has the surface solution of the
+    # sphere and its mirror image in full space under the incident wave and
+    # its image; the mirrored sphere of the full-space problem is wound
+    # outward by reversing xi, the image part keeps the node order and
+    # negates the terms linear in n_y (leaving that negation out moves the
+    # solution by 7e-2)
+    from oracle import halfspace
+    k, plane, d = 3.0, halfspace.Plane(2, -0.3, 1.0), np.array([0.6, 0.0, -0.8])
+    nodes, el = quad9_sphere(m, 0.2)
+    mesh = qo.OrderMesh(nodes, el, order)
+    Ah = (qo.toeplitz_block(mesh, np.eye(3), (0, 0, 0), k)
+          + qo.image_block(mesh, np.eye(3), (1, 1, 1), plane, (0, 0, 0), k))
+    ph = np.linalg.solve(Ah, qo.incident_with_image(mesh, k, d, plane))
+    rev = np.array([2, 1, 0, 5, 4, 3, 8, 7, 6])
+    N2 = np.concatenate([nodes, plane.mirror(nodes)])
+    E2 = np.concatenate([el, el[:, rev] + len(nodes)])
+    m2 = qo.OrderMesh(N2, E2, order)
+    e1, e2 = np.exp(1j * k * (m2.points @ d)), np.exp(1j * k * (plane.mirror(m2.points) @ d))
+    b2 = e1 + e2 + bem.coupling(k) * 1j * k * ((m2.normals @ d) * e1 + (plane.reflect(m2.normals) @ d) * e2)
+    p2 = np.linalg.solve(qo.dense_matrix(N2, E2, order, k), b2)
+    assert np.linalg.norm(ph - p2[:len(ph)]) / np.linalg.norm(ph) < 1e-9
+
+
+@pytest.mark.parametrize("counts,L", [((2, 1, 2), np.diag([0.5, 1.0, 0.45])), ((3, 2, 1), np.diag([0.5, 0.45, 1.0]))])
+def test_halfspace_structured_product_equals_the_dense_matrix(counts, L):
+    # Toeplitz part plus the image part (block Hankel along a perpendicular
+    # axis, applied to the cell-reversed vector) against the plain matrix
+    from oracle import halfspace
+    from workloads import random_complex_vectors
+    plane = halfspace.Plane(2, -0.3, 1.0)
+    nodes, el = quad9_sphere(1, 0.2)
+    A = qo.dense_matrix_halfspace(nodes, el, 1, L, counts, 3.0, plane, 0.3 + 0.2j)
+    x = random_complex_vectors(5, 1, A.shape[0])
+    y = qo.structured_matvec_halfspace(qo.OrderMesh(nodes, el, 1), L, counts, 3.0, plane, x, 0.3 + 0.2j)
+    assert np.linalg.norm(y - x @ A.T) / np.linalg.norm(x @ A.T) < 5e-9
