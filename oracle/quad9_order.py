@@ -402,3 +402,27 @@ def incident_with_image(mesh: OrderMesh, k, direction, plane, amp=1.0):
     p2 = amp * np.exp(1j * k * (Xm @ d))
     dp2 = 1j * k * (Nm @ d) * p2
     return (p1 + plane.Rp * p2) + bem.coupling(k) * (dp1 + plane.Rp * dp2)
+
+
+def field_points_halfspace(nodes, elems, order, lattice, counts, k, p, points, direction, plane, amp=1.0,
+                           beta=0.0):
+    """field_points with G_h: the incident wave and its image
+    R_p p_inc(M x), plus R_p times the surface's mirrored contribution (the
+    mirrored nodes in their order: D changes sign, S does not)."""
+    from types import SimpleNamespace
+    L = np.asarray(lattice, dtype=np.float64)
+    nodes = np.asarray(nodes, dtype=np.float64)
+    cells = bem.lattice_cells(counts)
+    allN = np.concatenate([nodes + np.asarray(c, dtype=np.float64) @ L for c in cells])
+    allE = np.concatenate([np.asarray(elems) + i * len(nodes) for i in range(len(cells))])
+    Y = allN[allE]
+    basis = PressureBasis(order)
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    tgt = SimpleNamespace(points=pts, normals=np.tile([0.0, 0.0, 1.0], (len(pts), 1)), basis=basis,
+                          nb=basis.nb, n=0)
+    d = np.asarray(direction, dtype=np.float64)
+    out = amp * (np.exp(1j * k * (pts @ d)) + plane.Rp * np.exp(1j * k * (plane.mirror(pts) @ d)))
+    D, _, S, _ = dhsk_block(tgt, Y, k)
+    Dm, _, Sm, _ = dhsk_block(tgt, plane.mirror(Y), k)
+    p = np.asarray(p)
+    return out + (D + 1j * k * beta * S) @ p + plane.Rp * ((-Dm + 1j * k * beta * Sm) @ p)

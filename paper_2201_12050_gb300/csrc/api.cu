@@ -372,8 +372,10 @@ namespace fmpb {
 // checks that every cell lies on one side of the plane, and uploads the
 // reflected unit cell (R v, reversed winding, so that its element normals are
 // R n and the quadrature rules apply unchanged).
+// npe: nodes per element (3: triangles, the centroid; 9: nine-node
+// quadrilaterals, the centre node 4).
 static fmpb_status halfspace_check(const CellGrid& g, const fmpb_operator_opts& o, const double* verts, int64_t nv,
-                                   const int32_t* tris, int64_t ntri, int* hankel) {
+                                   const int32_t* tris, int64_t ntri, int* hankel, int npe = 3) {
   const int ax = o.plane_axis;
   if (ax < 0 || ax > 2 || !std::isfinite(o.plane_offset) || !std::isfinite(o.Rp_re) || !std::isfinite(o.Rp_im)) {
     set_error("operator_create: half-space needs plane_axis 0..2 and finite plane_offset, R_p");
@@ -408,7 +410,9 @@ static fmpb_status halfspace_check(const CellGrid& g, const fmpb_operator_opts& 
     scale = fmax(scale, fabs(verts[3 * v + ax]));
   }
   for (int64_t t = 0; t < ntri; ++t) {
-    const double c = (verts[3 * tris[3 * t] + ax] + verts[3 * tris[3 * t + 1] + ax] + verts[3 * tris[3 * t + 2] + ax]) / 3.0;
+    const double c = npe == 9 ? verts[3 * (int64_t)tris[9 * t + 4] + ax]
+                              : (verts[3 * tris[3 * t] + ax] + verts[3 * tris[3 * t + 1] + ax] +
+                                 verts[3 * tris[3 * t + 2] + ax]) / 3.0;
     cmin = fmin(cmin, c);
     cmax = fmax(cmax, c);
   }
@@ -427,10 +431,19 @@ static fmpb_status halfspace_check(const CellGrid& g, const fmpb_operator_opts& 
 static fmpb_status setup_halfspace(fmpb_operator* op, const fmpb_operator_opts& o, const double* verts, int64_t nv,
                                    const int32_t* tris, int64_t ntri, cudaStream_t st) {
   int h = -1;
-  FMPB_TRY(halfspace_check(op->grid, o, verts, nv, tris, ntri, &h));
+  const bool quad9 = o.element == FMPB_ELEM_QUAD9;
+  FMPB_TRY(halfspace_check(op->grid, o, verts, nv, tris, ntri, &h, quad9 ? 9 : 3));
   const int ax = o.plane_axis;
   std::vector<double> rv(verts, verts + 3 * nv);
   for (int64_t v = 0; v < nv; ++v) rv[3 * v + ax] = -rv[3 * v + ax];
+  if (quad9) {
+    // nine-node cells keep their node order (the shapes keep their
+    // parameters); the image kernels change the sign of D and H instead
+    FMPB_TRY(upload_mesh_q9p(rv.data(), nv, tris, ntri, o.pressure_order, op->refl, st));
+    op->plane = PlaneDev{1, ax, o.plane_offset, mkc(o.Rp_re, o.Rp_im)};
+    op->hankel = h;
+    return FMPB_OK;
+  }
   std::vector<int32_t> rt(3 * ntri);
   for (int64_t t = 0; t < ntri; ++t) {
     rt[3 * t] = tris[3 * t];
@@ -518,10 +531,10 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   const bool quad9 = o.element == FMPB_ELEM_QUAD9;
   CHECK_ARG(o.pressure_order == 0 || (quad9 && (o.pressure_order == 1 || o.pressure_order == 2)),
             "operator_create: pressure of order 1 or 2 takes FMPB_ELEM_QUAD9 elements");
-  CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && !o.halfspace && o.precision != FMPB_BF16 &&
-                       !(o.form == FMPB_FORM_FMM && o.precision == FMPB_MIXED)),
-            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED) or the FMM form "
-            "(FP64 or FP32), in full space");
+  CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && o.precision != FMPB_BF16 &&
+                       !(o.form == FMPB_FORM_FMM && (o.precision == FMPB_MIXED || o.halfspace))),
+            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED; full or half "
+            "space) or the FMM form (FP64 or FP32, full space)");
   const cd beta = mkc(o.beta_re, o.beta_im);
   cudaStream_t st = (cudaStream_t)stream;
   fmpb_operator* op = new (std::nothrow) fmpb_operator();

@@ -124,12 +124,19 @@ fmpb_status upload_mesh_q9(const double* nodes, int64_t nn, const int32_t* elems
 // The same with discontinuous pressure of order 1 or 2 (quad9p.cu).
 fmpb_status upload_mesh_q9p(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, int order,
                             DeviceMesh& m, cudaStream_t st);
+struct ImageBlocks;
+// With img (every order, 0 included): the image blocks of m's collocation
+// points against the mirrored cell img->source (nodes R Y in their order).
 fmpb_status build_blocks_q9p(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
-                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);
+                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
+                             const ImageBlocks* img = nullptr);
 // out[r][p] += the scattered pressure of the surface solution surf at the
-// points (nine-node meshes of any pressure order; full space).
-fmpb_status field_scattered_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
-                               int64_t npts, const double* pts, cd* out, cudaStream_t st);
+// points (nine-node meshes of any pressure order; with pl.on also R_p times
+// the part of the mirrored cell refl).
+struct PlaneDev;
+fmpb_status field_scattered_q9(const DeviceMesh& m, const DeviceMesh* refl, const PlaneDev& pl, const CellGrid& g,
+                               double k, cd beta, int R, const cd* surf, int64_t npts, const double* pts, cd* out,
+                               cudaStream_t st);
 // build_blocks for a nine-node mesh (full space only).
 fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st);

@@ -48,22 +48,28 @@ __global__ void k_q9p_colloc(const Q9Elem* __restrict__ q9, int ne, int order, E
   el[r] = E;
 }
 
-// Stores the nb entries of row r, columns f nb .. f nb + nb - 1.
+// Entry of one column: dsign = -1 for the mirrored source cell of a
+// half-space operator, whose nodes keep their order so that its computed
+// normal is -R n (the terms linear in n_y, D and H, change sign).
 template <bool SK>
-__device__ __forceinline__ void q9p_store(cd* row, int nb, const cd* D, const cd* H, const cd* S, const cd* K,
-                                          double k, cd beta) {
-  for (int c = 0; c < nb; ++c) row[c] = SK ? bm_entry_adm(D[c], H[c], S[c], K[c], k, beta) : bm_entry(D[c], H[c], k);
+__device__ __forceinline__ cd q9p_entry(cd D, cd H, cd S, cd K, double dsign, double k, cd beta) {
+  D = cmulr(D, dsign);
+  H = cmulr(H, dsign);
+  return SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
 }
 
-// One thread per item (o, r, f): offset o, collocation dof r, source
-// element f; block o goes to out + dest[o] N N (N = ne nb dofs).  The
-// items of a dof's own element in the zero offset are left to k_q9p_self.
+// One thread per item (o, r, f): offset o, collocation dof r (el), source
+// element f (q9, far_tab: the cell itself, or the mirrored cell of a
+// half-space operator); block o goes to out + dest[o] N N (N = ne nb dofs),
+// stored by bw.  The items of a dof's own element in the zero offset are
+// left to k_q9p_self.
 template <bool SK>
 __global__ void __launch_bounds__(128) k_q9p_blocks(const Elem* __restrict__ el, const Q9Elem* __restrict__ q9,
                                                     const double* __restrict__ far_tab, int ne, int order,
                                                     const double* __restrict__ shifts,
                                                     const int64_t* __restrict__ dest, int n_off, int zero_off,
                                                     cd* __restrict__ out, double k, cd beta, Q9Rules R,
+                                                    double dsign, BlockWrite bw,
                                                     unsigned long long* __restrict__ near_list,
                                                     unsigned long long* __restrict__ near_count,
                                                     unsigned long long near_cap) {
@@ -120,7 +126,8 @@ __global__ void __launch_bounds__(128) k_q9p_blocks(const Elem* __restrict__ el,
       }
       q9p_near_sum<SK>(F.Y, B, R, dist < NEAR_RATIO * F.hmax, x, nx, sh, k, 0, 1, D, H, S, K);
     }
-    q9p_store<SK>(out + (size_t)dest[o] * N * N + (size_t)r * N + (size_t)f * nb, nb, D, H, S, K, k, beta);
+    cd* row = out + (size_t)dest[o] * N * N + (size_t)r * N + (size_t)f * nb;
+    for (int c = 0; c < nb; ++c) bw.put(row + c, q9p_entry<SK>(D[c], H[c], S[c], K[c], dsign, k, beta));
   }
 }
 
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(256) k_q9p_near(const Elem* __restrict__ el, c
                                                   const unsigned long long* __restrict__ list,
                                                   const unsigned long long* __restrict__ count,
                                                   unsigned long long cap, cd* __restrict__ out, double k, cd beta,
-                                                  Q9Rules R) {
+                                                  Q9Rules R, double dsign, BlockWrite bw) {
   const Q9Basis B = q9p_basis(order);
   const int nb = B.nb;
   const size_t N = (size_t)ne * nb;
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(256) k_q9p_near(const Elem* __restrict__ el, c
     }
     cd* row = out + (size_t)dest[o] * N * N + (size_t)r * N + (size_t)f * nb;
     for (int c = 0; c < nb; ++c)
-      if (lane == c) row[c] = SK ? bm_entry_adm(D[c], H[c], S[c], K[c], k, beta) : bm_entry(D[c], H[c], k);
+      if (lane == c) bw.put(row + c, q9p_entry<SK>(D[c], H[c], S[c], K[c], dsign, k, beta));
   }
 }
 
@@ -215,9 +222,13 @@ __global__ void __launch_bounds__(256) k_q9p_self(const Q9Elem* __restrict__ q9,
 
 // Scattered pressure at field points added to out[r][p] (which holds the
 // incident field): one CTA per (rhs, point), the threads split the (cell,
-// element) items, the partial sums are reduced in a fixed order.
+// element) items, the partial sums are reduced in a fixed order.  With a
+// plane, R_p times the same over the mirrored cell (refl: nodes R Y in their
+// order), placed for cell c at its position with the axis component
+// 2 offset - pos[axis].
 template <bool SK>
-__global__ void __launch_bounds__(256) k_field_q9(const Q9Elem* __restrict__ q9, int ne, int order, CellGrid g,
+__global__ void __launch_bounds__(256) k_field_q9(const Q9Elem* __restrict__ q9, const Q9Elem* __restrict__ refl,
+                                                  PlaneDev pl, int ne, int order, CellGrid g,
                                                   double k, cd beta, int R, const cd* __restrict__ surf,
                                                   int64_t npts, const double* __restrict__ pts, cd* __restrict__ out,
                                                   Q9Rules Rq) {
@@ -238,7 +249,12 @@ __global__ void __launch_bounds__(256) k_field_q9(const Q9Elem* __restrict__ q9,
       g.cell_position(c, pos);
       const Q9Elem& F = q9[f];
       const cd* pd = surf + (size_t)r * N + ((size_t)c * ne + f) * nb;
-      part = cadd(part, q9_field_element<SK>(F.Y, F.c, F.hmax, order, Rq, x, pos, k, ikb, pd));
+      part = cadd(part, q9_field_element<SK>(F.Y, F.c, F.hmax, order, Rq, x, pos, k, ikb, 1.0, pd));
+      if (pl.on) {
+        const Q9Elem& Fm = refl[f];
+        pos[pl.axis] = 2.0 * pl.offset - pos[pl.axis];
+        part = cfma(pl.Rp, q9_field_element<SK>(Fm.Y, Fm.c, Fm.hmax, order, Rq, x, pos, k, ikb, -1.0, pd), part);
+      }
     }
     sre[threadIdx.x] = part.x;
     sim[threadIdx.x] = part.y;
@@ -256,19 +272,21 @@ __global__ void __launch_bounds__(256) k_field_q9(const Q9Elem* __restrict__ q9,
 }
 
 // ------------------------------------------------------------ host side --
-fmpb_status field_scattered_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int R, const cd* surf,
-                               int64_t npts, const double* pts, cd* out, cudaStream_t st) {
-  if (m.nodes != 9 || !m.q9) {
-    set_error("field: not a nine-node mesh");
+fmpb_status field_scattered_q9(const DeviceMesh& m, const DeviceMesh* refl, const PlaneDev& pl, const CellGrid& g,
+                               double k, cd beta, int R, const cd* surf, int64_t npts, const double* pts, cd* out,
+                               cudaStream_t st) {
+  if (m.nodes != 9 || !m.q9 || (pl.on && (!refl || !refl->q9 || refl->q9_ne != m.q9_ne))) {
+    set_error("field: not a nine-node mesh, or a half-space operator without its mirrored cell");
     return FMPB_EINVAL;
   }
+  const Q9Elem* rq = pl.on ? refl->q9 : m.q9;
   const int64_t total = npts * R;
   if (total <= 0) return FMPB_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>(total, 152 * 16);
   if (beta.x == 0.0 && beta.y == 0.0)
-    FMPB_LAUNCH("field_q9", st, k_field_q9<false><<<blocks, 256, 0, st>>>(m.q9, m.q9_ne, m.q9_order, g, k, beta, R, surf, npts, pts, out, m.q9r));
+    FMPB_LAUNCH("field_q9", st, k_field_q9<false><<<blocks, 256, 0, st>>>(m.q9, rq, pl, m.q9_ne, m.q9_order, g, k, beta, R, surf, npts, pts, out, m.q9r));
   else
-    FMPB_LAUNCH("field_q9_adm", st, k_field_q9<true><<<blocks, 256, 0, st>>>(m.q9, m.q9_ne, m.q9_order, g, k, beta, R, surf, npts, pts, out, m.q9r));
+    FMPB_LAUNCH("field_q9_adm", st, k_field_q9<true><<<blocks, 256, 0, st>>>(m.q9, rq, pl, m.q9_ne, m.q9_order, g, k, beta, R, surf, npts, pts, out, m.q9r));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -300,20 +318,29 @@ fmpb_status upload_mesh_q9p(const double* nodes, int64_t nn, const int32_t* elem
 }
 
 fmpb_status build_blocks_q9p(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
-                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st) {
+                             const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
+                             const ImageBlocks* img) {
   const int ne = m.q9_ne, order = m.q9_order;
-  if (m.nodes != 9 || !m.q9 || order < 1 || order > 2 || (int64_t)ne * q9p_basis(order).nb != m.n) {
-    set_error("build_blocks_q9p: not a nine-node mesh with pressure of order 1 or 2");
+  const DeviceMesh& src = img ? *img->source : m;
+  if (m.nodes != 9 || !m.q9 || order < (img ? 0 : 1) || order > 2 || (int64_t)ne * q9p_basis(order).nb != m.n ||
+      src.nodes != 9 || !src.q9 || src.q9_ne != ne || src.q9_order != order) {
+    set_error("build_blocks_q9p: not a nine-node mesh with pressure of order 1 or 2 (0 too for image blocks), "
+              "or a mirrored cell that differs from it");
     return FMPB_EINVAL;
   }
   const size_t N = (size_t)m.n;
+  // shifts: -delta . lattice, or the image shifts given by the caller
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
   for (int o = 0; o < n_off; ++o) {
     const int32_t* dl = offsets + 3 * o;
-    if (dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
-    for (int d = 0; d < 3; ++d) shifts[3 * o + d] = -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
+    if (!img && dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
+    for (int d = 0; d < 3; ++d)
+      shifts[3 * o + d] = img ? img->shifts[3 * o + d]
+                              : -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
   }
+  const BlockWrite bw = img ? BlockWrite{img->scale, 1, img->accumulate ? 1 : 0} : BlockWrite{mkc(1.0, 0.0), 0, 0};
+  const double dsign = img ? -1.0 : 1.0;
   double* dshift = nullptr;
   int64_t* ddest = nullptr;
   FMPB_CUDA(cudaMalloc(&dshift, sizeof(double) * 3 * n_off));
@@ -333,12 +360,12 @@ fmpb_status build_blocks_q9p(const DeviceMesh& m, const CellGrid& g, double k, c
     const Q9Rules& R = m.q9r;
     cd* block0 = zero_off >= 0 ? out + (size_t)dest_host[zero_off] * N * N : nullptr;
     if (beta.x == 0.0 && beta.y == 0.0) {
-      FMPB_LAUNCH("q9p_blocks", st, k_q9p_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.q9, m.q9_far, ne, order, dshift, ddest, n_off, zero_off, out, k, beta, R, near_list, near_count, near_cap));
-      FMPB_LAUNCH("q9p_near", st, k_q9p_near<false><<<152 * 16, 256, 0, st>>>(m.el, m.q9, ne, order, dshift, ddest, near_list, near_count, near_cap, out, k, beta, R));
+      FMPB_LAUNCH("q9p_blocks", st, k_q9p_blocks<false><<<blocks, 128, 0, st>>>(m.el, src.q9, src.q9_far, ne, order, dshift, ddest, n_off, zero_off, out, k, beta, R, dsign, bw, near_list, near_count, near_cap));
+      FMPB_LAUNCH("q9p_near", st, k_q9p_near<false><<<152 * 16, 256, 0, st>>>(m.el, src.q9, ne, order, dshift, ddest, near_list, near_count, near_cap, out, k, beta, R, dsign, bw));
       if (block0) FMPB_LAUNCH("q9p_self", st, k_q9p_self<false><<<self_blocks, 256, 0, st>>>(m.q9, ne, order, block0, k, beta, R));
     } else {
-      FMPB_LAUNCH("q9p_blocks_adm", st, k_q9p_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.q9, m.q9_far, ne, order, dshift, ddest, n_off, zero_off, out, k, beta, R, near_list, near_count, near_cap));
-      FMPB_LAUNCH("q9p_near_adm", st, k_q9p_near<true><<<152 * 16, 256, 0, st>>>(m.el, m.q9, ne, order, dshift, ddest, near_list, near_count, near_cap, out, k, beta, R));
+      FMPB_LAUNCH("q9p_blocks_adm", st, k_q9p_blocks<true><<<blocks, 128, 0, st>>>(m.el, src.q9, src.q9_far, ne, order, dshift, ddest, n_off, zero_off, out, k, beta, R, dsign, bw, near_list, near_count, near_cap));
+      FMPB_LAUNCH("q9p_near_adm", st, k_q9p_near<true><<<152 * 16, 256, 0, st>>>(m.el, src.q9, ne, order, dshift, ddest, near_list, near_count, near_cap, out, k, beta, R, dsign, bw));
       if (block0) FMPB_LAUNCH("q9p_self_adm", st, k_q9p_self<true><<<self_blocks, 256, 0, st>>>(m.q9, ne, order, block0, k, beta, R));
     }
     e = cudaGetLastError();

@@ -26,22 +26,29 @@ constexpr int Q9P_MAXNB = 8;
 constexpr int Q9P_Q = 24;               // self rule: nodes per direction
 constexpr int Q9P_THETA = 4 * Q9P_Q;    // angular nodes of the self rule
 
+// Order 0 (one constant per element at the centre, N = 1) is included for
+// the kernels that serve every order (image blocks, field points).
 struct Q9Basis {
-  int order;   // 1 or 2
-  int nb;      // 4 or 8
-  double s;    // node half-width: 1/sqrt(3) or sqrt(3/5)
+  int order;   // 0, 1 or 2
+  int nb;      // 1, 4 or 8
+  double s;    // node half-width: 0, 1/sqrt(3) or sqrt(3/5)
 };
 
 __host__ __device__ inline Q9Basis q9p_basis(int order) {
   Q9Basis b;
   b.order = order;
-  b.nb = order == 1 ? 4 : 8;
-  b.s = order == 1 ? 1.0 / sqrt(3.0) : sqrt(3.0 / 5.0);
+  b.nb = order == 0 ? 1 : order == 1 ? 4 : 8;
+  b.s = order == 0 ? 0.0 : order == 1 ? 1.0 / sqrt(3.0) : sqrt(3.0 / 5.0);
   return b;
 }
 
 // Parameter coordinates of node a.
 __host__ __device__ inline void q9p_node(const Q9Basis& B, int a, double* xi, double* eta) {
+  if (B.order == 0) {
+    *xi = 0.0;
+    *eta = 0.0;
+    return;
+  }
   if (B.order == 1) {
     *xi = (a & 1) ? B.s : -B.s;
     *eta = (a & 2) ? B.s : -B.s;
@@ -56,6 +63,11 @@ __host__ __device__ inline void q9p_node(const Q9Basis& B, int a, double* xi, do
 // N_b and, if G is not null, dN_b/dxi, dN_b/deta at (xi, eta).
 __host__ __device__ inline void q9p_shape(const Q9Basis& B, double xi, double eta, double N[Q9P_MAXNB],
                                           double G[Q9P_MAXNB][2]) {
+  if (B.order == 0) {
+    N[0] = 1.0;
+    if (G) G[0][0] = G[0][1] = 0.0;
+    return;
+  }
   if (B.order == 1) {
     const double h = 0.5 / B.s;
     const double l[2] = {(B.s - xi) * h, (B.s + xi) * h};
@@ -100,7 +112,8 @@ __host__ __device__ inline void q9p_shape(const Q9Basis& B, double xi, double et
 }
 
 // Parameter point and weight of point p of the very-near rule of an order:
-// parts x parts sub-squares (parts = 4 or 8), 8 x 8 Gauss-Legendre each,
+// parts x parts sub-squares (parts = 2, 4 or 8; 2 is the quarter rule of
+// order 0, in the same order), 8 x 8 Gauss-Legendre each,
 // sub-square (i, j) at p / 64 = j parts + i, point (a, b) at p % 64 = 8 a + b.
 __host__ __device__ inline void q9p_vnear_point(const Q9Rules& R, int parts, int p, double* xi, double* eta,
                                                 double* w) {
@@ -121,7 +134,7 @@ __host__ __device__ inline void q9p_near_sum(const double Y[9][3], const Q9Basis
                                              int p0, int stride, cd* D, cd* H, cd* S, cd* K) {
   double am[9][3];
   q9_monomials(Y, am);
-  const int parts = B.order == 1 ? 4 : 8;
+  const int parts = B.order == 0 ? 2 : B.order == 1 ? 4 : 8;
   const int npts = very ? 64 * parts * parts : 64;
   for (int p = p0; p < npts; p += stride) {
     double xi, eta, w;
@@ -154,11 +167,12 @@ __host__ __device__ inline void q9p_near_sum(const double Y[9][3], const Q9Basis
 // by sh) to the pressure at a field point x: int (dG/dn_y + i k beta G) p dA
 // with p = sum_b N_b pd[b] (order 0: p = pd[0]), by the class rules of the
 // collocation points (order 0: quarters for the very-near class; orders 1, 2:
-// their sub-squares).  ikb = i k beta; SK: with the single layer.
+// their sub-squares).  ikb = i k beta; SK: with the single layer; dsign = -1
+// for a mirrored element whose nodes kept their order (computed normal -R n).
 template <bool SK>
 __host__ __device__ inline cd q9_field_element(const double Y[9][3], const double cen[3], double hmax, int order,
                                                const Q9Rules& R, const double x[3], const double sh[3], double k,
-                                               cd ikb, const cd* pd) {
+                                               cd ikb, double dsign, const cd* pd) {
   double dc[3];
   for (int d = 0; d < 3; ++d) dc[d] = x[d] - (cen[d] + sh[d]);
   const double dist = sqrt(q9_dot(dc, dc));
@@ -191,6 +205,7 @@ __host__ __device__ inline cd q9_field_element(const double Y[9][3], const doubl
       dens = mkc(0.0, 0.0);
       for (int b = 0; b < B.nb; ++b) dens = cadd(dens, cmulr(pd[b], N[b]));
     }
+    Dp = cmulr(Dp, dsign);
     const cd g = SK ? cfma(ikb, Sp, Dp) : Dp;
     acc = cfma(g, dens, acc);
   }

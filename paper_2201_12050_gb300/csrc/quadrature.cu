@@ -958,10 +958,7 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
                          const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
                          const ImageBlocks* img) {
   if (m.nodes == 9) {
-    if (img) {
-      set_error("build_blocks: half-space image blocks take flat triangles");
-      return FMPB_EINVAL;
-    }
+    if (img) return build_blocks_q9p(m, g, k, beta, n_off, offsets, dest_host, out, st, img);
     return build_blocks_q9(m, g, k, beta, n_off, offsets, dest_host, out, st);
   }
   // shifts: -delta . lattice, or the image shifts given by the caller
@@ -1121,17 +1118,14 @@ fmpb_status field_incident(const DeviceMesh& m, const DeviceMesh* refl, const Ce
     return FMPB_EINVAL;
   }
   if (m.nodes == 9) {
-    // nine-node quadrilaterals: the incident field, then the scattered part added
-    if (pl.on) {
-      set_error("field: nine-node quadrilaterals run in full space");
-      return FMPB_EINVAL;
-    }
+    // nine-node quadrilaterals: the incident field (with its image), then the
+    // scattered part added
     IncDev* dq = nullptr;
     FMPB_TRY(upload_incident(R, inc, k, &dq, st));
     const int64_t tq = (int64_t)npts * R;
     FMPB_LAUNCH("incident_points", st, k_incident_points<<<(unsigned)std::min<int64_t>((tq + 255) / 256, 152 * 32), 256, 0, st>>>(dq, pl, k, R, npts, pts, out));
     FMPB_CUDA(cudaGetLastError());
-    FMPB_TRY(field_scattered_q9(m, g, k, beta, R, surf, npts, pts, out, st));
+    FMPB_TRY(field_scattered_q9(m, refl, pl, g, k, beta, R, surf, npts, pts, out, st));
     FMPB_CUDA(cudaFreeAsync(dq, st));
     return FMPB_OK;
   }

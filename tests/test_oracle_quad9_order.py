@@ -289,3 +289,30 @@ def test_halfspace_structured_product_equals_the_dense_matrix(counts, L):
     x = random_complex_vectors(5, 1, A.shape[0])
     y = qo.structured_matvec_halfspace(qo.OrderMesh(nodes, el, 1), L, counts, 3.0, plane, x, 0.3 + 0.2j)
     assert np.linalg.norm(y - x @ A.T) / np.linalg.norm(x @ A.T) < 5e-9
+
+
+@pytest.mark.parametrize("order,m", [(0, 2), (2, 1)])
+def test_halfspace_field_points_image_method(order, m):
+    # the half-space field of a sphere above a rigid plane equals the
+    # full-space field of the sphere pair under the wave and its image
+    from oracle import halfspace
+    k, plane, d = 3.0, halfspace.Plane(2, -0.3, 1.0), np.array([0.6, 0.0, -0.8])
+    nodes, el = quad9_sphere(m, 0.2)
+    mesh = qo.OrderMesh(nodes, el, order)
+    Ah = (qo.toeplitz_block(mesh, np.eye(3), (0, 0, 0), k)
+          + qo.image_block(mesh, np.eye(3), (1, 1, 1), plane, (0, 0, 0), k))
+    ph = np.linalg.solve(Ah, qo.incident_with_image(mesh, k, d, plane))
+    rev = np.array([2, 1, 0, 5, 4, 3, 8, 7, 6])
+    N2 = np.concatenate([nodes, plane.mirror(nodes)])
+    E2 = np.concatenate([el, el[:, rev] + len(nodes)])
+    m2 = qo.OrderMesh(N2, E2, order)
+    e1, e2 = np.exp(1j * k * (m2.points @ d)), np.exp(1j * k * (plane.mirror(m2.points) @ d))
+    b2 = e1 + e2 + bem.coupling(k) * 1j * k * ((m2.normals @ d) * e1 + (plane.reflect(m2.normals) @ d) * e2)
+    p2 = np.linalg.solve(qo.dense_matrix(N2, E2, order, k), b2)
+    rng = np.random.default_rng(2)
+    pts = rng.uniform(-0.6, 0.6, (10, 3))
+    pts[:, 2] = rng.uniform(-0.25, 0.6, 10)
+    pts = pts[np.linalg.norm(pts, axis=1) > 0.23]
+    fh = qo.field_points_halfspace(nodes, el, order, np.eye(3), (1, 1, 1), k, ph, pts, d, plane)
+    f2 = qo.field_points(N2, E2, order, np.eye(3), (1, 1, 1), k, p2, pts, d) + np.exp(1j * k * (plane.mirror(pts) @ d))
+    assert np.abs(fh - f2).max() <= 1e-9 * np.abs(f2).max()
