@@ -285,16 +285,18 @@ class _Colloc:
         self.centroid, self.normal = mesh.points, mesh.normals
 
 
-def p2m_table(mesh: OrderMesh, k, nt, beta=0.0):
+def p2m_table(mesh: OrderMesh, k, nt, beta=0.0, dsign=1.0):
     """V_0 (B x n nb) of Eq. (p2m) with the pressure shapes: column f nb + b
     integrates N_b conj(dI_q/dn_y) (+ i k beta N_b conj(I_q)) over element f
-    with the far-class rule (4 x 4 Gauss-Legendre), each point's normal."""
+    with the far-class rule (4 x 4 Gauss-Legendre), each point's normal;
+    dsign = -1 for a mirrored cell whose nodes kept their order (its computed
+    normal is -R n: only the double-layer term changes sign)."""
     xi, eta, w0 = quad9.tensor_rule(quad9.Q_FAR4)
     y, ny, w = quad9._batch_rule(mesh.geo.Y, "far")        # n x 16 x 3, n x 16 x 3, n x 16
     N, _ = mesh.basis.eval(xi, eta)                          # nb x 16
     from . import special as sp
     g = sp.grad_regular_table(nt, y, k)                      # B x n x 16 x 3
-    src = np.conj(np.einsum("bnqi,nqi->bnq", g, ny))
+    src = dsign * np.conj(np.einsum("bnqi,nqi->bnq", g, ny))
     if beta != 0:
         I = sp.wave_table(nt, y.reshape(-1, 3), k, "I").reshape(-1, *w.shape)
         src = src + 1j * k * beta * np.conj(I)
@@ -426,3 +428,40 @@ def field_points_halfspace(nodes, elems, order, lattice, counts, k, p, points, d
     Dm, _, Sm, _ = dhsk_block(tgt, plane.mirror(Y), k)
     p = np.asarray(p)
     return out + (D + 1j * k * beta * S) @ p + plane.Rp * ((-Dm + 1j * k * beta * Sm) @ p)
+
+
+def fmm_image_matvec_explicit(cell: OrderMesh, lattice, counts, k, nt, plane, p, beta=0.0):
+    """The image part of Eq. (2dPeriodicFMM_halfspace), (S^ + U K^ V^) p, over
+    every (target cell, mirrored source cell) pair (halfspace.py's near set
+    and M2L translations): near pairs by image_block, far pairs through
+    U_0 K^ V^ with V^ = R_p times the P2M table of the reflected cell."""
+    from . import fmm, halfspace
+    p = np.atleast_2d(p)
+    h = halfspace.hankel_axis(lattice, counts, plane)
+    q = halfspace.reverse_cells(p, counts, h)
+    cells = bem.lattice_cells(counts)
+    n = cell.n * cell.nb
+    R = p.shape[0]
+    Q = q.reshape(R, len(cells), n)
+    near = set(halfspace.image_near_offsets(lattice, counts, plane))
+    refl = OrderMesh(plane.reflect(cell.geo.nodes), cell.geo.elems, cell.basis.order)
+    V0h = plane.Rp * p2m_table(refl, k, nt, beta, dsign=-1.0)
+    U0 = fmm.l2p_table(_Colloc(cell), k, nt)
+    Mom = Q @ V0h.T
+    Y = np.zeros((R, len(cells), n), dtype=complex)
+    cache = {}
+    for ci, c in enumerate(cells):
+        Lc = np.zeros((R, V0h.shape[0]), dtype=complex)
+        for cj, cq in enumerate(cells):
+            dt = tuple(a - b for a, b in zip(c, cq))
+            if dt in near:
+                if dt not in cache:
+                    cache[dt] = image_block(cell, lattice, counts, plane, dt, k, beta)
+                Y[:, ci] += Q[:, cj] @ cache[dt].T
+            else:
+                key = ("K", dt)
+                if key not in cache:
+                    cache[key] = fmm.m2l_block(-halfspace.image_shift(lattice, counts, plane, dt), k, nt)
+                Lc += Mom[:, cj] @ cache[key].T
+        Y[:, ci] += Lc @ U0.T
+    return Y.reshape(R, -1)

@@ -316,3 +316,23 @@ def test_halfspace_field_points_image_method(order, m):
     fh = qo.field_points_halfspace(nodes, el, order, np.eye(3), (1, 1, 1), k, ph, pts, d, plane)
     f2 = qo.field_points(N2, E2, order, np.eye(3), (1, 1, 1), k, p2, pts, d) + np.exp(1j * k * (plane.mirror(pts) @ d))
     assert np.abs(fh - f2).max() <= 1e-9 * np.abs(f2).max()
+
+
+@pytest.mark.parametrize("order,counts", [(1, (4, 1, 1)), (2, (1, 1, 4))])
+def test_fmm_image_product_tends_to_the_exact_image_part(order, counts):
+    # the image part of the FMPBEM with V^ = R_p P2M of the reflected cell
+    # (sign change on its double-layer term) converges to the exact image
+    # blocks' product; a perpendicular axis (1, 1, 4) exercises the Hankel
+    # part; without the sign change the product stalls near 0.2
+    from oracle import halfspace
+    from workloads import random_complex_vectors
+    nodes, el = quad9_sphere(1, 0.2)
+    plane = halfspace.Plane(2, -0.3, 0.8 - 0.3j)
+    cell = qo.OrderMesh(nodes, el, order)
+    L = np.eye(3)
+    image = {d: qo.image_block(cell, L, counts, plane, d, 2.0, 0.3j) for d in bem.all_offsets(counts)}
+    x = random_complex_vectors(9, 1, cell.n * cell.nb * 4)
+    exact = bem.toeplitz_matvec(image, counts, halfspace.reverse_cells(x, counts, halfspace.hankel_axis(L, counts, plane)))
+    errs = [np.linalg.norm(qo.fmm_image_matvec_explicit(cell, L, counts, 2.0, nt, plane, x, 0.3j) - exact)
+            / np.linalg.norm(exact) for nt in (4, 8, 12)]
+    assert errs[1] < 1e-3 * errs[0] and errs[2] < 1e-12, errs
