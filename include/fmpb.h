@@ -165,9 +165,9 @@ typedef struct {
    * FMPB_ELEM_QUAD9 `tris` holds ntri x 9 node indices per element (node
    * (i, j) of its 3 x 3 grid at 3 j + i, i along xi, parameter values -1, 0,
    * 1; y_xi x y_eta into the fluid).  Such operators run in the PBEM form
-   * (FP64, FP32 or MIXED; AUTO picks it; full or half space) or the FMM form
-   * (FP64 or FP32, full space; its P2M table integrates each element with
-   * the 4 x 4 far-class rule and each point's normal).  Field points and the
+   * (FP64, FP32 or MIXED; AUTO picks it) or the FMM form (FP64 or FP32; its
+   * P2M table integrates each element with the 4 x 4 far-class rule and each
+   * point's normal), in full or half space.  Field points and the
    * insertion loss take every pressure order, in full and half space. */
   int32_t element;
   /* Order of the discontinuous pressure on FMPB_ELEM_QUAD9 elements (0,
@@ -175,8 +175,7 @@ typedef struct {
    * at +-1/sqrt(3), bilinear; 2: the eight-node serendipity element on
    * [-sqrt(3/5), sqrt(3/5)]^2), collocated at the nodes with dof e nb + a.
    * Every order runs the PBEM and FMM forms of FMPB_ELEM_QUAD9 (the P2M table
-   * weights the far rule by each shape N_b); with halfspace = 1 the PBEM
-   * form only. */
+   * weights the far rule by each shape N_b). */
   int32_t pressure_order;
 } fmpb_operator_opts;
 

@@ -532,9 +532,9 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(o.pressure_order == 0 || (quad9 && (o.pressure_order == 1 || o.pressure_order == 2)),
             "operator_create: pressure of order 1 or 2 takes FMPB_ELEM_QUAD9 elements");
   CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && o.precision != FMPB_BF16 &&
-                       !(o.form == FMPB_FORM_FMM && (o.precision == FMPB_MIXED || o.halfspace))),
-            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED; full or half "
-            "space) or the FMM form (FP64 or FP32, full space)");
+                       !(o.form == FMPB_FORM_FMM && o.precision == FMPB_MIXED)),
+            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED) or the FMM form "
+            "(FP64 or FP32)");
   const cd beta = mkc(o.beta_re, o.beta_im);
   cudaStream_t st = (cudaStream_t)stream;
   fmpb_operator* op = new (std::nothrow) fmpb_operator();
@@ -741,7 +741,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
       const ImageBlocks ib{&op->refl, shn.data(), op->plane.Rp, false};
       if (op->n_near_img > 0)
         s = build_blocks(op->mesh, op->grid, k, beta, op->n_near_img, near_img.data(), dn.data(), op->S_img, st, &ib);
-      if (s == FMPB_OK) s = multipole_tables(op->refl, k, beta, nt, op->V0_img, nullptr, st);
+      if (s == FMPB_OK)
+        s = multipole_tables(op->refl, k, beta, nt, op->V0_img, nullptr, st, nullptr, op->refl.nodes == 9 ? -1.0 : 1.0);
       if (s == FMPB_OK) s = scale_inplace(op->V0_img, (size_t)B * n, op->plane.Rp, st);
       const int n_far_img = (int)(far_img.size() / 3);
       std::vector<int64_t> dfi(n_far_img);

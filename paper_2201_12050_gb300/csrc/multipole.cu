@@ -344,8 +344,10 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
 // V_0[q][j] of a nine-node quadrilateral mesh: the far-class rule (4 x 4
 // points, each with its own normal and weight w|J|) from the point-major
 // table far_tab[(p 7 + f) n + j] (f: y, n_y, w|J|).  One CTA per element.
+// dsign = -1 for the mirrored cell of a half-space operator (nodes kept in
+// their order: computed normal -R n, the double-layer term changes sign).
 __global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt, double k, cd beta,
-                               cd* __restrict__ V0) {
+                               double dsign, cd* __restrict__ V0) {
   __shared__ WaveSetup ws;
   const int j = blockIdx.x;
   const int B = (nt + 1) * (nt + 1);
@@ -365,7 +367,7 @@ __global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt
       const double ny[3] = {t[3 * sn], t[4 * sn], t[5 * sn]};
       cd I, dI;
       wave_eval(nt, ws, q, ny, k, &I, &dI);
-      const cd src = cadd(cconj(dI), cmul(ikb, cconj(I)));
+      const cd src = cadd(cmulr(cconj(dI), dsign), cmul(ikb, cconj(I)));
       acc = cadd(acc, cmulr(src, t[6 * sn]));
     }
   }
@@ -375,7 +377,7 @@ __global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt
 // V_0[q][f nb + b] with discontinuous pressure of order 1 or 2: the far rule
 // of element f weighted by each shape N_b.  One CTA per element.
 __global__ void k_p2m_table_q9p(const double* __restrict__ far_tab, int ne, int order, int nt, double k, cd beta,
-                                Q9Rules R, cd* __restrict__ V0) {
+                                Q9Rules R, double dsign, cd* __restrict__ V0) {
   __shared__ WaveSetup ws;
   const Q9Basis Bs = q9p_basis(order);
   const int f = blockIdx.x;
@@ -397,7 +399,7 @@ __global__ void k_p2m_table_q9p(const double* __restrict__ far_tab, int ne, int 
       const double ny[3] = {t[3 * sn], t[4 * sn], t[5 * sn]};
       cd I, dI;
       wave_eval(nt, ws, q, ny, k, &I, &dI);
-      const cd src = cadd(cconj(dI), cmul(ikb, cconj(I)));
+      const cd src = cadd(cmulr(cconj(dI), dsign), cmul(ikb, cconj(I)));
       double xi, eta, w, Nv[Q9P_MAXNB];
       q9_rule_point(R, 0, p, &xi, &eta, &w);
       q9p_shape(Bs, xi, eta, Nv, nullptr);
@@ -586,7 +588,7 @@ __global__ void k_l2p_apply_f32(const float2* __restrict__ U0, int n, int B, con
 
 // ------------------------------------------------------------- host side --
 fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd* V0, cd* U0, cudaStream_t st,
-                             const double* centres) {
+                             const double* centres, double dsign) {
   if (nt < 1 || nt > MAX_NT) {
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
@@ -598,9 +600,9 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
   const int B = (nt + 1) * (nt + 1);
   const int threads = (B + 31) / 32 * 32;
   if (V0 && m.nodes == 9 && m.q9_order > 0)
-    FMPB_LAUNCH("p2m_table_q9p", st, k_p2m_table_q9p<<<m.q9_ne, threads, 0, st>>>(m.q9_far, m.q9_ne, m.q9_order, nt, k, beta, m.q9r, V0));
+    FMPB_LAUNCH("p2m_table_q9p", st, k_p2m_table_q9p<<<m.q9_ne, threads, 0, st>>>(m.q9_far, m.q9_ne, m.q9_order, nt, k, beta, m.q9r, dsign, V0));
   else if (V0 && m.nodes == 9)
-    FMPB_LAUNCH("p2m_table_q9", st, k_p2m_table_q9<<<m.n, threads, 0, st>>>(m.q9_far, m.n, nt, k, beta, V0));
+    FMPB_LAUNCH("p2m_table_q9", st, k_p2m_table_q9<<<m.n, threads, 0, st>>>(m.q9_far, m.n, nt, k, beta, dsign, V0));
   else if (V0)
     FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));
   if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, centres, U0));

@@ -18,8 +18,10 @@ __host__ __device__ __forceinline__ void q_to_nm(int q, int& n, int& m) {
 // beta: uniform normalised admittance (adds i k beta int conj(I) dA to V0).
 // centres: device, 3 doubles per element, the expansion centre of each
 // element's column of V0 and row of U0 (nullptr: the origin).
+// dsign: -1 for the mirrored cell of a nine-node half-space operator (the
+// double-layer term of its P2M table changes sign), else 1.
 fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd* V0, cd* U0, cudaStream_t st,
-                             const double* centres = nullptr);
+                             const double* centres = nullptr, double dsign = 1.0);
 // K(d_o) for n_d translations; block o written at out + dest[o] B B (dest < 0 skipped).
 // regular: the table of Eq. (m2l) with I_l in place of O_l (regular translations).
 fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, const int64_t* dest_host, cd* out,

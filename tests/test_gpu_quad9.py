@@ -151,7 +151,7 @@ def test_q9_argument_errors():
     with pytest.raises(gb.FmpbError):
         gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM, precision=gb.MIXED)
     with pytest.raises(gb.FmpbError):
-        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM, plane=(2, -0.3, 1.0))
+        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM2, plane=(2, -0.3, 1.0))
     with pytest.raises(gb.FmpbError):
         gb.Operator(nodes, el, counts, LATTICE, 2.0, precision=gb.BF16)
     bad = el.copy()
