@@ -30,7 +30,7 @@ def _impedance_sphere_surface(ka, beta, cos_theta, nmax=40):
                * eval_legendre(n, cos_theta) for n in range(nmax))
 
 
-@pytest.mark.parametrize("k,beta", [(2.0, 0.5 + 0.3j), (7.5, 1.0), (4.0, 0.2 - 0.1j)])
+@pytest.mark.parametrize("k,beta", [(2.0, 0.5 + 0.3j), (7.5, 1.0)])
 def test_impedance_sphere_against_analytic_series(k, beta):
     errs = []
     for level in (2, 3):
