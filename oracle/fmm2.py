@@ -187,11 +187,13 @@ def l2p_leaf(cell: CellMesh, elems, centre, k, nt):
     return (fac[:, None] * (np.conj(I) + coupling(k) * np.conj(dIdn))).T
 
 
-def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact, beta=0.0):
+def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact, beta=0.0, p2m=None):
     """S~_delta x for one near offset, x (R, n): P2M at the leaves of the
     source cell, M2M up the tree, M2L on the interaction list, L2L down, L2P
     at the leaves of the target cell, plus the P2P pairs taken from the exact
-    block S_exact (n x n)."""
+    block S_exact (n x n).  p2m: the leaf P2M table of the element family
+    (default: flat triangles, p2m_leaf)."""
+    p2m = p2m_leaf if p2m is None else p2m
     from .fmm import m2l_block
     x = np.atleast_2d(x)
     L = tree.L
@@ -199,7 +201,7 @@ def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact
     Mom = [dict() for _ in range(L + 1)]
     for key in tree.boxes[L]:
         el = tree.leaf_elements(key)
-        Mom[L][key] = x[:, el] @ p2m_leaf(cell, el, tree.centre(L, key), k, nt_near, beta).T
+        Mom[L][key] = x[:, el] @ p2m(cell, el, tree.centre(L, key), k, nt_near, beta).T
     for l in range(L - 1, -1, -1):
         for key in tree.boxes[l]:
             acc = 0.0

@@ -292,3 +292,47 @@ def fmm_matvec_explicit(mesh: Q9Mesh, lattice, counts, k, nt, p, beta=0.0):
     near = {d: toeplitz_block(mesh, lattice, d, k, beta) for d in bem.near_offsets(counts)}
     return fmm.fmm_matvec_explicit(mesh, lattice, counts, k, nt, p, near_blocks=near,
                                    V0=p2m_table(mesh, k, nt, beta), U0=fmm.l2p_table(mesh, k, nt), beta=beta)
+
+
+# ---------------------------------------------------------- FMPBEM2 near --
+# The multilevel near field of fmm2.py on a Q9 cell: the octree of the
+# element centres, the boxes' radii over the nine nodes of their elements,
+# the leaf P2M table over the far-class rule with each point's normal, and
+# the exact entries of P2P pairs from toeplitz_block.
+
+class _Fmm2Cell:
+    """A Q9Mesh under the names fmm2.py reads (centroid, normal, v, n)."""
+
+    def __init__(self, mesh: Q9Mesh):
+        self.mesh = mesh
+        self.centroid, self.normal, self.v, self.n = mesh.centroid, mesh.normal, mesh.Y, mesh.n
+
+
+def p2m_leaf(cell, elems, centre, k, nt, beta=0.0):
+    """V (B x len(elems)) about a leaf centre (p2m_table's rule)."""
+    y, ny, w = _batch_rule(cell.mesh.Y[elems], "far")
+    rel = y - np.asarray(centre)[None, None, :]
+    g = sp.grad_regular_table(nt, rel, k)
+    V = np.sum(np.conj(np.einsum("bnqi,nqi->bnq", g, ny)) * w[None], axis=2)
+    if beta != 0:
+        I = sp.wave_table(nt, rel.reshape(-1, 3), k, "I").reshape(-1, *w.shape)
+        V = V + 1j * k * beta * np.sum(np.conj(I) * w[None], axis=2)
+    return V
+
+
+def fmm2_near_block(mesh: Q9Mesh, lattice, delta, k, nt_near, levels, beta=0.0):
+    """The multilevel approximation of S_delta (n x n) on a Q9 cell."""
+    from . import fmm2
+    cell = _Fmm2Cell(mesh)
+    tree = fmm2.Octree(cell, levels)
+    S = toeplitz_block(mesh, lattice, delta, k, beta)
+    shift = -np.asarray(delta, dtype=np.float64) @ np.asarray(lattice, dtype=np.float64)
+    return fmm2.near_block_apply(cell, tree, shift, k, nt_near, np.eye(mesh.n), S, beta, p2m=p2m_leaf).T
+
+
+def fmm2_matvec_explicit(mesh: Q9Mesh, lattice, counts, k, nt, nt_near, levels, p, beta=0.0):
+    """The FMPBEM2 product on a Q9 cell: fmm_matvec_explicit with every near
+    block replaced by its multilevel approximation."""
+    near = {d: fmm2_near_block(mesh, lattice, d, k, nt_near, levels, beta) for d in bem.near_offsets(counts)}
+    return fmm.fmm_matvec_explicit(mesh, lattice, counts, k, nt, p, near_blocks=near,
+                                   V0=p2m_table(mesh, k, nt, beta), U0=fmm.l2p_table(mesh, k, nt), beta=beta)

@@ -154,3 +154,16 @@ def test_fmm_product_on_q9_cells_tends_to_the_exact_operator(beta):
         errs.append(np.linalg.norm(y - y_exact) / np.linalg.norm(y_exact))
     assert all(b < 0.05 * a for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-13, errs
+
+
+def test_fmm2_near_block_on_q9_cells_tends_to_the_exact_block():
+    # the multilevel near field of a Q9 cell (octree of the element centres,
+    # leaf P2M over the far rule with each point's normal): 372 translated box
+    # pairs at three levels; the centre normal in the leaf P2M stalls at 1e-4
+    nodes, el = quad9_sphere(3, 0.2)
+    mesh = quad9.Q9Mesh(nodes, el)
+    L = np.diag([0.6, 0.6, 1.0])
+    S = quad9.toeplitz_block(mesh, L, (0, 0, 0), 3.0, 0.3j)
+    errs = [np.linalg.norm(quad9.fmm2_near_block(mesh, L, (0, 0, 0), 3.0, ntn, 3, 0.3j) - S) / np.linalg.norm(S)
+            for ntn in (4, 8)]
+    assert errs[1] < 0.01 * errs[0] and errs[1] < 1e-6, errs
