@@ -531,10 +531,10 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   const bool quad9 = o.element == FMPB_ELEM_QUAD9;
   CHECK_ARG(o.pressure_order == 0 || (quad9 && (o.pressure_order == 1 || o.pressure_order == 2)),
             "operator_create: pressure of order 1 or 2 takes FMPB_ELEM_QUAD9 elements");
-  CHECK_ARG(!quad9 || (o.form != FMPB_FORM_FMM2 && o.precision != FMPB_BF16 &&
+  CHECK_ARG(!quad9 || ((o.form != FMPB_FORM_FMM2 || o.pressure_order == 0) && o.precision != FMPB_BF16 &&
                        !(o.form == FMPB_FORM_FMM && o.precision == FMPB_MIXED)),
-            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED) or the FMM form "
-            "(FP64 or FP32)");
+            "operator_create: nine-node quadrilaterals run the PBEM form (FP64, FP32 or MIXED), the FMM form "
+            "(FP64 or FP32) or, with constant pressure, the FMPBEM2 form");
   const cd beta = mkc(o.beta_re, o.beta_im);
   cudaStream_t st = (cudaStream_t)stream;
   fmpb_operator* op = new (std::nothrow) fmpb_operator();

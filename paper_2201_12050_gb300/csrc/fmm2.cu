@@ -228,7 +228,7 @@ static fmpb_status upload(T** dst, const std::vector<T>& h, size_t& bytes, cudaS
 }
 
 fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const CellGrid& g, int levels, int nt_near,
-                       const std::vector<int32_t>& near_off, Near2& t, Near2Host& h) {
+                       const std::vector<int32_t>& near_off, Near2& t, Near2Host& h, int npe) {
   if (nt_near < 1 || nt_near > MAX_NT) {
     set_error("FMPBEM2: n_t,near must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
@@ -237,7 +237,9 @@ fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const Ce
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int j = 0; j < n; ++j)
     for (int d = 0; d < 3; ++d) {
-      const double c = (verts[3 * tris[3 * j] + d] + verts[3 * tris[3 * j + 1] + d] + verts[3 * tris[3 * j + 2] + d]) / 3.0;
+      const double c = npe == 9 ? verts[3 * (int64_t)tris[9 * j + 4] + d]
+                                : (verts[3 * tris[3 * j] + d] + verts[3 * tris[3 * j + 1] + d] +
+                                   verts[3 * tris[3 * j + 2] + d]) / 3.0;
       cen[3 * j + d] = c;
       lo[d] = std::min(lo[d], c);
       hi[d] = std::max(hi[d], c);
@@ -305,8 +307,8 @@ fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const Ce
     for (int j = 0; j < n; ++j) {
       double c[3];
       centre(l, ks[j], c);
-      for (int a = 0; a < 3; ++a) {
-        const double* v = verts + 3 * tris[3 * j + a];
+      for (int a = 0; a < npe; ++a) {
+        const double* v = verts + 3 * (int64_t)tris[(int64_t)npe * j + a];
         const double dx = v[0] - c[0], dy = v[1] - c[1], dz = v[2] - c[2];
         rho[l] = std::max(rho[l], std::sqrt(dx * dx + dy * dy + dz * dz));
       }
@@ -447,7 +449,7 @@ fmpb_status near2_build(const DeviceMesh& m, const CellGrid& g, const double* ve
                         cudaStream_t st) {
   const int n = m.n;
   Near2Host h;
-  FMPB_TRY(near2_plan(verts, tris, n, g, levels, nt_near, near_off, t, h));
+  FMPB_TRY(near2_plan(verts, tris, n, g, levels, nt_near, near_off, t, h, m.nodes));
   const int L = t.L, B = t.B;
   const double e0 = h.e0;
   const auto &parent = h.parent, &octant = h.octant, &cstart = h.cstart, &cidx = h.cidx, &lstart = h.lstart,

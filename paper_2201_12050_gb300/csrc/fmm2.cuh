@@ -49,8 +49,10 @@ struct Near2Host {
   std::vector<int64_t> pstart, plist, self_slot;
   double e0 = 0.0;
 };
+// npe: nodes per element (3: triangles, centroid; 9: nine-node
+// quadrilaterals, the centre node 4); box radii run over all of them.
 fmpb_status near2_plan(const double* verts, const int32_t* tris, int n, const CellGrid& g, int levels, int nt_near,
-                       const std::vector<int32_t>& near_off, Near2& t, Near2Host& h);
+                       const std::vector<int32_t>& near_off, Near2& t, Near2Host& h, int npe = 3);
 
 // Builds the tree, the interaction lists of every near offset and the device
 // tables (Sec. 3.3, Eqs. (m2m), (m2l), (l2l)).  verts/tris: the host mesh;

@@ -121,6 +121,10 @@ void free_mesh(DeviceMesh& m);
 // y_xi x y_eta into the fluid).
 fmpb_status upload_mesh_q9(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, DeviceMesh& m,
                            cudaStream_t st);
+// build_entries for a nine-node mesh with constant pressure (quad9.cu).
+fmpb_status build_entries_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                             const int32_t* offsets, const int64_t* list, int64_t count, const int64_t* self_slot,
+                             cd* out, cudaStream_t st);
 // The same with discontinuous pressure of order 1 or 2 (quad9p.cu).
 fmpb_status upload_mesh_q9p(const double* nodes, int64_t nn, const int32_t* elems, int64_t n, int order,
                             DeviceMesh& m, cudaStream_t st);

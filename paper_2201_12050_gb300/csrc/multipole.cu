@@ -347,7 +347,7 @@ __global__ void k_p2m_table(const Elem* __restrict__ el, int n, int nt, double k
 // dsign = -1 for the mirrored cell of a half-space operator (nodes kept in
 // their order: computed normal -R n, the double-layer term changes sign).
 __global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt, double k, cd beta,
-                               double dsign, cd* __restrict__ V0) {
+                               double dsign, const double* __restrict__ centres, cd* __restrict__ V0) {
   __shared__ WaveSetup ws;
   const int j = blockIdx.x;
   const int B = (nt + 1) * (nt + 1);
@@ -359,7 +359,9 @@ __global__ void k_p2m_table_q9(const double* __restrict__ far_tab, int n, int nt
     const double* t = far_tab + (size_t)p * 7 * sn + j;
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double y[3] = {t[0], t[sn], t[2 * sn]};
+      // about the cell origin, or about the element's own expansion centre
+      const double y[3] = {t[0] - (centres ? centres[3 * j] : 0.0), t[sn] - (centres ? centres[3 * j + 1] : 0.0),
+                           t[2 * sn] - (centres ? centres[3 * j + 2] : 0.0)};
       wave_setup(nt, y, k, &ws);
     }
     __syncthreads();
@@ -593,8 +595,8 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
     set_error("n_t must be 1..%d", MAX_NT);
     return FMPB_EINVAL;
   }
-  if (m.nodes == 9 && centres) {
-    set_error("multipole_tables: per-element expansion centres take flat triangles");
+  if (m.nodes == 9 && m.q9_order > 0 && centres) {
+    set_error("multipole_tables: per-element expansion centres take constant pressure on nine-node elements");
     return FMPB_EINVAL;
   }
   const int B = (nt + 1) * (nt + 1);
@@ -602,7 +604,7 @@ fmpb_status multipole_tables(const DeviceMesh& m, double k, cd beta, int nt, cd*
   if (V0 && m.nodes == 9 && m.q9_order > 0)
     FMPB_LAUNCH("p2m_table_q9p", st, k_p2m_table_q9p<<<m.q9_ne, threads, 0, st>>>(m.q9_far, m.q9_ne, m.q9_order, nt, k, beta, m.q9r, dsign, V0));
   else if (V0 && m.nodes == 9)
-    FMPB_LAUNCH("p2m_table_q9", st, k_p2m_table_q9<<<m.n, threads, 0, st>>>(m.q9_far, m.n, nt, k, beta, dsign, V0));
+    FMPB_LAUNCH("p2m_table_q9", st, k_p2m_table_q9<<<m.n, threads, 0, st>>>(m.q9_far, m.n, nt, k, beta, dsign, centres, V0));
   else if (V0)
     FMPB_LAUNCH("p2m_table", st, k_p2m_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, beta, m.qr, centres, V0));
   if (U0) FMPB_LAUNCH("l2p_table", st, k_l2p_table<<<m.n, threads, 0, st>>>(m.el, m.n, nt, k, centres, U0));

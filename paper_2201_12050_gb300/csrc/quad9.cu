@@ -179,10 +179,12 @@ __global__ void __launch_bounds__(256) k_q9_near_entries(const Elem* __restrict_
 }
 
 // Self term of every element, one warp per element:
-// T_ii = 1/2 + beta/2 - (D + (i/k) H) - i k beta (S + (i/k) K) at the centre.
+// T_ii = 1/2 + beta/2 - (D + (i/k) H) - i k beta (S + (i/k) K) at the centre,
+// stored at block0[i n + i], or with slot at block0[slot[i]] (listed
+// entries; -1: not listed).
 template <bool SK>
 __global__ void __launch_bounds__(256) k_q9_self(const Q9Elem* __restrict__ q9, int n, cd* __restrict__ block0,
-                                                 double k, cd beta, Q9Rules R) {
+                                                 double k, cd beta, Q9Rules R, const int64_t* __restrict__ slot) {
   const int lane = threadIdx.x & 31;
   const int e = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (e >= n) return;   // uniform across the warp
@@ -203,8 +205,56 @@ __global__ void __launch_bounds__(256) k_q9_self(const Q9Elem* __restrict__ q9, 
     }
   }
   if (lane == 0) {
-    const cd t = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
-    block0[(size_t)e * n + e] = cadd(t, mkc(0.5 + 0.5 * beta.x, 0.5 * beta.y));
+    const cd t = cadd(SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k), mkc(0.5 + 0.5 * beta.x, 0.5 * beta.y));
+    if (!slot)
+      block0[(size_t)e * n + e] = t;
+    else if (slot[e] >= 0)
+      block0[slot[e]] = t;
+  }
+}
+
+// Listed entries (o, i, j) of n_off blocks (idx = (o n + i) n + j), written
+// to out[e]: the exact entries a multilevel near field keeps.  Same classes
+// and arithmetic as k_q9_blocks, near classes in the thread itself; the self
+// entry of the zero offset is left to k_q9_self.
+template <bool SK>
+__global__ void __launch_bounds__(128) k_q9_entries(const Elem* __restrict__ el, const double* __restrict__ far_tab,
+                                                    const double* __restrict__ near_tab, int n,
+                                                    const double* __restrict__ shifts, int zero_off,
+                                                    const int64_t* __restrict__ list, int64_t count,
+                                                    cd* __restrict__ out, double k, cd beta) {
+  const size_t nn = (size_t)n * n;
+  const size_t sn = (size_t)n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const size_t idx = (size_t)list[e];
+    const int o = (int)(idx / nn);
+    const size_t rem = idx - (size_t)o * nn;
+    const int i = (int)(rem / n);
+    const int j = (int)(rem - (size_t)i * n);
+    if (o == zero_off && i == j) continue;
+    const Elem& Ti = el[i];
+    const double x[3] = {Ti.c[0], Ti.c[1], Ti.c[2]};
+    const double nx[3] = {Ti.nrm[0], Ti.nrm[1], Ti.nrm[2]};
+    const double sh[3] = {shifts[3 * o], shifts[3 * o + 1], shifts[3 * o + 2]};
+    const Elem& Ej = el[j];
+    double dc[3];
+    for (int d = 0; d < 3; ++d) dc[d] = x[d] - (Ej.c[d] + sh[d]);
+    const double dist = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
+    cd D = mkc(0.0, 0.0), H = mkc(0.0, 0.0), S = mkc(0.0, 0.0), K = mkc(0.0, 0.0);
+    if (dist >= FAR_RATIO * Ej.hmax) {
+#pragma unroll 1
+      for (int p = 0; p < Q9_FAR; ++p) {
+        const double* q = far_tab + (size_t)p * 7 * sn + j;
+        const double dv[3] = {x[0] - (q[0] + sh[0]), x[1] - (q[sn] + sh[1]), x[2] - (q[2 * sn] + sh[2])};
+        const double ny[3] = {q[3 * sn], q[4 * sn], q[5 * sn]};
+        q9_kernels<SK>(dv, nx, ny, q[6 * sn], k, D, H, S, K);
+      }
+    } else {
+      const bool very = dist < NEAR_RATIO * Ej.hmax;
+      const double* tab = near_tab + (size_t)j * Q9_NEAR_TAB * 8 + (very ? Q9_NEAR * 8 : 0);
+      q9_sum_table<SK>(tab, very ? Q9_VNEAR : Q9_NEAR, 0, 1, x, nx, sh, k, D, H, S, K);
+    }
+    out[e] = SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k);
   }
 }
 
@@ -310,12 +360,12 @@ fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd
       FMPB_LAUNCH("q9_blocks", st, k_q9_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_near, m.n, dshift, ddest, n_off, zero_off, out, k, beta, bw, near_list, near_count, near_cap));
       FMPB_LAUNCH("q9_near", st, k_q9_near_entries<false><<<152 * 16, 256, 0, st>>>(m.el, m.q9_near, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw));
       if (zero_off >= 0)
-        FMPB_LAUNCH("q9_self", st, k_q9_self<false><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n, k, beta, m.q9r));
+        FMPB_LAUNCH("q9_self", st, k_q9_self<false><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n, k, beta, m.q9r, nullptr));
     } else {
       FMPB_LAUNCH("q9_blocks_adm", st, k_q9_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_near, m.n, dshift, ddest, n_off, zero_off, out, k, beta, bw, near_list, near_count, near_cap));
       FMPB_LAUNCH("q9_near_adm", st, k_q9_near_entries<true><<<152 * 16, 256, 0, st>>>(m.el, m.q9_near, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw));
       if (zero_off >= 0)
-        FMPB_LAUNCH("q9_self_adm", st, k_q9_self<true><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n, k, beta, m.q9r));
+        FMPB_LAUNCH("q9_self_adm", st, k_q9_self<true><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n, k, beta, m.q9r, nullptr));
     }
     e = cudaGetLastError();
   }
@@ -324,6 +374,46 @@ fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd
   cudaFree(ddest);
   cudaFree(near_list);
   if (e != cudaSuccess) return cuda_status(e, "build_blocks_q9");
+  return FMPB_OK;
+}
+
+}  // namespace fmpb
+
+namespace fmpb {
+
+fmpb_status build_entries_q9(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
+                             const int32_t* offsets, const int64_t* list, int64_t count, const int64_t* self_slot,
+                             cd* out, cudaStream_t st) {
+  if (m.nodes != 9 || !m.q9 || m.q9_order != 0) {
+    set_error("build_entries: listed entries take flat triangles or constant pressure on nine-node elements");
+    return FMPB_EINVAL;
+  }
+  std::vector<double> shifts(3 * (size_t)n_off);
+  int zero_off = -1;
+  for (int o = 0; o < n_off; ++o) {
+    const int32_t* dl = offsets + 3 * o;
+    if (dl[0] == 0 && dl[1] == 0 && dl[2] == 0) zero_off = o;
+    for (int d = 0; d < 3; ++d) shifts[3 * o + d] = -(dl[0] * g.L[0][d] + dl[1] * g.L[1][d] + dl[2] * g.L[2][d]);
+  }
+  double* dshift = nullptr;
+  FMPB_CUDA(cudaMallocAsync(&dshift, sizeof(double) * 3 * n_off, st));
+  FMPB_CUDA(cudaMemcpyAsync(dshift, shifts.data(), sizeof(double) * 3 * n_off, cudaMemcpyHostToDevice, st));
+  if (count > 0) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((count + 127) / 128, 152 * 64);
+    if (beta.x == 0.0 && beta.y == 0.0)
+      FMPB_LAUNCH("q9_entries", st, k_q9_entries<false><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_near, m.n, dshift, zero_off, list, count, out, k, beta));
+    else
+      FMPB_LAUNCH("q9_entries_adm", st, k_q9_entries<true><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_near, m.n, dshift, zero_off, list, count, out, k, beta));
+  }
+  if (zero_off >= 0 && self_slot) {
+    const unsigned self_blocks = grid_for((size_t)m.n * 32, 256);
+    if (beta.x == 0.0 && beta.y == 0.0)
+      FMPB_LAUNCH("q9_self", st, k_q9_self<false><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out, k, beta, m.q9r, self_slot));
+    else
+      FMPB_LAUNCH("q9_self_adm", st, k_q9_self<true><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out, k, beta, m.q9r, self_slot));
+  }
+  FMPB_CUDA(cudaGetLastError());
+  FMPB_CUDA(cudaFreeAsync(dshift, st));
   return FMPB_OK;
 }
 

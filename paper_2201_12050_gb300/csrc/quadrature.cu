@@ -1030,10 +1030,7 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
 fmpb_status build_entries(const DeviceMesh& m, const CellGrid& g, double k, cd beta, int n_off,
                           const int32_t* offsets, const int64_t* list, int64_t count, const int64_t* self_slot,
                           cd* out, cudaStream_t st) {
-  if (m.nodes != 3) {
-    set_error("build_entries: listed entries take flat triangles");
-    return FMPB_EINVAL;
-  }
+  if (m.nodes == 9) return build_entries_q9(m, g, k, beta, n_off, offsets, list, count, self_slot, out, st);
   std::vector<double> shifts(3 * (size_t)n_off);
   int zero_off = -1;
   for (int o = 0; o < n_off; ++o) {

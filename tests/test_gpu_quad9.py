@@ -147,7 +147,7 @@ def test_q9_argument_errors():
     nodes, el = quad9_sphere(1, 0.2)
     counts = (2, 1, 1)
     with pytest.raises(gb.FmpbError):
-        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM2)
+        gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM2, precision=gb.FP32)
     with pytest.raises(gb.FmpbError):
         gb.Operator(nodes, el, counts, LATTICE, 2.0, form=gb.FORM_FMM, precision=gb.MIXED)
     with pytest.raises(gb.FmpbError):
