@@ -64,3 +64,33 @@ def test_server_reports_missing_device_as_status(L):
     st = L.fmpb_server_create(ctypes.byref(ServerOpts()), ctypes.byref(h))
     assert st in (-8, -2) and not h.value
     assert L.fmpb_server_submit(None, None, None, None) == -1
+
+
+def test_element_and_pressure_order_checks_are_host_side(L):
+    # combinations refused before any device work, so the checks run on any host
+    from paper_2201_12050_gb300._lib import OperatorOpts, Lattice
+    lat = Lattice()
+    for a in range(3):
+        lat.counts[a] = 1
+        lat.vectors[a][a] = 1.0
+    h = ctypes.c_void_p()
+
+    def create(**kw):
+        o = OperatorOpts()
+        for name, v in kw.items():
+            setattr(o, name, v)
+        return L.fmpb_operator_create(None, 0, None, 0, ctypes.byref(lat), 2.0, ctypes.byref(o), None, ctypes.byref(h))
+
+    cases = [dict(element=2),                                   # no such element
+             dict(pressure_order=1),                            # higher orders take quadrilaterals
+             dict(element=1, pressure_order=3),                 # no such order
+             dict(element=1, form=2, pressure_order=1),         # FMPBEM2: constant pressure only
+             dict(element=1, form=2, precision=1),              # FMPBEM2 runs FP64
+             dict(element=1, precision=2),                      # no BF16 tables on quadrilaterals
+             dict(element=1, form=0, precision=3)]              # the FMM form: FP64 or FP32
+    for kw in cases:
+        assert create(**kw) == -1, kw
+    assert not h.value
+    st = L.fmpb_build_blocks_q9p(None, 0, None, 0, 3, ctypes.byref(lat), 2.0, 0.0, 0.0, 1,
+                                 (ctypes.c_int32 * 3)(0, 0, 0), ctypes.c_void_p(1), None)
+    assert st == -1 and b"order" in L.fmpb_last_error()
