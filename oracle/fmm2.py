@@ -187,13 +187,17 @@ def l2p_leaf(cell: CellMesh, elems, centre, k, nt):
     return (fac[:, None] * (np.conj(I) + coupling(k) * np.conj(dIdn))).T
 
 
-def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact, beta=0.0, p2m=None):
+def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact, beta=0.0, p2m=None, l2p=None,
+                     dofs=None):
     """S~_delta x for one near offset, x (R, n): P2M at the leaves of the
     source cell, M2M up the tree, M2L on the interaction list, L2L down, L2P
     at the leaves of the target cell, plus the P2P pairs taken from the exact
-    block S_exact (n x n).  p2m: the leaf P2M table of the element family
-    (default: flat triangles, p2m_leaf)."""
+    block S_exact (n x n).  p2m, l2p: the leaf tables of the element family
+    (default: flat triangles, p2m_leaf and l2p_leaf); dofs: the dof indices of
+    a list of elements (default: one dof per element, the element's index)."""
     p2m = p2m_leaf if p2m is None else p2m
+    l2p = l2p_leaf if l2p is None else l2p
+    dofs = (lambda el: el) if dofs is None else dofs
     from .fmm import m2l_block
     x = np.atleast_2d(x)
     L = tree.L
@@ -201,7 +205,7 @@ def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact
     Mom = [dict() for _ in range(L + 1)]
     for key in tree.boxes[L]:
         el = tree.leaf_elements(key)
-        Mom[L][key] = x[:, el] @ p2m(cell, el, tree.centre(L, key), k, nt_near, beta).T
+        Mom[L][key] = x[:, dofs(el)] @ p2m(cell, el, tree.centre(L, key), k, nt_near, beta).T
     for l in range(L - 1, -1, -1):
         for key in tree.boxes[l]:
             acc = 0.0
@@ -217,12 +221,12 @@ def near_block_apply(cell: CellMesh, tree: Octree, shift, k, nt_near, x, S_exact
             for ch in tree.children(l, key):
                 T = l2l_matrix(tree.centre(l, key), tree.centre(l + 1, ch), k, nt_near)
                 Loc[l + 1][ch] = Loc[l + 1].get(ch, 0.0) + val @ T.T
-    y = np.zeros((x.shape[0], cell.n), dtype=complex)
+    y = np.zeros((x.shape[0], x.shape[1]), dtype=complex)
     for key, val in Loc[L].items():
         el = tree.leaf_elements(key)
-        y[:, el] += val @ l2p_leaf(cell, el, tree.centre(L, key), k, nt_near).T
+        y[:, dofs(el)] += val @ l2p(cell, el, tree.centre(L, key), k, nt_near).T
     for a, b in p2p:
-        ia, jb = tree.leaf_elements(a), tree.leaf_elements(b)
+        ia, jb = dofs(tree.leaf_elements(a)), dofs(tree.leaf_elements(b))
         y[:, ia] += x[:, jb] @ S_exact[np.ix_(ia, jb)].T
     return y
 

@@ -465,3 +465,51 @@ def fmm_image_matvec_explicit(cell: OrderMesh, lattice, counts, k, nt, plane, p,
                 Lc += Mom[:, cj] @ cache[key].T
         Y[:, ci] += Lc @ U0.T
     return Y.reshape(R, -1)
+
+
+# ---------------------------------------------------------- FMPBEM2 near --
+# fmm2.py's multilevel near field on a cell with pressure of any order: the
+# octree of the element centres (box radii over the nine nodes), leaf P2M
+# tables weighted by the shapes, leaf L2P tables at the elements' nodes, and
+# dofs e nb + a of each leaf element.
+
+class _Fmm2Cell:
+    def __init__(self, mesh: OrderMesh):
+        self.mesh = mesh
+        self.centroid, self.v, self.n = mesh.geo.centroid, mesh.geo.Y, mesh.geo.n
+
+
+def _leaf_p2m(cell, elems, centre, k, nt, beta=0.0):
+    from . import special as sp
+    mesh = cell.mesh
+    xi, eta, _ = quad9.tensor_rule(quad9.Q_FAR4)
+    y, ny, w = quad9._batch_rule(mesh.geo.Y[elems], "far")
+    N, _ = mesh.basis.eval(xi, eta)
+    rel = y - np.asarray(centre)[None, None, :]
+    g = sp.grad_regular_table(nt, rel, k)
+    src = np.conj(np.einsum("bnqi,nqi->bnq", g, ny))
+    if beta != 0:
+        src = src + 1j * k * beta * np.conj(sp.wave_table(nt, rel.reshape(-1, 3), k, "I").reshape(-1, *w.shape))
+    return np.einsum("bnq,nq,cq->bnc", src, w, N).reshape(src.shape[0], -1)
+
+
+def _leaf_l2p(cell, elems, centre, k, nt):
+    from . import fmm2
+    from types import SimpleNamespace
+    mesh, nb = cell.mesh, cell.mesh.nb
+    d = np.array([e * nb + a for e in elems for a in range(nb)])
+    pts = SimpleNamespace(centroid=mesh.points[d], normal=mesh.normals[d])
+    return fmm2.l2p_leaf(pts, np.arange(len(d)), centre, k, nt)
+
+
+def fmm2_near_block(mesh: OrderMesh, lattice, delta, k, nt_near, levels, beta=0.0):
+    """The multilevel approximation of S_delta ((n nb) x (n nb))."""
+    from . import fmm2
+    cell = _Fmm2Cell(mesh)
+    tree = fmm2.Octree(cell, levels)
+    S = toeplitz_block(mesh, lattice, delta, k, beta)
+    shift = -np.asarray(delta, dtype=np.float64) @ np.asarray(lattice, dtype=np.float64)
+    nb = mesh.nb
+    dofs = lambda el: np.array([e * nb + a for e in el for a in range(nb)], dtype=np.int64)
+    return fmm2.near_block_apply(cell, tree, shift, k, nt_near, np.eye(mesh.n * nb), S, beta,
+                                 p2m=_leaf_p2m, l2p=_leaf_l2p, dofs=dofs).T

@@ -336,3 +336,21 @@ def test_fmm_image_product_tends_to_the_exact_image_part(order, counts):
     errs = [np.linalg.norm(qo.fmm_image_matvec_explicit(cell, L, counts, 2.0, nt, plane, x, 0.3j) - exact)
             / np.linalg.norm(exact) for nt in (4, 8, 12)]
     assert errs[1] < 1e-3 * errs[0] and errs[2] < 1e-12, errs
+
+
+def test_fmm2_near_block_with_higher_order_pressure():
+    # the multilevel near field with shape-weighted leaf P2M tables and leaf
+    # L2P tables at the nodes: order 0 through this path is the constant
+    # element's; order 1 converges to the exact block (a leaf P2M that
+    # spreads each element's moment evenly over its shapes stalls at 5e-4)
+    from oracle import quad9 as q9
+    L = np.diag([0.6, 0.6, 1.0])
+    nodes, el = quad9_sphere(3, 0.2)
+    A0 = qo.fmm2_near_block(qo.OrderMesh(nodes, el, 0), L, (0, 0, 0), 3.0, 6, 3, 0.3j)
+    Aq = q9.fmm2_near_block(q9.Q9Mesh(nodes, el), L, (0, 0, 0), 3.0, 6, 3, 0.3j)
+    assert np.abs(A0 - Aq).max() <= 1e-14 * np.abs(Aq).max()
+    mesh = qo.OrderMesh(nodes, el, 1)
+    S = qo.toeplitz_block(mesh, L, (0, 0, 0), 3.0, 0.3j)
+    errs = [np.linalg.norm(qo.fmm2_near_block(mesh, L, (0, 0, 0), 3.0, ntn, 3, 0.3j) - S) / np.linalg.norm(S)
+            for ntn in (4, 8)]
+    assert errs[1] < 0.02 * errs[0] and errs[1] < 1e-6, errs
