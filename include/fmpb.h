@@ -365,6 +365,12 @@ fmpb_status fmpb_near2_plan_counts(const double *verts, int64_t nv, const int32_
                                    const fmpb_lattice *lattice, int near_levels, int n_t_near,
                                    int32_t *levels_out, int64_t *n_m2l, int64_t *n_p2p,
                                    int64_t *n_translations);
+/* The same plan on nine-node quadrilaterals (elems: n x 9 node indices; the
+ * octree of the element centres, node 4, with box radii over all nine nodes). */
+fmpb_status fmpb_near2_plan_counts_q9(const double *nodes, int64_t nn, const int32_t *elems, int64_t n,
+                                      const fmpb_lattice *lattice, int near_levels, int n_t_near,
+                                      int32_t *levels_out, int64_t *n_m2l, int64_t *n_p2p,
+                                      int64_t *n_translations);
 
 /*
  * Collocation blocks T_delta of Eq. (blockToeplizMatrix) (Sec. 2.2): entry

@@ -118,6 +118,7 @@ SIGNATURES = {
     "fmpb_insertion_loss": (INT, [P, INT, P, P, I64, P, P, P]),
     "fmpb_halfspace_plan": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, D, P, P, P]),
     "fmpb_near2_plan_counts": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, INT, P, P, P, P]),
+    "fmpb_near2_plan_counts_q9": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, INT, P, P, P, P]),
     "fmpb_field_incident": (INT, [P, INT, P, P, I64, P, P, P]),
     "fmpb_build_blocks_admittance": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
     "fmpb_multipole_tables_admittance": (INT, [P, I64, P, I64, D, D, D, INT, P, P, P]),

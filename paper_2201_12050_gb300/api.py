@@ -227,15 +227,16 @@ def halfspace_plan(verts, tris, counts, vectors, plane_axis, plane_offset):
 
 
 def near2_plan_counts(verts, tris, counts, vectors, near_levels=0, n_t_near=0):
-    """fmpb_near2_plan_counts (host only): (levels, M2L pairs, exact entries, translations)."""
+    """fmpb_near2_plan_counts, or fmpb_near2_plan_counts_q9 for nine-column
+    elements (host only): (levels, M2L pairs, exact entries, translations)."""
     v = _host(verts, np.float64)
     t = _host(tris, np.int32)
     lat = _lattice(counts, vectors)
     lv = ctypes.c_int32()
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    check(lib().fmpb_near2_plan_counts(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), int(near_levels),
-                                       int(n_t_near), ctypes.byref(lv), ctypes.byref(a), ctypes.byref(b),
-                                       ctypes.byref(c)))
+    fn = lib().fmpb_near2_plan_counts_q9 if t.ndim == 2 and t.shape[1] == 9 else lib().fmpb_near2_plan_counts
+    check(fn(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), int(near_levels), int(n_t_near), ctypes.byref(lv),
+             ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return lv.value, a.value, b.value, c.value
 
 

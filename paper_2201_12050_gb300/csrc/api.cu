@@ -967,14 +967,14 @@ fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* 
   return FMPB_OK;
 }
 
-fmpb_status fmpb_near2_plan_counts(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
-                                   const fmpb_lattice* lattice, int near_levels, int n_t_near, int32_t* levels_out,
-                                   int64_t* n_m2l, int64_t* n_p2p, int64_t* n_translations) {
-  CHECK_ARG(verts && tris && nv >= 3 && ntri >= 1 && ntri <= (1 << 20), "near2_plan: bad mesh");
+static fmpb_status near2_counts(const double* verts, int64_t nv, const int32_t* idx, int64_t n, int npe,
+                                const fmpb_lattice* lattice, int near_levels, int n_t_near, int32_t* levels_out,
+                                int64_t* n_m2l, int64_t* n_p2p, int64_t* n_translations) {
+  CHECK_ARG(verts && idx && nv >= npe && n >= 1 && n <= (1 << 20), "near2_plan: bad mesh");
   CHECK_ARG(levels_out && n_m2l && n_p2p && n_translations, "near2_plan: NULL output");
   CHECK_ARG(near_levels >= 0 && near_levels <= 10, "near2_plan: near_levels must be 0..10");
-  for (int64_t e = 0; e < 3 * ntri; ++e)
-    CHECK_ARG(tris[e] >= 0 && tris[e] < nv, "near2_plan: triangle index out of range");
+  for (int64_t e = 0; e < npe * n; ++e)
+    CHECK_ARG(idx[e] >= 0 && idx[e] < nv, "near2_plan: node index out of range");
   CellGrid g;
   FMPB_TRY(make_grid(lattice, g));
   std::vector<int32_t> near_off;
@@ -984,12 +984,26 @@ fmpb_status fmpb_near2_plan_counts(const double* verts, int64_t nv, const int32_
         if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) near_off.insert(near_off.end(), {dx, dy, dz});
   Near2 t;
   Near2Host h;
-  FMPB_TRY(near2_plan(verts, tris, (int)ntri, g, near_levels, n_t_near > 0 ? n_t_near : 6, near_off, t, h));
+  FMPB_TRY(near2_plan(verts, idx, (int)n, g, near_levels, n_t_near > 0 ? n_t_near : 6, near_off, t, h, npe));
   *levels_out = t.L;
   *n_m2l = t.n_m2l;
   *n_p2p = t.n_p2p;
   *n_translations = t.n_k;
   return FMPB_OK;
+}
+
+fmpb_status fmpb_near2_plan_counts(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                   const fmpb_lattice* lattice, int near_levels, int n_t_near, int32_t* levels_out,
+                                   int64_t* n_m2l, int64_t* n_p2p, int64_t* n_translations) {
+  return near2_counts(verts, nv, tris, ntri, 3, lattice, near_levels, n_t_near, levels_out, n_m2l, n_p2p,
+                      n_translations);
+}
+
+fmpb_status fmpb_near2_plan_counts_q9(const double* nodes, int64_t nn, const int32_t* elems, int64_t n,
+                                      const fmpb_lattice* lattice, int near_levels, int n_t_near, int32_t* levels_out,
+                                      int64_t* n_m2l, int64_t* n_p2p, int64_t* n_translations) {
+  return near2_counts(nodes, nn, elems, n, 9, lattice, near_levels, n_t_near, levels_out, n_m2l, n_p2p,
+                      n_translations);
 }
 
 fmpb_status fmpb_build_blocks(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,

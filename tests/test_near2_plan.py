@@ -67,3 +67,25 @@ def test_plan_rejects_bad_arguments():
     bad[0, 0] = 1000
     with pytest.raises(gb.FmpbError):
         gb.near2_plan_counts(v, bad, (2, 1, 1), np.diag([0.5, 1.0, 1.0]))
+
+
+@pytest.mark.parametrize("m,counts,lattice,levels", [
+    (3, (4, 3, 1), np.diag([0.6, 0.6, 1.0]), 2),
+    (3, (3, 2, 1), np.diag([0.5, 0.55, 1.0]), 3),
+    (4, (2, 2, 2), np.diag([0.5, 0.5, 0.5]), 2),
+])
+def test_plan_on_nine_node_elements_matches_the_oracle_lists(m, counts, lattice, levels):
+    # the octree of the element centres with box radii over all nine nodes
+    from oracle import quad9
+    from workloads import quad9_sphere
+    nodes, el = quad9_sphere(m, 0.2)
+    cell = quad9._Fmm2Cell(quad9.Q9Mesh(nodes, el))
+    tree = fmm2.Octree(cell, levels)
+    L = np.asarray(lattice, dtype=float)
+    n_m2l = n_p2p = 0
+    for d in bem.near_offsets(counts):
+        m2l, p2p = fmm2.interaction_lists(tree, -np.asarray(d, dtype=float) @ L)
+        n_m2l += len(m2l)
+        n_p2p += sum(len(tree.leaf_elements(a)) * len(tree.leaf_elements(b)) for a, b in p2p)
+    lv, got_m2l, got_p2p, _ = gb.near2_plan_counts(nodes, el, counts, lattice, near_levels=levels)
+    assert (lv, got_m2l, got_p2p) == (levels, n_m2l, n_p2p)
