@@ -353,6 +353,11 @@ fmpb_status fmpb_insertion_loss(const fmpb_operator *op, int R, const fmpb_c64 *
 fmpb_status fmpb_halfspace_plan(const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
                                 const fmpb_lattice *lattice, int plane_axis, double plane_offset,
                                 int32_t *hankel_axis, int32_t *n_near_image, double *dmin_far_image);
+/* The same plan on nine-node quadrilaterals (elems: n x 9 node indices; the
+ * one-side check reads the element centres, node 4, and all nodes). */
+fmpb_status fmpb_halfspace_plan_q9(const double *nodes, int64_t nn, const int32_t *elems, int64_t n,
+                                   const fmpb_lattice *lattice, int plane_axis, double plane_offset,
+                                   int32_t *hankel_axis, int32_t *n_near_image, double *dmin_far_image);
 
 /*
  * Host-side plan of the FMPBEM2 near field (FMPB_FORM_FMM2, Sec. 3.3), with

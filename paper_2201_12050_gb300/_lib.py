@@ -117,6 +117,7 @@ SIGNATURES = {
     "fmpb_rhs_incident": (INT, [P, INT, P, P, P]),
     "fmpb_insertion_loss": (INT, [P, INT, P, P, I64, P, P, P]),
     "fmpb_halfspace_plan": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, D, P, P, P]),
+    "fmpb_halfspace_plan_q9": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, D, P, P, P]),
     "fmpb_near2_plan_counts": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, INT, P, P, P, P]),
     "fmpb_near2_plan_counts_q9": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), INT, INT, P, P, P, P]),
     "fmpb_field_incident": (INT, [P, INT, P, P, I64, P, P, P]),

@@ -216,13 +216,15 @@ def _incidents(incidents):
 
 
 def halfspace_plan(verts, tris, counts, vectors, plane_axis, plane_offset):
-    """fmpb_halfspace_plan (host only): (perpendicular axis, near image offsets, nearest far image)."""
+    """fmpb_halfspace_plan, or fmpb_halfspace_plan_q9 for nine-column elements
+    (host only): (perpendicular axis, near image offsets, nearest far image)."""
     v = _host(verts, np.float64)
     t = _host(tris, np.int32)
     lat = _lattice(counts, vectors)
     h, nn, dmin = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    check(lib().fmpb_halfspace_plan(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), int(plane_axis),
-                                    float(plane_offset), ctypes.byref(h), ctypes.byref(nn), ctypes.byref(dmin)))
+    fn = lib().fmpb_halfspace_plan_q9 if t.ndim == 2 and t.shape[1] == 9 else lib().fmpb_halfspace_plan
+    check(fn(_ptr(v), len(v), _ptr(t), len(t), ctypes.byref(lat), int(plane_axis), float(plane_offset),
+             ctypes.byref(h), ctypes.byref(nn), ctypes.byref(dmin)))
     return h.value, nn.value, dmin.value
 
 

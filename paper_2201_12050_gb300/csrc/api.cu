@@ -930,13 +930,13 @@ fmpb_status fmpb_insertion_loss(const fmpb_operator* op, int R, const fmpb_c64* 
                         (const cd*)p, inc, npts, pts, il, (cudaStream_t)stream);
 }
 
-fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
-                                const fmpb_lattice* lattice, int plane_axis, double plane_offset,
-                                int32_t* hankel_axis, int32_t* n_near_image, double* dmin_far_image) {
-  CHECK_ARG(verts && tris && nv >= 3 && ntri >= 1, "halfspace_plan: bad mesh");
+static fmpb_status halfspace_plan_npe(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, int npe,
+                                      const fmpb_lattice* lattice, int plane_axis, double plane_offset,
+                                      int32_t* hankel_axis, int32_t* n_near_image, double* dmin_far_image) {
+  CHECK_ARG(verts && tris && nv >= npe && ntri >= 1, "halfspace_plan: bad mesh");
   CHECK_ARG(hankel_axis && n_near_image && dmin_far_image, "halfspace_plan: NULL output");
-  for (int64_t e = 0; e < 3 * ntri; ++e)
-    CHECK_ARG(tris[e] >= 0 && tris[e] < nv, "halfspace_plan: triangle index out of range");
+  for (int64_t e = 0; e < npe * ntri; ++e)
+    CHECK_ARG(tris[e] >= 0 && tris[e] < nv, "halfspace_plan: node index out of range");
   CellGrid g;
   FMPB_TRY(make_grid(lattice, g));
   fmpb_operator_opts o{};
@@ -945,7 +945,7 @@ fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* 
   o.plane_offset = plane_offset;
   o.Rp_re = 1.0;
   int h = -1;
-  FMPB_TRY(halfspace_check(g, o, verts, nv, tris, ntri, &h));
+  FMPB_TRY(halfspace_check(g, o, verts, nv, tris, ntri, &h, npe));
   std::vector<int32_t> offs;
   for (int dz = 1 - g.M[2]; dz < g.M[2]; ++dz)
     for (int dy = 1 - g.M[1]; dy < g.M[1]; ++dy)
@@ -965,6 +965,20 @@ fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* 
   *n_near_image = near;
   *dmin_far_image = dmin;
   return FMPB_OK;
+}
+
+fmpb_status fmpb_halfspace_plan(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri,
+                                const fmpb_lattice* lattice, int plane_axis, double plane_offset,
+                                int32_t* hankel_axis, int32_t* n_near_image, double* dmin_far_image) {
+  return halfspace_plan_npe(verts, nv, tris, ntri, 3, lattice, plane_axis, plane_offset, hankel_axis, n_near_image,
+                            dmin_far_image);
+}
+
+fmpb_status fmpb_halfspace_plan_q9(const double* nodes, int64_t nn, const int32_t* elems, int64_t n,
+                                   const fmpb_lattice* lattice, int plane_axis, double plane_offset,
+                                   int32_t* hankel_axis, int32_t* n_near_image, double* dmin_far_image) {
+  return halfspace_plan_npe(nodes, nn, elems, n, 9, lattice, plane_axis, plane_offset, hankel_axis, n_near_image,
+                            dmin_far_image);
 }
 
 static fmpb_status near2_counts(const double* verts, int64_t nv, const int32_t* idx, int64_t n, int npe,

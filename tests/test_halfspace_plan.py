@@ -46,3 +46,17 @@ def test_plan_rejects_oblique_lattices_and_crossing_cells():
         gb.halfspace_plan(v, t, (1, 1, 3), np.diag([1.0, 1.0, -0.5]), 2, -0.3)
     with pytest.raises(gb.FmpbError):
         gb.halfspace_plan(v, t, (2, 1, 1), np.diag([0.5, 1.0, 1.0]), 3, -0.3)
+
+
+@pytest.mark.parametrize("counts,lattice,plane", CASES[:2])
+def test_plan_on_nine_node_elements(counts, lattice, plane):
+    # the same plan from a quadrilateral cell, and the one-side check read from
+    # its element centres and nodes: a plane through the spheres is refused
+    from workloads import quad9_sphere
+    nodes, el = quad9_sphere(2, 0.2)
+    h, n_near, dmin = gb.halfspace_plan(nodes, el, counts, lattice, *plane)
+    pl = hs.Plane(plane[0], plane[1], 1.0)
+    assert h == hs.hankel_axis(lattice, counts, pl)
+    assert n_near == len(hs.image_near_offsets(lattice, counts, pl))
+    with pytest.raises(gb.FmpbError, match="EMESH"):
+        gb.halfspace_plan(nodes, el, counts, lattice, plane[0], 0.05)
