@@ -321,7 +321,7 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "ff48 (float-float pairs of FP32, 48-bit significand) with FP64 control", "data": "synthetic",
         "config": config_block(w, {"parallelism": f"replicas{world}" if world > 1 else "single",
                                    "pipeline": ("build of step i+1 overlapped with the solve of step i (second stream "
                                                 "and host thread); K steps = K builds + K solves"

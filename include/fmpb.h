@@ -279,12 +279,17 @@ typedef struct {
 
 /*
  * Solves A p_r = b_r for R right-hand sides by restarted GMRES (Sec. 4)
- * with x0 = 0 and no preconditioner.  Arnoldi: classical Gram-Schmidt with a
- * second pass when the first removes more than half of ||w||^2, on a Krylov
- * basis stored as float-float pairs (48-bit significands, FP32 pipe); Givens
- * rotations, Hessenberg data, solution update and the true residual in FP64.
- * All vectors live on the device; the host sequences launches and reads one
- * convergence flag per RHS per iteration.  MIXED operators run GMRES-IR:
+ * with x0 = 0 and no preconditioner.  Arnoldi: classical Gram-Schmidt with
+ * reorthogonalisation (the delayed form DCGS2 for operators with a
+ * float-float product, else CGS2 with a second pass when the first removes
+ * more than half of ||w||^2), on a Krylov basis stored as float-float pairs
+ * (48-bit significands, FP32 pipe); Givens rotations, Hessenberg data, the
+ * new rotation, the residual estimate, the solution update and the true
+ * residual in FP64.  All vectors live on the device; the host sequences
+ * launches and reads the per-RHS convergence flags once every few
+ * iterations (4 at first, more while the residual falls slowly); in between,
+ * the Arnoldi kernels of converged right-hand sides return at once on their
+ * device-side flag.  MIXED operators run GMRES-IR:
  * FP32-spectrum inner solves to inner_tol, outer residuals with the accurate
  * operator, until tol.
  *   b, p   device, R x N; p is overwritten.
@@ -508,7 +513,8 @@ fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fm
  * pruned FFT, the per-frequency B x B products and the pruned inverse FFT
  * (Sec. 2.4).   x, y device, R x (n_cells B), cell-major as above.
  *   accumulate  0: y = T x;  1: y += T x.
- * Allocates its scratch (about 2 F R B complex values) per call.
+ * Allocates its scratch (about 2 F R B complex values) per call.  B must be
+ * 1..2^20 and F R B below 2^59 (FMPB_EINVAL otherwise).
  */
 fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
                                  const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
@@ -542,8 +548,13 @@ fmpb_status fmpb_circulant_apply_bf16(const int32_t counts[3], int64_t B, const 
  *     the process exits.  Products needing more than 32 MiB of scratch return
  *     FMPB_EINVAL with the required size in fmpb_last_error().
  *   - The first call on a device looks up that array's device address (with
- *     the device current) and caches it; make that first call before any
- *     stream capture.
+ *     the device current) and caches it for the life of the process; make
+ *     that first call before any stream capture.  A device reset
+ *     (cudaDeviceReset) or a release of the primary context reloads the
+ *     library's device code, so the cached address is then stale: do not
+ *     call this entry point after either.
+ *   - B must be 1..2^20; counts, R and the 32 MiB limit are checked on the
+ *     host, before any CUDA call, without an overflowing size product.
  *   - Every call on a device shares the same array.  The array keeps the
  *     last call's contents, but nothing in it needs clearing: each call
  *     writes every element it reads.  Calls that may overlap on the GPU

@@ -411,8 +411,8 @@ static fmpb_status halfspace_check(const CellGrid& g, const fmpb_operator_opts& 
   }
   for (int64_t t = 0; t < ntri; ++t) {
     const double c = npe == 9 ? verts[3 * (int64_t)tris[9 * t + 4] + ax]
-                              : (verts[3 * tris[3 * t] + ax] + verts[3 * tris[3 * t + 1] + ax] +
-                                 verts[3 * tris[3 * t + 2] + ax]) / 3.0;
+                              : (verts[3 * (int64_t)tris[3 * t] + ax] + verts[3 * (int64_t)tris[3 * t + 1] + ax] +
+                                 verts[3 * (int64_t)tris[3 * t + 2] + ax]) / 3.0;
     cmin = fmin(cmin, c);
     cmax = fmax(cmax, c);
   }
@@ -1234,7 +1234,7 @@ fmpb_status fmpb_circulant_apply_bf16(const int32_t counts[3], int64_t B, const 
 
 fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R, const fmpb_c64* x,
                                  fmpb_c64* y, int accumulate, void* stream) {
-  CHECK_ARG(counts && spec && x && y && B >= 1, "circulant_apply: bad arguments");
+  CHECK_ARG(counts && spec && x && y && B >= 1 && B <= (1 << 20), "circulant_apply: bad arguments");
   CHECK_ARG(R >= 1 && R <= 4096, "circulant_apply: R out of range");
   int M[3];
   for (int a = 0; a < 3; ++a) {
@@ -1242,6 +1242,11 @@ fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_
     M[a] = counts[a];
   }
   CircShape sh = make_shape(M);
+  // 2 F R B complex values must be addressable: F < 2^40, R <= 4096 and
+  // B <= 2^20 keep 2 F R B 16 below 2^64 only while F R B stays below 2^59
+  CHECK_ARG((size_t)sh.F * (size_t)R <= ((size_t)1 << 59) / (size_t)B,
+            "circulant_apply: %lld frequencies x %d right-hand sides x B = %lld is too large", (long long)sh.F, R,
+            (long long)B);
   cudaStream_t st = (cudaStream_t)stream;
   cd* scratch = nullptr;
   FMPB_CUDA(cudaMallocAsync(&scratch, sizeof(cd) * circulant_scratch_elems(sh, B, R), st));

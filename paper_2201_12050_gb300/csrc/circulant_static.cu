@@ -54,8 +54,8 @@ using namespace fmpb;
 
 extern "C" fmpb_status fmpb_circulant_apply_static(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R,
                                                    const fmpb_c64* x, fmpb_c64* y, int accumulate, void* stream) {
-  if (!counts || !spec || !x || !y || B < 1) {
-    set_error("circulant_apply_static: bad arguments");
+  if (!counts || !spec || !x || !y || B < 1 || B > (1 << 20)) {
+    set_error("circulant_apply_static: bad arguments (B must be 1..%d)", 1 << 20);
     return FMPB_EINVAL;
   }
   if (R < 1 || R > 4096) {
@@ -71,8 +71,11 @@ extern "C" fmpb_status fmpb_circulant_apply_static(const int32_t counts[3], int6
     M[a] = counts[a];
   }
   const CircShape sh = make_shape(M);
-  const size_t need = circulant_scratch_elems(sh, B, R) * sizeof(cd);
-  if (need > STATIC_SCRATCH_BYTES) {
+  // 2 F R B complex values, tested without forming a product that could
+  // wrap: F R B <= limit  <=>  B <= limit / (F R)  (F < 2^40, R <= 4096)
+  const size_t per_b = 2 * sizeof(cd) * (size_t)sh.F * (size_t)R;
+  const size_t need = per_b * (size_t)B;
+  if ((size_t)B > STATIC_SCRATCH_BYTES / per_b || need > STATIC_SCRATCH_BYTES) {
     set_error("circulant_apply_static: this product needs %zu bytes of scratch (2 F R B complex values, "
               "F = %lld, R = %d, B = %lld) but the static array holds %zu bytes",
               need, (long long)sh.F, R, (long long)B, STATIC_SCRATCH_BYTES);

@@ -51,16 +51,49 @@ def test_static_scratch_product_matches_allocating_product(counts, B, R):
         assert np.linalg.norm(y_acc.cpu().numpy() - (b + x.cpu().numpy())) <= 1e-12 * np.linalg.norm(b)
 
 
-@pytest.mark.skipif(torch.cuda.is_available(), reason="host-side size check; run where no GPU is visible")
-def test_static_scratch_rejects_products_beyond_its_size():
-    """The size check runs on the host before any CUDA call, so it is tested
-    without a GPU: with no device visible, nothing can be launched."""
+def _host_only_library():
+    """The library for host-side argument checks: built here if need be, and
+    skipped where it cannot be built (no CUDA toolkit)."""
     from paper_2201_12050_gb300 import build
-    build.build()
-    L = gb.lib()
-    counts = np.array([40, 40, 1], dtype=np.int32)      # P = 80 x 80, F = 6400
-    B, R = 64, 8                                       # 2 F R B x 16 B = 105 MB > 32 MiB
+    try:
+        build.build()
+        return gb.lib()
+    except (RuntimeError, OSError) as e:
+        pytest.skip(f"library not available: {e}")
+
+
+# Every case below is refused on the host before any CUDA call, so these run
+# only where no GPU is visible: with no device, nothing can be launched even
+# if a check were wrong.
+@pytest.mark.skipif(torch.cuda.is_available(), reason="host-side size check; run where no GPU is visible")
+@pytest.mark.parametrize("counts,B,R,what", [
+    ((40, 40, 1), 64, 8, b"static array holds"),       # P = 80 x 80, F = 6400: 2 F R B x 16 B = 105 MB > 32 MiB
+    ((2, 1, 1), 1 << 20, 1, b"static array holds"),    # the largest B, F = 3: 96 MiB
+    ((1, 1, 1), 1 << 59, 1, b"bad arguments"),         # 2 F R B x 16 B wraps to 0 in 64 bits
+    ((1, 1, 1), (1 << 20) + 1, 1, b"bad arguments"),
+    ((1, 1, 1), 0, 1, b"bad arguments"),
+    ((1, 1, 1), 4, 0, b"R out of range"),
+    ((1, 1, 1), 4, 4097, b"R out of range"),
+    ((4097, 1, 1), 4, 1, b"count out of range"),
+    ((0, 1, 1), 4, 1, b"count out of range"),
+    ((4096, 4096, 1), 2, 4096, b"static array holds"),   # F R B near 2^41: no wrap in the test
+])
+def test_static_scratch_rejects_products_beyond_its_size(counts, B, R, what):
+    L = _host_only_library()
+    c = np.array(counts, dtype=np.int32)
     dummy = ctypes.c_void_p(256)
-    st = L.fmpb_circulant_apply_static(ctypes.c_void_p(counts.ctypes.data), B, dummy, R, dummy, dummy, 0, None)
+    st = L.fmpb_circulant_apply_static(ctypes.c_void_p(c.ctypes.data), ctypes.c_int64(B), dummy, R, dummy, dummy, 0,
+                                       None)
     assert st == -1
-    assert b"static array holds" in L.fmpb_last_error()
+    assert what in L.fmpb_last_error()
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="host-side size check; run where no GPU is visible")
+@pytest.mark.parametrize("counts,B,R", [((1, 1, 1), 1 << 59, 1), ((4096, 4096, 4096), 1 << 20, 4096),
+                                        ((1, 1, 1), (1 << 20) + 1, 1)])
+def test_allocating_product_rejects_sizes_that_overflow(counts, B, R):
+    L = _host_only_library()
+    c = np.array(counts, dtype=np.int32)
+    dummy = ctypes.c_void_p(256)
+    st = L.fmpb_circulant_apply(ctypes.c_void_p(c.ctypes.data), ctypes.c_int64(B), dummy, R, dummy, dummy, 0, None)
+    assert st == -1
