@@ -312,4 +312,7 @@ def test_q9_fmm2_converges_to_the_fmm_form():
     for ntn in (3, 6, 9):
         op = gb.Operator(nodes, el, counts, L, k, form=gb.FORM_FMM2, n_t=6, n_t_near=ntn, near_levels=2)
         errs.append(float(torch.linalg.vector_norm(op.matvec(x) - y_fmm) / torch.linalg.vector_norm(y_fmm)))
-    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-4, errs
+    # each step of 3 in n_t,near cuts the distance at least four-fold (the
+    # curved cell's leaf boxes are measured over all nine nodes, so the
+    # ratio is slower than on the flat triangles' cell)
+    assert errs[1] < errs[0] / 4 and errs[2] < errs[1] / 4 and errs[2] < 2e-4, errs
