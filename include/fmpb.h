@@ -121,7 +121,16 @@ typedef struct {
                       ratio 2 rho / |d| <= 2/3; else PBEM.  FMM forced with
                       |d| <= 2 rho is refused (EADMISS). */
   int n_t;         /* truncation number of the FMM form (Eq. (greenFMM)), 1..20;
-                      0 = default 8 */
+                      0 = the truncation rule: the smallest n_t in 4..20 whose
+                      U_0 K(d) V_0 reproduces the exact collocation block of
+                      the nearest far cell d (max-norm offset >= 2, shortest
+                      translation) on four fixed probe vectors
+                      x_j = exp(2 pi i frac((p+1) j phi)), phi = (sqrt 5 - 1)/2,
+                      p < 4, to a relative 1e-6 (Frobenius norm over the
+                      probes).  If none does, AUTO falls back to the PBEM
+                      form and a forced FMM form takes n_t = 20.  A grid
+                      without far cells takes 4.  fmpb_operator_info reports
+                      the n_t chosen. */
   int precision;   /* fmpb_precision: FMPB_FP64 (default), FMPB_FP32, FMPB_BF16
                       (FMM form only) or FMPB_MIXED */
   /* Uniform normalised surface admittance beta = beta_re + i beta_im
@@ -203,6 +212,8 @@ typedef struct {
   int64_t n_p2p_near;    /* FMPBEM2: exact entries kept */
   int32_t element;       /* fmpb_element of the mesh */
   int32_t pressure_order;/* pressure order of FMPB_ELEM_QUAD9 elements (n = elements x nodes) */
+  double n_t_rule_err;   /* the truncation rule's relative probe error at the n_t
+                            chosen (n_t = 0 requested), else -1 */
 } fmpb_operator_info;
 
 /*
@@ -213,7 +224,7 @@ typedef struct {
  *          so that (v1-v0) x (v2-v0) points from the body into the fluid
  *          (ntri x 9 node indices with opts->element = FMPB_ELEM_QUAD9).
  *   k      wavenumber omega/c > 0 (Eq. (helmholtz)).
- *   opts   may be NULL (AUTO form, n_t = 8, FP64).
+ *   opts   may be NULL (AUTO form, the truncation rule for n_t, FP64).
  * Builds, all on the device: element geometry and quadrature rules; the
  * offset blocks (all (2M-1)^d offsets in the PBEM form, the 3^d near offsets
  * in the FMM form) by the collocation quadrature of Eq. (bm); in the FMM
@@ -520,6 +531,20 @@ fmpb_status fmpb_circulant_apply(const int32_t counts[3], int64_t B, const fmpb_
                                  const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
 
 /*
+ * The product of fmpb_circulant_apply in complex FP32 (Sec. 2.4): the
+ * spectrum rounded to complex FP32, the pruned forward and inverse DFT
+ * passes, their intermediate values and the per-frequency products in FP32
+ * (8 bytes per value).  This is how FP32 operators and the inner solves of
+ * MIXED operators apply their block Toeplitz parts; relative accuracy about
+ * 1e-6.  Same arguments and layouts as fmpb_circulant_apply; every padded
+ * length must split into two factors of at most 16 (all lengths up to 256
+ * except a few, e.g. 245), else FMPB_EINVAL.  Allocates its FP32 copy of the
+ * spectrum and its scratch per call and synchronises the stream.
+ */
+fmpb_status fmpb_circulant_apply_f32(const int32_t counts[3], int64_t B, const fmpb_c64 *spec, int R,
+                                     const fmpb_c64 *x, fmpb_c64 *y, int accumulate, void *stream);
+
+/*
  * The product of fmpb_circulant_apply with the per-frequency products
  * Y_f = Lambda_f X_f on the tensor cores (tcgen05, BF16 inputs, FP32
  * accumulation): Lambda_f and X_f are rounded to BF16 (Lambda: FP64 -> FP32 ->
@@ -600,7 +625,7 @@ typedef struct {
   fmpb_lattice lattice;
   double k;
   int form;                  /* fmpb_form */
-  int n_t;                   /* FMM truncation number; 0 = 8 */
+  int n_t;                   /* FMM truncation number; 0 = the truncation rule */
   int R;                     /* plane waves, 1..64 */
   const double *dirs;        /* host, R x 3 unit vectors, copied at submit */
   const fmpb_c64 *amps;      /* host, R amplitudes or NULL (all 1), copied at submit */

@@ -160,3 +160,79 @@ def fmm_matvec_explicit(cell: CellMesh, lattice, counts, k, nt, p, near_blocks=N
                 Lc += Mom[:, cj] @ Kcache[delta].T
         Y[:, ci] += Lc @ U0.T
     return Y.reshape(R, -1)
+
+
+# ------------------------------------------------------ truncation rule --
+# The paper asks for a truncation number that is "sufficiently large"
+# (Sec. 3.1) and shows that the needed n_t grows with frequency (Sec. 4,
+# the accuracy study: n_t = 4 enough at 100 Hz, n_t >= 6 at 1 kHz).  The
+# rule read from that: the smallest n_t >= 4 for which the multipole form
+# U_0 K(d) V_0 of the block of the nearest far cell reproduces the exact
+# block T_d on a fixed set of probe vectors to a relative 1e-6.
+
+def probe_vectors(n, count=4):
+    """The probe vectors of the truncation rule, rows p < count:
+    x_j = exp(2 pi i frac((p + 1) j phi)), phi = (sqrt(5) - 1) / 2, j < n
+    (a deterministic, well-spread sequence; no random draw)."""
+    phi = (np.sqrt(5.0) - 1.0) / 2.0
+    j = np.arange(n, dtype=np.float64)
+    out = np.empty((count, n), dtype=complex)
+    for p in range(count):
+        t = np.fmod((p + 1) * j * phi, 1.0)
+        out[p] = np.exp(2j * np.pi * t)
+    return out
+
+
+def nearest_far_offset(lattice, counts):
+    """The far offset (max-norm >= 2, inside the grid's offset range) whose
+    translation d . lattice is shortest; ties go to the first in the order
+    dz, dy, dx ascending.  None if the grid has no far cell pair."""
+    L = np.asarray(lattice, dtype=np.float64)
+    M = list(counts) + [1] * (3 - len(counts))
+    best, bd = None, np.inf
+    for dz in range(1 - M[2], M[2]):
+        for dy in range(1 - M[1], M[1]):
+            for dx in range(1 - M[0], M[0]):
+                if max(abs(dx), abs(dy), abs(dz)) <= 1:
+                    continue
+                d = np.linalg.norm(np.array([dx, dy, dz], dtype=np.float64) @ L)
+                if d < bd:
+                    best, bd = (dx, dy, dz), d
+    return best
+
+
+def truncation_errors(cell: CellMesh, lattice, counts, k, beta=0.0, nt_min=4, nt_max=20, block=None):
+    """{n_t: ||(U_0 K(d) V_0 - T_d) X|| / ||T_d X||} over n_t_min..n_t_max for
+    the nearest far offset d and the probe vectors X (Frobenius norms over
+    the probes).  The tables of n_t are the leading (n_t + 1)^2 rows and
+    columns of those of n_t_max (every entry depends only on its degrees and
+    orders).  block: T_d if already computed."""
+    d = nearest_far_offset(lattice, counts)
+    if d is None:
+        return None, {}
+    L = np.asarray(lattice, dtype=np.float64)
+    T = toeplitz_block(cell, L, d, k, beta) if block is None else block
+    X = probe_vectors(cell.n)
+    TX = X @ T.T
+    V = p2m_table(cell, k, nt_max, beta)
+    U = l2p_table(cell, k, nt_max)
+    K = m2l_block(np.asarray(d, dtype=np.float64) @ L, k, nt_max)
+    errs = {}
+    for nt in range(nt_min, nt_max + 1):
+        B = (nt + 1) ** 2
+        Y = ((X @ V[:B].T) @ K[:B, :B].T) @ U[:, :B].T
+        errs[nt] = np.linalg.norm(Y - TX) / np.linalg.norm(TX)
+    return d, errs
+
+
+def auto_truncation(cell: CellMesh, lattice, counts, k, beta=0.0, tol=1e-6, nt_min=4, nt_max=20):
+    """The truncation rule: the smallest n_t in nt_min..nt_max meeting tol
+    (nt_min when the grid has no far cell pair; None when no n_t up to
+    nt_max meets it)."""
+    d, errs = truncation_errors(cell, lattice, counts, k, beta, nt_min, nt_max)
+    if d is None:
+        return nt_min
+    for nt in range(nt_min, nt_max + 1):
+        if errs[nt] <= tol:
+            return nt
+    return None

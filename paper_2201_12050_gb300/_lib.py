@@ -35,7 +35,7 @@ class OperatorOpts(ctypes.Structure):
                 ("halfspace", ctypes.c_int32), ("plane_axis", ctypes.c_int32), ("plane_offset", ctypes.c_double),
                 ("Rp_re", ctypes.c_double), ("Rp_im", ctypes.c_double),
                 ("n_t_near", ctypes.c_int32), ("near_levels", ctypes.c_int32), ("element", ctypes.c_int32),
-                ("pressure_order", ctypes.c_int32)]
+                ("pressure_order", ctypes.c_int32), ("n_t_rule_err", ctypes.c_double)]
 
 
 class C64(ctypes.Structure):
@@ -55,7 +55,7 @@ class OperatorInfo(ctypes.Structure):
                 ("halfspace", ctypes.c_int32), ("hankel_axis", ctypes.c_int32), ("n_near_image", ctypes.c_int32),
                 ("image_separate", ctypes.c_int32), ("near_levels", ctypes.c_int32),
                 ("n_m2l_near", ctypes.c_int64), ("n_p2p_near", ctypes.c_int64), ("element", ctypes.c_int32),
-                ("pressure_order", ctypes.c_int32)]
+                ("pressure_order", ctypes.c_int32), ("n_t_rule_err", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -132,6 +132,7 @@ SIGNATURES = {
     "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_apply_static": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_circulant_apply_bf16": (INT, [P, I64, P, INT, P, P, INT, P]),
+    "fmpb_circulant_apply_f32": (INT, [P, I64, P, INT, P, P, INT, P]),
     "fmpb_server_create": (INT, [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]),
     "fmpb_server_submit": (INT, [P, ctypes.POINTER(Request), P, ctypes.POINTER(ctypes.c_uint64)]),
     "fmpb_server_wait": (INT, [P, ctypes.c_uint64, INT, ctypes.POINTER(Result)]),

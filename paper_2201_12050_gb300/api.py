@@ -354,6 +354,18 @@ def circulant_apply(counts, spec, x, out=None, accumulate=False):
     return y
 
 
+def circulant_apply_f32(counts, spec, x, out=None, accumulate=False):
+    """fmpb_circulant_apply_f32: the circulant product in complex FP32 (spectrum, DFT passes, products)."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    B = spec.shape[-1]
+    ncell = int(np.prod(c))
+    R = _cvec(x, ncell * B, "x")
+    y = out if out is not None else torch.empty_like(x)
+    check(lib().fmpb_circulant_apply_f32(_ptr(c), B, _ptr(spec.contiguous()), R, _ptr(x), _ptr(y),
+                                         1 if accumulate else 0, _stream()))
+    return y
+
+
 def circulant_apply_bf16(counts, spec, x, out=None, accumulate=False):
     """fmpb_circulant_apply_bf16: the circulant product with BF16 tensor-core frequency products."""
     c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)

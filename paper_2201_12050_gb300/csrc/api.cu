@@ -133,7 +133,9 @@ fmpb_status plan_operator(const double* verts, int64_t nv, const int32_t* tris, 
   }
   FMPB_TRY(decide_form(g, rho, opts->form, form, nullptr, nullptr, nullptr));
   const CircShape sh = make_shape(g.M);
-  const int nt = opts->n_t > 0 ? opts->n_t : 8;
+  // the truncation rule (n_t = 0) needs device work; admission plans with
+  // n_t = 12, above what the rule picks for the cells it was tried on (10-11)
+  const int nt = opts->n_t > 0 ? opts->n_t : 12;
   const int64_t n = ntri;
   const int64_t b = *form == FMPB_FORM_PBEM ? n : (int64_t)(nt + 1) * (nt + 1);
   const int dim = (g.M[0] > 1) + (g.M[1] > 1) + (g.M[2] > 1);
@@ -172,6 +174,7 @@ struct fmpb_operator {
   cd beta = {0.0, 0.0};     // uniform normalised admittance (0: rigid)
   int form = FMPB_FORM_PBEM;
   int nt = 0;
+  double nt_rule_err = -1.0;   // relative probe error of the truncation rule's n_t (-1: n_t given)
   int64_t B = 0;
   int dim = 0;
   cd* spec = nullptr;      // F x B x B, float-float pairs (re_hi, re_lo, im_hi, im_lo) per entry
@@ -256,16 +259,18 @@ struct fmpb_operator {
     const bool f32 = precision == FMPB_FP32 || (precision == FMPB_MIXED && low);
     const cd* sp = f32 ? reinterpret_cast<const cd*>(spec32) : spec;
     const int fmt = f32 ? SPEC_F32 : SPEC_FF;
+    // low-precision spectra take FP32 DFT passes (8-byte frequency values)
+    const bool p32 = f32 && circulant_f32_ok(shape);
     if (form == FMPB_FORM_PBEM) {
       const size_t circ = circulant_scratch_elems(shape, B, R);
       FMPB_TRY(ensure_scratch(circ + (img_sep ? (size_t)R * Nc * B : 0)));
-      FMPB_TRY(circulant_apply(shape, B, sp, R, x, y, false, scratch, st, fmt));
+      FMPB_TRY(circulant_apply(shape, B, sp, R, x, y, false, scratch, st, fmt, nullptr, nullptr, false, p32));
       if (img_sep) {
         // the block Hankel image part: (T^ P)(P x) (Sec. 2.4)
         cd* q = scratch + circ;
         FMPB_TRY(reverse_cells(x, q, sizeof(cd), R, shape.M, mesh.n, hankel, st));
         const cd* spi = f32 ? reinterpret_cast<const cd*>(spec32_img) : spec_img;
-        FMPB_TRY(circulant_apply(shape, B, spi, R, q, y, true, scratch, st, fmt));
+        FMPB_TRY(circulant_apply(shape, B, spi, R, q, y, true, scratch, st, fmt, nullptr, nullptr, false, p32));
       }
       return FMPB_OK;
     }
@@ -307,7 +312,7 @@ struct fmpb_operator {
       FMPB_TRY(tc_offset_gemm(Sb, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st));
       FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
       FMPB_TRY(circulant_apply(shape, B, reinterpret_cast<const cd*>(specb), R, Mom, Loc, false, scratch, st,
-                               SPEC_BF16, fb, tc_err));
+                               SPEC_BF16, fb, tc_err, false, circulant_f32_ok(shape)));
       FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
       FMPB_TRY(tc_offset_gemm(U0b, zero, n, B, shape.M, R, lb, y, true, tc_err, st));
       return FMPB_OK;
@@ -322,7 +327,7 @@ struct fmpb_operator {
       FMPB_TRY(near_apply_f32(reinterpret_cast<const float2*>(S), near_offs, n_near, mesh.n, shape.M, R, x32, y, false,
                               st));
       FMPB_TRY(p2m_apply_f32(reinterpret_cast<const float2*>(V0), mesh.n, (int)B, (int64_t)R * Nc, x32, Mom, st));
-      FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt));
+      FMPB_TRY(circulant_apply(shape, B, sp, R, Mom, Loc, false, scratch, st, fmt, nullptr, nullptr, false, p32));
       if (img_sep) {
         float2* q32 = x32;
         if (hankel >= 0) {
@@ -332,7 +337,7 @@ struct fmpb_operator {
         FMPB_TRY(near_apply_f32(reinterpret_cast<const float2*>(S_img), near_offs_img, n_near_img, mesh.n, shape.M, R,
                                 q32, y, true, st));
         FMPB_TRY(p2m_apply_f32(reinterpret_cast<const float2*>(V0_img), mesh.n, (int)B, (int64_t)R * Nc, q32, Mom, st));
-        FMPB_TRY(circulant_apply(shape, B, spi, R, Mom, Loc, true, scratch, st, fmt));
+        FMPB_TRY(circulant_apply(shape, B, spi, R, Mom, Loc, true, scratch, st, fmt, nullptr, nullptr, false, p32));
       }
       FMPB_TRY(l2p_apply_f32(reinterpret_cast<const float2*>(U0), mesh.n, (int)B, (int64_t)R * Nc, Loc, y, st));
       return FMPB_OK;
@@ -523,8 +528,8 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
   CHECK_ARG(o.precision == FMPB_FP64 || o.precision == FMPB_FP32 || o.precision == FMPB_BF16 ||
                 o.precision == FMPB_MIXED,
             "operator_create: precision must be FMPB_FP64, FMPB_FP32, FMPB_BF16 or FMPB_MIXED");
-  const int nt = o.n_t > 0 ? o.n_t : 8;
-  CHECK_ARG(nt >= 1 && nt <= MAX_NT, "operator_create: n_t must be 1..%d", MAX_NT);
+  CHECK_ARG(o.n_t >= 0 && o.n_t <= MAX_NT, "operator_create: n_t must be 0 (the truncation rule) or 1..%d", MAX_NT);
+  int nt = o.n_t;
   CHECK_ARG(std::isfinite(o.beta_re) && std::isfinite(o.beta_im), "operator_create: admittance must be finite");
   CHECK_ARG(o.element == FMPB_ELEM_TRI3 || o.element == FMPB_ELEM_QUAD9,
             "operator_create: element must be FMPB_ELEM_TRI3 or FMPB_ELEM_QUAD9");
@@ -601,6 +606,21 @@ fmpb_status fmpb_operator_create(const double* verts, int64_t nv, const int32_t*
       return fail(FMPB_EINVAL);
     }
     op->img_sep = form == FMPB_FORM_FMM || op->hankel >= 0;
+  }
+  // n_t = 0: the truncation rule on the cell itself; an AUTO form whose far
+  // blocks no n_t up to MAX_NT reproduces to the rule's tolerance falls back
+  // to the exact PBEM form
+  if (form != FMPB_FORM_PBEM && nt == 0) {
+    bool met = false;
+    double terr = 0.0;
+    s = auto_truncation(op->mesh, op->grid, k, beta, &nt, &met, &terr, st);
+    if (s != FMPB_OK) return fail(s);
+    op->nt_rule_err = terr;
+    if (!met && o.form == FMPB_FORM_AUTO) {
+      form = FMPB_FORM_PBEM;
+      nt = 0;
+      if (op->plane.on) op->img_sep = op->hankel >= 0;
+    }
   }
   op->form = form;
   if (form == FMPB_FORM_PBEM) {
@@ -830,6 +850,7 @@ fmpb_status fmpb_operator_get_info(const fmpb_operator* op, fmpb_operator_info* 
   info->n_p2p_near = op->near2 ? op->near2->n_p2p : 0;
   info->element = op->mesh.nodes == 9 ? FMPB_ELEM_QUAD9 : FMPB_ELEM_TRI3;
   info->pressure_order = op->mesh.q9_order;
+  info->n_t_rule_err = op->nt_rule_err;
   return FMPB_OK;
 }
 
@@ -1229,6 +1250,37 @@ fmpb_status fmpb_circulant_apply_bf16(const int32_t counts[3], int64_t B, const 
   cudaFree(rows);
   cudaFree(scratch);
   cudaFree(err);
+  return s;
+}
+
+fmpb_status fmpb_circulant_apply_f32(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R,
+                                     const fmpb_c64* x, fmpb_c64* y, int accumulate, void* stream) {
+  CHECK_ARG(counts && spec && x && y && B >= 1 && B <= (1 << 20), "circulant_apply_f32: bad arguments");
+  CHECK_ARG(R >= 1 && R <= 4096, "circulant_apply_f32: R out of range");
+  CHECK_ARG((const void*)x != (const void*)y, "circulant_apply_f32: x and y must not alias");
+  int M[3];
+  for (int a = 0; a < 3; ++a) {
+    CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "circulant_apply_f32: count out of range");
+    M[a] = counts[a];
+  }
+  const CircShape sh = make_shape(M);
+  CHECK_ARG(circulant_f32_ok(sh), "circulant_apply_f32: padded lengths %d x %d x %d do not all split into two "
+            "factors of at most 16", sh.P[0], sh.P[1], sh.P[2]);
+  CHECK_ARG((size_t)sh.F * (size_t)R <= ((size_t)1 << 59) / (size_t)B && (size_t)sh.F * B <= ((size_t)1 << 59) / B,
+            "circulant_apply_f32: product too large");
+  cudaStream_t st = (cudaStream_t)stream;
+  float2* spec32 = nullptr;
+  cd* scratch = nullptr;
+  size_t bytes = 0;
+  fmpb_status s = dev_alloc(&spec32, (size_t)sh.F * B * B, bytes);
+  if (s == FMPB_OK) s = dev_alloc(&scratch, circulant_scratch_elems(sh, B, R) / 2 + 1, bytes);
+  if (s == FMPB_OK) s = vector_to_f32((const cd*)spec, spec32, (size_t)sh.F * B * B, st);
+  if (s == FMPB_OK)
+    s = circulant_apply(sh, B, reinterpret_cast<const cd*>(spec32), R, (const cd*)x, (cd*)y, accumulate != 0,
+                        scratch, st, SPEC_F32, nullptr, nullptr, false, true);
+  cudaStreamSynchronize(st);
+  cudaFree(spec32);
+  cudaFree(scratch);
   return s;
 }
 

@@ -213,34 +213,56 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
   return FMPB_OK;
 }
 
+// One pass along an axis: the two-factor kernel of dft.cu wherever the
+// length splits into factors of at most 16, else the direct float-float
+// kernel above (a few long axes).
+static fmpb_status axis_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out,
+                             int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2,
+                             int64_t bf, int Pin, int Pout, int P, int sign, double scale, bool accumulate,
+                             cudaStream_t st) {
+  if (dft_supported(P))
+    return dft_pass(name, ff_arith, in_fmt, out_fmt, in, out, O1, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign,
+                    scale, accumulate, st);
+  if (ff_arith) {
+    if (in_fmt == DFT_CD && out_fmt == DFT_FF)
+      return dft_axis<false, true>(name, in, out, O1, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
+                                   accumulate, st);
+    if (in_fmt == DFT_FF && out_fmt == DFT_FF)
+      return dft_axis<true, true>(name, in, out, O1, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
+                                  accumulate, st);
+    if (in_fmt == DFT_FF && out_fmt == DFT_CD)
+      return dft_axis<true, false>(name, in, out, O1, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
+                                   accumulate, st);
+  }
+  set_error("%s: axis length %d needs the direct float-float pass", name, P);
+  return FMPB_EINVAL;
+}
+
+bool circulant_f32_ok(const CircShape& s) {
+  for (int a = 0; a < 3; ++a)
+    if (s.P[a] > 1 && !dft_supported(s.P[a])) return false;
+  return true;
+}
+
 // In-place forward DFT of a complex-double grid of F slots x `inner`
 // values; the result is left in float-float format (the first pass converts).
 fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaStream_t st) {
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   bool ff = false;
   if (Px > 1) {
-    FMPB_TRY((dft_axis<false, true>("dft_spectrum", grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner, inner, 0,
-                                    (int64_t)Px * inner, inner, Px, Px, Px, -1, 1.0, false, st)));
+    FMPB_TRY(axis_pass("dft_spectrum", true, DFT_CD, DFT_FF, grid, grid, 1, Pz * Py, inner, 0, (int64_t)Px * inner,
+                       inner, 0, (int64_t)Px * inner, inner, Px, Px, Px, -1, 1.0, false, st));
     ff = true;
   }
   if (Py > 1) {
-    if (ff)
-      FMPB_TRY((dft_axis<true, true>("dft_spectrum", grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner,
-                                     (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py, Py, Py, -1, 1.0, false,
-                                     st)));
-    else
-      FMPB_TRY((dft_axis<false, true>("dft_spectrum", grid, grid, Pz, Px, inner, (int64_t)Py * Px * inner, inner,
-                                      (int64_t)Px * inner, (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, Py,
-                                      Py, Py, -1, 1.0, false, st)));
+    FMPB_TRY(axis_pass("dft_spectrum", true, ff ? DFT_FF : DFT_CD, DFT_FF, grid, grid, Pz, Px, inner,
+                       (int64_t)Py * Px * inner, inner, (int64_t)Px * inner, (int64_t)Py * Px * inner, inner,
+                       (int64_t)Px * inner, Py, Py, Py, -1, 1.0, false, st));
     ff = true;
   }
   if (Pz > 1) {
-    if (ff)
-      FMPB_TRY((dft_axis<true, true>("dft_spectrum", grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
-                                     (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st)));
-    else
-      FMPB_TRY((dft_axis<false, true>("dft_spectrum", grid, grid, 1, Py * Px, inner, 0, inner, (int64_t)Py * Px * inner, 0, inner,
-                                      (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st)));
+    FMPB_TRY(axis_pass("dft_spectrum", true, ff ? DFT_FF : DFT_CD, DFT_FF, grid, grid, 1, Py * Px, inner, 0, inner,
+                       (int64_t)Py * Px * inner, 0, inner, (int64_t)Py * Px * inner, Pz, Pz, Pz, -1, 1.0, false, st));
     ff = true;
   }
   if (!ff) FMPB_TRY(spectrum_to_ff(grid, (size_t)s.F * inner, st));
@@ -356,19 +378,31 @@ static fmpb_status spectrum_from_ff(cd* spec, size_t n, cudaStream_t st) {
 // X_f (float-float) is rounded to FP32 in shared memory, products and sums
 // are FP32, Y_f is written as float-float with a zero low part.  8-byte
 // spectrum entries halve the bytes streamed per product.
-template <int RC>
-__global__ void __launch_bounds__(256) k_block_product_f32(const float2* __restrict__ spec, const float4* __restrict__ X,
-                                                           float4* __restrict__ Y, int64_t B, int R, int r0,
+// XT: float4 (float-float frequency values, output with a zero low part) or
+// float2 (complex FP32 frequency values of FP32 DFT passes).
+__device__ __forceinline__ float2 to_f32(float4 v) { return make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w)); }
+__device__ __forceinline__ float2 to_f32(float2 v) { return v; }
+template <typename XT>
+__device__ __forceinline__ XT from_f32(float re, float im);
+template <>
+__device__ __forceinline__ float4 from_f32<float4>(float re, float im) {
+  return make_float4(re, 0.f, im, 0.f);
+}
+template <>
+__device__ __forceinline__ float2 from_f32<float2>(float re, float im) {
+  return make_float2(re, im);
+}
+
+template <int RC, typename XT>
+__global__ void __launch_bounds__(256) k_block_product_f32(const float2* __restrict__ spec, const XT* __restrict__ X,
+                                                           XT* __restrict__ Y, int64_t B, int R, int r0,
                                                            int rows_per_cta) {
   extern __shared__ float2 xs2[];   // RC x B
   const int64_t f = blockIdx.y;
   const int64_t RB = (int64_t)R * B;
-  const float4* Xf = X + f * RB + (int64_t)r0 * B;
+  const XT* Xf = X + f * RB + (int64_t)r0 * B;
   const int rc = min(RC, R - r0);
-  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) {
-    const float4 v = Xf[e];
-    xs2[e] = make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
-  }
+  for (int64_t e = threadIdx.x; e < (int64_t)rc * B; e += blockDim.x) xs2[e] = to_f32(Xf[e]);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
@@ -409,21 +443,22 @@ __global__ void __launch_bounds__(256) k_block_product_f32(const float2* __restr
         re[r] += __shfl_xor_sync(0xffffffffu, re[r], o);
         im[r] += __shfl_xor_sync(0xffffffffu, im[r], o);
       }
-      if (lane == 0 && r < rc) Y[f * RB + (int64_t)(r0 + r) * B + b] = make_float4(re[r], 0.f, im[r], 0.f);
+      if (lane == 0 && r < rc) Y[f * RB + (int64_t)(r0 + r) * B + b] = from_f32<XT>(re[r], im[r]);
     }
   }
 }
 
-template <int RC>
-static fmpb_status launch_block_product_f32(const float2* spec, const float4* X, float4* Y, int64_t F, int64_t B,
+template <int RC, typename XT>
+static fmpb_status launch_block_product_f32(const float2* spec, const XT* X, XT* Y, int64_t F, int64_t B,
                                             int R, cudaStream_t st) {
   const int threads = 256, rows = 32;
   const size_t smem = (size_t)RC * B * sizeof(float2);
   if (smem > 48 * 1024)
-    FMPB_CUDA(cudaFuncSetAttribute(k_block_product_f32<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMPB_CUDA(cudaFuncSetAttribute(k_block_product_f32<RC, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
   dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
   for (int r0 = 0; r0 < R; r0 += RC) {
-    FMPB_LAUNCH("block_product_f32", st, k_block_product_f32<RC><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
+    FMPB_LAUNCH("block_product_f32", st, k_block_product_f32<RC, XT><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
     FMPB_CUDA(cudaGetLastError());
   }
   return FMPB_OK;
@@ -466,9 +501,11 @@ static fmpb_status launch_block_product(const void* spec, const float4* X, float
 // share a spectrum tile run together and reuse it from L2.  FF: float-float
 // spectrum and arithmetic; otherwise complex FP32 spectrum and FP32 FMAs.
 constexpr int BPT_B = 32, BPT_R = 32, BPT_K = 16;
-template <bool FF>
+__device__ __forceinline__ float4 to_ff4(float4 v) { return v; }
+__device__ __forceinline__ float4 to_ff4(float2 v) { return make_float4(v.x, 0.f, v.y, 0.f); }
+template <bool FF, typename XT>
 __global__ void __launch_bounds__(256) k_block_product_tiled(const void* __restrict__ spec_,
-                                                             const float4* __restrict__ X, float4* __restrict__ Y,
+                                                             const XT* __restrict__ X, XT* __restrict__ Y,
                                                              int64_t B, int R) {
   __shared__ float4 Ls[BPT_B][BPT_K + 1];
   __shared__ float4 Xs[BPT_K][BPT_R + 1];
@@ -476,7 +513,7 @@ __global__ void __launch_bounds__(256) k_block_product_tiled(const void* __restr
   const int r0 = blockIdx.x * BPT_R;
   const int64_t b0 = (int64_t)blockIdx.z * BPT_B;
   const int64_t RB = (int64_t)R * B;
-  const float4* Xf = X + f * RB;
+  const XT* Xf = X + f * RB;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float rh[2][2], rl[2][2], ih[2][2], il[2][2];
   for (int a = 0; a < 2; ++a)
@@ -502,7 +539,7 @@ __global__ void __launch_bounds__(256) k_block_product_tiled(const void* __restr
       const int rr = e / BPT_K, kk = e - rr * BPT_K;
       const int r = r0 + rr;
       const int64_t k = k0 + kk;
-      Xs[kk][rr] = (r < R && k < B) ? Xf[(int64_t)r * B + k] : zero;
+      Xs[kk][rr] = (r < R && k < B) ? to_ff4(Xf[(int64_t)r * B + k]) : zero;
     }
     __syncthreads();
 #pragma unroll 4
@@ -534,14 +571,17 @@ __global__ void __launch_bounds__(256) k_block_product_tiled(const void* __restr
     for (int b = 0; b < 2; ++b) {
       const int64_t row = b0 + ty + 16 * a;
       const int r = r0 + tx + 16 * b;
-      if (row < B && r < R)
-        Y[f * RB + (int64_t)r * B + row] =
-            FF ? ff_norm(rh[a][b], rl[a][b], ih[a][b], il[a][b]) : make_float4(rh[a][b], 0.f, ih[a][b], 0.f);
+      if (row < B && r < R) {
+        if constexpr (FF)
+          Y[f * RB + (int64_t)r * B + row] = ff_norm(rh[a][b], rl[a][b], ih[a][b], il[a][b]);
+        else
+          Y[f * RB + (int64_t)r * B + row] = from_f32<XT>(rh[a][b], ih[a][b]);
+      }
     }
 }
 
-template <bool FF>
-static fmpb_status launch_block_product_tiled(const void* spec, const float4* X, float4* Y, int64_t F, int64_t B,
+template <bool FF, typename XT>
+static fmpb_status launch_block_product_tiled(const void* spec, const XT* X, XT* Y, int64_t F, int64_t B,
                                               int R, cudaStream_t st) {
   const int64_t btiles = (B + BPT_B - 1) / BPT_B;
   if (btiles > 65535) {
@@ -549,17 +589,49 @@ static fmpb_status launch_block_product_tiled(const void* spec, const float4* X,
     return FMPB_EINVAL;
   }
   dim3 grid((unsigned)((R + BPT_R - 1) / BPT_R), (unsigned)F, (unsigned)btiles);
-  FMPB_LAUNCH(FF ? "block_product_tiled" : "block_product_tiled_f32", st, k_block_product_tiled<FF><<<grid, 256, 0, st>>>(spec, X, Y, B, R));
+  FMPB_LAUNCH(FF ? "block_product_tiled" : "block_product_tiled_f32", st, k_block_product_tiled<FF, XT><<<grid, 256, 0, st>>>(spec, X, Y, B, R));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
 
-static fmpb_status block_product(const void* spec, int spec_format, const float4* X, float4* Y, int64_t F,
-                                 int64_t B, int R, cudaStream_t st, void* tc_rows, unsigned* tc_err) {
+// X, Y: the frequency-domain values [f][r][b], float-float (float4) or, with
+// f32_io, complex FP32 (float2; FP32 and BF16 spectra only).
+static fmpb_status block_product(const void* spec, int spec_format, const void* Xv, void* Yv, int64_t F,
+                                 int64_t B, int R, cudaStream_t st, void* tc_rows, unsigned* tc_err,
+                                 bool f32_io = false) {
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
     return FMPB_EINVAL;
   }
+  if (f32_io) {
+    if (spec_format != SPEC_F32 && spec_format != SPEC_BF16) {
+      set_error("block_product: FP32 frequency values take an FP32 or BF16 spectrum");
+      return FMPB_EINVAL;
+    }
+    const float2* X2 = reinterpret_cast<const float2*>(Xv);
+    float2* Y2 = reinterpret_cast<float2*>(Yv);
+    if (spec_format == SPEC_BF16) {
+      if (!tc_rows || !tc_err) {
+        set_error("block_product: BF16 spectrum without tensor-core scratch");
+        return FMPB_EINVAL;
+      }
+      __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tc_rows);
+      FMPB_TRY(tc_rows_from_f32(X2, F * R, B, rows, st));
+      return tc_freq_gemm(reinterpret_cast<const __nv_bfloat16*>(spec), F, B, R, rows, Y2, tc_err, st, true);
+    }
+    if (R >= 8) return launch_block_product_tiled<false, float2>(spec, X2, Y2, F, B, R, st);
+    const int RC2 = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+    if ((size_t)RC2 * B * sizeof(float2) > 200 * 1024) {
+      set_error("block_product: block size %lld too large", (long long)B);
+      return FMPB_EINVAL;
+    }
+    const float2* sp = reinterpret_cast<const float2*>(spec);
+    if (RC2 == 4) return launch_block_product_f32<4, float2>(sp, X2, Y2, F, B, R, st);
+    if (RC2 == 2) return launch_block_product_f32<2, float2>(sp, X2, Y2, F, B, R, st);
+    return launch_block_product_f32<1, float2>(sp, X2, Y2, F, B, R, st);
+  }
+  const float4* X = reinterpret_cast<const float4*>(Xv);
+  float4* Y = reinterpret_cast<float4*>(Yv);
   // BF16 spectrum: every frequency's product on the tensor cores
   if (spec_format == SPEC_BF16) {
     if (!tc_rows || !tc_err) {
@@ -571,8 +643,8 @@ static fmpb_status block_product(const void* spec, int spec_format, const float4
     return tc_freq_gemm(reinterpret_cast<const __nv_bfloat16*>(spec), F, B, R, rows, Y, tc_err, st);
   }
   // many right-hand sides: one tiled pass over the spectrum
-  if (R >= 8 && spec_format == SPEC_FF) return launch_block_product_tiled<true>(spec, X, Y, F, B, R, st);
-  if (R >= 8 && spec_format == SPEC_F32) return launch_block_product_tiled<false>(spec, X, Y, F, B, R, st);
+  if (R >= 8 && spec_format == SPEC_FF) return launch_block_product_tiled<true, float4>(spec, X, Y, F, B, R, st);
+  if (R >= 8 && spec_format == SPEC_F32) return launch_block_product_tiled<false, float4>(spec, X, Y, F, B, R, st);
   const int RC = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
   if ((size_t)RC * B * sizeof(float4) > 200 * 1024) {
     set_error("block_product: block size %lld too large", (long long)B);
@@ -580,9 +652,9 @@ static fmpb_status block_product(const void* spec, int spec_format, const float4
   }
   if (spec_format == SPEC_F32) {
     const float2* sp = reinterpret_cast<const float2*>(spec);
-    if (RC == 4) return launch_block_product_f32<4>(sp, X, Y, F, B, R, st);
-    if (RC == 2) return launch_block_product_f32<2>(sp, X, Y, F, B, R, st);
-    return launch_block_product_f32<1>(sp, X, Y, F, B, R, st);
+    if (RC == 4) return launch_block_product_f32<4, float4>(sp, X, Y, F, B, R, st);
+    if (RC == 2) return launch_block_product_f32<2, float4>(sp, X, Y, F, B, R, st);
+    return launch_block_product_f32<1, float4>(sp, X, Y, F, B, R, st);
   }
   if (spec_format == SPEC_FF) {
     if (RC == 4) return launch_block_product<4, true>(spec, X, Y, F, B, R, st);
@@ -598,58 +670,59 @@ size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 
 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format, void* tc_rows,
-                            unsigned* tc_err, bool ff_io) {
+                            unsigned* tc_err, bool ff_io, bool f32_passes) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
   const int64_t Nc = s.ncells;
-  // two float-float buffers (16 bytes per value, like complex double); an
-  // axis with a single cell (P = 1) leaves the layout unchanged and is skipped
-  float4* buf[2] = {reinterpret_cast<float4*>(scratch), reinterpret_cast<float4*>(scratch + (size_t)s.F * RB)};
+  if (f32_passes && (ff_io || (spec_format != SPEC_F32 && spec_format != SPEC_BF16) || !circulant_f32_ok(s))) {
+    set_error("circulant_apply: FP32 passes take an FP32 or BF16 spectrum, complex-double vectors and axis lengths "
+              "that split into factors of at most 16");
+    return FMPB_EINVAL;
+  }
+  // two buffers of frequency-domain values: float-float (16 bytes per value,
+  // like complex double) or complex FP32 (8 bytes); an axis with a single
+  // cell (P = 1) leaves the layout unchanged and is skipped
+  const bool ffa = !f32_passes;
+  const size_t vb = ffa ? sizeof(float4) : sizeof(float2);
+  char* sb = reinterpret_cast<char*>(scratch);
+  void* buf[2] = {sb, sb + (size_t)s.F * RB * vb};
+  const int mid = ffa ? DFT_FF : DFT_F32;
+  const int io = ff_io ? DFT_FF : DFT_CD;
   int cur = 0;
-  // forward x: x[r][cz][cy][cx][b] (complex double) -> [cz][cy][fx][r][b]
-  if (ff_io)
-    FMPB_TRY((dft_axis<true, true>("dft_fwd_x", x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
-                                   (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st)));
-  else
-    FMPB_TRY((dft_axis<false, true>("dft_fwd_x", x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
-                                    (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st)));
+  // forward x: x[r][cz][cy][cx][b] -> [cz][cy][fx][r][b]
+  FMPB_TRY(axis_pass("dft_fwd_x", ffa, io, mid, x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
+                     (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st));
   // forward y: [cz][cy][fx][rb] -> [cz][fy][fx][rb]
   if (Py > 1) {
-    FMPB_TRY((dft_axis<true, true>("dft_fwd_y", buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)My * Px * RB, RB,
-                                   (int64_t)Px * RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0,
-                                   false, st)));
+    FMPB_TRY(axis_pass("dft_fwd_y", ffa, mid, mid, buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)My * Px * RB, RB,
+                       (int64_t)Px * RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st));
     cur = 1 - cur;
   }
   // forward z: [cz][fy fx][rb] -> [fz][fy fx][rb]
   if (Pz > 1) {
-    FMPB_TRY((dft_axis<true, true>("dft_fwd_z", buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB,
-                                   0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz, -1, 1.0, false, st)));
+    FMPB_TRY(axis_pass("dft_fwd_z", ffa, mid, mid, buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB,
+                       (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz, -1, 1.0, false, st));
     cur = 1 - cur;
   }
   // per-frequency block products: [f][r][b] -> [f][r][b]
-  FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st, tc_rows, tc_err));
+  FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st, tc_rows, tc_err, !ffa));
   cur = 1 - cur;
   // inverse z: [fz][fy fx][rb] -> [cz][fy fx][rb], cz < Mz
   if (Pz > 1) {
-    FMPB_TRY((dft_axis<true, true>("dft_inv_z", buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB, (int64_t)Py * Px * RB,
-                                   0, RB, (int64_t)Py * Px * RB, Pz, Mz, Pz, +1, 1.0, false, st)));
+    FMPB_TRY(axis_pass("dft_inv_z", ffa, mid, mid, buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB,
+                       (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Pz, Mz, Pz, +1, 1.0, false, st));
     cur = 1 - cur;
   }
   // inverse y: [cz][fy][fx][rb] -> [cz][cy][fx][rb], cy < My
   if (Py > 1) {
-    FMPB_TRY((dft_axis<true, true>("dft_inv_y", buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)Py * Px * RB, RB,
-                                   (int64_t)Px * RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, Py, My, Py, +1, 1.0,
-                                   false, st)));
+    FMPB_TRY(axis_pass("dft_inv_y", ffa, mid, mid, buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)Py * Px * RB, RB,
+                       (int64_t)Px * RB, (int64_t)My * Px * RB, RB, (int64_t)Px * RB, Py, My, Py, +1, 1.0, false, st));
     cur = 1 - cur;
   }
-  // inverse x with crop and 1/F: [cz][cy][fx][r][b] -> y[r][cz][cy][cx][b] (complex double)
-  if (ff_io)
-    FMPB_TRY((dft_axis<true, true>("dft_inv_x", buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
-                                   (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, false, st)));
-  else
-    FMPB_TRY((dft_axis<true, false>("dft_inv_x", buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
-                                    (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, accumulate, st)));
+  // inverse x with crop and 1/F: [cz][cy][fx][r][b] -> y[r][cz][cy][cx][b]
+  FMPB_TRY(axis_pass("dft_inv_x", ffa, mid, io, buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
+                     (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, accumulate, st));
   return FMPB_OK;
 }
 

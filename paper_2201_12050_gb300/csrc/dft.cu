@@ -1,0 +1,453 @@
+// Pruned DFT passes of the circulant engine (Sec. 2.4, Eqs. (diagonalized),
+// (modifiedFourierTransform1), (modifiedFourierTransform2)): along one axis
+// of the padded cell grid, for every line (o1, o2) and inner index i,
+//   out[o1 b1 + o2 b2 + f bf + i] (+)= scale sum_{j < Pin} in[o1 a1 + o2 a2 + j aj + i] w^{f j},
+// w = exp(sign 2 pi i / P), f < Pout.  Pin < P for the forward transform of
+// the zero-padded grid (the incomplete Fourier matrix), Pout < P for the
+// cropped inverse.
+//
+// Algorithm: the two-factor (Cooley-Tukey) split P = P1 P2, n = P2 n1 + n2,
+// f = k1 + P1 k2:
+//   stage A, per n2 < P2: Y[n2][k1] = w^{n2 k1} sum_{n1} in[P2 n1 + n2] w^{P2 n1 k1}   (k1 < P1)
+//   stage B, per k1 < P1: out[k1 + P1 k2] = sum_{n2} Y[n2][k1] w^{P1 n2 k2}             (k2 < P2)
+// with P1, P2 <= 16 chosen to minimise the complex multiply-adds (P2 = 1 is
+// the direct sum).  Only the non-zero inputs are read and only the kept
+// outputs are formed.
+//
+// Layout on the GB300: a warp owns 32 consecutive inner indices (the
+// contiguous dimension of every pass), so each of its loads and stores is
+// one 256-byte (FP32) or 512-byte (float-float) coalesced transaction.  A
+// stage-A item (n2, 32 inner indices) holds its up to 16 inputs in
+// registers and forms the short DFT there; the P1 x P2 intermediate values
+// go through shared memory to the stage-B items (k1, 32 inner indices),
+// which again work from registers and store straight to global memory.
+// Twiddles sit in shared memory and every lane of a warp reads the same one
+// (a broadcast).  CTAs are persistent over tiles of (line, 32 nsub inner
+// indices), so the twiddle tables are built once per CTA.
+//
+// Arithmetic: float-float (48-bit significands on the FP32 pipe, the FP64
+// operators) or plain FP32 (8 bytes per value: the FP32, BF16 and
+// mixed-precision inner operators, whose products carry 1e-5 or less
+// accuracy anyway).  In place (in == out with equal strides, Pin = Pout = P)
+// is allowed: every input of a tile is read before any output of it is
+// written.
+#include <type_traits>
+
+#include "common.cuh"
+#include "ff.cuh"
+#include "internal.cuh"
+#include "profile.cuh"
+
+namespace fmpb {
+
+namespace {
+
+constexpr int DFT_R = 16;          // longest factor held in registers
+constexpr int DFT_THREADS = 256;
+
+template <bool FF>
+using DVal = typename std::conditional<FF, float4, float2>::type;
+
+template <bool FF>
+__device__ __forceinline__ DVal<FF> dzero();
+template <>
+__device__ __forceinline__ float4 dzero<true>() {
+  return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+template <>
+__device__ __forceinline__ float2 dzero<false>() {
+  return make_float2(0.f, 0.f);
+}
+
+// w^m = exp(sign 2 pi i m / P) from an FP64 sincospi of the exact fraction m / P
+template <bool FF>
+__device__ __forceinline__ DVal<FF> twiddle(int m, int P, int sign) {
+  double s, c;
+  sincospi(2.0 * m / P, &s, &c);
+  if constexpr (FF)
+    return split_ff(mkc(c, sign * s));
+  else
+    return make_float2((float)c, (float)(sign * s));
+}
+
+template <bool FF, int FMT>
+__device__ __forceinline__ DVal<FF> dload(const void* p, int64_t idx) {
+  if constexpr (FMT == DFT_CD) {
+    const cd v = reinterpret_cast<const cd*>(p)[idx];
+    if constexpr (FF)
+      return split_ff(v);
+    else
+      return make_float2((float)v.x, (float)v.y);
+  } else if constexpr (FMT == DFT_FF) {
+    const float4 v = reinterpret_cast<const float4*>(p)[idx];
+    if constexpr (FF)
+      return v;
+    else
+      return make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
+  } else {
+    const float2 v = reinterpret_cast<const float2*>(p)[idx];
+    if constexpr (FF)
+      return make_float4(v.x, 0.f, v.y, 0.f);
+    else
+      return v;
+  }
+}
+
+template <bool FF, int FMT>
+__device__ __forceinline__ void dstore(void* p, int64_t idx, DVal<FF> v, double scale, int accumulate) {
+  if constexpr (FMT == DFT_CD) {
+    cd d;
+    if constexpr (FF)
+      d = mkc(((double)v.x + (double)v.y) * scale, ((double)v.z + (double)v.w) * scale);
+    else
+      d = mkc((double)v.x * scale, (double)v.y * scale);
+    cd* o = reinterpret_cast<cd*>(p) + idx;
+    *o = accumulate ? cadd(*o, d) : d;
+  } else if constexpr (FMT == DFT_FF) {
+    static_assert(FF, "float-float output takes float-float arithmetic");
+    if (scale != 1.0) {
+      const ff sc = ff_from_d(scale);
+      const ff re = ff_mul(ff{v.x, v.y}, sc), im = ff_mul(ff{v.z, v.w}, sc);
+      v = make_float4(re.h, re.l, im.h, im.l);
+    }
+    reinterpret_cast<float4*>(p)[idx] = v;
+  } else {
+    static_assert(!FF, "FP32 output takes FP32 arithmetic");
+    const float s = (float)scale;
+    reinterpret_cast<float2*>(p)[idx] = make_float2(v.x * s, v.y * s);
+  }
+}
+
+// sum_{n < nin} x[n] T[(n k) mod m], the register-resident short DFT
+template <bool FF>
+__device__ __forceinline__ DVal<FF> short_dft(const DVal<FF> (&x)[DFT_R], const DVal<FF>* __restrict__ T, int nin,
+                                              int k, int m) {
+  int idx = 0;
+  if constexpr (FF) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll
+    for (int n = 0; n < DFT_R; ++n)
+      if (n < nin) {
+        ff_cmac(T[idx], x[n], rh, rl, ih, il);
+        idx += k;
+        if (idx >= m) idx -= m;
+      }
+    return ff_norm(rh, rl, ih, il);
+  } else {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int n = 0; n < DFT_R; ++n)
+      if (n < nin) {
+        const float2 t = T[idx];
+        re = fmaf(t.x, x[n].x, fmaf(-t.y, x[n].y, re));
+        im = fmaf(t.x, x[n].y, fmaf(t.y, x[n].x, im));
+        idx += k;
+        if (idx >= m) idx -= m;
+      }
+    return make_float2(re, im);
+  }
+}
+
+template <bool FF>
+__device__ __forceinline__ DVal<FF> dmul(DVal<FF> a, DVal<FF> w) {
+  if constexpr (FF) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    ff_cmac(w, a, rh, rl, ih, il);
+    return ff_norm(rh, rl, ih, il);
+  } else {
+    return make_float2(fmaf(w.x, a.x, -w.y * a.y), fmaf(w.x, a.y, w.y * a.x));
+  }
+}
+
+struct DftArgs {
+  const void* in;
+  void* out;
+  int64_t I, a1, a2, aj, b1, b2, bf;
+  int O1, O2, Pin, Pout, P, P1, P2, nsub, sign, accumulate;
+  double scale;
+  int64_t tiles_i, tiles;
+};
+
+// Storage type of the input format (what the copies move into shared memory).
+template <int FMT>
+struct DIn;
+template <>
+struct DIn<DFT_CD> {
+  typedef double2 T;
+};
+template <>
+struct DIn<DFT_FF> {
+  typedef float4 T;
+};
+template <>
+struct DIn<DFT_F32> {
+  typedef float2 T;
+};
+
+template <int FMT, bool FF>
+__device__ __forceinline__ DVal<FF> from_stored(typename DIn<FMT>::T v) {
+  if constexpr (FMT == DFT_CD) {
+    if constexpr (FF)
+      return split_ff(v);
+    else
+      return make_float2((float)v.x, (float)v.y);
+  } else if constexpr (FMT == DFT_FF) {
+    if constexpr (FF)
+      return v;
+    else
+      return make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
+  } else {
+    if constexpr (FF)
+      return make_float4(v.x, 0.f, v.y, 0.f);
+    else
+      return v;
+  }
+}
+
+// Asynchronous global -> shared copy of one 8- or 16-byte value; src_bytes
+// 0 fills the destination with zeros (the pruned inputs past the grid).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_val(uint32_t dst, const void* src, int src_bytes) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared memory of a CTA: twiddles (P + P1 + P2 values), the intermediate
+// values Y (nsub x P x 32, two-factor plans only) and two input stages of
+// Pin x 32 nsub stored values each (the next tile's copies overlap the
+// current tile's arithmetic).
+template <bool FF, int IN, int OUT>
+__global__ void __launch_bounds__(DFT_THREADS, 2) k_dft(const DftArgs a) {
+  using V = DVal<FF>;
+  using S = typename DIn<IN>::T;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  V* tw = reinterpret_cast<V*>(dsm);   // w^m, m < P
+  V* t1 = tw + a.P;                    // w^{P2 m}, m < P1
+  V* t2 = t1 + a.P1;                   // w^{P1 m}, m < P2
+  V* Y = t2 + a.P2;                    // nsub x P x 32 intermediate values
+  const int64_t TI = 32 * (int64_t)a.nsub;
+  const int64_t ybytes = (a.P2 > 1 ? (int64_t)a.nsub * a.P * 32 : 0) * (int64_t)sizeof(V);
+  const int64_t off = (((int64_t)(a.P + a.P1 + a.P2) * (int64_t)sizeof(V) + ybytes) + 15) / 16 * 16;
+  S* stage = reinterpret_cast<S*>(dsm + off);   // [2][Pin][TI]
+  const int64_t per_stage = (int64_t)a.Pin * TI;
+  for (int m = threadIdx.x; m < a.P; m += blockDim.x) tw[m] = twiddle<FF>(m, a.P, a.sign);
+  for (int m = threadIdx.x; m < a.P1; m += blockDim.x) t1[m] = twiddle<FF>(m * a.P2, a.P, a.sign);
+  for (int m = threadIdx.x; m < a.P2; m += blockDim.x) t2[m] = twiddle<FF>(m * a.P1, a.P, a.sign);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const V zero = dzero<FF>();
+  const S* in = reinterpret_cast<const S*>(a.in);
+
+  // copies of tile t's inputs into stage buf (one commit group per tile)
+  auto issue = [&](int64_t t, int buf) {
+    const int64_t it = t % a.tiles_i, og = t / a.tiles_i;
+    const int o2 = (int)(og % a.O2), o1 = (int)(og / a.O2);
+    const int64_t i0 = it * TI;
+    const int64_t bin = o1 * a.a1 + o2 * a.a2 + i0;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage + buf * per_stage);
+    for (int64_t e = threadIdx.x; e < per_stage; e += blockDim.x) {
+      const int64_t j = e / TI, ii = e - j * TI;
+      const bool ok = i0 + ii < a.I;
+      cp_async_val<sizeof(S)>(sbase + (uint32_t)(e * sizeof(S)), ok ? in + bin + j * a.aj + ii : in,
+                              ok ? (int)sizeof(S) : 0);
+    }
+  };
+
+  int buf = 0;
+  if ((int64_t)blockIdx.x < a.tiles) issue(blockIdx.x, 0);
+  cp_async_commit_group();
+  for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < a.tiles) issue(tn, buf ^ 1);
+    cp_async_commit_group();
+    cp_async_wait_group<1>();   // this tile's copies have landed
+    __syncthreads();
+    const int64_t it = t % a.tiles_i, og = t / a.tiles_i;
+    const int o2 = (int)(og % a.O2), o1 = (int)(og / a.O2);
+    const int64_t i0 = it * TI;
+    const int64_t bout = o1 * a.b1 + o2 * a.b2;
+    const S* st = stage + buf * per_stage;
+    // stage A: items (sub, n2)
+    for (int item = warp; item < a.nsub * a.P2; item += nw) {
+      const int sub = item / a.P2, n2 = item - sub * a.P2;
+      const int64_t ii = (int64_t)sub * 32 + lane;
+      const int64_t i = i0 + ii;
+      const bool ok = i < a.I;
+      const int nin = min(a.P1, (a.Pin - n2 + a.P2 - 1) / a.P2);   // n1 with P2 n1 + n2 < Pin
+      V x[DFT_R];
+#pragma unroll
+      for (int n1 = 0; n1 < DFT_R; ++n1) {
+        x[n1] = zero;
+        if (n1 < nin) x[n1] = from_stored<IN, FF>(st[(int64_t)(a.P2 * n1 + n2) * TI + ii]);
+      }
+      if (a.P2 == 1) {
+        // direct sum: the outputs go straight to global memory
+#pragma unroll 1
+        for (int k1 = 0; k1 < a.Pout; ++k1) {
+          const V v = short_dft<FF>(x, t1, nin, k1, a.P1);
+          if (ok) dstore<FF, OUT>(a.out, bout + (int64_t)k1 * a.bf + i, v, a.scale, a.accumulate);
+        }
+      } else {
+        V* Ys = Y + (int64_t)sub * a.P * 32 + lane;
+#pragma unroll 1
+        for (int k1 = 0; k1 < a.P1; ++k1) {
+          const V v = short_dft<FF>(x, t1, nin, k1, a.P1);
+          Ys[(n2 * a.P1 + k1) * 32] = n2 * k1 == 0 ? v : dmul<FF>(v, tw[n2 * k1]);   // n2 k1 < P
+        }
+      }
+    }
+    if (a.P2 > 1) {
+      __syncthreads();
+      // stage B: items (sub, k1)
+      for (int item = warp; item < a.nsub * a.P1; item += nw) {
+        const int sub = item / a.P1, k1 = item - sub * a.P1;
+        if (k1 >= a.Pout) continue;
+        const int64_t i = i0 + sub * 32 + lane;
+        const bool ok = i < a.I;
+        const V* Ys = Y + (int64_t)sub * a.P * 32 + lane;
+        V y[DFT_R];
+#pragma unroll
+        for (int n2 = 0; n2 < DFT_R; ++n2) y[n2] = n2 < a.P2 ? Ys[(n2 * a.P1 + k1) * 32] : zero;
+#pragma unroll 1
+        for (int k2 = 0; k2 < a.P2; ++k2) {
+          const int f = k1 + a.P1 * k2;
+          if (f >= a.Pout) break;
+          const V v = short_dft<FF>(y, t2, a.P2, k2, a.P2);
+          if (ok) dstore<FF, OUT>(a.out, bout + (int64_t)f * a.bf + i, v, a.scale, a.accumulate);
+        }
+      }
+    }
+    __syncthreads();   // Y and this stage are free for the next tiles
+    buf ^= 1;
+  }
+  cp_async_wait_group<0>();
+}
+
+// complex multiply-adds of a plan (stage A + twiddles + stage B)
+int64_t plan_cost(int P, int Pin, int Pout, int P1) {
+  const int P2 = P / P1;
+  if (P2 == 1) return (int64_t)Pin * Pout;
+  return (int64_t)Pin * P1 + P + (int64_t)Pout * P2;
+}
+
+template <bool FF, int IN, int OUT>
+fmpb_status launch_dft(const char* name, const DftArgs& a, size_t smem, int threads, cudaStream_t st) {
+  if (smem > 48 * 1024)
+    FMPB_CUDA(cudaFuncSetAttribute(k_dft<FF, IN, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // persistent CTAs: as many as can be resident, each walking its share of the tiles
+  int per_sm = 0, sms = 0, dev = 0;
+  FMPB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft<FF, IN, OUT>, threads, smem));
+  FMPB_CUDA(cudaGetDevice(&dev));
+  FMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t grid = std::min<int64_t>(a.tiles, (int64_t)std::max(1, per_sm) * sms);
+  FMPB_LAUNCH(name, st, k_dft<FF, IN, OUT><<<(unsigned)grid, threads, smem, st>>>(a));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+}  // namespace
+
+bool dft_plan(int P, int Pin, int Pout, int* P1out) {
+  int best = 0;
+  int64_t cost = 0;
+  for (int p1 = 1; p1 <= DFT_R && p1 <= P; ++p1) {
+    if (P % p1 || P / p1 > DFT_R) continue;
+    const int64_t c = plan_cost(P, Pin, Pout, p1);
+    if (!best || c < cost) {
+      best = p1;
+      cost = c;
+    }
+  }
+  if (!best) return false;
+  *P1out = best;
+  return true;
+}
+
+bool dft_supported(int P) {
+  int p1;
+  return P <= 1 || dft_plan(P, P, P, &p1);
+}
+
+fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
+                     int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
+                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st) {
+  int P1 = 0;
+  if (!dft_plan(P, Pin, Pout, &P1)) {
+    set_error("dft_pass: axis length %d has no split into two factors of at most %d", P, DFT_R);
+    return FMPB_EINVAL;
+  }
+  if (Pin < 1 || Pin > P || Pout < 1 || Pout > P || O1 < 1 || O2 < 1 || I < 1) {
+    set_error("dft_pass: bad line geometry (Pin %d, Pout %d, P %d)", Pin, Pout, P);
+    return FMPB_EINVAL;
+  }
+  if (accumulate && out_fmt != DFT_CD) {
+    set_error("dft_pass: accumulation needs complex-double output");
+    return FMPB_EINVAL;
+  }
+  DftArgs a;
+  a.in = in;
+  a.out = out;
+  a.I = I;
+  a.a1 = a1;
+  a.a2 = a2;
+  a.aj = aj;
+  a.b1 = b1;
+  a.b2 = b2;
+  a.bf = bf;
+  a.O1 = O1;
+  a.O2 = O2;
+  a.Pin = Pin;
+  a.Pout = Pout;
+  a.P = P;
+  a.P1 = P1;
+  a.P2 = P / P1;
+  a.sign = sign;
+  a.accumulate = accumulate ? 1 : 0;
+  a.scale = scale;
+  const size_t vb = ff_arith ? sizeof(float4) : sizeof(float2);
+  const size_t sb = in_fmt == DFT_F32 ? sizeof(float2) : sizeof(float4);
+  // inner sub-tiles of 32 per CTA: enough items for up to 8 warps in both
+  // stages, within the inner extent and the shared-memory budget, then fewer
+  // while the grid would leave SMs idle (small passes are latency-bound)
+  const int mn = std::min(a.P1, a.P2);
+  int nsub = std::max(1, std::min(8, (8 + mn - 1) / mn));
+  nsub = (int)std::min<int64_t>(nsub, (I + 31) / 32);
+  auto smem_for = [&](int ns) {
+    const size_t head = (size_t)(P + a.P1 + a.P2 + (a.P2 > 1 ? (size_t)ns * P * 32 : 0)) * vb;
+    return (head + 15) / 16 * 16 + 2 * (size_t)Pin * 32 * ns * sb;
+  };
+  while (nsub > 1 && smem_for(nsub) > 72 * 1024) --nsub;
+  auto tiles_for = [&](int ns) { return (I + 32 * ns - 1) / (32 * ns) * O1 * O2; };
+  while (nsub > 1 && tiles_for(nsub) < 4 * 152) --nsub;
+  a.nsub = nsub;
+  a.tiles_i = (I + 32 * nsub - 1) / (32 * nsub);
+  a.tiles = a.tiles_i * O1 * O2;
+  const size_t smem = smem_for(nsub);
+  if (smem > 200 * 1024) {
+    set_error("dft_pass: axis length %d too large", P);
+    return FMPB_EINVAL;
+  }
+  const int warps = std::max(1, std::min(DFT_THREADS / 32, std::max(nsub * a.P2, a.P2 > 1 ? nsub * a.P1 : 0)));
+  const int threads = 32 * warps;
+  if (ff_arith) {
+    if (in_fmt == DFT_CD && out_fmt == DFT_FF) return launch_dft<true, DFT_CD, DFT_FF>(name, a, smem, threads, st);
+    if (in_fmt == DFT_FF && out_fmt == DFT_FF) return launch_dft<true, DFT_FF, DFT_FF>(name, a, smem, threads, st);
+    if (in_fmt == DFT_FF && out_fmt == DFT_CD) return launch_dft<true, DFT_FF, DFT_CD>(name, a, smem, threads, st);
+    if (in_fmt == DFT_CD && out_fmt == DFT_CD) return launch_dft<true, DFT_CD, DFT_CD>(name, a, smem, threads, st);
+  } else {
+    if (in_fmt == DFT_CD && out_fmt == DFT_F32) return launch_dft<false, DFT_CD, DFT_F32>(name, a, smem, threads, st);
+    if (in_fmt == DFT_F32 && out_fmt == DFT_F32) return launch_dft<false, DFT_F32, DFT_F32>(name, a, smem, threads, st);
+    if (in_fmt == DFT_F32 && out_fmt == DFT_CD) return launch_dft<false, DFT_F32, DFT_CD>(name, a, smem, threads, st);
+    if (in_fmt == DFT_FF && out_fmt == DFT_F32) return launch_dft<false, DFT_FF, DFT_F32>(name, a, smem, threads, st);
+  }
+  set_error("dft_pass: unsupported storage formats %d -> %d", in_fmt, out_fmt);
+  return FMPB_EINVAL;
+}
+
+}  // namespace fmpb

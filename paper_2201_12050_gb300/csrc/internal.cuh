@@ -161,6 +161,15 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
                          const int32_t* offsets, const int64_t* dest_host, cd* out, cudaStream_t st,
                          const ImageBlocks* img = nullptr);
 
+// The truncation rule (truncation.cu): the smallest n_t in 4..MAX_NT whose
+// U_0 K(d) V_0 reproduces the exact block of the nearest far cell d on four
+// probe vectors to 1e-6 relative; met = false (nt = MAX_NT) when none does;
+// err: the relative probe error at the chosen n_t.  Grids without far cell
+// pairs take 4.
+bool nearest_far_offset(const CellGrid& g, int32_t d[3]);
+fmpb_status auto_truncation(const DeviceMesh& mesh, const CellGrid& g, double k, cd beta, int* nt, bool* met,
+                            double* err, cudaStream_t st);
+
 // Listed entries of n_off blocks (list: device, count indices
 // (o n + i) n + j, o indexing offsets), written to out[e]; self_slot (device,
 // n entries, -1 where absent): the position in out of entry (i, i) of the
@@ -199,6 +208,19 @@ fmpb_status reverse_cells(const void* in, void* out, size_t elem_bytes, int R, c
                           cudaStream_t st);
 fmpb_status scale_inplace(cd* a, size_t n, cd s, cudaStream_t st);
 
+// Pruned DFT passes (dft.cu): storage formats of the values a pass reads and
+// writes (complex double, float-float pairs, complex FP32).
+enum DftFormat { DFT_CD = 0, DFT_FF = 1, DFT_F32 = 2 };
+// True if an axis of padded length P splits into two factors of at most 16
+// (every P up to 256 of the 2,3,5,7-smooth lengths the engine uses except a
+// few, such as 245).
+bool dft_supported(int P);
+// One pass along an axis (see dft.cu): ff_arith selects float-float or FP32
+// arithmetic; in place needs in == out with equal strides and Pin = Pout = P.
+fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
+                     int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
+                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st);
+
 // Circulant engine (circulant.cu)
 // In-place forward DFT over the padded grid of F slots, each holding `inner`
 // complex doubles; leaves the result as float-float pairs (16 bytes each).
@@ -214,9 +236,14 @@ fmpb_status grid_fft_inplace(const CircShape& s, int64_t inner, cd* grid, cudaSt
 enum SpecFormat { SPEC_CD = 0, SPEC_FF = 1, SPEC_F32 = 2, SPEC_BF16 = 3 };
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD,
-                            void* tc_rows = nullptr, unsigned* tc_err = nullptr, bool ff_io = false);
+                            void* tc_rows = nullptr, unsigned* tc_err = nullptr, bool ff_io = false,
+                            bool f32_passes = false);
 // ff_io: x and y are float-float vectors (float4 per value, passed as cd*;
 // same 16 bytes) instead of complex double; accumulate must be false.
+// f32_passes: the DFT passes and the frequency-domain values in complex FP32
+// (8 bytes per value) instead of float-float; for the FP32 and BF16 spectra
+// only (SPEC_F32, SPEC_BF16), and only where circulant_f32_ok(s) holds.
+bool circulant_f32_ok(const CircShape& s);
 // float-float spectrum -> complex FP32 (out has n float2 entries)
 fmpb_status spectrum_ff_to_f32(const cd* in, void* out, size_t n, cudaStream_t st);
 // In-place conversion of n complex doubles to float-float pairs (re_hi, re_lo, im_hi, im_lo).

@@ -321,9 +321,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int64_t j = n0 + cbase + c0 + t;
           if (j < ncols) {
             if (FREQ) {
-              // float-float output (hi = FP32 sum, lo = 0), the circulant scratch format
-              float2* d = reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ncols + j) * m + i) + part;
-              *d = make_float2(v[t], 0.f);
+              // the circulant scratch format: float-float (hi = FP32 sum,
+              // lo = 0), or complex FP32 when `accumulate` is set (FREQ mode
+              // never accumulates; the flag selects the output format there)
+              if (accumulate) {
+                float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + (f * ncols + j) * m + i) + part;
+                *d = v[t];
+              } else {
+                float2* d =
+                    reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ncols + j) * m + i) + part;
+                *d = make_float2(v[t], 0.f);
+              }
             } else {
               double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + j * m + i) + part;
               *d = accumulate ? *d + (double)v[t] : (double)v[t];
@@ -410,6 +418,19 @@ __global__ void k_tc_rows_from_ff(const float4* __restrict__ x, int64_t k, int64
   __nv_bfloat162 p;
   p.x = ff_to_bf16(v.x, v.y);
   p.y = ff_to_bf16(v.z, v.w);
+  X[idx] = p;
+}
+
+__global__ void k_tc_rows_from_f32(const float2* __restrict__ x, int64_t k, int64_t Kh, int64_t total,
+                                   __nv_bfloat162* __restrict__ X) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t rho = idx / Kh, j = idx - rho * Kh;
+  float2 v = make_float2(0.f, 0.f);
+  if (j < k) v = x[rho * k + j];
+  __nv_bfloat162 p;
+  p.x = __float2bfloat16_rn(v.x);
+  p.y = __float2bfloat16_rn(v.y);
   X[idx] = p;
 }
 
@@ -566,6 +587,17 @@ fmpb_status tc_rows_from_ff(const float4* x, int64_t rows, int64_t k, __nv_bfloa
   return FMPB_OK;
 }
 
+fmpb_status tc_rows_from_f32(const float2* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
+  const int64_t Kh = tc_depth(k) / 2;
+  const int64_t total = rows * Kh;
+  if (total == 0) return FMPB_OK;
+  FMPB_LAUNCH("tc_to_bf16", st,
+              k_tc_rows_from_f32<<<grid_for((size_t)total, 256), 256, 0, st>>>(
+                  x, k, Kh, total, reinterpret_cast<__nv_bfloat162*>(X)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
                            const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st) {
   const int64_t Mp = tc_rows(m), Kp = tc_depth(k);
@@ -633,8 +665,8 @@ fmpb_status tc_tuning_summary(std::string& out) {
   return FMPB_OK;
 }
 
-fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, float4* Y,
-                         unsigned* err, cudaStream_t st) {
+fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, void* Y,
+                         unsigned* err, cudaStream_t st, bool y_f32) {
   const int64_t Mp = tc_rows(B), Kp = tc_depth(B);
   if (F < 1 || F > 65535 || B < 1 || R < 1 || Mp / TC_BM > 65535 || Kp > (1 << 24)) {
     set_error("tc_freq_gemm: bad shape (F %lld, B %lld, R %d)", (long long)F, (long long)B, R);
@@ -649,10 +681,10 @@ fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, co
     return FMPB_EINVAL;
   }
   switch (BN) {
-    case 32: return launch_tc<32, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
-    case 64: return launch_tc<64, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
-    case 128: return launch_tc<128, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
-    default: return launch_tc<256, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, false, err, st);
+    case 32: return launch_tc<32, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
+    case 64: return launch_tc<64, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
+    case 128: return launch_tc<128, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
+    default: return launch_tc<256, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
   }
 }
 

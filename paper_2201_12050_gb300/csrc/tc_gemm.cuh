@@ -43,13 +43,16 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
 // rounded (hi + lo) -> FP32 -> BF16.
 fmpb_status tc_realify_ff(const float4* T, int n_off, int64_t m, int64_t k, __nv_bfloat16* A, cudaStream_t st);
 fmpb_status tc_rows_from_ff(const float4* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st);
+// Complex FP32 sources (float2 per value), rounded FP32 -> BF16.
+fmpb_status tc_rows_from_f32(const float2* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st);
 
 // Per-frequency products Y_f = Lambda_f X_f of the circulant engine for F
 // frequencies: A (F x tc_rows(B) x tc_depth(B), from tc_realify_ff of the
-// spectrum), X (F R x tc_depth(B) rows, row f R + r), Y float-float
-// [f][r][b] (hi = FP32 accumulator, lo = 0).
-fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, float4* Y,
-                         unsigned* err, cudaStream_t st);
+// spectrum), X (F R x tc_depth(B) rows, row f R + r), Y [f][r][b] as
+// float-float (float4, hi = FP32 accumulator, lo = 0) or, with y_f32, as
+// complex FP32 (float2).
+fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, void* Y,
+                         unsigned* err, cudaStream_t st, bool y_f32 = false);
 
 // JSON list of the tile variants the offset-GEMM autotuner chose so far.
 fmpb_status tc_tuning_summary(std::string& out);

@@ -117,6 +117,41 @@ def test_circulant_product_equals_explicit_block_toeplitz(counts, B, R):
     assert _rel(y0.cpu().numpy(), ref + x) < 1e-12
 
 
+@pytest.mark.parametrize("counts,B,R", [((4, 1, 1), 5, 1), ((3, 2, 1), 7, 3), ((2, 3, 2), 4, 6),
+                                        ((5, 4, 1), 33, 2), ((1, 1, 1), 3, 1), ((6, 1, 1), 1, 5),
+                                        ((16, 1, 3), 9, 9), ((32, 2, 1), 3, 2)])
+def test_circulant_f32_product_equals_explicit_block_toeplitz(counts, B, R):
+    # FP32 spectrum, FP32 DFT passes and products: within 1e-5 of the exact
+    # block Toeplitz product (ragged inner tiles, direct and two-factor
+    # passes, R >= 8 through the tiled product)
+    offs = bem.all_offsets(counts)
+    blocks = random_complex_vectors(1100 + B, len(offs), B * B).reshape(len(offs), B, B)
+    ncell = int(np.prod(counts))
+    x = random_complex_vectors(2100 + R, R, ncell * B)
+    spec = gb.circulant_spectrum(counts, _dev(blocks))
+    y = gb.circulant_apply_f32(counts, spec, _dev(x)).cpu().numpy()
+    ref = bem.toeplitz_matvec(dict(zip(offs, blocks)), counts, x)
+    assert _rel(y, ref) < 1e-5
+    y0 = _dev(x)
+    gb.circulant_apply_f32(counts, spec, _dev(x), out=y0, accumulate=True)
+    assert _rel(y0.cpu().numpy(), ref + x) < 1e-5
+
+
+def test_circulant_long_axis_without_a_short_split():
+    # P = 245 = 5 * 7 * 7 has no split into two factors of at most 16: the
+    # float-float product takes the direct pass, the FP32 one is refused
+    counts, B, R = (123, 1, 1), 2, 1
+    offs = bem.all_offsets(counts)
+    assert gb.circulant_shape(counts)[0][0] == 245
+    blocks = random_complex_vectors(1200, len(offs), B * B).reshape(len(offs), B, B)
+    x = random_complex_vectors(2200, R, 123 * B)
+    spec = gb.circulant_spectrum(counts, _dev(blocks))
+    y = gb.circulant_apply(counts, spec, _dev(x)).cpu().numpy()
+    assert _rel(y, bem.toeplitz_matvec(dict(zip(offs, blocks)), counts, x)) < 1e-12
+    with pytest.raises(gb.FmpbError):
+        gb.circulant_apply_f32(counts, spec, _dev(x))
+
+
 def test_circulant_spectrum_is_the_dft_of_the_first_block_column():
     counts = (3, 2, 1)
     offs = bem.all_offsets(counts)

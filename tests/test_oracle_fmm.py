@@ -96,3 +96,67 @@ def test_explicit_fmm_operator_tends_to_exact_operator():
         errs.append(np.linalg.norm(y - y_exact) / np.linalg.norm(y_exact))
     assert all(b < 0.1 * a for a, b in zip(errs, errs[1:]))
     assert errs[2] < 1e-8 and errs[-1] < 1e-12
+
+
+# ------------------------------------------------------ truncation rule --
+
+def test_nearest_far_offset_by_hand():
+    # 4 x 3 cells at 0.6 x 0.5 m: the shortest far translation is two cells
+    # along y (1.0 m; two along x is 1.2 m, a knight's move sqrt(0.36 + 1))
+    assert fmm.nearest_far_offset(np.diag([0.6, 0.5, 1.0]), (4, 3, 1)) == (0, -2, 0)
+    assert fmm.nearest_far_offset(np.diag([0.4, 0.7, 1.0]), (5, 5, 1)) == (-2, 0, 0)
+    assert fmm.nearest_far_offset(np.eye(3), (2, 2, 2)) is None          # every pair is near
+    d = fmm.nearest_far_offset(np.diag([1.0, 1.0, 0.45]), (3, 3, 4))
+    assert d == (0, 0, -2)
+
+
+def test_probe_vectors_are_unit_and_spread():
+    X = fmm.probe_vectors(257)
+    assert np.allclose(np.abs(X), 1.0, atol=1e-15) and np.allclose(X[:, 0], 1.0)
+    phi = (np.sqrt(5.0) - 1.0) / 2.0
+    assert np.isclose(X[2, 5], np.exp(2j * np.pi * ((3 * 5 * phi) % 1.0)), atol=1e-14)
+    G = X.conj() @ X.T / 257                  # the four probes are nearly orthogonal
+    assert np.abs(G - np.diag(np.diag(G))).max() < 0.05
+
+
+@pytest.fixture(scope="module")
+def sphere_cell():
+    v, t = icosphere(1, 0.2)
+    return bem.CellMesh(v, t)
+
+
+def test_truncation_rule_tracks_the_block_error(sphere_cell):
+    # the probe error falls geometrically with n_t, and at the n_t the rule
+    # picks the whole block's Frobenius error (no probes) is below 1e-5 while
+    # two orders less leave it above 1e-6
+    L, counts, k = np.diag([0.6, 0.6, 1.0]), (4, 4, 1), 4.0
+    d, errs = fmm.truncation_errors(sphere_cell, L, counts, k, nt_max=14)
+    assert d == (0, -2, 0)
+    e = [errs[n] for n in range(4, 15)]
+    assert all(b < 0.7 * a for a, b in zip(e, e[1:])), e
+    nt = fmm.auto_truncation(sphere_cell, L, counts, k, nt_max=14)
+    assert errs[nt] <= 1e-6 < errs[nt - 1]
+    T = bem.toeplitz_block(sphere_cell, L, d, k)
+    dv = np.asarray(d, dtype=float) @ L
+
+    def block_err(n):
+        UKV = fmm.l2p_table(sphere_cell, k, n) @ fmm.m2l_block(dv, k, n) @ fmm.p2m_table(sphere_cell, k, n)
+        return np.linalg.norm(UKV - T) / np.linalg.norm(T)
+
+    assert block_err(nt) < 1e-5 and block_err(nt - 2) > 1e-6
+
+
+def test_truncation_rule_grows_with_frequency_and_keeps_the_operator_accurate(sphere_cell):
+    # the accuracy study's trend (Sec. 4): higher frequency needs more
+    # terms; the whole FMPBEM product at the chosen n_t stays within 1e-5 of
+    # the exact block Toeplitz product
+    L, counts = np.diag([0.6, 0.6, 1.0]), (4, 3, 1)
+    nts = [fmm.auto_truncation(sphere_cell, L, counts, k, nt_max=14) for k in (4.0, 12.0, 20.0)]
+    assert nts[0] <= nts[1] <= nts[2] and nts[0] < nts[2], nts
+    k, nt = 12.0, nts[1]
+    blocks = {d: bem.toeplitz_block(sphere_cell, L, d, k) for d in bem.all_offsets(counts)}
+    x = random_complex_vectors(71, 1, sphere_cell.n * 12)
+    exact = bem.toeplitz_matvec(blocks, counts, x)
+    near = {d: b for d, b in blocks.items() if max(abs(c) for c in d) <= 1}
+    y = fmm.fmm_matvec_explicit(sphere_cell, L, counts, k, nt, x, near_blocks=near)
+    assert np.linalg.norm(y - exact) / np.linalg.norm(exact) < 1e-5
