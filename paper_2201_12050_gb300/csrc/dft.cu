@@ -329,6 +329,63 @@ __global__ void __launch_bounds__(DFT_THREADS, 2) k_dft(const DftArgs a) {
   cp_async_wait_group<0>();
 }
 
+// Direct form for short input lines: one thread per (line, inner index)
+// loads its Pin inputs into registers (all loads in flight at once, 32
+// consecutive inner indices per warp) and forms every kept output as a
+// direct sum, with no shared-memory exchange and no barrier.  Pin * Pout
+// multiply-adds per line: the choice for FP32 arithmetic (cheap next to the
+// bytes it moves) and for float-float lines of a prime length.
+template <bool FF, int IN, int OUT, int MAXIN>
+__global__ void __launch_bounds__(256) k_dft_direct(const DftArgs a) {
+  using V = DVal<FF>;
+  using S = typename DIn<IN>::T;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  V* tw = reinterpret_cast<V*>(dsm);   // w^m, m < P
+  for (int m = threadIdx.x; m < a.P; m += blockDim.x) tw[m] = twiddle<FF>(m, a.P, a.sign);
+  __syncthreads();
+  const S* in = reinterpret_cast<const S*>(a.in);
+  const V zero = dzero<FF>();
+  const int64_t items = (int64_t)a.O1 * a.O2 * a.I;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = g % a.I, og = g / a.I;
+    const int o2 = (int)(og % a.O2), o1 = (int)(og / a.O2);
+    const S* src = in + o1 * a.a1 + o2 * a.a2 + i;
+    V x[MAXIN];
+#pragma unroll
+    for (int j = 0; j < MAXIN; ++j) x[j] = j < a.Pin ? from_stored<IN, FF>(src[(int64_t)j * a.aj]) : zero;
+    const int64_t dst = o1 * a.b1 + o2 * a.b2 + i;
+#pragma unroll 1
+    for (int f = 0; f < a.Pout; ++f) {
+      int idx = 0;
+      V v;
+      if constexpr (FF) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll
+        for (int j = 0; j < MAXIN; ++j)
+          if (j < a.Pin) {
+            ff_cmac(tw[idx], x[j], rh, rl, ih, il);
+            idx += f;
+            if (idx >= a.P) idx -= a.P;
+          }
+        v = ff_norm(rh, rl, ih, il);
+      } else {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int j = 0; j < MAXIN; ++j)
+          if (j < a.Pin) {
+            const float2 t = tw[idx];
+            re = fmaf(t.x, x[j].x, fmaf(-t.y, x[j].y, re));
+            im = fmaf(t.x, x[j].y, fmaf(t.y, x[j].x, im));
+            idx += f;
+            if (idx >= a.P) idx -= a.P;
+          }
+        v = make_float2(re, im);
+      }
+      dstore<FF, OUT>(a.out, dst + (int64_t)f * a.bf, v, a.scale, a.accumulate);
+    }
+  }
+}
+
 // complex multiply-adds of a plan (stage A + twiddles + stage B)
 int64_t plan_cost(int P, int Pin, int Pout, int P1) {
   const int P2 = P / P1;
@@ -349,6 +406,26 @@ fmpb_status launch_dft(const char* name, const DftArgs& a, size_t smem, int thre
   FMPB_LAUNCH(name, st, k_dft<FF, IN, OUT><<<(unsigned)grid, threads, smem, st>>>(a));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
+}
+
+template <bool FF, int IN, int OUT>
+fmpb_status launch_direct(const char* name, const DftArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)a.P * (FF ? sizeof(float4) : sizeof(float2));
+  const int64_t items = (int64_t)a.O1 * a.O2 * a.I;
+  int sms = 0, dev = 0;
+  FMPB_CUDA(cudaGetDevice(&dev));
+  FMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  auto go = [&](auto kern) -> fmpb_status {
+    int per_sm = 0;
+    FMPB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    const int64_t grid = std::min<int64_t>((items + 255) / 256, (int64_t)std::max(1, per_sm) * sms);
+    FMPB_LAUNCH(name, st, kern<<<(unsigned)grid, 256, smem, st>>>(a));
+    FMPB_CUDA(cudaGetLastError());
+    return FMPB_OK;
+  };
+  if (a.Pin <= 8) return go(k_dft_direct<FF, IN, OUT, 8>);
+  if (a.Pin <= 16) return go(k_dft_direct<FF, IN, OUT, 16>);
+  return go(k_dft_direct<FF, IN, OUT, 32>);
 }
 
 }  // namespace
@@ -410,6 +487,22 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   a.sign = sign;
   a.accumulate = accumulate ? 1 : 0;
   a.scale = scale;
+  const bool direct = ff_arith ? (a.P2 == 1 && Pin <= 16) : Pin <= 32;
+  if (direct) {
+    if (ff_arith) {
+      if (in_fmt == DFT_CD && out_fmt == DFT_FF) return launch_direct<true, DFT_CD, DFT_FF>(name, a, st);
+      if (in_fmt == DFT_FF && out_fmt == DFT_FF) return launch_direct<true, DFT_FF, DFT_FF>(name, a, st);
+      if (in_fmt == DFT_FF && out_fmt == DFT_CD) return launch_direct<true, DFT_FF, DFT_CD>(name, a, st);
+      if (in_fmt == DFT_CD && out_fmt == DFT_CD) return launch_direct<true, DFT_CD, DFT_CD>(name, a, st);
+    } else {
+      if (in_fmt == DFT_CD && out_fmt == DFT_F32) return launch_direct<false, DFT_CD, DFT_F32>(name, a, st);
+      if (in_fmt == DFT_F32 && out_fmt == DFT_F32) return launch_direct<false, DFT_F32, DFT_F32>(name, a, st);
+      if (in_fmt == DFT_F32 && out_fmt == DFT_CD) return launch_direct<false, DFT_F32, DFT_CD>(name, a, st);
+      if (in_fmt == DFT_FF && out_fmt == DFT_F32) return launch_direct<false, DFT_FF, DFT_F32>(name, a, st);
+    }
+    set_error("dft_pass: unsupported storage formats %d -> %d", in_fmt, out_fmt);
+    return FMPB_EINVAL;
+  }
   const size_t vb = ff_arith ? sizeof(float4) : sizeof(float2);
   const size_t sb = in_fmt == DFT_F32 ? sizeof(float2) : sizeof(float4);
   // inner sub-tiles of 32 per CTA: enough items for up to 8 warps in both
