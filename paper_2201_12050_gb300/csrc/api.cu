@@ -27,8 +27,14 @@ void set_error(const char* fmt, ...) {
   g_error = buf;
 }
 
+const char* take_failed_launch();
+
 fmpb_status cuda_status(cudaError_t e, const char* what) {
-  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  const char* k = take_failed_launch();
+  if (k)
+    set_error("CUDA error in %s: %s (refused launch of %s)", what, cudaGetErrorString(e), k);
+  else
+    set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? FMPB_ENOMEM : FMPB_ECUDA;
 }
 

@@ -203,9 +203,7 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
   // tile (down to 4 values, 64-byte segments) while the grid is small
   while (TI > 4 && ((I + TI - 1) / TI) * (int64_t)O1 * O2 < 4 * 152) TI /= 2;
   size_t smem = (size_t)(per_ti * TI + P) * sizeof(float4);
-  if (smem > 48 * 1024)
-    FMPB_CUDA(cudaFuncSetAttribute(k_dft_axis_ff<IN_FF, OUT_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  FMPB_CUDA((smem_limit_once<k_dft_axis_ff<IN_FF, OUT_FF>>(200 * 1024)));
   dim3 grid((unsigned)((I + TI - 1) / TI), (unsigned)O2, (unsigned)O1);
   FMPB_LAUNCH(name, st, k_dft_axis_ff<IN_FF, OUT_FF><<<grid, 256, smem, st>>>(in, out, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P,
                                                                            sign, scale, accumulate ? 1 : 0, (int)TI, P1));
@@ -453,9 +451,7 @@ static fmpb_status launch_block_product_f32(const float2* spec, const XT* X, XT*
                                             int R, cudaStream_t st) {
   const int threads = 256, rows = 32;
   const size_t smem = (size_t)RC * B * sizeof(float2);
-  if (smem > 48 * 1024)
-    FMPB_CUDA(cudaFuncSetAttribute(k_block_product_f32<RC, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  FMPB_CUDA((smem_limit_once<k_block_product_f32<RC, XT>>(200 * 1024)));
   dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
   for (int r0 = 0; r0 < R; r0 += RC) {
     FMPB_LAUNCH("block_product_f32", st, k_block_product_f32<RC, XT><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));
@@ -483,9 +479,7 @@ static fmpb_status launch_block_product(const void* spec, const float4* X, float
                                         cudaStream_t st) {
   const int threads = 256, rows = 32;
   const size_t smem = (size_t)RC * B * sizeof(float4);
-  if (smem > 48 * 1024)
-    FMPB_CUDA(cudaFuncSetAttribute(k_block_product_ff<RC, SPEC_FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  FMPB_CUDA((smem_limit_once<k_block_product_ff<RC, SPEC_FF>>(200 * 1024)));
   dim3 grid((unsigned)((B + rows - 1) / rows), (unsigned)F);
   for (int r0 = 0; r0 < R; r0 += RC) {
     FMPB_LAUNCH("block_product", st, k_block_product_ff<RC, SPEC_FF><<<grid, threads, smem, st>>>(spec, X, Y, B, R, r0, rows));

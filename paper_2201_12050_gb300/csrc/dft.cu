@@ -31,6 +31,7 @@
 // accuracy anyway).  In place (in == out with equal strides, Pin = Pout = P)
 // is allowed: every input of a tile is read before any output of it is
 // written.
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -393,10 +394,11 @@ int64_t plan_cost(int P, int Pin, int Pout, int P1) {
   return (int64_t)Pin * P1 + P + (int64_t)Pout * P2;
 }
 
+// Largest dynamic shared memory a two-factor pass may ask for.
+constexpr int DFT_MAX_SMEM = 200 * 1024;
 template <bool FF, int IN, int OUT>
 fmpb_status launch_dft(const char* name, const DftArgs& a, size_t smem, int threads, cudaStream_t st) {
-  if (smem > 48 * 1024)
-    FMPB_CUDA(cudaFuncSetAttribute(k_dft<FF, IN, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FMPB_CUDA((smem_limit_once<k_dft<FF, IN, OUT>>(DFT_MAX_SMEM)));
   // persistent CTAs: as many as can be resident, each walking its share of the tiles
   int per_sm = 0, sms = 0, dev = 0;
   FMPB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft<FF, IN, OUT>, threads, smem));
@@ -522,7 +524,7 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   a.tiles_i = (I + 32 * nsub - 1) / (32 * nsub);
   a.tiles = a.tiles_i * O1 * O2;
   const size_t smem = smem_for(nsub);
-  if (smem > 200 * 1024) {
+  if (smem > (size_t)DFT_MAX_SMEM) {
     set_error("dft_pass: axis length %d too large", P);
     return FMPB_EINVAL;
   }

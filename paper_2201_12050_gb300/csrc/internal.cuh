@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <mutex>
 #include <vector>
 #include <algorithm>
 
@@ -207,6 +208,19 @@ fmpb_status insertion_loss(const DeviceMesh& m, const DeviceMesh* refl, const Ce
 fmpb_status reverse_cells(const void* in, void* out, size_t elem_bytes, int R, const int M[3], int n, int h,
                           cudaStream_t st);
 fmpb_status scale_inplace(cd* a, size_t n, cd s, cudaStream_t st);
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per process
+// (thread-safe; later calls return the first call's status).  Operators are
+// built and applied from several host threads at once, so the limit is never
+// changed while another thread may be launching the kernel.
+// One instance (and one flag) per kernel: the kernel is a template argument.
+template <auto Kernel>
+inline cudaError_t smem_limit_once(int bytes) {
+  static std::once_flag once;
+  static cudaError_t status = cudaSuccess;
+  std::call_once(once, [&] { status = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
+  return status;
+}
 
 // Pruned DFT passes (dft.cu): storage formats of the values a pass reads and
 // writes (complex double, float-float pairs, complex FP32).

@@ -649,7 +649,11 @@ fmpb_status m2l_blocks(int nt, double k, int n_d, const double* dvecs_host, cons
 
 fmpb_status p2m_apply(const float4* V0, int n, int B, int64_t columns, const float4* p, cd* Mom, cudaStream_t st) {
   const size_t smem = sizeof(float4) * n;
-  if (smem > 48 * 1024) FMPB_CUDA(cudaFuncSetAttribute(k_p2m_apply_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 200 * 1024) {
+    set_error("p2m_apply: %zu bytes of shared memory per block", smem);
+    return FMPB_EINVAL;
+  }
+  FMPB_CUDA((smem_limit_once<k_p2m_apply_ff>(200 * 1024)));
   FMPB_LAUNCH("p2m_apply", st, k_p2m_apply_ff<<<(unsigned)columns, 256, smem, st>>>(V0, n, B, p, Mom));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;

@@ -35,6 +35,18 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+thread_local const char* t_failed_launch = nullptr;
+
+void note_launch(const char* name) {
+  if (!t_failed_launch && cudaPeekAtLastError() != cudaSuccess) t_failed_launch = name;
+}
+
+const char* take_failed_launch() {
+  const char* n = t_failed_launch;
+  t_failed_launch = nullptr;
+  return n;
+}
+
 bool profiling_enabled() { return g_enabled.load(std::memory_order_relaxed); }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 

@@ -19,10 +19,17 @@ struct ProfScope {
 
 }  // namespace fmpb
 
+namespace fmpb {
+// Remembers (per host thread) the name of a kernel whose launch was
+// refused, so that the status message of the check that follows names it.
+void note_launch(const char* name);
+}  // namespace fmpb
+
 // Launch a kernel under the profiler and count it.
 #define FMPB_LAUNCH(name, st, ...)              \
   do {                                          \
     ::fmpb::ProfScope _fmpb_prof(name, st);     \
     __VA_ARGS__;                                \
     ::fmpb::count_launch();                     \
+    ::fmpb::note_launch(name);                  \
   } while (0)

@@ -181,7 +181,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 //           row tile of an odd count runs its second half empty.
 template <int BN, bool FREQ, int MT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_gemm(const __nv_bfloat16* __restrict__ A, int64_t a_stride, int Kp, const __nv_bfloat16* __restrict__ X,
+    k_tc_gemm(const TcBatch batch, int64_t a_stride, int Kp, const __nv_bfloat16* __restrict__ X,
               void* __restrict__ y_, int m, int64_t ncols, int Mx, int My, int Mz, TcOffsets offs, int accumulate,
               unsigned* err) {
   using Tile = TcTile<BN, MT>;
@@ -194,9 +194,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int m0 = blockIdx.x * TC_BM * MT;
   const int64_t Mp = a_stride / Kp;
   const bool two = MT == 2 && m0 + TC_BM < Mp;   // second row half present
-  const int64_t n0 = (int64_t)(FREQ ? blockIdx.z : blockIdx.y) * BN;
+  // column tile of one operator of the batch: ncols columns per operator,
+  // stacked operator after operator in X and y (FREQ: within each frequency)
+  const int64_t ctile = FREQ ? blockIdx.z : blockIdx.y;
+  const int bop = (int)(ctile / batch.tiles);
+  const int64_t n0 = (ctile - (int64_t)bop * batch.tiles) * BN;
   const int64_t f = FREQ ? (int64_t)blockIdx.y : 0;
   const int Nc = Mx * My * Mz;
+  const int64_t ctot = ncols * batch.n;          // columns of all operators
+  const int64_t cbase = (int64_t)bop * ncols;    // this operator's first column
+  const __nv_bfloat16* __restrict__ A = batch.A[bop];
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const bool ok = bj[t] >= 0;
-        cp_async16(sb + t * 4096, ok ? X + (f * ncols + bj[t]) * Kp + k0 : X, ok ? 16 : 0);
+        cp_async16(sb + t * 4096, ok ? X + (f * ctot + cbase + bj[t]) * Kp + k0 : X, ok ? 16 : 0);
       }
     } else {
       const int dx = offs.d[o][0], dy = offs.d[o][1], dz = offs.d[o][2];
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = 0; t < NB; ++t) {
         const int sx = bx[t] - dx, sy = by[t] - dy, sz = bz[t] - dz;
         const bool ok = bj[t] >= 0 && sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz;
-        const __nv_bfloat16* src = ok ? X + (bj[t] - dlin) * Kp + k0 : X;
+        const __nv_bfloat16* src = ok ? X + (cbase + bj[t] - dlin) * Kp + k0 : X;
         cp_async16(sb + t * 4096, src, ok ? 16 : 0);
       }
     }
@@ -325,15 +332,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               // lo = 0), or complex FP32 when `accumulate` is set (FREQ mode
               // never accumulates; the flag selects the output format there)
               if (accumulate) {
-                float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + (f * ncols + j) * m + i) + part;
+                float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + (f * ctot + cbase + j) * m + i) +
+                           part;
                 *d = v[t];
               } else {
-                float2* d =
-                    reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ncols + j) * m + i) + part;
+                float2* d = reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ctot + cbase + j) * m + i) +
+                            part;
                 *d = make_float2(v[t], 0.f);
               }
             } else {
-              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + j * m + i) + part;
+              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + (cbase + j) * m + i) + part;
               *d = accumulate ? *d + (double)v[t] : (double)v[t];
             }
           }
@@ -435,13 +443,22 @@ __global__ void k_tc_rows_from_f32(const float2* __restrict__ x, int64_t k, int6
 }
 
 template <int BN, bool FREQ, int MT>
-fmpb_status launch_tc(dim3 grid, const __nv_bfloat16* A, int64_t a_stride, int64_t Kp, const __nv_bfloat16* X,
+fmpb_status launch_tc(dim3 grid, TcBatch batch, int64_t a_stride, int64_t Kp, const __nv_bfloat16* X,
                       void* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs, bool accumulate,
                       unsigned* err, cudaStream_t st) {
   using Tile = TcTile<BN, MT>;
-  FMPB_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, FREQ, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile::SMEM));
+  batch.tiles = (ncols + BN - 1) / BN;
+  if (FREQ)
+    grid.z = (unsigned)(batch.tiles * batch.n);
+  else
+    grid.y = (unsigned)(batch.tiles * batch.n);
+  if (batch.tiles * batch.n > 65535) {
+    set_error("tensor-core product: %lld column tiles exceed the launch limit", (long long)(batch.tiles * batch.n));
+    return FMPB_EINVAL;
+  }
+  FMPB_CUDA((smem_limit_once<k_tc_gemm<BN, FREQ, MT>>(Tile::SMEM)));
   FMPB_LAUNCH(FREQ ? "tc_block_product" : "tc_gemm", st,
-              (k_tc_gemm<BN, FREQ, MT><<<grid, TC_THREADS, Tile::SMEM, st>>>(A, a_stride, (int)Kp, X, y, (int)m,
+              (k_tc_gemm<BN, FREQ, MT><<<grid, TC_THREADS, Tile::SMEM, st>>>(batch, a_stride, (int)Kp, X, y, (int)m,
                                                                               ncols, M[0], M[1], M[2], offs,
                                                                               accumulate ? 1 : 0, err)));
   FMPB_CUDA(cudaGetLastError());
@@ -455,17 +472,12 @@ struct TcVariant {
 constexpr TcVariant TC_VARIANTS[] = {{1, 256}, {2, 256}, {2, 128}, {1, 128}};
 constexpr int TC_NVARIANTS = sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]);
 
-fmpb_status launch_offset_variant(int v, const __nv_bfloat16* A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
+fmpb_status launch_offset_variant(int v, const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
                                   cd* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs,
                                   bool accumulate, unsigned* err, cudaStream_t st) {
   const TcVariant t = TC_VARIANTS[v];
   const int64_t rows = (int64_t)TC_BM * t.mt;
-  const int64_t ntiles = (ncols + t.bn - 1) / t.bn;
-  if (ntiles > 65535) {
-    set_error("tc_offset_gemm: %lld columns exceed the launch limit", (long long)ncols);
-    return FMPB_EINVAL;
-  }
-  dim3 grid((unsigned)((Mp + rows - 1) / rows), (unsigned)ntiles);
+  dim3 grid((unsigned)((Mp + rows - 1) / rows), 1);
   switch (v) {
     case 0: return launch_tc<256, false, 1>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
     case 1: return launch_tc<256, false, 2>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
@@ -484,9 +496,9 @@ fmpb_status launch_offset_variant(int v, const __nv_bfloat16* A, int64_t Mp, int
 struct TuneKey {
   int dev;
   int64_t m, k, ncols;
-  int noff;
+  int noff, nbatch;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, m, k, ncols, noff) < std::tie(o.dev, o.m, o.k, o.ncols, o.noff);
+    return std::tie(dev, m, k, ncols, noff, nbatch) < std::tie(o.dev, o.m, o.k, o.ncols, o.noff, o.nbatch);
   }
 };
 struct TuneEntry {
@@ -497,13 +509,13 @@ std::mutex g_tune_mu;
 std::map<TuneKey, TuneEntry> g_tune;
 int g_forced_variant = -1;   // >= 0: fmpb_set_tile_variant override
 
-fmpb_status tune_offset_gemm(const TuneKey& key, const __nv_bfloat16* A, int64_t Mp, int64_t Kp,
+fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, int64_t Kp,
                              const __nv_bfloat16* X, cd* y, int64_t m, int64_t ncols, const int M[3],
                              const TcOffsets& offs, bool accumulate, unsigned* err, cudaStream_t st, int* chosen) {
   cd* out = y;
   cd* scratch = nullptr;
   if (accumulate) {
-    FMPB_CUDA(cudaMalloc(&scratch, sizeof(cd) * (size_t)ncols * m));
+    FMPB_CUDA(cudaMalloc(&scratch, sizeof(cd) * (size_t)ncols * A.n * m));
     out = scratch;
   }
   TuneEntry e{};
@@ -600,6 +612,19 @@ fmpb_status tc_rows_from_f32(const float2* x, int64_t rows, int64_t k, __nv_bflo
 
 fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
                            const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st) {
+  return tc_offset_gemm_batch(&A, 1, offs, m, k, M, R, X, y, accumulate, err, st);
+}
+
+fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, const TcOffsets& offs, int64_t m,
+                                 int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
+                                 unsigned* err, cudaStream_t st) {
+  if (n_ops < 1 || n_ops > TC_MAX_BATCH) {
+    set_error("tc_offset_gemm: %d operators in a batch (1..%d)", n_ops, TC_MAX_BATCH);
+    return FMPB_EINVAL;
+  }
+  TcBatch A{};
+  A.n = n_ops;
+  for (int o = 0; o < n_ops; ++o) A.A[o] = Aops[o];
   const int64_t Mp = tc_rows(m), Kp = tc_depth(k);
   const int64_t Nc = (int64_t)M[0] * M[1] * M[2];
   const int64_t ncols = Nc * R;
@@ -613,7 +638,7 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
   }
   int dev = 0;
   FMPB_CUDA(cudaGetDevice(&dev));
-  const TuneKey key{dev, m, k, ncols, offs.n};
+  const TuneKey key{dev, m, k, ncols, offs.n, n_ops};
   int v = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -667,6 +692,18 @@ fmpb_status tc_tuning_summary(std::string& out) {
 
 fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, void* Y,
                          unsigned* err, cudaStream_t st, bool y_f32) {
+  return tc_freq_gemm_batch(&A, 1, F, B, R, X, Y, err, st, y_f32);
+}
+
+fmpb_status tc_freq_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, int64_t F, int64_t B, int R,
+                               const __nv_bfloat16* X, void* Y, unsigned* err, cudaStream_t st, bool y_f32) {
+  if (n_ops < 1 || n_ops > TC_MAX_BATCH) {
+    set_error("tc_freq_gemm: %d operators in a batch (1..%d)", n_ops, TC_MAX_BATCH);
+    return FMPB_EINVAL;
+  }
+  TcBatch A{};
+  A.n = n_ops;
+  for (int o = 0; o < n_ops; ++o) A.A[o] = Aops[o];
   const int64_t Mp = tc_rows(B), Kp = tc_depth(B);
   if (F < 1 || F > 65535 || B < 1 || R < 1 || Mp / TC_BM > 65535 || Kp > (1 << 24)) {
     set_error("tc_freq_gemm: bad shape (F %lld, B %lld, R %d)", (long long)F, (long long)B, R);
@@ -675,11 +712,7 @@ fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, co
   const TcOffsets none{};
   const int M[3] = {1, 1, 1};
   const int BN = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
-  dim3 grid((unsigned)(Mp / TC_BM), (unsigned)F, (unsigned)((R + BN - 1) / BN));
-  if (grid.z > 65535) {
-    set_error("tc_freq_gemm: too many right-hand sides");
-    return FMPB_EINVAL;
-  }
+  dim3 grid((unsigned)(Mp / TC_BM), (unsigned)F, 1);
   switch (BN) {
     case 32: return launch_tc<32, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
     case 64: return launch_tc<64, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);

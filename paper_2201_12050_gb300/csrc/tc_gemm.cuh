@@ -15,6 +15,15 @@ struct TcOffsets {
   int d[TC_MAX_OFF][3];
 };
 
+// Operators of one batched launch: their realified tables (same shapes), the
+// columns of operator o following those of o - 1 in X and y.
+constexpr int TC_MAX_BATCH = 16;
+struct TcBatch {
+  int n;
+  int64_t tiles;   // column tiles per operator (set at launch)
+  const __nv_bfloat16* A[TC_MAX_BATCH];
+};
+
 // Shapes of the realified operands of a complex m x k block.
 //   Mp = 2 m rounded up to 128 (tile rows), Kp = 2 k rounded up to 64 (tile depth).
 inline int64_t tc_rows(int64_t m) { return (2 * m + 127) / 128 * 128; }
@@ -38,6 +47,11 @@ fmpb_status tc_rows_to_bf16(const cd* x, int64_t rows, int64_t k, __nv_bfloat16*
 // here) if a wait inside the kernel gave up.
 fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
                            const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st);
+// The same for n_ops operators with tables A[o] of one shape in one launch:
+// X and y hold the R Nc columns of operator 0, then those of operator 1, ...
+fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* A, int n_ops, const TcOffsets& offs, int64_t m,
+                                 int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
+                                 unsigned* err, cudaStream_t st);
 
 // Float-float sources (float4 per complex value: re_hi, re_lo, im_hi, im_lo),
 // rounded (hi + lo) -> FP32 -> BF16.
@@ -53,6 +67,11 @@ fmpb_status tc_rows_from_f32(const float2* x, int64_t rows, int64_t k, __nv_bflo
 // complex FP32 (float2).
 fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, void* Y,
                          unsigned* err, cudaStream_t st, bool y_f32 = false);
+// The same for n_ops spectra of one shape in one launch: at each frequency
+// f, X and Y hold the R rows of operator 0, then those of operator 1, ...
+// (F n_ops R rows in all).
+fmpb_status tc_freq_gemm_batch(const __nv_bfloat16* const* A, int n_ops, int64_t F, int64_t B, int R,
+                               const __nv_bfloat16* X, void* Y, unsigned* err, cudaStream_t st, bool y_f32 = false);
 
 // JSON list of the tile variants the offset-GEMM autotuner chose so far.
 fmpb_status tc_tuning_summary(std::string& out);
