@@ -490,7 +490,57 @@ def batching_section(gb, torch, stream, freq_index=3, n_t=12):
         out[name] = {"build_ms": build_ms, "matvec_64rhs_ms": mv_ms, "matvec_kernels_ms": kern}
         op.close()
     out["speedup_bf16_product_vs_fp64"] = out["fp64"]["matvec_64rhs_ms"] / out["bf16"]["matvec_64rhs_ms"]
+    out["frequency_batch"] = _guarded(frequency_batch, gb, torch, stream, w, v, t, n_t)
     return out
+
+
+def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=20):
+    """The whole batching workload: 8 frequencies x 64 directions (512
+    systems) with BF16 tensor-core operators, solved as 8 GMRES runs one
+    after the other and as one fmpb_solve_batch (one product sequence per
+    iteration over the 8 operators: near field, P2M, DFT passes, M2L and
+    L2P each one launch)."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ks = list(w.wavenumbers)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ops = [gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM, n_t=n_t, precision=gb.BF16) for k in ks]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    bs = torch.stack([op.rhs_plane_wave(w.directions) for op in ops])
+    R = bs.shape[1]
+    res = {"systems": len(ops) * R, "frequencies_hz": [round(k * SPEED_OF_SOUND / (2 * math.pi), 1) for k in ks],
+           "tol": tol, "restart": restart, "builds_s": build_s}
+    # one after the other
+    s0, s1 = ev(), ev()
+    s0.record(stream)
+    seq, seq_info = [], []
+    for o, op in enumerate(ops):
+        p, info = op.solve(bs[o], tol=tol, restart=restart, maxit=3000, raise_on_noconv=False)
+        seq.append(p)
+        seq_info.append(info)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    # one batched solve
+    b0, b1 = ev(), ev()
+    b0.record(stream)
+    pb, binfo = gb.solve_batch(ops, bs, tol=tol, restart=restart, maxit=3000, raise_on_noconv=False)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    bat_ms = b0.elapsed_time(b1)
+    res["sequential"] = {"ms": seq_ms, "solves_per_s": len(ops) * R * 1e3 / seq_ms,
+                         "iters_max_per_frequency": [max(i["iters"] for i in inf) for inf in seq_info]}
+    res["batched"] = {"ms": bat_ms, "solves_per_s": len(ops) * R * 1e3 / bat_ms,
+                      "iters_max_per_frequency": [max(i["iters"] for i in inf) for inf in binfo],
+                      "relres_true_max_per_frequency": [max(i["relres_true"] for i in inf) for inf in binfo],
+                      "all_converged": all(i["converged"] for inf in binfo for i in inf)}
+    res["batched_vs_sequential_rel_diff_per_frequency"] = [
+        float(torch.linalg.vector_norm(pb[o] - seq[o]) / torch.linalg.vector_norm(seq[o])) for o in range(len(ops))]
+    res["speedup_batched_vs_sequential"] = seq_ms / bat_ms
+    for op in ops:
+        op.close()
+    return res
 
 
 def serving_section(gb, n_sample=24):

@@ -314,6 +314,31 @@ fmpb_status fmpb_solve(const fmpb_operator *op, int R, const fmpb_c64 *b, fmpb_c
                        const fmpb_solve_opts *opts, fmpb_solve_info *info, void *stream);
 
 /*
+ * Solves the systems of n_ops operators at once (Sec. 4's GMRES, as in
+ * fmpb_solve), e.g. one lattice at several frequencies, R right-hand sides
+ * each: A_o p_{o,r} = b_{o,r}.  The Arnoldi steps of all n_ops R systems run
+ * together, one product sequence per iteration.  When the operators share
+ * one shape and apply their FMM form on the tensor cores (BF16 operators,
+ * and the inner products of MIXED ones: same mesh size, lattice and n_t,
+ * full space), every step of that product (near field, P2M, DFT passes,
+ * per-frequency M2L products, L2P) is one launch over all operators (Sec.
+ * 3.5, Eq. (FMPBEMsystem) applied to the stacked moments); otherwise each
+ * operator applies its own product within the shared iteration.  Every
+ * system keeps its own Krylov basis, residual and convergence test, so each
+ * result matches its own fmpb_solve up to rounding.
+ *   ops    host array of n_ops (1..16) operators with one N; MIXED operators
+ *          only with MIXED ones.
+ *   b, p   device, n_ops x R x N: system (o, r) at ((o R) + r) N; p is
+ *          overwritten.  R n_ops <= 4096.
+ *   info   host, n_ops x R entries (same order), may be NULL.
+ * Allocates the batched product's scratch per call; returns as fmpb_solve
+ * (FMPB_ECUDA also if a tensor-core wait of any operator gave up).
+ * Synchronises the stream.
+ */
+fmpb_status fmpb_solve_batch(const fmpb_operator *const *ops, int n_ops, int R, const fmpb_c64 *b, fmpb_c64 *p,
+                             const fmpb_solve_opts *opts, fmpb_solve_info *info, void *stream);
+
+/*
  * Synchronises the stream and reports whether any tensor-core product of
  * this operator (BF16 precision) gave up waiting for its MMAs since the
  * operator was built: every such wait is bounded (about one second), and a

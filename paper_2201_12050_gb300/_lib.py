@@ -110,6 +110,7 @@ SIGNATURES = {
     "fmpb_rhs_plane_wave": (INT, [P, INT, P, P, P, P]),
     "fmpb_matvec": (INT, [P, INT, P, P, P]),
     "fmpb_solve": (INT, [P, INT, P, P, ctypes.POINTER(SolveOpts), P, P]),
+    "fmpb_solve_batch": (INT, [P, INT, INT, P, P, ctypes.POINTER(SolveOpts), P, P]),
     "fmpb_operator_check": (INT, [P, P]),
     "fmpb_field": (INT, [P, INT, P, P, P, I64, P, P, P]),
     "fmpb_build_blocks": (INT, [P, I64, P, I64, ctypes.POINTER(Lattice), D, INT, P, P, P]),

@@ -191,6 +191,33 @@ class Operator:
         return out
 
 
+def solve_batch(ops, b, tol=1e-8, restart=30, maxit=1000, timeout_ms=0, out=None, raise_on_noconv=True,
+                inner_tol=0.0):
+    """fmpb_solve_batch: the systems of several operators with one N in one GMRES.
+
+    b: (n_ops, R, N) complex128 CUDA; returns (p of the same shape, info as a
+    list of n_ops lists of R dicts)."""
+    n_ops = len(ops)
+    if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.complex128 and b.is_contiguous()):
+        raise TypeError("b must be a contiguous complex128 CUDA tensor")
+    N = ops[0].N
+    if b.dim() != 3 or b.shape[0] != n_ops or b.shape[2] != N:
+        raise ValueError(f"b must have shape (n_ops, R, N) = ({n_ops}, R, {N})")
+    R = b.shape[1]
+    p = out if out is not None else torch.empty_like(b)
+    handles = (ctypes.c_void_p * n_ops)(*[op._h.value for op in ops])
+    opts = SolveOpts(float(tol), int(restart), int(maxit), int(timeout_ms), float(inner_tol))
+    infos = (SolveInfo * (n_ops * R))()
+    st = lib().fmpb_solve_batch(ctypes.cast(handles, ctypes.c_void_p), n_ops, R, _ptr(b), _ptr(p), ctypes.byref(opts),
+                                ctypes.cast(infos, ctypes.c_void_p), _stream())
+    info = [[{"iters": i.iters, "converged": bool(i.converged), "relres_est": i.relres_est,
+              "relres_true": i.relres_true, "refinements": i.refinements} for i in infos[o * R:(o + 1) * R]]
+            for o in range(n_ops)]
+    if st != 0 and (raise_on_noconv or st not in (-5, -6)):
+        check(st)
+    return p, info
+
+
 def build_blocks(verts, tris, counts, vectors, k, offsets):
     """fmpb_build_blocks: T_delta for each offset, (n_off, n, n) on the device."""
     v = _host(verts, np.float64)

@@ -913,6 +913,142 @@ fmpb_status fmpb_solve(const fmpb_operator* op, int R, const fmpb_c64* b, fmpb_c
   return c != FMPB_OK ? c : s;
 }
 
+// ------------------------------------------------ batched solves -------
+// Device scratch of a batched solve, grown on demand and freed with it.
+struct BatchScratch {
+  cd* p = nullptr;
+  size_t elems = 0;
+  ~BatchScratch() { cudaFree(p); }
+  fmpb_status ensure(size_t e) {
+    if (e <= elems) return FMPB_OK;
+    cudaFree(p);
+    p = nullptr;
+    elems = 0;
+    if (cudaMalloc((void**)&p, sizeof(cd) * e) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("solve_batch: cannot allocate %zu bytes of scratch", sizeof(cd) * e);
+      return FMPB_ENOMEM;
+    }
+    elems = e;
+    return FMPB_OK;
+  }
+};
+
+// Operators whose products can run as one sequence of tensor-core launches:
+// the FMM form on the tensor cores (BF16 operators; MIXED ones for their
+// inner products), one shape (mesh size, lattice, block size), full space,
+// no multilevel near field, on one device.
+static bool tc_batchable(const fmpb_operator* const* ops, int n_ops, bool low) {
+  if (n_ops < 2 || n_ops > TC_MAX_BATCH) return false;
+  const fmpb_operator* a = ops[0];
+  for (int q = 0; q < n_ops; ++q) {
+    const fmpb_operator* b = ops[q];
+    if (b->form != FMPB_FORM_FMM || b->near2 || b->plane.on) return false;
+    if (!(b->precision == FMPB_BF16 || (b->precision == FMPB_MIXED && low))) return false;
+    if (!b->Sb || !b->V0b || !b->U0b || !b->specb || !b->tc_err) return false;
+    if (b->device != a->device || b->mesh.n != a->mesh.n || b->B != a->B || b->shape.F != a->shape.F ||
+        b->n_near != a->n_near)
+      return false;
+    for (int c = 0; c < 3; ++c)
+      if (b->shape.M[c] != a->shape.M[c]) return false;
+    for (int i = 0; i < a->n_near; ++i)
+      for (int c = 0; c < 3; ++c)
+        if (b->near_tc.d[i][c] != a->near_tc.d[i][c]) return false;
+  }
+  return true;
+}
+
+// y = A_o x for every operator o at once (R right-hand sides each, operator
+// o's R N values after those of o - 1): each step of the FMM product (near
+// field, P2M, DFT passes, per-frequency M2L products, L2P) is one launch over
+// all operators.  Tensor-core waits report to the first operator's flag.
+static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, int R, const cd* x, cd* y,
+                                   cudaStream_t st, BatchScratch& sc) {
+  const fmpb_operator* a = ops[0];
+  const int Rt = n_ops * R;
+  const int64_t Nc = a->shape.ncells, n = a->mesh.n, B = a->B, F = a->shape.F;
+  const size_t circ = circulant_scratch_elems(a->shape, B, Rt);
+  const size_t mom = (size_t)Rt * Nc * B;
+  const size_t xb_elems = (size_t)Rt * Nc * tc_depth(n), lb_elems = (size_t)Rt * Nc * tc_depth(B);
+  const size_t fb_elems = (size_t)F * Rt * tc_depth(B);
+  const size_t extra = (2 * (xb_elems + lb_elems + fb_elems) + sizeof(cd) - 1) / sizeof(cd);
+  FMPB_TRY(sc.ensure(circ + 2 * mom + extra));
+  cd* Mom = sc.p + circ;
+  cd* Loc = Mom + mom;
+  __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(Loc + mom);
+  __nv_bfloat16* lb = xb + xb_elems;
+  __nv_bfloat16* fb = lb + lb_elems;
+  const __nv_bfloat16 *Sb[TC_MAX_BATCH], *V0b[TC_MAX_BATCH], *U0b[TC_MAX_BATCH];
+  const void* sp[TC_MAX_BATCH];
+  for (int q = 0; q < n_ops; ++q) {
+    Sb[q] = ops[q]->Sb;
+    V0b[q] = ops[q]->V0b;
+    U0b[q] = ops[q]->U0b;
+    sp[q] = ops[q]->specb;
+  }
+  TcOffsets zero{};
+  zero.n = 1;
+  unsigned* err = a->tc_err;
+  FMPB_TRY(tc_rows_to_bf16(x, (int64_t)Rt * Nc, n, xb, st));
+  FMPB_TRY(tc_offset_gemm_batch(Sb, n_ops, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st));
+  FMPB_TRY(tc_offset_gemm_batch(V0b, n_ops, zero, B, n, a->shape.M, R, xb, Mom, false, err, st));
+  FMPB_TRY(circulant_apply(a->shape, B, nullptr, Rt, Mom, Loc, false, sc.p, st, SPEC_BF16, fb, err, false,
+                           circulant_f32_ok(a->shape), sp, n_ops));
+  FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)Rt * Nc, B, lb, st));
+  FMPB_TRY(tc_offset_gemm_batch(U0b, n_ops, zero, n, B, a->shape.M, R, lb, y, true, err, st));
+  return FMPB_OK;
+}
+
+fmpb_status fmpb_solve_batch(const fmpb_operator* const* ops, int n_ops, int R, const fmpb_c64* b, fmpb_c64* p,
+                             const fmpb_solve_opts* opts, fmpb_solve_info* info, void* stream) {
+  CHECK_ARG(ops && b && p, "solve_batch: NULL argument");
+  CHECK_ARG(n_ops >= 1 && n_ops <= TC_MAX_BATCH, "solve_batch: 1..%d operators", TC_MAX_BATCH);
+  CHECK_ARG(R >= 1 && (int64_t)R * n_ops <= 4096, "solve_batch: R x operators must be 1..4096");
+  CHECK_ARG((const void*)b != (const void*)p, "solve_batch: b and p must not alias");
+  for (int q = 0; q < n_ops; ++q) CHECK_ARG(ops[q], "solve_batch: operator %d is NULL", q);
+  const int64_t N = (int64_t)ops[0]->mesh.n * ops[0]->shape.ncells;
+  const bool mixed = ops[0]->precision == FMPB_MIXED;
+  bool ff = true;
+  for (int q = 0; q < n_ops; ++q) {
+    const fmpb_operator* op = ops[q];
+    CHECK_ARG((int64_t)op->mesh.n * op->shape.ncells == N, "solve_batch: operator %d has another size", q);
+    CHECK_ARG((op->precision == FMPB_MIXED) == mixed, "solve_batch: MIXED operators batch only with MIXED ones");
+    ff = ff && op->has_ff_matvec() && op->precision == FMPB_FP64;
+  }
+  fmpb_solve_opts o = opts ? *opts : fmpb_solve_opts{0.0, 0, 0, 0, 0.0};
+  cudaStream_t st = (cudaStream_t)stream;
+  BatchScratch sc;
+  const int64_t RN = (int64_t)R * N;
+  auto loop = [&](bool low, const cd* x, cd* y, cudaStream_t s) -> fmpb_status {
+    for (int q = 0; q < n_ops; ++q)
+      FMPB_TRY(const_cast<fmpb_operator*>(ops[q])->matvec(R, x + q * RN, y + q * RN, s, low));
+    return FMPB_OK;
+  };
+  const bool fused = tc_batchable(ops, n_ops, false), fused_low = tc_batchable(ops, n_ops, true);
+  MatvecFn A = [&](int, const cd* x, cd* y, cudaStream_t s) -> fmpb_status {
+    return fused ? batch_matvec_tc(ops, n_ops, R, x, y, s, sc) : loop(false, x, y, s);
+  };
+  fmpb_status s;
+  if (mixed) {
+    MatvecFn Alow = [&](int, const cd* x, cd* y, cudaStream_t s2) -> fmpb_status {
+      return fused_low ? batch_matvec_tc(ops, n_ops, R, x, y, s2, sc) : loop(true, x, y, s2);
+    };
+    s = gmres_refined(A, Alow, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st);
+  } else {
+    const MatvecFfFn Aff = [&](int, const float4* x, float4* y, cudaStream_t s2) -> fmpb_status {
+      for (int q = 0; q < n_ops; ++q) FMPB_TRY(const_cast<fmpb_operator*>(ops[q])->matvec_ff(R, x + q * RN, y + q * RN, s2));
+      return FMPB_OK;
+    };
+    s = gmres_solve(A, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st, ff ? &Aff : nullptr);
+  }
+  if (s != FMPB_OK && s != FMPB_ENOCONV) return s;
+  for (int q = 0; q < n_ops; ++q) {
+    const fmpb_status c = fmpb_operator_check(ops[q], stream);
+    if (c != FMPB_OK) return c;
+  }
+  return s;
+}
+
 fmpb_status fmpb_operator_check(const fmpb_operator* op, void* stream) {
   CHECK_ARG(op, "operator_check: NULL operator");
   cudaStream_t st = (cudaStream_t)stream;
