@@ -471,7 +471,9 @@ def batching_section(gb, torch, stream, freq_index=3, n_t=12):
                    "operator_bytes": op.info["bytes_device"],
                    "tc_tiles_chosen": [{k_: e[k_] for k_ in ("m", "k", "columns", "offsets", "rows_per_cta",
                                                               "columns_per_cta", "ms")}
-                                       for e in gb.tuning_summary() if e["columns"] == nc * R]}
+                                       for e in gb.tuning_summary()
+                                       if e.get("kernel") == "tc_gemm" and e["columns"] == nc * R],
+                   "dft_plans_chosen": [e for e in gb.tuning_summary() if e.get("kernel") == "dft"]}
     op.close()
     # MIXED: BF16 inner products, float-float outer residuals
     op, build_ms = build(gb.MIXED)

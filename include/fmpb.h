@@ -710,8 +710,13 @@ fmpb_status fmpb_profile_summary(char *buf, size_t len);
  * offsets) times the tile variants (128 or 256 output rows and 128 or 256
  * output columns per CTA) on the caller's stream and keeps the fastest;
  * every entry lists the chosen tile and the time of each variant (ms, in
- * the order 128x256, 256x256, 256x128, 128x128).  EINVAL if buf is too
- * small. */
+ * the order 128x256, 256x256, 256x128, 128x128); "kernel": "tc_gemm".
+ * It also lists the plans the DFT-pass autotuner chose ("kernel": "dft"):
+ * the first out-of-place, non-accumulating pass of each shape (device,
+ * arithmetic, padded length P, inputs Pin, outputs Pout, inner extent, line
+ * count) times the direct form and every split P = P1 P2 into factors of at
+ * most 16 and keeps the fastest; "chosen" and "ms" name them ("direct<P>",
+ * "split<P1>").  EINVAL if buf is too small. */
 fmpb_status fmpb_tuning_summary(char *buf, size_t len);
 
 /* Forces one tile variant of the tensor-core offset GEMM for all later

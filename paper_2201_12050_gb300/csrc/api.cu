@@ -1294,8 +1294,14 @@ fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fm
 
 fmpb_status fmpb_tuning_summary(char* buf, size_t len) {
   CHECK_ARG(buf && len >= 3, "tuning_summary: buffer too small");
-  std::string out;
-  FMPB_TRY(tc_tuning_summary(out));
+  std::string out, dft;
+  FMPB_TRY(tc_tuning_summary(out));   // "[...]"
+  dft_tuning_summary(dft);
+  if (!dft.empty()) {
+    out.pop_back();
+    if (out.size() > 1) out += ", ";
+    out += dft + "]";
+  }
   CHECK_ARG(out.size() + 1 <= len, "tuning_summary: buffer of %zu bytes too small (%zu needed)", len, out.size() + 1);
   memcpy(buf, out.c_str(), out.size() + 1);
   return FMPB_OK;

@@ -31,7 +31,11 @@
 // accuracy anyway).  In place (in == out with equal strides, Pin = Pout = P)
 // is allowed: every input of a tile is read before any output of it is
 // written.
+#include <cstdio>
+#include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
 #include <type_traits>
 
 #include "common.cuh"
@@ -453,44 +457,20 @@ bool dft_supported(int P) {
   return P <= 1 || dft_plan(P, P, P, &p1);
 }
 
-fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
-                     int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
-                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st) {
-  int P1 = 0;
-  if (!dft_plan(P, Pin, Pout, &P1)) {
-    set_error("dft_pass: axis length %d has no split into two factors of at most %d", P, DFT_R);
-    return FMPB_EINVAL;
-  }
-  if (Pin < 1 || Pin > P || Pout < 1 || Pout > P || O1 < 1 || O2 < 1 || I < 1) {
-    set_error("dft_pass: bad line geometry (Pin %d, Pout %d, P %d)", Pin, Pout, P);
-    return FMPB_EINVAL;
-  }
-  if (accumulate && out_fmt != DFT_CD) {
-    set_error("dft_pass: accumulation needs complex-double output");
-    return FMPB_EINVAL;
-  }
-  DftArgs a;
-  a.in = in;
-  a.out = out;
-  a.I = I;
-  a.a1 = a1;
-  a.a2 = a2;
-  a.aj = aj;
-  a.b1 = b1;
-  a.b2 = b2;
-  a.bf = bf;
-  a.O1 = O1;
-  a.O2 = O2;
-  a.Pin = Pin;
-  a.Pout = Pout;
-  a.P = P;
-  a.P1 = P1;
-  a.P2 = P / P1;
-  a.sign = sign;
-  a.accumulate = accumulate ? 1 : 0;
-  a.scale = scale;
-  const bool direct = ff_arith ? (a.P2 == 1 && Pin <= 16) : Pin <= 32;
-  if (direct) {
+// One plan of a pass: kind 0 = the direct form, kind 1 = the two-factor
+// form with the split P1.
+struct DftPlan {
+  int kind, P1;
+};
+
+static fmpb_status run_plan(const char* name, const DftPlan& plan, bool ff_arith, int in_fmt, int out_fmt,
+                            DftArgs a, cudaStream_t st) {
+  const int P = a.P, Pin = a.Pin;
+  const int64_t I = a.I;
+  const int O1 = a.O1, O2 = a.O2;
+  a.P1 = plan.kind == 0 ? P : plan.P1;
+  a.P2 = P / a.P1;
+  if (plan.kind == 0) {
     if (ff_arith) {
       if (in_fmt == DFT_CD && out_fmt == DFT_FF) return launch_direct<true, DFT_CD, DFT_FF>(name, a, st);
       if (in_fmt == DFT_FF && out_fmt == DFT_FF) return launch_direct<true, DFT_FF, DFT_FF>(name, a, st);
@@ -543,6 +523,149 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   }
   set_error("dft_pass: unsupported storage formats %d -> %d", in_fmt, out_fmt);
   return FMPB_EINVAL;
+}
+
+// DFT-pass autotuner: the first out-of-place, non-accumulating call of a
+// pass shape times every candidate plan (the direct form where the inputs
+// fit the registers, the two-factor form for every split into factors of at
+// most 16) with CUDA events on the caller's stream, after one untimed launch
+// each, keeps the fastest and runs it once more, so that the output carries
+// the chosen plan's rounding on the first call as on every later one.  In-place and accumulating passes, passes inside
+// a stream capture and shapes with one candidate take the model's plan
+// (fewest multiply-adds; the direct form for FP32 lines of at most 32
+// inputs).
+struct DftKey {
+  int dev, ff, in, out, P, Pin, Pout;
+  int64_t I, lines;
+  bool operator<(const DftKey& o) const {
+    return std::tie(dev, ff, in, out, P, Pin, Pout, I, lines) <
+           std::tie(o.dev, o.ff, o.in, o.out, o.P, o.Pin, o.Pout, o.I, o.lines);
+  }
+};
+struct DftTuned {
+  DftPlan plan;
+  int n;
+  DftPlan cand[DFT_R + 1];
+  float ms[DFT_R + 1];
+};
+std::mutex g_dft_mu;
+std::map<DftKey, DftTuned> g_dft_tune;
+
+fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
+                     int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
+                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st) {
+  int P1 = 0;
+  if (!dft_plan(P, Pin, Pout, &P1)) {
+    set_error("dft_pass: axis length %d has no split into two factors of at most %d", P, DFT_R);
+    return FMPB_EINVAL;
+  }
+  if (Pin < 1 || Pin > P || Pout < 1 || Pout > P || O1 < 1 || O2 < 1 || I < 1) {
+    set_error("dft_pass: bad line geometry (Pin %d, Pout %d, P %d)", Pin, Pout, P);
+    return FMPB_EINVAL;
+  }
+  if (accumulate && out_fmt != DFT_CD) {
+    set_error("dft_pass: accumulation needs complex-double output");
+    return FMPB_EINVAL;
+  }
+  DftArgs a{};
+  a.in = in;
+  a.out = out;
+  a.I = I;
+  a.a1 = a1;
+  a.a2 = a2;
+  a.aj = aj;
+  a.b1 = b1;
+  a.b2 = b2;
+  a.bf = bf;
+  a.O1 = O1;
+  a.O2 = O2;
+  a.Pin = Pin;
+  a.Pout = Pout;
+  a.P = P;
+  a.sign = sign;
+  a.accumulate = accumulate ? 1 : 0;
+  a.scale = scale;
+  // the model's plan
+  const bool direct_ok = ff_arith ? Pin <= 16 : Pin <= 32;
+  DftPlan model{1, P1};
+  if (ff_arith ? (P / P1 == 1 && direct_ok) : direct_ok) model = DftPlan{0, P};
+  if (P / P1 == 1 && !direct_ok) model = DftPlan{1, P1};
+  // candidates
+  DftPlan cand[DFT_R + 1];
+  int nc = 0;
+  if (direct_ok) cand[nc++] = DftPlan{0, P};
+  for (int p1 = 2; p1 <= DFT_R && p1 < P; ++p1)
+    if (P % p1 == 0 && P / p1 <= DFT_R && nc <= DFT_R) cand[nc++] = DftPlan{1, p1};
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FMPB_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (in == out || accumulate || cap != cudaStreamCaptureStatusNone || nc < 2)
+    return run_plan(name, model, ff_arith, in_fmt, out_fmt, a, st);
+  int dev = 0;
+  FMPB_CUDA(cudaGetDevice(&dev));
+  const DftKey key{dev, ff_arith ? 1 : 0, in_fmt, out_fmt, P, Pin, Pout, I, (int64_t)O1 * O2};
+  {
+    std::lock_guard<std::mutex> lk(g_dft_mu);
+    auto it = g_dft_tune.find(key);
+    if (it != g_dft_tune.end()) {
+      const DftPlan chosen = it->second.plan;
+      return run_plan(name, chosen, ff_arith, in_fmt, out_fmt, a, st);
+    }
+  }
+  DftTuned tuned{};
+  tuned.n = nc;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  fmpb_status s = FMPB_OK;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "dft tuning events");
+  float best = 1e30f;
+  DftPlan chosen = model;
+  for (int c = 0; c < nc && s == FMPB_OK; ++c) {
+    tuned.cand[c] = cand[c];
+    s = run_plan(name, cand[c], ff_arith, in_fmt, out_fmt, a, st);
+    if (s == FMPB_OK && cudaEventRecord(t0, st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "dft tuning");
+    if (s == FMPB_OK) s = run_plan(name, cand[c], ff_arith, in_fmt, out_fmt, a, st);
+    if (s == FMPB_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
+      s = cuda_status(cudaGetLastError(), "dft tuning");
+    float ms = 0.f;
+    if (s == FMPB_OK && cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) s = cuda_status(cudaGetLastError(), "dft tuning");
+    tuned.ms[c] = ms;
+    if (s == FMPB_OK && ms < best) {
+      best = ms;
+      chosen = cand[c];
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (s != FMPB_OK) return s;
+  tuned.plan = chosen;
+  {
+    std::lock_guard<std::mutex> lk(g_dft_mu);
+    g_dft_tune[key] = tuned;
+  }
+  // the chosen plan writes the output last, so that the first call of a
+  // shape gives the same rounding as every later one
+  return run_plan(name, chosen, ff_arith, in_fmt, out_fmt, a, st);
+}
+
+void dft_tuning_summary(std::string& out) {
+  std::lock_guard<std::mutex> lk(g_dft_mu);
+  char buf[256];
+  for (const auto& kv : g_dft_tune) {
+    const DftKey& k = kv.first;
+    const DftTuned& t = kv.second;
+    int n = snprintf(buf, sizeof(buf),
+                     "%s{\"kernel\": \"dft\", \"device\": %d, \"arith\": \"%s\", \"P\": %d, \"Pin\": %d, "
+                     "\"Pout\": %d, \"inner\": %lld, \"lines\": %lld, \"chosen\": \"%s%d\", \"ms\": {",
+                     out.size() > 1 ? ", " : "", k.dev, k.ff ? "ff" : "f32", k.P, k.Pin, k.Pout, (long long)k.I,
+                     (long long)k.lines, t.plan.kind == 0 ? "direct" : "split", t.plan.kind == 0 ? k.P : t.plan.P1);
+    out.append(buf, n);
+    for (int c = 0; c < t.n; ++c) {
+      n = snprintf(buf, sizeof(buf), "%s\"%s%d\": %.4f", c ? ", " : "", t.cand[c].kind == 0 ? "direct" : "split",
+                   t.cand[c].kind == 0 ? k.P : t.cand[c].P1, t.ms[c]);
+      out.append(buf, n);
+    }
+    out += "}}";
+  }
 }
 
 }  // namespace fmpb

@@ -231,6 +231,8 @@ enum DftFormat { DFT_CD = 0, DFT_FF = 1, DFT_F32 = 2 };
 bool dft_supported(int P);
 // One pass along an axis (see dft.cu): ff_arith selects float-float or FP32
 // arithmetic; in place needs in == out with equal strides and Pin = Pout = P.
+// Appends the DFT autotuner's choices as JSON objects (comma-separated) to out.
+void dft_tuning_summary(std::string& out);
 fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
                      int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
                      int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st);
