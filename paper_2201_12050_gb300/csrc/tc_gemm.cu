@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int64_t f = FREQ ? (int64_t)blockIdx.y : 0;
   const int Nc = Mx * My * Mz;
   const int64_t ctot = ncols * batch.n;          // columns of all operators
-  const int64_t cbase = (int64_t)bop * ncols;    // this operator's first column
+  const int64_t obase = (int64_t)bop * ncols;    // this operator's first column
   const __nv_bfloat16* __restrict__ A = batch.A[bop];
 
   if (tid == 0) {
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const bool ok = bj[t] >= 0;
-        cp_async16(sb + t * 4096, ok ? X + (f * ctot + cbase + bj[t]) * Kp + k0 : X, ok ? 16 : 0);
+        cp_async16(sb + t * 4096, ok ? X + (f * ctot + obase + bj[t]) * Kp + k0 : X, ok ? 16 : 0);
       }
     } else {
       const int dx = offs.d[o][0], dy = offs.d[o][1], dz = offs.d[o][2];
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = 0; t < NB; ++t) {
         const int sx = bx[t] - dx, sy = by[t] - dy, sz = bz[t] - dz;
         const bool ok = bj[t] >= 0 && sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz;
-        const __nv_bfloat16* src = ok ? X + (cbase + bj[t] - dlin) * Kp + k0 : X;
+        const __nv_bfloat16* src = ok ? X + (obase + bj[t] - dlin) * Kp + k0 : X;
         cp_async16(sb + t * 4096, src, ok ? 16 : 0);
       }
     }
@@ -332,16 +332,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               // lo = 0), or complex FP32 when `accumulate` is set (FREQ mode
               // never accumulates; the flag selects the output format there)
               if (accumulate) {
-                float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + (f * ctot + cbase + j) * m + i) +
+                float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + (f * ctot + obase + j) * m + i) +
                            part;
                 *d = v[t];
               } else {
-                float2* d = reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ctot + cbase + j) * m + i) +
+                float2* d = reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ctot + obase + j) * m + i) +
                             part;
                 *d = make_float2(v[t], 0.f);
               }
             } else {
-              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + (cbase + j) * m + i) + part;
+              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + (obase + j) * m + i) + part;
               *d = accumulate ? *d + (double)v[t] : (double)v[t];
             }
           }
