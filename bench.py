@@ -55,6 +55,9 @@ def parse():
                     help="small case for kernel captures: product/build = 3x8 cylinders (1.8 GB spectrum) at "
                          "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, BF16; gmres = 320 "
                          "Arnoldi steps of the full crystal at 300 Hz")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="run only the serving study on the first N requests of the seeded stream (FP64, MIXED, "
+                         "and the 10 Hz-snapped cache variant)")
     ap.add_argument("--only-headline", action="store_true",
                     help="skip the FMM, mixed-precision, serving and batching sections")
     ap.add_argument("--no-overlap", action="store_true",
@@ -545,38 +548,81 @@ def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=20):
     return res
 
 
-def serving_section(gb, n_sample=24):
-    """The serving loop on a bounded sample of the seeded request stream
-    (Poisson arrivals at 50 req/s, grids 4x4..64x8, 100-2000 Hz, 1-16 plane
-    waves): the first n_sample sphere-cell requests, submitted at their arrival
-    times.  Sphere cells use the FMM form with n_t = ceil(1.5 k rho) + 4."""
-    from workloads import serving_stream, icosphere
-    sv, stri = icosphere(2, 0.2)
-    reqs = [r for r in serving_stream(400) if r["cell"] == "sphere"][:n_sample]
+def run_serving(gb, reqs, precision, snap_hz=None, tol=TOL):
+    """Replays requests of the seeded serving stream at their arrival times
+    through the serving runtime (both cells; the AUTO form and the library's
+    truncation rule, as a caller without tuning would submit them) and
+    summarises latency, queueing and service times, cache use and HBM.
+    snap_hz: frequencies rounded to this grid (the cache variant)."""
+    from workloads import icosphere, capped_cylinder
+    cells = {"sphere": icosphere(2, 0.2), "cylinder": capped_cylinder(0.15, 3.0, 20, 29)}
     t0 = time.perf_counter()
-    with gb.Server(max_batch_rhs=64, tol=TOL, restart=SHORT_RESTART, maxit=MAXIT) as srv:
+    with gb.Server(max_batch_rhs=64, precision=precision, tol=tol, restart=SHORT_RESTART, maxit=MAXIT) as srv:
         tickets = []
         base = reqs[0]["t"]
         for r in reqs:
             delay = (r["t"] - base) - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            nt = int(min(20, max(6, math.ceil(1.5 * r["k"] * 0.2) + 4)))
-            tickets.append(srv.submit(sv, stri, r["counts"], r["lattice"], r["k"], r["dirs"], form=gb.FORM_FMM,
-                                      n_t=nt))
+            k = r["k"]
+            if snap_hz:
+                f = max(snap_hz, round(r["freq_hz"] / snap_hz) * snap_hz)
+                k = 2.0 * math.pi * f / SPEED_OF_SOUND
+            v, t = cells[r["cell"]]
+            tickets.append(srv.submit(v, t, r["counts"], r["lattice"], k, r["dirs"], form=gb.FORM_AUTO, n_t=0))
         results = [srv.wait(tk)[0] for tk in tickets]
         st = srv.stats()
     wall = time.perf_counter() - t0
     ok = [x for x in results if x["status_name"] == "FMPB_OK"]
-    return {"sample": f"first {n_sample} sphere-cell requests of the seeded 50 req/s stream",
-            "offered_req_per_s": (len(reqs) - 1) / (reqs[-1]["t"] - base) if len(reqs) > 1 else None,
-            "achieved_solves_per_s": len(ok) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "mean_ms": st["mean_ms"], "completed": st["completed"], "failed": st["failed"],
-            "batches": st["batches"], "cache_hits": st["cache_hits"],
-            "hbm_high_water_bytes": st["hbm_high_water"],
-            "iters_max": max(x["iters_max"] for x in results), "relres_true_max": max(x["relres_true_max"] for x in results),
-            "failures": [{k_: x.get(k_) for k_ in ("status_name", "error", "iters_max", "relres_true_max")}
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    queue = [x["queue_ms"] for x in ok]
+    service = [x["build_ms"] + x["solve_ms"] for x in ok]
+    span = reqs[-1]["t"] - base
+    return {"requests": len(reqs), "cells": {c: sum(1 for r in reqs if r["cell"] == c) for c in cells},
+            "offered_req_per_s": (len(reqs) - 1) / span if span > 0 else None,
+            "achieved_solves_per_s": len(ok) / wall, "wall_s": wall,
+            "latency_p50_ms": st["p50_ms"], "latency_p99_ms": st["p99_ms"], "latency_mean_ms": st["mean_ms"],
+            "queue_p50_ms": pct(queue, 50), "queue_p99_ms": pct(queue, 99),
+            "service_p50_ms": pct(service, 50), "service_p99_ms": pct(service, 99),
+            "build_mean_ms": float(np.mean([x["build_ms"] for x in ok])) if ok else None,
+            "solve_mean_ms": float(np.mean([x["solve_ms"] for x in ok])) if ok else None,
+            "completed": st["completed"], "failed": st["failed"], "batches": st["batches"],
+            "cache_hits": st["cache_hits"], "hbm_high_water_bytes": st["hbm_high_water"],
+            "iters_max": max((x["iters_max"] for x in results), default=None),
+            "relres_true_max": max((x["relres_true_max"] for x in ok), default=None),
+            "failures": [{k_: x.get(k_) for k_ in ("status_name", "iters_max", "relres_true_max")}
                          for x in results if x["status_name"] != "FMPB_OK"]}
+
+
+def serving_section(gb, n_sample=24):
+    """The serving runtime on the first n_sample requests of the seeded stream
+    (Poisson arrivals at 50 req/s, sphere or capped-cylinder cells on grids
+    4x4..64x8, 100-2000 Hz, 1-16 plane waves) at their arrival times, plain
+    FP64 operators.  The full comparison (hundreds of requests, plain FP64
+    beside MIXED, and the 10 Hz-snapped cache variant) is `--serving N`."""
+    from workloads import serving_stream
+    reqs = serving_stream(max(n_sample, 2))[:n_sample]
+    out = run_serving(gb, reqs, gb.FP64)
+    out["sample"] = f"first {n_sample} requests of the seeded 50 req/s stream, both cells, FP64"
+    return out
+
+
+def run_serving_study(args):
+    """`--serving N`: the first N requests of the seeded stream replayed three
+    times through the serving runtime: plain FP64 operators, MIXED operators
+    (FP32 / BF16 inner products, float-float outer residuals, same 1e-8
+    tolerance), and FP64 with frequencies snapped to a 10 Hz grid (the cache
+    variant).  Prints one JSON line."""
+    import torch
+    import paper_2201_12050_gb300 as gb
+    from workloads import serving_stream
+    torch.cuda.set_device(0)
+    reqs = serving_stream(args.serving)
+    out = {"serving_study": f"first {args.serving} requests of the seeded 50 req/s stream (both cells)",
+           "fp64": run_serving(gb, reqs, gb.FP64)}
+    out["mixed"] = _guarded(run_serving, gb, reqs, gb.MIXED)
+    out["fp64_snapped_10hz"] = _guarded(run_serving, gb, reqs, gb.FP64, 10.0)
+    print(json.dumps(out))
 
 
 def mixed_section(gb, torch, stream, args, w, v, t, sols, fp64_ms_per_step, world, rank):
@@ -1392,7 +1438,9 @@ def run_profile_case(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.profile_case:
+    if a.serving:
+        run_serving_study(a)
+    elif a.profile_case:
         run_profile_case(a)
     elif a.impl == "reference":
         run_reference(a)
