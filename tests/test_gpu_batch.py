@@ -91,5 +91,7 @@ def test_batch_argument_errors():
     rhs = torch.zeros((2, 1, a.N), dtype=torch.complex128, device="cuda")
     with pytest.raises(gb.FmpbError):
         gb.solve_batch([a, m], rhs)                      # MIXED beside BF16
+    with pytest.raises(gb.FmpbError):
+        gb.solve_batch([a, b], rhs)                      # another size (refused by the library)
     with pytest.raises(ValueError):
-        gb.solve_batch([a, b], rhs)                      # another size
+        gb.solve_batch([a, a], rhs[:, :, :-1].contiguous())   # right-hand sides of the wrong length
