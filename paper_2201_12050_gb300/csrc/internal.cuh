@@ -29,6 +29,49 @@ struct FfConst {
   ff inv4pi;
 };
 
+// Float-float helpers of the far-class quadrature (quadrature.cu, quad9.cu).
+__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
+  return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
+
+// e^{i psi} for |psi| <= 0.75 * 2^m
+__device__ __forceinline__ ffc expi_ff(ff psi, int m, const FfConst& C) {
+  const float sc = ldexpf(1.f, -m);
+  const ff p = {psi.h * sc, psi.l * sc};    // exact scaling by a power of two
+  const ff z = ff_mul(p, p);
+  ff c = C.ccos[NTAY - 1], s = C.csin[NTAY - 1];
+#pragma unroll
+  for (int k = NTAY - 2; k >= 0; --k) {
+    c = ff_add(C.ccos[k], ff_mul(z, c));
+    s = ff_add(C.csin[k], ff_mul(z, s));
+  }
+  s = ff_mul(p, s);
+  for (int i = 0; i < m; ++i) {
+    const ff cs = ff_mul(c, s);
+    c = ff_sub(ff_mul(c, c), ff_mul(s, s));
+    s = {2.f * cs.h, 2.f * cs.l};
+  }
+  return {c, s};
+}
+
+// 2 pi split into two doubles (2 pi = TWO_PI_HI + TWO_PI_LO to ~1e-32)
+constexpr double TWO_PI_HI = 6.283185307179586;
+constexpr double TWO_PI_LO = 2.4492935982947064e-16;
+
+// Fills the Taylor coefficients and 1/(4 pi) of C (every other field untouched).
+__device__ inline void ff_const_series(FfConst& C) {
+  double f = 1.0;   // (2k)! and (2k+1)!, exact in FP64 up to 17!
+  for (int k = 0; k < NTAY; ++k) {
+    const double f2k = f;
+    const double f2k1 = f * (2 * k + 1);
+    const double sgn = (k & 1) ? -1.0 : 1.0;
+    C.ccos[k] = ff_from_d(sgn / f2k);
+    C.csin[k] = ff_from_d(sgn / f2k1);
+    f = f2k1 * (2 * k + 2);
+  }
+  C.inv4pi = ff_from_d(0.25 / PI);
+}
+
 // Gauss-Legendre node i (ascending) and weight of order q on [0, 1]
 // (Newton's method on P_q).
 __host__ __device__ void gl_node(int q, int i, double* t, double* w);
@@ -110,6 +153,10 @@ struct DeviceMesh {
   int q9_ne = 0;
   Q9Elem* q9 = nullptr;
   double* q9_far = nullptr;
+  // the far rule again in float-float pairs relative to the element centre
+  // (u = y - c, n_y, w|J|; q9_farff[(p 7 + f) n + e]) for the float-float
+  // far class of constant-pressure elements
+  float2* q9_farff = nullptr;
   double* q9_near = nullptr;
   Q9Rules q9r;
 };

@@ -72,12 +72,120 @@ __global__ void k_q9_points(const Q9Elem* __restrict__ q9, int n, Q9Rules R, dou
   }
 }
 
+// Far rule in float-float about each element's centre (the constant-pressure
+// far class below): u = y - c, n_y, w|J| as (hi, lo) pairs, point-major and
+// field-major like the FP64 table; thread 0 also fills the series constants.
+__global__ void k_q9_far_ff(const double* __restrict__ far_tab, const Elem* __restrict__ el, int n,
+                            float2* __restrict__ farff, FfConst* __restrict__ fc) {
+  const size_t sn = (size_t)n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (size_t)Q9_FAR * sn;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(idx / sn), e = (int)(idx - (size_t)p * sn);
+    const double* q = far_tab + (size_t)p * 7 * sn + e;
+    for (int f = 0; f < 7; ++f) {
+      const double v = f < 3 ? q[f * sn] - el[e].c[f] : q[f * sn];
+      const ff w = ff_from_d(v);
+      farff[((size_t)p * 7 + f) * sn + e] = make_float2(w.h, w.l);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    FfConst C{};
+    ff_const_series(C);
+    *fc = C;
+  }
+}
+
+// D, H (S, K) of a far constant-pressure element j in float-float (the
+// triangles' far class, here with the curved element's per-point normal):
+// FP64 keeps e = x - (c + shift), |e| and the reference phase k|e| mod 2 pi;
+// per point u = y - c, Delta = |u|^2 - 2 e.u, r = sqrt(|e|^2 + Delta),
+// delta = Delta / (|e| + r), e^{ikr} = e^{ik|e|} e^{ik delta}.
+template <bool SK>
+__device__ void q9_far_ff(const float2* __restrict__ tab, size_t sn, int j, const double dc[3], double dist,
+                          const double nx[3], double k, double hmax, const FfConst& C, cd& D, cd& H, cd& S,
+                          cd& K) {
+  const ff ef[3] = {ff_from_d(dc[0]), ff_from_d(dc[1]), ff_from_d(dc[2])};
+  const ff nxf[3] = {ff_from_d(nx[0]), ff_from_d(nx[1]), ff_from_d(nx[2])};
+  const ff kf = ff_from_d(k);
+  const ff rho2 = ff_dot3(ef, ef);
+  const ff rho = ff_sqrt(rho2);
+  const ff enx = ff_dot3(ef, nxf);
+  double th = k * dist;
+  const double qn = rint(th * (1.0 / TWO_PI_HI));
+  th = fma(-qn, TWO_PI_HI, th);
+  th = fma(-qn, TWO_PI_LO, th);
+  const ffc Eref = expi_ff(ff_from_d(th), 3, C);
+  // |k delta| <= k |u| <= 1.5 k hmax on the curved element
+  int m = 2;
+  const float kh = (float)(1.5 * k * hmax);
+  while (kh > 0.75f * (float)(1 << m) && m < 12) ++m;
+  ff Dre = ff_make(0.f), Dim = ff_make(0.f), Hre = ff_make(0.f), Him = ff_make(0.f);
+  ff Sre = ff_make(0.f), Sim = ff_make(0.f), Kre = ff_make(0.f), Kim = ff_make(0.f);
+#pragma unroll 1
+  for (int p = 0; p < Q9_FAR; ++p) {
+    const float2* q = tab + (size_t)p * 7 * sn + j;
+    ff u[3], ny[3];
+    for (int d = 0; d < 3; ++d) {
+      const float2 a = q[d * sn], b = q[(3 + d) * sn];
+      u[d] = ff{a.x, a.y};
+      ny[d] = ff{b.x, b.y};
+    }
+    const float2 wq = q[6 * sn];
+    const ff w = ff{wq.x, wq.y};
+    const ff eu = ff_dot3(ef, u);
+    const ff Delta = ff_sub(ff_dot3(u, u), ff{2.f * eu.h, 2.f * eu.l});
+    const ff r = ff_sqrt(ff_add(rho2, Delta));
+    const ff delta = ff_div(Delta, ff_add(rho, r));
+    const ffc E = ffc_mul(Eref, expi_ff(ff_mul(kf, delta), m, C));
+    const ff ir = ff_rcp(r);
+    const ff ir2 = ff_mul(ir, ir);
+    const ff ir3 = ff_mul(ir2, ir);
+    const ff ir5 = ff_mul(ir3, ir2);
+    const ff kr = ff_mul(kf, r);
+    // x - y = e - u
+    const ff dny = ff_sub(ff_dot3(ef, ny), ff_dot3(u, ny));
+    const ff dnx = ff_sub(enx, ff_dot3(u, nxf));
+    const ff nn = ff_dot3(nxf, ny);
+    const ff are = ff_add(E.re, ff_mul(E.im, kr));
+    const ff aim = ff_sub(E.im, ff_mul(E.re, kr));
+    const ff t3 = ff_sub(ff_make(3.f), ff_mul(kr, kr));
+    const ff kr3 = ff_mul_f(kr, 3.f);
+    const ff bre = ff_add(ff_mul(E.re, t3), ff_mul(E.im, kr3));
+    const ff bim = ff_sub(ff_mul(E.im, t3), ff_mul(E.re, kr3));
+    const ff wi = ff_mul(w, C.inv4pi);
+    const ff wir3 = ff_mul(wi, ir3);
+    const ff f = ff_mul(wir3, dny);
+    const ff g1 = ff_mul(wir3, nn);
+    const ff g2 = ff_mul(ff_mul(ff_mul(wi, ir5), dnx), dny);
+    Dre = ff_add(Dre, ff_mul(are, f));
+    Dim = ff_add(Dim, ff_mul(aim, f));
+    Hre = ff_add(Hre, ff_sub(ff_mul(are, g1), ff_mul(bre, g2)));
+    Him = ff_add(Him, ff_sub(ff_mul(aim, g1), ff_mul(bim, g2)));
+    if (SK) {
+      const ff gs = ff_mul(wi, ir);
+      Sre = ff_add(Sre, ff_mul(E.re, gs));
+      Sim = ff_add(Sim, ff_mul(E.im, gs));
+      const ff gk = ff_mul(wir3, dnx);
+      Kre = ff_sub(Kre, ff_mul(are, gk));
+      Kim = ff_sub(Kim, ff_mul(aim, gk));
+    }
+  }
+  D = mkc(ff_to_d(Dre), ff_to_d(Dim));
+  H = mkc(ff_to_d(Hre), ff_to_d(Him));
+  if (SK) {
+    S = mkc(ff_to_d(Sre), ff_to_d(Sim));
+    K = mkc(ff_to_d(Kre), ff_to_d(Kim));
+  }
+}
+
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
 // out + dest[o] n n.  The diagonal of the zero offset is left to k_q9_self.
 // Far entries are summed here; near and very-near entries are listed for
 // k_q9_near_entries, or summed here when the list is full.
 template <bool SK>
 __global__ void __launch_bounds__(128) k_q9_blocks(const Elem* __restrict__ el, const double* __restrict__ far_tab,
+                                                   const float2* __restrict__ far_ff,
+                                                   const FfConst* __restrict__ fc,
                                                    const double* __restrict__ near_tab, int n,
                                                    const double* __restrict__ shifts,
                                                    const int64_t* __restrict__ dest, int n_off, int zero_off,
@@ -105,12 +213,16 @@ __global__ void __launch_bounds__(128) k_q9_blocks(const Elem* __restrict__ el, 
     const double dist = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
     cd D = mkc(0.0, 0.0), H = mkc(0.0, 0.0), S = mkc(0.0, 0.0), K = mkc(0.0, 0.0);
     if (dist >= FAR_RATIO * Ej.hmax) {
+      if (far_ff) {
+        q9_far_ff<SK>(far_ff, sn, j, dc, dist, nx, k, Ej.hmax, *fc, D, H, S, K);
+      } else {
 #pragma unroll 1
-      for (int p = 0; p < Q9_FAR; ++p) {
-        const double* q = far_tab + (size_t)p * 7 * sn + j;
-        const double dv[3] = {x[0] - (q[0] + sh[0]), x[1] - (q[sn] + sh[1]), x[2] - (q[2 * sn] + sh[2])};
-        const double ny[3] = {q[3 * sn], q[4 * sn], q[5 * sn]};
-        q9_kernels<SK>(dv, nx, ny, q[6 * sn], k, D, H, S, K);
+        for (int p = 0; p < Q9_FAR; ++p) {
+          const double* q = far_tab + (size_t)p * 7 * sn + j;
+          const double dv[3] = {x[0] - (q[0] + sh[0]), x[1] - (q[sn] + sh[1]), x[2] - (q[2 * sn] + sh[2])};
+          const double ny[3] = {q[3 * sn], q[4 * sn], q[5 * sn]};
+          q9_kernels<SK>(dv, nx, ny, q[6 * sn], k, D, H, S, K);
+        }
       }
     } else {
       if (near_list) {
@@ -310,12 +422,15 @@ fmpb_status upload_mesh_q9(const double* nodes, int64_t nn, const int32_t* elems
   if (e == cudaSuccess) e = cudaMalloc(&m.q9, sizeof(Q9Elem) * n);
   if (e == cudaSuccess) e = cudaMalloc(&m.q9_far, sizeof(double) * Q9_FAR * 7 * n);
   if (e == cudaSuccess) e = cudaMalloc(&m.q9_near, sizeof(double) * Q9_NEAR_TAB * 8 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&m.q9_farff, sizeof(float2) * Q9_FAR * 7 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&m.fc_dev, sizeof(FfConst));
   if (e == cudaSuccess) e = cudaMemcpyAsync(dnodes, nodes, sizeof(double) * 3 * nn, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(delems, elems, sizeof(int32_t) * 9 * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     FMPB_LAUNCH("q9_prepare", st, k_q9_prepare<<<grid_for(n, 128), 128, 0, st>>>(dnodes, delems, (int)n, R, m.q9, m.el));
     const size_t pts = (size_t)n * (Q9_FAR + Q9_NEAR_TAB);
     FMPB_LAUNCH("q9_points", st, k_q9_points<<<(unsigned)std::min<size_t>(grid_for(pts, 256), 152 * 32), 256, 0, st>>>(m.q9, (int)n, R, m.q9_far, m.q9_near));
+    FMPB_LAUNCH("q9_far_ff", st, k_q9_far_ff<<<(unsigned)std::min<size_t>(grid_for((size_t)n * Q9_FAR, 256), 152 * 32), 256, 0, st>>>(m.q9_far, m.el, (int)n, m.q9_farff, m.fc_dev));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -357,12 +472,12 @@ fmpb_status build_blocks_q9(const DeviceMesh& m, const CellGrid& g, double k, cd
     const unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
     const unsigned self_blocks = grid_for((size_t)m.n * 32, 256);
     if (beta.x == 0.0 && beta.y == 0.0) {
-      FMPB_LAUNCH("q9_blocks", st, k_q9_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_near, m.n, dshift, ddest, n_off, zero_off, out, k, beta, bw, near_list, near_count, near_cap));
+      FMPB_LAUNCH("q9_blocks", st, k_q9_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_farff, m.fc_dev, m.q9_near, m.n, dshift, ddest, n_off, zero_off, out, k, beta, bw, near_list, near_count, near_cap));
       FMPB_LAUNCH("q9_near", st, k_q9_near_entries<false><<<152 * 16, 256, 0, st>>>(m.el, m.q9_near, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw));
       if (zero_off >= 0)
         FMPB_LAUNCH("q9_self", st, k_q9_self<false><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n, k, beta, m.q9r, nullptr));
     } else {
-      FMPB_LAUNCH("q9_blocks_adm", st, k_q9_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_near, m.n, dshift, ddest, n_off, zero_off, out, k, beta, bw, near_list, near_count, near_cap));
+      FMPB_LAUNCH("q9_blocks_adm", st, k_q9_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.q9_far, m.q9_farff, m.fc_dev, m.q9_near, m.n, dshift, ddest, n_off, zero_off, out, k, beta, bw, near_list, near_count, near_cap));
       FMPB_LAUNCH("q9_near_adm", st, k_q9_near_entries<true><<<152 * 16, 256, 0, st>>>(m.el, m.q9_near, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw));
       if (zero_off >= 0)
         FMPB_LAUNCH("q9_self_adm", st, k_q9_self<true><<<self_blocks, 256, 0, st>>>(m.q9, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n, k, beta, m.q9r, nullptr));

@@ -255,47 +255,10 @@ __global__ void k_prepare_ff(const Elem* __restrict__ el, int n, FfElem* __restr
       C.t[i] = ff_from_d(qr->t3[i]);
       for (int j = 0; j < Q_FAR; ++j) C.W[i * Q_FAR + j] = ff_from_d(qr->t3[i] * qr->w3[i] * qr->w3[j]);
     }
-    double f = 1.0;   // (2k)! and (2k+1)!, exact in FP64 up to 17!
-    for (int k = 0; k < NTAY; ++k) {
-      const double f2k = f;                     // (2k)!
-      const double f2k1 = f * (2 * k + 1);      // (2k+1)!
-      const double sgn = (k & 1) ? -1.0 : 1.0;
-      C.ccos[k] = ff_from_d(sgn / f2k);
-      C.csin[k] = ff_from_d(sgn / f2k1);
-      f = f2k1 * (2 * k + 2);
-    }
-    C.inv4pi = ff_from_d(0.25 / PI);
+    ff_const_series(C);
     *fc = C;
   }
 }
-
-__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
-  return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
-}
-
-// e^{i psi} for |psi| <= 0.75 * 2^m
-__device__ __forceinline__ ffc expi_ff(ff psi, int m, const FfConst& C) {
-  const float sc = ldexpf(1.f, -m);
-  const ff p = {psi.h * sc, psi.l * sc};    // exact scaling by a power of two
-  const ff z = ff_mul(p, p);
-  ff c = C.ccos[NTAY - 1], s = C.csin[NTAY - 1];
-#pragma unroll
-  for (int k = NTAY - 2; k >= 0; --k) {
-    c = ff_add(C.ccos[k], ff_mul(z, c));
-    s = ff_add(C.csin[k], ff_mul(z, s));
-  }
-  s = ff_mul(p, s);
-  for (int i = 0; i < m; ++i) {
-    const ff cs = ff_mul(c, s);
-    c = ff_sub(ff_mul(c, c), ff_mul(s, s));
-    s = {2.f * cs.h, 2.f * cs.l};
-  }
-  return {c, s};
-}
-
-// 2 pi split into two doubles (2 pi = TWO_PI_HI + TWO_PI_LO to ~1e-32)
-constexpr double TWO_PI_HI = 6.283185307179586;
-constexpr double TWO_PI_LO = 2.4492935982947064e-16;
 
 // D, H (and with SK also S, K) of a far element.  ef = x - (c + shift) in
 // float-float (formed on the FP32 pipe from float-float centroids and shift;
@@ -944,6 +907,7 @@ void free_mesh(DeviceMesh& m) {
   if (m.fc_dev) cudaFree(m.fc_dev);
   if (m.q9) cudaFree(m.q9);
   if (m.q9_far) cudaFree(m.q9_far);
+  if (m.q9_farff) cudaFree(m.q9_farff);
   if (m.q9_near) cudaFree(m.q9_near);
   m.el = nullptr;
   m.qr_dev = nullptr;
@@ -951,6 +915,7 @@ void free_mesh(DeviceMesh& m) {
   m.fc_dev = nullptr;
   m.q9 = nullptr;
   m.q9_far = nullptr;
+  m.q9_farff = nullptr;
   m.q9_near = nullptr;
 }
 
