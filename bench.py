@@ -499,7 +499,7 @@ def batching_section(gb, torch, stream, freq_index=3, n_t=12):
     return out
 
 
-def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=20):
+def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=30, maxit=600):
     """The whole batching workload: 8 frequencies x 64 directions (512
     systems) with BF16 tensor-core operators, solved as 8 GMRES runs one
     after the other and as one fmpb_solve_batch (one product sequence per
@@ -515,13 +515,13 @@ def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=20):
     bs = torch.stack([op.rhs_plane_wave(w.directions) for op in ops])
     R = bs.shape[1]
     res = {"systems": len(ops) * R, "frequencies_hz": [round(k * SPEED_OF_SOUND / (2 * math.pi), 1) for k in ks],
-           "tol": tol, "restart": restart, "builds_s": build_s}
+           "tol": tol, "restart": restart, "maxit": maxit, "builds_s": build_s}
     # one after the other
     s0, s1 = ev(), ev()
     s0.record(stream)
     seq, seq_info = [], []
     for o, op in enumerate(ops):
-        p, info = op.solve(bs[o], tol=tol, restart=restart, maxit=3000, raise_on_noconv=False)
+        p, info = op.solve(bs[o], tol=tol, restart=restart, maxit=maxit, raise_on_noconv=False)
         seq.append(p)
         seq_info.append(info)
     s1.record(stream)
@@ -530,16 +530,17 @@ def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=20):
     # one batched solve
     b0, b1 = ev(), ev()
     b0.record(stream)
-    pb, binfo = gb.solve_batch(ops, bs, tol=tol, restart=restart, maxit=3000, raise_on_noconv=False)
+    pb, binfo = gb.solve_batch(ops, bs, tol=tol, restart=restart, maxit=maxit, raise_on_noconv=False)
     b1.record(stream)
     torch.cuda.synchronize()
     bat_ms = b0.elapsed_time(b1)
     res["sequential"] = {"ms": seq_ms, "solves_per_s": len(ops) * R * 1e3 / seq_ms,
-                         "iters_max_per_frequency": [max(i["iters"] for i in inf) for inf in seq_info]}
+                         "iters_max_per_frequency": [max(i["iters"] for i in inf) for inf in seq_info],
+                         "converged": sum(i["converged"] for inf in seq_info for i in inf)}
     res["batched"] = {"ms": bat_ms, "solves_per_s": len(ops) * R * 1e3 / bat_ms,
                       "iters_max_per_frequency": [max(i["iters"] for i in inf) for inf in binfo],
                       "relres_true_max_per_frequency": [max(i["relres_true"] for i in inf) for inf in binfo],
-                      "all_converged": all(i["converged"] for inf in binfo for i in inf)}
+                      "converged": sum(i["converged"] for inf in binfo for i in inf)}
     res["batched_vs_sequential_rel_diff_per_frequency"] = [
         float(torch.linalg.vector_norm(pb[o] - seq[o]) / torch.linalg.vector_norm(seq[o])) for o in range(len(ops))]
     res["speedup_batched_vs_sequential"] = seq_ms / bat_ms
@@ -595,15 +596,16 @@ def run_serving(gb, reqs, precision, snap_hz=None, tol=TOL):
 
 
 def serving_section(gb, n_sample=24):
-    """The serving runtime on the first n_sample requests of the seeded stream
-    (Poisson arrivals at 50 req/s, sphere or capped-cylinder cells on grids
-    4x4..64x8, 100-2000 Hz, 1-16 plane waves) at their arrival times, plain
-    FP64 operators.  The full comparison (hundreds of requests, plain FP64
-    beside MIXED, and the 10 Hz-snapped cache variant) is `--serving N`."""
+    """The serving runtime on the first n_sample sphere-cell requests of the
+    seeded stream (Poisson arrivals at 50 req/s, grids 4x4..64x8, 100-2000 Hz,
+    1-16 plane waves) at their arrival times, plain FP64 operators: a bounded
+    sample for the default run.  The study with both cells (the capped
+    cylinders take the PBEM form with spectra up to 44 GB), plain FP64 beside
+    MIXED and the 10 Hz-snapped cache variant is `--serving N`."""
     from workloads import serving_stream
-    reqs = serving_stream(max(n_sample, 2))[:n_sample]
+    reqs = [r for r in serving_stream(400) if r["cell"] == "sphere"][:n_sample]
     out = run_serving(gb, reqs, gb.FP64)
-    out["sample"] = f"first {n_sample} requests of the seeded 50 req/s stream, both cells, FP64"
+    out["sample"] = f"first {n_sample} sphere-cell requests of the seeded 50 req/s stream, FP64"
     return out
 
 

@@ -962,8 +962,11 @@ static bool tc_batchable(const fmpb_operator* const* ops, int n_ops, bool low) {
 // o's R N values after those of o - 1): each step of the FMM product (near
 // field, P2M, DFT passes, per-frequency M2L products, L2P) is one launch over
 // all operators.  Tensor-core waits report to the first operator's flag.
+// active (host, n_ops R entries, may be null): systems still iterating; an
+// operator none of whose systems iterates is left out of the tensor-core
+// products (its outputs are not read), the DFT passes still run over all.
 static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, int R, const cd* x, cd* y,
-                                   cudaStream_t st, BatchScratch& sc) {
+                                   cudaStream_t st, BatchScratch& sc, const int* active = nullptr) {
   const fmpb_operator* a = ops[0];
   const int Rt = n_ops * R;
   const int64_t Nc = a->shape.ncells, n = a->mesh.n, B = a->B, F = a->shape.F;
@@ -980,22 +983,30 @@ static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, i
   __nv_bfloat16* fb = lb + lb_elems;
   const __nv_bfloat16 *Sb[TC_MAX_BATCH], *V0b[TC_MAX_BATCH], *U0b[TC_MAX_BATCH];
   const void* sp[TC_MAX_BATCH];
+  int blk[TC_MAX_BATCH];
+  int na = 0;
   for (int q = 0; q < n_ops; ++q) {
-    Sb[q] = ops[q]->Sb;
-    V0b[q] = ops[q]->V0b;
-    U0b[q] = ops[q]->U0b;
-    sp[q] = ops[q]->specb;
+    bool on = !active;
+    for (int r = 0; active && r < R && !on; ++r) on = active[q * R + r] != 0;
+    if (!on) continue;
+    Sb[na] = ops[q]->Sb;
+    V0b[na] = ops[q]->V0b;
+    U0b[na] = ops[q]->U0b;
+    sp[na] = ops[q]->specb;
+    blk[na] = q;
+    ++na;
   }
+  if (na == 0) return FMPB_OK;
   TcOffsets zero{};
   zero.n = 1;
   unsigned* err = a->tc_err;
   FMPB_TRY(tc_rows_to_bf16(x, (int64_t)Rt * Nc, n, xb, st));
-  FMPB_TRY(tc_offset_gemm_batch(Sb, n_ops, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st));
-  FMPB_TRY(tc_offset_gemm_batch(V0b, n_ops, zero, B, n, a->shape.M, R, xb, Mom, false, err, st));
+  FMPB_TRY(tc_offset_gemm_batch(Sb, na, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st, blk));
+  FMPB_TRY(tc_offset_gemm_batch(V0b, na, zero, B, n, a->shape.M, R, xb, Mom, false, err, st, blk));
   FMPB_TRY(circulant_apply(a->shape, B, nullptr, Rt, Mom, Loc, false, sc.p, st, SPEC_BF16, fb, err, false,
-                           circulant_f32_ok(a->shape), sp, n_ops));
+                           circulant_f32_ok(a->shape), sp, na, blk, n_ops));
   FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)Rt * Nc, B, lb, st));
-  FMPB_TRY(tc_offset_gemm_batch(U0b, n_ops, zero, n, B, a->shape.M, R, lb, y, true, err, st));
+  FMPB_TRY(tc_offset_gemm_batch(U0b, na, zero, n, B, a->shape.M, R, lb, y, true, err, st, blk));
   return FMPB_OK;
 }
 
@@ -1025,8 +1036,18 @@ fmpb_status fmpb_solve_batch(const fmpb_operator* const* ops, int n_ops, int R, 
     return FMPB_OK;
   };
   const bool fused = tc_batchable(ops, n_ops, false), fused_low = tc_batchable(ops, n_ops, true);
+  // systems still iterating (published by the GMRES driver at every poll of
+  // its convergence flags): operators whose systems have all stopped are
+  // left out of the products
+  std::vector<int> act((size_t)n_ops * R, 1);
   MatvecFn A = [&](int, const cd* x, cd* y, cudaStream_t s) -> fmpb_status {
-    return fused ? batch_matvec_tc(ops, n_ops, R, x, y, s, sc) : loop(false, x, y, s);
+    if (fused) return batch_matvec_tc(ops, n_ops, R, x, y, s, sc, act.data());
+    for (int q = 0; q < n_ops; ++q) {
+      bool on = false;
+      for (int r = 0; r < R && !on; ++r) on = act[(size_t)q * R + r] != 0;
+      if (on) FMPB_TRY(const_cast<fmpb_operator*>(ops[q])->matvec(R, x + q * RN, y + q * RN, s, false));
+    }
+    return FMPB_OK;
   };
   fmpb_status s;
   if (mixed) {
@@ -1036,10 +1057,14 @@ fmpb_status fmpb_solve_batch(const fmpb_operator* const* ops, int n_ops, int R, 
     s = gmres_refined(A, Alow, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st);
   } else {
     const MatvecFfFn Aff = [&](int, const float4* x, float4* y, cudaStream_t s2) -> fmpb_status {
-      for (int q = 0; q < n_ops; ++q) FMPB_TRY(const_cast<fmpb_operator*>(ops[q])->matvec_ff(R, x + q * RN, y + q * RN, s2));
+      for (int q = 0; q < n_ops; ++q) {
+        bool on = false;
+        for (int r = 0; r < R && !on; ++r) on = act[(size_t)q * R + r] != 0;
+        if (on) FMPB_TRY(const_cast<fmpb_operator*>(ops[q])->matvec_ff(R, x + q * RN, y + q * RN, s2));
+      }
       return FMPB_OK;
     };
-    s = gmres_solve(A, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st, ff ? &Aff : nullptr);
+    s = gmres_solve(A, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st, ff ? &Aff : nullptr, act.data());
   }
   if (s != FMPB_OK && s != FMPB_ENOCONV) return s;
   for (int q = 0; q < n_ops; ++q) {

@@ -592,9 +592,11 @@ static fmpb_status launch_block_product_tiled(const void* spec, const XT* X, XT*
 // f32_io, complex FP32 (float2; FP32 and BF16 spectra only).
 static fmpb_status block_product(const void* spec, int spec_format, const void* Xv, void* Yv, int64_t F,
                                  int64_t B, int R, cudaStream_t st, void* tc_rows, unsigned* tc_err,
-                                 bool f32_io = false, const void* const* spec_batch = nullptr, int n_ops = 1) {
-  if (n_ops > 1) {
-    if (spec_format != SPEC_BF16 || !spec_batch || R % n_ops || !tc_rows || !tc_err) {
+                                 bool f32_io = false, const void* const* spec_batch = nullptr, int n_ops = 1,
+                                 const int* batch_blk = nullptr, int n_blocks = 0) {
+  if (spec_batch) {
+    const int nb = n_blocks > 0 ? n_blocks : n_ops;
+    if (spec_format != SPEC_BF16 || n_ops < 1 || nb < n_ops || R % nb || !tc_rows || !tc_err) {
       set_error("block_product: a batch of operators takes BF16 spectra and R a multiple of the operator count");
       return FMPB_EINVAL;
     }
@@ -609,7 +611,7 @@ static fmpb_status block_product(const void* spec, int spec_format, const void* 
       FMPB_TRY(tc_rows_from_f32(reinterpret_cast<const float2*>(Xv), F * R, B, rows, st));
     else
       FMPB_TRY(tc_rows_from_ff(reinterpret_cast<const float4*>(Xv), F * R, B, rows, st));
-    return tc_freq_gemm_batch(A, n_ops, F, B, R / n_ops, rows, Yv, tc_err, st, f32_io);
+    return tc_freq_gemm_batch(A, n_ops, F, B, R / nb, rows, Yv, tc_err, st, f32_io, batch_blk, nb);
   }
   if (F > 65535) {
     set_error("block_product: %lld frequencies exceed the launch limit", (long long)F);
@@ -683,7 +685,7 @@ size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format, void* tc_rows,
                             unsigned* tc_err, bool ff_io, bool f32_passes, const void* const* spec_batch,
-                            int n_ops) {
+                            int n_ops, const int* batch_blk, int n_blocks) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
@@ -720,7 +722,7 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   }
   // per-frequency block products: [f][r][b] -> [f][r][b]
   FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st, tc_rows, tc_err, !ffa,
-                         spec_batch, n_ops));
+                         spec_batch, n_ops, batch_blk, n_blocks));
   cur = 1 - cur;
   // inverse z: [fz][fy fx][rb] -> [cz][fy fx][rb], cz < Mz
   if (Pz > 1) {

@@ -744,7 +744,7 @@ struct DevBuf {
 }  // namespace
 
 fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
-                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff) {
+                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff, int* active_host) {
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int m = o.restart > 0 ? o.restart : 30;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
@@ -853,11 +853,16 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
 
   std::vector<double> hres(R), hbn(R), hest(R);
   std::vector<int> hact(R), iters(R, 0);
+  auto publish = [&](bool all) {
+    if (active_host)
+      for (int r = 0; r < R; ++r) active_host[r] = all ? 1 : hact[r];
+  };
   int total_it = 0;
   bool timed_out = false;
   bool first = true;
   while (true) {
     // r0 = b - A x  (x = 0 on the first cycle)
+    publish(true);
     if (first) {
       FMPB_CUDA(cudaMemcpyAsync(W, b, sizeof(cd) * vstride, cudaMemcpyDeviceToDevice, st));
     } else {
@@ -871,6 +876,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     FMPB_CUDA(cudaGetLastError());
     FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
     FMPB_CUDA(cudaStreamSynchronize(st));
+    publish(false);
     bool any = false;
     for (int r = 0; r < R; ++r) any |= hact[r] != 0;
     if (!any) break;
@@ -904,6 +910,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
         FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         FMPB_CUDA(cudaStreamSynchronize(st));
+        publish(false);
         any = false;
         double cur = 0.0;
         for (int r = 0; r < R; ++r)
@@ -965,6 +972,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
         FMPB_CUDA(cudaMemcpyAsync(hest.data(), s.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         FMPB_CUDA(cudaStreamSynchronize(st));
+        publish(false);
         any = false;
         double cur = 0.0;
         for (int r = 0; r < R; ++r)
@@ -990,6 +998,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     if (!any || timed_out || total_it >= maxit) break;
   }
   // true residual with one more product
+  publish(true);
   FMPB_TRY(A(R, x, W, st));
   FMPB_LAUNCH("residual", st, k_residual<<<vec_blocks, 256, 0, st>>>(b, W, vstride));
   FMPB_TRY(norms(W, s.beta, nullptr));

@@ -12,8 +12,13 @@ typedef std::function<fmpb_status(int R, const cd* x, cd* y, cudaStream_t st)> M
 // operator has one; it saves the conversions around every Arnoldi product.
 typedef std::function<fmpb_status(int R, const float4* x, float4* y, cudaStream_t st)> MatvecFfFn;
 
+// active_host (host, R entries, may be null): kept equal to the systems
+// still iterating as of the last poll of the convergence flags (all 1 around
+// the restart and true-residual products), so that a caller's product may
+// skip systems that have stopped.
 fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
-                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff = nullptr);
+                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff = nullptr,
+                        int* active_host = nullptr);
 // GMRES-IR: accurate residuals with A, corrections by GMRES with Alow.
 fmpb_status gmres_refined(const MatvecFn& A, const MatvecFn& Alow, int R, int64_t N, const cd* b, cd* x,
                           const fmpb_solve_opts& o, fmpb_solve_info* info, cudaStream_t st);

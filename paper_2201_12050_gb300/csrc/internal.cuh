@@ -300,10 +300,14 @@ enum SpecFormat { SPEC_CD = 0, SPEC_FF = 1, SPEC_F32 = 2, SPEC_BF16 = 3 };
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD,
                             void* tc_rows = nullptr, unsigned* tc_err = nullptr, bool ff_io = false,
-                            bool f32_passes = false, const void* const* spec_batch = nullptr, int n_ops = 1);
-// spec_batch, n_ops > 1: the products of n_ops operators of one shape in one
-// pass sequence (BF16 spectra only): R counts the right-hand sides of all
-// operators, R / n_ops per operator, operator o's after those of o - 1.
+                            bool f32_passes = false, const void* const* spec_batch = nullptr, int n_ops = 1,
+                            const int* batch_blk = nullptr, int n_blocks = 0);
+// spec_batch: the products of several operators of one shape in one pass
+// sequence (BF16 spectra only).  R counts the right-hand sides of n_blocks
+// operator blocks (R / n_blocks each, block b's after those of b - 1); the
+// per-frequency products run for the n_ops operators listed, operator q's
+// spectrum spec_batch[q] acting on block batch_blk[q] (null: q; n_blocks 0:
+// n_ops).  The DFT passes run over all blocks.
 // ff_io: x and y are float-float vectors (float4 per value, passed as cd*;
 // same 16 bytes) instead of complex double; accumulate must be false.
 // f32_passes: the DFT passes and the frequency-domain values in complex FP32

@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int64_t n0 = (ctile - (int64_t)bop * batch.tiles) * BN;
   const int64_t f = FREQ ? (int64_t)blockIdx.y : 0;
   const int Nc = Mx * My * Mz;
-  const int64_t ctot = ncols * batch.n;          // columns of all operators
-  const int64_t obase = (int64_t)bop * ncols;    // this operator's first column
+  const int64_t ctot = ncols * batch.nblk;                // columns of all operator blocks
+  const int64_t obase = (int64_t)batch.blk[bop] * ncols;  // this operator's first column
   const __nv_bfloat16* __restrict__ A = batch.A[bop];
 
   if (tid == 0) {
@@ -515,7 +515,7 @@ fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, i
   cd* out = y;
   cd* scratch = nullptr;
   if (accumulate) {
-    FMPB_CUDA(cudaMalloc(&scratch, sizeof(cd) * (size_t)ncols * A.n * m));
+    FMPB_CUDA(cudaMalloc(&scratch, sizeof(cd) * (size_t)ncols * A.nblk * m));
     out = scratch;
   }
   TuneEntry e{};
@@ -617,14 +617,19 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
 
 fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, const TcOffsets& offs, int64_t m,
                                  int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
-                                 unsigned* err, cudaStream_t st) {
+                                 unsigned* err, cudaStream_t st, const int* blk) {
   if (n_ops < 1 || n_ops > TC_MAX_BATCH) {
     set_error("tc_offset_gemm: %d operators in a batch (1..%d)", n_ops, TC_MAX_BATCH);
     return FMPB_EINVAL;
   }
   TcBatch A{};
   A.n = n_ops;
-  for (int o = 0; o < n_ops; ++o) A.A[o] = Aops[o];
+  A.nblk = 0;
+  for (int o = 0; o < n_ops; ++o) {
+    A.A[o] = Aops[o];
+    A.blk[o] = blk ? blk[o] : o;
+    A.nblk = std::max(A.nblk, A.blk[o] + 1);
+  }
   const int64_t Mp = tc_rows(m), Kp = tc_depth(k);
   const int64_t Nc = (int64_t)M[0] * M[1] * M[2];
   const int64_t ncols = Nc * R;
@@ -696,14 +701,23 @@ fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, co
 }
 
 fmpb_status tc_freq_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, int64_t F, int64_t B, int R,
-                               const __nv_bfloat16* X, void* Y, unsigned* err, cudaStream_t st, bool y_f32) {
+                               const __nv_bfloat16* X, void* Y, unsigned* err, cudaStream_t st, bool y_f32,
+                               const int* blk, int n_blocks) {
   if (n_ops < 1 || n_ops > TC_MAX_BATCH) {
     set_error("tc_freq_gemm: %d operators in a batch (1..%d)", n_ops, TC_MAX_BATCH);
     return FMPB_EINVAL;
   }
   TcBatch A{};
   A.n = n_ops;
-  for (int o = 0; o < n_ops; ++o) A.A[o] = Aops[o];
+  A.nblk = n_blocks > 0 ? n_blocks : n_ops;
+  for (int o = 0; o < n_ops; ++o) {
+    A.A[o] = Aops[o];
+    A.blk[o] = blk ? blk[o] : o;
+    if (A.blk[o] < 0 || A.blk[o] >= A.nblk) {
+      set_error("tc_freq_gemm: operator block %d outside 0..%d", A.blk[o], A.nblk - 1);
+      return FMPB_EINVAL;
+    }
+  }
   const int64_t Mp = tc_rows(B), Kp = tc_depth(B);
   if (F < 1 || F > 65535 || B < 1 || R < 1 || Mp / TC_BM > 65535 || Kp > (1 << 24)) {
     set_error("tc_freq_gemm: bad shape (F %lld, B %lld, R %d)", (long long)F, (long long)B, R);

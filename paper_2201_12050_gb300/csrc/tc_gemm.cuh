@@ -22,6 +22,8 @@ struct TcBatch {
   int n;
   int64_t tiles;   // column tiles per operator (set at launch)
   const __nv_bfloat16* A[TC_MAX_BATCH];
+  int blk[TC_MAX_BATCH];   // operator q's column block in X and y (q itself unless a subset runs)
+  int nblk;                // column blocks in X and y
 };
 
 // Shapes of the realified operands of a complex m x k block.
@@ -49,9 +51,11 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
                            const __nv_bfloat16* X, cd* y, bool accumulate, unsigned* err, cudaStream_t st);
 // The same for n_ops operators with tables A[o] of one shape in one launch:
 // X and y hold the R Nc columns of operator 0, then those of operator 1, ...
+// blk (may be null): the column block of each listed operator, for a subset
+// of the operators whose columns X and y hold (null: 0, 1, ..., n_ops - 1).
 fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* A, int n_ops, const TcOffsets& offs, int64_t m,
                                  int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
-                                 unsigned* err, cudaStream_t st);
+                                 unsigned* err, cudaStream_t st, const int* blk = nullptr);
 
 // Float-float sources (float4 per complex value: re_hi, re_lo, im_hi, im_lo),
 // rounded (hi + lo) -> FP32 -> BF16.
@@ -71,7 +75,8 @@ fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, co
 // f, X and Y hold the R rows of operator 0, then those of operator 1, ...
 // (F n_ops R rows in all).
 fmpb_status tc_freq_gemm_batch(const __nv_bfloat16* const* A, int n_ops, int64_t F, int64_t B, int R,
-                               const __nv_bfloat16* X, void* Y, unsigned* err, cudaStream_t st, bool y_f32 = false);
+                               const __nv_bfloat16* X, void* Y, unsigned* err, cudaStream_t st, bool y_f32 = false,
+                               const int* blk = nullptr, int n_blocks = 0);
 
 // JSON list of the tile variants the offset-GEMM autotuner chose so far.
 fmpb_status tc_tuning_summary(std::string& out);
