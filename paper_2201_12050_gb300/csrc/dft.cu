@@ -346,7 +346,13 @@ __global__ void __launch_bounds__(256) k_dft_direct(const DftArgs a) {
   using S = typename DIn<IN>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
   V* tw = reinterpret_cast<V*>(dsm);   // w^m, m < P
+  V* tf = tw + a.P;                    // w^{(f j) mod P} at f Pin + j: no index arithmetic in the sums
   for (int m = threadIdx.x; m < a.P; m += blockDim.x) tw[m] = twiddle<FF>(m, a.P, a.sign);
+  __syncthreads();
+  for (int e = threadIdx.x; e < a.Pout * a.Pin; e += blockDim.x) {
+    const int f = e / a.Pin, j = e - f * a.Pin;
+    tf[e] = tw[(f * j) % a.P];
+  }
   __syncthreads();
   const S* in = reinterpret_cast<const S*>(a.in);
   const V zero = dzero<FF>();
@@ -361,28 +367,22 @@ __global__ void __launch_bounds__(256) k_dft_direct(const DftArgs a) {
     const int64_t dst = o1 * a.b1 + o2 * a.b2 + i;
 #pragma unroll 1
     for (int f = 0; f < a.Pout; ++f) {
-      int idx = 0;
+      const V* tr = tf + f * a.Pin;
       V v;
       if constexpr (FF) {
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
 #pragma unroll
         for (int j = 0; j < MAXIN; ++j)
-          if (j < a.Pin) {
-            ff_cmac(tw[idx], x[j], rh, rl, ih, il);
-            idx += f;
-            if (idx >= a.P) idx -= a.P;
-          }
+          if (j < a.Pin) ff_cmac(tr[j], x[j], rh, rl, ih, il);
         v = ff_norm(rh, rl, ih, il);
       } else {
         float re = 0.f, im = 0.f;
 #pragma unroll
         for (int j = 0; j < MAXIN; ++j)
           if (j < a.Pin) {
-            const float2 t = tw[idx];
+            const float2 t = tr[j];
             re = fmaf(t.x, x[j].x, fmaf(-t.y, x[j].y, re));
             im = fmaf(t.x, x[j].y, fmaf(t.y, x[j].x, im));
-            idx += f;
-            if (idx >= a.P) idx -= a.P;
           }
         v = make_float2(re, im);
       }
@@ -416,7 +416,7 @@ fmpb_status launch_dft(const char* name, const DftArgs& a, size_t smem, int thre
 
 template <bool FF, int IN, int OUT>
 fmpb_status launch_direct(const char* name, const DftArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.P * (FF ? sizeof(float4) : sizeof(float2));
+  const size_t smem = (size_t)(a.P + a.Pout * a.Pin) * (FF ? sizeof(float4) : sizeof(float2));
   const int64_t items = (int64_t)a.O1 * a.O2 * a.I;
   int sms = 0, dev = 0;
   FMPB_CUDA(cudaGetDevice(&dev));
