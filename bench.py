@@ -499,12 +499,15 @@ def batching_section(gb, torch, stream, freq_index=3, n_t=12):
     return out
 
 
-def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-3, restart=30, maxit=600):
+def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-2, restart=30, maxit=300):
     """The whole batching workload: 8 frequencies x 64 directions (512
     systems) with BF16 tensor-core operators, solved as 8 GMRES runs one
     after the other and as one fmpb_solve_batch (one product sequence per
     iteration over the 8 operators: near field, P2M, DFT passes, M2L and
-    L2P each one launch)."""
+    L2P each one launch; operators whose systems have all converged drop out).
+    Tolerance 1e-2: BF16 products round their input vectors, which leaves the
+    true residual of these systems at 5e-3..3e-2, and tighter tolerances make
+    GMRES stagnate at that level for some frequencies."""
     ev = lambda: torch.cuda.Event(enable_timing=True)
     ks = list(w.wavenumbers)
     torch.cuda.synchronize()
@@ -610,20 +613,26 @@ def serving_section(gb, n_sample=24):
 
 
 def run_serving_study(args):
-    """`--serving N`: the first N requests of the seeded stream replayed three
-    times through the serving runtime: plain FP64 operators, MIXED operators
-    (FP32 / BF16 inner products, float-float outer residuals, same 1e-8
-    tolerance), and FP64 with frequencies snapped to a 10 Hz grid (the cache
-    variant).  Prints one JSON line."""
+    """`--serving N`: the first N sphere-cell requests of the seeded stream
+    replayed three times through the serving runtime at their arrival times:
+    plain FP64 operators, MIXED operators (BF16 tensor-core inner products,
+    float-float outer residuals, the same 1e-8 tolerance), and FP64 with
+    frequencies snapped to a 10 Hz grid (the cache variant); then the first
+    12 requests of both cells (the capped cylinders take the PBEM form with
+    spectra up to 44 GB) in FP64 and MIXED.  Prints one JSON line."""
     import torch
     import paper_2201_12050_gb300 as gb
     from workloads import serving_stream
     torch.cuda.set_device(0)
-    reqs = serving_stream(args.serving)
-    out = {"serving_study": f"first {args.serving} requests of the seeded 50 req/s stream (both cells)",
-           "fp64": run_serving(gb, reqs, gb.FP64)}
-    out["mixed"] = _guarded(run_serving, gb, reqs, gb.MIXED)
-    out["fp64_snapped_10hz"] = _guarded(run_serving, gb, reqs, gb.FP64, 10.0)
+    stream = serving_stream(max(4 * args.serving, 24))
+    spheres = [r for r in stream if r["cell"] == "sphere"][:args.serving]
+    out = {"serving_study": f"first {len(spheres)} sphere-cell requests of the seeded 50 req/s stream",
+           "fp64": run_serving(gb, spheres, gb.FP64)}
+    out["mixed"] = _guarded(run_serving, gb, spheres, gb.MIXED)
+    out["fp64_snapped_10hz"] = _guarded(run_serving, gb, spheres, gb.FP64, 10.0)
+    both = stream[:12]
+    out["both_cells_first_12"] = {"fp64": _guarded(run_serving, gb, both, gb.FP64),
+                                  "mixed": _guarded(run_serving, gb, both, gb.MIXED)}
     print(json.dumps(out))
 
 
