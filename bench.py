@@ -530,6 +530,10 @@ def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-2, restart=30, maxit
     s1.record(stream)
     torch.cuda.synchronize()
     seq_ms = s0.elapsed_time(s1)
+    # the batched products' first launches tune their tile shapes (as the
+    # single products' did in the section before): two untimed iterations
+    gb.solve_batch(ops, bs, tol=tol, restart=2, maxit=2, raise_on_noconv=False)
+    torch.cuda.synchronize()
     # one batched solve
     b0, b1 = ev(), ev()
     b0.record(stream)
@@ -547,8 +551,19 @@ def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-2, restart=30, maxit
     res["batched_vs_sequential_rel_diff_per_frequency"] = [
         float(torch.linalg.vector_norm(pb[o] - seq[o]) / torch.linalg.vector_norm(seq[o])) for o in range(len(ops))]
     res["speedup_batched_vs_sequential"] = seq_ms / bat_ms
+    res["tc_tiles_chosen_batched"] = [{k_: e[k_] for k_ in ("m", "k", "columns", "offsets", "rows_per_cta",
+                                                         "columns_per_cta", "ms")}
+                                      for e in gb.tuning_summary() if e.get("kernel") == "tc_gemm" and e.get("batched")]
     for op in ops:
         op.close()
+    # each frequency's batched solution against the FP64 (float-float) operator
+    res64 = []
+    for o, k in enumerate(ks):
+        op64 = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_FMM, n_t=n_t)
+        res64.append(float((torch.linalg.vector_norm(op64.matvec(pb[o]) - bs[o], dim=1) /
+                            torch.linalg.vector_norm(bs[o], dim=1)).max()))
+        op64.close()
+    res["batched"]["relres_fp64_operator_max_per_frequency"] = res64
     return res
 
 
@@ -594,8 +609,9 @@ def run_serving(gb, reqs, precision, snap_hz=None, tol=TOL):
             "cache_hits": st["cache_hits"], "hbm_high_water_bytes": st["hbm_high_water"],
             "iters_max": max((x["iters_max"] for x in results), default=None),
             "relres_true_max": max((x["relres_true_max"] for x in ok), default=None),
-            "failures": [{k_: x.get(k_) for k_ in ("status_name", "iters_max", "relres_true_max")}
-                         for x in results if x["status_name"] != "FMPB_OK"]}
+            "failures": [dict({k_: x.get(k_) for k_ in ("status_name", "iters_max", "relres_true_max")},
+                              cell=r["cell"], counts=list(r["counts"]), freq_hz=round(r["freq_hz"], 1))
+                         for r, x in zip(reqs, results) if x["status_name"] != "FMPB_OK"]}
 
 
 def serving_section(gb, n_sample=24):

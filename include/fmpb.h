@@ -707,8 +707,10 @@ fmpb_status fmpb_profile_summary(char *buf, size_t len);
 
 /* Writes a JSON list of the tile shapes the tensor-core autotuner chose:
  * the first product of each shape (device, rows m, depth k, columns,
- * offsets) times the tile variants (128 or 256 output rows and 128 or 256
- * output columns per CTA) on the caller's stream and keeps the fastest;
+ * offsets; single products and operator batches apart, "batched", one
+ * choice for every operator count of a batch) times the tile variants (128
+ * or 256 output rows and 128 or 256 output columns per CTA) on the caller's
+ * stream and keeps the fastest;
  * every entry lists the chosen tile and the time of each variant (ms, in
  * the order 128x256, 256x256, 256x128, 128x128); "kernel": "tc_gemm".
  * It also lists the plans the DFT-pass autotuner chose ("kernel": "dft"):

@@ -643,7 +643,10 @@ fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, co
   }
   int dev = 0;
   FMPB_CUDA(cudaGetDevice(&dev));
-  const TuneKey key{dev, m, k, ncols, offs.n, n_ops};
+  // single products and batches tune apart; a batch's choice holds for any
+  // operator count (the tile grid only grows by whole copies of one
+  // operator's), so operators dropping out of a batched solve cost no retuning
+  const TuneKey key{dev, m, k, ncols, offs.n, n_ops == 1 ? 1 : 2};
   int v = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -680,9 +683,10 @@ fmpb_status tc_tuning_summary(std::string& out) {
     const TcVariant t = TC_VARIANTS[kv.second.variant];
     int n = snprintf(buf, sizeof(buf),
                      "%s{\"kernel\": \"tc_gemm\", \"device\": %d, \"m\": %lld, \"k\": %lld, \"columns\": %lld, "
-                     "\"offsets\": %d, \"rows_per_cta\": %d, \"columns_per_cta\": %d, \"ms\": [",
+                     "\"offsets\": %d, \"batched\": %s, \"rows_per_cta\": %d, \"columns_per_cta\": %d, \"ms\": [",
                      first ? "" : ", ", kv.first.dev, (long long)kv.first.m, (long long)kv.first.k,
-                     (long long)kv.first.ncols, kv.first.noff, TC_BM * t.mt, t.bn);
+                     (long long)kv.first.ncols, kv.first.noff, kv.first.nbatch > 1 ? "true" : "false",
+                     TC_BM * t.mt, t.bn);
     out.append(buf, n);
     for (int v = 0; v < TC_NVARIANTS; ++v) {
       n = snprintf(buf, sizeof(buf), "%s%.4f", v ? ", " : "", kv.second.ms[v]);
