@@ -32,6 +32,7 @@
 // Every wait is bounded (one second of wall time); a wait that gives up sets
 // an error word for the host, and the CTA still drains its copies and frees
 // its tensor memory before it returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cstdio>
@@ -354,6 +355,260 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) tmem_dealloc(tmem, Tile::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Offset GEMM fed by the tensor memory accelerator.
+//
+// The columns of one output tile are a brick of source cells x right-hand
+// sides (bx x by x bz cells, br right-hand sides, x fastest), so the B tile of
+// offset delta is one 5-D TMA box of X viewed as (Kp, Mx, My, Mz, R nblk)
+// starting at the brick's origin minus delta: source cells outside the grid
+// (negative or too large coordinates) arrive as zeros from the copy engine.
+// A is a 2-D box (64 x 128 rows) of the realified tables viewed as
+// (Kp, n_off Mp).  Both use the 128-byte swizzle, which is the canonical
+// K-major layout the MMA descriptors name.
+//
+// Warp roles (256 threads):
+//   - warp 0, one lane: producer.  For K-step kt it waits until stage
+//     kt % NS is free (the MMAs of step kt - NS have completed), announces
+//     the stage's bytes on its `full` mbarrier and issues the TMA copies;
+//   - warp 1, one lane: MMA issuer.  It waits for `full`, issues the step's
+//     four 128 x N x 16 MMAs per accumulator and commits them to `empty`;
+//     after the last step it commits to `done`;
+//   - warp 2 allocates and frees the tensor memory;
+//   - all eight warps wait for `done` and run the epilogue (tcgen05.ld of
+//     their 32-lane quarter, coalesced complex-double stores).
+// Every wait is bounded (one second).  A wait that gives up raises a shared
+// abort flag that ends the other role's loop, the CTA then waits (bounded)
+// for every copy it issued and for its MMAs, sets the error word, frees its
+// tensor memory and returns.
+struct TcMaps {
+  CUtensorMap a[TC_MAX_BATCH];   // per operator: A as (Kp, n_off Mp) BF16
+  CUtensorMap x;                 // X as (Kp, Mx, My, Mz, R nblk) BF16
+};
+struct TcBrick {
+  int bx, by, bz, br;       // cells along x, y, z and right-hand sides per tile
+  int ntx, nty, ntz, ntr;   // tiles along each of them (per operator)
+  int rows;                 // bx by bz br: B rows of one stage
+  int n;                    // MMA N: rows rounded up to 16
+};
+
+template <int MT, int BNC>
+struct TmaTile {
+  static constexpr int A_HALF = TC_BM * TC_BK * 2;   // one 128-row A box
+  static constexpr int A_BYTES = MT * A_HALF;
+  static constexpr int B_BYTES = BNC * TC_BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // a multiple of 1024
+  static constexpr int CTRL = 128;                         // mbarriers, TMEM address, flags
+  static constexpr int FIT = (227 * 1024 - 1024 - CTRL) / STAGE_BYTES;
+  static constexpr int STAGES = FIT < 6 ? FIT : 6;
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + CTRL;   // 1024: alignment slack
+  static constexpr int TMEM_COLS = MT * BNC;
+  static_assert(STAGES >= 3, "tile too large for the shared-memory ring");
+  static_assert(2 * STAGES * 8 + 8 + 16 <= CTRL, "control block too small");
+};
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzle:
+// rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset),
+// layout type 2 (bits 61-63); the leading byte offset is unused for this
+// layout (field 1).  Advancing the start address by 32 bytes selects the
+// next 16-element K slice within the swizzle atom.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void* map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], "
+      "[%2];\n" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+// As mbar_wait_bounded, but also gives up when another role raised the abort
+// flag; a timeout raises it.
+__device__ bool mbar_wait_abortable(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > TC_WAIT_NS) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// The long wait of the idle warps for the end of the main loop: polls with a
+// short sleep so that they take few issue slots from the two working lanes.
+__device__ bool mbar_wait_sleepy(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > TC_WAIT_NS) return false;
+    __nanosleep(256);
+  }
+  return true;
+}
+
+template <int MT, int BNC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gemm_tma(const __grid_constant__ TcMaps maps, const TcBatch batch, const TcBrick bk, int Kp, int Mp,
+                  cd* __restrict__ y, int m, int64_t ncols, int Mx, int My, int Mz, int R, const TcOffsets offs,
+                  int accumulate, unsigned* err) {
+  using Tile = TmaTile<MT, BNC>;
+  constexpr int NS = Tile::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;   // the 128-byte swizzle wants 1024-byte aligned stages
+  unsigned char* ctrl = smem_raw + (sbase - raw) + NS * Tile::STAGE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);
+  uint64_t* empty = full + NS;
+  uint64_t* done = empty + NS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* n_loaded = abort_flag + 1;   // K-steps whose copies the producer issued
+  volatile int* n_mma = abort_flag + 2;      // K-steps whose MMAs were issued
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_BM * MT;
+  const bool two = MT == 2 && m0 + TC_BM < Mp;   // second row half present
+  const int64_t tiles = (int64_t)bk.ntx * bk.nty * bk.ntz * bk.ntr;
+  const int bop = (int)(blockIdx.y / tiles);
+  int64_t rem = (int64_t)blockIdx.y - (int64_t)bop * tiles;
+  const int tx = (int)(rem % bk.ntx);
+  rem /= bk.ntx;
+  const int ty = (int)(rem % bk.nty);
+  rem /= bk.nty;
+  const int tz = (int)(rem % bk.ntz);
+  const int tr = (int)(rem / bk.ntz);
+  const int x0 = tx * bk.bx, y0 = ty * bk.by, z0 = tz * bk.bz, r0 = tr * bk.br;
+  const int blk = batch.blk[bop];
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    *n_loaded = 0;
+    *n_mma = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 2) {
+    tmem_alloc(smem_u32(tmem_slot), Tile::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int kt_per_off = Kp / TC_BK;
+  const int KT = offs.n * kt_per_off;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    const void* amap = &maps.a[bop];
+    const void* xmap = &maps.x;
+    const uint32_t tx_bytes = (uint32_t)((two ? 2 : 1) * Tile::A_HALF + bk.rows * TC_BK * 2);
+    int kt = 0;
+    for (; kt < KT; ++kt) {
+      const int s = kt % NS;
+      if (kt >= NS && !mbar_wait_abortable(smem_u32(&empty[s]), ((kt / NS) - 1) & 1, abort_flag)) break;
+      const int o = kt / kt_per_off;
+      const int k0 = (kt - o * kt_per_off) * TC_BK;
+      const uint32_t sa = sbase + s * Tile::STAGE_BYTES, sb = sa + Tile::A_BYTES;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, tx_bytes);
+      tma_load_2d(sa, amap, fb, k0, o * Mp + m0);
+      if (two) tma_load_2d(sa + Tile::A_HALF, amap, fb, k0, o * Mp + m0 + TC_BM);
+      tma_load_5d(sb, xmap, fb, k0, x0 - offs.d[o][0], y0 - offs.d[o][1], z0 - offs.d[o][2], blk * R + r0);
+    }
+    *n_loaded = kt;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bk.n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    int kt = 0;
+    for (; kt < KT; ++kt) {
+      const int s = kt % NS;
+      if (!mbar_wait_abortable(smem_u32(&full[s]), (kt / NS) & 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t a0 = sbase + s * Tile::STAGE_BYTES, b0 = a0 + Tile::A_BYTES;
+#pragma unroll
+      for (int q = 0; q < TC_BK / 16; ++q) {
+        tc_mma(tmem, smem_desc_sw128(a0 + 32 * q), smem_desc_sw128(b0 + 32 * q), idesc, (kt | q) != 0);
+        if (two)
+          tc_mma(tmem + BNC, smem_desc_sw128(a0 + Tile::A_HALF + 32 * q), smem_desc_sw128(b0 + 32 * q), idesc,
+                 (kt | q) != 0);
+      }
+      tc_commit(smem_u32(&empty[s]));
+    }
+    *n_mma = kt;
+    tc_commit(smem_u32(done));   // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+  const bool mma_done = mbar_wait_sleepy(smem_u32(done), 0);
+  const bool bad = __syncthreads_or(!mma_done || *abort_flag != 0);
+  if (bad) {
+    // copies issued for steps whose MMAs never ran are still landing
+    if (tid == 0) {
+      for (int kt = *n_mma; kt < *n_loaded; ++kt) mbar_wait_bounded(smem_u32(&full[kt % NS]), (kt / NS) & 1);
+      atomicOr(err, 1u);
+    }
+  } else {
+    tc_fence_after();
+    const int quarter = warp & 3, half = warp >> 2;
+    const int64_t gm = (int64_t)m0 + (MT == 2 ? half * TC_BM : 0) + quarter * 32 + lane;
+    const bool row_ok = gm < 2 * (int64_t)m;
+    const int64_t i = gm >> 1;
+    const int part = (int)(gm & 1);
+    // MT = 1: warps 0-3 and 4-7 read the two column halves of the accumulator;
+    // MT = 2: warps 0-3 read accumulator 0 (rows 0..127), warps 4-7 accumulator 1
+    const int cbeg = MT == 2 ? 0 : half * (BNC / 2);
+    const int cend = MT == 2 ? ((half == 0 || two) ? bk.n : 0) : min(bk.n, cbeg + BNC / 2);
+    const uint32_t tcol = MT == 2 ? (uint32_t)(half * BNC) : 0u;
+    const int Nc = Mx * My * Mz;
+    cd* yb = y + (int64_t)blk * ncols * m;
+#pragma unroll 1
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + tcol + (uint32_t)c0, v);
+      if (row_ok) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int col = c0 + t;
+          if (col >= bk.rows) break;
+          int q = col;
+          const int cx = x0 + q % bk.bx;
+          q /= bk.bx;
+          const int cy = y0 + q % bk.by;
+          q /= bk.by;
+          const int cz = z0 + q % bk.bz;
+          const int r = r0 + q / bk.bz;
+          if (cx < Mx && cy < My && cz < Mz && r < R) {
+            const int64_t j = (int64_t)r * Nc + ((int64_t)cz * My + cy) * Mx + cx;
+            double* d = reinterpret_cast<double*>(yb + j * m + i) + part;
+            *d = accumulate ? *d + (double)v[t] : (double)v[t];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tmem_dealloc(tmem, Tile::TMEM_COLS);
+}
+
 __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) { return __float2bfloat16_rn(__double2float_rn(v)); }
 
 __global__ void k_tc_realify(const cd* __restrict__ T, int64_t m, int64_t k, int64_t Mh, int64_t Kh, int64_t total,
@@ -472,17 +727,118 @@ struct TcVariant {
 constexpr TcVariant TC_VARIANTS[] = {{1, 256}, {2, 256}, {2, 128}, {1, 128}};
 constexpr int TC_NVARIANTS = sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]);
 
+// cuTensorMapEncodeTiled, fetched from the driver once (the library does not
+// link the driver library itself).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// A BF16 tensor of `rank` dimensions (dims innermost first, byte strides of
+// dims 1..rank-1) read in boxes `box` with the 128-byte swizzle; elements
+// outside the tensor read as zero.
+fmpb_status encode_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                       const cuuint64_t* strides, const cuuint32_t* box) {
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) {
+    set_error("tensor-core product: the driver offers no cuTensorMapEncodeTiled");
+    return FMPB_ECUDA;
+  }
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("tensor-core product: tensor map encoding failed (driver status %d)", (int)r);
+    return FMPB_ECUDA;
+  }
+  return FMPB_OK;
+}
+
+// The brick of cells x right-hand sides per output tile, at most `cap`
+// columns: the one with the least work counted as tiles x (N + 128), N the
+// MMA width of a tile (its columns rounded up to 16) and 128 the rows of A a
+// tile copies per K-step in units of B rows (ties: more columns per tile).
+TcBrick pick_brick(int Mx, int My, int Mz, int R, int cap) {
+  TcBrick best{};
+  double best_cost = INFINITY;
+  for (int bx = 1; bx <= std::min(Mx, cap); ++bx)
+    for (int by = 1; by <= std::min(My, cap / bx); ++by)
+      for (int bz = 1; bz <= std::min(Mz, cap / (bx * by)); ++bz) {
+        const int br = std::min(R, cap / (bx * by * bz));
+        TcBrick b{bx, by, bz, br, (Mx + bx - 1) / bx, (My + by - 1) / by, (Mz + bz - 1) / bz, (R + br - 1) / br,
+                  bx * by * bz * br, 0};
+        b.n = (b.rows + 15) / 16 * 16;
+        const double cost = (double)b.ntx * b.nty * b.ntz * b.ntr * (b.n + 128);
+        if (cost < best_cost || (cost == best_cost && b.rows > best.rows)) {
+          best_cost = cost;
+          best = b;
+        }
+      }
+  return best;
+}
+
+template <int MT, int BNC>
+fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X, cd* y, int64_t m,
+                       int64_t ncols, const int M[3], int R, const TcOffsets& offs, bool accumulate, unsigned* err,
+                       cudaStream_t st) {
+  using Tile = TmaTile<MT, BNC>;
+  const TcBrick bk = pick_brick(M[0], M[1], M[2], R, BNC);
+  const int64_t tiles = (int64_t)bk.ntx * bk.nty * bk.ntz * bk.ntr;
+  if (tiles * A.n > 65535 || Mp * offs.n > INT32_MAX || (int64_t)R * A.nblk > INT32_MAX) {
+    set_error("tensor-core product: %lld column tiles exceed the launch limit", (long long)(tiles * A.n));
+    return FMPB_EINVAL;
+  }
+  TcMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)(Mp * offs.n)};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+    for (int o = 0; o < A.n; ++o) FMPB_TRY(encode_map(&maps.a[o], A.A[o], 2, dims, strides, box));
+  }
+  {
+    const cuuint64_t dims[5] = {(cuuint64_t)Kp, (cuuint64_t)M[0], (cuuint64_t)M[1], (cuuint64_t)M[2],
+                                (cuuint64_t)R * A.nblk};
+    const cuuint64_t strides[4] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * M[0], (cuuint64_t)Kp * 2 * M[0] * M[1],
+                                   (cuuint64_t)Kp * 2 * M[0] * M[1] * M[2]};
+    const cuuint32_t box[5] = {(cuuint32_t)TC_BK, (cuuint32_t)bk.bx, (cuuint32_t)bk.by, (cuuint32_t)bk.bz,
+                               (cuuint32_t)bk.br};
+    FMPB_TRY(encode_map(&maps.x, X, 5, dims, strides, box));
+  }
+  const int64_t rows = (int64_t)TC_BM * MT;
+  const dim3 grid((unsigned)((Mp + rows - 1) / rows), (unsigned)(tiles * A.n));
+  FMPB_CUDA((smem_limit_once<k_tc_gemm_tma<MT, BNC>>(Tile::SMEM)));
+  FMPB_LAUNCH("tc_gemm", st,
+              (k_tc_gemm_tma<MT, BNC><<<grid, TC_THREADS, Tile::SMEM, st>>>(
+                  maps, A, bk, (int)Kp, (int)Mp, y, (int)m, ncols, M[0], M[1], M[2], R, offs, accumulate ? 1 : 0,
+                  err)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
+// Tile variants of the offset GEMM: (row tiles per CTA, output columns per CTA).
 fmpb_status launch_offset_variant(int v, const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
-                                  cd* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs,
+                                  cd* y, int64_t m, int64_t ncols, const int M[3], int R, const TcOffsets& offs,
                                   bool accumulate, unsigned* err, cudaStream_t st) {
-  const TcVariant t = TC_VARIANTS[v];
-  const int64_t rows = (int64_t)TC_BM * t.mt;
-  dim3 grid((unsigned)((Mp + rows - 1) / rows), 1);
   switch (v) {
-    case 0: return launch_tc<256, false, 1>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
-    case 1: return launch_tc<256, false, 2>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
-    case 2: return launch_tc<128, false, 2>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
-    default: return launch_tc<128, false, 1>(grid, A, Mp * Kp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+    case 0: return launch_tma<1, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
+    case 1: return launch_tma<2, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
+    case 2: return launch_tma<2, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
+    default: return launch_tma<1, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
   }
 }
 
@@ -510,7 +866,7 @@ std::map<TuneKey, TuneEntry> g_tune;
 int g_forced_variant = -1;   // >= 0: fmpb_set_tile_variant override
 
 fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, int64_t Kp,
-                             const __nv_bfloat16* X, cd* y, int64_t m, int64_t ncols, const int M[3],
+                             const __nv_bfloat16* X, cd* y, int64_t m, int64_t ncols, const int M[3], int R,
                              const TcOffsets& offs, bool accumulate, unsigned* err, cudaStream_t st, int* chosen) {
   cd* out = y;
   cd* scratch = nullptr;
@@ -526,9 +882,9 @@ fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, i
   float best = 1e30f;
   int bestv = 0;
   for (int v = 0; v < TC_NVARIANTS && s == FMPB_OK; ++v) {
-    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, offs, false, err, st);
+    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, false, err, st);
     if (s == FMPB_OK && cudaEventRecord(t0, st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tune");
-    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, offs, false, err, st);
+    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, false, err, st);
     if (s == FMPB_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
       s = cuda_status(cudaGetLastError(), "tune");
     float ms = 0.f;
@@ -659,9 +1015,9 @@ fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, co
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   FMPB_CUDA(cudaStreamIsCapturing(st, &cap));
   if (v < 0 && cap == cudaStreamCaptureStatusNone)
-    FMPB_TRY(tune_offset_gemm(key, A, Mp, Kp, X, y, m, ncols, M, offs, accumulate, err, st, &v));
+    FMPB_TRY(tune_offset_gemm(key, A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st, &v));
   if (v < 0) v = 0;   // no tuning inside a stream capture
-  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, offs, accumulate, err, st);
+  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
 }
 
 fmpb_status tc_force_variant(int v) {
