@@ -529,6 +529,19 @@ fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int3
                                   fmpb_c64 *y, int accumulate, void *stream);
 
 /*
+ * The same with a second product in the same FP32 accumulation, the form of
+ * the FMM product's near field plus its L2P term (Sec. 3.5:
+ * y_c = sum_delta S_delta p_{c - delta} + U_0 L_c):
+ *   y[r][c] (+)= sum_o T_o x[r][c - delta_o] + T2 x2[r][c]
+ *   T2  device, m x k2 complex;   x2  device, R x n_cells x k2;  1 <= k2 <= 2^20.
+ * Same rounding, allocation and error behaviour as fmpb_offset_gemm_bf16.
+ */
+fmpb_status fmpb_offset_gemm2_bf16(const int32_t counts[3], int n_off, const int32_t *offsets,
+                                   int64_t m, int64_t k, const fmpb_c64 *T, int R, const fmpb_c64 *x,
+                                   int64_t k2, const fmpb_c64 *T2, const fmpb_c64 *x2, fmpb_c64 *y,
+                                   int accumulate, void *stream);
+
+/*
  * Padded circulant lengths P_a (smallest 2,3,5,7-smooth integer >= 2 M_a - 1,
  * 1 for M_a = 1) and F = P_0 P_1 P_2 for a cell grid.
  */

@@ -128,6 +128,7 @@ SIGNATURES = {
     "fmpb_build_blocks_q9p": (INT, [P, I64, P, I64, INT, ctypes.POINTER(Lattice), D, D, D, INT, P, P, P]),
     "fmpb_m2l_blocks": (INT, [D, INT, INT, P, P, P]),
     "fmpb_offset_gemm_bf16": (INT, [P, INT, P, I64, I64, P, INT, P, P, INT, P]),
+    "fmpb_offset_gemm2_bf16": (INT, [P, INT, P, I64, I64, P, INT, P, I64, P, P, P, INT, P]),
     "fmpb_circulant_shape": (INT, [P, P, P]),
     "fmpb_circulant_spectrum": (INT, [P, I64, P, P, P]),
     "fmpb_circulant_apply": (INT, [P, I64, P, INT, P, P, INT, P]),

@@ -352,6 +352,29 @@ def offset_gemm_bf16(counts, offsets, T, x, out=None, accumulate=False):
     return y
 
 
+def offset_gemm2_bf16(counts, offsets, T, x, T2, x2, out=None, accumulate=False):
+    """fmpb_offset_gemm2_bf16: y[r, c] (+)= sum_o T[o] x[r, c - delta_o] + T2 x2[r, c]
+    in one tensor-core accumulation.
+
+    T: (n_off, m, k), T2: (m, k2) complex128 CUDA; x: (R, n_cells * k),
+    x2: (R, n_cells * k2); returns (R, n_cells * m)."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    off = _host(offsets, np.int32).reshape(-1, 3)
+    n_off, m, k = T.shape
+    m2, k2 = T2.shape
+    if m2 != m:
+        raise ValueError(f"T2 has {m2} rows, T has {m}")
+    ncell = int(np.prod(c))
+    R = _cvec(x, ncell * k, "x")
+    if _cvec(x2, ncell * k2, "x2") != R:
+        raise ValueError("x and x2 hold different numbers of right-hand sides")
+    y = out if out is not None else torch.empty((R, ncell * m), dtype=torch.complex128, device="cuda")
+    check(lib().fmpb_offset_gemm2_bf16(_ptr(c), int(n_off), _ptr(off), int(m), int(k), _ptr(T.contiguous()), R,
+                                       _ptr(x), int(k2), _ptr(T2.contiguous()), _ptr(x2), _ptr(y),
+                                       1 if accumulate else 0, _stream()))
+    return y
+
+
 def circulant_shape(counts):
     c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
     P = np.zeros(3, dtype=np.int32)

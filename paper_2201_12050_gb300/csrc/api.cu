@@ -314,13 +314,16 @@ struct fmpb_operator {
       __nv_bfloat16* fb = lb + lb_elems;
       TcOffsets zero{};
       zero.n = 1;
+      // P2M, M2L (circulant), then the near field with the L2P term as the
+      // tail of the same tensor-core accumulation: y = sum S_d x + U_0 L
       FMPB_TRY(tc_rows_to_bf16(x, (int64_t)R * Nc, n, xb, st));
-      FMPB_TRY(tc_offset_gemm(Sb, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st));
       FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
       FMPB_TRY(circulant_apply(shape, B, reinterpret_cast<const cd*>(specb), R, Mom, Loc, false, scratch, st,
                                SPEC_BF16, fb, tc_err, false, circulant_f32_ok(shape)));
       FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
-      FMPB_TRY(tc_offset_gemm(U0b, zero, n, B, shape.M, R, lb, y, true, tc_err, st));
+      const __nv_bfloat16* sb1[1] = {Sb};
+      const __nv_bfloat16* ub1[1] = {U0b};
+      FMPB_TRY(tc_offset_gemm_batch(sb1, 1, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st, nullptr, ub1, B, lb));
       return FMPB_OK;
     }
     // the image part of a half-space operator (Eq. (2dPeriodicFMM_halfspace)):
@@ -1001,12 +1004,11 @@ static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, i
   zero.n = 1;
   unsigned* err = a->tc_err;
   FMPB_TRY(tc_rows_to_bf16(x, (int64_t)Rt * Nc, n, xb, st));
-  FMPB_TRY(tc_offset_gemm_batch(Sb, na, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st, blk));
   FMPB_TRY(tc_offset_gemm_batch(V0b, na, zero, B, n, a->shape.M, R, xb, Mom, false, err, st, blk));
   FMPB_TRY(circulant_apply(a->shape, B, nullptr, Rt, Mom, Loc, false, sc.p, st, SPEC_BF16, fb, err, false,
                            circulant_f32_ok(a->shape), sp, na, blk, n_ops));
   FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)Rt * Nc, B, lb, st));
-  FMPB_TRY(tc_offset_gemm_batch(U0b, na, zero, n, B, a->shape.M, R, lb, y, true, err, st, blk));
+  FMPB_TRY(tc_offset_gemm_batch(Sb, na, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st, blk, U0b, B, lb));
   return FMPB_OK;
 }
 
@@ -1334,14 +1336,20 @@ fmpb_status fmpb_tuning_summary(char* buf, size_t len) {
 
 fmpb_status fmpb_set_tile_variant(int variant) { return tc_force_variant(variant); }
 
-fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
-                                  const fmpb_c64* T, int R, const fmpb_c64* x, fmpb_c64* y, int accumulate,
-                                  void* stream) {
+namespace {
+fmpb_status offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
+                             const fmpb_c64* T, int R, const fmpb_c64* x, int64_t k2, const fmpb_c64* T2,
+                             const fmpb_c64* x2, fmpb_c64* y, int accumulate, void* stream) {
   CHECK_ARG(counts && offsets && T && x && y, "offset_gemm_bf16: NULL argument");
   CHECK_ARG(n_off >= 1 && n_off <= TC_MAX_OFF, "offset_gemm_bf16: n_off must be 1..%d", TC_MAX_OFF);
   CHECK_ARG(m >= 1 && m <= (1 << 20) && k >= 1 && k <= (1 << 20), "offset_gemm_bf16: m or k out of range");
   CHECK_ARG(R >= 1 && R <= 4096, "offset_gemm_bf16: R out of range");
   CHECK_ARG((const void*)x != (const void*)y, "offset_gemm_bf16: x and y must not alias");
+  const bool tail = T2 != nullptr;
+  if (tail) {
+    CHECK_ARG(x2 && k2 >= 1 && k2 <= (1 << 20), "offset_gemm2_bf16: x2 NULL or k2 out of range");
+    CHECK_ARG((const void*)x2 != (const void*)y, "offset_gemm2_bf16: x2 and y must not alias");
+  }
   int M[3];
   int64_t Nc = 1;
   for (int a = 0; a < 3; ++a) {
@@ -1356,17 +1364,26 @@ fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int3
   cudaStream_t st = (cudaStream_t)stream;
   const size_t a_elems = (size_t)n_off * tc_rows(m) * tc_depth(k);
   const size_t x_elems = (size_t)R * Nc * tc_depth(k);
-  __nv_bfloat16 *Ab = nullptr, *Xb = nullptr;
+  __nv_bfloat16 *Ab = nullptr, *Xb = nullptr, *A2b = nullptr, *X2b = nullptr;
   unsigned* err = nullptr;
   size_t bytes = 0;
   fmpb_status s = dev_alloc(&Ab, a_elems, bytes);
   if (s == FMPB_OK) s = dev_alloc(&Xb, x_elems, bytes);
+  if (s == FMPB_OK && tail) s = dev_alloc(&A2b, (size_t)tc_rows(m) * tc_depth(k2), bytes);
+  if (s == FMPB_OK && tail) s = dev_alloc(&X2b, (size_t)R * Nc * tc_depth(k2), bytes);
   if (s == FMPB_OK) s = dev_alloc(&err, 1, bytes);
   if (s == FMPB_OK && cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess)
     s = cuda_status(cudaGetLastError(), "memset");
   if (s == FMPB_OK) s = tc_realify((const cd*)T, n_off, m, k, Ab, st);
   if (s == FMPB_OK) s = tc_rows_to_bf16((const cd*)x, (int64_t)R * Nc, k, Xb, st);
-  if (s == FMPB_OK) s = tc_offset_gemm(Ab, offs, m, k, M, R, Xb, (cd*)y, accumulate != 0, err, st);
+  if (s == FMPB_OK && tail) s = tc_realify((const cd*)T2, 1, m, k2, A2b, st);
+  if (s == FMPB_OK && tail) s = tc_rows_to_bf16((const cd*)x2, (int64_t)R * Nc, k2, X2b, st);
+  if (s == FMPB_OK) {
+    const __nv_bfloat16* a1[1] = {Ab};
+    const __nv_bfloat16* a2[1] = {A2b};
+    s = tc_offset_gemm_batch(a1, 1, offs, m, k, M, R, Xb, (cd*)y, accumulate != 0, err, st, nullptr,
+                             tail ? a2 : nullptr, tail ? k2 : 0, X2b);
+  }
   unsigned flag = 0;
   if (s == FMPB_OK && cudaMemcpyAsync(&flag, err, sizeof(flag), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     s = cuda_status(cudaGetLastError(), "offset_gemm_bf16");
@@ -1378,8 +1395,24 @@ fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int3
   cudaStreamSynchronize(st);
   cudaFree(Ab);
   cudaFree(Xb);
+  cudaFree(A2b);
+  cudaFree(X2b);
   cudaFree(err);
   return s;
+}
+}  // namespace
+
+fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
+                                  const fmpb_c64* T, int R, const fmpb_c64* x, fmpb_c64* y, int accumulate,
+                                  void* stream) {
+  return offset_gemm_bf16(counts, n_off, offsets, m, k, T, R, x, 0, nullptr, nullptr, y, accumulate, stream);
+}
+
+fmpb_status fmpb_offset_gemm2_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
+                                   const fmpb_c64* T, int R, const fmpb_c64* x, int64_t k2, const fmpb_c64* T2,
+                                   const fmpb_c64* x2, fmpb_c64* y, int accumulate, void* stream) {
+  CHECK_ARG(T2, "offset_gemm2_bf16: NULL argument");
+  return offset_gemm_bf16(counts, n_off, offsets, m, k, T, R, x, k2, T2, x2, y, accumulate, stream);
 }
 
 fmpb_status fmpb_circulant_apply_bf16(const int32_t counts[3], int64_t B, const fmpb_c64* spec, int R,

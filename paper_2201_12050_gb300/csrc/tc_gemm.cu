@@ -365,7 +365,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // (negative or too large coordinates) arrive as zeros from the copy engine.
 // A is a 2-D box (64 x 128 rows) of the realified tables viewed as
 // (Kp, n_off Mp).  Both use the 128-byte swizzle, which is the canonical
-// K-major layout the MMA descriptors name.
+// K-major layout the MMA descriptors name.  An optional tail of kt2 more
+// K-steps adds A2 X2 (offset zero, depth Kp2) into the same accumulator: the
+// L2P term U_0 L_c of the FMM product joins the near field in one pass.
 //
 // Warp roles (256 threads):
 //   - warp 0, one lane: producer.  For K-step kt it waits until stage
@@ -382,8 +384,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // for every copy it issued and for its MMAs, sets the error word, frees its
 // tensor memory and returns.
 struct TcMaps {
-  CUtensorMap a[TC_MAX_BATCH];   // per operator: A as (Kp, n_off Mp) BF16
-  CUtensorMap x;                 // X as (Kp, Mx, My, Mz, R nblk) BF16
+  CUtensorMap a[TC_MAX_BATCH];    // per operator: A as (Kp, n_off Mp) BF16
+  CUtensorMap a2[TC_MAX_BATCH];   // per operator: the tail's A2 as (Kp2, Mp) BF16
+  CUtensorMap x;                  // X as (Kp, Mx, My, Mz, R nblk) BF16
+  CUtensorMap x2;                 // the tail's X2 as (Kp2, Mx, My, Mz, R nblk) BF16
+};
+// The tail product of the offset GEMM: per operator A2 (Mp x tc_depth(k)
+// rows, offset zero) times X2 (rows of depth tc_depth(k), the columns of X).
+struct TcTail {
+  const __nv_bfloat16* A[TC_MAX_BATCH];
+  int64_t k;
+  const __nv_bfloat16* X;
 };
 struct TcBrick {
   int bx, by, bz, br;       // cells along x, y, z and right-hand sides per tile
@@ -463,7 +474,7 @@ template <int MT, int BNC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm_tma(const __grid_constant__ TcMaps maps, const TcBatch batch, const TcBrick bk, int Kp, int Mp,
                   cd* __restrict__ y, int m, int64_t ncols, int Mx, int My, int Mz, int R, const TcOffsets offs,
-                  int accumulate, unsigned* err) {
+                  int kt2, int accumulate, unsigned* err) {
   using Tile = TmaTile<MT, BNC>;
   constexpr int NS = Tile::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -513,25 +524,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int kt_per_off = Kp / TC_BK;
-  const int KT = offs.n * kt_per_off;
+  const int KT1 = offs.n * kt_per_off;
+  const int KT = KT1 + kt2;
 
   if (warp == 0 && lane == 0) {
     // producer
     const void* amap = &maps.a[bop];
     const void* xmap = &maps.x;
+    const void* amap2 = &maps.a2[bop];
+    const void* xmap2 = &maps.x2;
     const uint32_t tx_bytes = (uint32_t)((two ? 2 : 1) * Tile::A_HALF + bk.rows * TC_BK * 2);
     int kt = 0;
     for (; kt < KT; ++kt) {
       const int s = kt % NS;
       if (kt >= NS && !mbar_wait_abortable(smem_u32(&empty[s]), ((kt / NS) - 1) & 1, abort_flag)) break;
-      const int o = kt / kt_per_off;
-      const int k0 = (kt - o * kt_per_off) * TC_BK;
       const uint32_t sa = sbase + s * Tile::STAGE_BYTES, sb = sa + Tile::A_BYTES;
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, tx_bytes);
-      tma_load_2d(sa, amap, fb, k0, o * Mp + m0);
-      if (two) tma_load_2d(sa + Tile::A_HALF, amap, fb, k0, o * Mp + m0 + TC_BM);
-      tma_load_5d(sb, xmap, fb, k0, x0 - offs.d[o][0], y0 - offs.d[o][1], z0 - offs.d[o][2], blk * R + r0);
+      if (kt < KT1) {
+        const int o = kt / kt_per_off;
+        const int k0 = (kt - o * kt_per_off) * TC_BK;
+        tma_load_2d(sa, amap, fb, k0, o * Mp + m0);
+        if (two) tma_load_2d(sa + Tile::A_HALF, amap, fb, k0, o * Mp + m0 + TC_BM);
+        tma_load_5d(sb, xmap, fb, k0, x0 - offs.d[o][0], y0 - offs.d[o][1], z0 - offs.d[o][2], blk * R + r0);
+      } else {
+        const int k0 = (kt - KT1) * TC_BK;
+        tma_load_2d(sa, amap2, fb, k0, m0);
+        if (two) tma_load_2d(sa + Tile::A_HALF, amap2, fb, k0, m0 + TC_BM);
+        tma_load_5d(sb, xmap2, fb, k0, x0, y0, z0, blk * R + r0);
+      }
     }
     *n_loaded = kt;
   } else if (warp == 1 && lane == 0) {
@@ -632,19 +653,6 @@ __global__ void k_tc_realify(const cd* __restrict__ T, int64_t m, int64_t k, int
   base[(2 * i + 1) * Kh + j] = bot;
 }
 
-__global__ void k_tc_rows_to_bf16(const cd* __restrict__ x, int64_t k, int64_t Kh, int64_t total,
-                                  __nv_bfloat162* __restrict__ X) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int64_t rho = idx / Kh, j = idx - rho * Kh;
-  cd v = mkc(0.0, 0.0);
-  if (j < k) v = x[rho * k + j];
-  __nv_bfloat162 p;
-  p.x = to_bf16(v.x);
-  p.y = to_bf16(v.y);
-  X[idx] = p;
-}
-
 // Float-float (float4: re_hi, re_lo, im_hi, im_lo) sources: the value is
 // hi + lo, whose FP32 rounding is hi for normalised pairs.
 __device__ __forceinline__ __nv_bfloat16 ff_to_bf16(float hi, float lo) {
@@ -671,30 +679,39 @@ __global__ void k_tc_realify_ff(const float4* __restrict__ T, int64_t m, int64_t
   base[(2 * i + 1) * Kh + j] = bot;
 }
 
-__global__ void k_tc_rows_from_ff(const float4* __restrict__ x, int64_t k, int64_t Kh, int64_t total,
-                                  __nv_bfloat162* __restrict__ X) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int64_t rho = idx / Kh, j = idx - rho * Kh;
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (j < k) v = x[rho * k + j];
+__device__ __forceinline__ __nv_bfloat162 bf16_pair(cd v) {
+  __nv_bfloat162 p;
+  p.x = to_bf16(v.x);
+  p.y = to_bf16(v.y);
+  return p;
+}
+__device__ __forceinline__ __nv_bfloat162 bf16_pair(float4 v) {
   __nv_bfloat162 p;
   p.x = ff_to_bf16(v.x, v.y);
   p.y = ff_to_bf16(v.z, v.w);
-  X[idx] = p;
+  return p;
 }
-
-__global__ void k_tc_rows_from_f32(const float2* __restrict__ x, int64_t k, int64_t Kh, int64_t total,
-                                   __nv_bfloat162* __restrict__ X) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int64_t rho = idx / Kh, j = idx - rho * Kh;
-  float2 v = make_float2(0.f, 0.f);
-  if (j < k) v = x[rho * k + j];
+__device__ __forceinline__ __nv_bfloat162 bf16_pair(float2 v) {
   __nv_bfloat162 p;
   p.x = __float2bfloat16_rn(v.x);
   p.y = __float2bfloat16_rn(v.y);
-  X[idx] = p;
+  return p;
+}
+// Rows of X: one warp per row, the lanes over its Kh (re, im) pairs (reads of
+// consecutive complex values, 4-byte stores, zeros past k).
+template <typename Src>
+__global__ void k_tc_rows(const Src* __restrict__ x, int k, int Kh, int64_t rows, __nv_bfloat162* __restrict__ X) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const int lane = threadIdx.x & 31;
+  const Src* __restrict__ xr = x + row * k;
+  __nv_bfloat162* __restrict__ Xr = X + row * Kh;
+  for (int j = lane; j < Kh; j += 32) {
+    __nv_bfloat162 p;
+    p.x = p.y = __float2bfloat16_rn(0.f);
+    if (j < k) p = bf16_pair(xr[j]);
+    Xr[j] = p;
+  }
 }
 
 template <int BN, bool FREQ, int MT>
@@ -793,8 +810,8 @@ TcBrick pick_brick(int Mx, int My, int Mz, int R, int cap) {
 
 template <int MT, int BNC>
 fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X, cd* y, int64_t m,
-                       int64_t ncols, const int M[3], int R, const TcOffsets& offs, bool accumulate, unsigned* err,
-                       cudaStream_t st) {
+                       int64_t ncols, const int M[3], int R, const TcOffsets& offs, const TcTail* tail,
+                       bool accumulate, unsigned* err, cudaStream_t st) {
   using Tile = TmaTile<MT, BNC>;
   const TcBrick bk = pick_brick(M[0], M[1], M[2], R, BNC);
   const int64_t tiles = (int64_t)bk.ntx * bk.nty * bk.ntz * bk.ntr;
@@ -819,13 +836,29 @@ fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bflo
                                (cuuint32_t)bk.br};
     FMPB_TRY(encode_map(&maps.x, X, 5, dims, strides, box));
   }
+  int kt2 = 0;
+  if (tail) {
+    const int64_t Kp2 = tc_depth(tail->k);
+    kt2 = (int)(Kp2 / TC_BK);
+    const cuuint64_t adims[2] = {(cuuint64_t)Kp2, (cuuint64_t)Mp};
+    const cuuint64_t astrides[1] = {(cuuint64_t)Kp2 * 2};
+    const cuuint32_t abox[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+    for (int o = 0; o < A.n; ++o) FMPB_TRY(encode_map(&maps.a2[o], tail->A[o], 2, adims, astrides, abox));
+    const cuuint64_t dims[5] = {(cuuint64_t)Kp2, (cuuint64_t)M[0], (cuuint64_t)M[1], (cuuint64_t)M[2],
+                                (cuuint64_t)R * A.nblk};
+    const cuuint64_t strides[4] = {(cuuint64_t)Kp2 * 2, (cuuint64_t)Kp2 * 2 * M[0],
+                                   (cuuint64_t)Kp2 * 2 * M[0] * M[1], (cuuint64_t)Kp2 * 2 * M[0] * M[1] * M[2]};
+    const cuuint32_t box[5] = {(cuuint32_t)TC_BK, (cuuint32_t)bk.bx, (cuuint32_t)bk.by, (cuuint32_t)bk.bz,
+                               (cuuint32_t)bk.br};
+    FMPB_TRY(encode_map(&maps.x2, tail->X, 5, dims, strides, box));
+  }
   const int64_t rows = (int64_t)TC_BM * MT;
   const dim3 grid((unsigned)((Mp + rows - 1) / rows), (unsigned)(tiles * A.n));
   FMPB_CUDA((smem_limit_once<k_tc_gemm_tma<MT, BNC>>(Tile::SMEM)));
   FMPB_LAUNCH("tc_gemm", st,
               (k_tc_gemm_tma<MT, BNC><<<grid, TC_THREADS, Tile::SMEM, st>>>(
-                  maps, A, bk, (int)Kp, (int)Mp, y, (int)m, ncols, M[0], M[1], M[2], R, offs, accumulate ? 1 : 0,
-                  err)));
+                  maps, A, bk, (int)Kp, (int)Mp, y, (int)m, ncols, M[0], M[1], M[2], R, offs, kt2,
+                  accumulate ? 1 : 0, err)));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -833,12 +866,12 @@ fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bflo
 // Tile variants of the offset GEMM: (row tiles per CTA, output columns per CTA).
 fmpb_status launch_offset_variant(int v, const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
                                   cd* y, int64_t m, int64_t ncols, const int M[3], int R, const TcOffsets& offs,
-                                  bool accumulate, unsigned* err, cudaStream_t st) {
+                                  const TcTail* tail, bool accumulate, unsigned* err, cudaStream_t st) {
   switch (v) {
-    case 0: return launch_tma<1, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
-    case 1: return launch_tma<2, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
-    case 2: return launch_tma<2, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
-    default: return launch_tma<1, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
+    case 0: return launch_tma<1, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
+    case 1: return launch_tma<2, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
+    case 2: return launch_tma<2, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
+    default: return launch_tma<1, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
   }
 }
 
@@ -853,8 +886,9 @@ struct TuneKey {
   int dev;
   int64_t m, k, ncols;
   int noff, nbatch;
+  int64_t k2;   // depth of a tail product (0: none)
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, m, k, ncols, noff, nbatch) < std::tie(o.dev, o.m, o.k, o.ncols, o.noff, o.nbatch);
+    return std::tie(dev, m, k, ncols, noff, nbatch, k2) < std::tie(o.dev, o.m, o.k, o.ncols, o.noff, o.nbatch, o.k2);
   }
 };
 struct TuneEntry {
@@ -867,7 +901,8 @@ int g_forced_variant = -1;   // >= 0: fmpb_set_tile_variant override
 
 fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, int64_t Kp,
                              const __nv_bfloat16* X, cd* y, int64_t m, int64_t ncols, const int M[3], int R,
-                             const TcOffsets& offs, bool accumulate, unsigned* err, cudaStream_t st, int* chosen) {
+                             const TcOffsets& offs, const TcTail* tail, bool accumulate, unsigned* err,
+                             cudaStream_t st, int* chosen) {
   cd* out = y;
   cd* scratch = nullptr;
   if (accumulate) {
@@ -882,9 +917,9 @@ fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, i
   float best = 1e30f;
   int bestv = 0;
   for (int v = 0; v < TC_NVARIANTS && s == FMPB_OK; ++v) {
-    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, false, err, st);
+    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, tail, false, err, st);
     if (s == FMPB_OK && cudaEventRecord(t0, st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tune");
-    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, false, err, st);
+    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, tail, false, err, st);
     if (s == FMPB_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
       s = cuda_status(cudaGetLastError(), "tune");
     float ms = 0.f;
@@ -923,15 +958,23 @@ fmpb_status tc_realify(const cd* T, int n_off, int64_t m, int64_t k, __nv_bfloat
   return FMPB_OK;
 }
 
-fmpb_status tc_rows_to_bf16(const cd* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
+template <typename Src>
+fmpb_status rows_to_bf16(const Src* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
   const int64_t Kh = tc_depth(k) / 2;
-  const int64_t total = rows * Kh;
-  if (total == 0) return FMPB_OK;
+  if (rows == 0) return FMPB_OK;
+  if (Kh > INT32_MAX) {
+    set_error("tensor-core rows: depth %lld too large", (long long)k);
+    return FMPB_EINVAL;
+  }
   FMPB_LAUNCH("tc_to_bf16", st,
-              k_tc_rows_to_bf16<<<grid_for((size_t)total, 256), 256, 0, st>>>(
-                  x, k, Kh, total, reinterpret_cast<__nv_bfloat162*>(X)));
+              k_tc_rows<Src><<<grid_for((size_t)rows * 32, 256), 256, 0, st>>>(
+                  x, (int)k, (int)Kh, rows, reinterpret_cast<__nv_bfloat162*>(X)));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
+}
+
+fmpb_status tc_rows_to_bf16(const cd* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
+  return rows_to_bf16(x, rows, k, X, st);
 }
 
 fmpb_status tc_realify_ff(const float4* T, int n_off, int64_t m, int64_t k, __nv_bfloat16* A, cudaStream_t st) {
@@ -945,25 +988,11 @@ fmpb_status tc_realify_ff(const float4* T, int n_off, int64_t m, int64_t k, __nv
 }
 
 fmpb_status tc_rows_from_ff(const float4* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
-  const int64_t Kh = tc_depth(k) / 2;
-  const int64_t total = rows * Kh;
-  if (total == 0) return FMPB_OK;
-  FMPB_LAUNCH("tc_to_bf16", st,
-              k_tc_rows_from_ff<<<grid_for((size_t)total, 256), 256, 0, st>>>(
-                  x, k, Kh, total, reinterpret_cast<__nv_bfloat162*>(X)));
-  FMPB_CUDA(cudaGetLastError());
-  return FMPB_OK;
+  return rows_to_bf16(x, rows, k, X, st);
 }
 
 fmpb_status tc_rows_from_f32(const float2* x, int64_t rows, int64_t k, __nv_bfloat16* X, cudaStream_t st) {
-  const int64_t Kh = tc_depth(k) / 2;
-  const int64_t total = rows * Kh;
-  if (total == 0) return FMPB_OK;
-  FMPB_LAUNCH("tc_to_bf16", st,
-              k_tc_rows_from_f32<<<grid_for((size_t)total, 256), 256, 0, st>>>(
-                  x, k, Kh, total, reinterpret_cast<__nv_bfloat162*>(X)));
-  FMPB_CUDA(cudaGetLastError());
-  return FMPB_OK;
+  return rows_to_bf16(x, rows, k, X, st);
 }
 
 fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_t m, int64_t k, const int M[3], int R,
@@ -973,7 +1002,8 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
 
 fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, const TcOffsets& offs, int64_t m,
                                  int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
-                                 unsigned* err, cudaStream_t st, const int* blk) {
+                                 unsigned* err, cudaStream_t st, const int* blk, const __nv_bfloat16* const* A2,
+                                 int64_t k2, const __nv_bfloat16* X2) {
   if (n_ops < 1 || n_ops > TC_MAX_BATCH) {
     set_error("tc_offset_gemm: %d operators in a batch (1..%d)", n_ops, TC_MAX_BATCH);
     return FMPB_EINVAL;
@@ -997,12 +1027,23 @@ fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, co
     set_error("tc_offset_gemm: %lld columns exceed the launch limit", (long long)ncols);
     return FMPB_EINVAL;
   }
+  TcTail tail{};
+  const bool has_tail = A2 != nullptr;
+  if (has_tail) {
+    if (!X2 || k2 < 1 || tc_depth(k2) > (1 << 24)) {
+      set_error("tc_offset_gemm: bad tail product (depth %lld)", (long long)k2);
+      return FMPB_EINVAL;
+    }
+    for (int o = 0; o < n_ops; ++o) tail.A[o] = A2[o];
+    tail.k = k2;
+    tail.X = X2;
+  }
   int dev = 0;
   FMPB_CUDA(cudaGetDevice(&dev));
   // single products and batches tune apart; a batch's choice holds for any
   // operator count (the tile grid only grows by whole copies of one
   // operator's), so operators dropping out of a batched solve cost no retuning
-  const TuneKey key{dev, m, k, ncols, offs.n, n_ops == 1 ? 1 : 2};
+  const TuneKey key{dev, m, k, ncols, offs.n, n_ops == 1 ? 1 : 2, has_tail ? k2 : 0};
   int v = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1015,9 +1056,11 @@ fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, co
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   FMPB_CUDA(cudaStreamIsCapturing(st, &cap));
   if (v < 0 && cap == cudaStreamCaptureStatusNone)
-    FMPB_TRY(tune_offset_gemm(key, A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st, &v));
+    FMPB_TRY(tune_offset_gemm(key, A, Mp, Kp, X, y, m, ncols, M, R, offs, has_tail ? &tail : nullptr, accumulate,
+                              err, st, &v));
   if (v < 0) v = 0;   // no tuning inside a stream capture
-  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, R, offs, accumulate, err, st);
+  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, R, offs, has_tail ? &tail : nullptr, accumulate, err,
+                               st);
 }
 
 fmpb_status tc_force_variant(int v) {

@@ -53,9 +53,14 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
 // X and y hold the R Nc columns of operator 0, then those of operator 1, ...
 // blk (may be null): the column block of each listed operator, for a subset
 // of the operators whose columns X and y hold (null: 0, 1, ..., n_ops - 1).
+// A2 (may be null): a tail product added in the same accumulator, per
+// operator A2[o] (tc_rows(m) x tc_depth(k2), offset zero) times X2 (rows of
+// depth tc_depth(k2), laid out as X): y (+)= sum_o T_o x_{c - delta_o} + T2 x2_c.
 fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* A, int n_ops, const TcOffsets& offs, int64_t m,
                                  int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
-                                 unsigned* err, cudaStream_t st, const int* blk = nullptr);
+                                 unsigned* err, cudaStream_t st, const int* blk = nullptr,
+                                 const __nv_bfloat16* const* A2 = nullptr, int64_t k2 = 0,
+                                 const __nv_bfloat16* X2 = nullptr);
 
 // Float-float sources (float4 per complex value: re_hi, re_lo, im_hi, im_lo),
 // rounded (hi + lo) -> FP32 -> BF16.

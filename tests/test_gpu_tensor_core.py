@@ -132,6 +132,30 @@ def test_offset_gemm_accumulates_and_skips_cells_outside_the_grid(tile_variant):
     assert np.abs(only_outside).max() == 0.0
 
 
+@pytest.mark.parametrize("tile_variant", [-1, 0, 1, 2, 3], indirect=True)
+@pytest.mark.parametrize("counts,offsets,m,k,k2,R,accumulate", [
+    ((5, 4, 3), OFF27, 20, 20, 9, 3, False),        # ragged M, N and K; a one-step tail
+    ((16, 12, 1), OFF9, 300, 150, 81, 2, True),     # half-empty 256-row tile, a three-step tail
+    ((4, 3, 2), [(1, 0, 0), (-1, 1, 1), (2, 0, 0)], 33, 17, 40, 2, False),   # sources outside the grid
+])
+def test_offset_gemm_with_tail_equals_product_of_rounded_inputs(counts, offsets, m, k, k2, R, accumulate,
+                                                                tile_variant):
+    # the FMM product's near field plus L2P term in one accumulation:
+    # y = sum_o T_o x_{c - delta_o} + T2 x2_c
+    T, x = _case(11 + m + k2, counts, offsets, m, k, R)
+    T2, x2 = _case(13 + k2, counts, [(0, 0, 0)], m, k2, R)
+    Nc = int(np.prod(counts))
+    y0 = random_complex_vectors(17, R, Nc * m) if accumulate else np.zeros((R, Nc * m), dtype=np.complex128)
+    y = gb.offset_gemm2_bf16(counts, offsets, _dev(T), _dev(x), _dev(T2[0]), _dev(x2), out=_dev(y0.copy()),
+                             accumulate=accumulate).cpu().numpy()
+    ref = y0 + _reference(counts, offsets, _cbf16(T), _cbf16(x)) + \
+        _reference(counts, [(0, 0, 0)], _cbf16(T2), _cbf16(x2))
+    err = _rel(y, ref)
+    assert err < 1e-5, err
+    with pytest.raises(ValueError):
+        gb.offset_gemm2_bf16(counts, offsets, _dev(T), _dev(x), _dev(T2[0, :-1]), _dev(x2))
+
+
 @pytest.mark.parametrize("counts,B,R", [((3, 4, 1), 40, 70), ((2, 3, 2), 81, 5), ((5, 1, 1), 169, 64),
                                           ((2, 2, 1), 30, 300)])
 def test_circulant_bf16_equals_rounded_frequency_products(counts, B, R):
