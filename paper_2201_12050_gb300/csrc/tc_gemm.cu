@@ -15,20 +15,16 @@
 //
 // The per-frequency block products of the circulant engine (Sec. 2.4:
 // Y_f = Lambda_f X_f for every padded-grid frequency f) are the other dense
-// complex GEMMs of the method once many right-hand sides share the spectrum;
-// the same kernel runs them with A = Lambda_f chosen by the frequency.
+// complex GEMMs of the method once many right-hand sides share the spectrum.
 //
-// Kernel structure (one CTA per 128 x BN output tile, BN = 32..256, 256 threads):
-//   - all threads stage A (128 x 64) and B (BN x 64) tiles with cp.async into
-//     a 4-deep ring of shared-memory stages, in the no-swizzle K-major layout
-//     of 8-row x 16-byte core matrices; B rows of source cells outside the
-//     grid are zero-filled by the copy itself (source size 0);
-//   - one thread issues four 128 x BN x 16 MMAs per stage into a BN-column
-//     FP32 accumulator in tensor memory and commits them to the stage's
-//     mbarrier, which releases the stage for the next copy;
-//   - after the last commit the eight warps read the accumulator back with
-//     tcgen05.ld (each warp its 32-lane quarter, half of the columns) and
-//     write or add complex-double output with coalesced stores.
+// Two kernels, both fed by the tensor memory accelerator (TMA) into rings of
+// 128-byte-swizzled shared-memory stages, with one producer lane, one
+// MMA-issuing lane (tcgen05.mma into FP32 accumulators in tensor memory) and
+// the epilogue read back by tcgen05.ld:
+//   - k_tc_gemm_tma: the offset GEMM, one CTA per output tile of 128 or 256
+//     rows and a brick of (cell, right-hand side) columns (see there);
+//   - k_tc_freq_tma: the per-frequency products on a persistent grid with a
+//     double-buffered accumulator (see there).
 // Every wait is bounded (one second of wall time); a wait that gives up sets
 // an error word for the host, and the CTA still drains its copies and frees
 // its tensor memory before it returns.
@@ -52,57 +48,10 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
-constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 256;
-constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
-constexpr int TC_BAR_BYTES = 64;   // TC_STAGES mbarriers + the tensor-memory address
-// BN output columns and MT x 128 output rows per CTA (MT accumulators of BN
-// tensor-memory columns each); as many stages as fit (at most TC_STAGES).
-template <int BN, int MT>
-struct TcTile {
-  static constexpr int A_BYTES = MT * TC_A_BYTES;
-  static constexpr int B_BYTES = BN * TC_BK * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int FIT = (227 * 1024 - TC_BAR_BYTES) / STAGE_BYTES;
-  static constexpr int STAGES = FIT < TC_STAGES ? FIT : TC_STAGES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + TC_BAR_BYTES;
-  static constexpr int TMEM_COLS = MT * BN;
-  static_assert(STAGES >= 3, "tile too large for the shared-memory ring");
-  // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A
-  // and B in BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
-  // N / 8 in bits 17-22, M / 16 in bits 24-28.
-  static constexpr uint32_t IDESC =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-};
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;
 
-// Core-matrix strides of the no-swizzle K-major layout: the 16-byte rows of
-// one 8 x 8 core matrix are contiguous (128 bytes), core matrices adjacent in
-// K are 128 bytes apart and those adjacent in M (or N) TC_BK / 8 * 128 bytes.
-constexpr uint32_t TC_LBO = 128;
-constexpr uint32_t TC_SBO = (TC_BK / 8) * 128;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading
-// byte offset / 16 (16-29), stride byte offset / 16 (32-45), the fixed
-// version field 1 (46-47), base offset 0, no swizzling (61-63 = 0).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
-         (1ull << 46);
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// Make this thread's completed generic-proxy writes to shared memory visible
-// to the tensor cores, which read their operands through the async proxy.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
@@ -169,190 +118,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Two ways of choosing the operands of one output tile:
-//   OFFSET: columns j = r Nc + c (rhs r, cell c), A_o shared by all columns,
-//           B row of column j for offset o = x row of the source cell
-//           c - delta_o (zero outside the grid); K runs over offsets x depth.
-//   FREQ:   blockIdx.y = frequency f with its own A_f, columns j = r < R,
-//           B row of column j = x row f R + r; K runs over the depth.
-//   MT = 2: a CTA owns 256 output rows in two accumulators and uses each B
-//           tile it copies for both (half the B traffic per flop); the last
-//           row tile of an odd count runs its second half empty.
-template <int BN, bool FREQ, int MT>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_gemm(const TcBatch batch, int64_t a_stride, int Kp, const __nv_bfloat16* __restrict__ X,
-              void* __restrict__ y_, int m, int64_t ncols, int Mx, int My, int Mz, TcOffsets offs, int accumulate,
-              unsigned* err) {
-  using Tile = TcTile<BN, MT>;
-  constexpr int NS = Tile::STAGES;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * Tile::STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NS);
-  const uint32_t sbase = smem_u32(smem);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TC_BM * MT;
-  const int64_t Mp = a_stride / Kp;
-  const bool two = MT == 2 && m0 + TC_BM < Mp;   // second row half present
-  // column tile of one operator of the batch: ncols columns per operator,
-  // stacked operator after operator in X and y (FREQ: within each frequency)
-  const int64_t ctile = FREQ ? blockIdx.z : blockIdx.y;
-  const int bop = (int)(ctile / batch.tiles);
-  const int64_t n0 = (ctile - (int64_t)bop * batch.tiles) * BN;
-  const int64_t f = FREQ ? (int64_t)blockIdx.y : 0;
-  const int Nc = Mx * My * Mz;
-  const int64_t ctot = ncols * batch.nblk;                // columns of all operator blocks
-  const int64_t obase = (int64_t)batch.blk[bop] * ncols;  // this operator's first column
-  const __nv_bfloat16* __restrict__ A = batch.A[bop];
-
-  if (tid == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  if (warp == 0) {
-    tmem_alloc(smem_u32(tmem_slot), Tile::TMEM_COLS);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  // This thread's copies: the 16-byte chunk q = tid + 256 t of a stage sits
-  // at byte 16 q, i.e. row ((q >> 6) << 3) + (q & 7) and K chunk (q >> 3) & 7.
-  const int kc = (tid >> 3) & 7;
-  const int rlo = (tid >> 6) * 8 + (tid & 7);   // row for t = 0; t adds 32 rows
-  constexpr int NB = BN / 32;                   // B chunks per thread and stage
-  int64_t bj[NB];
-  int bx[NB], by[NB], bz[NB];
-#pragma unroll
-  for (int t = 0; t < NB; ++t) {
-    const int64_t j = n0 + rlo + 32 * t;
-    bj[t] = j < ncols ? j : -1;
-    const int c = FREQ ? 0 : (int)(j % Nc);
-    bx[t] = c % Mx;
-    by[t] = (c / Mx) % My;
-    bz[t] = c / (Mx * My);
-  }
-  const int kt_per_off = Kp / TC_BK;
-  const int KT = (FREQ ? 1 : offs.n) * kt_per_off;
-  const __nv_bfloat16* Af = A + f * a_stride;
-
-  auto load_stage = [&](int it, int s) {
-    const int o = FREQ ? 0 : it / kt_per_off;
-    const int k0 = (it - o * kt_per_off) * TC_BK + kc * 8;
-    const uint32_t sa = sbase + s * Tile::STAGE_BYTES + tid * 16;
-    const uint32_t sb = sa + Tile::A_BYTES;
-    const __nv_bfloat16* arow = Af + o * a_stride + (int64_t)(m0 + rlo) * Kp + k0;
-#pragma unroll
-    for (int t = 0; t < MT * TC_BM / 32; ++t)
-      if (t < TC_BM / 32 || two) cp_async16(sa + t * 4096, arow + (int64_t)(32 * t) * Kp, 16);
-    if (FREQ) {
-#pragma unroll
-      for (int t = 0; t < NB; ++t) {
-        const bool ok = bj[t] >= 0;
-        cp_async16(sb + t * 4096, ok ? X + (f * ctot + obase + bj[t]) * Kp + k0 : X, ok ? 16 : 0);
-      }
-    } else {
-      const int dx = offs.d[o][0], dy = offs.d[o][1], dz = offs.d[o][2];
-      const int64_t dlin = ((int64_t)dz * My + dy) * Mx + dx;
-#pragma unroll
-      for (int t = 0; t < NB; ++t) {
-        const int sx = bx[t] - dx, sy = by[t] - dy, sz = bz[t] - dz;
-        const bool ok = bj[t] >= 0 && sx >= 0 && sx < Mx && sy >= 0 && sy < My && sz >= 0 && sz < Mz;
-        const __nv_bfloat16* src = ok ? X + (obase + bj[t] - dlin) * Kp + k0 : X;
-        cp_async16(sb + t * 4096, src, ok ? 16 : 0);
-      }
-    }
-  };
-
-  bool bad = false;
-#pragma unroll 1
-  for (int s = 0; s < NS - 1; ++s) {
-    if (s < KT) load_stage(s, s);
-    cp_async_commit();
-  }
-  int kt = 0;
-#pragma unroll 1
-  for (; kt < KT; ++kt) {
-    const int s = kt % NS;
-    cp_async_wait<NS - 2>();
-    fence_proxy_async();
-    if (__syncthreads_or(bad)) break;
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = sbase + s * Tile::STAGE_BYTES, b0 = a0 + Tile::A_BYTES;
-#pragma unroll
-      for (int q = 0; q < TC_BK / 16; ++q) {
-        tc_mma(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), Tile::IDESC, (kt | q) != 0);
-        if (two)   // rows 128..255 of the stage, second accumulator
-          tc_mma(tmem + BN, smem_desc(a0 + TC_A_BYTES + 256 * q), smem_desc(b0 + 256 * q), Tile::IDESC,
-                 (kt | q) != 0);
-      }
-      tc_commit(smem_u32(&bars[s]));
-    }
-    const int nk = kt + NS - 1;
-    if (nk < KT) {
-      // stage nk % NS was last read by the MMAs of step kt - 1
-      if (kt >= 1) bad = !mbar_wait_bounded(smem_u32(&bars[(kt - 1) % NS]), ((kt - 1) / NS) & 1);
-      if (!bad) load_stage(nk, nk % NS);
-    }
-    cp_async_commit();
-  }
-  const int last = kt - 1;   // MMAs were issued for steps 0 .. last
-  bool ok = true;
-  if (last >= 0) ok = mbar_wait_bounded(smem_u32(&bars[last % NS]), (last / NS) & 1);
-  cp_async_wait<0>();
-  ok = !__syncthreads_or(!ok || bad || last != KT - 1);
-  if (!ok) {
-    if (tid == 0) atomicOr(err, 1u);
-  } else {
-    tc_fence_after();
-    // MT = 1: warps 0-3 and 4-7 read the two column halves of the accumulator;
-    // MT = 2: warps 0-3 read accumulator 0 (rows 0..127), warps 4-7 accumulator 1
-    const int quarter = warp & 3, half = warp >> 2;
-    const int64_t gm = (int64_t)m0 + (MT == 2 ? half * TC_BM : 0) + quarter * 32 + lane;
-    const bool row_ok = gm < 2 * (int64_t)m;
-    const int64_t i = gm >> 1;
-    const int part = (int)(gm & 1);
-    const int cbase = MT == 2 ? 0 : half * (BN / 2);
-    const int ncol = MT == 2 ? ((half == 0 || two) ? BN : 0) : BN / 2;
-    const uint32_t tcol = MT == 2 ? (uint32_t)(half * BN) : (uint32_t)cbase;
-#pragma unroll 1
-    for (int c0 = 0; c0 < ncol; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + tcol + (uint32_t)c0, v);
-      if (row_ok) {
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int64_t j = n0 + cbase + c0 + t;
-          if (j < ncols) {
-            if (FREQ) {
-              // the circulant scratch format: float-float (hi = FP32 sum,
-              // lo = 0), or complex FP32 when `accumulate` is set (FREQ mode
-              // never accumulates; the flag selects the output format there)
-              if (accumulate) {
-                float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + (f * ctot + obase + j) * m + i) +
-                           part;
-                *d = v[t];
-              } else {
-                float2* d = reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + (f * ctot + obase + j) * m + i) +
-                            part;
-                *d = make_float2(v[t], 0.f);
-              }
-            } else {
-              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + (obase + j) * m + i) + part;
-              *d = accumulate ? *d + (double)v[t] : (double)v[t];
-            }
-          }
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, Tile::TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -630,6 +395,218 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 2) tmem_dealloc(tmem, Tile::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Per-frequency products Y_f = Lambda_f X_f (the circulant engine's block
+// products with many right-hand sides) on a persistent grid.
+//
+// Work item = (frequency f, operator, column tile, 128-row tile); one CTA per
+// SM takes items blockIdx.x, blockIdx.x + gridDim.x, ...  Each item is
+// Kp / 64 K-steps of a 128 x N x 64 MMA group, A from the realified spectrum
+// (a 2-D box of (Kp, F Mp)) and B from the rows f ctot + column of X (a 2-D
+// box of (Kp, F ctot)), both TMA copies into a ring of up to eight stages.
+// The spectrum is read once per product and only from HBM, so the kernel is a
+// stream: the producer runs ahead across items, and the accumulator is
+// double-buffered in tensor memory so that the epilogue of item c overlaps
+// the MMAs of item c + 1.
+//   - warp 0, one lane: producer (TMA);
+//   - warp 1, one lane: MMA issuer; before reusing accumulator c & 1 it waits
+//     for the epilogue's `tempty`, after an item's last step it commits `tfull`;
+//   - warp 2: tensor-memory allocation;
+//   - warps 4-7: epilogue, one 32-lane quarter each (tcgen05.ld), then one
+//     arrival per warp on `tempty`.
+// Waits are bounded as in the offset kernel (shared abort flag, drain of the
+// copies in flight, error word).
+template <int BNC>
+struct FreqTile {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = BNC * TC_BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // a multiple of 1024 for BNC >= 8
+  static constexpr int CTRL = 256;
+  static constexpr int FIT = (227 * 1024 - 1024 - CTRL) / STAGE_BYTES;
+  static constexpr int STAGES = FIT < 8 ? FIT : 8;
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + CTRL;
+  static constexpr int TMEM_COLS = 2 * BNC < 32 ? 32 : 2 * BNC;   // two accumulators
+  static_assert(STAGES >= 3, "tile too large for the shared-memory ring");
+  static_assert((2 * STAGES + 5) * 8 + 16 <= CTRL, "control block too small");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+// As mbar_wait_sleepy, but also gives up when the abort flag is raised, and
+// raises it on a timeout.
+__device__ bool mbar_wait_sleepy_abortable(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > TC_WAIT_NS) {
+      *abort_flag = 1;
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <int BNC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_freq_tma(const __grid_constant__ TcMaps maps, const TcBatch batch, int Kp, int Mp, int64_t F, int B, int R,
+                  int64_t ctot, int bn_rows, int n, void* __restrict__ y_, int f32_out, unsigned* err) {
+  using Tile = FreqTile<BNC>;
+  constexpr int NS = Tile::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  unsigned char* ctrl = smem_raw + (sbase - raw) + NS * Tile::STAGE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);
+  uint64_t* empty = full + NS;
+  uint64_t* tfull = empty + NS;   // [2]
+  uint64_t* tempty = tfull + 2;   // [2]
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* n_loaded = abort_flag + 1;   // K-steps whose copies were issued
+  volatile int* n_mma = abort_flag + 2;      // K-steps whose MMAs were issued
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int RT = Mp / TC_BM;
+  const int CT = (R + BNC - 1) / BNC;
+  const int64_t items = F * batch.n * CT * RT;
+  const int64_t my_items = (int64_t)blockIdx.x < items ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int KS = Kp / TC_BK;
+  // item -> (f, operator, column tile, row tile), row tiles fastest
+  auto decode = [&](int64_t it, int64_t& f, int& op, int& ct, int& rt) {
+    rt = (int)(it % RT);
+    it /= RT;
+    ct = (int)(it % CT);
+    it /= CT;
+    op = (int)(it % batch.n);
+    f = it / batch.n;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 4);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    *n_loaded = 0;
+    *n_mma = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 2) {
+    tmem_alloc(smem_u32(tmem_slot), Tile::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint32_t tx_bytes = (uint32_t)(Tile::A_BYTES + bn_rows * TC_BK * 2);
+    int64_t kt = 0;
+    bool stop = false;
+    for (int64_t c = 0; c < my_items && !stop; ++c) {
+      int64_t f;
+      int op, ct, rt;
+      decode(blockIdx.x + c * gridDim.x, f, op, ct, rt);
+      const int arow = (int)(f * Mp + rt * TC_BM);
+      const int xrow = (int)(f * ctot + (int64_t)batch.blk[op] * R + ct * BNC);
+      for (int ks = 0; ks < KS; ++ks, ++kt) {
+        const int s = (int)(kt % NS);
+        if (kt >= NS && !mbar_wait_abortable(smem_u32(&empty[s]), (uint32_t)(((kt / NS) - 1) & 1), abort_flag)) {
+          stop = true;
+          break;
+        }
+        const uint32_t sa = sbase + s * Tile::STAGE_BYTES, sb = sa + Tile::A_BYTES;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, tx_bytes);
+        tma_load_2d(sa, &maps.a[op], fb, ks * TC_BK, arow);
+        tma_load_2d(sb, &maps.x, fb, ks * TC_BK, xrow);
+      }
+    }
+    *n_loaded = (int)kt;
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    int64_t kt = 0;
+    bool stop = false;
+    for (int64_t c = 0; c < my_items && !stop; ++c) {
+      const int buf = (int)(c & 1);
+      if (c >= 2 && !mbar_wait_abortable(smem_u32(&tempty[buf]), (uint32_t)(((c >> 1) - 1) & 1), abort_flag)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(buf * BNC);
+      for (int ks = 0; ks < KS; ++ks, ++kt) {
+        const int s = (int)(kt % NS);
+        if (!mbar_wait_abortable(smem_u32(&full[s]), (uint32_t)((kt / NS) & 1), abort_flag)) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = sbase + s * Tile::STAGE_BYTES, b0 = a0 + Tile::A_BYTES;
+#pragma unroll
+        for (int q = 0; q < TC_BK / 16; ++q)
+          tc_mma(d, smem_desc_sw128(a0 + 32 * q), smem_desc_sw128(b0 + 32 * q), idesc, (ks | q) != 0);
+        tc_commit(smem_u32(&empty[s]));
+      }
+      if (!stop) tc_commit(smem_u32(&tfull[buf]));
+    }
+    *n_mma = (int)kt;
+    tc_commit(smem_u32(done));
+  } else if (warp >= 4) {
+    const int quarter = warp & 3;
+    for (int64_t c = 0; c < my_items; ++c) {
+      const int buf = (int)(c & 1);
+      if (!mbar_wait_sleepy_abortable(smem_u32(&tfull[buf]), (uint32_t)((c >> 1) & 1), abort_flag)) break;
+      tc_fence_after();
+      int64_t f;
+      int op, ct, rt;
+      decode(blockIdx.x + c * gridDim.x, f, op, ct, rt);
+      const int gm = rt * TC_BM + quarter * 32 + lane;
+      const bool row_ok = gm < 2 * B;
+      const int b = gm >> 1, part = gm & 1;
+      const int64_t ybase = f * ctot + (int64_t)batch.blk[op] * R;
+#pragma unroll 1
+      for (int c0 = 0; c0 < n; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BNC + c0), v);
+        if (row_ok) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int j = ct * BNC + c0 + t;
+            if (j < R && c0 + t < bn_rows) {
+              const int64_t e = (ybase + j) * B + b;
+              if (f32_out)
+                reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + e)[part] = v[t];
+              else
+                reinterpret_cast<float2*>(reinterpret_cast<float4*>(y_) + e)[part] = make_float2(v[t], 0.f);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  const bool mma_done = mbar_wait_sleepy(smem_u32(done), 0);
+  const bool bad = __syncthreads_or(!mma_done || *abort_flag != 0);
+  if (bad && tid == 0) {
+    for (int kt = *n_mma; kt < *n_loaded; ++kt) mbar_wait_bounded(smem_u32(&full[kt % NS]), (kt / NS) & 1);
+    atomicOr(err, 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tmem_dealloc(tmem, Tile::TMEM_COLS);
+}
+
 __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) { return __float2bfloat16_rn(__double2float_rn(v)); }
 
 __global__ void k_tc_realify(const cd* __restrict__ T, int64_t m, int64_t k, int64_t Mh, int64_t Kh, int64_t total,
@@ -713,36 +690,6 @@ __global__ void k_tc_rows(const Src* __restrict__ x, int k, int Kh, int64_t rows
     Xr[j] = p;
   }
 }
-
-template <int BN, bool FREQ, int MT>
-fmpb_status launch_tc(dim3 grid, TcBatch batch, int64_t a_stride, int64_t Kp, const __nv_bfloat16* X,
-                      void* y, int64_t m, int64_t ncols, const int M[3], const TcOffsets& offs, bool accumulate,
-                      unsigned* err, cudaStream_t st) {
-  using Tile = TcTile<BN, MT>;
-  batch.tiles = (ncols + BN - 1) / BN;
-  if (FREQ)
-    grid.z = (unsigned)(batch.tiles * batch.n);
-  else
-    grid.y = (unsigned)(batch.tiles * batch.n);
-  if (batch.tiles * batch.n > 65535) {
-    set_error("tensor-core product: %lld column tiles exceed the launch limit", (long long)(batch.tiles * batch.n));
-    return FMPB_EINVAL;
-  }
-  FMPB_CUDA((smem_limit_once<k_tc_gemm<BN, FREQ, MT>>(Tile::SMEM)));
-  FMPB_LAUNCH(FREQ ? "tc_block_product" : "tc_gemm", st,
-              (k_tc_gemm<BN, FREQ, MT><<<grid, TC_THREADS, Tile::SMEM, st>>>(batch, a_stride, (int)Kp, X, y, (int)m,
-                                                                              ncols, M[0], M[1], M[2], offs,
-                                                                              accumulate ? 1 : 0, err)));
-  FMPB_CUDA(cudaGetLastError());
-  return FMPB_OK;
-}
-
-// Tile variants of the offset GEMM: (row tiles per CTA, output columns per CTA).
-struct TcVariant {
-  int mt, bn;
-};
-constexpr TcVariant TC_VARIANTS[] = {{1, 256}, {2, 256}, {2, 128}, {1, 128}};
-constexpr int TC_NVARIANTS = sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]);
 
 // cuTensorMapEncodeTiled, fetched from the driver once (the library does not
 // link the driver library itself).
@@ -864,6 +811,12 @@ fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bflo
 }
 
 // Tile variants of the offset GEMM: (row tiles per CTA, output columns per CTA).
+struct TcVariant {
+  int mt, bn;
+};
+constexpr TcVariant TC_VARIANTS[] = {{1, 256}, {2, 256}, {2, 128}, {1, 128}};
+constexpr int TC_NVARIANTS = sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]);
+
 fmpb_status launch_offset_variant(int v, const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
                                   cd* y, int64_t m, int64_t ncols, const int M[3], int R, const TcOffsets& offs,
                                   const TcTail* tail, bool accumulate, unsigned* err, cudaStream_t st) {
@@ -1098,6 +1051,59 @@ fmpb_status tc_tuning_summary(std::string& out) {
   return FMPB_OK;
 }
 
+// SMs of the current device (the persistent grids' size), read once per device.
+int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> counts;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = counts.find(dev);
+  if (it != counts.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  counts[dev] = n;
+  return n;
+}
+
+template <int BNC>
+fmpb_status launch_freq(const TcBatch& A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, void* Y, bool y_f32,
+                        unsigned* err, cudaStream_t st) {
+  using Tile = FreqTile<BNC>;
+  const int64_t Mp = tc_rows(B), Kp = tc_depth(B);
+  const int64_t ctot = (int64_t)R * A.nblk;
+  const int bn_rows = std::min(R, BNC);
+  const int n = (bn_rows + 15) / 16 * 16;
+  TcMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)(F * Mp)};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+    for (int o = 0; o < A.n; ++o) FMPB_TRY(encode_map(&maps.a[o], A.A[o], 2, dims, strides, box));
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)(F * ctot)};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)bn_rows};
+    FMPB_TRY(encode_map(&maps.x, X, 2, dims, strides, box));
+  }
+  const int64_t items = F * A.n * ((R + BNC - 1) / BNC) * (Mp / TC_BM);
+  const unsigned grid = (unsigned)std::min<int64_t>(items, sm_count());
+  FMPB_CUDA((smem_limit_once<k_tc_freq_tma<BNC>>(Tile::SMEM)));
+  FMPB_LAUNCH("tc_block_product", st,
+              (k_tc_freq_tma<BNC><<<grid, TC_THREADS, Tile::SMEM, st>>>(maps, A, (int)Kp, (int)Mp, F, (int)B, R, ctot,
+                                                                       bn_rows, n, Y, y_f32 ? 1 : 0, err)));
+  FMPB_CUDA(cudaGetLastError());
+  return FMPB_OK;
+}
+
 fmpb_status tc_freq_gemm(const __nv_bfloat16* A, int64_t F, int64_t B, int R, const __nv_bfloat16* X, void* Y,
                          unsigned* err, cudaStream_t st, bool y_f32) {
   return tc_freq_gemm_batch(&A, 1, F, B, R, X, Y, err, st, y_f32);
@@ -1122,19 +1128,20 @@ fmpb_status tc_freq_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, int6
     }
   }
   const int64_t Mp = tc_rows(B), Kp = tc_depth(B);
-  if (F < 1 || F > 65535 || B < 1 || R < 1 || Mp / TC_BM > 65535 || Kp > (1 << 24)) {
+  if (F < 1 || B < 1 || R < 1 || Mp / TC_BM > 65535 || Kp > (1 << 24)) {
     set_error("tc_freq_gemm: bad shape (F %lld, B %lld, R %d)", (long long)F, (long long)B, R);
     return FMPB_EINVAL;
   }
-  const TcOffsets none{};
-  const int M[3] = {1, 1, 1};
+  if ((int64_t)F * Mp > INT32_MAX || (int64_t)F * R * A.nblk > INT32_MAX) {
+    set_error("tc_freq_gemm: %lld frequencies exceed the copy coordinates", (long long)F);
+    return FMPB_EINVAL;
+  }
   const int BN = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
-  dim3 grid((unsigned)(Mp / TC_BM), (unsigned)F, 1);
   switch (BN) {
-    case 32: return launch_tc<32, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
-    case 64: return launch_tc<64, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
-    case 128: return launch_tc<128, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
-    default: return launch_tc<256, true, 1>(grid, A, Mp * Kp, Kp, X, Y, B, R, M, none, y_f32, err, st);
+    case 32: return launch_freq<32>(A, F, B, R, X, Y, y_f32, err, st);
+    case 64: return launch_freq<64>(A, F, B, R, X, Y, y_f32, err, st);
+    case 128: return launch_freq<128>(A, F, B, R, X, Y, y_f32, err, st);
+    default: return launch_freq<256>(A, F, B, R, X, Y, y_f32, err, st);
   }
 }
 
