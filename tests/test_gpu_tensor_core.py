@@ -112,7 +112,8 @@ def test_offset_gemm_equals_product_of_rounded_inputs(counts, offsets, m, k, R, 
 def test_autotuner_records_its_choice():
     T, x = _case(5, (6, 5, 1), OFF9, 64, 40, 3)
     gb.offset_gemm_bf16((6, 5, 1), OFF9, _dev(T), _dev(x))
-    entries = [e for e in gb.tuning_summary() if (e["m"], e["k"], e["columns"], e["offsets"]) == (64, 40, 90, 9)]
+    entries = [e for e in gb.tuning_summary()
+               if e.get("kernel") == "tc_gemm" and (e["m"], e["k"], e["columns"], e["offsets"]) == (64, 40, 90, 9)]
     assert len(entries) == 1
     e = entries[0]
     assert e["rows_per_cta"] in (128, 256) and e["columns_per_cta"] in (128, 256) and len(e["ms"]) == 4
