@@ -258,6 +258,42 @@ struct fmpb_operator {
                            scratch, st, SPEC_FF, nullptr, nullptr, true);
   }
 
+  // The BF16 tensor-core product of the FMM form (BF16 operators and the
+  // inner products of MIXED FMM operators) on complex double (x_f32, y_f32
+  // false) or complex FP32 vectors: P2M, M2L through the circulant engine,
+  // then the near field with the L2P term as the tail of the same
+  // tensor-core accumulation, y = sum S_d x + U_0 L.
+  bool has_tc_matvec() const { return form == FMPB_FORM_FMM && !near2 && Sb != nullptr; }
+  fmpb_status matvec_tc(int R, const void* x, bool x_f32, void* y, bool y_f32, cudaStream_t st) {
+    const int64_t Nc = shape.ncells;
+    const int n = mesh.n;
+    const size_t circ = circulant_scratch_elems(shape, B, R);
+    const size_t mom = (size_t)R * Nc * B;
+    const size_t xb_elems = (size_t)R * Nc * tc_depth(n), lb_elems = (size_t)R * Nc * tc_depth(B);
+    const size_t fb_elems = (size_t)shape.F * R * tc_depth(B);
+    const size_t extra = (2 * (xb_elems + lb_elems + fb_elems) + sizeof(cd) - 1) / sizeof(cd);
+    FMPB_TRY(ensure_scratch(circ + 2 * mom + extra));
+    cd* Mom = scratch + circ;
+    cd* Loc = Mom + mom;
+    __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(Loc + mom);
+    __nv_bfloat16* lb = xb + xb_elems;
+    __nv_bfloat16* fb = lb + lb_elems;
+    TcOffsets zero{};
+    zero.n = 1;
+    if (x_f32)
+      FMPB_TRY(tc_rows_from_f32(reinterpret_cast<const float2*>(x), (int64_t)R * Nc, n, xb, st));
+    else
+      FMPB_TRY(tc_rows_to_bf16(reinterpret_cast<const cd*>(x), (int64_t)R * Nc, n, xb, st));
+    FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
+    FMPB_TRY(circulant_apply(shape, B, reinterpret_cast<const cd*>(specb), R, Mom, Loc, false, scratch, st,
+                             SPEC_BF16, fb, tc_err, false, circulant_f32_ok(shape)));
+    FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
+    const __nv_bfloat16* sb1[1] = {Sb};
+    const __nv_bfloat16* ub1[1] = {U0b};
+    return tc_offset_gemm_batch(sb1, 1, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st, nullptr, ub1, B, lb,
+                                y_f32);
+  }
+
   // low: the inner product of a MIXED operator (PBEM form: the FP32 spectrum;
   // FMM form: the BF16 tensor-core path of BF16 operators)
   fmpb_status matvec(int R, const cd* x, cd* y, cudaStream_t st, bool low = false) {
@@ -301,31 +337,7 @@ struct fmpb_operator {
     cd* Mom = scratch + circ;
     cd* Loc = Mom + mom;
     float4* xff = reinterpret_cast<float4*>(Loc + mom);
-    if (precision == FMPB_BF16 || (precision == FMPB_MIXED && low)) {
-      const int n = mesh.n;
-      const size_t xb_elems = (size_t)R * Nc * tc_depth(n), lb_elems = (size_t)R * Nc * tc_depth(B);
-      const size_t fb_elems = (size_t)shape.F * R * tc_depth(B);
-      const size_t extra = (2 * (xb_elems + lb_elems + fb_elems) + sizeof(cd) - 1) / sizeof(cd);
-      FMPB_TRY(ensure_scratch(circ + 2 * mom + extra));
-      Mom = scratch + circ;
-      Loc = Mom + mom;
-      __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(Loc + mom);
-      __nv_bfloat16* lb = xb + xb_elems;
-      __nv_bfloat16* fb = lb + lb_elems;
-      TcOffsets zero{};
-      zero.n = 1;
-      // P2M, M2L (circulant), then the near field with the L2P term as the
-      // tail of the same tensor-core accumulation: y = sum S_d x + U_0 L
-      FMPB_TRY(tc_rows_to_bf16(x, (int64_t)R * Nc, n, xb, st));
-      FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
-      FMPB_TRY(circulant_apply(shape, B, reinterpret_cast<const cd*>(specb), R, Mom, Loc, false, scratch, st,
-                               SPEC_BF16, fb, tc_err, false, circulant_f32_ok(shape)));
-      FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
-      const __nv_bfloat16* sb1[1] = {Sb};
-      const __nv_bfloat16* ub1[1] = {U0b};
-      FMPB_TRY(tc_offset_gemm_batch(sb1, 1, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st, nullptr, ub1, B, lb));
-      return FMPB_OK;
-    }
+    if (precision == FMPB_BF16 || (precision == FMPB_MIXED && low)) return matvec_tc(R, x, false, y, false, st);
     // the image part of a half-space operator (Eq. (2dPeriodicFMM_halfspace)):
     // near blocks S^ and P2M table V^ of the mirrored cell act on q = P x, its
     // M2L spectrum adds to the same local expansions (U^ = U)
@@ -901,15 +913,23 @@ fmpb_status fmpb_solve(const fmpb_operator* op, int R, const fmpb_c64* b, fmpb_c
   MatvecFn A = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st); };
   const int64_t N = (int64_t)op->mesh.n * op->shape.ncells;
   fmpb_status s;
+  // BF16 tensor-core products (BF16 operators, the inner solves of MIXED FMM
+  // operators) iterate on an FP32 Krylov basis
+  const MatvecF32Fn A32 = [mop](int r, const float2* x, float2* y, cudaStream_t st) {
+    return mop->matvec_tc(r, x, true, y, true, st);
+  };
   if (op->precision == FMPB_MIXED) {
     MatvecFn Alow = [mop](int r, const cd* x, cd* y, cudaStream_t st) { return mop->matvec(r, x, y, st, true); };
-    s = gmres_refined(A, Alow, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream);
+    s = gmres_refined(A, Alow, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream,
+                      mop->has_tc_matvec() ? &A32 : nullptr);
   } else {
     const MatvecFfFn Aff = [mop](int r, const float4* x, float4* y, cudaStream_t st) {
       return mop->matvec_ff(r, x, y, st);
     };
+    const bool tc = op->precision == FMPB_BF16 && mop->has_tc_matvec();
     s = gmres_solve(A, R, N, (const cd*)b, (cd*)p, o, info, (cudaStream_t)stream,
-                    mop->has_ff_matvec() && op->precision == FMPB_FP64 ? &Aff : nullptr);
+                    mop->has_ff_matvec() && op->precision == FMPB_FP64 ? &Aff : nullptr, nullptr,
+                    tc ? &A32 : nullptr);
   }
   if (s != FMPB_OK && s != FMPB_ENOCONV) return s;
   const fmpb_status c = fmpb_operator_check(op, stream);
@@ -968,8 +988,10 @@ static bool tc_batchable(const fmpb_operator* const* ops, int n_ops, bool low) {
 // active (host, n_ops R entries, may be null): systems still iterating; an
 // operator none of whose systems iterates is left out of the tensor-core
 // products (its outputs are not read), the DFT passes still run over all.
-static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, int R, const cd* x, cd* y,
-                                   cudaStream_t st, BatchScratch& sc, const int* active = nullptr) {
+// x, y: complex double, or with x_f32 / y_f32 complex FP32 (float2).
+static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, int R, const void* x, void* y,
+                                   cudaStream_t st, BatchScratch& sc, const int* active = nullptr,
+                                   bool x_f32 = false, bool y_f32 = false) {
   const fmpb_operator* a = ops[0];
   const int Rt = n_ops * R;
   const int64_t Nc = a->shape.ncells, n = a->mesh.n, B = a->B, F = a->shape.F;
@@ -1003,12 +1025,16 @@ static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, i
   TcOffsets zero{};
   zero.n = 1;
   unsigned* err = a->tc_err;
-  FMPB_TRY(tc_rows_to_bf16(x, (int64_t)Rt * Nc, n, xb, st));
+  if (x_f32)
+    FMPB_TRY(tc_rows_from_f32(reinterpret_cast<const float2*>(x), (int64_t)Rt * Nc, n, xb, st));
+  else
+    FMPB_TRY(tc_rows_to_bf16(reinterpret_cast<const cd*>(x), (int64_t)Rt * Nc, n, xb, st));
   FMPB_TRY(tc_offset_gemm_batch(V0b, na, zero, B, n, a->shape.M, R, xb, Mom, false, err, st, blk));
   FMPB_TRY(circulant_apply(a->shape, B, nullptr, Rt, Mom, Loc, false, sc.p, st, SPEC_BF16, fb, err, false,
                            circulant_f32_ok(a->shape), sp, na, blk, n_ops));
   FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)Rt * Nc, B, lb, st));
-  FMPB_TRY(tc_offset_gemm_batch(Sb, na, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st, blk, U0b, B, lb));
+  FMPB_TRY(tc_offset_gemm_batch(Sb, na, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st, blk, U0b, B, lb,
+                                y_f32));
   return FMPB_OK;
 }
 
@@ -1052,11 +1078,20 @@ fmpb_status fmpb_solve_batch(const fmpb_operator* const* ops, int n_ops, int R, 
     return FMPB_OK;
   };
   fmpb_status s;
+  // fused BF16 tensor-core products iterate on an FP32 Krylov basis
+  const MatvecF32Fn Alow32 = [&](int, const float2* x, float2* y, cudaStream_t s2) -> fmpb_status {
+    return batch_matvec_tc(ops, n_ops, R, x, y, s2, sc, nullptr, true, true);
+  };
+  const MatvecF32Fn A32 = [&](int, const float2* x, float2* y, cudaStream_t s2) -> fmpb_status {
+    return batch_matvec_tc(ops, n_ops, R, x, y, s2, sc, act.data(), true, true);
+  };
   if (mixed) {
     MatvecFn Alow = [&](int, const cd* x, cd* y, cudaStream_t s2) -> fmpb_status {
       return fused_low ? batch_matvec_tc(ops, n_ops, R, x, y, s2, sc) : loop(true, x, y, s2);
     };
-    s = gmres_refined(A, Alow, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st);
+    s = gmres_refined(A, Alow, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st, fused_low ? &Alow32 : nullptr);
+  } else if (fused) {
+    s = gmres_solve(A, n_ops * R, N, (const cd*)b, (cd*)p, o, info, st, nullptr, act.data(), &A32);
   } else {
     const MatvecFfFn Aff = [&](int, const float4* x, float4* y, cudaStream_t s2) -> fmpb_status {
       for (int q = 0; q < n_ops; ++q) {

@@ -713,6 +713,185 @@ __global__ void k_update_x_ff(const float4* __restrict__ V, int64_t vstride, Gmr
   }
 }
 
+// ---------------------------------------------------- FP32 Krylov basis --
+// Operators whose products carry BF16 rounding (BF16 tensor-core operators
+// and the inner solves of GMRES-IR) keep their basis in complex FP32: every
+// Gram-Schmidt pass moves half the bytes of a float-float basis and needs a
+// small fraction of its instructions.  The per-thread FP32 sums (a few
+// thousand terms at most, relative error far below the BF16 rounding of the
+// products) are reduced across threads in FP64, and the coefficients, the
+// Hessenberg matrix and the rotations stay FP64 as in the float-float path.
+
+__device__ __forceinline__ void cmac_conj_f(float2 x, float2 y, float& re, float& im) {   // += conj(x) y
+  re = fmaf(x.x, y.x, fmaf(x.y, y.y, re));
+  im = fmaf(x.x, y.y, fmaf(-x.y, y.x, im));
+}
+__device__ __forceinline__ void cmac_f(float2 a, float2 b, float& re, float& im) {   // += a b
+  re = fmaf(a.x, b.x, fmaf(-a.y, b.y, re));
+  im = fmaf(a.x, b.y, fmaf(a.y, b.x, im));
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP32 basis: partial sums of conj(V_v) p and (if z) conj(V_v) z for v < nvec,
+// DOTF_VB vectors per CTA; per-thread FP32 sums, FP64 across threads in a
+// fixed order.  Same partial layout as k_dots2_ff.
+constexpr int DOTF_VB = 4;
+__global__ void __launch_bounds__(RED_THREADS) k_dots2_f32(const float2* __restrict__ V, int64_t vstride, int nvec,
+                                                           const float2* __restrict__ p, const float2* __restrict__ z,
+                                                           int R, int64_t N, cd* __restrict__ part_p,
+                                                           cd* __restrict__ part_z, const int* __restrict__ active) {
+  const int blk = blockIdx.x, v0 = blockIdx.y * DOTF_VB, r = blockIdx.z;
+  const int nq = min(DOTF_VB, nvec - v0);
+  const int ntgt = z ? 2 : 1;
+  float pr[DOTF_VB], pi[DOTF_VB], zr[DOTF_VB], zi[DOTF_VB];
+#pragma unroll
+  for (int q = 0; q < DOTF_VB; ++q) pr[q] = pi[q] = zr[q] = zi[q] = 0.f;
+  if (active[r]) {
+    const float2* a = V + (int64_t)v0 * vstride + (int64_t)r * N;
+    const float2* pp = p + (int64_t)r * N;
+    const float2* zz = z ? z + (int64_t)r * N : nullptr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < N; i += stride) {
+      const float2 yp = pp[i];
+      const float2 yz = zz ? zz[i] : make_float2(0.f, 0.f);
+      float2 x[DOTF_VB];
+#pragma unroll
+      for (int q = 0; q < DOTF_VB; ++q) x[q] = q < nq ? a[(int64_t)q * vstride + i] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < DOTF_VB; ++q) {
+        cmac_conj_f(x[q], yp, pr[q], pi[q]);
+        cmac_conj_f(x[q], yz, zr[q], zi[q]);
+      }
+    }
+  }
+  __shared__ cd sh[2][RED_THREADS / 32][DOTF_VB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < DOTF_VB; ++q) {
+    const double a = warp_sum_d((double)pr[q]), b = warp_sum_d((double)pi[q]);
+    const double c = warp_sum_d((double)zr[q]), d = warp_sum_d((double)zi[q]);
+    if (lane == 0) {
+      sh[0][warp][q] = mkc(a, b);
+      sh[1][warp][q] = mkc(c, d);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < ntgt * nq) {
+    const int tgt = threadIdx.x / nq, q = threadIdx.x - tgt * nq;
+    double re = 0.0, im = 0.0;
+    for (int u = 0; u < RED_THREADS / 32; ++u) {
+      re += sh[tgt][u][q].x;
+      im += sh[tgt][u][q].y;
+    }
+    cd* out = tgt ? part_z : part_p;
+    out[((int64_t)(v0 + q) * R + r) * gridDim.x + blk] = mkc(re, im);
+  }
+}
+
+// FP32 basis: q_j = (p - Q t) / beta into slot j and the next pending vector
+// (z - Q c_{0..j-1} - q_j c_j) / beta into slot j + 1 (the step of
+// k_update2_ff), the two halves of a CTA taking the two halves of the basis.
+__global__ void __launch_bounds__(2 * SUB_ROWS) k_update2_f32(float2* __restrict__ V, int64_t vstride, int j,
+                                                              const cd* __restrict__ hA, const cd* __restrict__ cbuf,
+                                                              const double* __restrict__ inv, int R, int64_t N,
+                                                              const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  __shared__ float2 ts[MAX_RESTART], cs[MAX_RESTART];
+  __shared__ float2 op[SUB_ROWS], oz[SUB_ROWS];
+  for (int v = threadIdx.x; v < j; v += blockDim.x) {
+    const cd t = hA[v * R + r], c = cbuf[v * R + r];
+    ts[v] = make_float2((float)-t.x, (float)-t.y);
+    cs[v] = make_float2((float)-c.x, (float)-c.y);
+  }
+  const float invf = (float)inv[r];
+  const cd cj = cbuf[j * R + r];
+  const float2 mcj = make_float2((float)-cj.x, (float)-cj.y);
+  const int row = threadIdx.x & (SUB_ROWS - 1), half = threadIdx.x / SUB_ROWS;
+  const int nh = (j + 1) / 2;
+  const int vb = half ? nh : 0, ve = half ? j : nh;
+  __syncthreads();
+  float2* P = V + (int64_t)j * vstride + (int64_t)r * N;
+  float2* Z = V + (int64_t)(j + 1) * vstride + (int64_t)r * N;
+  const float2* Vr = V + (int64_t)r * N;
+  for (int64_t base = (int64_t)blockIdx.x * SUB_ROWS; base < N; base += (int64_t)gridDim.x * SUB_ROWS) {
+    const int64_t i = base + row;
+    const bool ok = i < N;
+    float pre = 0.f, pim = 0.f, zre = 0.f, zim = 0.f;
+    if (ok) {
+      if (!half) {
+        const float2 p0 = P[i], z0 = Z[i];
+        pre = p0.x;
+        pim = p0.y;
+        zre = z0.x;
+        zim = z0.y;
+      }
+      int v = vb;
+      for (; v + 3 < ve; v += 4) {
+        float2 a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          cmac_f(a[q], ts[v + q], pre, pim);
+          cmac_f(a[q], cs[v + q], zre, zim);
+        }
+      }
+      for (; v < ve; ++v) {
+        const float2 a = Vr[(int64_t)v * vstride + i];
+        cmac_f(a, ts[v], pre, pim);
+        cmac_f(a, cs[v], zre, zim);
+      }
+    }
+    if (half) {
+      op[row] = make_float2(pre, pim);
+      oz[row] = make_float2(zre, zim);
+    }
+    __syncthreads();
+    if (!half && ok) {
+      const float2 a = op[row], b = oz[row];
+      const float2 q = make_float2((pre + a.x) * invf, (pim + a.y) * invf);
+      float wre = zre + b.x, wim = zim + b.y;
+      cmac_f(q, mcj, wre, wim);
+      P[i] = q;
+      Z[i] = make_float2(wre * invf, wim * invf);
+    }
+    __syncthreads();
+  }
+}
+
+// y[r] = FP32(x[r] * s[r])
+__global__ void k_scale_to_f32(const cd* __restrict__ x, float2* __restrict__ y, const double* __restrict__ s, int R,
+                               int64_t N, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  const double f = s[r];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const cd v = x[(int64_t)r * N + i];
+    y[(int64_t)r * N + i] = make_float2((float)(v.x * f), (float)(v.y * f));
+  }
+}
+
+// x[r] += sum_{i < jcount[r]} V_i[r] y_i[r]  (FP32 basis, FP64 accumulation)
+__global__ void k_update_x_f32(const float2* __restrict__ V, int64_t vstride, GmresState s, cd* __restrict__ x, int R,
+                               int m, int64_t N) {
+  const int r = blockIdx.y;
+  const int J = s.jcount[r];
+  if (J == 0) return;
+  const cd* y = s.g + r * (m + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    cd acc = x[(int64_t)r * N + i];
+    for (int v = 0; v < J; ++v) {
+      const float2 b = V[(int64_t)v * vstride + (int64_t)r * N + i];
+      acc = cfma(mkc((double)b.x, (double)b.y), y[v], acc);
+    }
+    x[(int64_t)r * N + i] = acc;
+  }
+}
+
 // NaN / Inf scan of the right-hand side.
 __global__ void k_finite_check(const cd* __restrict__ b, int64_t total, int* __restrict__ bad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -744,7 +923,8 @@ struct DevBuf {
 }  // namespace
 
 fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x, const fmpb_solve_opts& o,
-                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff, int* active_host) {
+                        fmpb_solve_info* info, cudaStream_t st, const MatvecFfFn* Aff, int* active_host,
+                        const MatvecF32Fn* A32) {
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int m = o.restart > 0 ? o.restart : 30;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
@@ -754,6 +934,8 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   }
   auto t0 = std::chrono::steady_clock::now();
   const int64_t vstride = (int64_t)R * N;
+  const bool f32b = A32 != nullptr;   // FP32 Krylov basis (float2 values)
+  const size_t vbytes = f32b ? sizeof(float2) : sizeof(float4);
   // device memory: basis (m+1) R N, work vector R N, small state
   DevBuf Vb, Wb, Tb, Sb, Pb;
   // control state: carve one allocation; the first pass (base = null) sizes it
@@ -796,7 +978,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     bad = (int*)take(sizeof(int));
     if (pass == 0) {
       small = off;
-      if (cudaMalloc(&Vb.p, sizeof(cd) * (size_t)(m + 1) * vstride) != cudaSuccess ||
+      if (cudaMalloc(&Vb.p, vbytes * (size_t)(m + 1) * vstride) != cudaSuccess ||
           cudaMalloc(&Wb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess ||
           cudaMalloc(&Tb.p, sizeof(cd) * (size_t)vstride) != cudaSuccess || cudaMalloc(&Sb.p, small) != cudaSuccess ||
           cudaMalloc(&Pb.p, 2 * sizeof(cd) * (size_t)(m + 2) * R * RED_BLOCKS) != cudaSuccess) {
@@ -807,6 +989,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     }
   }
   float4* V = (float4*)Vb.p;   // float-float basis
+  float2* V32 = (float2*)Vb.p;  // or the FP32 basis
   cd* W = (cd*)Wb.p;           // product output / residual (FP64)
   cd* T = (cd*)Tb.p;           // product input (FP64 copy of v_j)
   cd* partial = (cd*)Pb.p;
@@ -816,9 +999,13 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
   // kept for the H t corrections
   DevBuf Hb;
   const size_t hraw_bytes = sizeof(cd) * (size_t)R * m * (m + 1);
-  const bool dcgs2 = Aff != nullptr && hraw_bytes <= ((size_t)1 << 30) &&
+  const bool dcgs2 = (Aff != nullptr || f32b) && hraw_bytes <= ((size_t)1 << 30) &&
                      cudaMalloc(&Hb.p, hraw_bytes) == cudaSuccess;
   if (!dcgs2) cudaGetLastError();
+  if (f32b && !dcgs2) {
+    set_error("gmres: cannot allocate the Hessenberg copy (%zu bytes) of the FP32-basis solver", hraw_bytes);
+    return FMPB_ENOMEM;
+  }
   cd* Hraw = (cd*)Hb.p;
 
   const unsigned vec_blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 4);
@@ -872,7 +1059,10 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
     first = false;
     FMPB_TRY(norms(W, s.beta, s.inv));
     FMPB_LAUNCH("cycle_start", st, k_cycle_start<<<rb, 64, 0, st>>>(s, R, m, tol));
-    FMPB_LAUNCH("scale_to_ff", st, k_scale_to_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active));
+    if (f32b)
+      FMPB_LAUNCH("scale_to_f32", st, k_scale_to_f32<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V32, s.inv, R, N, s.active));
+    else
+      FMPB_LAUNCH("scale_to_ff", st, k_scale_to_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(W, V, s.inv, R, N, s.active));
     FMPB_CUDA(cudaGetLastError());
     FMPB_CUDA(cudaMemcpyAsync(hact.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
     FMPB_CUDA(cudaStreamSynchronize(st));
@@ -887,19 +1077,31 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       for (int j = 0; j < m && total_it < maxit; ++j) {
         float4* vj = V + (int64_t)j * vstride;       // pending p
         float4* vn = V + (int64_t)(j + 1) * vstride; // z = A p
-        FMPB_TRY((*Aff)(R, vj, vn, st));
+        float2* vj32 = V32 + (int64_t)j * vstride;
+        float2* vn32 = V32 + (int64_t)(j + 1) * vstride;
+        if (f32b)
+          FMPB_TRY((*A32)(R, vj32, vn32, st));
+        else
+          FMPB_TRY((*Aff)(R, vj, vn, st));
         jdone = j + 1;
         // row blocks per vector group: about two waves of CTAs in total, so
         // that a long basis gives each thread many rows and the per-CTA
         // reduction is amortised (a short one keeps up to nb row blocks)
-        const int vg = (j + 2 + DOT2_VB - 1) / DOT2_VB;
+        const int vper = f32b ? DOTF_VB : DOT2_VB;
+        const int vg = (j + 2 + vper - 1) / vper;
         const int nb2 = std::max(1, std::min(nb, (152 * 4 * 2 + vg * R - 1) / (vg * R)));
-        FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
+        if (f32b)
+          FMPB_LAUNCH("dots_dcgs2_f32", st, k_dots2_f32<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V32, vstride, j + 2, vj32, vn32, R, N, partial, partial2, s.active));
+        else
+          FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb2, (j + 2) * R, h, 0));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb2, (j + 1) * R, hB, 0));
         FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
         FMPB_LAUNCH("dcgs2_hess_t", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
-        FMPB_LAUNCH("update_dcgs2", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
+        if (f32b)
+          FMPB_LAUNCH("update_dcgs2_f32", st, k_update2_f32<<<dim3(sub_blocks, R), 256, 0, st>>>(V32, vstride, j, h, cbuf, s.inv, R, N, s.active));
+        else
+          FMPB_LAUNCH("update_dcgs2", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
         if (j >= 1) FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, j - 1, tol));
         FMPB_CUDA(cudaGetLastError());
         ++total_it;
@@ -931,7 +1133,10 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       }
       // finish the pending column (a full cycle, or the iteration limit)
       if (any && jdone > 0) {
-        FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
+        if (f32b)
+          FMPB_LAUNCH("dots", st, k_dots2_f32<<<dim3(nb, (jdone + 1 + DOTF_VB - 1) / DOTF_VB, R), RED_THREADS, 0, st>>>(V32, vstride, jdone + 1, V32 + (int64_t)jdone * vstride, nullptr, R, N, partial, nullptr, s.active));
+        else
+          FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((jdone + 1) * R, 64), 64, 0, st>>>(partial, nb, (jdone + 1) * R, h, 0));
         FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
         FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, jdone - 1, tol));
@@ -993,7 +1198,10 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       }
     }
     FMPB_LAUNCH("backsolve", st, k_backsolve<<<R, 32, 0, st>>>(s, R, m));
-    FMPB_LAUNCH("update_x", st, k_update_x_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
+    if (f32b)
+      FMPB_LAUNCH("update_x", st, k_update_x_f32<<<dim3(vec_blocks, R), 256, 0, st>>>(V32, vstride, s, x, R, m, N));
+    else
+      FMPB_LAUNCH("update_x", st, k_update_x_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(V, vstride, s, x, R, m, N));
     FMPB_CUDA(cudaGetLastError());
     if (!any || timed_out || total_it >= maxit) break;
   }
@@ -1072,7 +1280,8 @@ __global__ void k_norm2_partial(const cd* __restrict__ v, int64_t N, double* __r
 // A_low d = r is solved by GMRES with the low-precision operator to the
 // relative tolerance inner_tol, and x += d, until ||r|| / ||b|| <= tol.
 fmpb_status gmres_refined(const MatvecFn& A, const MatvecFn& Alow, int R, int64_t N, const cd* b, cd* x,
-                          const fmpb_solve_opts& o, fmpb_solve_info* info, cudaStream_t st) {
+                          const fmpb_solve_opts& o, fmpb_solve_info* info, cudaStream_t st,
+                          const MatvecF32Fn* Alow32) {
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
@@ -1152,7 +1361,7 @@ fmpb_status gmres_refined(const MatvecFn& A, const MatvecFn& Alow, int R, int64_
     inner.tol = inner_tol;
     inner.maxit = maxit - total_it;
     std::vector<fmpb_solve_info> ii(R);
-    fmpb_status s = gmres_solve(Alow, R, N, r, d, inner, ii.data(), st);
+    fmpb_status s = gmres_solve(Alow, R, N, r, d, inner, ii.data(), st, nullptr, nullptr, Alow32);
     if (s != FMPB_OK && s != FMPB_ENOCONV && s != FMPB_ETIMEOUT) return s;
     int it_max = 0;
     for (int q = 0; q < R; ++q) {

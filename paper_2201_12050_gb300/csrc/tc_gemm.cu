@@ -238,8 +238,8 @@ __device__ bool mbar_wait_sleepy(uint32_t bar, uint32_t parity) {
 template <int MT, int BNC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm_tma(const __grid_constant__ TcMaps maps, const TcBatch batch, const TcBrick bk, int Kp, int Mp,
-                  cd* __restrict__ y, int m, int64_t ncols, int Mx, int My, int Mz, int R, const TcOffsets offs,
-                  int kt2, int accumulate, unsigned* err) {
+                  void* __restrict__ y_, int m, int64_t ncols, int Mx, int My, int Mz, int R,
+                  const TcOffsets offs, int kt2, int accumulate, int out_f32, unsigned* err) {
   using Tile = TmaTile<MT, BNC>;
   constexpr int NS = Tile::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int cend = MT == 2 ? ((half == 0 || two) ? bk.n : 0) : min(bk.n, cbeg + BNC / 2);
     const uint32_t tcol = MT == 2 ? (uint32_t)(half * BNC) : 0u;
     const int Nc = Mx * My * Mz;
-    cd* yb = y + (int64_t)blk * ncols * m;
+    const int64_t yoff = (int64_t)blk * ncols * m;
 #pragma unroll 1
     for (int c0 = cbeg; c0 < cend; c0 += 16) {
       float v[16];
@@ -382,9 +382,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int cz = z0 + q % bk.bz;
           const int r = r0 + q / bk.bz;
           if (cx < Mx && cy < My && cz < Mz && r < R) {
-            const int64_t j = (int64_t)r * Nc + ((int64_t)cz * My + cy) * Mx + cx;
-            double* d = reinterpret_cast<double*>(yb + j * m + i) + part;
-            *d = accumulate ? *d + (double)v[t] : (double)v[t];
+            const int64_t e = yoff + ((int64_t)r * Nc + ((int64_t)cz * My + cy) * Mx + cx) * m + i;
+            if (out_f32) {
+              float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + e) + part;
+              *d = accumulate ? *d + v[t] : v[t];
+            } else {
+              double* d = reinterpret_cast<double*>(reinterpret_cast<cd*>(y_) + e) + part;
+              *d = accumulate ? *d + (double)v[t] : (double)v[t];
+            }
           }
         }
       }
@@ -756,9 +761,9 @@ TcBrick pick_brick(int Mx, int My, int Mz, int R, int cap) {
 }
 
 template <int MT, int BNC>
-fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X, cd* y, int64_t m,
+fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X, void* y, int64_t m,
                        int64_t ncols, const int M[3], int R, const TcOffsets& offs, const TcTail* tail,
-                       bool accumulate, unsigned* err, cudaStream_t st) {
+                       bool accumulate, bool y_f32, unsigned* err, cudaStream_t st) {
   using Tile = TmaTile<MT, BNC>;
   const TcBrick bk = pick_brick(M[0], M[1], M[2], R, BNC);
   const int64_t tiles = (int64_t)bk.ntx * bk.nty * bk.ntz * bk.ntr;
@@ -805,7 +810,7 @@ fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bflo
   FMPB_LAUNCH("tc_gemm", st,
               (k_tc_gemm_tma<MT, BNC><<<grid, TC_THREADS, Tile::SMEM, st>>>(
                   maps, A, bk, (int)Kp, (int)Mp, y, (int)m, ncols, M[0], M[1], M[2], R, offs, kt2,
-                  accumulate ? 1 : 0, err)));
+                  accumulate ? 1 : 0, y_f32 ? 1 : 0, err)));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
 }
@@ -818,13 +823,13 @@ constexpr TcVariant TC_VARIANTS[] = {{1, 256}, {2, 256}, {2, 128}, {1, 128}};
 constexpr int TC_NVARIANTS = sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]);
 
 fmpb_status launch_offset_variant(int v, const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bfloat16* X,
-                                  cd* y, int64_t m, int64_t ncols, const int M[3], int R, const TcOffsets& offs,
-                                  const TcTail* tail, bool accumulate, unsigned* err, cudaStream_t st) {
+                                  void* y, int64_t m, int64_t ncols, const int M[3], int R, const TcOffsets& offs,
+                                  const TcTail* tail, bool accumulate, bool y_f32, unsigned* err, cudaStream_t st) {
   switch (v) {
-    case 0: return launch_tma<1, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
-    case 1: return launch_tma<2, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
-    case 2: return launch_tma<2, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
-    default: return launch_tma<1, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, err, st);
+    case 0: return launch_tma<1, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, y_f32, err, st);
+    case 1: return launch_tma<2, 256>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, y_f32, err, st);
+    case 2: return launch_tma<2, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, y_f32, err, st);
+    default: return launch_tma<1, 128>(A, Mp, Kp, X, y, m, ncols, M, R, offs, tail, accumulate, y_f32, err, st);
   }
 }
 
@@ -853,10 +858,10 @@ std::map<TuneKey, TuneEntry> g_tune;
 int g_forced_variant = -1;   // >= 0: fmpb_set_tile_variant override
 
 fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, int64_t Kp,
-                             const __nv_bfloat16* X, cd* y, int64_t m, int64_t ncols, const int M[3], int R,
-                             const TcOffsets& offs, const TcTail* tail, bool accumulate, unsigned* err,
+                             const __nv_bfloat16* X, void* y, int64_t m, int64_t ncols, const int M[3], int R,
+                             const TcOffsets& offs, const TcTail* tail, bool accumulate, bool y_f32, unsigned* err,
                              cudaStream_t st, int* chosen) {
-  cd* out = y;
+  void* out = y;
   cd* scratch = nullptr;
   if (accumulate) {
     FMPB_CUDA(cudaMalloc(&scratch, sizeof(cd) * (size_t)ncols * A.nblk * m));
@@ -870,9 +875,9 @@ fmpb_status tune_offset_gemm(const TuneKey& key, const TcBatch& A, int64_t Mp, i
   float best = 1e30f;
   int bestv = 0;
   for (int v = 0; v < TC_NVARIANTS && s == FMPB_OK; ++v) {
-    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, tail, false, err, st);
+    s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, tail, false, y_f32, err, st);
     if (s == FMPB_OK && cudaEventRecord(t0, st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "tune");
-    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, tail, false, err, st);
+    if (s == FMPB_OK) s = launch_offset_variant(v, A, Mp, Kp, X, out, m, ncols, M, R, offs, tail, false, y_f32, err, st);
     if (s == FMPB_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
       s = cuda_status(cudaGetLastError(), "tune");
     float ms = 0.f;
@@ -954,9 +959,9 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
 }
 
 fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, const TcOffsets& offs, int64_t m,
-                                 int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
+                                 int64_t k, const int M[3], int R, const __nv_bfloat16* X, void* y, bool accumulate,
                                  unsigned* err, cudaStream_t st, const int* blk, const __nv_bfloat16* const* A2,
-                                 int64_t k2, const __nv_bfloat16* X2) {
+                                 int64_t k2, const __nv_bfloat16* X2, bool y_f32) {
   if (n_ops < 1 || n_ops > TC_MAX_BATCH) {
     set_error("tc_offset_gemm: %d operators in a batch (1..%d)", n_ops, TC_MAX_BATCH);
     return FMPB_EINVAL;
@@ -1010,10 +1015,10 @@ fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, co
   FMPB_CUDA(cudaStreamIsCapturing(st, &cap));
   if (v < 0 && cap == cudaStreamCaptureStatusNone)
     FMPB_TRY(tune_offset_gemm(key, A, Mp, Kp, X, y, m, ncols, M, R, offs, has_tail ? &tail : nullptr, accumulate,
-                              err, st, &v));
+                              y_f32, err, st, &v));
   if (v < 0) v = 0;   // no tuning inside a stream capture
-  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, R, offs, has_tail ? &tail : nullptr, accumulate, err,
-                               st);
+  return launch_offset_variant(v, A, Mp, Kp, X, y, m, ncols, M, R, offs, has_tail ? &tail : nullptr, accumulate,
+                               y_f32, err, st);
 }
 
 fmpb_status tc_force_variant(int v) {

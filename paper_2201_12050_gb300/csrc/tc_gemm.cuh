@@ -56,11 +56,12 @@ fmpb_status tc_offset_gemm(const __nv_bfloat16* A, const TcOffsets& offs, int64_
 // A2 (may be null): a tail product added in the same accumulator, per
 // operator A2[o] (tc_rows(m) x tc_depth(k2), offset zero) times X2 (rows of
 // depth tc_depth(k2), laid out as X): y (+)= sum_o T_o x_{c - delta_o} + T2 x2_c.
+// y_f32: y holds complex FP32 (float2) values instead of complex double.
 fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* A, int n_ops, const TcOffsets& offs, int64_t m,
-                                 int64_t k, const int M[3], int R, const __nv_bfloat16* X, cd* y, bool accumulate,
+                                 int64_t k, const int M[3], int R, const __nv_bfloat16* X, void* y, bool accumulate,
                                  unsigned* err, cudaStream_t st, const int* blk = nullptr,
                                  const __nv_bfloat16* const* A2 = nullptr, int64_t k2 = 0,
-                                 const __nv_bfloat16* X2 = nullptr);
+                                 const __nv_bfloat16* X2 = nullptr, bool y_f32 = false);
 
 // Float-float sources (float4 per complex value: re_hi, re_lo, im_hi, im_lo),
 // rounded (hi + lo) -> FP32 -> BF16.
