@@ -319,6 +319,8 @@ def run_ours(args):
     halfspace = halfspace_section(gb, torch, stream) if sections else None
     fmm2 = fmm2_section(gb, torch, stream) if sections else None
     quad9 = _guarded(quad9_section, gb, torch, stream) if sections else None
+    c0 = _guarded(config0_section, gb, torch, stream) if sections else None
+    config0, p_c0 = (c0 if isinstance(c0, tuple) else (c0, None))
     mixed = (mixed_section(gb, torch, stream, args, w, v, t, sols, ms / args.steps, world, rank)
              if not args.only_headline else None)
 
@@ -347,9 +349,12 @@ def run_ours(args):
         "halfspace": halfspace,
         "fmm2": fmm2,
         "quad9": quad9,
+        "config0": config0,
     }
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, v, t, iters_by_freq)
+        if p_c0 is not None:
+            config0["cpu_baseline"] = _guarded(config0_dense_baseline, p_c0)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -1325,6 +1330,61 @@ def cpu_baseline(w, v, t, iters_by_freq):
                 "seconds_per_solve": sec_per_solve}
     finally:
         ot.close()
+
+
+def config0_section(gb, torch, stream, reps=20):
+    """The 1 x 4 row of rigid spheres (N = 1,280, k = 2, unit plane wave along
+    +x; the plain method, i.e. the PBEM form, FP64 class, GMRES to 1e-8):
+    operator build + right-hand side + solve on the GPU, timed over `reps`
+    repetitions after one untimed run.  Returns the section and the last
+    solution (host), which the oracle's dense solve is compared with."""
+    w = WORKLOADS["sphere_row_4"]
+    v, t = w.mesh()
+    k = w.wavenumbers[0]
+
+    def one():
+        op = gb.Operator(v, t, w.counts, w.lattice, k, form=gb.FORM_PBEM)
+        b = op.rhs_plane_wave(w.directions)
+        p, info = op.solve(b, tol=TOL)
+        op.close()
+        return p, info
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        p, info = one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "sphere_row_4: 1x4 rigid spheres r=0.2 m, lattice 1.0 m, 320 tri/cell, N=1280, k=2, "
+                        "plane wave +x, PBEM form, GMRES tol 1e-8",
+            "ms_per_solve_incl_build": ms, "solves_per_s": 1e3 / ms, "reps": reps,
+            "iters": info[0]["iters"], "relres_true": info[0]["relres_true"]}, p.cpu().numpy()[0]
+
+
+def config0_dense_baseline(p_gpu):
+    """The oracle's whole solve of the same system on the host, measured end
+    to end: assembly of the 1,280 x 1,280 collocation matrix (vectorised
+    numpy, one process), the right-hand side, and the LAPACK solve (numpy's
+    default thread count); plus the relative distance of the GPU solution."""
+    from oracle import bem, solve as osolve
+    w = WORKLOADS["sphere_row_4"]
+    v, t = w.mesh()
+    k = w.wavenumbers[0]
+    t0 = time.perf_counter()
+    A = bem.dense_matrix(v, t, w.lattice, w.counts, k)
+    t1 = time.perf_counter()
+    b = bem.plane_wave_rhs(bem.CellMesh(v, t), w.lattice, w.counts, k, w.directions[0])
+    p = osolve.dense_solve(A, b)
+    t2 = time.perf_counter()
+    return {"value": 1.0 / (t2 - t0), "unit": "solves/s", "kind": "oracle", "cores": 1,
+            "cores_detail": "assembly in one process (vectorised numpy); the LAPACK solve with numpy's default "
+                            f"thread count on {os.cpu_count()} host cores",
+            "sample": "the whole dense solve of the 1x4 sphere row, measured once",
+            "seconds_assembly": t1 - t0, "seconds_rhs_and_solve": t2 - t1, "seconds_total": t2 - t0,
+            "gpu_solution_rel_diff": float(np.linalg.norm(p_gpu - p) / np.linalg.norm(p))}
 
 
 def run_reference(args):
