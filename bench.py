@@ -19,6 +19,7 @@ counts.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -501,15 +502,20 @@ def batching_section(gb, torch, stream, freq_index=3, n_t=12):
         op.close()
     out["speedup_bf16_product_vs_fp64"] = out["fp64"]["matvec_64rhs_ms"] / out["bf16"]["matvec_64rhs_ms"]
     out["frequency_batch"] = _guarded(frequency_batch, gb, torch, stream, w, v, t, n_t)
+    # a smaller case (8 x 8 x 4 cells, 8 directions per frequency), where one
+    # operator's products do not fill the GPU on their own
+    small = dataclasses.replace(w, counts=(8, 8, 4), directions=w.directions[:8])
+    out["frequency_batch_small"] = _guarded(frequency_batch, gb, torch, stream, small, v, t, n_t)
     return out
 
 
 def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-2, restart=30, maxit=300):
-    """The whole batching workload: 8 frequencies x 64 directions (512
-    systems) with BF16 tensor-core operators, solved as 8 GMRES runs one
-    after the other and as one fmpb_solve_batch (one product sequence per
-    iteration over the 8 operators: near field, P2M, DFT passes, M2L and
-    L2P each one launch; operators whose systems have all converged drop out).
+    """The whole batching workload: the workload's frequencies x directions
+    (8 x 64 = 512 systems on the 16 x 16 x 4 lattice) with BF16 tensor-core
+    operators, solved as one GMRES run per frequency, one after the other, and
+    as one fmpb_solve_batch (one product sequence per iteration over the
+    operators: near field, P2M, DFT passes, M2L and L2P each one launch;
+    operators whose systems have all converged drop out).
     Tolerance 1e-2: BF16 products round their input vectors, which leaves the
     true residual of these systems at 5e-3..3e-2, and tighter tolerances make
     GMRES stagnate at that level for some frequencies."""
@@ -522,7 +528,7 @@ def frequency_batch(gb, torch, stream, w, v, t, n_t, tol=1e-2, restart=30, maxit
     build_s = time.perf_counter() - t0
     bs = torch.stack([op.rhs_plane_wave(w.directions) for op in ops])
     R = bs.shape[1]
-    res = {"systems": len(ops) * R, "frequencies_hz": [round(k * SPEED_OF_SOUND / (2 * math.pi), 1) for k in ks],
+    res = {"grid": list(w.counts), "rhs_per_frequency": R, "systems": len(ops) * R, "frequencies_hz": [round(k * SPEED_OF_SOUND / (2 * math.pi), 1) for k in ks],
            "tol": tol, "restart": restart, "maxit": maxit, "builds_s": build_s}
     # one after the other
     s0, s1 = ev(), ev()

@@ -739,17 +739,30 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // DOTF_VB vectors per CTA; per-thread FP32 sums, FP64 across threads in a
 // fixed order.  Same partial layout as k_dots2_ff.
 constexpr int DOTF_VB = 4;
+// Grid extent over systems of the FP32-basis kernels, which loop over the rest.
+constexpr int SYS_GRID = 64;
 __global__ void __launch_bounds__(RED_THREADS) k_dots2_f32(const float2* __restrict__ V, int64_t vstride, int nvec,
                                                            const float2* __restrict__ p, const float2* __restrict__ z,
                                                            int R, int64_t N, cd* __restrict__ part_p,
                                                            cd* __restrict__ part_z, const int* __restrict__ active) {
-  const int blk = blockIdx.x, v0 = blockIdx.y * DOTF_VB, r = blockIdx.z;
+  const int blk = blockIdx.x, v0 = blockIdx.y * DOTF_VB;
   const int nq = min(DOTF_VB, nvec - v0);
   const int ntgt = z ? 2 : 1;
-  float pr[DOTF_VB], pi[DOTF_VB], zr[DOTF_VB], zi[DOTF_VB];
+  __shared__ cd sh[2][RED_THREADS / 32][DOTF_VB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // systems r = blockIdx.z, + gridDim.z, ...: a batch of many systems, most
+  // of them stopped, costs no CTA launches for the stopped ones
+  for (int r = blockIdx.z; r < R; r += gridDim.z) {
+    if (!active[r]) {
+      if (threadIdx.x < ntgt * nq) {
+        const int tgt = threadIdx.x / nq, q = threadIdx.x - tgt * nq;
+        (tgt ? part_z : part_p)[((int64_t)(v0 + q) * R + r) * gridDim.x + blk] = mkc(0.0, 0.0);
+      }
+      continue;
+    }
+    float pr[DOTF_VB], pi[DOTF_VB], zr[DOTF_VB], zi[DOTF_VB];
 #pragma unroll
-  for (int q = 0; q < DOTF_VB; ++q) pr[q] = pi[q] = zr[q] = zi[q] = 0.f;
-  if (active[r]) {
+    for (int q = 0; q < DOTF_VB; ++q) pr[q] = pi[q] = zr[q] = zi[q] = 0.f;
     const float2* a = V + (int64_t)v0 * vstride + (int64_t)r * N;
     const float2* pp = p + (int64_t)r * N;
     const float2* zz = z ? z + (int64_t)r * N : nullptr;
@@ -766,28 +779,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots2_f32(const float2* __restr
         cmac_conj_f(x[q], yz, zr[q], zi[q]);
       }
     }
-  }
-  __shared__ cd sh[2][RED_THREADS / 32][DOTF_VB];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();   // the previous system's reads of sh are done
 #pragma unroll
-  for (int q = 0; q < DOTF_VB; ++q) {
-    const double a = warp_sum_d((double)pr[q]), b = warp_sum_d((double)pi[q]);
-    const double c = warp_sum_d((double)zr[q]), d = warp_sum_d((double)zi[q]);
-    if (lane == 0) {
-      sh[0][warp][q] = mkc(a, b);
-      sh[1][warp][q] = mkc(c, d);
+    for (int q = 0; q < DOTF_VB; ++q) {
+      const double a0 = warp_sum_d((double)pr[q]), b0 = warp_sum_d((double)pi[q]);
+      const double c0 = warp_sum_d((double)zr[q]), d0 = warp_sum_d((double)zi[q]);
+      if (lane == 0) {
+        sh[0][warp][q] = mkc(a0, b0);
+        sh[1][warp][q] = mkc(c0, d0);
+      }
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < ntgt * nq) {
-    const int tgt = threadIdx.x / nq, q = threadIdx.x - tgt * nq;
-    double re = 0.0, im = 0.0;
-    for (int u = 0; u < RED_THREADS / 32; ++u) {
-      re += sh[tgt][u][q].x;
-      im += sh[tgt][u][q].y;
+    __syncthreads();
+    if (threadIdx.x < ntgt * nq) {
+      const int tgt = threadIdx.x / nq, q = threadIdx.x - tgt * nq;
+      double re = 0.0, im = 0.0;
+      for (int u = 0; u < RED_THREADS / 32; ++u) {
+        re += sh[tgt][u][q].x;
+        im += sh[tgt][u][q].y;
+      }
+      (tgt ? part_z : part_p)[((int64_t)(v0 + q) * R + r) * gridDim.x + blk] = mkc(re, im);
     }
-    cd* out = tgt ? part_z : part_p;
-    out[((int64_t)(v0 + q) * R + r) * gridDim.x + blk] = mkc(re, im);
   }
 }
 
@@ -798,68 +809,71 @@ __global__ void __launch_bounds__(2 * SUB_ROWS) k_update2_f32(float2* __restrict
                                                               const cd* __restrict__ hA, const cd* __restrict__ cbuf,
                                                               const double* __restrict__ inv, int R, int64_t N,
                                                               const int* __restrict__ active) {
-  const int r = blockIdx.y;
-  if (!active[r]) return;
   __shared__ float2 ts[MAX_RESTART], cs[MAX_RESTART];
   __shared__ float2 op[SUB_ROWS], oz[SUB_ROWS];
-  for (int v = threadIdx.x; v < j; v += blockDim.x) {
-    const cd t = hA[v * R + r], c = cbuf[v * R + r];
-    ts[v] = make_float2((float)-t.x, (float)-t.y);
-    cs[v] = make_float2((float)-c.x, (float)-c.y);
-  }
-  const float invf = (float)inv[r];
-  const cd cj = cbuf[j * R + r];
-  const float2 mcj = make_float2((float)-cj.x, (float)-cj.y);
-  const int row = threadIdx.x & (SUB_ROWS - 1), half = threadIdx.x / SUB_ROWS;
-  const int nh = (j + 1) / 2;
-  const int vb = half ? nh : 0, ve = half ? j : nh;
-  __syncthreads();
-  float2* P = V + (int64_t)j * vstride + (int64_t)r * N;
-  float2* Z = V + (int64_t)(j + 1) * vstride + (int64_t)r * N;
-  const float2* Vr = V + (int64_t)r * N;
-  for (int64_t base = (int64_t)blockIdx.x * SUB_ROWS; base < N; base += (int64_t)gridDim.x * SUB_ROWS) {
-    const int64_t i = base + row;
-    const bool ok = i < N;
-    float pre = 0.f, pim = 0.f, zre = 0.f, zim = 0.f;
-    if (ok) {
-      if (!half) {
-        const float2 p0 = P[i], z0 = Z[i];
-        pre = p0.x;
-        pim = p0.y;
-        zre = z0.x;
-        zim = z0.y;
-      }
-      int v = vb;
-      for (; v + 3 < ve; v += 4) {
-        float2 a[4];
+  // systems r = blockIdx.y, + gridDim.y, ... (stopped systems cost no CTA launches)
+  for (int r = blockIdx.y; r < R; r += gridDim.y) {
+    if (!active[r]) continue;
+    __syncthreads();   // the previous system's reads of ts, cs are done
+    for (int v = threadIdx.x; v < j; v += blockDim.x) {
+      const cd t = hA[v * R + r], c = cbuf[v * R + r];
+      ts[v] = make_float2((float)-t.x, (float)-t.y);
+      cs[v] = make_float2((float)-c.x, (float)-c.y);
+    }
+    const float invf = (float)inv[r];
+    const cd cj = cbuf[j * R + r];
+    const float2 mcj = make_float2((float)-cj.x, (float)-cj.y);
+    const int row = threadIdx.x & (SUB_ROWS - 1), half = threadIdx.x / SUB_ROWS;
+    const int nh = (j + 1) / 2;
+    const int vb = half ? nh : 0, ve = half ? j : nh;
+    __syncthreads();
+    float2* P = V + (int64_t)j * vstride + (int64_t)r * N;
+    float2* Z = V + (int64_t)(j + 1) * vstride + (int64_t)r * N;
+    const float2* Vr = V + (int64_t)r * N;
+    for (int64_t base = (int64_t)blockIdx.x * SUB_ROWS; base < N; base += (int64_t)gridDim.x * SUB_ROWS) {
+      const int64_t i = base + row;
+      const bool ok = i < N;
+      float pre = 0.f, pim = 0.f, zre = 0.f, zim = 0.f;
+      if (ok) {
+        if (!half) {
+          const float2 p0 = P[i], z0 = Z[i];
+          pre = p0.x;
+          pim = p0.y;
+          zre = z0.x;
+          zim = z0.y;
+        }
+        int v = vb;
+        for (; v + 3 < ve; v += 4) {
+          float2 a[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
+          for (int q = 0; q < 4; ++q) a[q] = Vr[(int64_t)(v + q) * vstride + i];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          cmac_f(a[q], ts[v + q], pre, pim);
-          cmac_f(a[q], cs[v + q], zre, zim);
+          for (int q = 0; q < 4; ++q) {
+            cmac_f(a[q], ts[v + q], pre, pim);
+            cmac_f(a[q], cs[v + q], zre, zim);
+          }
+        }
+        for (; v < ve; ++v) {
+          const float2 a = Vr[(int64_t)v * vstride + i];
+          cmac_f(a, ts[v], pre, pim);
+          cmac_f(a, cs[v], zre, zim);
         }
       }
-      for (; v < ve; ++v) {
-        const float2 a = Vr[(int64_t)v * vstride + i];
-        cmac_f(a, ts[v], pre, pim);
-        cmac_f(a, cs[v], zre, zim);
+      if (half) {
+        op[row] = make_float2(pre, pim);
+        oz[row] = make_float2(zre, zim);
       }
+      __syncthreads();
+      if (!half && ok) {
+        const float2 a = op[row], b = oz[row];
+        const float2 q = make_float2((pre + a.x) * invf, (pim + a.y) * invf);
+        float wre = zre + b.x, wim = zim + b.y;
+        cmac_f(q, mcj, wre, wim);
+        P[i] = q;
+        Z[i] = make_float2(wre * invf, wim * invf);
+      }
+      __syncthreads();
     }
-    if (half) {
-      op[row] = make_float2(pre, pim);
-      oz[row] = make_float2(zre, zim);
-    }
-    __syncthreads();
-    if (!half && ok) {
-      const float2 a = op[row], b = oz[row];
-      const float2 q = make_float2((pre + a.x) * invf, (pim + a.y) * invf);
-      float wre = zre + b.x, wim = zim + b.y;
-      cmac_f(q, mcj, wre, wim);
-      P[i] = q;
-      Z[i] = make_float2(wre * invf, wim * invf);
-    }
-    __syncthreads();
   }
 }
 
@@ -875,20 +889,25 @@ __global__ void k_scale_to_f32(const cd* __restrict__ x, float2* __restrict__ y,
   }
 }
 
-// x[r] += sum_{i < jcount[r]} V_i[r] y_i[r]  (FP32 basis, FP64 accumulation)
+// x[r] += sum_{i < jcount[r]} V_i[r] y_i[r] with an FP32 basis: the
+// correction is summed in FP32 (the basis and the products behind it carry
+// far larger roundings) and added to x in FP64.
 __global__ void k_update_x_f32(const float2* __restrict__ V, int64_t vstride, GmresState s, cd* __restrict__ x, int R,
                                int m, int64_t N) {
   const int r = blockIdx.y;
   const int J = s.jcount[r];
   if (J == 0) return;
-  const cd* y = s.g + r * (m + 1);
+  __shared__ float2 ys[MAX_RESTART];
+  for (int v = threadIdx.x; v < J; v += blockDim.x) {
+    const cd y = s.g[r * (m + 1) + v];
+    ys[v] = make_float2((float)y.x, (float)y.y);
+  }
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    cd acc = x[(int64_t)r * N + i];
-    for (int v = 0; v < J; ++v) {
-      const float2 b = V[(int64_t)v * vstride + (int64_t)r * N + i];
-      acc = cfma(mkc((double)b.x, (double)b.y), y[v], acc);
-    }
-    x[(int64_t)r * N + i] = acc;
+    float re = 0.f, im = 0.f;
+    for (int v = 0; v < J; ++v) cmac_f(V[(int64_t)v * vstride + (int64_t)r * N + i], ys[v], re, im);
+    cd& xi = x[(int64_t)r * N + i];
+    xi = mkc(xi.x + (double)re, xi.y + (double)im);
   }
 }
 
@@ -1089,9 +1108,10 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         // reduction is amortised (a short one keeps up to nb row blocks)
         const int vper = f32b ? DOTF_VB : DOT2_VB;
         const int vg = (j + 2 + vper - 1) / vper;
-        const int nb2 = std::max(1, std::min(nb, (152 * 4 * 2 + vg * R - 1) / (vg * R)));
+        const int Rg = f32b ? std::min(R, SYS_GRID) : R;   // FP32 kernels loop over systems
+        const int nb2 = std::max(1, std::min(nb, (152 * 4 * 2 + vg * Rg - 1) / (vg * Rg)));
         if (f32b)
-          FMPB_LAUNCH("dots_dcgs2_f32", st, k_dots2_f32<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V32, vstride, j + 2, vj32, vn32, R, N, partial, partial2, s.active));
+          FMPB_LAUNCH("dots_dcgs2_f32", st, k_dots2_f32<<<dim3(nb2, vg, Rg), RED_THREADS, 0, st>>>(V32, vstride, j + 2, vj32, vn32, R, N, partial, partial2, s.active));
         else
           FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb2, (j + 2) * R, h, 0));
@@ -1099,7 +1119,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
         FMPB_LAUNCH("dcgs2_hess_t", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
         if (f32b)
-          FMPB_LAUNCH("update_dcgs2_f32", st, k_update2_f32<<<dim3(sub_blocks, R), 256, 0, st>>>(V32, vstride, j, h, cbuf, s.inv, R, N, s.active));
+          FMPB_LAUNCH("update_dcgs2_f32", st, k_update2_f32<<<dim3(sub_blocks, std::min(R, SYS_GRID)), 256, 0, st>>>(V32, vstride, j, h, cbuf, s.inv, R, N, s.active));
         else
           FMPB_LAUNCH("update_dcgs2", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
         if (j >= 1) FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, j - 1, tol));
@@ -1134,7 +1154,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
       // finish the pending column (a full cycle, or the iteration limit)
       if (any && jdone > 0) {
         if (f32b)
-          FMPB_LAUNCH("dots", st, k_dots2_f32<<<dim3(nb, (jdone + 1 + DOTF_VB - 1) / DOTF_VB, R), RED_THREADS, 0, st>>>(V32, vstride, jdone + 1, V32 + (int64_t)jdone * vstride, nullptr, R, N, partial, nullptr, s.active));
+          FMPB_LAUNCH("dots", st, k_dots2_f32<<<dim3(nb, (jdone + 1 + DOTF_VB - 1) / DOTF_VB, std::min(R, SYS_GRID)), RED_THREADS, 0, st>>>(V32, vstride, jdone + 1, V32 + (int64_t)jdone * vstride, nullptr, R, N, partial, nullptr, s.active));
         else
           FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((jdone + 1) * R, 64), 64, 0, st>>>(partial, nb, (jdone + 1) * R, h, 0));
