@@ -400,15 +400,19 @@ int64_t plan_cost(int P, int Pin, int Pout, int P1) {
 
 // Largest dynamic shared memory a two-factor pass may ask for.
 constexpr int DFT_MAX_SMEM = 200 * 1024;
+// Grid of a pass: at most this many waves of resident CTAs.
+constexpr int DFT_WAVES = 8;
 template <bool FF, int IN, int OUT>
 fmpb_status launch_dft(const char* name, const DftArgs& a, size_t smem, int threads, cudaStream_t st) {
   FMPB_CUDA((smem_limit_once<k_dft<FF, IN, OUT>>(DFT_MAX_SMEM)));
-  // persistent CTAs: as many as can be resident, each walking its share of the tiles
+  // CTAs walking their share of the tiles, DFT_WAVES times as many as can be
+  // resident: few enough to amortise the twiddle set-up, short-lived enough
+  // that a pass run beside another stream's kernels frees SM slots often
   int per_sm = 0, sms = 0, dev = 0;
   FMPB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft<FF, IN, OUT>, threads, smem));
   FMPB_CUDA(cudaGetDevice(&dev));
   FMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t grid = std::min<int64_t>(a.tiles, (int64_t)std::max(1, per_sm) * sms);
+  const int64_t grid = std::min<int64_t>(a.tiles, (int64_t)std::max(1, per_sm) * sms * DFT_WAVES);
   FMPB_LAUNCH(name, st, k_dft<FF, IN, OUT><<<(unsigned)grid, threads, smem, st>>>(a));
   FMPB_CUDA(cudaGetLastError());
   return FMPB_OK;
@@ -424,7 +428,7 @@ fmpb_status launch_direct(const char* name, const DftArgs& a, cudaStream_t st) {
   auto go = [&](auto kern) -> fmpb_status {
     int per_sm = 0;
     FMPB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
-    const int64_t grid = std::min<int64_t>((items + 255) / 256, (int64_t)std::max(1, per_sm) * sms);
+    const int64_t grid = std::min<int64_t>((items + 255) / 256, (int64_t)std::max(1, per_sm) * sms * DFT_WAVES);
     FMPB_LAUNCH(name, st, kern<<<(unsigned)grid, 256, smem, st>>>(a));
     FMPB_CUDA(cudaGetLastError());
     return FMPB_OK;

@@ -970,13 +970,17 @@ fmpb_status build_blocks(const DeviceMesh& m, const CellGrid& g, double k, cd be
   unsigned long long* near_count = near_list ? near_list + near_cap : nullptr;
   if (e == cudaSuccess) e = cudaMemsetAsync(near_count, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
-    unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 64);
+    // short-lived CTAs (about a dozen entries per thread at the headline's
+    // size): a build that runs beside a solve on a lower-priority stream
+    // frees SM slots every few microseconds, so the solve's kernels do not
+    // wait for CTAs that would otherwise hold their SMs for tens of ms
+    unsigned blocks = (unsigned)std::min<size_t>(grid_for(total, 128), (size_t)152 * 1024);
     if (beta.x == 0.0 && beta.y == 0.0) {
       FMPB_LAUNCH("build_blocks", st, k_build_blocks<false><<<blocks, 128, 0, st>>>(m.el, m.ffel, src.el, src.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, bw, m.qr, m.fc, near_list, near_count, near_cap));
-      FMPB_LAUNCH("build_near", st, k_near_entries<false><<<152 * 16, 256, 0, st>>>(m.el, src.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw, m.qr));
+      FMPB_LAUNCH("build_near", st, k_near_entries<false><<<152 * 128, 256, 0, st>>>(m.el, src.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw, m.qr));
     } else {
       FMPB_LAUNCH("build_blocks_adm", st, k_build_blocks<true><<<blocks, 128, 0, st>>>(m.el, m.ffel, src.el, src.ffel, m.n, dshift, dshiftf, ddest, n_off, zero_off, out, k, beta, bw, m.qr, m.fc, near_list, near_count, near_cap));
-      FMPB_LAUNCH("build_near_adm", st, k_near_entries<true><<<152 * 16, 256, 0, st>>>(m.el, src.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw, m.qr));
+      FMPB_LAUNCH("build_near_adm", st, k_near_entries<true><<<152 * 128, 256, 0, st>>>(m.el, src.el, m.n, dshift, ddest, near_list, near_count, near_cap, out, k, beta, bw, m.qr));
     }
     if (zero_off >= 0)
       FMPB_LAUNCH("self_terms", st, k_self_terms<<<grid_for(m.n, 64), 64, 0, st>>>(m.el, m.n, out + (size_t)dest_host[zero_off] * m.n * m.n,
