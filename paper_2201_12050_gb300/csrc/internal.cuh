@@ -89,6 +89,15 @@ __host__ __device__ __forceinline__ cd bm_entry_adm(cd D, cd H, cd S, cd K, doub
   return cadd(bm_entry(D, H, k), cmul(beta, t));
 }
 
+// The same with rk = 1 / k given (no division per entry).
+__host__ __device__ __forceinline__ cd bm_entry_rk(cd D, cd H, double rk) {
+  return mkc(-D.x + H.y * rk, -D.y - H.x * rk);
+}
+__host__ __device__ __forceinline__ cd bm_entry_adm_rk(cd D, cd H, cd S, cd K, double k, double rk, cd beta) {
+  const cd t = mkc(K.x + k * S.y, K.y - k * S.x);   // K - i k S
+  return cadd(bm_entry_rk(D, H, rk), cmul(beta, t));
+}
+
 // How a block kernel stores an entry: out = v, or out (+)= scale v (image
 // blocks of a half-space operator: R_p times the entries, added to the
 // full-space blocks when both share one block Toeplitz pattern).

@@ -260,13 +260,14 @@ __global__ void k_prepare_ff(const Elem* __restrict__ el, int n, FfElem* __restr
   }
 }
 
-// D, H (and with SK also S, K) of a far element.  ef = x - (c + shift) in
-// float-float (formed on the FP32 pipe from float-float centroids and shift;
-// about 1e-13 relative to |e| >= 4 h), dist = |e| in FP64 for the reference
-// phase.
+// D, H (and with SK also S, K) of a far element as float-float sums
+// acc = {Re D, Im D, Re H, Im H, Re S, Im S, Re K, Im K}.  ef = x - (c + shift)
+// in float-float (formed on the FP32 pipe from float-float centroids and
+// shift; about 1e-13 relative to |e| >= 4 h), dist = |e| in FP64 for the
+// reference phase.
 template <bool SK>
-__device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff nxf[3], double k, ff kf,
-                          const FfConst& C, cd& D, cd& H, cd& S, cd& K) {
+__device__ void far_sums_ff(const FfElem& F, const ff ef[3], double dist, const ff nxf[3], double k, ff kf,
+                            const FfConst& C, ff (&acc)[8]) {
   const ff rho2 = ff_dot3(ef, ef);
   const ff rho = ff_sqrt(rho2);
   const ff dny = ff_dot3(ef, F.ny);           // (x - y).n_y is constant on the flat element
@@ -334,11 +335,26 @@ __device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff
       }
     }
   }
-  D = mkc(ff_to_d(Dre), ff_to_d(Dim));
-  H = mkc(ff_to_d(Hre), ff_to_d(Him));
+  acc[0] = Dre;
+  acc[1] = Dim;
+  acc[2] = Hre;
+  acc[3] = Him;
+  acc[4] = Sre;
+  acc[5] = Sim;
+  acc[6] = Kre;
+  acc[7] = Kim;
+}
+
+template <bool SK>
+__device__ void far_dh_ff(const FfElem& F, const ff ef[3], double dist, const ff nxf[3], double k, ff kf,
+                          const FfConst& C, cd& D, cd& H, cd& S, cd& K) {
+  ff a[8];
+  far_sums_ff<SK>(F, ef, dist, nxf, k, kf, C, a);
+  D = mkc(ff_to_d(a[0]), ff_to_d(a[1]));
+  H = mkc(ff_to_d(a[2]), ff_to_d(a[3]));
   if (SK) {
-    S = mkc(ff_to_d(Sre), ff_to_d(Sim));
-    K = mkc(ff_to_d(Kre), ff_to_d(Kim));
+    S = mkc(ff_to_d(a[4]), ff_to_d(a[5]));
+    K = mkc(ff_to_d(a[6]), ff_to_d(a[7]));
   }
 }
 
@@ -363,6 +379,41 @@ __device__ void element_dh_mixed(const Elem& E, const FfElem& F, const double sh
     element_dh(E, shift, x, nx, k, qr, D, H);
 }
 
+// The block entry T (Burton-Miller combination of D and H, with SK the
+// admittance terms) of element E seen from x, dist = |x - (c + shift)| in
+// FP64 as the caller computed it, rk = 1 / k.  The far class forms the
+// rigid combination -(D + (i/k) H) in float-float and converts once; the
+// near classes and the admittance combination run in FP64.
+template <bool SK>
+__device__ cd element_entry_mixed(const Elem& E, const FfElem& F, const double shift[3], const ff shf[3],
+                                  const double x[3], const ff xf[3], const double nx[3], const ff nxf[3],
+                                  double dist, double k, ff kf, double rk, ff rkf, cd beta, const QuadRules& qr,
+                                  const FfConst& C) {
+  cd D, H, S, K;
+  if (dist >= FAR_RATIO * E.hmax) {
+    const ff ef[3] = {ff_sub(ff_sub(xf[0], F.c[0]), shf[0]), ff_sub(ff_sub(xf[1], F.c[1]), shf[1]),
+                      ff_sub(ff_sub(xf[2], F.c[2]), shf[2])};
+    ff a[8];
+    far_sums_ff<SK>(F, ef, dist, nxf, k, kf, C, a);
+    if (!SK) {
+      const ff tre = ff_sub(ff_mul(a[3], rkf), a[0]);        // -Re D + Im H / k
+      const ff tim = ff_neg(ff_add(a[1], ff_mul(a[2], rkf)));  // -(Im D + Re H / k)
+      return mkc(ff_to_d(tre), ff_to_d(tim));
+    }
+    D = mkc(ff_to_d(a[0]), ff_to_d(a[1]));
+    H = mkc(ff_to_d(a[2]), ff_to_d(a[3]));
+    S = mkc(ff_to_d(a[4]), ff_to_d(a[5]));
+    K = mkc(ff_to_d(a[6]), ff_to_d(a[7]));
+    return bm_entry_adm_rk(D, H, S, K, k, rk, beta);
+  }
+  if (SK) {
+    element_dhsk(E, shift, x, nx, k, qr, D, H, S, K);
+    return bm_entry_adm_rk(D, H, S, K, k, rk, beta);
+  }
+  element_dh(E, shift, x, nx, k, qr, D, H);
+  return bm_entry_rk(D, H, rk);
+}
+
 // One thread per entry (o, i, j) of n_off blocks of n x n; block o goes to
 // out + dest[o] * n * n.  The diagonal of the zero offset is left to
 // k_self_terms.  Far-class entries are computed here; near and very-near
@@ -378,6 +429,8 @@ __global__ void k_build_blocks(const Elem* __restrict__ tel, const FfElem* __res
                                FfConst C, unsigned long long* __restrict__ near_list,
                                unsigned long long* __restrict__ near_count, unsigned long long near_cap) {
   const ff kf = ff_from_d(k);
+  const double rk = 1.0 / k;
+  const ff rkf = ff_from_d(rk);
   const size_t nn = (size_t)n * n;
   const size_t total = nn * (size_t)n_off;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -407,9 +460,8 @@ __global__ void k_build_blocks(const Elem* __restrict__ tel, const FfElem* __res
         continue;
       }
     }
-    cd D, H, S, K;
-    element_dh_mixed<SK>(Ej, fel[j], sh, shf, x, xf, nx, nxf, k, kf, qr, C, D, H, S, K);
-    bw.put(out + (size_t)dest[o] * nn + rem, SK ? bm_entry_adm(D, H, S, K, k, beta) : bm_entry(D, H, k));
+    bw.put(out + (size_t)dest[o] * nn + rem,
+           element_entry_mixed<SK>(Ej, fel[j], sh, shf, x, xf, nx, nxf, dist, k, kf, rk, rkf, beta, qr, C));
   }
 }
 
