@@ -738,7 +738,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // FP32 basis: partial sums of conj(V_v) p and (if z) conj(V_v) z for v < nvec,
 // DOTF_VB vectors per CTA; per-thread FP32 sums, FP64 across threads in a
 // fixed order.  Same partial layout as k_dots2_ff.
-constexpr int DOTF_VB = 4;
+constexpr int DOTF_VB = 8;
 // Grid extent over systems of the FP32-basis kernels, which loop over the rest.
 constexpr int SYS_GRID = 64;
 __global__ void __launch_bounds__(RED_THREADS) k_dots2_f32(const float2* __restrict__ V, int64_t vstride, int nvec,
