@@ -729,8 +729,9 @@ fmpb_status fmpb_profile_summary(char *buf, size_t len);
  * It also lists the plans the DFT-pass autotuner chose ("kernel": "dft"):
  * the first out-of-place, non-accumulating pass of each shape (device,
  * arithmetic, padded length P, inputs Pin, outputs Pout, inner extent, line
- * count) times the direct form and every split P = P1 P2 into factors of at
- * most 16 and keeps the fastest; "chosen" and "ms" name them ("direct<P>",
+ * count) times the direct form, the radix-2 form (FP32 passes of length 8,
+ * 16 or 32) and every split P = P1 P2 into factors of at most 16 and keeps
+ * the fastest; "chosen" and "ms" name them ("direct<P>", "fft2_<P>",
  * "split<P1>").  EINVAL if buf is too small. */
 fmpb_status fmpb_tuning_summary(char *buf, size_t len);
 
@@ -740,6 +741,15 @@ fmpb_status fmpb_tuning_summary(char *buf, size_t len);
  * For tests and tuning studies; the variants give the same results up to
  * FP32 accumulation order.  EINVAL outside -1..3. */
 fmpb_status fmpb_set_tile_variant(int variant);
+
+/* Forces one plan kind for every later DFT pass of the circulant products in
+ * this process, where the pass has it: 0 the direct form (inputs in
+ * registers), 1 the two-factor form with the split of fewest multiply-adds,
+ * 2 the radix-2 form (FP32 passes of length 8, 16 or 32); a pass without the
+ * requested kind takes the model's plan.  -1 restores the autotuner.  For
+ * tests and tuning studies: the plans give the same results up to rounding.
+ * EINVAL outside -1..2. */
+fmpb_status fmpb_set_dft_plan(int kind);
 
 #ifdef __cplusplus
 }

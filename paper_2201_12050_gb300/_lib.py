@@ -146,6 +146,7 @@ SIGNATURES = {
     "fmpb_profile_summary": (INT, [ctypes.c_char_p, ctypes.c_size_t]),
     "fmpb_tuning_summary": (INT, [ctypes.c_char_p, ctypes.c_size_t]),
     "fmpb_set_tile_variant": (INT, [INT]),
+    "fmpb_set_dft_plan": (INT, [INT]),
 }
 
 _lib = None

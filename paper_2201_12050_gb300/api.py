@@ -454,6 +454,11 @@ def set_tile_variant(variant: int):
     check(lib().fmpb_set_tile_variant(int(variant)))
 
 
+def set_dft_plan(kind: int):
+    """fmpb_set_dft_plan: force a DFT plan kind (0 direct, 1 two-factor, 2 radix-2) or autotune (-1)."""
+    check(lib().fmpb_set_dft_plan(int(kind)))
+
+
 def tuning_summary() -> list:
     """fmpb_tuning_summary: tile shapes chosen by the tensor-core autotuner."""
     import json

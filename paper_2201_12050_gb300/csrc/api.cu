@@ -1371,6 +1371,8 @@ fmpb_status fmpb_tuning_summary(char* buf, size_t len) {
 
 fmpb_status fmpb_set_tile_variant(int variant) { return tc_force_variant(variant); }
 
+fmpb_status fmpb_set_dft_plan(int kind) { return dft_force_plan(kind); }
+
 namespace {
 fmpb_status offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* offsets, int64_t m, int64_t k,
                              const fmpb_c64* T, int R, const fmpb_c64* x, int64_t k2, const fmpb_c64* T2,

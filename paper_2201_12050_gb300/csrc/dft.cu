@@ -49,6 +49,7 @@ namespace {
 
 constexpr int DFT_R = 16;          // longest factor held in registers
 constexpr int DFT_THREADS = 256;
+constexpr int DFT_WAVES = 8;       // grid of a pass: at most this many waves of resident CTAs
 
 template <bool FF>
 using DVal = typename std::conditional<FF, float4, float2>::type;
@@ -391,6 +392,84 @@ __global__ void __launch_bounds__(256) k_dft_direct(const DftArgs a) {
   }
 }
 
+// FP32 passes of a power-of-two length P <= 32: the whole line in
+// registers (zeros past Pin) and log2 P radix-2 decimation-in-frequency
+// stages, which leave X_f in bit-reversed order: register k holds X_f with
+// f the LG-bit reversal of k, and the first Pout are stored.  P/2 log2 P
+// butterflies per line against Pin Pout complex multiply-adds of the direct
+// form (80 against 512 for the 16 -> 32 forward pass).  Twiddles w^m from
+// shared memory (broadcast reads); every register index is a compile-time
+// constant.
+__host__ __device__ constexpr int ilog2(int p) { return p <= 1 ? 0 : 1 + ilog2(p / 2); }
+
+template <int IN, int OUT, int P>
+__global__ void __launch_bounds__(256) k_dft_fft2(const DftArgs a) {
+  static_assert(P >= 2 && P <= 32 && (P & (P - 1)) == 0, "radix-2 lengths 2..32");
+  constexpr int LG = ilog2(P);
+  using S = typename DIn<IN>::T;
+  __shared__ float2 tw[P];   // w^m, m < P
+  for (int m = threadIdx.x; m < P; m += blockDim.x) tw[m] = twiddle<false>(m, P, a.sign);
+  __syncthreads();
+  const S* in = reinterpret_cast<const S*>(a.in);
+  const int64_t items = (int64_t)a.O1 * a.O2 * a.I;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = g % a.I, og = g / a.I;
+    const int o2 = (int)(og % a.O2), o1 = (int)(og / a.O2);
+    const S* src = in + o1 * a.a1 + o2 * a.a2 + i;
+    float2 v[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      v[j] = j < a.Pin ? from_stored<IN, false>(src[(int64_t)j * a.aj]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int sg = 0; sg < LG; ++sg) {
+      const int h = P >> (sg + 1), m = 2 * h, step = 1 << sg;   // span m, twiddle w^(t step)
+#pragma unroll
+      for (int k = 0; k < P; k += m)
+#pragma unroll
+        for (int t = 0; t < h; ++t) {
+          const float2 u = v[k + t], x = v[k + t + h];
+          v[k + t] = make_float2(u.x + x.x, u.y + x.y);
+          float2 d = make_float2(u.x - x.x, u.y - x.y);
+          if (t != 0) {
+            const float2 w = tw[t * step];
+            d = make_float2(fmaf(w.x, d.x, -w.y * d.y), fmaf(w.x, d.y, w.y * d.x));
+          }
+          v[k + t + h] = d;
+        }
+    }
+    const int64_t dst = o1 * a.b1 + o2 * a.b2 + i;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int f = (int)(__brev((unsigned)k) >> (32 - LG));
+      if (f < a.Pout) dstore<false, OUT>(a.out, dst + (int64_t)f * a.bf, v[k], a.scale, a.accumulate);
+    }
+  }
+}
+
+template <int IN, int OUT>
+fmpb_status launch_fft2(const char* name, const DftArgs& a, cudaStream_t st) {
+  const int64_t items = (int64_t)a.O1 * a.O2 * a.I;
+  int sms = 0, dev = 0;
+  FMPB_CUDA(cudaGetDevice(&dev));
+  FMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  auto go = [&](auto kern) -> fmpb_status {
+    int per_sm = 0;
+    FMPB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+    const int64_t grid = std::min<int64_t>((items + 255) / 256, (int64_t)std::max(1, per_sm) * sms * DFT_WAVES);
+    FMPB_LAUNCH(name, st, kern<<<(unsigned)grid, 256, 0, st>>>(a));
+    FMPB_CUDA(cudaGetLastError());
+    return FMPB_OK;
+  };
+  switch (a.P) {
+    case 8: return go(k_dft_fft2<IN, OUT, 8>);
+    case 16: return go(k_dft_fft2<IN, OUT, 16>);
+    case 32: return go(k_dft_fft2<IN, OUT, 32>);
+    default: break;
+  }
+  set_error("dft_pass: no radix-2 pass of length %d", a.P);
+  return FMPB_EINVAL;
+}
+
 // complex multiply-adds of a plan (stage A + twiddles + stage B)
 int64_t plan_cost(int P, int Pin, int Pout, int P1) {
   const int P2 = P / P1;
@@ -400,8 +479,6 @@ int64_t plan_cost(int P, int Pin, int Pout, int P1) {
 
 // Largest dynamic shared memory a two-factor pass may ask for.
 constexpr int DFT_MAX_SMEM = 200 * 1024;
-// Grid of a pass: at most this many waves of resident CTAs.
-constexpr int DFT_WAVES = 8;
 template <bool FF, int IN, int OUT>
 fmpb_status launch_dft(const char* name, const DftArgs& a, size_t smem, int threads, cudaStream_t st) {
   FMPB_CUDA((smem_limit_once<k_dft<FF, IN, OUT>>(DFT_MAX_SMEM)));
@@ -462,18 +539,29 @@ bool dft_supported(int P) {
 }
 
 // One plan of a pass: kind 0 = the direct form, kind 1 = the two-factor
-// form with the split P1.
+// form with the split P1, kind 2 = the radix-2 form (FP32, P a power of two
+// up to 32).
 struct DftPlan {
   int kind, P1;
 };
+bool fft2_ok(bool ff_arith, int P) { return !ff_arith && (P == 8 || P == 16 || P == 32); }
+const char* plan_name(int kind) { return kind == 0 ? "direct" : (kind == 1 ? "split" : "fft2_"); }
 
 static fmpb_status run_plan(const char* name, const DftPlan& plan, bool ff_arith, int in_fmt, int out_fmt,
                             DftArgs a, cudaStream_t st) {
   const int P = a.P, Pin = a.Pin;
   const int64_t I = a.I;
   const int O1 = a.O1, O2 = a.O2;
-  a.P1 = plan.kind == 0 ? P : plan.P1;
+  a.P1 = plan.kind == 1 ? plan.P1 : P;
   a.P2 = P / a.P1;
+  if (plan.kind == 2) {
+    if (in_fmt == DFT_CD && out_fmt == DFT_F32) return launch_fft2<DFT_CD, DFT_F32>(name, a, st);
+    if (in_fmt == DFT_F32 && out_fmt == DFT_F32) return launch_fft2<DFT_F32, DFT_F32>(name, a, st);
+    if (in_fmt == DFT_F32 && out_fmt == DFT_CD) return launch_fft2<DFT_F32, DFT_CD>(name, a, st);
+    if (in_fmt == DFT_FF && out_fmt == DFT_F32) return launch_fft2<DFT_FF, DFT_F32>(name, a, st);
+    set_error("dft_pass: unsupported storage formats %d -> %d", in_fmt, out_fmt);
+    return FMPB_EINVAL;
+  }
   if (plan.kind == 0) {
     if (ff_arith) {
       if (in_fmt == DFT_CD && out_fmt == DFT_FF) return launch_direct<true, DFT_CD, DFT_FF>(name, a, st);
@@ -549,11 +637,12 @@ struct DftKey {
 struct DftTuned {
   DftPlan plan;
   int n;
-  DftPlan cand[DFT_R + 1];
-  float ms[DFT_R + 1];
+  DftPlan cand[DFT_R + 2];
+  float ms[DFT_R + 2];
 };
 std::mutex g_dft_mu;
 std::map<DftKey, DftTuned> g_dft_tune;
+int g_dft_forced = -1;   // >= 0: fmpb_set_dft_plan override (plan kind)
 
 fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
                      int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
@@ -595,11 +684,25 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   if (ff_arith ? (P / P1 == 1 && direct_ok) : direct_ok) model = DftPlan{0, P};
   if (P / P1 == 1 && !direct_ok) model = DftPlan{1, P1};
   // candidates
-  DftPlan cand[DFT_R + 1];
+  DftPlan cand[DFT_R + 2];
   int nc = 0;
   if (direct_ok) cand[nc++] = DftPlan{0, P};
+  if (fft2_ok(ff_arith, P)) cand[nc++] = DftPlan{2, P};
   for (int p1 = 2; p1 <= DFT_R && p1 < P; ++p1)
     if (P % p1 == 0 && P / p1 <= DFT_R && nc <= DFT_R) cand[nc++] = DftPlan{1, p1};
+  int forced = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_dft_mu);
+    forced = g_dft_forced;
+  }
+  if (forced >= 0) {
+    // the requested kind where the pass has it, else the model's plan
+    DftPlan f = model;
+    if (forced == 0 && direct_ok) f = DftPlan{0, P};
+    if (forced == 1 && P / P1 > 1) f = DftPlan{1, P1};
+    if (forced == 2 && fft2_ok(ff_arith, P)) f = DftPlan{2, P};
+    return run_plan(name, f, ff_arith, in_fmt, out_fmt, a, st);
+  }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   FMPB_CUDA(cudaStreamIsCapturing(st, &cap));
   if (in == out || accumulate || cap != cudaStreamCaptureStatusNone || nc < 2)
@@ -651,6 +754,16 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   return run_plan(name, chosen, ff_arith, in_fmt, out_fmt, a, st);
 }
 
+fmpb_status dft_force_plan(int kind) {
+  if (kind < -1 || kind > 2) {
+    set_error("set_dft_plan: plan kind %d outside -1..2", kind);
+    return FMPB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_dft_mu);
+  g_dft_forced = kind;
+  return FMPB_OK;
+}
+
 void dft_tuning_summary(std::string& out) {
   std::lock_guard<std::mutex> lk(g_dft_mu);
   char buf[256];
@@ -661,11 +774,11 @@ void dft_tuning_summary(std::string& out) {
                      "%s{\"kernel\": \"dft\", \"device\": %d, \"arith\": \"%s\", \"P\": %d, \"Pin\": %d, "
                      "\"Pout\": %d, \"inner\": %lld, \"lines\": %lld, \"chosen\": \"%s%d\", \"ms\": {",
                      out.size() > 1 ? ", " : "", k.dev, k.ff ? "ff" : "f32", k.P, k.Pin, k.Pout, (long long)k.I,
-                     (long long)k.lines, t.plan.kind == 0 ? "direct" : "split", t.plan.kind == 0 ? k.P : t.plan.P1);
+                     (long long)k.lines, plan_name(t.plan.kind), t.plan.kind == 1 ? t.plan.P1 : k.P);
     out.append(buf, n);
     for (int c = 0; c < t.n; ++c) {
-      n = snprintf(buf, sizeof(buf), "%s\"%s%d\": %.4f", c ? ", " : "", t.cand[c].kind == 0 ? "direct" : "split",
-                   t.cand[c].kind == 0 ? k.P : t.cand[c].P1, t.ms[c]);
+      n = snprintf(buf, sizeof(buf), "%s\"%s%d\": %.4f", c ? ", " : "", plan_name(t.cand[c].kind),
+                   t.cand[c].kind == 1 ? t.cand[c].P1 : k.P, t.ms[c]);
       out.append(buf, n);
     }
     out += "}}";

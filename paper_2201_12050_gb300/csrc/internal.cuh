@@ -289,6 +289,9 @@ bool dft_supported(int P);
 // arithmetic; in place needs in == out with equal strides and Pin = Pout = P.
 // Appends the DFT autotuner's choices as JSON objects (comma-separated) to out.
 void dft_tuning_summary(std::string& out);
+// Forces one plan kind of every DFT pass (0 direct, 1 two-factor, 2 radix-2)
+// where the pass has it, or restores the autotuner (-1).
+fmpb_status dft_force_plan(int kind);
 fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
                      int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
                      int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st);

@@ -137,6 +137,28 @@ def test_circulant_f32_product_equals_explicit_block_toeplitz(counts, B, R):
     assert _rel(y0.cpu().numpy(), ref + x) < 1e-5
 
 
+@pytest.fixture
+def dft_plan(request):
+    gb.set_dft_plan(request.param)
+    yield request.param
+    gb.set_dft_plan(-1)
+
+
+@pytest.mark.parametrize("dft_plan", [0, 1, 2], indirect=True)
+@pytest.mark.parametrize("counts,B,R", [((16, 1, 3), 9, 9), ((16, 2, 1), 5, 3), ((3, 16, 1), 7, 2)])
+def test_circulant_f32_every_plan_kind(counts, B, R, dft_plan):
+    # every plan kind of the FP32 passes forced in turn, on grids whose 16-cell
+    # axes pad to P = 32 (the radix-2 form's length), against the exact product
+    offs = bem.all_offsets(counts)
+    blocks = random_complex_vectors(1200 + B, len(offs), B * B).reshape(len(offs), B, B)
+    ncell = int(np.prod(counts))
+    x = random_complex_vectors(2200 + R, R, ncell * B)
+    spec = gb.circulant_spectrum(counts, _dev(blocks))
+    y = gb.circulant_apply_f32(counts, spec, _dev(x)).cpu().numpy()
+    ref = bem.toeplitz_matvec(dict(zip(offs, blocks)), counts, x)
+    assert _rel(y, ref) < 1e-5
+
+
 def test_circulant_long_axis_without_a_short_split():
     # P = 245 = 5 * 7 * 7 has no split into two factors of at most 16: the
     # float-float product takes the direct pass, the FP32 one is refused
