@@ -352,6 +352,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       atomicOr(err, 1u);
     }
   } else {
+    // output column of every tile column (-1: outside the grid), decoded
+    // once per CTA into the first stage's shared memory (the main loop has
+    // finished with it) instead of per thread and column in the stores
+    const int Nc = Mx * My * Mz;
+    int64_t* colj = reinterpret_cast<int64_t*>(smem_raw + (sbase - raw));
+    for (int col = tid; col < bk.rows; col += TC_THREADS) {
+      int q = col;
+      const int cx = x0 + q % bk.bx;
+      q /= bk.bx;
+      const int cy = y0 + q % bk.by;
+      q /= bk.by;
+      const int cz = z0 + q % bk.bz;
+      const int r = r0 + q / bk.bz;
+      colj[col] = (cx < Mx && cy < My && cz < Mz && r < R)
+                      ? (int64_t)r * Nc + ((int64_t)cz * My + cy) * Mx + cx
+                      : (int64_t)-1;
+    }
+    __syncthreads();
     tc_fence_after();
     const int quarter = warp & 3, half = warp >> 2;
     const int64_t gm = (int64_t)m0 + (MT == 2 ? half * TC_BM : 0) + quarter * 32 + lane;
@@ -363,7 +381,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int cbeg = MT == 2 ? 0 : half * (BNC / 2);
     const int cend = MT == 2 ? ((half == 0 || two) ? bk.n : 0) : min(bk.n, cbeg + BNC / 2);
     const uint32_t tcol = MT == 2 ? (uint32_t)(half * BNC) : 0u;
-    const int Nc = Mx * My * Mz;
     const int64_t yoff = (int64_t)blk * ncols * m;
 #pragma unroll 1
     for (int c0 = cbeg; c0 < cend; c0 += 16) {
@@ -374,15 +391,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = 0; t < 16; ++t) {
           const int col = c0 + t;
           if (col >= bk.rows) break;
-          int q = col;
-          const int cx = x0 + q % bk.bx;
-          q /= bk.bx;
-          const int cy = y0 + q % bk.by;
-          q /= bk.by;
-          const int cz = z0 + q % bk.bz;
-          const int r = r0 + q / bk.bz;
-          if (cx < Mx && cy < My && cz < Mz && r < R) {
-            const int64_t e = yoff + ((int64_t)r * Nc + ((int64_t)cz * My + cy) * Mx + cx) * m + i;
+          const int64_t jc = colj[col];
+          if (jc >= 0) {
+            const int64_t e = yoff + jc * m + i;
             if (out_f32) {
               float* d = reinterpret_cast<float*>(reinterpret_cast<float2*>(y_) + e) + part;
               *d = accumulate ? *d + v[t] : v[t];
