@@ -23,6 +23,8 @@
 // operator's spectrum are stored as float-float (16 bytes per complex value,
 // the size of complex double); inputs and outputs of the product are complex
 // double.
+#include <utility>
+
 #include "common.cuh"
 #include "internal.cuh"
 #include "profile.cuh"
@@ -217,10 +219,10 @@ static fmpb_status dft_axis(const char* name, const void* in, void* out, int O1,
 static fmpb_status axis_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out,
                              int O1, int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2,
                              int64_t bf, int Pin, int Pout, int P, int sign, double scale, bool accumulate,
-                             cudaStream_t st) {
+                             cudaStream_t st, int64_t row_b = 0, int row_kh = 0) {
   if (dft_supported(P))
     return dft_pass(name, ff_arith, in_fmt, out_fmt, in, out, O1, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign,
-                    scale, accumulate, st);
+                    scale, accumulate, st, row_b, row_kh);
   if (ff_arith) {
     if (in_fmt == DFT_CD && out_fmt == DFT_FF)
       return dft_axis<false, true>(name, in, out, O1, O2, I, a1, a2, aj, b1, b2, bf, Pin, Pout, P, sign, scale,
@@ -593,7 +595,7 @@ static fmpb_status launch_block_product_tiled(const void* spec, const XT* X, XT*
 static fmpb_status block_product(const void* spec, int spec_format, const void* Xv, void* Yv, int64_t F,
                                  int64_t B, int R, cudaStream_t st, void* tc_rows, unsigned* tc_err,
                                  bool f32_io = false, const void* const* spec_batch = nullptr, int n_ops = 1,
-                                 const int* batch_blk = nullptr, int n_blocks = 0) {
+                                 const int* batch_blk = nullptr, int n_blocks = 0, bool rows_ready = false) {
   if (spec_batch) {
     const int nb = n_blocks > 0 ? n_blocks : n_ops;
     if (spec_format != SPEC_BF16 || n_ops < 1 || nb < n_ops || R % nb || !tc_rows || !tc_err) {
@@ -607,10 +609,12 @@ static fmpb_status block_product(const void* spec, int spec_format, const void* 
     const __nv_bfloat16* A[TC_MAX_BATCH];
     for (int o = 0; o < n_ops; ++o) A[o] = reinterpret_cast<const __nv_bfloat16*>(spec_batch[o]);
     __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tc_rows);
-    if (f32_io)
+    if (rows_ready) {
+    } else if (f32_io) {
       FMPB_TRY(tc_rows_from_f32(reinterpret_cast<const float2*>(Xv), F * R, B, rows, st));
-    else
+    } else {
       FMPB_TRY(tc_rows_from_ff(reinterpret_cast<const float4*>(Xv), F * R, B, rows, st));
+    }
     return tc_freq_gemm_batch(A, n_ops, F, B, R / nb, rows, Yv, tc_err, st, f32_io, batch_blk, nb);
   }
   if (F > 65535) {
@@ -630,7 +634,7 @@ static fmpb_status block_product(const void* spec, int spec_format, const void* 
         return FMPB_EINVAL;
       }
       __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tc_rows);
-      FMPB_TRY(tc_rows_from_f32(X2, F * R, B, rows, st));
+      if (!rows_ready) FMPB_TRY(tc_rows_from_f32(X2, F * R, B, rows, st));
       return tc_freq_gemm(reinterpret_cast<const __nv_bfloat16*>(spec), F, B, R, rows, Y2, tc_err, st, true);
     }
     if (R >= 8) return launch_block_product_tiled<false, float2>(spec, X2, Y2, F, B, R, st);
@@ -704,25 +708,43 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
   void* buf[2] = {sb, sb + (size_t)s.F * RB * vb};
   const int mid = ffa ? DFT_FF : DFT_F32;
   const int io = ff_io ? DFT_FF : DFT_CD;
+  // FP32 passes ahead of tensor-core products: the last forward pass writes
+  // the BF16 rows of the products itself (no FP32 frequency values and no
+  // conversion pass); row f R + r holds the B values of (f, r)
+  const int last = Pz > 1 ? 2 : (Py > 1 ? 1 : 0);
+  const int lastP = s.P[last], lastM = s.M[last];
+  const bool rows = !ffa && spec_format == SPEC_BF16 && tc_rows && dft_supported(lastP) &&
+                    dft_rows_ok(lastP, lastM);
+  const int row_kh = (int)(tc_depth(B) / 2);
+  auto fwd_out = [&](int axis, int cur_fmt, void* dst) -> std::pair<int, void*> {
+    return rows && axis == last ? std::make_pair((int)DFT_BF16R, tc_rows) : std::make_pair(cur_fmt, dst);
+  };
   int cur = 0;
   // forward x: x[r][cz][cy][cx][b] -> [cz][cy][fx][r][b]
-  FMPB_TRY(axis_pass("dft_fwd_x", ffa, io, mid, x, buf[cur], R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
-                     (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st));
+  {
+    const auto o = fwd_out(0, mid, buf[cur]);
+    FMPB_TRY(axis_pass("dft_fwd_x", ffa, io, o.first, x, o.second, R, Mz * My, B, Nc * B, (int64_t)Mx * B, B, B,
+                       (int64_t)Px * RB, RB, Mx, Px, Px, -1, 1.0, false, st, B, row_kh));
+  }
   // forward y: [cz][cy][fx][rb] -> [cz][fy][fx][rb]
   if (Py > 1) {
-    FMPB_TRY(axis_pass("dft_fwd_y", ffa, mid, mid, buf[cur], buf[1 - cur], Mz, Px, RB, (int64_t)My * Px * RB, RB,
-                       (int64_t)Px * RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st));
+    const auto o = fwd_out(1, mid, buf[1 - cur]);
+    FMPB_TRY(axis_pass("dft_fwd_y", ffa, mid, o.first, buf[cur], o.second, Mz, Px, RB, (int64_t)My * Px * RB, RB,
+                       (int64_t)Px * RB, (int64_t)Py * Px * RB, RB, (int64_t)Px * RB, My, Py, Py, -1, 1.0, false, st,
+                       B, row_kh));
     cur = 1 - cur;
   }
   // forward z: [cz][fy fx][rb] -> [fz][fy fx][rb]
   if (Pz > 1) {
-    FMPB_TRY(axis_pass("dft_fwd_z", ffa, mid, mid, buf[cur], buf[1 - cur], 1, Py * Px, RB, 0, RB,
-                       (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz, -1, 1.0, false, st));
+    const auto o = fwd_out(2, mid, buf[1 - cur]);
+    FMPB_TRY(axis_pass("dft_fwd_z", ffa, mid, o.first, buf[cur], o.second, 1, Py * Px, RB, 0, RB,
+                       (int64_t)Py * Px * RB, 0, RB, (int64_t)Py * Px * RB, Mz, Pz, Pz, -1, 1.0, false, st, B,
+                       row_kh));
     cur = 1 - cur;
   }
   // per-frequency block products: [f][r][b] -> [f][r][b]
   FMPB_TRY(block_product(spec, spec_format, buf[cur], buf[1 - cur], s.F, B, R, st, tc_rows, tc_err, !ffa,
-                         spec_batch, n_ops, batch_blk, n_blocks));
+                         spec_batch, n_ops, batch_blk, n_blocks, rows));
   cur = 1 - cur;
   // inverse z: [fz][fy fx][rb] -> [cz][fy fx][rb], cz < Mz
   if (Pz > 1) {

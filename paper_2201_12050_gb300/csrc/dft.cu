@@ -31,6 +31,8 @@
 // accuracy anyway).  In place (in == out with equal strides, Pin = Pout = P)
 // is allowed: every input of a tile is read before any output of it is
 // written.
+#include <cuda_bf16.h>
+
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -172,7 +174,20 @@ struct DftArgs {
   int O1, O2, Pin, Pout, P, P1, P2, nsub, sign, accumulate;
   double scale;
   int64_t tiles_i, tiles;
+  // DFT_BF16R output: values per row, pairs per row, and the output strides
+  // b1, b2, bf in rows (multiples of row_b)
+  int64_t row_b, b1r, b2r, bfr;
+  int row_kh;
 };
+
+// Store of value f of an item whose inner index i sits in row `rowbase`
+// (plus f bfr) at pair `col` of the BF16 rows.
+__device__ __forceinline__ void store_bf16r(const DftArgs& a, int64_t rowbase, int64_t col, int f, float2 v) {
+  __nv_bfloat162 p;
+  p.x = __float2bfloat16_rn(v.x);
+  p.y = __float2bfloat16_rn(v.y);
+  reinterpret_cast<__nv_bfloat162*>(a.out)[(rowbase + (int64_t)f * a.bfr) * a.row_kh + col] = p;
+}
 
 // Storage type of the input format (what the copies move into shared memory).
 template <int FMT>
@@ -366,6 +381,12 @@ __global__ void __launch_bounds__(256) k_dft_direct(const DftArgs a) {
 #pragma unroll
     for (int j = 0; j < MAXIN; ++j) x[j] = j < a.Pin ? from_stored<IN, FF>(src[(int64_t)j * a.aj]) : zero;
     const int64_t dst = o1 * a.b1 + o2 * a.b2 + i;
+    int64_t rowbase = 0, col = 0;
+    if constexpr (OUT == DFT_BF16R) {
+      const int64_t ib = i / a.row_b;
+      rowbase = o1 * a.b1r + o2 * a.b2r + ib;
+      col = i - ib * a.row_b;
+    }
 #pragma unroll 1
     for (int f = 0; f < a.Pout; ++f) {
       const V* tr = tf + f * a.Pin;
@@ -387,7 +408,10 @@ __global__ void __launch_bounds__(256) k_dft_direct(const DftArgs a) {
           }
         v = make_float2(re, im);
       }
-      dstore<FF, OUT>(a.out, dst + (int64_t)f * a.bf, v, a.scale, a.accumulate);
+      if constexpr (OUT == DFT_BF16R)
+        store_bf16r(a, rowbase, col, f, v);
+      else
+        dstore<FF, OUT>(a.out, dst + (int64_t)f * a.bf, v, a.scale, a.accumulate);
     }
   }
 }
@@ -438,10 +462,21 @@ __global__ void __launch_bounds__(256) k_dft_fft2(const DftArgs a) {
         }
     }
     const int64_t dst = o1 * a.b1 + o2 * a.b2 + i;
+    int64_t rowbase = 0, col = 0;
+    if constexpr (OUT == DFT_BF16R) {
+      const int64_t ib = i / a.row_b;
+      rowbase = o1 * a.b1r + o2 * a.b2r + ib;
+      col = i - ib * a.row_b;
+    }
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       const int f = (int)(__brev((unsigned)k) >> (32 - LG));
-      if (f < a.Pout) dstore<false, OUT>(a.out, dst + (int64_t)f * a.bf, v[k], a.scale, a.accumulate);
+      if (f < a.Pout) {
+        if constexpr (OUT == DFT_BF16R)
+          store_bf16r(a, rowbase, col, f, v[k]);
+        else
+          dstore<false, OUT>(a.out, dst + (int64_t)f * a.bf, v[k], a.scale, a.accumulate);
+      }
     }
   }
 }
@@ -555,6 +590,8 @@ static fmpb_status run_plan(const char* name, const DftPlan& plan, bool ff_arith
   a.P1 = plan.kind == 1 ? plan.P1 : P;
   a.P2 = P / a.P1;
   if (plan.kind == 2) {
+    if (in_fmt == DFT_F32 && out_fmt == DFT_BF16R) return launch_fft2<DFT_F32, DFT_BF16R>(name, a, st);
+    if (in_fmt == DFT_CD && out_fmt == DFT_BF16R) return launch_fft2<DFT_CD, DFT_BF16R>(name, a, st);
     if (in_fmt == DFT_CD && out_fmt == DFT_F32) return launch_fft2<DFT_CD, DFT_F32>(name, a, st);
     if (in_fmt == DFT_F32 && out_fmt == DFT_F32) return launch_fft2<DFT_F32, DFT_F32>(name, a, st);
     if (in_fmt == DFT_F32 && out_fmt == DFT_CD) return launch_fft2<DFT_F32, DFT_CD>(name, a, st);
@@ -569,6 +606,8 @@ static fmpb_status run_plan(const char* name, const DftPlan& plan, bool ff_arith
       if (in_fmt == DFT_FF && out_fmt == DFT_CD) return launch_direct<true, DFT_FF, DFT_CD>(name, a, st);
       if (in_fmt == DFT_CD && out_fmt == DFT_CD) return launch_direct<true, DFT_CD, DFT_CD>(name, a, st);
     } else {
+      if (in_fmt == DFT_F32 && out_fmt == DFT_BF16R) return launch_direct<false, DFT_F32, DFT_BF16R>(name, a, st);
+      if (in_fmt == DFT_CD && out_fmt == DFT_BF16R) return launch_direct<false, DFT_CD, DFT_BF16R>(name, a, st);
       if (in_fmt == DFT_CD && out_fmt == DFT_F32) return launch_direct<false, DFT_CD, DFT_F32>(name, a, st);
       if (in_fmt == DFT_F32 && out_fmt == DFT_F32) return launch_direct<false, DFT_F32, DFT_F32>(name, a, st);
       if (in_fmt == DFT_F32 && out_fmt == DFT_CD) return launch_direct<false, DFT_F32, DFT_CD>(name, a, st);
@@ -644,9 +683,18 @@ std::mutex g_dft_mu;
 std::map<DftKey, DftTuned> g_dft_tune;
 int g_dft_forced = -1;   // >= 0: fmpb_set_dft_plan override (plan kind)
 
+bool dft_rows_ok(int P, int Pin) { return Pin <= 32 || fft2_ok(false, P); }
+
 fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
                      int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
-                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st) {
+                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st,
+                     int64_t row_b, int row_kh) {
+  const bool rows = out_fmt == DFT_BF16R;
+  if (rows && (ff_arith || accumulate || row_b < 1 || row_kh < row_b || b1 % row_b || b2 % row_b || bf % row_b ||
+               !dft_rows_ok(P, Pin))) {
+    set_error("dft_pass: BF16 rows take an FP32 direct or radix-2 pass whose output strides are whole rows");
+    return FMPB_EINVAL;
+  }
   int P1 = 0;
   if (!dft_plan(P, Pin, Pout, &P1)) {
     set_error("dft_pass: axis length %d has no split into two factors of at most %d", P, DFT_R);
@@ -678,6 +726,13 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   a.sign = sign;
   a.accumulate = accumulate ? 1 : 0;
   a.scale = scale;
+  if (rows) {
+    a.row_b = row_b;
+    a.row_kh = row_kh;
+    a.b1r = b1 / row_b;
+    a.b2r = b2 / row_b;
+    a.bfr = bf / row_b;
+  }
   // the model's plan
   const bool direct_ok = ff_arith ? Pin <= 16 : Pin <= 32;
   DftPlan model{1, P1};
@@ -688,8 +743,9 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
   int nc = 0;
   if (direct_ok) cand[nc++] = DftPlan{0, P};
   if (fft2_ok(ff_arith, P)) cand[nc++] = DftPlan{2, P};
-  for (int p1 = 2; p1 <= DFT_R && p1 < P; ++p1)
+  for (int p1 = 2; p1 <= DFT_R && p1 < P && !rows; ++p1)
     if (P % p1 == 0 && P / p1 <= DFT_R && nc <= DFT_R) cand[nc++] = DftPlan{1, p1};
+  if (rows) model = direct_ok ? DftPlan{0, P} : DftPlan{2, P};
   int forced = -1;
   {
     std::lock_guard<std::mutex> lk(g_dft_mu);
@@ -699,7 +755,7 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
     // the requested kind where the pass has it, else the model's plan
     DftPlan f = model;
     if (forced == 0 && direct_ok) f = DftPlan{0, P};
-    if (forced == 1 && P / P1 > 1) f = DftPlan{1, P1};
+    if (forced == 1 && P / P1 > 1 && !rows) f = DftPlan{1, P1};
     if (forced == 2 && fft2_ok(ff_arith, P)) f = DftPlan{2, P};
     return run_plan(name, f, ff_arith, in_fmt, out_fmt, a, st);
   }

@@ -280,7 +280,10 @@ inline cudaError_t smem_limit_once(int bytes) {
 
 // Pruned DFT passes (dft.cu): storage formats of the values a pass reads and
 // writes (complex double, float-float pairs, complex FP32).
-enum DftFormat { DFT_CD = 0, DFT_FF = 1, DFT_F32 = 2 };
+enum DftFormat { DFT_CD = 0, DFT_FF = 1, DFT_F32 = 2, DFT_BF16R = 3 };
+// DFT_BF16R (output only, FP32 passes): the values as the BF16 rows of the
+// tensor-core products, value e = row B + b at pair b of row `row`
+// (row_kh pairs per row; pairs b >= B are left untouched).
 // True if an axis of padded length P splits into two factors of at most 16
 // (every P up to 256 of the 2,3,5,7-smooth lengths the engine uses except a
 // few, such as 245).
@@ -294,7 +297,11 @@ void dft_tuning_summary(std::string& out);
 fmpb_status dft_force_plan(int kind);
 fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, const void* in, void* out, int O1,
                      int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
-                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st);
+                     int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st,
+                     int64_t row_b = 0, int row_kh = 0);
+// True if a forward FP32 pass of this length can write DFT_BF16R rows (the
+// direct or the radix-2 form).
+bool dft_rows_ok(int P, int Pin);
 
 // Circulant engine (circulant.cu)
 // In-place forward DFT over the padded grid of F slots, each holding `inner`

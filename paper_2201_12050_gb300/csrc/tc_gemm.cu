@@ -1105,7 +1105,9 @@ fmpb_status launch_freq(const TcBatch& A, int64_t F, int64_t B, int R, const __n
     for (int o = 0; o < A.n; ++o) FMPB_TRY(encode_map(&maps.a[o], A.A[o], 2, dims, strides, box));
   }
   {
-    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)(F * ctot)};
+    // the rows' real extent is 2 B values: the padding up to Kp reads as zero
+    // from the copy engine, so whoever writes the rows may leave it untouched
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * B), (cuuint64_t)(F * ctot)};
     const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
     const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)bn_rows};
     FMPB_TRY(encode_map(&maps.x, X, 2, dims, strides, box));
