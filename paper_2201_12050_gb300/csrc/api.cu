@@ -285,9 +285,13 @@ struct fmpb_operator {
     else
       FMPB_TRY(tc_rows_to_bf16(reinterpret_cast<const cd*>(x), (int64_t)R * Nc, n, xb, st));
     FMPB_TRY(tc_offset_gemm(V0b, zero, B, n, shape.M, R, xb, Mom, false, tc_err, st));
+    // local expansions straight into the BF16 rows of the L2P tail where the
+    // FP32 passes can write them
+    const bool p32 = circulant_f32_ok(shape);
+    const bool lrows = p32 && dft_rows_ok(shape.P[0], shape.P[0]);
     FMPB_TRY(circulant_apply(shape, B, reinterpret_cast<const cd*>(specb), R, Mom, Loc, false, scratch, st,
-                             SPEC_BF16, fb, tc_err, false, circulant_f32_ok(shape)));
-    FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
+                             SPEC_BF16, fb, tc_err, false, p32, nullptr, 1, nullptr, 0, lrows ? lb : nullptr));
+    if (!lrows) FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)R * Nc, B, lb, st));
     const __nv_bfloat16* sb1[1] = {Sb};
     const __nv_bfloat16* ub1[1] = {U0b};
     return tc_offset_gemm_batch(sb1, 1, near_tc, n, n, shape.M, R, xb, y, false, tc_err, st, nullptr, ub1, B, lb,
@@ -1030,9 +1034,11 @@ static fmpb_status batch_matvec_tc(const fmpb_operator* const* ops, int n_ops, i
   else
     FMPB_TRY(tc_rows_to_bf16(reinterpret_cast<const cd*>(x), (int64_t)Rt * Nc, n, xb, st));
   FMPB_TRY(tc_offset_gemm_batch(V0b, na, zero, B, n, a->shape.M, R, xb, Mom, false, err, st, blk));
-  FMPB_TRY(circulant_apply(a->shape, B, nullptr, Rt, Mom, Loc, false, sc.p, st, SPEC_BF16, fb, err, false,
-                           circulant_f32_ok(a->shape), sp, na, blk, n_ops));
-  FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)Rt * Nc, B, lb, st));
+  const bool p32 = circulant_f32_ok(a->shape);
+  const bool lrows = p32 && dft_rows_ok(a->shape.P[0], a->shape.P[0]);
+  FMPB_TRY(circulant_apply(a->shape, B, nullptr, Rt, Mom, Loc, false, sc.p, st, SPEC_BF16, fb, err, false, p32, sp,
+                           na, blk, n_ops, lrows ? lb : nullptr));
+  if (!lrows) FMPB_TRY(tc_rows_to_bf16(Loc, (int64_t)Rt * Nc, B, lb, st));
   FMPB_TRY(tc_offset_gemm_batch(Sb, na, a->near_tc, n, n, a->shape.M, R, xb, y, false, err, st, blk, U0b, B, lb,
                                 y_f32));
   return FMPB_OK;

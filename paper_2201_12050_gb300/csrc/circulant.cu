@@ -689,7 +689,7 @@ size_t circulant_scratch_elems(const CircShape& s, int64_t B, int R) { return 2 
 fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R, const cd* x, cd* y,
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format, void* tc_rows,
                             unsigned* tc_err, bool ff_io, bool f32_passes, const void* const* spec_batch,
-                            int n_ops, const int* batch_blk, int n_blocks) {
+                            int n_ops, const int* batch_blk, int n_blocks, void* y_rows) {
   const int Mx = s.M[0], My = s.M[1], Mz = s.M[2];
   const int Px = s.P[0], Py = s.P[1], Pz = s.P[2];
   const int64_t RB = (int64_t)R * B;
@@ -759,6 +759,16 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
     cur = 1 - cur;
   }
   // inverse x with crop and 1/F: [cz][cy][fx][r][b] -> y[r][cz][cy][cx][b]
+  // (or straight into the BF16 rows of a tensor-core product, row r Nc + c)
+  if (y_rows) {
+    if (ffa || accumulate || !dft_supported(Px) || !dft_rows_ok(Px, Px)) {
+      set_error("circulant_apply: BF16 result rows take FP32 passes without accumulation");
+      return FMPB_EINVAL;
+    }
+    FMPB_TRY(axis_pass("dft_inv_x", ffa, mid, DFT_BF16R, buf[cur], y_rows, R, Mz * My, B, B, (int64_t)Px * RB, RB,
+                       Nc * B, (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, false, st, B, row_kh));
+    return FMPB_OK;
+  }
   FMPB_TRY(axis_pass("dft_inv_x", ffa, mid, io, buf[cur], y, R, Mz * My, B, B, (int64_t)Px * RB, RB, Nc * B,
                      (int64_t)Mx * B, B, Px, Mx, Px, +1, 1.0 / (double)s.F, accumulate, st));
   return FMPB_OK;

@@ -183,9 +183,10 @@ struct DftArgs {
 // Store of value f of an item whose inner index i sits in row `rowbase`
 // (plus f bfr) at pair `col` of the BF16 rows.
 __device__ __forceinline__ void store_bf16r(const DftArgs& a, int64_t rowbase, int64_t col, int f, float2 v) {
+  const float sc = (float)a.scale;
   __nv_bfloat162 p;
-  p.x = __float2bfloat16_rn(v.x);
-  p.y = __float2bfloat16_rn(v.y);
+  p.x = __float2bfloat16_rn(v.x * sc);
+  p.y = __float2bfloat16_rn(v.y * sc);
   reinterpret_cast<__nv_bfloat162*>(a.out)[(rowbase + (int64_t)f * a.bfr) * a.row_kh + col] = p;
 }
 

@@ -299,8 +299,8 @@ fmpb_status dft_pass(const char* name, bool ff_arith, int in_fmt, int out_fmt, c
                      int O2, int64_t I, int64_t a1, int64_t a2, int64_t aj, int64_t b1, int64_t b2, int64_t bf,
                      int Pin, int Pout, int P, int sign, double scale, bool accumulate, cudaStream_t st,
                      int64_t row_b = 0, int row_kh = 0);
-// True if a forward FP32 pass of this length can write DFT_BF16R rows (the
-// direct or the radix-2 form).
+// True if an FP32 pass of length P with Pin inputs can write DFT_BF16R rows
+// (the direct or the radix-2 form).
 bool dft_rows_ok(int P, int Pin);
 
 // Circulant engine (circulant.cu)
@@ -320,7 +320,11 @@ fmpb_status circulant_apply(const CircShape& s, int64_t B, const cd* spec, int R
                             bool accumulate, cd* scratch, cudaStream_t st, int spec_format = SPEC_CD,
                             void* tc_rows = nullptr, unsigned* tc_err = nullptr, bool ff_io = false,
                             bool f32_passes = false, const void* const* spec_batch = nullptr, int n_ops = 1,
-                            const int* batch_blk = nullptr, int n_blocks = 0);
+                            const int* batch_blk = nullptr, int n_blocks = 0, void* y_rows = nullptr);
+// y_rows (FP32 passes, not accumulating): the result as the BF16 rows of a
+// tensor-core product instead of y, row r Nc + c holding the B values of
+// cell c of right-hand side r (tc_depth(B) / 2 pairs per row, the padding
+// untouched); y is then not written.
 // spec_batch: the products of several operators of one shape in one pass
 // sequence (BF16 spectra only).  R counts the right-hand sides of n_blocks
 // operator blocks (R / n_blocks each, block b's after those of b - 1); the

@@ -791,7 +791,9 @@ fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bflo
     for (int o = 0; o < A.n; ++o) FMPB_TRY(encode_map(&maps.a[o], A.A[o], 2, dims, strides, box));
   }
   {
-    const cuuint64_t dims[5] = {(cuuint64_t)Kp, (cuuint64_t)M[0], (cuuint64_t)M[1], (cuuint64_t)M[2],
+    // the rows' real extent: their padding up to Kp reads as zero from the
+    // copy engine, so whoever writes them may leave it untouched
+    const cuuint64_t dims[5] = {(cuuint64_t)(A.kx > 0 ? A.kx : Kp), (cuuint64_t)M[0], (cuuint64_t)M[1], (cuuint64_t)M[2],
                                 (cuuint64_t)R * A.nblk};
     const cuuint64_t strides[4] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * M[0], (cuuint64_t)Kp * 2 * M[0] * M[1],
                                    (cuuint64_t)Kp * 2 * M[0] * M[1] * M[2]};
@@ -807,7 +809,7 @@ fmpb_status launch_tma(const TcBatch& A, int64_t Mp, int64_t Kp, const __nv_bflo
     const cuuint64_t astrides[1] = {(cuuint64_t)Kp2 * 2};
     const cuuint32_t abox[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
     for (int o = 0; o < A.n; ++o) FMPB_TRY(encode_map(&maps.a2[o], tail->A[o], 2, adims, astrides, abox));
-    const cuuint64_t dims[5] = {(cuuint64_t)Kp2, (cuuint64_t)M[0], (cuuint64_t)M[1], (cuuint64_t)M[2],
+    const cuuint64_t dims[5] = {(cuuint64_t)(2 * tail->k), (cuuint64_t)M[0], (cuuint64_t)M[1], (cuuint64_t)M[2],
                                 (cuuint64_t)R * A.nblk};
     const cuuint64_t strides[4] = {(cuuint64_t)Kp2 * 2, (cuuint64_t)Kp2 * 2 * M[0],
                                    (cuuint64_t)Kp2 * 2 * M[0] * M[1], (cuuint64_t)Kp2 * 2 * M[0] * M[1] * M[2]};
@@ -985,6 +987,7 @@ fmpb_status tc_offset_gemm_batch(const __nv_bfloat16* const* Aops, int n_ops, co
     A.blk[o] = blk ? blk[o] : o;
     A.nblk = std::max(A.nblk, A.blk[o] + 1);
   }
+  A.kx = 2 * k;
   const int64_t Mp = tc_rows(m), Kp = tc_depth(k);
   const int64_t Nc = (int64_t)M[0] * M[1] * M[2];
   const int64_t ncols = Nc * R;

@@ -24,6 +24,7 @@ struct TcBatch {
   const __nv_bfloat16* A[TC_MAX_BATCH];
   int blk[TC_MAX_BATCH];   // operator q's column block in X and y (q itself unless a subset runs)
   int nblk;                // column blocks in X and y
+  int64_t kx;              // values of a row of X that hold data (2 k); the rest of its depth reads as zero
 };
 
 // Shapes of the realified operands of a complex m x k block.
