@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-case", default=None,
-                    choices=["product", "build", "near", "batch", "gmres", "barrier", "admittance", "fmm2"],
+                    choices=["product", "build", "near", "batch", "batch_full", "solve_bf16", "gmres", "barrier",
+                             "admittance", "fmm2"],
                     help="small case for kernel captures: product/build = 3x8 cylinders (1.8 GB spectrum) at "
                          "500 Hz; near = 32x32 sphere array FMM; batch = 8x8x4 cube lattice, 64 RHS, BF16; gmres = 320 "
                          "Arnoldi steps of the full crystal at 300 Hz")
@@ -1443,7 +1444,9 @@ def run_profile_case(args):
     product/build: 3 x 8 cylinders at 500 Hz (PBEM, spectrum 1.84 GB), one build
     and 4 products; near: the 32 x 32 sphere array (FMM form), one build and 3
     products; batch: 8 x 8 x 4 cubes, BF16 (tensor-core) FMM operator, 3 products
-    of 64 right-hand sides; barrier: the half-space cylinder barrier (FMM form,
+    of 64 right-hand sides (batch_full: the 16 x 16 x 4 lattice, about 4 GB);
+    solve_bf16: the 8 x 8 x 4 BF16 operator's 64-RHS solve, 60 iterations on
+    the FP32 Krylov basis; barrier: the half-space cylinder barrier (FMM form,
     block Hankel image part), one build and 3 products; fmm2: the 5 x 10 fine
     spheres in the FMPBEM2 form, one build and 3 products; admittance: the 3 x 8
     cylinders at 500 Hz with beta = 0.4 + 0.2i, one build.  Prints one JSON
@@ -1495,7 +1498,19 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "admittance", "N": op.N, "F": op.info["F"]}))
         return
-    if args.profile_case in ("near", "batch"):
+    if args.profile_case == "solve_bf16":
+        # 8 x 8 x 4 cubes, BF16 operator, 64 right-hand sides, GMRES(30) toward
+        # 1e-3 for 60 iterations on the FP32 Krylov basis (1.76 GB)
+        w2 = WORKLOADS["cube_lattice_16x16x4"]
+        v2, t2 = w2.mesh()
+        op = gb.Operator(v2, t2, (8, 8, 4), w2.lattice, w2.wavenumbers[3], form=gb.FORM_FMM, n_t=12,
+                         precision=gb.BF16)
+        b = op.rhs_plane_wave(w2.directions)
+        p, info = op.solve(b, tol=1e-3, restart=30, maxit=60, raise_on_noconv=False)
+        print(json.dumps({"profile_case": args.profile_case, "N": op.N, "R": b.shape[0],
+                          "iters": max(i["iters"] for i in info)}))
+        return
+    if args.profile_case in ("near", "batch", "batch_full"):
         if args.profile_case == "near":
             w2 = WORKLOADS["sphere_array_32x32"]
             v2, t2 = w2.mesh()
@@ -1504,7 +1519,8 @@ def run_profile_case(args):
         else:
             w2 = WORKLOADS["cube_lattice_16x16x4"]
             v2, t2 = w2.mesh()
-            op = gb.Operator(v2, t2, (8, 8, 4), w2.lattice, w2.wavenumbers[3], form=gb.FORM_FMM, n_t=12,
+            counts = w2.counts if args.profile_case == "batch_full" else (8, 8, 4)
+            op = gb.Operator(v2, t2, counts, w2.lattice, w2.wavenumbers[3], form=gb.FORM_FMM, n_t=12,
                              precision=gb.BF16)
             x = op.rhs_plane_wave(w2.directions)
         y = torch.empty_like(x)
