@@ -728,8 +728,10 @@ fmpb_status fmpb_profile_summary(char *buf, size_t len);
  * the order 128x256, 256x256, 256x128, 128x128); "kernel": "tc_gemm".
  * It also lists the plans the DFT-pass autotuner chose ("kernel": "dft"):
  * the first out-of-place, non-accumulating pass of each shape (device,
- * arithmetic, padded length P, inputs Pin, outputs Pout, inner extent, line
- * count) times the direct form, the radix-2 form (FP32 passes of length 8,
+ * arithmetic and storage formats, padded length P, inputs Pin, outputs Pout;
+ * its inner extent and line count are reported, but later passes of the
+ * shape take its plan whatever theirs, so that operators batched together
+ * round as they do alone) times the direct form, the radix-2 form (FP32 passes of length 8,
  * 16 or 32) and every split P = P1 P2 into factors of at most 16 and keeps
  * the fastest; "chosen" and "ms" name them ("direct<P>", "fft2_<P>",
  * "split<P1>").  EINVAL if buf is too small. */

@@ -666,12 +666,16 @@ static fmpb_status run_plan(const char* name, const DftPlan& plan, bool ff_arith
 // a stream capture and shapes with one candidate take the model's plan
 // (fewest multiply-adds; the direct form for FP32 lines of at most 32
 // inputs).
+// The key is the line shape and arithmetic only: every later pass of that
+// shape, whatever its inner extent and line count, takes the plan its first
+// timed pass chose, so that operators batched together round exactly as
+// they do alone (the inner extent and line count of that first pass are
+// kept for the summary).
 struct DftKey {
   int dev, ff, in, out, P, Pin, Pout;
   int64_t I, lines;
   bool operator<(const DftKey& o) const {
-    return std::tie(dev, ff, in, out, P, Pin, Pout, I, lines) <
-           std::tie(o.dev, o.ff, o.in, o.out, o.P, o.Pin, o.Pout, o.I, o.lines);
+    return std::tie(dev, ff, in, out, P, Pin, Pout) < std::tie(o.dev, o.ff, o.in, o.out, o.P, o.Pin, o.Pout);
   }
 };
 struct DftTuned {
