@@ -629,7 +629,9 @@ def run_serving(gb, reqs, precision, snap_hz=None, tol=TOL):
 def serving_section(gb, n_sample=24):
     """The serving runtime on the first n_sample sphere-cell requests of the
     seeded stream (Poisson arrivals at 50 req/s, grids 4x4..64x8, 100-2000 Hz,
-    1-16 plane waves) at their arrival times, plain FP64 operators: a bounded
+    1-16 plane waves) at their arrival times, plain FP64 operators, and the
+    same requests with MIXED operators (BF16 tensor-core inner products,
+    float-float outer residuals, the same 1e-8 tolerance) in "mixed": a bounded
     sample for the default run.  The study with both cells (the capped
     cylinders take the PBEM form with spectra up to 44 GB), plain FP64 beside
     MIXED and the 10 Hz-snapped cache variant is `--serving N`."""
@@ -637,6 +639,7 @@ def serving_section(gb, n_sample=24):
     reqs = [r for r in serving_stream(400) if r["cell"] == "sphere"][:n_sample]
     out = run_serving(gb, reqs, gb.FP64)
     out["sample"] = f"first {n_sample} sphere-cell requests of the seeded 50 req/s stream, FP64"
+    out["mixed"] = _guarded(run_serving, gb, reqs, gb.MIXED)
     return out
 
 
