@@ -55,6 +55,19 @@ def test_argument_errors_are_statuses_not_crashes(L):
     L.fmpb_operator_destroy(None)
 
 
+def test_plan_overrides_check_their_range(L):
+    # the tile-variant and DFT-plan overrides are host-side settings: valid
+    # values (and -1, back to the autotuners) are accepted without a GPU, the
+    # rest are FMPB_EINVAL with a message
+    for kind in (0, 1, 2, -1):
+        assert L.fmpb_set_dft_plan(kind) == 0
+    for bad in (3, -2):
+        assert L.fmpb_set_dft_plan(bad) == -1 and b"plan kind" in L.fmpb_last_error()
+    for v in (0, 3, -1):
+        assert L.fmpb_set_tile_variant(v) == 0
+    assert L.fmpb_set_tile_variant(4) == -1
+
+
 def test_server_reports_missing_device_as_status(L):
     import torch
     if torch.cuda.is_available():
