@@ -517,11 +517,31 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots2_ff(const float4* __restri
 // One warp per rhs: beta, the final column j - 1 (hc, raw copy in Hraw,
 // subdiagonal in wnorm) and the update coefficients c.  t = hA[0..j-1],
 // pp = hA[j], b = hB[0..j-1], pz = hB[j].
-__global__ void k_dcgs_coef(GmresState s, const cd* __restrict__ hA, const cd* __restrict__ hB,
+// With part_p (and part_z) given, the warp first reduces its system's
+// projection partials into hA[0..j+1] and hB[0..j] in the fixed order of
+// k_reduce_partials (two launches fewer per step); stopped systems are left
+// out, and nothing downstream reads their entries.
+__global__ void k_dcgs_coef(GmresState s, cd* __restrict__ hA, cd* __restrict__ hB,
                             const cd* __restrict__ sprev, cd* __restrict__ hc, cd* __restrict__ cbuf,
-                            cd* __restrict__ Hraw, double* __restrict__ wnorm, int R, int m, int j) {
+                            cd* __restrict__ Hraw, double* __restrict__ wnorm, int R, int m, int j,
+                            const cd* __restrict__ part_p = nullptr, const cd* __restrict__ part_z = nullptr,
+                            int nblk = 0) {
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (r >= R || !s.active[r]) return;
+  if (part_p) {
+    for (int v = lane; v < j + 2; v += 32) {
+      const int64_t e = (int64_t)v * R + r;
+      cd a = mkc(0.0, 0.0);
+      for (int b = 0; b < nblk; ++b) a = cadd(a, part_p[e * nblk + b]);
+      hA[e] = a;
+      if (v < j + 1) {
+        cd z = mkc(0.0, 0.0);
+        for (int b = 0; b < nblk; ++b) z = cadd(z, part_z[e * nblk + b]);
+        hB[e] = z;
+      }
+    }
+    __syncwarp();
+  }
   double tt = 0.0, tbr = 0.0, tbi = 0.0;
   for (int v = lane; v < j; v += 32) {
     const cd t = hA[v * R + r], b = hB[v * R + r];
@@ -1114,9 +1134,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
           FMPB_LAUNCH("dots_dcgs2_f32", st, k_dots2_f32<<<dim3(nb2, vg, Rg), RED_THREADS, 0, st>>>(V32, vstride, j + 2, vj32, vn32, R, N, partial, partial2, s.active));
         else
           FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
-        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 2) * R, 64), 64, 0, st>>>(partial, nb2, (j + 2) * R, h, 0));
-        FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((j + 1) * R, 64), 64, 0, st>>>(partial2, nb2, (j + 1) * R, hB, 0));
-        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j));
+        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j, partial, partial2, nb2));
         FMPB_LAUNCH("dcgs2_hess_t", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
         if (f32b)
           FMPB_LAUNCH("update_dcgs2_f32", st, k_update2_f32<<<dim3(sub_blocks, std::min(R, SYS_GRID)), 256, 0, st>>>(V32, vstride, j, h, cbuf, s.inv, R, N, s.active));
