@@ -139,31 +139,36 @@ __device__ __forceinline__ ffc ffc_shfl_up(ffc a, int off) {
           {__shfl_up_sync(0xffffffffu, a.im.h, off), __shfl_up_sync(0xffffffffu, a.im.l, off)}};
 }
 
-__global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* __restrict__ wnorm, int R, int m,
-                         int j, double tol) {
-  const int r = blockIdx.x, lane = threadIdx.x;
+constexpr int GIV_WARPS = 4;   // warps of a k_givens CTA (one CTA per system)
+__global__ void __launch_bounds__(32 * GIV_WARPS) k_givens(GmresState s, const cd* __restrict__ h,
+                                                           const double* __restrict__ wnorm, int R, int m, int j,
+                                                           double tol) {
+  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NT = 32 * GIV_WARPS;
   if (!s.active[r]) return;
-  if (lane == 0) s.iters[r] += 1;
+  if (tid == 0) s.iters[r] += 1;
   __shared__ ffc col[MAX_RESTART + 1];
   __shared__ ff csv[MAX_RESTART];
   __shared__ ffc snv[MAX_RESTART];
-  for (int i = lane; i <= j; i += 32) col[i] = ffc_from_cd(h[i * R + r]);
-  for (int i = lane; i < j; i += 32) {
+  __shared__ ffc wal[GIV_WARPS], wbe[GIV_WARPS];   // each warp's composed map
+  for (int i = tid; i <= j; i += NT) col[i] = ffc_from_cd(h[i * R + r]);
+  for (int i = tid; i < j; i += NT) {
     csv[i] = ff_from_d(s.cs[r * m + i]);
     snv[i] = ffc_from_cd(s.sn[r * m + i]);
   }
-  __syncwarp();
+  __syncthreads();
   // [c  s; -conj(s) c] applied to (a_i, h_{i+1}) for i < j, a_0 = h_0: the
   // rotated entry is c_i a_i + s_i h_{i+1} and the carried one
-  // a_{i+1} = -conj(s_i) a_i + c_i h_{i+1}, an affine recurrence.  Each lane
-  // composes the maps of one chunk of ceil(j/32) rotations, a shuffle scan
-  // gives every lane the value entering its chunk, and each lane then
-  // rotates its chunk: sequential depth about 2 j / 32 + 5 instead of j.
+  // a_{i+1} = -conj(s_i) a_i + c_i h_{i+1}, an affine recurrence.  Each of
+  // the 128 threads composes the maps of one chunk of ceil(j/128) rotations;
+  // a shuffle scan within each warp and the composed warp maps give every
+  // thread the value entering its chunk, and each thread then rotates its
+  // chunk: sequential depth about 2 j / 128 + 9 instead of j.
   cd* Hcol = s.H + ((int64_t)r * m + j) * (m + 1);
   __shared__ ffc carry;
   {
-    const int L = (j + 31) / 32;
-    const int i0 = min(j, lane * L), i1 = min(j, i0 + L);
+    const int L = (j + NT - 1) / NT;
+    const int i0 = min(j, tid * L), i1 = min(j, i0 + L);
     const ffc one = {ff_make(1.f), ff_make(0.f)}, zero = {ff_make(0.f), ff_make(0.f)};
     ffc al = one, be = zero;   // chunk map z -> al z + be
     for (int i = i0; i < i1; ++i) {
@@ -171,16 +176,23 @@ __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* _
       be = ffc_add(ffc_mul(ai, be), ffc_scale(col[i + 1], csv[i]));
       al = ffc_mul(ai, al);
     }
-    for (int off = 1; off < 32; off <<= 1) {   // inclusive scan: later map after earlier
+    for (int off = 1; off < 32; off <<= 1) {   // inclusive scan within the warp: later map after earlier
       const ffc pa = ffc_shfl_up(al, off), pb = ffc_shfl_up(be, off);
       if (lane >= off) {
         be = ffc_add(ffc_mul(al, pb), be);
         al = ffc_mul(al, pa);
       }
     }
+    if (lane == 31) {
+      wal[warp] = al;
+      wbe[warp] = be;
+    }
+    __syncthreads();
+    // the value entering this warp: the maps of the warps before it applied to a_0
+    ffc aw = col[0];
+    for (int u = 0; u < warp; ++u) aw = ffc_add(ffc_mul(wal[u], aw), wbe[u]);
     const ffc pa = ffc_shfl_up(al, 1), pb = ffc_shfl_up(be, 1);
-    const ffc a0 = col[0];
-    ffc a = lane == 0 ? a0 : ffc_add(ffc_mul(pa, a0), pb);
+    ffc a = lane == 0 ? aw : ffc_add(ffc_mul(pa, aw), pb);
     for (int i = i0; i < i1; ++i) {
       const ff c = csv[i];
       const ffc sn = snv[i];
@@ -188,9 +200,10 @@ __global__ void k_givens(GmresState s, const cd* __restrict__ h, const double* _
       Hcol[i] = ffc_to_cd(ffc_add(ffc_scale(a, c), ffc_mul(sn, b)));
       a = ffc_sub(ffc_scale(b, c), ffc_mul(ffc_conj(sn), a));
     }
-    if ((i0 < i1 && i1 == j) || (j == 0 && lane == 0)) carry = a;
+    if ((i0 < i1 && i1 == j) || (j == 0 && tid == 0)) carry = a;
   }
-  __syncwarp();
+  __syncthreads();
+  if (warp != 0) return;
   __shared__ cd top;
   if (lane == 0) {
     cd ad = ffc_to_cd(carry);
@@ -1140,7 +1153,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
           FMPB_LAUNCH("update_dcgs2_f32", st, k_update2_f32<<<dim3(sub_blocks, std::min(R, SYS_GRID)), 256, 0, st>>>(V32, vstride, j, h, cbuf, s.inv, R, N, s.active));
         else
           FMPB_LAUNCH("update_dcgs2", st, k_update2_ff<<<dim3(sub_blocks, R), 256, 0, st>>>(V, vstride, j, h, cbuf, s.inv, R, N, s.active));
-        if (j >= 1) FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, j - 1, tol));
+        if (j >= 1) FMPB_LAUNCH("givens", st, k_givens<<<R, 32 * GIV_WARPS, 0, st>>>(s, hc, wnorm, R, m, j - 1, tol));
         FMPB_CUDA(cudaGetLastError());
         ++total_it;
         // The host looks at the convergence flags only every `block`
@@ -1177,7 +1190,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
           FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((jdone + 1) * R, 64), 64, 0, st>>>(partial, nb, (jdone + 1) * R, h, 0));
         FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
-        FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, hc, wnorm, R, m, jdone - 1, tol));
+        FMPB_LAUNCH("givens", st, k_givens<<<R, 32 * GIV_WARPS, 0, st>>>(s, hc, wnorm, R, m, jdone - 1, tol));
         FMPB_CUDA(cudaGetLastError());
       }
     } else {
@@ -1205,7 +1218,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         // h += h2 and ||w|| where the second pass ran; normalise
         FMPB_LAUNCH("sqrt_real", st, k_finish<<<grid_for(R, 4), 128, 0, st>>>(pnorm, (int)sub_blocks, nrm2, need, h2, h, j + 1, wnorm, s.inv, R));
         FMPB_LAUNCH("scale", st, k_scale_ff<<<dim3(vec_blocks, R), 256, 0, st>>>(vn, s.inv, R, N, s.active));
-        FMPB_LAUNCH("givens", st, k_givens<<<R, 32, 0, st>>>(s, h, wnorm, R, m, j, tol));
+        FMPB_LAUNCH("givens", st, k_givens<<<R, 32 * GIV_WARPS, 0, st>>>(s, h, wnorm, R, m, j, tol));
         FMPB_CUDA(cudaGetLastError());
         ++total_it;
         // The host looks at the convergence flags only every `block`
