@@ -311,7 +311,7 @@ def run_ours(args):
     # dominant kernel of the timed steps
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     total_prof = sum(v_[1] for v_ in prof.values())
-    roof = dominant_roofline(dom, prof, w, v, t, args.steps, hbm_peak, peaks, bp_gbs, bp_ms / bp_launches)
+    roof = dominant_roofline(dom, prof, w, v, t, args.steps, hbm_peak, peaks, bp_gbs, bp_ms / bp_launches, B, F)
 
     sections = rank == 0 and not args.only_headline
     fmm = fmm_section(gb, torch, stream) if sections else None
@@ -1157,7 +1157,13 @@ def quadrature_points(w, v, t):
     return int(total)
 
 
-def dominant_roofline(dom, prof, w, v, t, steps, hbm_peak, peaks, bp_gbs, bp_ms_per_launch):
+# DRAM bytes per frequency of the float-float block product with B = 1200 and
+# one right-hand side, measured with ncu (see dominant_roofline)
+BP_TRAFFIC_SHAPE = (1200, 1)
+BP_TRAFFIC_PER_FREQUENCY = (1729498624 + 3911424) / 75
+
+
+def dominant_roofline(dom, prof, w, v, t, steps, hbm_peak, peaks, bp_gbs, bp_ms_per_launch, B=0, F=0):
     name, (launches, total_ms) = dom
     per_launch_s = total_ms / launches / 1e3
     if name == "build_blocks":
@@ -1172,9 +1178,14 @@ def dominant_roofline(dom, prof, w, v, t, steps, hbm_peak, peaks, bp_gbs, bp_ms_
                 "peak_source": "nominal FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)"}
     if name == "block_product":
         # achieved from the product loop on one operator (the timed steps
-        # overlap the next build, which shares the SMs with these launches)
+        # overlap the next build, which shares the SMs with these launches);
+        # traffic: DRAM bytes per frequency of k_block_product_ff<1,1> from an
+        # ncu capture of `--profile-case product` (B = 1200, one right-hand
+        # side, 75 frequencies: 1,729,498,624 read + 3,911,424 written), scaled
+        # by the frequencies of a launch (every frequency streams its own block)
+        traffic = (BP_TRAFFIC_PER_FREQUENCY * F if (B, len(w.directions)) == BP_TRAFFIC_SHAPE else None)
         return {"kernel": name, "bound": "hbm", "achieved": bp_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": bp_gbs / hbm_peak, "traffic": None, "launches": launches,
+                "frac": bp_gbs / hbm_peak, "traffic": traffic, "launches": launches,
                 "ms_per_launch": bp_ms_per_launch, "ms_per_launch_in_timed_steps": per_launch_s * 1e3,
                 "peak_source": "measured hbm_gbs"}
     return {"kernel": name, "bound": "unmodelled", "launches": launches, "ms_per_launch": per_launch_s * 1e3,
