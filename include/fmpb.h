@@ -521,8 +521,10 @@ fmpb_status fmpb_m2l_blocks(double k, int n_t, int n_d, const double *dvecs, fmp
  * numbers as 2 x 2 real blocks) with FP32 accumulation; y is complex double.
  * So the result equals the exact product of the rounded inputs up to FP32
  * accumulation error.  Allocates its BF16 copies of T and x per call and
- * synchronises the stream.  FMPB_ECUDA if a bounded wait in the kernel gave
- * up (see fmpb_operator_check).
+ * synchronises the stream.  FMPB_EINVAL, before any device call, for m or k
+ * outside 1..2^20, R outside 1..4096, counts outside 1..4096, more than 2^30
+ * cells or more than 65,535 x 128 columns (cells x R); FMPB_ECUDA if a
+ * bounded wait in the kernel gave up (see fmpb_operator_check).
  */
 fmpb_status fmpb_offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t *offsets,
                                   int64_t m, int64_t k, const fmpb_c64 *T, int R, const fmpb_c64 *x,
@@ -553,6 +555,8 @@ fmpb_status fmpb_circulant_shape(const int32_t counts[3], int32_t P[3], int64_t 
  *   blocks  device, (2M_x-1)(2M_y-1)(2M_z-1) x B x B, offsets ordered with
  *           delta_x fastest, each from 1-M_a to M_a-1.
  *   spec    device, F x B x B (frequency-major).
+ * FMPB_EINVAL, before any device call, for B outside 1..2^20, counts outside
+ * 1..4096, more than 2^24 cells, or F B^2 values beyond 2^59.
  */
 fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fmpb_c64 *blocks,
                                     fmpb_c64 *spec, void *stream);

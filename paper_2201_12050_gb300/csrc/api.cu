@@ -71,6 +71,10 @@ static fmpb_status make_grid(const fmpb_lattice* lat, CellGrid& g) {
 
 template <typename T>
 static fmpb_status dev_alloc(T** p, size_t count, size_t& bytes) {
+  if (count > SIZE_MAX / sizeof(T)) {
+    set_error("cannot allocate %zu elements of %zu bytes on the device", count, sizeof(T));
+    return FMPB_ENOMEM;
+  }
   cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1351,13 +1355,21 @@ fmpb_status fmpb_m2l_blocks(double k, int n_t, int n_d, const double* dvecs, fmp
 
 fmpb_status fmpb_circulant_spectrum(const int32_t counts[3], int64_t B, const fmpb_c64* blocks, fmpb_c64* spec,
                                     void* stream) {
-  CHECK_ARG(counts && blocks && spec && B >= 1, "circulant_spectrum: bad arguments");
+  CHECK_ARG(counts && blocks && spec && B >= 1 && B <= (1 << 20), "circulant_spectrum: bad arguments");
   int M[3];
+  int64_t nc = 1;
   for (int a = 0; a < 3; ++a) {
     CHECK_ARG(counts[a] >= 1 && counts[a] <= 4096, "circulant_spectrum: count out of range");
     M[a] = counts[a];
+    nc *= M[a];
   }
-  return circulant_spectrum_from_blocks(make_shape(M), B, (const cd*)blocks, (cd*)spec, (cudaStream_t)stream);
+  // (2M-1)^3 <= 8 x cells offsets are listed on the host; the F B^2 spectrum
+  // values must be addressable in bytes
+  CHECK_ARG(nc <= (1 << 24), "circulant_spectrum: too many cells (%lld)", (long long)nc);
+  const CircShape sh = make_shape(M);
+  CHECK_ARG((size_t)sh.F * (size_t)B <= ((size_t)1 << 59) / (size_t)B,
+            "circulant_spectrum: %lld frequencies x B^2 = %lld^2 is too large", (long long)sh.F, (long long)B);
+  return circulant_spectrum_from_blocks(sh, B, (const cd*)blocks, (cd*)spec, (cudaStream_t)stream);
 }
 
 fmpb_status fmpb_tuning_summary(char* buf, size_t len) {
@@ -1400,6 +1412,11 @@ fmpb_status offset_gemm_bf16(const int32_t counts[3], int n_off, const int32_t* 
     M[a] = counts[a];
     Nc *= M[a];
   }
+  // the launch limits of the tensor-core product, checked before the sizes
+  // of the device copies below are formed: at most 2^30 cells and 65,535
+  // column tiles of 128 (cells x right-hand sides)
+  CHECK_ARG(Nc <= (1 << 30) && (Nc * R + 127) / 128 <= 65535,
+            "offset_gemm_bf16: %lld cells x %d right-hand sides exceed the launch limit", (long long)Nc, R);
   TcOffsets offs{};
   offs.n = n_off;
   for (int i = 0; i < n_off; ++i)

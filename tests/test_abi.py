@@ -68,6 +68,34 @@ def test_plan_overrides_check_their_range(L):
     assert L.fmpb_set_tile_variant(4) == -1
 
 
+def test_product_sizes_are_checked_before_device_calls(L):
+    # sizes whose device copies would not be addressable are refused on the
+    # host, before any device call; the dummy pointers are never touched, so
+    # the check runs only where no GPU is visible
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    dummy = ctypes.c_void_p(256)
+    big = (ctypes.c_int32 * 3)(4096, 4096, 4096)
+    one = (ctypes.c_int32 * 3)(1, 1, 1)
+    off = (ctypes.c_int32 * 3)(0, 0, 0)
+    # 2^36 cells x 4096 right-hand sides x 2^21 BF16 values wraps in 64 bits
+    assert L.fmpb_offset_gemm_bf16(big, 1, off, 64, 1 << 20, dummy, 4096, dummy, ctypes.c_void_p(512), 0,
+                                   None) == -1
+    assert b"launch limit" in L.fmpb_last_error()
+    assert L.fmpb_offset_gemm2_bf16(big, 1, off, 64, 64, dummy, 1, dummy, 64, dummy, dummy,
+                                    ctypes.c_void_p(512), 0, None) == -1
+    assert b"launch limit" in L.fmpb_last_error()
+    # one column tile too many: 65,535 x 128 + 1 columns
+    cols = (ctypes.c_int32 * 3)(65535 * 128 // 4096 + 1, 1, 1)
+    assert L.fmpb_offset_gemm_bf16(cols, 1, off, 64, 64, dummy, 4096, dummy, ctypes.c_void_p(512), 0,
+                                   None) == -1
+    # B^2 x 16 bytes wraps for B = 2^32; too many cells for the offset list
+    for counts, B in ((one, 1 << 32), (one, (1 << 20) + 1), (big, 4)):
+        assert L.fmpb_circulant_spectrum(counts, B, dummy, ctypes.c_void_p(512), None) == -1
+        assert b"circulant_spectrum" in L.fmpb_last_error()
+
+
 def test_server_reports_missing_device_as_status(L):
     import torch
     if torch.cuda.is_available():
