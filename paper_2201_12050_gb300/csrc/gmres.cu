@@ -527,34 +527,45 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots2_ff(const float4* __restri
   }
 }
 
-// One warp per rhs: beta, the final column j - 1 (hc, raw copy in Hraw,
+// One CTA per rhs: beta, the final column j - 1 (hc, raw copy in Hraw,
 // subdiagonal in wnorm) and the update coefficients c.  t = hA[0..j-1],
 // pp = hA[j], b = hB[0..j-1], pz = hB[j].
-// With part_p (and part_z) given, the warp first reduces its system's
-// projection partials into hA[0..j+1] and hB[0..j] in the fixed order of
-// k_reduce_partials (two launches fewer per step); stopped systems are left
-// out, and nothing downstream reads their entries.
-__global__ void k_dcgs_coef(GmresState s, cd* __restrict__ hA, cd* __restrict__ hB,
-                            const cd* __restrict__ sprev, cd* __restrict__ hc, cd* __restrict__ cbuf,
-                            cd* __restrict__ Hraw, double* __restrict__ wnorm, int R, int m, int j,
-                            const cd* __restrict__ part_p = nullptr, const cd* __restrict__ part_z = nullptr,
-                            int nblk = 0) {
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (r >= R || !s.active[r]) return;
+// With part_p (and part_z) given, the CTA's threads first reduce the system's
+// projection partials into hA[0..j+1] and hB[0..j], one entry per thread,
+// each summed over its nblk row blocks in the fixed order of
+// k_reduce_partials (loads issued eight at a time, so that a long basis does
+// not wait on one L2 round trip per partial); then its first warp does the
+// rest.  Stopped systems are left out, and nothing downstream reads their
+// entries.
+constexpr int COEF_THREADS = 256;
+__global__ void __launch_bounds__(COEF_THREADS) k_dcgs_coef(GmresState s, cd* __restrict__ hA, cd* __restrict__ hB,
+                                                             const cd* __restrict__ sprev, cd* __restrict__ hc,
+                                                             cd* __restrict__ cbuf, cd* __restrict__ Hraw,
+                                                             double* __restrict__ wnorm, int R, int m, int j,
+                                                             const cd* __restrict__ part_p = nullptr,
+                                                             const cd* __restrict__ part_z = nullptr, int nblk = 0) {
+  const int r = blockIdx.x, lane = threadIdx.x & 31;
+  if (!s.active[r]) return;   // uniform over the CTA
   if (part_p) {
-    for (int v = lane; v < j + 2; v += 32) {
-      const int64_t e = (int64_t)v * R + r;
+    const int na = j + 2;
+    for (int it = threadIdx.x; it < na + j + 1; it += blockDim.x) {
+      const bool isz = it >= na;
+      const int64_t e = (int64_t)(isz ? it - na : it) * R + r;
+      const cd* src = (isz ? part_z : part_p) + e * nblk;
       cd a = mkc(0.0, 0.0);
-      for (int b = 0; b < nblk; ++b) a = cadd(a, part_p[e * nblk + b]);
-      hA[e] = a;
-      if (v < j + 1) {
-        cd z = mkc(0.0, 0.0);
-        for (int b = 0; b < nblk; ++b) z = cadd(z, part_z[e * nblk + b]);
-        hB[e] = z;
+      for (int b = 0; b < nblk; b += 8) {
+        cd x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = b + u < nblk ? src[b + u] : mkc(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (b + u < nblk) a = cadd(a, x[u]);
       }
+      (isz ? hB : hA)[e] = a;
     }
-    __syncwarp();
+    __syncthreads();
   }
+  if (threadIdx.x >= 32) return;
   double tt = 0.0, tbr = 0.0, tbi = 0.0;
   for (int v = lane; v < j; v += 32) {
     const cd t = hA[v * R + r], b = hB[v * R + r];
@@ -1147,7 +1158,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
           FMPB_LAUNCH("dots_dcgs2_f32", st, k_dots2_f32<<<dim3(nb2, vg, Rg), RED_THREADS, 0, st>>>(V32, vstride, j + 2, vj32, vn32, R, N, partial, partial2, s.active));
         else
           FMPB_LAUNCH("dots_dcgs2", st, k_dots2_ff<<<dim3(nb2, vg, R), RED_THREADS, 0, st>>>(V, vstride, j + 2, vj, vn, R, N, partial, partial2, s.active));
-        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j, partial, partial2, nb2));
+        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<R, COEF_THREADS, 0, st>>>(s, h, hB, sprev, hc, cbuf, Hraw, wnorm, R, m, j, partial, partial2, nb2));
         FMPB_LAUNCH("dcgs2_hess_t", st, k_hess_t<<<dim3((unsigned)((j + 1 + 7) / 8), R), 256, 0, st>>>(s.active, Hraw, h, cbuf, s.inv, sprev, R, m, j));
         if (f32b)
           FMPB_LAUNCH("update_dcgs2_f32", st, k_update2_f32<<<dim3(sub_blocks, std::min(R, SYS_GRID)), 256, 0, st>>>(V32, vstride, j, h, cbuf, s.inv, R, N, s.active));
@@ -1189,7 +1200,7 @@ fmpb_status gmres_solve(const MatvecFn& A, int R, int64_t N, const cd* b, cd* x,
         else
           FMPB_LAUNCH("dots", st, k_dots_ff4<<<dim3(nb, (jdone + 1 + DOT_VB - 1) / DOT_VB, R), RED_THREADS, 0, st>>>(V, vstride, jdone + 1, V + (int64_t)jdone * vstride, R, N, partial, s.active));
         FMPB_LAUNCH("reduce_partials", st, k_reduce_partials<<<grid_for((jdone + 1) * R, 64), 64, 0, st>>>(partial, nb, (jdone + 1) * R, h, 0));
-        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<grid_for(R, 4), 128, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
+        FMPB_LAUNCH("dcgs2_coef", st, k_dcgs_coef<<<R, COEF_THREADS, 0, st>>>(s, h, h, sprev, hc, cbuf, Hraw, wnorm, R, m, jdone));
         FMPB_LAUNCH("givens", st, k_givens<<<R, 32 * GIV_WARPS, 0, st>>>(s, hc, wnorm, R, m, jdone - 1, tol));
         FMPB_CUDA(cudaGetLastError());
       }
