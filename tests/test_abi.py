@@ -45,6 +45,30 @@ def test_host_only_calls(L):
     assert e.value.name == "FMPB_EINVAL"
 
 
+def test_padded_lengths_are_the_smallest_smooth_embedding_for_every_count(L):
+    # every count the library accepts: P = 1 for one cell, else the smallest
+    # 2,3,5,7-smooth P >= 2M - 1 (found here by trial division); F = P0 P1 P2
+    from paper_2201_12050_gb300 import circulant_shape, FmpbError
+
+    def smooth(n):
+        for f in (2, 3, 5, 7):
+            while n % f == 0:
+                n //= f
+        return n == 1
+
+    for M in range(1, 4097):
+        P = 1
+        if M > 1:
+            P = 2 * M - 1
+            while not smooth(P):
+                P += 1
+        got, F = circulant_shape([1, M, 1])
+        assert got == [1, P, 1] and F == P, M
+    assert circulant_shape([4096, 4096, 4096])[1] == 8192 ** 3
+    with pytest.raises(FmpbError):
+        circulant_shape([4097, 1, 1])
+
+
 def test_argument_errors_are_statuses_not_crashes(L):
     h = ctypes.c_void_p()
     st = L.fmpb_operator_create(None, 0, None, 0, None, 1.0, None, None, None)
