@@ -69,6 +69,23 @@ def test_padded_lengths_are_the_smallest_smooth_embedding_for_every_count(L):
         circulant_shape([4097, 1, 1])
 
 
+def test_spectrum_holds_at_least_the_printed_number_of_blocks(L):
+    # the spectrum of Sec. 2.4 holds (2M_x-1)(2M_y-1) blocks
+    # (tests/golden/paper_storage_counts.txt); the library pads each length
+    # to a 2,3,5,7-smooth P >= 2M - 1, so it holds exactly that many where
+    # 2M - 1 is smooth and more elsewhere
+    from paper_2201_12050_gb300 import circulant_shape
+    line = next(l for l in open(os.path.join(ROOT, "tests", "golden", "paper_storage_counts.txt"))
+                if l.startswith("spectrum_blocks"))
+    expr = line.split("|")[1].strip()
+    assert re.fullmatch(r"[0-9MxMy*()+\- ]+", expr)
+    for Mx, My in ((5, 5), (5, 10), (5, 100), (3, 20), (2, 3)):
+        printed = eval(expr, {"__builtins__": {}}, {"Mx": Mx, "My": My})
+        P, F = circulant_shape([Mx, My, 1])
+        assert F >= printed
+        assert (F == printed) == (P[0] == 2 * Mx - 1 and P[1] == 2 * My - 1)
+
+
 def test_argument_errors_are_statuses_not_crashes(L):
     h = ctypes.c_void_p()
     st = L.fmpb_operator_create(None, 0, None, 0, None, 1.0, None, None, None)
