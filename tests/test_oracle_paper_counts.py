@@ -98,3 +98,10 @@ def test_sphere_array_discretisation_matches_the_example():
         assert 5 * My * len(el) == value("array_dofs", 5, My)
     w = WORKLOADS["sphere_array_5x5_q9"]
     assert w.counts[0] == 5 and int(np.prod(w.counts)) * len(el) == value("array_dofs", 5, w.counts[1])
+    assert int(np.prod(w.counts)) * len(el) == value("array_5x5_dofs")
+    # elements with an edge on the equator z = 0, from above: one ring around
+    # the sphere (the cube-sphere's equator is a grid line for an even m)
+    zmin = np.array([nodes[e, 2].min() for e in el])
+    ring = np.sum(np.abs(zmin) < 1e-12)
+    assert ring == value("sphere_circumference")
+    assert np.allclose(np.linalg.norm(nodes, axis=1), 0.1)
