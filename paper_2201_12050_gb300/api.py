@@ -404,6 +404,20 @@ def circulant_apply(counts, spec, x, out=None, accumulate=False):
     return y
 
 
+def circulant_apply_static(counts, spec, x, out=None, accumulate=False):
+    """fmpb_circulant_apply_static: circulant_apply without device allocation
+    (its scratch is the library's fixed static array; larger products raise
+    FMPB_EINVAL).  out must be given by callers that cannot allocate either."""
+    c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
+    B = spec.shape[-1]
+    ncell = int(np.prod(c))
+    R = _cvec(x, ncell * B, "x")
+    y = out if out is not None else torch.empty_like(x)
+    check(lib().fmpb_circulant_apply_static(_ptr(c), B, _ptr(spec), R, _ptr(x), _ptr(y), 1 if accumulate else 0,
+                                            _stream()))
+    return y
+
+
 def circulant_apply_f32(counts, spec, x, out=None, accumulate=False):
     """fmpb_circulant_apply_f32: the circulant product in complex FP32 (spectrum, DFT passes, products)."""
     c = _host(list(counts) + [1] * (3 - len(counts)), np.int32)
@@ -426,6 +440,12 @@ def circulant_apply_bf16(counts, spec, x, out=None, accumulate=False):
     check(lib().fmpb_circulant_apply_bf16(_ptr(c), B, _ptr(spec.contiguous()), R, _ptr(x), _ptr(y),
                                           1 if accumulate else 0, _stream()))
     return y
+
+
+def version():
+    """fmpb_version: (major, minor) of the library."""
+    v = lib().fmpb_version()
+    return v >> 16, v & 0xFFFF
 
 
 def kernel_launches() -> int:

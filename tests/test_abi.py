@@ -32,6 +32,22 @@ def test_every_declared_symbol_is_exported_and_bound(L):
     assert sorted(SIGNATURES) == names
 
 
+def test_every_declared_call_has_a_binding_of_the_same_name(L):
+    # the Python binding calls every entry point of the header
+    # (fmpb_last_error feeds its exceptions)
+    import paper_2201_12050_gb300 as gb
+    api_src = open(os.path.join(ROOT, "paper_2201_12050_gb300", "api.py")).read()
+    for n in _declared():
+        if n != "fmpb_last_error":
+            assert re.search(rf"(lib\(\)|self\._lib)\.{n}\b", api_src), n
+    assert gb.version() == (0, 1)
+    # device vectors must be complex128 CUDA tensors: refused before any call
+    import torch
+    x = torch.zeros(4, dtype=torch.complex128)
+    with pytest.raises(TypeError):
+        gb.circulant_apply_static([2, 1, 1], torch.zeros((3, 2, 2), dtype=torch.complex128), x)
+
+
 def test_host_only_calls(L):
     from paper_2201_12050_gb300 import circulant_shape, FmpbError
     assert L.fmpb_version() == (0 << 16) | 1
