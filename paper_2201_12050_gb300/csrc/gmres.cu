@@ -1,12 +1,19 @@
 // Restarted GMRES for R independent right-hand sides sharing each product
 // (Sec. 4: the systems of Eqs. (toeplitzBEM) and (FMPBEMsystem) are solved by
-// GMRES with a relative residual tolerance).  Every vector, the Hessenberg
-// columns and the Givens rotations live on the device in FP64; the Arnoldi
-// step is classical Gram-Schmidt with a second pass whenever the first one
-// removed more than half of ||w||^2 (Kahan-Parlett "twice is enough").  The host sequences launches and
-// reads one residual estimate per RHS per iteration (the only device to host
-// traffic), and enforces the wall-clock limit between launches: no kernel
-// waits on anything.
+// GMRES with a relative residual tolerance).  Everything lives on the device:
+// the Krylov basis as float-float pairs (48-bit significand; FP32 values for
+// the BF16 inner solves), the product vectors, Hessenberg columns, rotations
+// and least-squares update in FP64 (the stored rotations applied to a new
+// column in float-float, as a scan).  The Arnoldi step is DCGS2, classical
+// Gram-Schmidt whose reorthogonalising second pass is folded into the next
+// step's projections (one dots and one update pass over the basis per step),
+// where the operator multiplies basis vectors directly (float-float or FP32)
+// and the raw Hessenberg copy fits; otherwise classical Gram-Schmidt
+// with a second pass whenever the first one removed more than half of
+// ||w||^2 (Kahan-Parlett "twice is enough").  The host sequences launches,
+// reads the convergence flags and residual estimates every few iterations
+// (the only device to host traffic; next_block sets the cadence) and enforces
+// the wall-clock limit between launches: no kernel waits on anything.
 #include <chrono>
 #include <functional>
 
