@@ -16,13 +16,17 @@
 // Grid layout: slot-major, slot f = (fz Py + fy) Px + fx, then R x B (RHS
 // outer, coefficient inner); spectrum [f][b][b'] row-major.
 //
-// Arithmetic: GB300 executes FP64 at 1/58 of its FP32 rate, so every pass
-// (DFTs and block products) runs in float-float arithmetic on the FP32 pipe:
-// values are (hi, lo) FP32 pairs carrying 48 significand bits, products are
-// exact via the fma residual and sums use two-sum.  Intermediate grids and the
-// operator's spectrum are stored as float-float (16 bytes per complex value,
-// the size of complex double); inputs and outputs of the product are complex
-// double.
+// Arithmetic: GB300 executes FP64 at 1/58 of its FP32 rate, so for the FP64
+// operators every pass (DFTs and block products) runs in float-float
+// arithmetic on the FP32 pipe: values are (hi, lo) FP32 pairs carrying 48
+// significand bits, products are exact via the fma residual and sums use
+// two-sum.  Intermediate grids and the spectrum are then stored as
+// float-float (16 bytes per complex value, the size of complex double).  The
+// reduced-precision operators keep an FP32 spectrum (SPEC_F32, FP32 passes)
+// or a realified BF16 one whose frequency products run on the tensor cores
+// (SPEC_BF16; the last forward pass writes their BF16 rows).  Inputs and
+// outputs of the product are complex double, or FP32 vectors for the FP32
+// Krylov basis.
 #include <utility>
 
 #include "common.cuh"

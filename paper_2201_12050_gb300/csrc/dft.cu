@@ -12,7 +12,11 @@
 //   stage B, per k1 < P1: out[k1 + P1 k2] = sum_{n2} Y[n2][k1] w^{P1 n2 k2}             (k2 < P2)
 // with P1, P2 <= 16 chosen to minimise the complex multiply-adds (P2 = 1 is
 // the direct sum).  Only the non-zero inputs are read and only the kept
-// outputs are formed.
+// outputs are formed.  Two more forms need no shared-memory exchange: the
+// direct sum (k_dft_direct, a thread's inputs all in flight at once) and,
+// for FP32 lines of 8, 16 or 32, a radix-2 FFT in registers (k_dft_fft2).
+// A pass runs the model's choice or, for a new line shape, the fastest of
+// the forms it admits, timed once on its first call (the autotuner below).
 //
 // Layout on the GB300: a warp owns 32 consecutive inner indices (the
 // contiguous dimension of every pass), so each of its loads and stores is
