@@ -22,7 +22,7 @@ Contents (each function cites the part of the paper it follows):
   P2M and L2P tables shared by all cells, M2L blocks from the Wigner formula,
   the explicit (unconvolved) operator S + U K V of Sec. 3.2, and an
   independent M2L built by projecting the outgoing wave on a sphere.
-* ``solve``    -- dense and matrix-free GMRES drivers (library primitives).
+* ``solve``    -- the dense solve of reference solutions (a library primitive).
 
 Pins of every part live in ``tests/test_oracle_*.py`` (marked not-gpu).
 """
